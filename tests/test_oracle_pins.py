@@ -1,0 +1,490 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test fixes part of the oracle to a library routine, a closed form, an invariant or a
+brute-force computation, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+import ctypes
+import ctypes.util
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.special import logsumexp
+
+import oracle as O
+from paper_2510_27191_b300 import workloads as WL
+from tests.brute import soft_expectimax
+
+SEEDS = [0x0123456789ABCDEF, 1, 0xFFFFFFFFFFFFFFFF, 0x9E3779B97F4A7C15]
+
+
+# ----------------------------------------------------------------------------------------
+# Philox4x32-10: two independent library implementations of the published generator.
+# ----------------------------------------------------------------------------------------
+def _curand():
+    for name in ("/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")):
+        if name and os.path.exists(name) if name.startswith("/") else name:
+            try:
+                return ctypes.CDLL(name)
+            except OSError:
+                pass
+    return None
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_philox_matches_curand_host_generator(seed):
+    """cuRAND's host Philox4_32_10 generator emits block m from counter (0, 0, m, 0)."""
+    cr = _curand()
+    if cr is None:
+        pytest.skip("libcurand not found")
+    gen = ctypes.c_void_p()
+    assert cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    assert cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+    n_blocks = 512
+    buf = (ctypes.c_uint32 * (4 * n_blocks))()
+    assert cr.curandGenerate(gen, buf, ctypes.c_size_t(4 * n_blocks)) == 0
+    cr.curandDestroyGenerator(gen)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for m in list(range(0, 64)) + [255, 256, 511]:
+        assert O.philox((0, 0, m, 0), key) == list(buf[4 * m:4 * m + 4]), m
+
+
+def test_philox_matches_triton_interpreter():
+    """Triton's philox (interpreter mode, CPU) uses counter (offset, 0, 0, 0)."""
+    script = textwrap.dedent("""
+        import os
+        os.environ["TRITON_INTERPRET"] = "1"
+        import torch, triton, triton.language as tl
+        @triton.jit
+        def k(out_ptr, seed, n: tl.constexpr):
+            offs = tl.arange(0, n)
+            a, b, c, d = tl.randint4x(seed, offs, 10)
+            tl.store(out_ptr + offs * 4 + 0, a)
+            tl.store(out_ptr + offs * 4 + 1, b)
+            tl.store(out_ptr + offs * 4 + 2, c)
+            tl.store(out_ptr + offs * 4 + 3, d)
+        for seed in (%s):
+            out = torch.zeros(64 * 4, dtype=torch.int32)
+            k[(1,)](out, seed, 64)
+            print(seed, *[(v & 0xffffffff) for v in out.tolist()])
+    """ % ", ".join(str(s) for s in SEEDS[:2]))
+    try:
+        res = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True,
+                             timeout=600)
+    except Exception as e:  # pragma: no cover
+        pytest.skip(f"triton interpreter unavailable: {e}")
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr[-300:])
+    for line in res.stdout.strip().splitlines():
+        vals = [int(v) for v in line.split()]
+        seed, words = vals[0], vals[1:]
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for i in range(64):
+            assert O.philox((i, 0, 0, 0), key) == words[4 * i:4 * i + 4]
+
+
+def test_philox_statistics():
+    """Uniform byte histogram (chi-square) and 32-bit word moments over 2^16 blocks."""
+    key = (0x12345678, 0x9ABCDEF0)
+    words = np.array([O.philox((i, 7, i * 3, 1), key) for i in range(1 << 14)],
+                     dtype=np.uint64).ravel()
+    u = words / 2.0**32
+    n = len(u)
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / n)
+    by = np.concatenate([(words >> s) & 0xFF for s in (0, 8, 16, 24)]).astype(np.int64)
+    chi2 = stats.chisquare(np.bincount(by, minlength=256)).pvalue
+    assert chi2 > 1e-4
+    # counter sensitivity: neighbouring counters in each word give unrelated outputs
+    base = O.philox((5, 6, 7, 8), key)
+    for w in range(4):
+        c = [5, 6, 7, 8]
+        c[w] ^= 1
+        other = O.philox(c, key)
+        flips = sum(bin(a ^ b).count("1") for a, b in zip(base, other))
+        assert 40 < flips < 88
+
+
+def test_uniform_mapping_exact_and_open():
+    """u = (2 (x >> 9) + 1) 2^-24 lies in (0, 1) and is exact in float32."""
+    for x in (0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF, 0x12345678):
+        u = O.uniform(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+    assert O.uniform(0) == 2.0**-24
+    assert O.uniform(0xFFFFFFFF) == 1.0 - 2.0**-24
+
+
+def test_box_muller_moments():
+    """Box-Muller output is N(0,1), the pair uncorrelated (CLT bands over 2^17 pairs)."""
+    key = (3, 4)
+    g = []
+    for i in range(1 << 15):
+        w = O.philox((i, 0, 0, 0), key)
+        g.extend(O.box_muller(w[0], w[1]))
+        g.extend(O.box_muller(w[2], w[3]))
+    g = np.array(g)
+    n = len(g)
+    assert abs(g.mean()) < 5 / math.sqrt(n)
+    assert abs(g.var() - 1) < 5 * math.sqrt(2 / n)
+    assert abs(stats.skew(g)) < 5 * math.sqrt(6 / n)
+    assert abs(stats.kurtosis(g)) < 5 * math.sqrt(24 / n)
+    assert abs(np.corrcoef(g[0::2], g[1::2])[0, 1]) < 5 / math.sqrt(n / 2)
+    assert stats.kstest(g, "norm").pvalue > 1e-4
+
+
+# ----------------------------------------------------------------------------------------
+# NAV2D model pieces.
+# ----------------------------------------------------------------------------------------
+def test_nav_step_noise_moments_and_rewards():
+    """Interior steps move by delta_a + N(0, 0.1^2 I); reward -1 outside the goal disc."""
+    key = (11, 12)
+    deltas = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+    for a, (dx, dy) in enumerate(deltas):
+        mv = []
+        for i in range(4000):
+            w = O.philox((i, a, 0, 0), key)
+            ox, oy, r = O.nav_step(5.0, 5.0, a, w[0], w[1])
+            assert r == -1.0
+            mv.append((ox - 5.0, oy - 5.0))
+        mv = np.array(mv)
+        n = len(mv)
+        assert np.all(np.abs(mv.mean(0) - (dx, dy)) < 5 * 0.1 / math.sqrt(n))
+        assert np.all(np.abs(mv.std(0) - 0.1) < 5 * 0.1 / math.sqrt(2 * n))
+
+
+def test_nav_step_clamp_goal_and_absorbing():
+    w = O.philox((0, 0, 0, 0), (1, 2))
+    ox, oy, r = O.nav_step(9.95, 0.0, 0, w[0], w[1])   # pushed past the east wall
+    assert 0.0 <= ox <= 10.0 and 0.0 <= oy <= 10.0
+    # find a draw that lands in the goal from (1.0, 0.1) moving west
+    hits = 0
+    for i in range(200):
+        w = O.philox((i, 1, 0, 0), (1, 2))
+        ox, oy, r = O.nav_step(1.0, 0.1, 1, w[0], w[1])
+        inside = ox * ox + oy * oy <= 0.25
+        assert r == (100.0 if inside else -1.0)
+        hits += inside
+    assert hits > 0
+    # a terminal state does not move and earns nothing
+    ox, oy, r = O.nav_step(0.2, 0.1, 0, 123, 456)
+    assert (ox, oy, r) == (0.2, 0.1, 0.0)
+
+
+def test_nav_loglik_is_bivariate_normal_logpdf():
+    """log Z(o|s') equals scipy's isotropic normal log-density with sigma 0.5|x-9|+0.05."""
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        sx, sy = rng.uniform(0, 10, 2)
+        ox, oy = rng.normal(0, 3, 2) + (sx, sy)
+        sg = 0.5 * abs(sx - 9) + 0.05
+        ref = stats.multivariate_normal.logpdf([ox, oy], mean=[sx, sy], cov=sg * sg * np.eye(2))
+        assert O.nav_loglik(sx, sy, ox, oy) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def test_nav_heuristic_is_discounted_return_of_the_greedy_path():
+    """At an integer number m of moves the heuristic is sum_t gamma^t r_t for
+    r = (-1, ..., -1, +100) of length m, and 0 at terminal states."""
+    gamma = 0.95
+    for m in range(1, 15):
+        ret = sum(-(gamma ** t) for t in range(m - 1)) + 100 * gamma ** (m - 1)
+        x = (m + 0.5) / 2
+        assert O.nav_heuristic(x, x, gamma) == pytest.approx(ret, rel=1e-12)
+    assert O.nav_heuristic(0.1, 0.2, gamma) == 0.0
+    # continuity across the clamp at one move
+    assert O.nav_heuristic(0.75, 0.75 + 1e-9, gamma) == pytest.approx(100.0, rel=1e-9)
+
+
+# ----------------------------------------------------------------------------------------
+# GRID model pieces.
+# ----------------------------------------------------------------------------------------
+def _grid_model():
+    rx, ry = WL.grid_layout(1)
+    return O.make_model(O.GRID, rock_x=rx, rock_y=ry), rx, ry
+
+
+def test_grid_transitions_hand_checked():
+    m, rx, ry = _grid_model()
+    s0 = int(WL.pack_grid_state(0b10110101, 4, 6)[()])
+    assert O.grid_step(m, s0, 0) == (int(WL.pack_grid_state(0b10110101, 5, 6)[()]), 0.0)
+    assert O.grid_step(m, s0, 1) == (int(WL.pack_grid_state(0b10110101, 3, 6)[()]), 0.0)
+    assert O.grid_step(m, s0, 2) == (int(WL.pack_grid_state(0b10110101, 4, 7)[()]), 0.0)
+    assert O.grid_step(m, s0, 3) == (int(WL.pack_grid_state(0b10110101, 4, 5)[()]), 0.0)
+    # walls: west at x=0, north at y=10, south at y=0 stay put with no reward
+    for (x, y, a) in ((0, 3, 1), (3, 10, 2), (3, 0, 3)):
+        s = int(WL.pack_grid_state(7, x, y)[()])
+        assert O.grid_step(m, s, a) == (s, 0.0)
+    # east from x=10 exits: terminal, +10, absorbing afterwards
+    s = int(WL.pack_grid_state(7, 10, 4)[()])
+    e, r = O.grid_step(m, s, 0)
+    assert r == 10.0 and e == int(WL.pack_grid_state(7, 11, 4, terminal=True)[()])
+    for a in range(13):
+        assert O.grid_step(m, e, a) == (e, 0.0)
+    # collect on rock r: +10 and clear when good, -10 and keep when bad; 0 off rocks
+    for r_i in range(8):
+        good = int(WL.pack_grid_state(0xFF, rx[r_i], ry[r_i])[()])
+        out, rew = O.grid_step(m, good, 4)
+        assert rew == 10.0 and out == good & ~(1 << r_i)
+        bad = int(WL.pack_grid_state(0xFF & ~(1 << r_i), rx[r_i], ry[r_i])[()])
+        assert O.grid_step(m, bad, 4) == (bad, -10.0)
+    off = [(x, y) for x in range(11) for y in range(11) if (x, y) not in set(zip(rx, ry))][0]
+    s = int(WL.pack_grid_state(0xFF, *off)[()])
+    assert O.grid_step(m, s, 4) == (s, 0.0)
+    # sensing leaves the state alone and costs nothing
+    for a in range(5, 13):
+        assert O.grid_step(m, s0, a) == (s0, 0.0)
+
+
+def test_grid_sense_accuracy_and_thresholds():
+    m, rx, ry = _grid_model()
+    assert O.grid_acc(0) == 1.0 and O.grid_threshold(0) == 2**32
+    for d2 in range(1, 222):
+        acc = 0.5 + 0.5 * math.exp(-math.sqrt(d2) / 4)
+        assert O.grid_acc(d2) == pytest.approx(acc, rel=1e-15)
+        assert O.grid_threshold(d2) == math.floor(acc * 2**32)
+        assert O.grid_threshold(d2) <= O.grid_threshold(d2 - 1)
+    # likelihoods form a distribution over {NULL, good, bad} for every state and action
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        s = int(WL.pack_grid_state(rng.integers(256), rng.integers(11), rng.integers(11))[()])
+        for a in range(13):
+            tot = sum(math.exp(O.grid_loglik(m, s, a, o)) for o in range(3))
+            assert tot == pytest.approx(1.0, abs=1e-12)
+    # the sampled sense outcome is correct with frequency acc (rock 0 seen from 3 cells away)
+    x0 = max(0, rx[0] - 3)
+    s = int(WL.pack_grid_state(1, x0, ry[0])[()])
+    d2 = (x0 - rx[0]) ** 2
+    key = (9, 9)
+    n = 20000
+    good = sum(O.grid_draw_obs(m, s, 5, O.philox((i, 0, 0, 0), key)[0]) == 1 for i in range(n))
+    acc = O.grid_acc(d2)
+    assert abs(good / n - acc) < 5 * math.sqrt(acc * (1 - acc) / n)
+    # at distance 0 the sensor never lies
+    s = int(WL.pack_grid_state(1, rx[0], ry[0])[()])
+    assert all(O.grid_draw_obs(m, s, 5, w) == 1 for w in (0, 2**31, 2**32 - 1))
+
+
+# ----------------------------------------------------------------------------------------
+# The backup's closed form (Eq. 1 with one Eq. 3 update).
+# ----------------------------------------------------------------------------------------
+def test_belief_value_limits_and_invariants():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        A = int(rng.integers(2, 14))
+        q = rng.normal(0, 10, A)
+        pi = rng.uniform(0.05, 1, A)
+        lpi = np.log(pi / pi.sum())
+        # eta -> 0: max Q + eta log pibar(a*) <= V <= max Q
+        for eta in (1e-1, 1e-2, 1e-3):
+            v = O.belief_value(q, lpi, eta)
+            a_star = int(np.argmax(q))
+            assert q.max() + eta * lpi[a_star] - 1e-9 <= v <= q.max() + 1e-9
+        # Jensen: V >= sum pibar Q for every eta, with equality as eta -> infinity
+        for eta in (0.1, 1.0, 10.0, 1e6):
+            assert O.belief_value(q, lpi, eta) >= float(np.exp(lpi) @ q) - 1e-9
+        assert O.belief_value(q, lpi, 1e8) == pytest.approx(float(np.exp(lpi) @ q), abs=1e-5)
+        # equal Q under any pibar: V = Q exactly (up to rounding)
+        c = float(rng.normal(0, 50))
+        assert O.belief_value(np.full(A, c), lpi, 0.7) == pytest.approx(c, abs=1e-12)
+        # agrees with scipy's logsumexp
+        assert O.belief_value(q, lpi, 0.3) == pytest.approx(0.3 * logsumexp(lpi + q / 0.3),
+                                                             rel=1e-13)
+
+
+# ----------------------------------------------------------------------------------------
+# Whole estimator: exact where there is no sampling at all.
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("eta", [0.05, 0.5, 2.0, 20.0])
+@pytest.mark.parametrize("pi", [None, (0.8, 0.2)])
+def test_toy2_enumerate_equals_brute_force_soft_expectimax(depth, eta, pi):
+    """Deterministic T, enumerated O, the two states as weighted root particles: the tree
+    estimate is the exact Reference-Based value (Eq. 1-2), root Q and action included."""
+    b0 = np.array([0.6, 0.4])
+    kw = dict(branch_mode=O.ENUMERATE)
+    lpi = np.log([0.5, 0.5])
+    if pi is not None:
+        kw.update(pi_mode=O.PI_FIXED, pi_fixed=pi)
+        lpi = np.log(np.array(pi) / sum(pi))
+    m = O.make_model(O.TOY2, **kw)
+    r = O.plan(m, 2, depth, 2, eta, 0.95, 42, root_s=np.array([0, 1]), root_w=b0)
+    assert r["status"] == O.OK
+    v, q = soft_expectimax(b0, depth, eta, 0.95, lpi)
+    assert r["v_root"] == pytest.approx(v, abs=1e-12)
+    np.testing.assert_allclose(r["q_root"], q, atol=1e-12)
+    assert r["action"] == int(np.argmax(q + eta * lpi))
+    assert np.exp(lpi + q / eta - v / eta) == pytest.approx(r["policy"], abs=1e-12)
+
+
+def test_toy2_small_eta_tends_to_hard_expectimax():
+    b0 = np.array([0.3, 0.7])
+    m = O.make_model(O.TOY2, branch_mode=O.ENUMERATE)
+    hard, _ = soft_expectimax(b0, 3, 1.0, 0.9, np.log([0.5, 0.5]), hard=True)
+    prev = None
+    for eta in (0.1, 0.01, 0.001):
+        r = O.plan(m, 2, 3, 2, eta, 0.9, 1, root_s=np.array([0, 1]), root_w=b0)
+        gap = hard - r["v_root"]
+        assert -1e-12 <= gap <= 3 * eta * math.log(2) + 1e-12   # one log 2 per level
+        if prev is not None:
+            assert gap <= prev + 1e-12
+        prev = gap
+
+
+def test_toy2_extra_enumerate_branch_has_zero_weight():
+    """W > |O|: the surplus branch has omega = 0 and leaves every value unchanged."""
+    b0 = np.array([0.6, 0.4])
+    m = O.make_model(O.TOY2, branch_mode=O.ENUMERATE)
+    r2 = O.plan(m, 2, 2, 2, 1.0, 0.95, 3, root_s=np.array([0, 1]), root_w=b0)
+    r3 = O.plan(m, 2, 2, 3, 1.0, 0.95, 3, root_s=np.array([0, 1]), root_w=b0)
+    assert r3["v_root"] == pytest.approx(r2["v_root"], abs=1e-12)
+    assert np.all(np.isneginf(r3["lomega"][1][2::3]))
+
+
+def test_toy2_sampled_depth1_converges_to_exact():
+    """SAMPLE mode, N = 2^16 particles drawn from b0, depth 1: Q(root, a) is the mean
+    immediate reward, within a 5-sigma CLT band of the exact value."""
+    b0 = (0.6, 0.4)
+    s, w = WL.toy2_root_sampled(1 << 16, 5, b0)
+    m = O.make_model(O.TOY2)
+    r = O.plan(m, len(s), 1, 2, 1.0, 0.95, 9, root_s=s, root_w=w)
+    _, q = soft_expectimax(b0, 1, 1.0, 0.95, np.log([0.5, 0.5]))
+    sd_r = math.sqrt(0.6 * 0.4) * 2.0 / math.sqrt(len(s))        # reward 1 vs -1 for a=0
+    assert abs(r["q_root"][0] - q[0]) < 5 * sd_r
+    assert r["q_root"][1] == pytest.approx(-0.1, abs=1e-12)
+
+
+def test_toy2_sampled_many_branches_tends_to_exact_depth2():
+    """SAMPLE mode with many observation branches: the self-normalised importance average
+    over branches estimates E_o V(tau(b,a,o)); with W = 48 and N = 4096 the root Q lies
+    within a loose band of the exact value."""
+    b0 = (0.6, 0.4)
+    s, w = WL.toy2_root_sampled(4096, 6, b0)
+    m = O.make_model(O.TOY2)
+    r = O.plan(m, len(s), 2, 48, 1.0, 0.95, 11, root_s=s, root_w=w, outputs=False)
+    assert r["status"] == O.OK
+    _, q = soft_expectimax(b0, 2, 1.0, 0.95, np.log([0.5, 0.5]))
+    np.testing.assert_allclose(r["q_root"], q, atol=0.1)
+
+
+def test_sampled_branch_weights_have_unit_mean():
+    """omega_k = p(o_k)/q(o_k) is an importance ratio of the uniform-index proposal, so its
+    average over many branches of a weighted node tends to 1."""
+    s, w = WL.grid_root(512, 3, weights="random")
+    rx, ry = WL.grid_layout(2)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    sense = []
+    for seed in range(1, 9):
+        r = O.plan(m, len(s), 1, 64, 1.0, 0.95, seed, root_s=s, root_w=w)
+        assert r["status"] == O.OK
+        om = np.exp(r["lomega"][1]).reshape(13, 64)
+        np.testing.assert_allclose(om[:5], 1.0, atol=1e-12)  # NULL observations: omega = 1
+        sense.append(om[5:].ravel())
+    sense = np.concatenate(sense)
+    assert abs(sense.mean() - 1.0) < 5 * sense.std() / math.sqrt(sense.size)
+    # uniform root weights: omega = 1 exactly for every branch
+    s, _ = WL.grid_root(512, 3)
+    r = O.plan(m, len(s), 1, 5, 1.0, 0.95, 13, root_s=s)
+    np.testing.assert_allclose(np.exp(r["lomega"][1]), 1.0, atol=1e-12)
+
+
+def test_all_terminal_child_has_zero_value():
+    """From x = 10 moving east every particle exits: Q(root, east) = 10 + gamma * 0."""
+    rx, ry = WL.grid_layout(1)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    bits = np.arange(64) % 256
+    s = WL.pack_grid_state(bits, 10, 2)
+    r = O.plan(m, len(s), 2, 3, 1.0, 0.95, 4, root_s=s)
+    assert r["q_root"][0] == pytest.approx(10.0, abs=1e-12)
+    for k in range(3):
+        assert r["V"][1][k] == 0.0
+        np.testing.assert_array_equal(r["Q"][1][k], 0.0)
+
+
+def test_depth0_is_weighted_mean_heuristic():
+    x, y, w = WL.nav_root(300, 8, weights="random")
+    m = O.make_model(O.NAV2D)
+    r = O.plan(m, 300, 0, 4, 1.0, 0.9, 1, root_x=x, root_y=y, root_w=w)
+    x64, y64, w64 = x.astype(float), y.astype(float), w.astype(float)
+    w64 = np.where(x64 ** 2 + y64 ** 2 <= 0.25, 0.0, w64)
+    w64 /= w64.sum()
+    h = np.array([O.nav_heuristic(a, b, 0.9) for a, b in zip(x64, y64)])
+    assert r["v_root"] == pytest.approx(float(w64 @ h), rel=1e-12)
+    np.testing.assert_allclose(r["q_root"], r["v_root"])
+    assert r["action"] == 0
+
+
+def test_degenerate_root_is_reported():
+    m = O.make_model(O.NAV2D)
+    x = np.array([0.1, 0.2], dtype=np.float32)
+    r = O.plan(m, 2, 2, 2, 1.0, 0.9, 1, root_x=x, root_y=x)
+    assert r["status"] == O.E_DEGENERATE
+
+
+def test_subtree_mode_reproduces_full_tree_values():
+    """Expanding only the subtree below a path gives the same node values as the full tree
+    (the Philox counters are keyed by global node index)."""
+    x, y, _ = WL.nav_root(64, 2)
+    m = O.make_model(O.NAV2D, pi_mode=O.PI_NAV_DIST, pi_temp=2.0)
+    full = O.plan(m, 64, 3, 2, 0.5, 0.95, 5, root_x=x, root_y=y)
+    path = (5, 3)
+    sub = O.plan(m, 64, 3, 2, 0.5, 0.95, 5, root_x=x, root_y=y, path=path)
+    g2 = path[0] * 8 + path[1]
+    assert sub["V"][2][0] == full["V"][2][g2]
+    np.testing.assert_array_equal(sub["Q"][2][0], full["Q"][2][g2])
+    np.testing.assert_array_equal(sub["V"][3], full["V"][3][g2 * 8:(g2 + 1) * 8])
+    assert sub["rbar"][1][0] == full["rbar"][1][path[0]]
+
+
+# ----------------------------------------------------------------------------------------
+# SIR belief update.
+# ----------------------------------------------------------------------------------------
+def test_belief_update_is_bayes_posterior_without_resampling():
+    """Deterministic TOY2 transition, no resampling: weights are the exact posterior."""
+    m = O.make_model(O.TOY2)
+    s = np.array([0, 1, 1, 0, 1], dtype=np.int32)
+    w = np.array([0.3, 0.2, 0.2, 0.2, 0.1])
+    rc, out = O.belief_update(m, np.log(w), 1, 0, seed=1, t=0, s=s)
+    assert rc == O.OK and not out["resampled"]
+    sp = 1 - s
+    like = np.where(sp == 0, 0.85, 0.15)
+    post = w * like / (w * like).sum()
+    np.testing.assert_allclose(np.exp(out["lw"]), post, atol=1e-14)
+    np.testing.assert_array_equal(out["s"], sp)
+    assert out["ess"] == pytest.approx(1 / np.sum(post ** 2), rel=1e-12)
+
+
+def test_systematic_resampling_copy_counts():
+    """Systematic resampling copies particle k either floor(N w_k) or ceil(N w_k) times."""
+    rx, ry = WL.grid_layout(1)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    N = 1000
+    s, _ = WL.grid_root(N, 4)
+    # sense rock 0 from its own cell: zero-likelihood particles force a resample
+    s = WL.pack_grid_state(np.asarray(s) & 0xFF, rx[0], ry[0])
+    rng = np.random.default_rng(2)
+    w = rng.uniform(0.1, 1, N)
+    w /= w.sum()
+    rc, out = O.belief_update(m, np.log(w), 5, 1, seed=3, t=7, s=s)
+    assert rc == O.OK
+    like = np.where((np.asarray(s) & 1) == 1, 1.0, 0.0)
+    post = w * like / (w * like).sum()
+    assert out["resampled"]
+    counts = np.bincount(out["ancestors"], minlength=N)
+    assert np.all(counts >= np.floor(N * post) - 1e-9)
+    assert np.all(counts <= np.ceil(N * post) + 1e-9)
+    assert np.all(counts[like == 0] == 0)
+    np.testing.assert_allclose(out["lw"], -math.log(N))
+
+
+def test_belief_update_zero_likelihood_is_degenerate():
+    rx, ry = WL.grid_layout(1)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    s = WL.pack_grid_state(np.zeros(8, dtype=np.int64), rx[0], ry[0])   # rock 0 bad everywhere
+    rc, _ = O.belief_update(m, np.full(8, -math.log(8)), 5, 1, seed=1, t=0, s=s)
+    assert rc == O.E_DEGENERATE
