@@ -1,0 +1,346 @@
+"""Benchmark of the VOPP planning hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vopp|reference]
+                    [--workload nav1024_d4 | nav256_d3 | grid2048_d5]
+
+One step = one full plan (root preparation, every level's expansion, the fused leaf
+expansion and backup, the FP64 root and the action choice) of the default workload: a
+2-D navigation POMDP with 1024 root particles uniform in [0,10]^2, depth 4, 4 actions x 4
+observation branches (65,536 leaves, 7.16e7 particle-steps by the sum_l (A W)^l N rule),
+eta = 0.5, gamma = 0.95, distance-softmax reference policy of temperature 2.  Inputs are
+synthetic and seeded; the root particles are resident in HBM when the timed region starts.
+
+`value` is particle-steps/s over the device-timed steps (CUDA events on the library's
+stream around each plan, L2 flushed before each step by writing 256 MB).  `e2e` repeats the
+measurement through the same C ABI with host root buffers (host->device copy of the inputs
+and device->host copy of the result inside the timed region).  N > 1 runs independent
+plans per rank (different seeds; no collective on the data path) and reports the
+whole-job aggregate over max-over-ranks time.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this method has) on a
+bounded sample of the same workload, on the host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_27191_b300 import workloads as WL  # noqa: E402
+
+METRIC = "particle-steps/s and plans/s at <=1e-4 rel err; p50/p99 plan latency (served vs plain)"
+UNIT = "particle-steps/s"
+
+WORKLOADS = {
+    "nav1024_d4": WL.CONFIG2,
+    "nav256_d3": WL.CONFIG1,
+    "grid2048_d5": WL.CONFIG3,
+}
+
+# Leaf-kernel roofline: issue-bound FP32/INT/SFU arithmetic.  Algorithmic instruction count
+# per particle-step of the fused leaf step (counted in the design notes) and the issue peak
+# of the B300: 148 SMs x 4 schedulers x 32 lanes per clock at the maximum SM clock.
+ALG_INSTR_PER_STEP = {WL.NAV2D: 106.0, WL.GRID: 52.0, WL.TOY2: 40.0}
+SMS = 148
+LANES_PER_CLK = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus and world > 1:
+        raise SystemExit(f"WORLD_SIZE {world} != --gpus {n_gpus}")
+    return rank, world, local
+
+
+def run_reference(args, spec, rank, world):
+    """FP64 oracle on the host: each step plans one level-1 subtree (1/(A W) of the tree)."""
+    import oracle as O
+    if rank != 0:
+        return
+    m = O.make_model(spec.kind, pi_mode=spec.pi_mode, pi_temp=spec.pi_temp,
+                     rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
+                     rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None)
+    root = _root_arrays(spec)
+    AW = spec.A * spec.W
+    steps_per_sample = sum(AW ** l for l in range(1, spec.D)) * spec.N + spec.N
+
+    def sample(i):
+        path = (i % AW,)
+        kw = dict(root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"))
+        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=path,
+                   outputs=False, **kw)
+        return r["particle_steps"]
+
+    for i in range(args.warmup):
+        sample(i)
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(args.steps):
+        done += sample(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = done / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(spec, args),
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                            "sample": f"one level-1 subtree per step ({steps_per_sample} "
+                                      f"particle-steps, 1/{AW} of the plan), single thread"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def _root_arrays(spec):
+    if spec.kind == WL.NAV2D:
+        x, y, _ = WL.nav_root(spec.N, spec.root_seed)
+        return dict(x=x, y=y)
+    s, _ = WL.grid_root(spec.N, spec.root_seed)
+    return dict(s=s)
+
+
+def _config(spec, args):
+    return {"workload": f"{WL.KIND_NAMES[spec.kind]} N={spec.N} D={spec.D} A={spec.A} W={spec.W} "
+                        f"eta={spec.eta} gamma={spec.gamma} pi={'softmax(-dist/2)' if spec.pi_mode == WL.PI_NAV_SOFTMAX_DIST else 'uniform'}",
+            "particle_steps_per_plan": spec.steps, "leaves": (spec.A * spec.W) ** spec.D,
+            "root_particles": spec.N, "depth": spec.D, "branches": spec.A * spec.W,
+            "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas{args.gpus}"}
+
+
+def cpu_baseline(spec, budget_s=20.0):
+    """The oracle timed as it stands on the host (one thread) over a bounded sample."""
+    import oracle as O
+    m = O.make_model(spec.kind, pi_mode=spec.pi_mode, pi_temp=spec.pi_temp,
+                     rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
+                     rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None)
+    root = _root_arrays(spec)
+    AW = spec.A * spec.W
+    t0 = time.perf_counter()
+    done, n = 0, 0
+    while time.perf_counter() - t0 < budget_s and n < AW:
+        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(n,),
+                   outputs=False, root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"))
+        done += r["particle_steps"]
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"kind": "oracle", "value": done / dt, "unit": UNIT, "cores": 1,
+            "sample": f"{n} of {AW} level-1 subtrees of the same plan ({done} particle-steps), "
+                      f"FP64, single thread, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vopp", choices=["vopp", "reference"])
+    ap.add_argument("--workload", default="nav1024_d4", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, spec, rank, world)
+        return
+
+    import torch
+    from paper_2510_27191_b300 import vopp as V
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    ctx = V.vopp_ctx_create(local, 0, stream.cuda_stream)
+    model = V.vopp_create_model(ctx, V.make_desc(spec.kind, pi_mode=spec.pi_mode,
+                                                 pi_temp=spec.pi_temp,
+                                                 rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
+                                                 rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None))
+    root = _root_arrays(spec)
+    host_states = (np.concatenate([root["x"], root["y"]]).astype(np.float32) if spec.kind == WL.NAV2D
+                   else root["s"].astype(np.int32))
+    dev_states = torch.from_numpy(host_states).cuda()
+    pinned = torch.from_numpy(host_states).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    seeds = [spec.seed + 1000 * rank + i for i in range(args.warmup + args.steps)]
+
+    def plan(states, seed):
+        return V.vopp_plan(model, states, None, spec.N, spec.D, spec.W, spec.eta, spec.gamma,
+                           None, seed)
+
+    def timed_pass(states, n_steps, seed0):
+        times, res = [], None
+        for i in range(n_steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = plan(states, seeds[(seed0 + i) % len(seeds)])
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return times, res
+
+    for i in range(args.warmup):
+        plan(dev_states, seeds[i])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    V.vopp_ctx_reset_kernel_times(ctx)
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        times, last = timed_pass(dev_states, args.steps, args.warmup)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    counters = V.vopp_ctx_counters(ctx)
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = spec.steps * args.steps * world
+    value = units / (total_ms / 1e3)
+    lat = np.array(times)
+
+    # roofline of the dominant kernel (the fused leaf expansion), per-kernel events
+    V.vopp_ctx_set_timing(ctx, True)
+    V.vopp_ctx_reset_kernel_times(ctx)
+    timed_pass(dev_states, args.steps, args.warmup)
+    kt = V.vopp_ctx_kernel_times(ctx)
+    V.vopp_ctx_set_timing(ctx, False)
+    leaf_ms, leaf_n = kt["leaf"]
+    leaf_avg_s = leaf_ms / max(leaf_n, 1) / 1e3
+    AW = spec.A * spec.W
+    leaf_steps = (AW ** spec.D + (AW ** (spec.D - 1) if spec.D >= 2 else 0)) * spec.N
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2032.0))
+    peak_ops = SMS * LANES_PER_CLK * sm_max * 1e6
+    achieved_ops = ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_avg_s
+    total_kernel_ms = sum(v[0] for v in kt.values())
+
+    # end to end through the C ABI with host buffers
+    V.vopp_ctx_reset_kernel_times(ctx)
+    e2e_times, _ = timed_pass(pinned.numpy(), args.steps, args.warmup)
+    c2 = V.vopp_ctx_counters(ctx)
+    e2e_ms = float(sum(e2e_times))
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded root particles; no datasets)",
+            "config": _config(spec, args),
+            "plans_per_s": args.steps * world / (total_ms / 1e3),
+            "nodes_per_s": (sum(AW ** l for l in range(spec.D + 1))) * args.steps * world / (total_ms / 1e3),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "wall_s": t_wall,
+            "gpu_launches": int(counters["launches"]),
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(c2["h2d_bytes"] // max(args.steps, 1)),
+                    "d2h_bytes_per_step": int(c2["d2h_bytes"] // max(args.steps, 1))},
+            "roofline": {"kernel": "k_leaf", "bound": "alu", "achieved": achieved_ops / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "Tinstr/s",
+                         "frac": achieved_ops / peak_ops, "traffic": None,
+                         "peak_source": f"148 SMs x 128 lanes/clk x {sm_max:.0f} MHz ({pk_src} max clock)",
+                         "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
+                         "units_per_launch": leaf_steps, "avg_launch_ms": leaf_avg_s * 1e3,
+                         "share_of_step": leaf_ms / max(total_kernel_ms, 1e-9)},
+            "kernels_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items() if v[1]},
+            "clocks": clk.summary(),
+            "result": {"action": int(last["action"]), "v_root": last["v_root"]},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(spec)
+        print(json.dumps(out))
+    V.vopp_model_destroy(model)
+    V.vopp_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

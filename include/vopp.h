@@ -1,0 +1,257 @@
+/*
+ * vopp.h -- C ABI of libvopp, a B300 (sm_103a) implementation of the data-parallel hot path
+ * of VOPP, the Vectorized Online POMDP Planner ("Vectorized Online POMDP Planning",
+ * arXiv 2510.27191).
+ *
+ * What one plan computes (paper Sec. III):
+ *   - Alg. 1: sample the root belief (here: the caller's weighted particle set), run one
+ *     search episode, back it up, return argmax_a Psi(root, a).
+ *   - Alg. 2 (forward search), full-width form: every belief node expands every action a and
+ *     W observation branches per action.  Each branch steps ALL N particles of its parent
+ *     through the generative model G(s,a) -> (s', o, r) (Sec. III-B), draws one
+ *     observation o_k from a representative particle (or enumerates o_k = k), and reweights
+ *     the particles by Z(o_k | s', a).  Leaves (depth D) take the weighted mean of a
+ *     state-based heuristic (Alg. 2 ValueHeuristic).
+ *   - Alg. 3 (backup), closed form of one Eq. 3 preference update from the reference
+ *     policy pibar: Q(b,a) = (1/W) sum_k rbar_k + gamma * sum_k omega_k V_k / sum_k omega_k,
+ *     V(b) = eta * log sum_a pibar(a|b) exp(Q(b,a)/eta)  (Eq. 1; eta is the temperature,
+ *     the paper's eta is 1/eta).
+ *   - Sec. III-B: the belief update tau(b,a,o) is a sequential importance resampling filter.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an int status (VOPP_OK or a negative VOPP_E_* code); no C++
+ *     exception crosses the ABI.  vopp_last_error() gives a thread-local message for the most
+ *     recent failure on the calling thread.
+ *   - Caller buffers are only read or written during the call; the library keeps no pointer
+ *     to them after it returns.  Pointers are host pointers unless the call takes
+ *     ptr_flags with VOPP_PTR_DEVICE set, in which case they are device pointers on the
+ *     context's device (e.g. a torch tensor's data_ptr()).
+ *   - The library owns all device memory it allocates (per-context arena, models, agents);
+ *     destroy functions release it.
+ *   - All device work is issued on the context's CUDA stream (given at creation; 0 = the
+ *     legacy default stream).  Blocking calls synchronise that stream before returning.
+ *   - Kernels never trap: device-side failures (zero-mass beliefs, exhausted waits) are
+ *     reported through a device status word that the host reads back.
+ *   - A context, and every model and agent created from it, must be used by one host thread
+ *     at a time.
+ */
+#ifndef VOPP_H
+#define VOPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VOPP_API __attribute__((visibility("default")))
+#else
+#define VOPP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------- */
+#define VOPP_OK 0
+#define VOPP_E_INVALID (-1)    /* an argument is out of range or a pointer is NULL        */
+#define VOPP_E_NOMEM (-2)      /* a device or host allocation failed                      */
+#define VOPP_E_BUDGET (-3)     /* the plan's predicted footprint exceeds the HBM budget   */
+#define VOPP_E_CUDA (-4)       /* a CUDA runtime call failed (message in vopp_last_error) */
+#define VOPP_E_TIMEOUT (-5)    /* a bounded device-side wait gave up                      */
+#define VOPP_E_DEGENERATE (-6) /* the (root or updated) belief has zero total weight      */
+#define VOPP_E_BUSY (-7)       /* the ticket's plan has not completed yet                 */
+
+/* ---- model kinds, branch modes, reference policies ----------------------------------- */
+#define VOPP_NAV2D 0 /* continuous 2-D navigation, state (x,y) in [0,10]^2, 4 actions     */
+#define VOPP_GRID 1  /* 11x11 grid sensing, packed int32 state, 13 actions, obs {0,1,2}  */
+#define VOPP_TOY2 2  /* 2 states, 2 actions, 2 observations (test model)                  */
+
+#define VOPP_BRANCH_SAMPLE 0    /* o_k drawn from a uniformly chosen representative      */
+#define VOPP_BRANCH_ENUMERATE 1 /* branch k is observation k (discrete models, W >= |O|) */
+
+#define VOPP_PI_UNIFORM 0  /* pibar(a|b) = 1/A                                            */
+#define VOPP_PI_FIXED 1    /* pibar(a|b) = pi_fixed[a] / sum pi_fixed                       */
+#define VOPP_PI_NAV_DIST 2 /* pibar(a|b) ~ exp(-|clamp(mu_b + delta_a)| / pi_temp), NAV2D   */
+
+#define VOPP_PTR_DEVICE 1u /* ptr_flags bit: the state/weight pointers are device pointers */
+
+/* result flags */
+#define VOPP_FLAG_DEGENERATE_BRANCH 1u /* some action had sum_k omega_k = 0 (future := 0) */
+#define VOPP_FLAG_FP64_ROOT 2u         /* the root backup ran in FP64                     */
+
+/* tree detail kept on the device after a plan (vopp_ctx_set_tree_detail) */
+#define VOPP_TREE_MINIMAL 0 /* only what the backup needs                                 */
+#define VOPP_TREE_FULL 1    /* also leaf-level branch stats, representatives, observations */
+
+/* tree fields readable with vopp_tree_read (per level, indexed by node or child) */
+#define VOPP_FIELD_V 0      /* float  V[node]               levels 0..D (D: leaves, FULL)  */
+#define VOPP_FIELD_Q 1      /* float  Q[node][A]            levels 0..D-1                  */
+#define VOPP_FIELD_RBAR 2   /* float  rbar[child]           levels 1..D (D only if FULL)   */
+#define VOPP_FIELD_LOMEGA 3 /* float  log omega[child]      levels 1..D (D only if FULL)   */
+#define VOPP_FIELD_REP 4    /* int32  representative j      levels 1..D (FULL)             */
+#define VOPP_FIELD_OBS 5    /* float  observation[child][2] levels 1..D (FULL)             */
+#define VOPP_FIELD_PX 6     /* float  NAV2D x[node][N]      materialised levels            */
+#define VOPP_FIELD_PY 7     /* float  NAV2D y[node][N]      materialised levels            */
+#define VOPP_FIELD_PS 8     /* int32  GRID/TOY2 s[node][N]  materialised levels            */
+#define VOPP_FIELD_PLW 9    /* float  log weight[node][N]   materialised levels            */
+#define VOPP_FIELD_MU 10    /* float  weighted mean particle [node][2] (VOPP_PI_NAV_DIST) */
+
+#define VOPP_MAX_ACTIONS 16
+#define VOPP_MAX_DEPTH 8
+#define VOPP_MAX_PARTICLES 65536 /* agents / belief updates; a plan's leaf kernel stages one
+                                     node's particles in shared memory, which bounds N to
+                                     12,600 (NAV2D) or 16,800 (GRID, TOY2) at A*W <= 64 */
+
+typedef struct vopp_ctx vopp_ctx;
+typedef struct vopp_model vopp_model;
+typedef struct vopp_agent vopp_agent;
+
+/* Model description.  The POMDP 8-tuple of Sec. II-A fixed by kind; layout fields apply
+ * to VOPP_GRID (rock cells, all distinct, none on the start cell (0,5)). */
+typedef struct {
+  int32_t kind;        /* VOPP_NAV2D | VOPP_GRID | VOPP_TOY2                               */
+  int32_t branch_mode; /* VOPP_BRANCH_SAMPLE | VOPP_BRANCH_ENUMERATE                      */
+  int32_t pi_mode;     /* VOPP_PI_UNIFORM | VOPP_PI_FIXED | VOPP_PI_NAV_DIST                */
+  int32_t h_zero;      /* 1: leaf heuristic forced to 0                                    */
+  float pi_temp;       /* temperature of VOPP_PI_NAV_DIST                                  */
+  float pi_fixed[VOPP_MAX_ACTIONS]; /* VOPP_PI_FIXED weights (>= 0, positive sum)          */
+  int32_t rock_x[8], rock_y[8];     /* VOPP_GRID rock cells                                */
+} vopp_model_desc;
+
+/* Result of one plan (Alg. 1 action selection and the root's backed-up values). */
+typedef struct {
+  int32_t action;                    /* argmax_a Q(root,a) + eta log pibar(a|root), lowest
+                                        index on ties                                      */
+  uint32_t flags;                    /* VOPP_FLAG_*                                        */
+  double v_root;                     /* V(root)                                            */
+  double q[VOPP_MAX_ACTIONS];        /* Q(root, a), a < A                                  */
+  double policy[VOPP_MAX_ACTIONS];   /* pi*(a) = pibar(a) exp((Q_a - V)/eta)               */
+  uint64_t particle_steps;           /* sum_{l=1..D} (A W)^l N generative-model steps      */
+  uint64_t nodes;                    /* belief nodes in the tree, root included            */
+  uint32_t degenerate_actions;       /* actions whose branch weights all vanished          */
+  uint32_t reserved;
+} vopp_plan_result;
+
+/* Per-plan parameters (used by agents, batches and the serving queue). */
+typedef struct {
+  int32_t depth;          /* D >= 0 action levels                                          */
+  int32_t width;          /* W >= 1 observation branches per action                        */
+  float eta;              /* temperature > 0                                               */
+  float gamma;            /* discount in (0,1)                                             */
+  uint64_t seed;          /* Philox key of the plan                                        */
+  const float *pi_bar;    /* [A] host weights overriding the model's reference policy, or NULL */
+} vopp_plan_params;
+
+/* One plan of a batch: root particles (host or device per ptr_flags) plus parameters. */
+typedef struct {
+  vopp_model *model;
+  const void *root_states;  /* NAV2D: float[2N] (x[0..N-1] then y[0..N-1]); GRID/TOY2: int32[N] */
+  const float *root_weights;/* [N] or NULL for uniform                                    */
+  int32_t n_particles;
+  uint32_t ptr_flags;
+  vopp_plan_params params;
+} vopp_plan_request;
+
+/* ---- context ------------------------------------------------------------------------- */
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t
+ * cast to an integer; 0 = legacy default stream).  hbm_budget_bytes caps the device arena
+ * the context may allocate (0 = 80% of the device's free memory at creation). */
+VOPP_API int vopp_ctx_create(int device, size_t hbm_budget_bytes, uintptr_t cuda_stream, vopp_ctx **out);
+VOPP_API void vopp_ctx_destroy(vopp_ctx *ctx);
+/* VOPP_TREE_MINIMAL (default) or VOPP_TREE_FULL. */
+VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
+/* Tuning options (vopp_ctx_set_option):
+ *   VOPP_OPT_LEAF_GEN        1 (default): the leaf kernel builds level D-1 in shared memory
+ *                            from level D-2; 0: level D-1 is materialised in HBM first
+ *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 256)
+ *   VOPP_OPT_GRID_CAP        maximum CTAs of an expansion / leaf launch (grid-stride beyond)
+ *   VOPP_OPT_TAIL_MAX_NODES  levels with at most this many nodes are backed up by the
+ *                            single-CTA tail kernel (default 2048)
+ * Results do not depend on any option. */
+#define VOPP_OPT_LEAF_GEN 1
+#define VOPP_OPT_LEAF_THREADS 2
+#define VOPP_OPT_GRID_CAP 3
+#define VOPP_OPT_TAIL_MAX_NODES 4
+VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
+/* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
+VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
+/* Per-kernel-family accumulated device time (ms) and launch counts since the last reset.
+ * names[i] receives a static string; arrays hold at least *n entries on input; *n is set
+ * to the number of families written. */
+VOPP_API int vopp_ctx_kernel_times(vopp_ctx *ctx, const char **names, double *ms, uint64_t *launches,
+                          int *n);
+VOPP_API int vopp_ctx_reset_kernel_times(vopp_ctx *ctx);
+/* Host->device and device->host bytes the context copied, and kernels it launched, since
+ * the last vopp_ctx_reset_kernel_times (each pointer may be NULL). */
+VOPP_API int vopp_ctx_counters(vopp_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h_bytes,
+                               uint64_t *launches);
+/* Device bytes a plan of this shape needs in the arena (for admission control). */
+VOPP_API int vopp_plan_footprint(const vopp_model *model, int32_t n_particles, int32_t depth,
+                        int32_t width, size_t *bytes);
+
+/* ---- models -------------------------------------------------------------------------- */
+/* Validate a model description and upload its constant tables. */
+VOPP_API int vopp_create_model(vopp_ctx *ctx, const vopp_model_desc *desc, vopp_model **out);
+VOPP_API void vopp_model_destroy(vopp_model *model);
+/* Number of actions A of the model's kind (4, 13 or 2); negative status on NULL. */
+VOPP_API int vopp_model_num_actions(const vopp_model *model);
+
+/* ---- one plan (Alg. 1 with one full-width search and one backup) ---------------------- */
+/* root_states: NAV2D float[2N] (x then y), GRID/TOY2 int32[N]; root_weights: [N] or NULL.
+ * Weights must be >= 0; particles that are terminal at the root get weight 0; zero total
+ * weight returns VOPP_E_DEGENERATE.  pi_bar: [A] host weights or NULL (model's policy).
+ * Errors: VOPP_E_INVALID for depth < 0 or > VOPP_MAX_DEPTH, width < 1, N < 1 or
+ * > VOPP_MAX_PARTICLES, eta <= 0, gamma outside (0,1), invalid pi_bar; VOPP_E_BUDGET when
+ * the footprint exceeds the budget.  Depth 0 returns V = weighted mean heuristic, every
+ * Q equal to it and the action argmax pibar. */
+VOPP_API int vopp_plan(vopp_model *model, const void *root_states, const float *root_weights,
+              int32_t n_particles, int32_t depth, int32_t width, float eta, float gamma,
+              const float *pi_bar, uint64_t seed, uint32_t ptr_flags, vopp_plan_result *out);
+
+/* Copy `count` elements of a tree field of the most recent plan on this context, starting
+ * at element `offset` of that level's array, into dst (host, or device with ptr_flags).
+ * Valid until the next plan on the context. */
+VOPP_API int vopp_tree_read(vopp_ctx *ctx, int32_t field, int32_t level, uint64_t offset, uint64_t count,
+                   void *dst, uint32_t ptr_flags);
+
+/* Same as vopp_tree_read for plan `plan` (0-based) of the most recent batch. */
+VOPP_API int vopp_tree_read_plan(vopp_ctx *ctx, int32_t plan, int32_t field, int32_t level, uint64_t offset,
+                        uint64_t count, void *dst, uint32_t ptr_flags);
+
+/* The GRID sense-outcome thresholds floor(acc(d2) 2^32), d2 = 0..n-1 (n <= 256), exactly
+ * as uploaded by vopp_create_model: a sampled outcome is correct iff a Philox word is below
+ * thr[d2].  Host-only; needs no device. */
+VOPP_API int vopp_grid_thresholds(uint64_t *thr, int32_t n);
+
+/* ---- agents: device-resident beliefs with the SIR update (Sec. III-B) ---------------- */
+VOPP_API int vopp_agent_create(vopp_model *model, const void *states, const float *weights, int32_t n,
+                      uint64_t seed, uint32_t ptr_flags, vopp_agent **out);
+VOPP_API int vopp_agent_plan(vopp_agent *agent, const vopp_plan_params *params, vopp_plan_result *out);
+/* tau(b, a, o): propagate every particle under `action` (Philox purpose 3, time step t of
+ * the agent), reweight by Z(obs | s', a), resample systematically when ESS < N/2.  obs is a
+ * host pointer: NAV2D float[2], GRID/TOY2 int32[1].  On VOPP_E_DEGENERATE (every particle
+ * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
+VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
+                       int32_t *resampled_out);
+/* Copy the agent's particles (NAV2D x then y as float[2N]; GRID/TOY2 int32[N]) and
+ * normalised log weights out; ancestors (int32[N], may be NULL) of the last update. */
+VOPP_API int vopp_agent_get_particles(vopp_agent *agent, void *states, float *log_weights,
+                             int32_t *ancestors, uint32_t ptr_flags);
+VOPP_API int vopp_agent_num_particles(const vopp_agent *agent);
+VOPP_API void vopp_agent_destroy(vopp_agent *agent);
+
+/* ---- batches: many uneven plans per launch sequence ----------------------------------- */
+/* Run n independent plans with one launch per stage covering every plan (plans of
+ * different models, N, D and W mix freely).  Results equal those of n separate vopp_plan
+ * calls with the same arguments.  All models must belong to ctx. */
+VOPP_API int vopp_plan_batch(vopp_ctx *ctx, int32_t n, const vopp_plan_request *reqs,
+                    vopp_plan_result *outs);
+
+VOPP_API const char *vopp_last_error(void);
+/* Library version string. */
+VOPP_API const char *vopp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOPP_H */

@@ -1,0 +1,1029 @@
+// vopp_api.cu -- host side of the libvopp C ABI (include/vopp.h).
+//
+// A context owns one CUDA stream handle, a device arena for tree storage (bounded by the
+// HBM budget), a metadata block (plan descriptors, stage tables, results, root copies)
+// mirrored in pinned host memory, and optional per-kernel event timing.  A plan call, or
+// a batch of plans, is turned into a short sequence of launches -- root preparation, one
+// materialising expansion per level, the fused leaf expansion, large-level backups and
+// the per-plan tail with the FP64 root -- each launch covering every plan of the batch.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vopp.h"
+#include "vopp_internal.h"
+
+using namespace vopp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(VOPP_E_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));          \
+  } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+unsigned long long ipow(unsigned long long b, int e) {
+  unsigned long long r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+const char *kFamilies[] = {"root_prep", "expand", "leaf", "backup", "backup_tail", "belief"};
+enum { F_ROOT = 0, F_EXPAND, F_LEAF, F_BACKUP, F_TAIL, F_BELIEF, F_COUNT };
+
+struct TimedLaunch {
+  int family;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Objects.
+// ---------------------------------------------------------------------------------------
+struct vopp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  char *arena = nullptr;
+  size_t arena_cap = 0;
+  char *meta = nullptr;          // device metadata block
+  char *hmeta = nullptr;         // pinned host mirror
+  size_t meta_cap = 0;
+  int tree_detail = VOPP_TREE_MINIMAL;
+  int leaf_gen = 1;              // generate level D-1 inside the leaf kernel
+  int leaf_threads = 256;
+  int grid_cap = 1 << 30;
+  int tail_max_nodes = 2048;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<TimedLaunch> pending;
+  double fam_ms[F_COUNT] = {0};
+  unsigned long long fam_n[F_COUNT] = {0};
+  unsigned long long h2d_bytes = 0, d2h_bytes = 0, launches = 0;
+  // last launch, for vopp_tree_read
+  std::vector<PlanDesc> last_desc;
+  std::vector<int> last_ok;
+};
+
+struct vopp_model {
+  vopp_ctx *ctx = nullptr;
+  vopp_model_desc desc{};
+  DevModel host{};
+  DevModel *dev = nullptr;
+  int A = 0;
+};
+
+struct vopp_agent {
+  vopp_model *model = nullptr;
+  int N = 0;
+  uint64_t seed = 0;
+  unsigned long long t = 0;
+  float *xy = nullptr, *lw = nullptr;   // NAV2D: xy[2N] (x then y)
+  int *s = nullptr;                     // GRID / TOY2
+  float *txy = nullptr, *tlw = nullptr;
+  int *ts = nullptr;
+  double *cdf = nullptr;
+  int *anc = nullptr;
+  BeliefOut *dout = nullptr, *hout = nullptr;
+};
+
+// ---------------------------------------------------------------------------------------
+// Plan layout in the arena.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct PlanShape {
+  int kind, A, W, AW, N, D, pi_mode;
+  int leaf_gen, keep_leaf, keep_debug, mat_top;
+};
+
+struct PlanLayout {
+  size_t bytes = 0;
+  size_t px[kMaxDepth], py[kMaxDepth], plw[kMaxDepth], ps[kMaxDepth];
+  size_t rbar[kMaxDepth + 1], lom[kMaxDepth + 1], V[kMaxDepth + 1], Q[kMaxDepth],
+      mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1];
+};
+
+constexpr size_t kNone = ~(size_t)0;
+
+PlanShape make_shape(const vopp_model *m, int N, int D, int W, const vopp_ctx *ctx) {
+  PlanShape s{};
+  s.kind = m->desc.kind;
+  s.A = m->A;
+  s.W = W;
+  s.AW = m->A * W;
+  s.N = N;
+  s.D = D;
+  s.pi_mode = m->desc.pi_mode;
+  s.leaf_gen = (D >= 2 && ctx->leaf_gen) ? 1 : 0;
+  s.keep_debug = ctx->tree_detail == VOPP_TREE_FULL;
+  s.keep_leaf = (ctx->tree_detail == VOPP_TREE_FULL || D == 1) ? 1 : 0;
+  s.mat_top = (D == 0) ? 0 : (s.leaf_gen ? D - 2 : D - 1);
+  return s;
+}
+
+PlanLayout make_layout(const PlanShape &s) {
+  PlanLayout L;
+  for (int i = 0; i < kMaxDepth; ++i) L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = kNone;
+  for (int i = 0; i <= kMaxDepth; ++i) L.rbar[i] = L.lom[i] = L.V[i] = L.rep[i] = L.obs[i] = kNone;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  for (int l = 0; l <= s.mat_top; ++l) {
+    const size_t n = (size_t)ipow(s.AW, l) * (size_t)s.N;
+    if (s.kind == kNav) { L.px[l] = take(4 * n); L.py[l] = take(4 * n); }
+    else L.ps[l] = take(4 * n);
+    L.plw[l] = take(4 * n);
+  }
+  for (int l = 0; l <= s.D; ++l) {
+    const size_t nodes = (size_t)ipow(s.AW, l);
+    const bool node_level = l < s.D || s.D == 0;   // depth 0: the root holds V and Q
+    const bool keep = node_level || s.keep_leaf;
+    if (keep) L.V[l] = take(4 * nodes);
+    if (node_level) L.Q[l] = take(4 * nodes * s.A);
+    if (node_level && s.pi_mode == kPiNavDist) L.mu[l] = take(8 * nodes);
+    if (l >= 1 && keep) { L.rbar[l] = take(4 * nodes); L.lom[l] = take(4 * nodes); }
+    if (l >= 1 && keep && s.keep_debug) { L.rep[l] = take(4 * nodes); L.obs[l] = take(8 * nodes); }
+  }
+  L.bytes = off;
+  return L;
+}
+
+int validate_plan_args(const vopp_model *m, int N, int D, int W, float eta, float gamma,
+                       const float *pi_bar) {
+  if (!m) return fail(VOPP_E_INVALID, "model is NULL");
+  if (D < 0 || D > VOPP_MAX_DEPTH) return fail(VOPP_E_INVALID, "depth %d outside [0,%d]", D, VOPP_MAX_DEPTH);
+  if (W < 1 || m->A * W > kMaxAW) return fail(VOPP_E_INVALID, "width %d invalid (A*W <= %d)", W, kMaxAW);
+  if (N < 1 || N > VOPP_MAX_PARTICLES) return fail(VOPP_E_INVALID, "n_particles %d outside [1,%d]", N, VOPP_MAX_PARTICLES);
+  // the leaf kernel stages one node's particle set in shared memory
+  if (leaf_smem_bytes(m->desc.kind, N, m->A * W) > kLeafSmemLimit)
+    return fail(VOPP_E_INVALID, "n_particles %d too large for the leaf kernel's node buffer", N);
+  if (!(eta > 0.f) || !std::isfinite(eta)) return fail(VOPP_E_INVALID, "eta must be > 0");
+  if (!(gamma > 0.f && gamma < 1.f)) return fail(VOPP_E_INVALID, "gamma must be in (0,1)");
+  if (m->desc.branch_mode == VOPP_BRANCH_ENUMERATE) {
+    const int nobs = m->host.n_obs;
+    if (nobs <= 0 || W < nobs) return fail(VOPP_E_INVALID, "ENUMERATE needs a discrete model and width >= |O|");
+  }
+  if (pi_bar) {
+    double s = 0.0;
+    for (int a = 0; a < m->A; ++a) {
+      if (!(pi_bar[a] >= 0.f) || !std::isfinite(pi_bar[a])) return fail(VOPP_E_INVALID, "pi_bar[%d] invalid", a);
+      s += pi_bar[a];
+    }
+    if (!(s > 0.0)) return fail(VOPP_E_INVALID, "pi_bar sums to 0");
+  }
+  // tree size: nodes per level must stay inside 2^40 so that indices fit comfortably
+  if ((double)D * std::log((double)m->A * W) > 40.0 * std::log(2.0))
+    return fail(VOPP_E_INVALID, "tree too large");
+  return VOPP_OK;
+}
+
+int ensure_arena(vopp_ctx *c, size_t bytes) {
+  if (bytes <= c->arena_cap) return VOPP_OK;
+  if (bytes > c->budget)
+    return fail(VOPP_E_BUDGET, "plan needs %zu bytes, budget is %zu", bytes, c->budget);
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->arena) cudaFree(c->arena);
+  c->arena = nullptr;
+  c->arena_cap = 0;
+  size_t want = std::min(c->budget, std::max(bytes, (size_t)(1.25 * (double)bytes)));
+  want = align_up(want, 1 << 20);
+  if (want > c->budget) want = bytes;
+  if (cudaMalloc(&c->arena, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->arena = nullptr;
+      return fail(VOPP_E_NOMEM, "cudaMalloc of %zu arena bytes failed", bytes);
+    }
+    want = bytes;
+  }
+  c->arena_cap = want;
+  return VOPP_OK;
+}
+
+int ensure_meta(vopp_ctx *c, size_t bytes) {
+  if (bytes <= c->meta_cap) return VOPP_OK;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->meta) cudaFree(c->meta);
+  if (c->hmeta) cudaFreeHost(c->hmeta);
+  c->meta = c->hmeta = nullptr;
+  c->meta_cap = 0;
+  const size_t want = align_up(std::max(bytes, (size_t)1 << 16) * 2, 1 << 16);
+  if (cudaMalloc(&c->meta, want) != cudaSuccess) { cudaGetLastError(); return fail(VOPP_E_NOMEM, "meta alloc"); }
+  if (cudaMallocHost(&c->hmeta, want) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->meta);
+    c->meta = nullptr;
+    return fail(VOPP_E_NOMEM, "pinned meta alloc");
+  }
+  c->meta_cap = want;
+  return VOPP_OK;
+}
+
+// ---- timing -----------------------------------------------------------------------------
+void timed_begin(vopp_ctx *c, int fam, TimedLaunch &t) {
+  t.family = fam;
+  t.a = t.b = nullptr;
+  if (!c->timing) return;
+  while (c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  t.a = c->ev_pool[c->ev_used++];
+  t.b = c->ev_pool[c->ev_used++];
+  cudaEventRecord(t.a, c->stream);
+}
+void timed_end(vopp_ctx *c, TimedLaunch &t) {
+  if (!c->timing) return;
+  cudaEventRecord(t.b, c->stream);
+  c->pending.push_back(t);
+}
+void timed_collect(vopp_ctx *c) {
+  for (auto &t : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      c->fam_ms[t.family] += ms;
+      c->fam_n[t.family] += 1;
+    }
+  }
+  c->pending.clear();
+  c->ev_used = 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// One launch sequence for a set of plans.
+// ---------------------------------------------------------------------------------------
+struct Job {
+  const vopp_model *model;
+  PlanShape shape;
+  PlanLayout lay;
+  size_t arena_off;
+  const void *states;
+  const float *weights;
+  const float *log_weights;   // device log weights (agents)
+  uint32_t ptr_flags;
+  vopp_plan_params p;
+};
+
+struct StageBuild {
+  int family;
+  int level;
+  std::vector<int> plans, levels;
+  std::vector<long long> prefix;
+  long long total = 0;
+  int maxN = 0;
+  size_t smem = 0;
+  StageTable st{};
+};
+
+int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *statuses) {
+  const int n = (int)jobs.size();
+  // arena
+  size_t arena_bytes = 0;
+  for (auto &j : jobs) { j.arena_off = arena_bytes; arena_bytes = align_up(arena_bytes + j.lay.bytes, 256); }
+  int rc = ensure_arena(c, std::max<size_t>(arena_bytes, 256));
+  if (rc) return rc;
+
+  // stages
+  std::vector<StageBuild> stages;
+  auto nodes = [](const Job &j, int l) { return (long long)ipow(j.shape.AW, l); };
+  {
+    StageBuild s;
+    s.family = F_ROOT;
+    s.level = 0;
+    for (int i = 0; i < n; ++i) { s.plans.push_back(i); s.prefix.push_back(i); }
+    s.prefix.push_back(n);
+    s.total = n;
+    stages.push_back(s);
+  }
+  int max_mat = 0, maxD = 0;
+  for (auto &j : jobs) { max_mat = std::max(max_mat, j.shape.mat_top); maxD = std::max(maxD, j.shape.D); }
+  for (int l = 0; l < max_mat; ++l) {
+    StageBuild s;
+    s.family = F_EXPAND;
+    s.level = l;
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+      if (jobs[i].shape.mat_top > l) {
+        s.plans.push_back(i);
+        s.levels.push_back(l);
+        s.prefix.push_back(acc);
+        acc += nodes(jobs[i], l + 1);
+        s.maxN = std::max(s.maxN, jobs[i].shape.N);
+      }
+    }
+    s.prefix.push_back(acc);
+    s.total = acc;
+    if (acc) stages.push_back(s);
+  }
+  {
+    StageBuild s;
+    s.family = F_LEAF;
+    s.level = 0;
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+      if (jobs[i].shape.D >= 1) {
+        s.plans.push_back(i);
+        s.prefix.push_back(acc);
+        acc += nodes(jobs[i], jobs[i].shape.D - 1);
+        s.smem = std::max(s.smem, leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW));
+      }
+    }
+    s.prefix.push_back(acc);
+    s.total = acc;
+    if (acc) stages.push_back(s);
+  }
+  std::vector<int> tail_top(n, -1);
+  for (int i = 0; i < n; ++i) {
+    const auto &sh = jobs[i].shape;
+    int top = -1;
+    for (int l = sh.D - 2; l >= 1; --l)
+      if ((long long)ipow(sh.AW, l) <= c->tail_max_nodes) { top = l; break; }
+    tail_top[i] = top;
+  }
+  for (int l = maxD - 2; l >= 1; --l) {
+    StageBuild s;
+    s.family = F_BACKUP;
+    s.level = l;
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+      const auto &sh = jobs[i].shape;
+      if (l <= sh.D - 2 && l > tail_top[i]) {
+        s.plans.push_back(i);
+        s.levels.push_back(l);
+        s.prefix.push_back(acc);
+        acc += nodes(jobs[i], l);
+      }
+    }
+    s.prefix.push_back(acc);
+    s.total = acc;
+    if (acc) stages.push_back(s);
+  }
+  {
+    StageBuild s;
+    s.family = F_TAIL;
+    s.level = 0;
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+      if (jobs[i].shape.D >= 1) {
+        s.plans.push_back(i);
+        s.levels.push_back(tail_top[i] < 0 ? 0 : tail_top[i]);
+        s.prefix.push_back(acc++);
+      }
+    }
+    s.prefix.push_back(acc);
+    s.total = acc;
+    if (acc) stages.push_back(s);
+  }
+
+  // metadata block: [results n][descs n][stage tables][root copies]
+  size_t off = 0;
+  const size_t off_res = off; off = align_up(off + sizeof(DevResult) * n, 256);
+  const size_t off_desc = off; off = align_up(off + sizeof(PlanDesc) * n, 256);
+  std::vector<size_t> st_off(stages.size());
+  for (size_t s = 0; s < stages.size(); ++s) {
+    st_off[s] = off;
+    const size_t k = stages[s].plans.size();
+    off = align_up(off + 4 * k, 8);            // plan ids
+    off = align_up(off + 8 * (k + 1), 8);      // prefix
+    off = align_up(off + 4 * k, 256);          // levels
+  }
+  std::vector<size_t> root_off(n, kNone);
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    if (!(j.ptr_flags & VOPP_PTR_DEVICE) && j.states) {
+      root_off[i] = off;
+      const size_t sb = (j.shape.kind == kNav ? 8 : 4) * (size_t)j.shape.N;
+      const size_t wb = j.weights ? 4 * (size_t)j.shape.N : 0;
+      off = align_up(off + sb + wb, 256);
+    }
+  }
+  rc = ensure_meta(c, off);
+  if (rc) return rc;
+  char *H = c->hmeta, *Dm = c->meta;
+  std::memset(H + off_res, 0, sizeof(DevResult) * n);
+  PlanDesc *hd = reinterpret_cast<PlanDesc *>(H + off_desc);
+  const PlanDesc *dd = reinterpret_cast<const PlanDesc *>(Dm + off_desc);
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    const PlanShape &sh = j.shape;
+    PlanDesc P;
+    std::memset(&P, 0, sizeof P);
+    P.kind = sh.kind; P.A = sh.A; P.W = sh.W; P.AW = sh.AW; P.N = sh.N; P.D = sh.D;
+    P.branch_mode = j.model->desc.branch_mode;
+    P.pi_mode = sh.pi_mode;
+    P.h_zero = j.model->desc.h_zero;
+    P.leaf_gen = sh.leaf_gen; P.keep_leaf = sh.keep_leaf; P.keep_debug = sh.keep_debug;
+    P.eta = j.p.eta; P.inv_eta = 1.0f / j.p.eta; P.gamma = j.p.gamma;
+    P.pi_temp = j.model->desc.pi_temp;
+    // reference policy (uniform / fixed / caller override), normalised in double
+    {
+      double w[kMaxActions], s = 0.0;
+      for (int a = 0; a < sh.A; ++a) {
+        if (j.p.pi_bar) w[a] = j.p.pi_bar[a];
+        else if (sh.pi_mode == kPiFixed) w[a] = j.model->desc.pi_fixed[a];
+        else w[a] = 1.0;
+        s += w[a];
+      }
+      for (int a = 0; a < sh.A; ++a) P.log_pi[a] = w[a] > 0.0 ? (float)std::log(w[a] / s) : -INFINITY;
+      if (j.p.pi_bar && P.pi_mode == kPiNavDist) P.pi_mode = kPiFixed;
+    }
+    const double g = j.p.gamma;
+    P.h_a0 = (float)(-1.0 / (1.0 - g));
+    P.h_b0 = (float)(100.0 + 1.0 / (1.0 - g));
+    P.log2_gamma = (float)std::log2(g);
+    P.key0 = (uint32_t)j.p.seed;
+    P.key1 = (uint32_t)(j.p.seed >> 32);
+    P.model = j.model->dev;
+    char *base = c->arena + j.arena_off;
+    const PlanLayout &L = j.lay;
+    auto fp = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<float *>(base + o); };
+    auto ip = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<int *>(base + o); };
+    for (int l = 0; l < kMaxDepth; ++l) {
+      P.px[l] = fp(L.px[l]); P.py[l] = fp(L.py[l]); P.plw[l] = fp(L.plw[l]); P.ps[l] = ip(L.ps[l]);
+      P.Q[l] = fp(L.Q[l]); P.mu[l] = fp(L.mu[l]);
+    }
+    for (int l = 0; l <= kMaxDepth; ++l) {
+      P.rbar[l] = fp(L.rbar[l]); P.lom[l] = fp(L.lom[l]); P.V[l] = fp(L.V[l]);
+      P.rep[l] = ip(L.rep[l]); P.obs[l] = fp(L.obs[l]);
+    }
+    P.result = reinterpret_cast<DevResult *>(Dm + off_res) + i;
+    // root input
+    if (j.log_weights) {
+      P.root_lw = j.log_weights;
+    }
+    if (j.ptr_flags & VOPP_PTR_DEVICE || !j.states) {
+      if (sh.kind == kNav) {
+        P.root_x = static_cast<const float *>(j.states);
+        P.root_y = P.root_x + sh.N;
+      } else {
+        P.root_s = static_cast<const int *>(j.states);
+      }
+      P.root_w = j.weights;
+    } else {
+      char *hb = H + root_off[i];
+      const char *db = Dm + root_off[i];
+      const size_t sb = (sh.kind == kNav ? 8 : 4) * (size_t)sh.N;
+      std::memcpy(hb, j.states, sb);
+      if (sh.kind == kNav) {
+        P.root_x = reinterpret_cast<const float *>(db);
+        P.root_y = P.root_x + sh.N;
+      } else {
+        P.root_s = reinterpret_cast<const int *>(db);
+      }
+      if (j.weights) {
+        std::memcpy(hb + sb, j.weights, 4 * (size_t)sh.N);
+        P.root_w = reinterpret_cast<const float *>(db + sb);
+      }
+    }
+    hd[i] = P;
+  }
+  for (size_t s = 0; s < stages.size(); ++s) {
+    StageBuild &sb = stages[s];
+    const size_t k = sb.plans.size();
+    size_t o = st_off[s];
+    int *hp = reinterpret_cast<int *>(H + o);
+    for (size_t i = 0; i < k; ++i) hp[i] = sb.plans[i];
+    sb.st.plan = reinterpret_cast<const int *>(Dm + o);
+    o = align_up(o + 4 * k, 8);
+    long long *hq = reinterpret_cast<long long *>(H + o);
+    for (size_t i = 0; i <= k; ++i) hq[i] = sb.prefix[i];
+    sb.st.prefix = reinterpret_cast<const long long *>(Dm + o);
+    o = align_up(o + 8 * (k + 1), 8);
+    if (!sb.levels.empty()) {
+      int *hl = reinterpret_cast<int *>(H + o);
+      for (size_t i = 0; i < k; ++i) hl[i] = sb.levels[i];
+      sb.st.levels = reinterpret_cast<const int *>(Dm + o);
+    } else {
+      sb.st.levels = nullptr;
+    }
+    sb.st.n_plans = (int)k;
+    sb.st.level = sb.level;
+  }
+  CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, c->stream));
+  c->h2d_bytes += off;
+  c->d2h_bytes += sizeof(DevResult) * n;
+  c->launches += stages.size();
+
+  for (auto &sb : stages) {
+    TimedLaunch tl;
+    timed_begin(c, sb.family, tl);
+    cudaError_t e = cudaSuccess;
+    switch (sb.family) {
+      case F_ROOT: e = launch_root_prep(dd, sb.st, c->stream); break;
+      case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, c->grid_cap, c->stream); break;
+      case F_LEAF: e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads, c->grid_cap, c->stream); break;
+      case F_BACKUP: e = launch_backup(dd, sb.st, sb.total, c->stream); break;
+      case F_TAIL: e = launch_backup_tail(dd, sb.st, c->stream); break;
+    }
+    timed_end(c, tl);
+    if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
+  }
+  CUDA_TRY(cudaMemcpyAsync(H + off_res, Dm + off_res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  timed_collect(c);
+
+  c->last_desc.assign(hd, hd + n);
+  c->last_ok.assign(n, 1);
+  const DevResult *hr = reinterpret_cast<const DevResult *>(H + off_res);
+  int first_err = VOPP_OK;
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    vopp_plan_result &o = outs[i];
+    std::memset(&o, 0, sizeof o);
+    int st = VOPP_OK;
+    if (hr[i].status & kStatusDegenerateRoot) {
+      st = VOPP_E_DEGENERATE;
+      o.action = -1;
+      c->last_ok[i] = 0;
+    } else {
+      o.action = hr[i].action;
+      o.v_root = hr[i].v_root;
+      for (int a = 0; a < j.shape.A; ++a) { o.q[a] = hr[i].q[a]; o.policy[a] = hr[i].policy[a]; }
+    }
+    o.flags = hr[i].flags | (hr[i].degenerate ? VOPP_FLAG_DEGENERATE_BRANCH : 0u);
+    o.degenerate_actions = hr[i].degenerate;
+    unsigned long long steps = 0, nodes_total = 1;
+    for (int l = 1; l <= j.shape.D; ++l) {
+      steps += ipow(j.shape.AW, l) * (unsigned long long)j.shape.N;
+      nodes_total += ipow(j.shape.AW, l);
+    }
+    o.particle_steps = steps;
+    o.nodes = nodes_total;
+    if (statuses) statuses[i] = st;
+    if (st && !first_err) first_err = st;
+  }
+  if (first_err == VOPP_E_DEGENERATE) fail(VOPP_E_DEGENERATE, "root belief has zero total weight");
+  return first_err;
+}
+
+int make_job(vopp_ctx *c, vopp_model *m, const void *states, const float *weights, int N,
+             const vopp_plan_params &p, uint32_t ptr_flags, Job &j) {
+  int rc = validate_plan_args(m, N, p.depth, p.width, p.eta, p.gamma, p.pi_bar);
+  if (rc) return rc;
+  if (!states) return fail(VOPP_E_INVALID, "root_states is NULL");
+  if (weights && !(ptr_flags & VOPP_PTR_DEVICE)) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) {
+      if (!(weights[i] >= 0.f) || !std::isfinite(weights[i])) return fail(VOPP_E_INVALID, "weight %d invalid", i);
+      s += weights[i];
+    }
+    if (!(s > 0.0)) return fail(VOPP_E_DEGENERATE, "root weights sum to 0");
+  }
+  j.model = m;
+  j.shape = make_shape(m, N, p.depth, p.width, c);
+  j.lay = make_layout(j.shape);
+  j.states = states;
+  j.weights = weights;
+  j.log_weights = nullptr;
+  j.ptr_flags = ptr_flags;
+  j.p = p;
+  return VOPP_OK;
+}
+
+void fill_grid_tables(DevModel &d, const vopp_model_desc &m) {
+  for (int c = 0; c < 121; ++c) d.rock_at[c] = -1;
+  for (int r = 0; r < 8; ++r) {
+    d.rock_x[r] = m.rock_x[r];
+    d.rock_y[r] = m.rock_y[r];
+    d.rock_at[m.rock_x[r] + 11 * m.rock_y[r]] = r;
+  }
+  for (int d2 = 0; d2 < kGridD2; ++d2) {
+    const double acc = 0.5 + 0.5 * std::exp(-std::sqrt((double)d2) / 4.0);
+    d.thr[d2] = (unsigned long long)std::floor(acc * 4294967296.0);
+    d.lacc[d2] = (float)std::log(acc);
+    d.l1macc[d2] = (acc < 1.0) ? (float)std::log(1.0 - acc) : -INFINITY;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char *vopp_last_error(void) { return g_err.c_str(); }
+const char *vopp_version(void) { return "vopp-b300 0.1 (sm_103a)"; }
+
+int vopp_ctx_create(int device, size_t hbm_budget_bytes, uintptr_t cuda_stream, vopp_ctx **out) {
+  if (!out) return fail(VOPP_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(VOPP_E_INVALID, "device %d of %d", device, ndev);
+  CUDA_TRY(cudaSetDevice(device));
+  vopp_ctx *c = new (std::nothrow) vopp_ctx;
+  if (!c) return fail(VOPP_E_NOMEM, "ctx alloc");
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete c; return fail(VOPP_E_CUDA, "cudaMemGetInfo"); }
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
+  *out = c;
+  return VOPP_OK;
+}
+
+void vopp_ctx_destroy(vopp_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->arena) cudaFree(c->arena);
+  if (c->meta) cudaFree(c->meta);
+  if (c->hmeta) cudaFreeHost(c->hmeta);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int vopp_ctx_set_tree_detail(vopp_ctx *c, int detail) {
+  if (!c || (detail != VOPP_TREE_MINIMAL && detail != VOPP_TREE_FULL))
+    return fail(VOPP_E_INVALID, "bad tree detail");
+  c->tree_detail = detail;
+  return VOPP_OK;
+}
+
+int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
+  if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  switch (option) {
+    case VOPP_OPT_LEAF_GEN: c->leaf_gen = value ? 1 : 0; return VOPP_OK;
+    case VOPP_OPT_LEAF_THREADS:
+      if (value < 32 || value > 256 || value % 32) return fail(VOPP_E_INVALID, "leaf threads");
+      c->leaf_threads = (int)value;
+      return VOPP_OK;
+    case VOPP_OPT_GRID_CAP:
+      if (value < 1) return fail(VOPP_E_INVALID, "grid cap");
+      c->grid_cap = (int)std::min<int64_t>(value, 1 << 30);
+      return VOPP_OK;
+    case VOPP_OPT_TAIL_MAX_NODES:
+      if (value < 1) return fail(VOPP_E_INVALID, "tail max nodes");
+      c->tail_max_nodes = (int)std::min<int64_t>(value, 1 << 20);
+      return VOPP_OK;
+    default: return fail(VOPP_E_INVALID, "unknown option %d", option);
+  }
+}
+
+int vopp_ctx_set_timing(vopp_ctx *c, int enable) {
+  if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  c->timing = enable != 0;
+  return VOPP_OK;
+}
+
+int vopp_ctx_kernel_times(vopp_ctx *c, const char **names, double *ms, uint64_t *launches, int *n) {
+  if (!c || !n) return fail(VOPP_E_INVALID, "NULL argument");
+  const int m = std::min(*n, (int)F_COUNT);
+  for (int i = 0; i < m; ++i) {
+    if (names) names[i] = kFamilies[i];
+    if (ms) ms[i] = c->fam_ms[i];
+    if (launches) launches[i] = c->fam_n[i];
+  }
+  *n = m;
+  return VOPP_OK;
+}
+
+int vopp_ctx_reset_kernel_times(vopp_ctx *c) {
+  if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  for (int i = 0; i < F_COUNT; ++i) { c->fam_ms[i] = 0; c->fam_n[i] = 0; }
+  c->h2d_bytes = c->d2h_bytes = c->launches = 0;
+  return VOPP_OK;
+}
+
+int vopp_ctx_counters(vopp_ctx *c, uint64_t *h2d_bytes, uint64_t *d2h_bytes, uint64_t *launches) {
+  if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  if (h2d_bytes) *h2d_bytes = c->h2d_bytes;
+  if (d2h_bytes) *d2h_bytes = c->d2h_bytes;
+  if (launches) *launches = c->launches;
+  return VOPP_OK;
+}
+
+int vopp_plan_footprint(const vopp_model *m, int32_t N, int32_t D, int32_t W, size_t *bytes) {
+  if (!m || !bytes) return fail(VOPP_E_INVALID, "NULL argument");
+  int rc = validate_plan_args(m, N, D, W, 1.f, 0.5f, nullptr);
+  if (rc) return rc;
+  *bytes = make_layout(make_shape(m, N, D, W, m->ctx)).bytes;
+  return VOPP_OK;
+}
+
+int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
+  if (!c || !d || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  *out = nullptr;
+  if (d->kind < VOPP_NAV2D || d->kind > VOPP_TOY2) return fail(VOPP_E_INVALID, "kind %d", d->kind);
+  if (d->branch_mode != VOPP_BRANCH_SAMPLE && d->branch_mode != VOPP_BRANCH_ENUMERATE)
+    return fail(VOPP_E_INVALID, "branch_mode");
+  if (d->branch_mode == VOPP_BRANCH_ENUMERATE && d->kind == VOPP_NAV2D)
+    return fail(VOPP_E_INVALID, "ENUMERATE needs a discrete observation space");
+  if (d->pi_mode < VOPP_PI_UNIFORM || d->pi_mode > VOPP_PI_NAV_DIST)
+    return fail(VOPP_E_INVALID, "pi_mode");
+  if (d->pi_mode == VOPP_PI_NAV_DIST && (d->kind != VOPP_NAV2D || !(d->pi_temp > 0.f)))
+    return fail(VOPP_E_INVALID, "NAV_DIST needs NAV2D and pi_temp > 0");
+  const int A = d->kind == VOPP_NAV2D ? 4 : d->kind == VOPP_GRID ? 13 : 2;
+  if (d->pi_mode == VOPP_PI_FIXED) {
+    double s = 0.0;
+    for (int a = 0; a < A; ++a) {
+      if (!(d->pi_fixed[a] >= 0.f)) return fail(VOPP_E_INVALID, "pi_fixed[%d]", a);
+      s += d->pi_fixed[a];
+    }
+    if (!(s > 0.0)) return fail(VOPP_E_INVALID, "pi_fixed sums to 0");
+  }
+  if (d->kind == VOPP_GRID) {
+    for (int r = 0; r < 8; ++r) {
+      const int x = d->rock_x[r], y = d->rock_y[r];
+      if (x < 0 || x > 10 || y < 0 || y > 10) return fail(VOPP_E_INVALID, "rock %d off grid", r);
+      if (x == 0 && y == 5) return fail(VOPP_E_INVALID, "rock %d on the start cell", r);
+      for (int q = 0; q < r; ++q)
+        if (d->rock_x[q] == x && d->rock_y[q] == y) return fail(VOPP_E_INVALID, "rocks %d,%d coincide", q, r);
+    }
+  }
+  vopp_model *m = new (std::nothrow) vopp_model;
+  if (!m) return fail(VOPP_E_NOMEM, "model alloc");
+  m->ctx = c;
+  m->desc = *d;
+  m->A = A;
+  DevModel &h = m->host;
+  std::memset(&h, 0, sizeof h);
+  h.kind = d->kind;
+  h.A = A;
+  h.n_obs = d->kind == VOPP_NAV2D ? 0 : (d->kind == VOPP_GRID ? 3 : 2);
+  h.branch_mode = d->branch_mode;
+  h.pi_mode = d->pi_mode;
+  h.h_zero = d->h_zero;
+  h.pi_temp = d->pi_temp;
+  if (d->kind == VOPP_GRID) fill_grid_tables(h, *d);
+  h.toy_thr = (unsigned long long)std::floor(0.85 * 4294967296.0);
+  h.toy_lc = (float)std::log(0.85);
+  h.toy_lw = (float)std::log(0.15);
+  cudaSetDevice(c->device);
+  if (cudaMalloc(&m->dev, sizeof(DevModel)) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return fail(VOPP_E_NOMEM, "model device alloc");
+  }
+  if (cudaMemcpy(m->dev, &h, sizeof(DevModel), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->dev);
+    delete m;
+    return fail(VOPP_E_CUDA, "model upload");
+  }
+  *out = m;
+  return VOPP_OK;
+}
+
+void vopp_model_destroy(vopp_model *m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->ctx->stream);
+  cudaFree(m->dev);
+  delete m;
+}
+
+int vopp_model_num_actions(const vopp_model *m) {
+  if (!m) return fail(VOPP_E_INVALID, "model is NULL");
+  return m->A;
+}
+
+int vopp_grid_thresholds(uint64_t *thr, int32_t n) {
+  if (!thr || n < 1 || n > kGridD2) return fail(VOPP_E_INVALID, "bad arguments");
+  vopp_model_desc d;
+  std::memset(&d, 0, sizeof d);
+  for (int r = 0; r < 8; ++r) { d.rock_x[r] = r; d.rock_y[r] = 0; }
+  DevModel *h = new (std::nothrow) DevModel;
+  if (!h) return fail(VOPP_E_NOMEM, "host alloc");
+  fill_grid_tables(*h, d);
+  for (int i = 0; i < n; ++i) thr[i] = h->thr[i];
+  delete h;
+  return VOPP_OK;
+}
+
+int vopp_plan(vopp_model *m, const void *root_states, const float *root_weights, int32_t N,
+              int32_t depth, int32_t width, float eta, float gamma, const float *pi_bar,
+              uint64_t seed, uint32_t ptr_flags, vopp_plan_result *out) {
+  if (!m || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = m->ctx;
+  vopp_plan_params p{depth, width, eta, gamma, seed, pi_bar};
+  std::vector<Job> jobs(1);
+  int rc = make_job(c, m, root_states, root_weights, N, p, ptr_flags, jobs[0]);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  return run_jobs(c, jobs, out, nullptr);
+}
+
+int vopp_plan_batch(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, vopp_plan_result *outs) {
+  if (!c || !reqs || !outs || n < 1) return fail(VOPP_E_INVALID, "bad batch arguments");
+  std::vector<Job> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    const vopp_plan_request &r = reqs[i];
+    if (!r.model || r.model->ctx != c) return fail(VOPP_E_INVALID, "request %d: model of another context", i);
+    int rc = make_job(c, r.model, r.root_states, r.root_weights, r.n_particles, r.params, r.ptr_flags, jobs[i]);
+    if (rc) return rc;
+  }
+  cudaSetDevice(c->device);
+  std::vector<int> st(n);
+  int rc = run_jobs(c, jobs, outs, st.data());
+  return rc;
+}
+
+int vopp_tree_read(vopp_ctx *c, int32_t field, int32_t level, uint64_t offset, uint64_t count,
+                   void *dst, uint32_t ptr_flags) {
+  return vopp_tree_read_plan(c, 0, field, level, offset, count, dst, ptr_flags);
+}
+
+int vopp_tree_read_plan(vopp_ctx *c, int32_t plan, int32_t field, int32_t level, uint64_t offset,
+                        uint64_t count, void *dst, uint32_t ptr_flags) {
+  if (!c || !dst) return fail(VOPP_E_INVALID, "NULL argument");
+  if (plan < 0 || plan >= (int)c->last_desc.size()) return fail(VOPP_E_INVALID, "no such plan");
+  const PlanDesc &P = c->last_desc[plan];
+  if (level < 0 || level > P.D) return fail(VOPP_E_INVALID, "level %d", level);
+  const unsigned long long nodes = ipow(P.AW, level);
+  const void *src = nullptr;
+  size_t esz = 4;
+  unsigned long long len = nodes;
+  const int lv = level;
+  switch (field) {
+    case VOPP_FIELD_V: src = P.V[lv]; break;
+    case VOPP_FIELD_Q: src = lv < kMaxDepth ? P.Q[lv] : nullptr; len = nodes * P.A; break;
+    case VOPP_FIELD_RBAR: src = P.rbar[lv]; break;
+    case VOPP_FIELD_LOMEGA: src = P.lom[lv]; break;
+    case VOPP_FIELD_REP: src = P.rep[lv]; break;
+    case VOPP_FIELD_OBS: src = P.obs[lv]; len = 2 * nodes; break;
+    case VOPP_FIELD_PX: src = lv < kMaxDepth ? P.px[lv] : nullptr; len = nodes * P.N; break;
+    case VOPP_FIELD_PY: src = lv < kMaxDepth ? P.py[lv] : nullptr; len = nodes * P.N; break;
+    case VOPP_FIELD_PS: src = lv < kMaxDepth ? P.ps[lv] : nullptr; len = nodes * P.N; break;
+    case VOPP_FIELD_PLW: src = lv < kMaxDepth ? P.plw[lv] : nullptr; len = nodes * P.N; break;
+    case VOPP_FIELD_MU: src = lv < kMaxDepth ? P.mu[lv] : nullptr; len = 2 * nodes; break;
+    default: return fail(VOPP_E_INVALID, "field %d", field);
+  }
+  if (!src) return fail(VOPP_E_INVALID, "field %d not kept at level %d", field, level);
+  if (offset > len || count > len - offset) return fail(VOPP_E_INVALID, "range outside the level");
+  const cudaMemcpyKind kind = (ptr_flags & VOPP_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(dst, static_cast<const char *>(src) + offset * esz, count * esz, kind, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return VOPP_OK;
+}
+
+// ---- agents -----------------------------------------------------------------------------
+int vopp_agent_create(vopp_model *m, const void *states, const float *weights, int32_t n,
+                      uint64_t seed, uint32_t ptr_flags, vopp_agent **out) {
+  if (!m || !states || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  if (n < 1 || n > VOPP_MAX_PARTICLES) return fail(VOPP_E_INVALID, "n %d", n);
+  *out = nullptr;
+  vopp_ctx *c = m->ctx;
+  cudaSetDevice(c->device);
+  const bool nav = m->desc.kind == VOPP_NAV2D;
+  const bool dev = ptr_flags & VOPP_PTR_DEVICE;
+  std::vector<float> lw(n);
+  std::vector<float> wtmp;
+  const float *w = weights;
+  if (weights && dev) {
+    wtmp.resize(n);
+    CUDA_TRY(cudaMemcpy(wtmp.data(), weights, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+    w = wtmp.data();
+  }
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double wi = w ? w[i] : 1.0;
+    if (!(wi >= 0.0)) return fail(VOPP_E_INVALID, "weight %d", i);
+    s += wi;
+  }
+  if (!(s > 0.0)) return fail(VOPP_E_DEGENERATE, "weights sum to 0");
+  for (int i = 0; i < n; ++i) {
+    const double wi = w ? w[i] : 1.0;
+    lw[i] = wi > 0.0 ? (float)std::log(wi / s) : -INFINITY;
+  }
+  vopp_agent *g = new (std::nothrow) vopp_agent;
+  if (!g) return fail(VOPP_E_NOMEM, "agent alloc");
+  g->model = m;
+  g->N = n;
+  g->seed = seed;
+  bool ok = true;
+  auto al = [&](void **p, size_t b) { if (ok && cudaMalloc(p, b) != cudaSuccess) { cudaGetLastError(); ok = false; } };
+  if (nav) { al((void **)&g->xy, 8 * (size_t)n); al((void **)&g->txy, 8 * (size_t)n); }
+  else { al((void **)&g->s, 4 * (size_t)n); al((void **)&g->ts, 4 * (size_t)n); }
+  al((void **)&g->lw, 4 * (size_t)n);
+  al((void **)&g->tlw, 4 * (size_t)n);
+  al((void **)&g->cdf, 8 * (size_t)n);
+  al((void **)&g->anc, 4 * (size_t)n);
+  al((void **)&g->dout, sizeof(BeliefOut));
+  if (ok && cudaMallocHost((void **)&g->hout, sizeof(BeliefOut)) != cudaSuccess) { cudaGetLastError(); ok = false; }
+  if (!ok) { vopp_agent_destroy(g); return fail(VOPP_E_NOMEM, "agent device alloc"); }
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = nav ? cudaMemcpy(g->xy, states, 8 * (size_t)n, k) : cudaMemcpy(g->s, states, 4 * (size_t)n, k);
+  if (e == cudaSuccess) e = cudaMemcpy(g->lw, lw.data(), 4 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { vopp_agent_destroy(g); return fail(VOPP_E_CUDA, "agent upload: %s", cudaGetErrorString(e)); }
+  *out = g;
+  return VOPP_OK;
+}
+
+void vopp_agent_destroy(vopp_agent *g) {
+  if (!g) return;
+  if (g->model) cudaStreamSynchronize(g->model->ctx->stream);
+  cudaFree(g->xy); cudaFree(g->txy); cudaFree(g->s); cudaFree(g->ts);
+  cudaFree(g->lw); cudaFree(g->tlw); cudaFree(g->cdf); cudaFree(g->anc); cudaFree(g->dout);
+  if (g->hout) cudaFreeHost(g->hout);
+  delete g;
+}
+
+int vopp_agent_num_particles(const vopp_agent *g) {
+  if (!g) return fail(VOPP_E_INVALID, "agent is NULL");
+  return g->N;
+}
+
+int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *out) {
+  if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = g->model->ctx;
+  std::vector<Job> jobs(1);
+  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  int rc = make_job(c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, jobs[0]);
+  if (rc) return rc;
+  jobs[0].log_weights = g->lw;
+  cudaSetDevice(c->device);
+  return run_jobs(c, jobs, out, nullptr);
+}
+
+int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,
+                       int32_t *resampled_out) {
+  if (!g || !obs) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_model *m = g->model;
+  if (action < 0 || action >= m->A) return fail(VOPP_E_INVALID, "action %d", action);
+  vopp_ctx *c = m->ctx;
+  cudaSetDevice(c->device);
+  BeliefArgs B;
+  std::memset(&B, 0, sizeof B);
+  B.kind = m->desc.kind;
+  B.N = g->N;
+  B.action = action;
+  B.key0 = (uint32_t)g->seed;
+  B.key1 = (uint32_t)(g->seed >> 32);
+  B.t = g->t;
+  if (B.kind == kNav) {
+    B.x = g->xy; B.y = g->xy + g->N; B.tx = g->txy; B.ty = g->txy + g->N;
+    const float *o = static_cast<const float *>(obs);
+    B.obs_f[0] = o[0];
+    B.obs_f[1] = o[1];
+  } else {
+    B.s = g->s; B.ts = g->ts;
+    B.obs_i = *static_cast<const int32_t *>(obs);
+  }
+  B.lw = g->lw;
+  B.tlw = g->tlw;
+  B.cdf = g->cdf;
+  B.anc = g->anc;
+  B.model = m->dev;
+  B.out = g->dout;
+  TimedLaunch tl;
+  timed_begin(c, F_BELIEF, tl);
+  cudaError_t e = launch_belief(B, c->stream);
+  c->launches += 1;
+  c->d2h_bytes += sizeof(BeliefOut);
+  timed_end(c, tl);
+  if (e != cudaSuccess) return fail(VOPP_E_CUDA, "belief launch: %s", cudaGetErrorString(e));
+  CUDA_TRY(cudaMemcpyAsync(g->hout, g->dout, sizeof(BeliefOut), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  timed_collect(c);
+  if (g->hout->status) return fail(VOPP_E_DEGENERATE, "observation has zero likelihood under every particle");
+  if (ess_out) *ess_out = g->hout->ess;
+  if (resampled_out) *resampled_out = g->hout->resampled;
+  g->t += 1;
+  return VOPP_OK;
+}
+
+int vopp_agent_get_particles(vopp_agent *g, void *states, float *log_weights, int32_t *ancestors,
+                             uint32_t ptr_flags) {
+  if (!g) return fail(VOPP_E_INVALID, "agent is NULL");
+  vopp_ctx *c = g->model->ctx;
+  const cudaMemcpyKind k = (ptr_flags & VOPP_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = (size_t)g->N;
+  if (states) {
+    if (g->model->desc.kind == VOPP_NAV2D) CUDA_TRY(cudaMemcpyAsync(states, g->xy, 8 * n, k, c->stream));
+    else CUDA_TRY(cudaMemcpyAsync(states, g->s, 4 * n, k, c->stream));
+  }
+  if (log_weights) CUDA_TRY(cudaMemcpyAsync(log_weights, g->lw, 4 * n, k, c->stream));
+  if (ancestors) CUDA_TRY(cudaMemcpyAsync(ancestors, g->anc, 4 * n, k, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return VOPP_OK;
+}
+
+}  // extern "C"

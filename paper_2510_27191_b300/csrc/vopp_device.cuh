@@ -1,0 +1,381 @@
+// vopp_device.cuh -- device-side building blocks of the VOPP hot path on sm_103a.
+//
+// Philox4x32-10 counter RNG, the uniform / Gaussian conventions, the three generative
+// models (G(s,a) -> (s', o, r) of Sec. III-B, with their observation likelihoods and leaf
+// heuristics), compensated sums and warp / block reductions, and the plan descriptor that
+// the expansion and backup kernels read.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace vopp {
+
+constexpr int kMaxDepth = 8;
+constexpr int kMaxActions = 16;
+constexpr int kMaxAW = 256;           // actions x branches per node
+constexpr int kGridD2 = 256;          // squared agent-rock distances 0..221 (table padded)
+constexpr int kNav = 0, kGrid = 1, kToy = 2;
+constexpr int kSample = 0, kEnumerate = 1;
+constexpr int kPiUniform = 0, kPiFixed = 1, kPiNavDist = 2;
+
+// Philox purposes (high byte of counter word 0).
+constexpr uint32_t kPurposeTransition = 0, kPurposeObservation = 1, kPurposeBeliefStep = 3,
+                   kPurposeResample = 4;
+
+// Device status bits.
+constexpr uint32_t kStatusDegenerateRoot = 1u;
+
+// ---------------------------------------------------------------------------------------
+// Constant tables of one model, built on the host at model creation.
+// ---------------------------------------------------------------------------------------
+struct DevModel {
+  int kind, A, n_obs, branch_mode, pi_mode, h_zero;
+  float pi_temp;
+  float log_pi_fixed[kMaxActions];
+  int rock_x[8], rock_y[8];
+  int rock_at[121];                     // GRID: rock index of cell x + 11 y, or -1
+  unsigned long long thr[kGridD2];      // GRID: floor(acc(d2) 2^32), acc(0) -> 2^32
+  float lacc[kGridD2], l1macc[kGridD2]; // GRID: log acc, log(1 - acc)   (-inf at acc = 1)
+  unsigned long long toy_thr;           // TOY2: floor(0.85 2^32)
+  float toy_lc, toy_lw;                 // TOY2: log 0.85, log 0.15
+};
+
+struct DevResult {
+  int status;                 // kStatus* bits
+  int action;
+  unsigned flags;
+  unsigned degenerate;        // number of (node, action) pairs with vanished branch weights
+  double v_root;
+  double q[kMaxActions];
+  double policy[kMaxActions];
+};
+
+// Everything one plan's kernels need.  Level l has nodes(l) = AW^l belief nodes; the
+// child of node n through slot a*W + k is n*AW + a*W + k.
+struct PlanDesc {
+  int kind, A, W, AW, N, D, branch_mode, pi_mode, h_zero;
+  int leaf_gen;               // 1: level D-1 particles are generated in the leaf kernel
+  int keep_leaf;              // store branch stats at level D
+  int keep_debug;             // store representatives / observations
+  float eta, inv_eta, gamma, pi_temp;
+  float log_pi[kMaxActions];  // uniform / fixed reference policy
+  float h_a0, h_b0, log2_gamma;  // NAV2D heuristic: h = a0 + b0 gamma^(m-1)
+  uint32_t key0, key1;
+  const DevModel *model;
+  // root input (device copy or caller device pointer)
+  const float *root_x, *root_y;
+  const int *root_s;
+  const float *root_w;        // linear weights (or null = uniform)
+  const float *root_lw;       // log weights (agents); overrides root_w when set
+  // particle stores per level (levels 0 .. D-1, only those materialised)
+  float *px[kMaxDepth], *py[kMaxDepth], *plw[kMaxDepth];
+  int *ps[kMaxDepth];
+  // per-node / per-child arrays
+  float *rbar[kMaxDepth + 1], *lom[kMaxDepth + 1], *V[kMaxDepth + 1];
+  float *Q[kMaxDepth];
+  float *mu[kMaxDepth];       // weighted mean particle (x,y) per node, kPiNavDist only
+  int *rep[kMaxDepth + 1];
+  float *obs[kMaxDepth + 1];  // 2 floats per child
+  DevResult *result;
+};
+
+// A launch covers work items of several plans: plan i owns items [prefix[i], prefix[i+1]).
+struct StageTable {
+  int n_plans;
+  int level;                  // level of the work items (meaning depends on the kernel)
+  const int *plan;            // [n_plans] plan index into the descriptor array
+  const long long *prefix;    // [n_plans + 1]
+  const int *levels;          // [n_plans] per-plan level (overrides `level` when non-null)
+};
+
+__device__ __forceinline__ int find_plan(const StageTable &st, long long item) {
+  int lo = 0, hi = st.n_plans - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (st.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter words:
+//   c0 = idx | purpose << 24, c1 = level | action << 8 | branch << 16, (c2, c3) = node.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, uint32_t purpose,
+                                      uint32_t level, uint32_t a, uint32_t k,
+                                      unsigned long long node) {
+  return philox(make_uint4(idx | (purpose << 24), level | (a << 8) | (k << 16),
+                           (uint32_t)node, (uint32_t)(node >> 32)),
+                k0, k1);
+}
+
+// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float u01(uint32_t x) {
+  return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+}
+
+// Box-Muller: two N(0,1) values from two Philox words.
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  const float u1 = u01(a), u2 = u01(b);
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+// ---------------------------------------------------------------------------------------
+// Compensated (Kahan) accumulation and online log-sum-exp.
+// ---------------------------------------------------------------------------------------
+struct Kahan {
+  float s, c;
+  __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void scale(float f) { s *= f; c *= f; }
+  __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
+};
+
+// Streaming sum of exp(L_i - m) (and of exp(L_i - m) h_i) with a running maximum m.
+struct OnlineLSE {
+  float m;
+  Kahan s, h;
+  __device__ __forceinline__ void init() { m = -CUDART_INF_F; s.init(); h.init(); }
+  __device__ __forceinline__ void add(float L, float hv) {
+    if (!(L > -CUDART_INF_F)) return;            // zero weight contributes nothing
+    if (L > m) {
+      const float t = __expf(m - L);             // 0 when m = -inf
+      s.scale(t); h.scale(t);
+      m = L;
+      s.add(1.0f); h.add(hv);
+    } else {
+      const float t = __expf(L - m);
+      s.add(t); h.add(t * hv);
+    }
+  }
+  __device__ __forceinline__ void add(float L) {
+    if (!(L > -CUDART_INF_F)) return;
+    if (L > m) {
+      const float t = __expf(m - L);
+      s.scale(t);
+      m = L;
+      s.add(1.0f);
+    } else {
+      s.add(__expf(L - m));
+    }
+  }
+};
+
+// Merge of two (max, sum, hsum) partials; sums are plain floats after compensation.
+__device__ __forceinline__ void lse_merge(float &m, float &s, float &h, float m2, float s2,
+                                          float h2) {
+  const float M = fmaxf(m, m2);
+  if (!(M > -CUDART_INF_F)) { m = M; s = 0.f; h = 0.f; return; }
+  const float f1 = (m > -CUDART_INF_F) ? __expf(m - M) : 0.f;
+  const float f2 = (m2 > -CUDART_INF_F) ? __expf(m2 - M) : 0.f;
+  s = s * f1 + s2 * f2;
+  h = h * f1 + h2 * f2;
+  m = M;
+}
+
+__device__ __forceinline__ void warp_lse(float &m, float &s, float &h) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float m2 = __shfl_xor_sync(0xffffffffu, m, o);
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+    lse_merge(m, s, h, m2, s2, h2);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reductions (every thread gets the result).  `red` holds >= 32 floats.
+__device__ __forceinline__ float block_sum(float v, float *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float t = (lane < nw) ? red[lane] : 0.f;
+  t = warp_sum(t);
+  return t;
+}
+
+__device__ __forceinline__ float block_max(float v, float *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float t = (lane < nw) ? red[lane] : -CUDART_INF_F;
+  return warp_max(t);
+}
+
+// ---------------------------------------------------------------------------------------
+// Models.  Each provides: a particle type, step (transition + reward, absorbing terminals),
+// draw_obs (o ~ Z(.|s',a) from Philox words), loglik (log Z(o|s',a), -inf if impossible)
+// and heuristic (leaf ValueHeuristic of Alg. 2).
+// ---------------------------------------------------------------------------------------
+struct NavModel {
+  static constexpr bool kStochastic = true;
+  struct S { float x, y; };
+  struct O { float x, y; };
+
+  __device__ __forceinline__ static bool terminal(const S &s) {
+    return s.x * s.x + s.y * s.y <= 0.25f;
+  }
+  __device__ __forceinline__ static float step(S &s, int a, uint32_t wa, uint32_t wb,
+                                               const DevModel &) {
+    if (terminal(s)) return 0.0f;
+    const float2 g = box_muller(wa, wb);
+    const float dx = (a == 0) ? 1.0f : ((a == 1) ? -1.0f : 0.0f);
+    const float dy = (a == 2) ? 1.0f : ((a == 3) ? -1.0f : 0.0f);
+    s.x = fminf(fmaxf((s.x + dx) + 0.1f * g.x, 0.0f), 10.0f);
+    s.y = fminf(fmaxf((s.y + dy) + 0.1f * g.y, 0.0f), 10.0f);
+    return terminal(s) ? 100.0f : -1.0f;
+  }
+  __device__ __forceinline__ static float sigma(float x) { return 0.5f * fabsf(x - 9.0f) + 0.05f; }
+  __device__ __forceinline__ static O draw_obs(const S &s, int, uint32_t w0, uint32_t w1,
+                                               const DevModel &) {
+    const float2 g = box_muller(w0, w1);
+    const float sg = sigma(s.x);
+    return O{s.x + sg * g.x, s.y + sg * g.y};
+  }
+  __device__ __forceinline__ static O enum_obs(int k) { return O{(float)k, 0.f}; }
+  __device__ __forceinline__ static float loglik(const S &s, int, const O &o, const DevModel &) {
+    const float sg = sigma(s.x);
+    const float inv = __frcp_rn(sg);
+    const float dx = o.x - s.x, dy = o.y - s.y;
+    const float d2 = dx * dx + dy * dy;
+    return -0.5f * d2 * (inv * inv) - 2.0f * __logf(sg) - 1.8378770664093453f;  // log 2 pi
+  }
+  __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
+    if (P.h_zero || terminal(s)) return 0.0f;
+    const float m = fmaxf(s.x + s.y - 0.5f, 1.0f);
+    const float gk = exp2f((m - 1.0f) * P.log2_gamma);
+    return fmaf(P.h_b0, gk, P.h_a0);
+  }
+  __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2(o.x, o.y); }
+};
+
+__device__ __forceinline__ int gx(int s) { return (s >> 8) & 0xF; }
+__device__ __forceinline__ int gy(int s) { return (s >> 12) & 0xF; }
+__device__ __forceinline__ int gterm(int s) { return (s >> 16) & 1; }
+__device__ __forceinline__ int gpack(int rocks, int x, int y, int t) {
+  return (rocks & 0xFF) | (x << 8) | (y << 12) | (t << 16);
+}
+
+struct GridModel {
+  static constexpr bool kStochastic = false;
+  struct S { int s; };
+  struct O { int o; };
+
+  __device__ __forceinline__ static bool terminal(const S &s) { return gterm(s.s) != 0; }
+  __device__ __forceinline__ static float step(S &st, int a, uint32_t, uint32_t,
+                                               const DevModel &m) {
+    const int s = st.s;
+    if (gterm(s)) return 0.0f;
+    int x = gx(s), y = gy(s), rocks = s & 0xFF;
+    float r = 0.0f;
+    if (a == 0) {
+      if (x == 10) { st.s = gpack(rocks, 11, y, 1); return 10.0f; }
+      x += 1;
+    } else if (a == 1) {
+      x = (x > 0) ? x - 1 : x;
+    } else if (a == 2) {
+      y = (y < 10) ? y + 1 : y;
+    } else if (a == 3) {
+      y = (y > 0) ? y - 1 : y;
+    } else if (a == 4) {
+      const int rk = (x <= 10) ? m.rock_at[x + 11 * y] : -1;
+      if (rk >= 0) {
+        if ((rocks >> rk) & 1) { r = 10.0f; rocks &= ~(1 << rk); }
+        else r = -10.0f;
+      }
+    }
+    st.s = gpack(rocks, x, y, 0);
+    return r;
+  }
+  __device__ __forceinline__ static int d2(const S &s, int rk, const DevModel &m) {
+    const int dx = gx(s.s) - m.rock_x[rk], dy = gy(s.s) - m.rock_y[rk];
+    return dx * dx + dy * dy;
+  }
+  __device__ __forceinline__ static O draw_obs(const S &s, int a, uint32_t w0, uint32_t,
+                                               const DevModel &m) {
+    if (a < 5) return O{0};
+    const int rk = a - 5, bit = (s.s >> rk) & 1;
+    const bool correct = (unsigned long long)w0 < m.thr[d2(s, rk, m)];
+    const int seen = correct ? bit : 1 - bit;
+    return O{seen ? 1 : 2};
+  }
+  __device__ __forceinline__ static O enum_obs(int k) { return O{k}; }
+  __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
+    if (a < 5) return (o.o == 0) ? 0.0f : -CUDART_INF_F;
+    if (o.o != 1 && o.o != 2) return -CUDART_INF_F;
+    const int rk = a - 5, bit = (s.s >> rk) & 1;
+    const int dd = d2(s, rk, m);
+    return ((o.o == 1) == (bit == 1)) ? m.lacc[dd] : m.l1macc[dd];
+  }
+  __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
+    if (P.h_zero || gterm(s.s)) return 0.0f;
+    return 10.0f * exp2f((float)(10 - gx(s.s)) * P.log2_gamma);
+  }
+  __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
+};
+
+struct ToyModel {
+  static constexpr bool kStochastic = false;
+  struct S { int s; };
+  struct O { int o; };
+
+  __device__ __forceinline__ static bool terminal(const S &) { return false; }
+  __device__ __forceinline__ static float step(S &st, int a, uint32_t, uint32_t, const DevModel &) {
+    const int s = st.s;
+    st.s = (a == 1) ? 1 - s : s;
+    return (a == 1) ? -0.1f : (s == 0 ? 1.0f : -1.0f);
+  }
+  __device__ __forceinline__ static O draw_obs(const S &s, int, uint32_t w0, uint32_t,
+                                               const DevModel &m) {
+    const bool correct = (unsigned long long)w0 < m.toy_thr;
+    return O{correct ? s.s : 1 - s.s};
+  }
+  __device__ __forceinline__ static O enum_obs(int k) { return O{k}; }
+  __device__ __forceinline__ static float loglik(const S &s, int, const O &o, const DevModel &m) {
+    if (o.o != 0 && o.o != 1) return -CUDART_INF_F;
+    return (o.o == s.s) ? m.toy_lc : m.toy_lw;
+  }
+  __device__ __forceinline__ static float heuristic(const S &, const PlanDesc &) { return 0.0f; }
+  __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
+};
+
+}  // namespace vopp

@@ -1,0 +1,48 @@
+// vopp_internal.h -- declarations shared by the kernels and the host-side C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vopp_device.cuh"
+
+namespace vopp {
+
+struct BeliefOut {
+  int status;       // 0 ok, 1 degenerate (every particle has zero likelihood)
+  int resampled;
+  double ess;
+};
+
+struct BeliefArgs {
+  int kind, N, action;
+  uint32_t key0, key1;
+  unsigned long long t;        // agent time step (Philox node word)
+  float *x, *y, *lw;           // current belief (NAV2D x, y)
+  int *s;                      // current belief (GRID / TOY2)
+  float *tx, *ty, *tlw;        // propagated particles (scratch)
+  int *ts;
+  double *cdf;                 // [N] scratch
+  int *anc;                    // [N] ancestors of the update
+  float obs_f[2];
+  int obs_i;
+  const DevModel *model;
+  BeliefOut *out;
+};
+
+// Dynamic shared memory a leaf CTA may use (B300: 227 KB per block, kept below it).
+constexpr size_t kLeafSmemLimit = 200 * 1024;
+size_t leaf_smem_bytes(int kind, int N, int AW);
+size_t expand_smem_bytes(int N);
+cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s);
+cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
+                          int grid_cap, cudaStream_t s);
+cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
+                        int threads, int grid_cap, cudaStream_t s);
+cudaError_t launch_backup(const PlanDesc *d, const StageTable &st, long long total_nodes,
+                          cudaStream_t s);
+cudaError_t launch_backup_tail(const PlanDesc *d, const StageTable &st, cudaStream_t s);
+cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
+
+}  // namespace vopp

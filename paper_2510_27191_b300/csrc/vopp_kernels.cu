@@ -1,0 +1,802 @@
+// vopp_kernels.cu -- the VOPP hot path on sm_103a.
+//
+// Full-width belief-tree expansion (Alg. 2, full-width form) and the closed-form
+// Reference-Based backup (Alg. 3 with one Eq. 3 update, Eq. 1 value):
+//   k_root_prep   normalise the root belief, zero terminal particles (Alg. 1 sample step)
+//   k_expand      materialise level l+1 children: step every particle of the parent under
+//                 (a, k), draw the branch observation, reweight, write the child SoA
+//   k_leaf        per level-(D-1) node: build its particle set in shared memory (or load
+//                 it), expand all A*W leaf children without writing particles (weighted
+//                 heuristic mean, branch weights, mean reward), then back the node up
+//   k_backup      Q and V of every node of one level from its children's branch stats
+//   k_backup_tail remaining small levels in one CTA per plan, root level in FP64, action
+//   k_belief      SIR belief update tau(b, a, o) of one agent (Sec. III-B)
+//
+// No tensor cores: nothing here is a dense contraction.  The leaf kernel is bound by FP32
+// / SFU issue (Philox integer multiplies, Box-Muller, log / exp); the others are small.
+#include "vopp_device.cuh"
+#include "vopp_internal.h"
+
+namespace vopp {
+
+// ---------------------------------------------------------------------------------------
+// Particle-set views (SoA): global level stores and shared-memory node buffers.
+// ---------------------------------------------------------------------------------------
+template <class M> struct PSet;
+
+template <> struct PSet<NavModel> {
+  float *x, *y, *lw, *w;  // w only for shared-memory buffers
+  __device__ __forceinline__ NavModel::S get(int i) const { return NavModel::S{x[i], y[i]}; }
+  __device__ __forceinline__ void put(int i, const NavModel::S &s) const { x[i] = s.x; y[i] = s.y; }
+  static constexpr int kSmemBytes = 16;  // per particle in a shared node buffer
+  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
+    const long long b = node * P.N;
+    return PSet{P.px[l] + b, P.py[l] + b, P.plw[l] + b, nullptr};
+  }
+  __device__ static PSet smem(float *base, int N) {
+    return PSet{base, base + N, base + 2 * N, base + 3 * N};
+  }
+};
+
+template <class M> struct PSetInt {
+  int *s;
+  float *lw, *w;
+  __device__ __forceinline__ typename M::S get(int i) const { return typename M::S{s[i]}; }
+  __device__ __forceinline__ void put(int i, const typename M::S &v) const { s[i] = v.s; }
+  static constexpr int kSmemBytes = 12;
+  __device__ static PSetInt level(const PlanDesc &P, int l, long long node) {
+    const long long b = node * P.N;
+    return PSetInt{P.ps[l] + b, P.plw[l] + b, nullptr};
+  }
+  __device__ static PSetInt smem(float *base, int N) {
+    return PSetInt{reinterpret_cast<int *>(base), base + N, base + 2 * N};
+  }
+};
+template <> struct PSet<GridModel> : PSetInt<GridModel> {
+  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
+    PSet r; static_cast<PSetInt<GridModel> &>(r) = PSetInt<GridModel>::level(P, l, node); return r;
+  }
+  __device__ static PSet smem(float *base, int N) {
+    PSet r; static_cast<PSetInt<GridModel> &>(r) = PSetInt<GridModel>::smem(base, N); return r;
+  }
+};
+template <> struct PSet<ToyModel> : PSetInt<ToyModel> {
+  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
+    PSet r; static_cast<PSetInt<ToyModel> &>(r) = PSetInt<ToyModel>::level(P, l, node); return r;
+  }
+  __device__ static PSet smem(float *base, int N) {
+    PSet r; static_cast<PSetInt<ToyModel> &>(r) = PSetInt<ToyModel>::smem(base, N); return r;
+  }
+};
+
+template <class M> __device__ __forceinline__ float2 state_xy(const typename M::S &s);
+template <> __device__ __forceinline__ float2 state_xy<NavModel>(const NavModel::S &s) {
+  return make_float2(s.x, s.y);
+}
+template <> __device__ __forceinline__ float2 state_xy<GridModel>(const GridModel::S &) {
+  return make_float2(0.f, 0.f);
+}
+template <> __device__ __forceinline__ float2 state_xy<ToyModel>(const ToyModel::S &) {
+  return make_float2(0.f, 0.f);
+}
+
+template <class M>
+__device__ __forceinline__ typename M::S load_root(const PlanDesc &P, int i);
+template <> __device__ __forceinline__ NavModel::S load_root<NavModel>(const PlanDesc &P, int i) {
+  return NavModel::S{P.root_x[i], P.root_y[i]};
+}
+template <> __device__ __forceinline__ GridModel::S load_root<GridModel>(const PlanDesc &P, int i) {
+  return GridModel::S{P.root_s[i]};
+}
+template <> __device__ __forceinline__ ToyModel::S load_root<ToyModel>(const PlanDesc &P, int i) {
+  return ToyModel::S{P.root_s[i]};
+}
+
+// Transition words of particle i of branch (l, node, a, k): pair i/2, half i&1.
+template <class M>
+__device__ __forceinline__ float step_particle(const PlanDesc &P, typename M::S &s, int i, int l,
+                                               int a, int k, unsigned long long node,
+                                               const DevModel &dm) {
+  uint32_t wa = 0, wb = 0;
+  if (M::kStochastic) {
+    const uint4 w = draw(P.key0, P.key1, (uint32_t)(i >> 1), kPurposeTransition, l, a, k, node);
+    wa = (i & 1) ? w.z : w.x;
+    wb = (i & 1) ? w.w : w.y;
+  }
+  return M::step(s, a, wa, wb, dm);
+}
+
+// The branch observation of (l, node, a, k): enumerated, or drawn from the representative
+// particle j = floor(u N / 2^32) after its own transition.
+template <class M, class Src>
+__device__ __forceinline__ typename M::O branch_obs(const PlanDesc &P, const Src &src, int l, int a,
+                                                    int k, unsigned long long node,
+                                                    const DevModel &dm, int &j) {
+  if (P.branch_mode == kEnumerate) { j = -1; return M::enum_obs(k); }
+  const uint4 w = draw(P.key0, P.key1, 0u, kPurposeObservation, l, a, k, node);
+  j = (int)(((unsigned long long)w.z * (unsigned long long)P.N) >> 32);
+  typename M::S sj = src.get(j);
+  step_particle<M>(P, sj, j, l, a, k, node, dm);
+  return M::draw_obs(sj, a, w.x, w.y, dm);
+}
+
+// log pibar(a | node) for a < A into lpi (computed by every calling thread).
+__device__ __forceinline__ float log_pibar(const PlanDesc &P, float2 mu, int a) {
+  if (P.pi_mode != kPiNavDist) return P.log_pi[a];
+  float z[4], zm = -CUDART_INF_F;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float dx = (b == 0) ? 1.f : (b == 1 ? -1.f : 0.f);
+    const float dy = (b == 2) ? 1.f : (b == 3 ? -1.f : 0.f);
+    const float cx = fminf(fmaxf(mu.x + dx, 0.f), 10.f), cy = fminf(fmaxf(mu.y + dy, 0.f), 10.f);
+    z[b] = -sqrtf(cx * cx + cy * cy) / P.pi_temp;
+    zm = fmaxf(zm, z[b]);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) s += __expf(z[b] - zm);
+  return z[a & 3] - zm - logf(s);
+}
+
+// ---------------------------------------------------------------------------------------
+// Child construction (Alg. 2: G, observation, weighting) by a whole CTA.
+//   src: parent's particles (level l), dst: child's particle buffer (global or shared);
+//   scratchL / scratchE: N floats each (may alias dst.lw / dst.w for shared buffers).
+// Writes the branch stats of the child and returns them in the out parameters.
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
+                            unsigned long long child, const PSet<M> &src, const PSet<M> &dst,
+                            float *scratchL, float *scratchE, float *red, bool dst_has_w,
+                            float2 *mu_out) {
+  const int N = P.N, AW = P.AW, W = P.W;
+  const unsigned long long parent = child / (unsigned long long)AW;
+  const int slot = (int)(child - parent * (unsigned long long)AW);
+  const int a = slot / W, k = slot - (slot / W) * W;
+  int j;
+  const typename M::O o = branch_obs<M>(P, src, l, a, k, parent, dm, j);
+
+  Kahan R;
+  R.init();
+  float m1 = -CUDART_INF_F, m0 = -CUDART_INF_F;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    typename M::S s = src.get(i);
+    const float lw = src.lw[i];
+    const float r = step_particle<M>(P, s, i, l, a, k, parent, dm);
+    const float ell = M::loglik(s, a, o, dm);
+    const float L = lw + ell;
+    if (lw > -CUDART_INF_F) R.add(__expf(lw) * r);
+    dst.put(i, s);
+    scratchL[i] = L;
+    scratchE[i] = ell;
+    m1 = fmaxf(m1, L);
+    m0 = fmaxf(m0, ell);
+  }
+  m1 = block_max(m1, red);
+  m0 = block_max(m0, red);
+  const float rbar = block_sum(R.value(), red);
+
+  Kahan S1, S0, MX, MY;
+  S1.init(); S0.init(); MX.init(); MY.init();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float e1 = (m1 > -CUDART_INF_F) ? __expf(scratchL[i] - m1) : 0.f;
+    const float e0 = (m0 > -CUDART_INF_F) ? __expf(scratchE[i] - m0) : 0.f;
+    S1.add(e1);
+    S0.add(e0);
+    if (P.pi_mode == kPiNavDist) {
+      const float2 xy = state_xy<M>(dst.get(i));
+      MX.add(e1 * xy.x);
+      MY.add(e1 * xy.y);
+    }
+  }
+  const float s1 = block_sum(S1.value(), red);
+  const float s0 = block_sum(S0.value(), red);
+  float mx = 0.f, my = 0.f;
+  if (P.pi_mode == kPiNavDist) {
+    mx = block_sum(MX.value(), red);
+    my = block_sum(MY.value(), red);
+  }
+  const float lse1 = (s1 > 0.f) ? m1 + logf(s1) : -CUDART_INF_F;
+  float lom;
+  if (P.branch_mode == kEnumerate) lom = lse1;
+  else lom = (lse1 > -CUDART_INF_F) ? logf((float)N) + lse1 - (m0 + logf(s0)) : -CUDART_INF_F;
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float nl = (lse1 > -CUDART_INF_F) ? scratchL[i] - lse1 : -CUDART_INF_F;
+    dst.lw[i] = nl;
+    if (dst_has_w) dst.w[i] = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
+  }
+  const int cl = l + 1;
+  if (threadIdx.x == 0) {
+    P.rbar[cl][child] = rbar;
+    P.lom[cl][child] = lom;
+    float2 mu = make_float2(0.f, 0.f);
+    if (s1 > 0.f) mu = make_float2(mx / s1, my / s1);
+    if (P.pi_mode == kPiNavDist && P.mu[cl]) {
+      P.mu[cl][2 * child] = mu.x;
+      P.mu[cl][2 * child + 1] = mu.y;
+    }
+    if (mu_out) *mu_out = mu;
+    if (P.keep_debug) {
+      P.rep[cl][child] = j;
+      const float2 of = M::obs_f2(o);
+      P.obs[cl][2 * child] = of.x;
+      P.obs[cl][2 * child + 1] = of.y;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// Backup of one node (Alg. 3 lines computing R, W, Q, then Eq. 1 value) from branch stats
+// held in arrays indexed by slot a*W + k.  Executed by the lanes of one warp (a = lane).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void node_backup_warp(const PlanDesc &P, const float *rb,
+                                                 const float *lo, const float *vc, float2 mu,
+                                                 float *q_out, float *v_out) {
+  const int lane = threadIdx.x & 31, A = P.A, W = P.W;
+  float q = 0.f, z = -CUDART_INF_F;
+  if (lane < A) {
+    float rs = 0.f, M = -CUDART_INF_F;
+    for (int k = 0; k < W; ++k) {
+      rs += rb[lane * W + k];
+      M = fmaxf(M, lo[lane * W + k]);
+    }
+    float fut = 0.f;
+    if (M > -CUDART_INF_F) {
+      Kahan num, den;
+      num.init(); den.init();
+      for (int k = 0; k < W; ++k) {
+        const float om = __expf(lo[lane * W + k] - M);
+        num.add(om * vc[lane * W + k]);
+        den.add(om);
+      }
+      fut = num.value() / den.value();
+    } else {
+      atomicAdd(&P.result->degenerate, 1u);
+    }
+    q = rs / (float)W + P.gamma * fut;
+    z = log_pibar(P, mu, lane) + q * P.inv_eta;
+    q_out[lane] = q;
+  }
+  const float zm = warp_max(z);
+  float e = (lane < A && z > -CUDART_INF_F) ? __expf(z - zm) : 0.f;
+  e = warp_sum(e);
+  if (lane == 0) *v_out = P.eta * (zm + logf(e));
+}
+
+// ---------------------------------------------------------------------------------------
+// K1: root preparation (one CTA per plan).
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red) {
+  const int N = P.N;
+  PSet<M> dst = PSet<M>::level(P, 0, 0);
+  // log weights of the caller's belief; terminal particles and non-positive weights -> -inf
+  float m = -CUDART_INF_F;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const typename M::S s = load_root<M>(P, i);
+    float lw;
+    if (P.root_lw) {
+      lw = P.root_lw[i];
+    } else {
+      const float w = P.root_w ? P.root_w[i] : 1.0f;
+      lw = (w > 0.f) ? logf(w) : -CUDART_INF_F;
+    }
+    if (!(lw > -CUDART_INF_F) || M::terminal(s)) lw = -CUDART_INF_F;
+    dst.put(i, s);
+    dst.lw[i] = lw;
+    m = fmaxf(m, lw);
+  }
+  m = block_max(m, red);
+  if (!(m > -CUDART_INF_F)) {
+    if (threadIdx.x == 0) P.result->status |= kStatusDegenerateRoot;
+    return;
+  }
+  Kahan T;
+  T.init();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float lw = dst.lw[i];
+    if (lw > -CUDART_INF_F) T.add(__expf(lw - m));
+  }
+  const float lse = m + logf(block_sum(T.value(), red));
+  Kahan MX, MY, H;
+  MX.init(); MY.init(); H.init();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float lw = dst.lw[i];
+    const float nl = (lw > -CUDART_INF_F) ? lw - lse : -CUDART_INF_F;
+    dst.lw[i] = nl;
+    const float wn = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
+    const typename M::S s = dst.get(i);
+    const float2 xy = state_xy<M>(s);
+    MX.add(wn * xy.x);
+    MY.add(wn * xy.y);
+    if (P.D == 0) H.add(wn * M::heuristic(s, P));
+  }
+  const float mx = block_sum(MX.value(), red), my = block_sum(MY.value(), red);
+  const float hv = block_sum(H.value(), red);
+  if (threadIdx.x == 0) {
+    if (P.mu[0]) { P.mu[0][0] = mx; P.mu[0][1] = my; }
+    if (P.D == 0) {
+      // depth 0: V = weighted mean heuristic, every Q equal to it, action = argmax pibar
+      DevResult *R = P.result;
+      R->v_root = hv;
+      int best = 0;
+      float bl = -CUDART_INF_F;
+      for (int a = 0; a < P.A; ++a) {
+        const float lp = log_pibar(P, make_float2(mx, my), a);
+        R->q[a] = hv;
+        R->policy[a] = exp((double)lp);
+        if (lp > bl) { bl = lp; best = a; }
+        P.Q[0][a] = hv;
+      }
+      R->action = best;
+      P.V[0][0] = hv;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_root_prep(const PlanDesc *plans, StageTable st) {
+  __shared__ float red[32];
+  const PlanDesc &P = plans[st.plan[blockIdx.x]];
+  const DevModel &dm = *P.model;
+  switch (P.kind) {
+    case kNav: root_prep_plan<NavModel>(P, dm, red); break;
+    case kGrid: root_prep_plan<GridModel>(P, dm, red); break;
+    default: root_prep_plan<ToyModel>(P, dm, red); break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K2: materialise children at level l+1 (one CTA per child).
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, float *smem,
+                            float *red) {
+  const DevModel &dm = *P.model;
+  const unsigned long long parent = child / (unsigned long long)P.AW;
+  PSet<M> src = PSet<M>::level(P, l, (long long)parent);
+  PSet<M> dst = PSet<M>::level(P, l + 1, (long long)child);
+  build_child<M>(P, dm, l, child, src, dst, smem, smem + P.N, red, false, nullptr);
+}
+
+__global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTable st,
+                                                long long total) {
+  extern __shared__ float smem[];
+  __shared__ float red[32];
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int pi = find_plan(st, item);
+    const PlanDesc &P = plans[st.plan[pi]];
+    const int l = st.levels ? st.levels[pi] : st.level;
+    const unsigned long long child = (unsigned long long)(item - st.prefix[pi]);
+    switch (P.kind) {
+      case kNav: expand_item<NavModel>(P, l, child, smem, red); break;
+      case kGrid: expand_item<GridModel>(P, l, child, smem, red); break;
+      default: expand_item<ToyModel>(P, l, child, smem, red); break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K3: leaf expansion of one level-(D-1) node, fused with its backup.
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const PSet<M> &nb,
+                                int l, unsigned long long node, int slot, float *sm_rb,
+                                float *sm_lo, float *sm_v) {
+  const int lane = threadIdx.x & 31, N = P.N, W = P.W;
+  const int a = slot / W, k = slot - (slot / W) * W;
+  int j;
+  const typename M::O o = branch_obs<M>(P, nb, l, a, k, node, dm, j);
+
+  OnlineLSE L1, L0;
+  L1.init(); L0.init();
+  Kahan R;
+  R.init();
+  const int npairs = (N + 1) >> 1;
+  for (int p = lane; p < npairs; p += 32) {
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (M::kStochastic) w = draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, l, a, k, node);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int i = 2 * p + e;
+      if (i < N) {
+        typename M::S s = nb.get(i);
+        const float lw = nb.lw[i], wi = nb.w[i];
+        const float r = M::step(s, a, e ? w.z : w.x, e ? w.w : w.y, dm);
+        const float ell = M::loglik(s, a, o, dm);
+        const float h = M::heuristic(s, P);
+        R.add(wi * r);
+        L1.add(lw + ell, h);
+        L0.add(ell);
+      }
+    }
+  }
+  float m1 = L1.m, s1 = L1.s.value(), h1 = L1.h.value();
+  float m0 = L0.m, s0 = L0.s.value(), h0 = 0.f;
+  warp_lse(m1, s1, h1);
+  warp_lse(m0, s0, h0);
+  const float rbar = warp_sum(R.value());
+  if (lane == 0) {
+    const float lse1 = (s1 > 0.f) ? m1 + logf(s1) : -CUDART_INF_F;
+    float lom;
+    if (P.branch_mode == kEnumerate) lom = lse1;
+    else lom = (lse1 > -CUDART_INF_F) ? logf((float)N) + lse1 - (m0 + logf(s0)) : -CUDART_INF_F;
+    const float v = (s1 > 0.f) ? h1 / s1 : 0.f;
+    sm_rb[slot] = rbar;
+    sm_lo[slot] = lom;
+    sm_v[slot] = v;
+    if (P.keep_leaf) {
+      const unsigned long long c = node * (unsigned long long)P.AW + (unsigned long long)slot;
+      P.rbar[l + 1][c] = rbar;
+      P.lom[l + 1][c] = lom;
+      P.V[l + 1][c] = v;
+      if (P.keep_debug) {
+        P.rep[l + 1][c] = j;
+        const float2 of = M::obs_f2(o);
+        P.obs[l + 1][2 * c] = of.x;
+        P.obs[l + 1][2 * c + 1] = of.y;
+      }
+    }
+  }
+}
+
+template <class M>
+__device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *smem, float *red) {
+  const DevModel &dm = *P.model;
+  const int N = P.N, AW = P.AW, l = P.D - 1;
+  PSet<M> nb = PSet<M>::smem(smem, N);
+  float *sm_rb = smem + (M::kStochastic ? 4 : 3) * N;
+  float *sm_lo = sm_rb + AW, *sm_v = sm_lo + AW;
+  __shared__ float2 s_mu;
+
+  if (P.leaf_gen) {
+    const unsigned long long parent = node / (unsigned long long)AW;
+    PSet<M> src = PSet<M>::level(P, l - 1, (long long)parent);
+    float2 mu;
+    build_child<M>(P, dm, l - 1, node, src, nb, nb.lw, nb.w, red, true, &mu);
+    if (threadIdx.x == 0) s_mu = mu;
+  } else {
+    PSet<M> src = PSet<M>::level(P, l, (long long)node);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      nb.put(i, src.get(i));
+      const float lw = src.lw[i];
+      nb.lw[i] = lw;
+      nb.w[i] = (lw > -CUDART_INF_F) ? __expf(lw) : 0.f;
+    }
+    if (threadIdx.x == 0)
+      s_mu = (P.pi_mode == kPiNavDist) ? make_float2(P.mu[l][2 * node], P.mu[l][2 * node + 1])
+                                       : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int slot = wid; slot < AW; slot += nw)
+    leaf_child_warp<M>(P, dm, nb, l, node, slot, sm_rb, sm_lo, sm_v);
+  __syncthreads();
+
+  if (wid == 0) {
+    __shared__ float s_q[kMaxActions];
+    __shared__ float s_v;
+    node_backup_warp(P, sm_rb, sm_lo, sm_v, s_mu, s_q, &s_v);
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < P.A) P.Q[l][node * P.A + lane] = s_q[lane];
+    if (lane == 0) P.V[l][node] = s_v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_leaf(const PlanDesc *plans, StageTable st,
+                                              long long total) {
+  extern __shared__ float smem[];
+  __shared__ float red[32];
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int pi = find_plan(st, item);
+    const PlanDesc &P = plans[st.plan[pi]];
+    const unsigned long long node = (unsigned long long)(item - st.prefix[pi]);
+    switch (P.kind) {
+      case kNav: leaf_item<NavModel>(P, node, smem, red); break;
+      case kGrid: leaf_item<GridModel>(P, node, smem, red); break;
+      default: leaf_item<ToyModel>(P, node, smem, red); break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K4: backup of one level (16 lanes per node, lane = action), FP32.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void backup_node16(const PlanDesc &P, int l, unsigned long long n,
+                                              int a, bool valid) {
+  const int A = P.A, W = P.W, AW = P.AW;
+  float q = 0.f, z = -CUDART_INF_F;
+  if (valid && a < A) {
+    const unsigned long long c0 = n * (unsigned long long)AW + (unsigned long long)(a * W);
+    const float *rb = P.rbar[l + 1] + c0, *lo = P.lom[l + 1] + c0, *vc = P.V[l + 1] + c0;
+    float rs = 0.f, M = -CUDART_INF_F;
+    for (int k = 0; k < W; ++k) { rs += rb[k]; M = fmaxf(M, lo[k]); }
+    float fut = 0.f;
+    if (M > -CUDART_INF_F) {
+      Kahan num, den;
+      num.init(); den.init();
+      for (int k = 0; k < W; ++k) {
+        const float om = __expf(lo[k] - M);
+        num.add(om * vc[k]);
+        den.add(om);
+      }
+      fut = num.value() / den.value();
+    } else {
+      atomicAdd(&P.result->degenerate, 1u);
+    }
+    q = rs / (float)W + P.gamma * fut;
+    float2 mu = make_float2(0.f, 0.f);
+    if (P.pi_mode == kPiNavDist) mu = make_float2(P.mu[l][2 * n], P.mu[l][2 * n + 1]);
+    z = log_pibar(P, mu, a) + q * P.inv_eta;
+    P.Q[l][n * A + a] = q;
+  }
+  float zm = z;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o, 16));
+  float e = (valid && a < A && z > -CUDART_INF_F) ? __expf(z - zm) : 0.f;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
+  if (valid && a == 0) P.V[l][n] = P.eta * (zm + logf(e));
+}
+
+__global__ void __launch_bounds__(256) k_backup(const PlanDesc *plans, StageTable st,
+                                                long long total_threads) {
+  // whole warps iterate together (the 16-lane shuffles run under a full-warp mask)
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+       t - (threadIdx.x & 31) < total_threads; t += (long long)gridDim.x * blockDim.x) {
+    const long long node_item = t >> 4;
+    const bool valid = t < total_threads;
+    const long long safe = valid ? node_item : ((total_threads - 1) >> 4);
+    const int pi = find_plan(st, safe);
+    const PlanDesc &P = plans[st.plan[pi]];
+    const int l = st.levels ? st.levels[pi] : st.level;
+    backup_node16(P, l, (unsigned long long)(safe - st.prefix[pi]), (int)(t & 15), valid);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Tail: the plan's small levels top..1 in FP32 (one CTA), then the root in FP64 and the
+// Alg. 1 action choice.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_backup_tail(const PlanDesc *plans, StageTable st) {
+  const int pi = blockIdx.x;
+  const PlanDesc &P = plans[st.plan[pi]];
+  if (P.result->status & kStatusDegenerateRoot) return;
+  const int top = st.levels ? st.levels[pi] : st.level;
+  for (int l = top; l >= 1; --l) {
+    unsigned long long nodes = 1;
+    for (int i = 0; i < l; ++i) nodes *= (unsigned long long)P.AW;
+    const unsigned long long tasks = nodes * 16ull;
+    for (unsigned long long t = threadIdx.x; t - (threadIdx.x & 31) < tasks; t += blockDim.x) {
+      const bool valid = t < tasks;
+      backup_node16(P, l, valid ? (t >> 4) : 0, (int)(t & 15), valid);
+    }
+    __syncthreads();
+  }
+  // root level in double precision
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, A = P.A, W = P.W;
+    double q = 0.0, z = -CUDART_INF;
+    float2 mu = make_float2(0.f, 0.f);
+    if (P.pi_mode == kPiNavDist) mu = make_float2(P.mu[0][0], P.mu[0][1]);
+    double lp = -CUDART_INF;
+    if (lane < A) {
+      double rs = 0.0;
+      float M = -CUDART_INF_F;
+      for (int k = 0; k < W; ++k) {
+        rs += (double)P.rbar[1][lane * W + k];
+        M = fmaxf(M, P.lom[1][lane * W + k]);
+      }
+      double fut = 0.0;
+      if (M > -CUDART_INF_F) {
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < W; ++k) {
+          const double om = exp((double)P.lom[1][lane * W + k] - (double)M);
+          num += om * (double)P.V[1][lane * W + k];
+          den += om;
+        }
+        fut = num / den;
+      } else {
+        atomicAdd(&P.result->degenerate, 1u);
+      }
+      q = rs / (double)W + (double)P.gamma * fut;
+      lp = (double)log_pibar(P, mu, lane);
+      z = lp + q / (double)P.eta;
+    }
+    double zm = z;
+    for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+    double e = (lane < A && z > -CUDART_INF) ? exp(z - zm) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    const double v = (double)P.eta * (zm + log(e));
+    // argmax of Q + eta log pibar, lowest index on ties
+    double sc = (lane < A) ? q + (double)P.eta * lp : -CUDART_INF;
+    int best = (lane < A) ? lane : 1 << 30;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
+      const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      if (sc2 > sc || (sc2 == sc && b2 < best)) { sc = sc2; best = b2; }
+    }
+    DevResult *R = P.result;
+    if (lane < A) {
+      R->q[lane] = q;
+      R->policy[lane] = exp(lp + (q - v) / (double)P.eta);
+      P.Q[0][lane] = (float)q;
+    }
+    if (lane == 0) {
+      R->v_root = v;
+      R->action = best;
+      R->flags |= 2u;
+      P.V[0][0] = (float)v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K5: SIR belief update of one agent (one CTA, up to 65536 particles).
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red, double *dred) {
+  const int N = B.N;
+  PSet<M> cur, nxt;
+  if constexpr (M::kStochastic) {
+    cur = PSet<M>{B.x, B.y, B.lw, nullptr};
+    nxt = PSet<M>{B.tx, B.ty, B.tlw, nullptr};
+  } else {
+    cur.s = B.s; cur.lw = B.lw; cur.w = nullptr;
+    nxt.s = B.ts; nxt.lw = B.tlw; nxt.w = nullptr;
+  }
+  typename M::O o;
+  if constexpr (M::kStochastic) o = typename M::O{B.obs_f[0], B.obs_f[1]};
+  else o = typename M::O{B.obs_i};
+
+  float m = -CUDART_INF_F;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    typename M::S s = cur.get(i);
+    uint32_t wa = 0, wb = 0;
+    if (M::kStochastic) {
+      const uint4 w = draw(B.key0, B.key1, (uint32_t)(i >> 1), kPurposeBeliefStep, 0, 0, 0, B.t);
+      wa = (i & 1) ? w.z : w.x;
+      wb = (i & 1) ? w.w : w.y;
+    }
+    M::step(s, B.action, wa, wb, dm);
+    const float L = cur.lw[i] + M::loglik(s, B.action, o, dm);
+    nxt.put(i, s);
+    nxt.lw[i] = L;
+    m = fmaxf(m, L);
+  }
+  m = block_max(m, red);
+  if (!(m > -CUDART_INF_F)) {
+    if (threadIdx.x == 0) { B.out->status = 1; B.out->ess = 0.0; B.out->resampled = 0; }
+    return;
+  }
+  Kahan S;
+  S.init();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) S.add(__expf(nxt.lw[i] - m));
+  const float lse = m + logf(block_sum(S.value(), red));
+  Kahan Q2;
+  Q2.init();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float nl = nxt.lw[i] - lse;
+    nxt.lw[i] = nl;
+    const float w = __expf(nl);
+    Q2.add(w * w);
+  }
+  const float sw2 = block_sum(Q2.value(), red);
+  const float ess = 1.0f / sw2;
+  const bool resample = ess < 0.5f * (float)N;
+
+  if (resample) {
+    // inclusive CDF in FP64: contiguous chunk per thread, then a block scan of chunk sums
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int chunk = (N + T - 1) / T;
+    const int b = tid * chunk, e = min(N, b + chunk);
+    double acc = 0.0;
+    for (int i = b; i < e; ++i) acc += (double)__expf(nxt.lw[i]);
+    dred[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double run = 0.0;
+      for (int t = 0; t < T; ++t) { const double v = dred[t]; dred[t] = run; run += v; }
+      dred[T] = run;
+    }
+    __syncthreads();
+    double run = dred[tid];
+    for (int i = b; i < e; ++i) { run += (double)__expf(nxt.lw[i]); B.cdf[i] = run; }
+    __syncthreads();
+    const double total = B.cdf[N - 1];
+    const uint4 w = draw(B.key0, B.key1, 0u, kPurposeResample, 0, 0, 0, B.t);
+    const double u0 = (double)u01(w.x);
+    const float nlw = -logf((float)N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double pos = (u0 + (double)i) / (double)N * total;
+      int lo = 0, hi = N - 1;     // first k with pos < cdf[k], else N-1
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pos < B.cdf[mid]) hi = mid; else lo = mid + 1;
+      }
+      B.anc[i] = lo;
+      cur.put(i, nxt.get(lo));
+      cur.lw[i] = nlw;
+    }
+  } else {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      cur.put(i, nxt.get(i));
+      cur.lw[i] = nxt.lw[i];
+      B.anc[i] = i;
+    }
+  }
+  if (threadIdx.x == 0) {
+    B.out->status = 0;
+    B.out->ess = (double)ess;
+    B.out->resampled = resample ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_belief(BeliefArgs B) {
+  __shared__ float red[32];
+  __shared__ double dred[1025];
+  const DevModel &dm = *B.model;
+  switch (B.kind) {
+    case kNav: belief_plan<NavModel>(B, dm, red, dred); break;
+    case kGrid: belief_plan<GridModel>(B, dm, red, dred); break;
+    default: belief_plan<ToyModel>(B, dm, red, dred); break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------------------
+size_t leaf_smem_bytes(int kind, int N, int AW) {
+  const int per = (kind == kNav) ? 16 : 12;
+  return (size_t)per * N + 3 * sizeof(float) * (size_t)AW + 64;
+}
+size_t expand_smem_bytes(int N) { return 8 * (size_t)N + 64; }
+
+cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s) {
+  k_root_prep<<<st.n_plans, 1024, 0, s>>>(d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
+                          int grid_cap, cudaStream_t s) {
+  const size_t smem = expand_smem_bytes(maxN);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long long grid = total < grid_cap ? total : grid_cap;
+  k_expand<<<(unsigned)grid, 256, smem, s>>>(d, st, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
+                        int threads, int grid_cap, cudaStream_t s) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long long grid = total < grid_cap ? total : grid_cap;
+  k_leaf<<<(unsigned)grid, threads, smem, s>>>(d, st, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backup(const PlanDesc *d, const StageTable &st, long long total_nodes,
+                          cudaStream_t s) {
+  const long long threads = total_nodes * 16;
+  long long grid = (threads + 255) / 256;
+  if (grid > (1ll << 20)) grid = 1ll << 20;
+  k_backup<<<(unsigned)grid, 256, 0, s>>>(d, st, threads);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backup_tail(const PlanDesc *d, const StageTable &st, cudaStream_t s) {
+  k_backup_tail<<<st.n_plans, 1024, 0, s>>>(d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s) {
+  k_belief<<<1, 1024, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+}  // namespace vopp

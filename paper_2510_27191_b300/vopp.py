@@ -1,0 +1,330 @@
+"""Thin ctypes binding of libvopp (include/vopp.h): the same entry points, argument
+marshalling only.  Every step of a plan runs in the library's CUDA kernels; this module
+never computes any part of the method.  Importing it fails loudly when libvopp.so is
+missing; there is no CPU fallback.
+
+PyTorch supplies device memory and streams: pass ``torch.cuda`` tensors (their data_ptr()
+becomes a device pointer, VOPP_PTR_DEVICE) and ``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvopp.so")
+
+VOPP_OK, VOPP_E_INVALID, VOPP_E_NOMEM, VOPP_E_BUDGET = 0, -1, -2, -3
+VOPP_E_CUDA, VOPP_E_TIMEOUT, VOPP_E_DEGENERATE, VOPP_E_BUSY = -4, -5, -6, -7
+VOPP_NAV2D, VOPP_GRID, VOPP_TOY2 = 0, 1, 2
+VOPP_BRANCH_SAMPLE, VOPP_BRANCH_ENUMERATE = 0, 1
+VOPP_PI_UNIFORM, VOPP_PI_FIXED, VOPP_PI_NAV_DIST = 0, 1, 2
+VOPP_PTR_DEVICE = 1
+VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT = 1, 2
+VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
+(VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
+ VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU) = range(11)
+VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP, VOPP_OPT_TAIL_MAX_NODES = 1, 2, 3, 4
+VOPP_MAX_ACTIONS = 16
+NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
+
+ERRORS = {VOPP_E_INVALID: "VOPP_E_INVALID", VOPP_E_NOMEM: "VOPP_E_NOMEM",
+          VOPP_E_BUDGET: "VOPP_E_BUDGET", VOPP_E_CUDA: "VOPP_E_CUDA",
+          VOPP_E_TIMEOUT: "VOPP_E_TIMEOUT", VOPP_E_DEGENERATE: "VOPP_E_DEGENERATE",
+          VOPP_E_BUSY: "VOPP_E_BUSY"}
+
+
+class VoppError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class vopp_model_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("branch_mode", ctypes.c_int32),
+                ("pi_mode", ctypes.c_int32), ("h_zero", ctypes.c_int32),
+                ("pi_temp", ctypes.c_float), ("pi_fixed", ctypes.c_float * VOPP_MAX_ACTIONS),
+                ("rock_x", ctypes.c_int32 * 8), ("rock_y", ctypes.c_int32 * 8)]
+
+
+class vopp_plan_result(ctypes.Structure):
+    _fields_ = [("action", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("v_root", ctypes.c_double), ("q", ctypes.c_double * VOPP_MAX_ACTIONS),
+                ("policy", ctypes.c_double * VOPP_MAX_ACTIONS),
+                ("particle_steps", ctypes.c_uint64), ("nodes", ctypes.c_uint64),
+                ("degenerate_actions", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class vopp_plan_params(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("width", ctypes.c_int32), ("eta", ctypes.c_float),
+                ("gamma", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("pi_bar", ctypes.POINTER(ctypes.c_float))]
+
+
+class vopp_plan_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_void_p), ("root_states", ctypes.c_void_p),
+                ("root_weights", ctypes.c_void_p), ("n_particles", ctypes.c_int32),
+                ("ptr_flags", ctypes.c_uint32), ("params", vopp_plan_params)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvopp.so not built ({LIB_PATH}); run "
+                          "`python -m paper_2510_27191_b300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, u64, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
+    sz, fp, dp = ctypes.c_size_t, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "vopp_ctx_create": ([ctypes.c_int, sz, ctypes.c_size_t, ctypes.POINTER(vp)], ctypes.c_int),
+        "vopp_ctx_destroy": ([vp], None),
+        "vopp_ctx_set_tree_detail": ([vp, ctypes.c_int], ctypes.c_int),
+        "vopp_ctx_set_option": ([vp, i32, i64], ctypes.c_int),
+        "vopp_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "vopp_ctx_kernel_times": ([vp, ctypes.POINTER(ctypes.c_char_p), dp,
+                                   ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "vopp_ctx_reset_kernel_times": ([vp], ctypes.c_int),
+        "vopp_ctx_counters": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                               ctypes.POINTER(u64)], ctypes.c_int),
+        "vopp_plan_footprint": ([vp, i32, i32, i32, ctypes.POINTER(sz)], ctypes.c_int),
+        "vopp_create_model": ([vp, ctypes.POINTER(vopp_model_desc), ctypes.POINTER(vp)], ctypes.c_int),
+        "vopp_model_destroy": ([vp], None),
+        "vopp_model_num_actions": ([vp], ctypes.c_int),
+        "vopp_grid_thresholds": ([ctypes.POINTER(u64), i32], ctypes.c_int),
+        "vopp_plan": ([vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, fp, u64, u32,
+                       ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_tree_read": ([vp, i32, i32, u64, u64, vp, u32], ctypes.c_int),
+        "vopp_tree_read_plan": ([vp, i32, i32, i32, u64, u64, vp, u32], ctypes.c_int),
+        "vopp_agent_create": ([vp, vp, vp, i32, u64, u32, ctypes.POINTER(vp)], ctypes.c_int),
+        "vopp_agent_plan": ([vp, ctypes.POINTER(vopp_plan_params),
+                             ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_belief_update": ([vp, i32, vp, dp, ctypes.POINTER(i32)], ctypes.c_int),
+        "vopp_agent_get_particles": ([vp, vp, vp, vp, u32], ctypes.c_int),
+        "vopp_agent_num_particles": ([vp], ctypes.c_int),
+        "vopp_agent_destroy": ([vp], None),
+        "vopp_plan_batch": ([vp, i32, ctypes.POINTER(vopp_plan_request),
+                             ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_last_error": ([], ctypes.c_char_p),
+        "vopp_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise VoppError(rc, lib.vopp_last_error().decode())
+    return rc
+
+
+# ---- the C entry points under their own names (ctypes handles as ints) ------------------
+def vopp_ctx_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    check(lib.vopp_ctx_create(device, hbm_budget_bytes, cuda_stream, ctypes.byref(h)))
+    return h.value
+
+
+def vopp_ctx_destroy(ctx: int) -> None:
+    lib.vopp_ctx_destroy(ctx)
+
+
+def vopp_ctx_set_tree_detail(ctx: int, detail: int) -> None:
+    check(lib.vopp_ctx_set_tree_detail(ctx, detail))
+
+
+def vopp_ctx_set_option(ctx: int, option: int, value: int) -> None:
+    check(lib.vopp_ctx_set_option(ctx, option, value))
+
+
+def vopp_ctx_set_timing(ctx: int, enable: bool) -> None:
+    check(lib.vopp_ctx_set_timing(ctx, int(enable)))
+
+
+def vopp_ctx_kernel_times(ctx: int) -> dict:
+    n = ctypes.c_int(16)
+    names = (ctypes.c_char_p * 16)()
+    ms = (ctypes.c_double * 16)()
+    cnt = (ctypes.c_uint64 * 16)()
+    check(lib.vopp_ctx_kernel_times(ctx, names, ms, cnt, ctypes.byref(n)))
+    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(n.value)}
+
+
+def vopp_ctx_reset_kernel_times(ctx: int) -> None:
+    check(lib.vopp_ctx_reset_kernel_times(ctx))
+
+
+def vopp_ctx_counters(ctx: int) -> dict:
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib.vopp_ctx_counters(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(h2d_bytes=a.value, d2h_bytes=b.value, launches=c.value)
+
+
+def make_desc(kind: int, branch_mode: int = VOPP_BRANCH_SAMPLE, pi_mode: int = VOPP_PI_UNIFORM,
+              pi_temp: float = 2.0, pi_fixed=None, rock_x=None, rock_y=None,
+              h_zero: bool = False) -> vopp_model_desc:
+    d = vopp_model_desc()
+    d.kind, d.branch_mode, d.pi_mode, d.h_zero, d.pi_temp = kind, branch_mode, pi_mode, int(h_zero), pi_temp
+    if pi_fixed is not None:
+        for a, v in enumerate(pi_fixed):
+            d.pi_fixed[a] = float(v)
+    if rock_x is not None:
+        for r in range(8):
+            d.rock_x[r], d.rock_y[r] = int(rock_x[r]), int(rock_y[r])
+    return d
+
+
+def vopp_create_model(ctx: int, desc: vopp_model_desc) -> int:
+    h = ctypes.c_void_p()
+    check(lib.vopp_create_model(ctx, ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def vopp_model_destroy(model: int) -> None:
+    lib.vopp_model_destroy(model)
+
+
+def vopp_model_num_actions(model: int) -> int:
+    return check(lib.vopp_model_num_actions(model))
+
+
+def vopp_grid_thresholds(n: int = 222) -> np.ndarray:
+    out = (ctypes.c_uint64 * n)()
+    check(lib.vopp_grid_thresholds(out, n))
+    return np.array(out[:], dtype=np.uint64)
+
+
+def vopp_plan_footprint(model: int, n: int, depth: int, width: int) -> int:
+    b = ctypes.c_size_t()
+    check(lib.vopp_plan_footprint(model, n, depth, width, ctypes.byref(b)))
+    return b.value
+
+
+def _addr(a):
+    """(pointer, is_device, keepalive) for a numpy array, torch tensor or None."""
+    if a is None:
+        return None, False, None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), bool(a.is_cuda), a
+    arr = np.ascontiguousarray(a)
+    return arr.ctypes.data, False, arr
+
+
+def _result_dict(r: vopp_plan_result, A: int) -> dict:
+    return dict(action=r.action, flags=r.flags, v_root=r.v_root, q=np.array(r.q[:A]),
+                policy=np.array(r.policy[:A]), particle_steps=r.particle_steps, nodes=r.nodes,
+                degenerate_actions=r.degenerate_actions)
+
+
+def vopp_plan(model: int, root_states, root_weights, n_particles: int, depth: int, width: int,
+              eta: float, gamma: float, pi_bar=None, seed: int = 0, ptr_flags: int | None = None) -> dict:
+    """root_states: NAV2D float32[2N] (x then y), GRID/TOY2 int32[N]; numpy (host) or torch
+    CUDA tensors (device).  Returns the vopp_plan_result as a dict."""
+    sp, sdev, keep1 = _addr(root_states)
+    wp, wdev, keep2 = _addr(root_weights)
+    if ptr_flags is None:
+        ptr_flags = VOPP_PTR_DEVICE if sdev else 0
+    pib = None
+    if pi_bar is not None:
+        pib = (ctypes.c_float * len(pi_bar))(*[float(v) for v in pi_bar])
+    r = vopp_plan_result()
+    check(lib.vopp_plan(model, sp, wp, n_particles, depth, width, eta, gamma,
+                        ctypes.cast(pib, ctypes.POINTER(ctypes.c_float)) if pib is not None else None,
+                        seed & 0xFFFFFFFFFFFFFFFF, ptr_flags, ctypes.byref(r)))
+    del keep1, keep2
+    return _result_dict(r, vopp_model_num_actions(model))
+
+
+def vopp_tree_read(ctx: int, field: int, level: int, count: int, offset: int = 0, plan: int = 0,
+                   out=None) -> np.ndarray:
+    dtype = np.int32 if field in (VOPP_FIELD_REP, VOPP_FIELD_PS) else np.float32
+    if out is None:
+        out = np.empty(count, dtype=dtype)
+    check(lib.vopp_tree_read_plan(ctx, plan, field, level, offset, count, out.ctypes.data, 0))
+    return out
+
+
+def vopp_agent_create(model: int, states, weights, n: int, seed: int) -> int:
+    sp, sdev, k1 = _addr(states)
+    wp, _, k2 = _addr(weights)
+    h = ctypes.c_void_p()
+    check(lib.vopp_agent_create(model, sp, wp, n, seed & 0xFFFFFFFFFFFFFFFF,
+                                VOPP_PTR_DEVICE if sdev else 0, ctypes.byref(h)))
+    del k1, k2
+    return h.value
+
+
+def make_params(depth: int, width: int, eta: float, gamma: float, seed: int, pi_bar=None):
+    p = vopp_plan_params()
+    p.depth, p.width, p.eta, p.gamma, p.seed = depth, width, eta, gamma, seed & 0xFFFFFFFFFFFFFFFF
+    keep = None
+    if pi_bar is not None:
+        keep = (ctypes.c_float * len(pi_bar))(*[float(v) for v in pi_bar])
+        p.pi_bar = ctypes.cast(keep, ctypes.POINTER(ctypes.c_float))
+    return p, keep
+
+
+def vopp_agent_plan(agent: int, model: int, depth: int, width: int, eta: float, gamma: float,
+                    seed: int, pi_bar=None) -> dict:
+    p, keep = make_params(depth, width, eta, gamma, seed, pi_bar)
+    r = vopp_plan_result()
+    check(lib.vopp_agent_plan(agent, ctypes.byref(p), ctypes.byref(r)))
+    del keep
+    return _result_dict(r, vopp_model_num_actions(model))
+
+
+def vopp_belief_update(agent: int, action: int, obs, kind: int):
+    if kind == VOPP_NAV2D:
+        o = (ctypes.c_float * 2)(float(obs[0]), float(obs[1]))
+    else:
+        o = (ctypes.c_int32 * 1)(int(np.atleast_1d(obs)[0]))
+    ess = ctypes.c_double()
+    res = ctypes.c_int32()
+    check(lib.vopp_belief_update(agent, action, o, ctypes.byref(ess), ctypes.byref(res)))
+    return ess.value, bool(res.value)
+
+
+def vopp_agent_get_particles(agent: int, kind: int):
+    n = check(lib.vopp_agent_num_particles(agent))
+    st = np.empty(2 * n, dtype=np.float32) if kind == VOPP_NAV2D else np.empty(n, dtype=np.int32)
+    lw = np.empty(n, dtype=np.float32)
+    anc = np.empty(n, dtype=np.int32)
+    check(lib.vopp_agent_get_particles(agent, st.ctypes.data, lw.ctypes.data, anc.ctypes.data, 0))
+    return st, lw, anc
+
+
+def vopp_agent_destroy(agent: int) -> None:
+    lib.vopp_agent_destroy(agent)
+
+
+def vopp_plan_batch(ctx: int, requests: list) -> tuple[list, list]:
+    """requests: dicts with model, states, weights, n, depth, width, eta, gamma, seed, pi_bar,
+    A.  Returns (results, keepalive)."""
+    n = len(requests)
+    reqs = (vopp_plan_request * n)()
+    keep = []
+    for i, q in enumerate(requests):
+        sp, sdev, k1 = _addr(q["states"])
+        wp, _, k2 = _addr(q.get("weights"))
+        keep += [k1, k2]
+        p, k3 = make_params(q["depth"], q["width"], q["eta"], q["gamma"], q["seed"], q.get("pi_bar"))
+        keep.append(k3)
+        reqs[i].model = q["model"]
+        reqs[i].root_states = sp
+        reqs[i].root_weights = wp
+        reqs[i].n_particles = q["n"]
+        reqs[i].ptr_flags = VOPP_PTR_DEVICE if sdev else 0
+        reqs[i].params = p
+    outs = (vopp_plan_result * n)()
+    check(lib.vopp_plan_batch(ctx, n, reqs, outs))
+    return [_result_dict(outs[i], requests[i]["A"]) for i in range(n)], keep
+
+
+def vopp_version() -> str:
+    return lib.vopp_version().decode()

@@ -1,0 +1,194 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (needs a GPU).
+
+Tolerance: |gpu - oracle| <= 1e-4 * max(|oracle|, 1) for every value (node V and Q,
+branch mean rewards, log branch weights, particle coordinates and log weights);
+integers (representatives j, grid states, discrete observations) bit-exact.  Nodes at or
+below an oracle-flagged near-threshold NAV2D goal test (|x^2+y^2-0.25| < 1e-5, where FP32
+and FP64 may take different sides) are exempt from the per-node check; the root is always
+compared.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_27191_b300 import workloads as WL
+from tests.parity import RTOL, Gpu, Spec, action_agrees, assert_close, compare_full_tree
+
+pytestmark = pytest.mark.gpu
+
+
+def _full(spec, leaf_gen=True, leaf_threads=None, device_inputs=False):
+    g = Gpu(spec, leaf_gen=leaf_gen, leaf_threads=leaf_threads)
+    try:
+        res = g.plan(device_inputs=device_inputs)
+        top = spec.D - 1 if not leaf_gen or spec.D < 2 else spec.D - 2
+        orc = spec.run_oracle(dump_levels=max(top, 0))
+        assert orc["status"] == O.OK
+        compare_full_tree(spec, g, res, orc, max(top, 0))
+        assert action_agrees(res, orc, spec)
+        assert res["particle_steps"] == orc["particle_steps"]
+        return res, orc
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("eta", [0.05, 1.0])
+def test_toy2_enumerate_matches_oracle(depth, eta):
+    spec = Spec(WL.TOY2, 2, depth, 2, eta=eta, branch_mode=WL.BRANCH_ENUMERATE,
+                root=dict(s=np.array([0, 1], np.int32), w=np.array([0.6, 0.4], np.float32)))
+    _full(spec)
+
+
+@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (257, 2, 4), (1, 3, 2), (1000, 2, 3)])
+@pytest.mark.parametrize("leaf_gen", [True, False])
+def test_nav_small_full_tree(N, D, W, leaf_gen):
+    _full(Spec(WL.NAV2D, N, D, W, eta=0.7, seed=3, root_seed=N), leaf_gen=leaf_gen)
+
+
+def test_nav_nav_dist_policy_and_weights():
+    _full(Spec(WL.NAV2D, 200, 3, 2, eta=0.5, seed=9, pi_mode=WL.PI_NAV_SOFTMAX_DIST,
+               weights="sparse", root_seed=4))
+
+
+@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (333, 2, 3), (2048, 2, 1)])
+@pytest.mark.parametrize("leaf_gen", [True, False])
+def test_grid_small_full_tree_bit_exact_integers(N, D, W, leaf_gen):
+    _full(Spec(WL.GRID, N, D, W, seed=5, weights="random", root_seed=2), leaf_gen=leaf_gen)
+
+
+def test_grid_enumerate_and_fixed_policy():
+    _full(Spec(WL.GRID, 96, 2, 3, branch_mode=WL.BRANCH_ENUMERATE, pi_mode=WL.PI_FIXED,
+               pi_fixed=[3, 1, 1, 1, 2, 1, 1, 1, 1, 1, 1, 1, 1], seed=7))
+
+
+def test_caller_pi_bar_overrides_model_policy():
+    _full(Spec(WL.NAV2D, 128, 2, 2, pi_mode=WL.PI_NAV_SOFTMAX_DIST, pi_bar=[0.1, 0.2, 0.3, 0.4]))
+
+
+def test_leaf_threads_do_not_change_results():
+    spec = Spec(WL.NAV2D, 300, 2, 4, seed=11)
+    r1 = Gpu(spec, leaf_threads=256)
+    a = r1.plan()
+    r1.close()
+    r2 = Gpu(spec, leaf_threads=64)
+    b = r2.plan()
+    r2.close()
+    assert_close(b["q"], a["q"], "Q across leaf CTA sizes")
+
+
+def test_device_inputs_equal_host_inputs():
+    spec = Spec(WL.NAV2D, 500, 2, 3, weights="random", seed=2)
+    g = Gpu(spec)
+    try:
+        a = g.plan(device_inputs=False)
+        b = g.plan(device_inputs=True)
+        assert a["q"].tolist() == b["q"].tolist() and a["action"] == b["action"]
+    finally:
+        g.close()
+
+
+def test_deterministic_replay():
+    spec = Spec(WL.GRID, 1024, 3, 3, seed=21)
+    g = Gpu(spec)
+    try:
+        a = g.plan()
+        b = g.plan()
+        assert a["q"].tolist() == b["q"].tolist() and a["v_root"] == b["v_root"]
+        c = g.plan(seed=22)
+        assert c["q"].tolist() != a["q"].tolist()
+    finally:
+        g.close()
+
+
+def test_config1_full_tree():
+    """NAV2D, N=256, depth 3, 4 actions x 4 branches, eta 1, gamma 0.95: every node."""
+    spec = Spec.from_plan(WL.CONFIG1)
+    for seed in range(1, 6):
+        spec.seed = seed
+        _full(spec)
+
+
+def test_depth0_and_degenerate_root():
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(WL.NAV2D, 100, 0, 2, seed=1, weights="random")
+    g = Gpu(spec)
+    try:
+        res = g.plan()
+        orc = spec.run_oracle()
+        assert_close([res["v_root"]], [orc["v_root"]], "depth-0 V")
+        assert_close(res["q"], orc["q_root"], "depth-0 Q")
+        assert res["action"] == orc["action"]
+        # every root particle inside the goal disc: zero mass
+        x = np.full(8, 0.1, np.float32)
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_plan(g.model, np.concatenate([x, x]), None, 8, 2, 2, 1.0, 0.95, None, 1)
+        assert e.value.code == V.VOPP_E_DEGENERATE
+    finally:
+        g.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(WL.NAV2D, 16, 2, 2)
+    g = Gpu(spec)
+    st = spec.states()
+    bad = [dict(depth=-1), dict(depth=9), dict(width=0), dict(n=0), dict(n=70000), dict(eta=0.0),
+           dict(gamma=1.0), dict(gamma=0.0), dict(pi_bar=[0, 0, 0, 0]), dict(pi_bar=[1, -1, 1, 1])]
+    try:
+        for b in bad:
+            kw = dict(n=16, depth=2, width=2, eta=1.0, gamma=0.9, pi_bar=None)
+            kw.update(b)
+            with pytest.raises(V.VoppError) as e:
+                V.vopp_plan(g.model, st, None, kw["n"], kw["depth"], kw["width"], kw["eta"],
+                            kw["gamma"], kw["pi_bar"], 1)
+            assert e.value.code == V.VOPP_E_INVALID, b
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_plan(g.model, st, np.zeros(16, np.float32), 16, 2, 2, 1.0, 0.9, None, 1)
+        assert e.value.code == V.VOPP_E_DEGENERATE
+        # budget: a context with a 1 MB budget refuses a large plan
+        ctx = V.vopp_ctx_create(0, 1 << 20, 0)
+        m = V.vopp_create_model(ctx, V.make_desc(WL.NAV2D))
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_plan(m, np.zeros(2 * 4096, np.float32) + 5, None, 4096, 4, 4, 1.0, 0.9, None, 1)
+        assert e.value.code == V.VOPP_E_BUDGET
+        V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
+    finally:
+        g.close()
+
+
+def test_config2_root_and_sampled_subtrees():
+    """NAV2D, N=1024, depth 4, 4x4 branches, eta 0.5, distance-softmax reference policy:
+    root Q/V against the full oracle; every node of three sampled level-2 subtrees."""
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec.from_plan(WL.CONFIG2)
+    g = Gpu(spec)
+    try:
+        res = g.plan()
+        orc = spec.run_oracle(outputs=False)
+        assert_close(res["q"], orc["q_root"], "C2 root Q")
+        assert_close([res["v_root"]], [orc["v_root"]], "C2 root V")
+        assert action_agrees(res, orc, spec)
+        AW = 16
+        rng = np.random.default_rng(0)
+        for _ in range(3):
+            path = tuple(int(v) for v in rng.integers(0, AW, 2))
+            sub = spec.run_oracle(path=path)
+            node2 = path[0] * AW + path[1]
+            assert_close(g.read(V.VOPP_FIELD_V, 2, 1, node2), sub["V"][2], f"V2 {path}")
+            assert_close(g.read(V.VOPP_FIELD_Q, 2, 4, node2 * 4), sub["Q"][2][0], f"Q2 {path}")
+            n3 = np.arange(AW) + node2 * AW
+            assert_close(g.read(V.VOPP_FIELD_V, 3, AW, node2 * AW), sub["V"][3], f"V3 {path}",
+                         ~sub["near"][3].astype(bool))
+            assert_close(g.read(V.VOPP_FIELD_Q, 3, AW * 4, node2 * AW * 4),
+                         sub["Q"][3].ravel(), f"Q3 {path}")
+            assert_close(g.read(V.VOPP_FIELD_RBAR, 4, AW * AW, node2 * AW * AW), sub["rbar"][4],
+                         f"rbar4 {path}")
+            assert_close(g.read(V.VOPP_FIELD_LOMEGA, 4, AW * AW, node2 * AW * AW),
+                         sub["lomega"][4], f"lomega4 {path}")
+            np.testing.assert_array_equal(g.read(V.VOPP_FIELD_REP, 4, AW * AW, node2 * AW * AW),
+                                          sub["rep"][4])
+            del n3
+    finally:
+        g.close()
