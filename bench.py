@@ -44,6 +44,9 @@ WORKLOADS = {
     "nav1024_d4": WL.CONFIG2,
     "nav256_d3": WL.CONFIG1,
     "grid2048_d5": WL.CONFIG3,
+    # smaller grid plan (depth 4) used for kernel profiles
+    "grid2048_d4": WL.PlanSpec(kind=WL.GRID, N=2048, D=4, W=3, eta=1.0, gamma=0.95, seed=1,
+                               layout_seed=1, root_seed=1),
 }
 
 # Leaf-kernel roofline: issue-bound FP32/INT/SFU arithmetic.  Algorithmic instruction count

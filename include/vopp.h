@@ -163,7 +163,7 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 /* Tuning options (vopp_ctx_set_option):
  *   VOPP_OPT_LEAF_GEN        1 (default): the leaf kernel builds level D-1 in shared memory
  *                            from level D-2; 0: level D-1 is materialised in HBM first
- *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 256)
+ *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 128)
  *   VOPP_OPT_GRID_CAP        maximum CTAs of an expansion / leaf launch (grid-stride beyond)
  *   VOPP_OPT_TAIL_MAX_NODES  levels with at most this many nodes are backed up by the
  *                            single-CTA tail kernel (default 2048)

@@ -16,7 +16,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/vopp.h"
+#include "vopp.h"
 #include "vopp_internal.h"
 
 using namespace vopp;
@@ -75,7 +75,7 @@ struct vopp_ctx {
   size_t meta_cap = 0;
   int tree_detail = VOPP_TREE_MINIMAL;
   int leaf_gen = 1;              // generate level D-1 inside the leaf kernel
-  int leaf_threads = 256;
+  int leaf_threads = 128;
   int grid_cap = 1 << 30;
   int tail_max_nodes = 2048;
   bool timing = false;
@@ -620,6 +620,8 @@ void fill_grid_tables(DevModel &d, const vopp_model_desc &m) {
     d.thr[d2] = (unsigned long long)std::floor(acc * 4294967296.0);
     d.lacc[d2] = (float)std::log(acc);
     d.l1macc[d2] = (acc < 1.0) ? (float)std::log(1.0 - acc) : -INFINITY;
+    d.lacc2[d2] = (float)std::log2(acc);
+    d.l1macc2[d2] = (acc < 1.0) ? (float)std::log2(1.0 - acc) : -INFINITY;
   }
 }
 
@@ -778,6 +780,8 @@ int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
   h.toy_thr = (unsigned long long)std::floor(0.85 * 4294967296.0);
   h.toy_lc = (float)std::log(0.85);
   h.toy_lw = (float)std::log(0.15);
+  h.toy_lc2 = (float)std::log2(0.85);
+  h.toy_lw2 = (float)std::log2(0.15);
   cudaSetDevice(c->device);
   if (cudaMalloc(&m->dev, sizeof(DevModel)) != cudaSuccess) {
     cudaGetLastError();

@@ -38,8 +38,10 @@ struct DevModel {
   int rock_at[121];                     // GRID: rock index of cell x + 11 y, or -1
   unsigned long long thr[kGridD2];      // GRID: floor(acc(d2) 2^32), acc(0) -> 2^32
   float lacc[kGridD2], l1macc[kGridD2]; // GRID: log acc, log(1 - acc)   (-inf at acc = 1)
+  float lacc2[kGridD2], l1macc2[kGridD2]; // the same in base 2
   unsigned long long toy_thr;           // TOY2: floor(0.85 2^32)
   float toy_lc, toy_lw;                 // TOY2: log 0.85, log 0.15
+  float toy_lc2, toy_lw2;               // TOY2: log2 0.85, log2 0.15
 };
 
 struct DevResult {
@@ -117,6 +119,30 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Round keys of Philox4x32-10 for one key: rk[2r], rk[2r+1] = (k0, k1) + r (W0, W1).
+struct PhiloxKeys {
+  uint32_t k[20];
+  __device__ __forceinline__ void init(uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+      k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+  }
+};
+
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, uint32_t purpose,
                                       uint32_t level, uint32_t a, uint32_t k,
                                       unsigned long long node) {
@@ -125,18 +151,53 @@ __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, ui
                 k0, k1);
 }
 
-// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).
+// u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).  Built from the float
+// 1 + (x >> 9) 2^-23 in [1, 2) minus (1 - 2^-24); the difference is representable, so the
+// subtraction is exact.
 __device__ __forceinline__ float u01(uint32_t x) {
-  return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+  return __uint_as_float((x >> 9) | 0x3F800000u) - 0.999999940395355225f;
 }
 
-// Box-Muller: two N(0,1) values from two Philox words.
+// Hardware base-2 exponential / logarithm (PTX ex2.approx / lg2.approx, flush-to-zero):
+// ex2(-inf) = +0, lg2(+0) = -inf.
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.44269504088896341f;
+constexpr float kLn2 = 0.693147180559945309f;
+
+// -ln(u) for u in (0, 1).  Where -ln u > 2^-8 the hardware base-2 logarithm (absolute
+// error ~2^-22) gives a relative error below 5e-5 that shrinks as u moves away from 1;
+// for u > 1 - 2^-8 the Taylor series -ln(1 - v) = v + v^2/2 + v^3/3 + v^4/4 (v = 1 - u,
+// exact) truncates below v^4 / 5 < 1e-10 relative.
+__device__ __forceinline__ float neg_log_u(float u) {
+  const float v = 1.0f - u;
+  float ser = fmaf(v, 0.25f, 0.33333334f);
+  ser = fmaf(v, ser, 0.5f);
+  ser = fmaf(v, ser, 1.0f);
+  ser *= v;
+  const float hw = -kLn2 * lg2(u);
+  return (v < 0.00390625f) ? ser : hw;
+}
+
+// Box-Muller: (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  The angle is taken as
+// t = 2 pi (u2 - 1/2) in (-pi, pi), where the hardware sine / cosine are accurate, and
+// cos(2 pi u2) = -cos t, sin(2 pi u2) = -sin t.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   const float u1 = u01(a), u2 = u01(b);
-  const float r = sqrtf(-2.0f * logf(u1));
-  float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  return make_float2(r * c, r * s);
+  const float s = 2.0f * neg_log_u(u1);
+  const float r = s * rsqrtf(s);
+  const float t = 6.28318531f * (u2 - 0.5f);
+  float sn, cs;
+  __sincosf(t, &sn, &cs);
+  return make_float2(-r * cs, -r * sn);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -185,26 +246,21 @@ struct OnlineLSE {
   }
 };
 
-// Merge of two (max, sum, hsum) partials; sums are plain floats after compensation.
-__device__ __forceinline__ void lse_merge(float &m, float &s, float &h, float m2, float s2,
-                                          float h2) {
-  const float M = fmaxf(m, m2);
-  if (!(M > -CUDART_INF_F)) { m = M; s = 0.f; h = 0.f; return; }
-  const float f1 = (m > -CUDART_INF_F) ? __expf(m - M) : 0.f;
-  const float f2 = (m2 > -CUDART_INF_F) ? __expf(m2 - M) : 0.f;
-  s = s * f1 + s2 * f2;
-  h = h * f1 + h2 * f2;
-  m = M;
-}
-
-__device__ __forceinline__ void warp_lse(float &m, float &s, float &h) {
+// Warp-wide merge of per-lane max-shifted sums (m, s, h): the lanes agree on the largest
+// shift M first, rescale by 2^(m - M) (base-2 shifts) and add.  Every lane gets the result.
+__device__ __forceinline__ void warp_lse2(float &m, float &s, float &h) {
+  float M = m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+  const float f = (m > -CUDART_INF_F) ? ex2(m - M) : 0.f;
+  s *= f;
+  h *= f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const float m2 = __shfl_xor_sync(0xffffffffu, m, o);
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
-    lse_merge(m, s, h, m2, s2, h2);
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    h += __shfl_xor_sync(0xffffffffu, h, o);
   }
+  m = M;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -254,36 +310,51 @@ struct NavModel {
   __device__ __forceinline__ static bool terminal(const S &s) {
     return s.x * s.x + s.y * s.y <= 0.25f;
   }
+  __device__ __forceinline__ static float dx_of(int a) { return (a == 0) ? 1.0f : ((a == 1) ? -1.0f : 0.0f); }
+  __device__ __forceinline__ static float dy_of(int a) { return (a == 2) ? 1.0f : ((a == 3) ? -1.0f : 0.0f); }
+  // Transition s' = clamp(s + delta_a + 0.1 g, 0, 10); reward +100 on entering the goal disc,
+  // -1 otherwise; terminal states stay put with reward 0.
   __device__ __forceinline__ static float step(S &s, int a, uint32_t wa, uint32_t wb,
                                                const DevModel &) {
-    if (terminal(s)) return 0.0f;
+    const bool term = terminal(s);
     const float2 g = box_muller(wa, wb);
-    const float dx = (a == 0) ? 1.0f : ((a == 1) ? -1.0f : 0.0f);
-    const float dy = (a == 2) ? 1.0f : ((a == 3) ? -1.0f : 0.0f);
-    s.x = fminf(fmaxf((s.x + dx) + 0.1f * g.x, 0.0f), 10.0f);
-    s.y = fminf(fmaxf((s.y + dy) + 0.1f * g.y, 0.0f), 10.0f);
-    return terminal(s) ? 100.0f : -1.0f;
+    const float nx = fminf(fmaxf(fmaf(0.1f, g.x, s.x + dx_of(a)), 0.0f), 10.0f);
+    const float ny = fminf(fmaxf(fmaf(0.1f, g.y, s.y + dy_of(a)), 0.0f), 10.0f);
+    const float r = (nx * nx + ny * ny <= 0.25f) ? 100.0f : -1.0f;
+    s.x = term ? s.x : nx;
+    s.y = term ? s.y : ny;
+    return term ? 0.0f : r;
   }
-  __device__ __forceinline__ static float sigma(float x) { return 0.5f * fabsf(x - 9.0f) + 0.05f; }
+  __device__ __forceinline__ static float sigma(float x) { return fmaf(0.5f, fabsf(x - 9.0f), 0.05f); }
   __device__ __forceinline__ static O draw_obs(const S &s, int, uint32_t w0, uint32_t w1,
                                                const DevModel &) {
     const float2 g = box_muller(w0, w1);
     const float sg = sigma(s.x);
-    return O{s.x + sg * g.x, s.y + sg * g.y};
+    return O{fmaf(sg, g.x, s.x), fmaf(sg, g.y, s.y)};
   }
   __device__ __forceinline__ static O enum_obs(int k) { return O{(float)k, 0.f}; }
-  __device__ __forceinline__ static float loglik(const S &s, int, const O &o, const DevModel &) {
+  // log2 N(o; s', sigma(x')^2 I) = log2 e (-|o - s'|^2 / (2 sigma^2)) - 2 log2 sigma
+  //                                 - log2(2 pi)
+  __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &) {
     const float sg = sigma(s.x);
-    const float inv = __frcp_rn(sg);
+    const float inv = __fdividef(1.0f, sg);
     const float dx = o.x - s.x, dy = o.y - s.y;
-    const float d2 = dx * dx + dy * dy;
-    return -0.5f * d2 * (inv * inv) - 2.0f * __logf(sg) - 1.8378770664093453f;  // log 2 pi
+    const float d2 = fmaf(dx, dx, dy * dy);
+    return fmaf(-0.721347520f * d2, inv * inv, fmaf(-2.0f, lg2(sg), -2.65149613f));
+  }
+  __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
+    return kLn2 * loglik2(s, a, o, m);
+  }
+  // h = a0 + b0 gamma^(m-1), m = max(1, x + y - 1/2); 0 at terminal states.  hz is 0 when
+  // the heuristic is forced to zero, 1 otherwise.
+  __device__ __forceinline__ static float heuristic(const S &s, float log2g, float a0, float b0,
+                                                    bool hz) {
+    const float m = fmaxf(s.x + s.y - 0.5f, 1.0f);
+    const float h = fmaf(b0, ex2((m - 1.0f) * log2g), a0);
+    return (hz || terminal(s)) ? 0.0f : h;
   }
   __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
-    if (P.h_zero || terminal(s)) return 0.0f;
-    const float m = fmaxf(s.x + s.y - 0.5f, 1.0f);
-    const float gk = exp2f((m - 1.0f) * P.log2_gamma);
-    return fmaf(P.h_b0, gk, P.h_a0);
+    return heuristic(s, P.log2_gamma, P.h_a0, P.h_b0, P.h_zero != 0);
   }
   __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2(o.x, o.y); }
 };
@@ -346,9 +417,19 @@ struct GridModel {
     const int dd = d2(s, rk, m);
     return ((o.o == 1) == (bit == 1)) ? m.lacc[dd] : m.l1macc[dd];
   }
+  __device__ __forceinline__ static float loglik2(const S &s, int a, const O &o, const DevModel &m) {
+    if (a < 5) return (o.o == 0) ? 0.0f : -CUDART_INF_F;
+    if (o.o != 1 && o.o != 2) return -CUDART_INF_F;
+    const int rk = a - 5, bit = (s.s >> rk) & 1;
+    const int dd = d2(s, rk, m);
+    return ((o.o == 1) == (bit == 1)) ? m.lacc2[dd] : m.l1macc2[dd];
+  }
+  __device__ __forceinline__ static float heuristic(const S &s, float log2g, float, float, bool hz) {
+    const float h = 10.0f * ex2((float)(10 - gx(s.s)) * log2g);
+    return (hz || gterm(s.s)) ? 0.0f : h;
+  }
   __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
-    if (P.h_zero || gterm(s.s)) return 0.0f;
-    return 10.0f * exp2f((float)(10 - gx(s.s)) * P.log2_gamma);
+    return heuristic(s, P.log2_gamma, P.h_a0, P.h_b0, P.h_zero != 0);
   }
   __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
 };
@@ -374,6 +455,11 @@ struct ToyModel {
     if (o.o != 0 && o.o != 1) return -CUDART_INF_F;
     return (o.o == s.s) ? m.toy_lc : m.toy_lw;
   }
+  __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &m) {
+    if (o.o != 0 && o.o != 1) return -CUDART_INF_F;
+    return (o.o == s.s) ? m.toy_lc2 : m.toy_lw2;
+  }
+  __device__ __forceinline__ static float heuristic(const S &, float, float, float, bool) { return 0.0f; }
   __device__ __forceinline__ static float heuristic(const S &, const PlanDesc &) { return 0.0f; }
   __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
 };

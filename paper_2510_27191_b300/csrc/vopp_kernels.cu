@@ -20,53 +20,124 @@
 namespace vopp {
 
 // ---------------------------------------------------------------------------------------
-// Particle-set views (SoA): global level stores and shared-memory node buffers.
+// Particle-set views.
+//   GNode: a node's particles in a global level store (SoA x[N], y[N] / s[N], lw[N]); the
+//          linear weight is exp(lw).
+//   SNode: a node's particles in shared memory, pair-interleaved so that one 16-byte load
+//          gives both particles of a Philox pair: NAV2D {x0,x1,y0,y1}, GRID/TOY2 {s0,s1};
+//          then {lw0,lw1,w0,w1}.  Odd N pads the last pair with a zero-weight particle.
 // ---------------------------------------------------------------------------------------
-template <class M> struct PSet;
-
-template <> struct PSet<NavModel> {
-  float *x, *y, *lw, *w;  // w only for shared-memory buffers
+template <class M> struct GNode;
+template <> struct GNode<NavModel> {
+  float *x, *y, *lwp;
+  __device__ static GNode at(const PlanDesc &P, int l, long long node) {
+    const long long b = node * P.N;
+    return GNode{P.px[l] + b, P.py[l] + b, P.plw[l] + b};
+  }
   __device__ __forceinline__ NavModel::S get(int i) const { return NavModel::S{x[i], y[i]}; }
   __device__ __forceinline__ void put(int i, const NavModel::S &s) const { x[i] = s.x; y[i] = s.y; }
-  static constexpr int kSmemBytes = 16;  // per particle in a shared node buffer
-  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
+  __device__ __forceinline__ float lw(int i) const { return lwp[i]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { lwp[i] = v; }
+};
+template <class M> struct GNodeInt {
+  int *s;
+  float *lwp;
+  __device__ static GNodeInt at(const PlanDesc &P, int l, long long node) {
     const long long b = node * P.N;
-    return PSet{P.px[l] + b, P.py[l] + b, P.plw[l] + b, nullptr};
+    return GNodeInt{P.ps[l] + b, P.plw[l] + b};
   }
-  __device__ static PSet smem(float *base, int N) {
-    return PSet{base, base + N, base + 2 * N, base + 3 * N};
+  __device__ __forceinline__ typename M::S get(int i) const { return typename M::S{s[i]}; }
+  __device__ __forceinline__ void put(int i, const typename M::S &v) const { s[i] = v.s; }
+  __device__ __forceinline__ float lw(int i) const { return lwp[i]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { lwp[i] = v; }
+};
+template <> struct GNode<GridModel> : GNodeInt<GridModel> {
+  __device__ static GNode at(const PlanDesc &P, int l, long long node) {
+    GNode r; static_cast<GNodeInt<GridModel> &>(r) = GNodeInt<GridModel>::at(P, l, node); return r;
+  }
+};
+template <> struct GNode<ToyModel> : GNodeInt<ToyModel> {
+  __device__ static GNode at(const PlanDesc &P, int l, long long node) {
+    GNode r; static_cast<GNodeInt<ToyModel> &>(r) = GNodeInt<ToyModel>::at(P, l, node); return r;
   }
 };
 
-template <class M> struct PSetInt {
-  int *s;
-  float *lw, *w;
-  __device__ __forceinline__ typename M::S get(int i) const { return typename M::S{s[i]}; }
-  __device__ __forceinline__ void put(int i, const typename M::S &v) const { s[i] = v.s; }
-  static constexpr int kSmemBytes = 12;
-  __device__ static PSetInt level(const PlanDesc &P, int l, long long node) {
-    const long long b = node * P.N;
-    return PSetInt{P.ps[l] + b, P.plw[l] + b, nullptr};
+template <class M> struct SNode;
+template <> struct SNode<NavModel> {
+  float4 *A, *B;
+  static constexpr int kPairBytes = 32;
+  __device__ static SNode at(float *base, int npairs) {
+    float4 *p = reinterpret_cast<float4 *>(base);
+    return SNode{p, p + npairs};
   }
-  __device__ static PSetInt smem(float *base, int N) {
-    return PSetInt{reinterpret_cast<int *>(base), base + N, base + 2 * N};
+  __device__ __forceinline__ NavModel::S get(int i) const {
+    const float *a = reinterpret_cast<const float *>(A + (i >> 1));
+    return NavModel::S{a[i & 1], a[2 + (i & 1)]};
+  }
+  __device__ __forceinline__ void put(int i, const NavModel::S &s) const {
+    float *a = reinterpret_cast<float *>(A + (i >> 1));
+    a[i & 1] = s.x;
+    a[2 + (i & 1)] = s.y;
+  }
+  __device__ __forceinline__ void get_pair(int p, NavModel::S &s0, NavModel::S &s1) const {
+    const float4 a = A[p];
+    s0 = NavModel::S{a.x, a.z};
+    s1 = NavModel::S{a.y, a.w};
+  }
+  __device__ __forceinline__ float lw(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[i & 1]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
+  __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
+  __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+};
+template <class M> struct SNodeInt {
+  int2 *A;
+  float4 *B;
+  static constexpr int kPairBytes = 24;
+  __device__ static SNodeInt at(float *base, int npairs) {
+    float4 *b = reinterpret_cast<float4 *>(base);
+    return SNodeInt{reinterpret_cast<int2 *>(b + npairs), b};
+  }
+  __device__ __forceinline__ typename M::S get(int i) const {
+    return typename M::S{reinterpret_cast<const int *>(A + (i >> 1))[i & 1]};
+  }
+  __device__ __forceinline__ void put(int i, const typename M::S &v) const {
+    reinterpret_cast<int *>(A + (i >> 1))[i & 1] = v.s;
+  }
+  __device__ __forceinline__ void get_pair(int p, typename M::S &s0, typename M::S &s1) const {
+    const int2 a = A[p];
+    s0 = typename M::S{a.x};
+    s1 = typename M::S{a.y};
+  }
+  __device__ __forceinline__ float lw(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[i & 1]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
+  __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
+  __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+};
+template <> struct SNode<GridModel> : SNodeInt<GridModel> {
+  __device__ static SNode at(float *base, int np) {
+    SNode r; static_cast<SNodeInt<GridModel> &>(r) = SNodeInt<GridModel>::at(base, np); return r;
   }
 };
-template <> struct PSet<GridModel> : PSetInt<GridModel> {
-  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
-    PSet r; static_cast<PSetInt<GridModel> &>(r) = PSetInt<GridModel>::level(P, l, node); return r;
-  }
-  __device__ static PSet smem(float *base, int N) {
-    PSet r; static_cast<PSetInt<GridModel> &>(r) = PSetInt<GridModel>::smem(base, N); return r;
+template <> struct SNode<ToyModel> : SNodeInt<ToyModel> {
+  __device__ static SNode at(float *base, int np) {
+    SNode r; static_cast<SNodeInt<ToyModel> &>(r) = SNodeInt<ToyModel>::at(base, np); return r;
   }
 };
-template <> struct PSet<ToyModel> : PSetInt<ToyModel> {
-  __device__ static PSet level(const PlanDesc &P, int l, long long node) {
-    PSet r; static_cast<PSetInt<ToyModel> &>(r) = PSetInt<ToyModel>::level(P, l, node); return r;
-  }
-  __device__ static PSet smem(float *base, int N) {
-    PSet r; static_cast<PSetInt<ToyModel> &>(r) = PSetInt<ToyModel>::smem(base, N); return r;
-  }
+
+// Scratch for the two per-particle values a child build keeps between its passes.
+struct ScratchArrays {           // K2: dynamic shared memory, N floats each
+  float *L, *E;
+  __device__ __forceinline__ float getL(int i) const { return L[i]; }
+  __device__ __forceinline__ void setL(int i, float v) const { L[i] = v; }
+  __device__ __forceinline__ float getE(int i) const { return E[i]; }
+  __device__ __forceinline__ void setE(int i, float v) const { E[i] = v; }
+};
+template <class M> struct ScratchInNode {   // K3: the destination node's lw / w slots
+  SNode<M> n;
+  __device__ __forceinline__ float getL(int i) const { return n.lw(i); }
+  __device__ __forceinline__ void setL(int i, float v) const { n.set_lw(i, v); }
+  __device__ __forceinline__ float getE(int i) const { return n.w(i); }
+  __device__ __forceinline__ void setE(int i, float v) const { n.set_w(i, v); }
 };
 
 template <class M> __device__ __forceinline__ float2 state_xy(const typename M::S &s);
@@ -92,18 +163,12 @@ template <> __device__ __forceinline__ ToyModel::S load_root<ToyModel>(const Pla
   return ToyModel::S{P.root_s[i]};
 }
 
-// Transition words of particle i of branch (l, node, a, k): pair i/2, half i&1.
+// Transition Philox words of particle pair p of branch (l, node, a, k).
 template <class M>
-__device__ __forceinline__ float step_particle(const PlanDesc &P, typename M::S &s, int i, int l,
-                                               int a, int k, unsigned long long node,
-                                               const DevModel &dm) {
-  uint32_t wa = 0, wb = 0;
-  if (M::kStochastic) {
-    const uint4 w = draw(P.key0, P.key1, (uint32_t)(i >> 1), kPurposeTransition, l, a, k, node);
-    wa = (i & 1) ? w.z : w.x;
-    wb = (i & 1) ? w.w : w.y;
-  }
-  return M::step(s, a, wa, wb, dm);
+__device__ __forceinline__ uint4 pair_words(const PlanDesc &P, int p, int l, int a, int k,
+                                            unsigned long long node) {
+  if (!M::kStochastic) return make_uint4(0u, 0u, 0u, 0u);
+  return draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, l, a, k, node);
 }
 
 // The branch observation of (l, node, a, k): enumerated, or drawn from the representative
@@ -116,40 +181,61 @@ __device__ __forceinline__ typename M::O branch_obs(const PlanDesc &P, const Src
   const uint4 w = draw(P.key0, P.key1, 0u, kPurposeObservation, l, a, k, node);
   j = (int)(((unsigned long long)w.z * (unsigned long long)P.N) >> 32);
   typename M::S sj = src.get(j);
-  step_particle<M>(P, sj, j, l, a, k, node, dm);
+  const uint4 t = pair_words<M>(P, j >> 1, l, a, k, node);
+  M::step(sj, a, (j & 1) ? t.z : t.x, (j & 1) ? t.w : t.y, dm);
   return M::draw_obs(sj, a, w.x, w.y, dm);
 }
 
-// log pibar(a | node) for a < A into lpi (computed by every calling thread).
+// log pibar(a | node) for a < A (computed by every calling thread).
 __device__ __forceinline__ float log_pibar(const PlanDesc &P, float2 mu, int a) {
   if (P.pi_mode != kPiNavDist) return P.log_pi[a];
   float z[4], zm = -CUDART_INF_F;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const float dx = (b == 0) ? 1.f : (b == 1 ? -1.f : 0.f);
-    const float dy = (b == 2) ? 1.f : (b == 3 ? -1.f : 0.f);
-    const float cx = fminf(fmaxf(mu.x + dx, 0.f), 10.f), cy = fminf(fmaxf(mu.y + dy, 0.f), 10.f);
+    const float cx = fminf(fmaxf(mu.x + NavModel::dx_of(b), 0.f), 10.f);
+    const float cy = fminf(fmaxf(mu.y + NavModel::dy_of(b), 0.f), 10.f);
     z[b] = -sqrtf(cx * cx + cy * cy) / P.pi_temp;
     zm = fmaxf(zm, z[b]);
   }
   float s = 0.f;
 #pragma unroll
   for (int b = 0; b < 4; ++b) s += __expf(z[b] - zm);
-  return z[a & 3] - zm - logf(s);
+  float za = z[0];
+#pragma unroll
+  for (int b = 1; b < 4; ++b) za = (a == b) ? z[b] : za;
+  return za - zm - __logf(s);
+}
+
+// Several block-wide reductions at once (sum or max per slot); `red` holds >= 32*K floats.
+template <int K>
+__device__ __forceinline__ void block_reduce(float (&v)[K], const bool (&is_max)[K], float *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = is_max[k] ? warp_max(v[k]) : warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float t = (lane < nw) ? red[k * 32 + lane] : (is_max[k] ? -CUDART_INF_F : 0.f);
+    v[k] = is_max[k] ? warp_max(t) : warp_sum(t);
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------------
-// Child construction (Alg. 2: G, observation, weighting) by a whole CTA.
-//   src: parent's particles (level l), dst: child's particle buffer (global or shared);
-//   scratchL / scratchE: N floats each (may alias dst.lw / dst.w for shared buffers).
-// Writes the branch stats of the child and returns them in the out parameters.
+// Child construction (Alg. 2: G, observation, weighting) by a whole CTA, one Philox pair
+// per thread iteration.  src: parent particles (level l); dst: the child's particles;
+// sc: two per-particle scratch values between the passes.
 // ---------------------------------------------------------------------------------------
-template <class M>
+template <class M, class Src, class Dst, class Scr>
 __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
-                            unsigned long long child, const PSet<M> &src, const PSet<M> &dst,
-                            float *scratchL, float *scratchE, float *red, bool dst_has_w,
-                            float2 *mu_out) {
-  const int N = P.N, AW = P.AW, W = P.W;
+                            unsigned long long child, const Src &src, const Dst &dst,
+                            const Scr &sc, float *red, bool dst_has_w, float2 *mu_out) {
+  const int N = P.N, AW = P.AW, W = P.W, npairs = (N + 1) >> 1;
   const unsigned long long parent = child / (unsigned long long)AW;
   const int slot = (int)(child - parent * (unsigned long long)AW);
   const int a = slot / W, k = slot - (slot / W) * W;
@@ -159,28 +245,40 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   Kahan R;
   R.init();
   float m1 = -CUDART_INF_F, m0 = -CUDART_INF_F;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    typename M::S s = src.get(i);
-    const float lw = src.lw[i];
-    const float r = step_particle<M>(P, s, i, l, a, k, parent, dm);
-    const float ell = M::loglik(s, a, o, dm);
-    const float L = lw + ell;
-    if (lw > -CUDART_INF_F) R.add(__expf(lw) * r);
-    dst.put(i, s);
-    scratchL[i] = L;
-    scratchE[i] = ell;
-    m1 = fmaxf(m1, L);
-    m0 = fmaxf(m0, ell);
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    const uint4 w = pair_words<M>(P, p, l, a, k, parent);
+    float rp = 0.f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int i = 2 * p + e;
+      if (i < N) {
+        typename M::S s = src.get(i);
+        const float lw = src.lw(i);
+        const float r = M::step(s, a, e ? w.z : w.x, e ? w.w : w.y, dm);
+        const float ell = M::loglik(s, a, o, dm);
+        const float L = lw + ell;
+        rp += (lw > -CUDART_INF_F) ? __expf(lw) * r : 0.f;
+        dst.put(i, s);
+        sc.setL(i, L);
+        sc.setE(i, ell);
+        m1 = fmaxf(m1, L);
+        m0 = fmaxf(m0, ell);
+      }
+    }
+    R.add(rp);
   }
-  m1 = block_max(m1, red);
-  m0 = block_max(m0, red);
-  const float rbar = block_sum(R.value(), red);
-
+  {
+    float v[2] = {m1, m0};
+    const bool mx[2] = {true, true};
+    block_reduce<2>(v, mx, red);
+    m1 = v[0];
+    m0 = v[1];
+  }
   Kahan S1, S0, MX, MY;
   S1.init(); S0.init(); MX.init(); MY.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float e1 = (m1 > -CUDART_INF_F) ? __expf(scratchL[i] - m1) : 0.f;
-    const float e0 = (m0 > -CUDART_INF_F) ? __expf(scratchE[i] - m0) : 0.f;
+    const float e1 = (m1 > -CUDART_INF_F) ? __expf(sc.getL(i) - m1) : 0.f;
+    const float e0 = (m0 > -CUDART_INF_F) ? __expf(sc.getE(i) - m0) : 0.f;
     S1.add(e1);
     S0.add(e0);
     if (P.pi_mode == kPiNavDist) {
@@ -189,22 +287,21 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       MY.add(e1 * xy.y);
     }
   }
-  const float s1 = block_sum(S1.value(), red);
-  const float s0 = block_sum(S0.value(), red);
-  float mx = 0.f, my = 0.f;
-  if (P.pi_mode == kPiNavDist) {
-    mx = block_sum(MX.value(), red);
-    my = block_sum(MY.value(), red);
+  float v[5] = {R.value(), S1.value(), S0.value(), MX.value(), MY.value()};
+  {
+    const bool mx[5] = {false, false, false, false, false};
+    block_reduce<5>(v, mx, red);
   }
-  const float lse1 = (s1 > 0.f) ? m1 + logf(s1) : -CUDART_INF_F;
+  const float rbar = v[0], s1 = v[1], s0 = v[2], mx = v[3], my = v[4];
+  const float lse1 = (s1 > 0.f) ? m1 + __logf(s1) : -CUDART_INF_F;
   float lom;
   if (P.branch_mode == kEnumerate) lom = lse1;
-  else lom = (lse1 > -CUDART_INF_F) ? logf((float)N) + lse1 - (m0 + logf(s0)) : -CUDART_INF_F;
+  else lom = (lse1 > -CUDART_INF_F) ? __logf((float)N) + lse1 - (m0 + __logf(s0)) : -CUDART_INF_F;
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float nl = (lse1 > -CUDART_INF_F) ? scratchL[i] - lse1 : -CUDART_INF_F;
-    dst.lw[i] = nl;
-    if (dst_has_w) dst.w[i] = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
+    const float nl = (lse1 > -CUDART_INF_F) ? sc.getL(i) - lse1 : -CUDART_INF_F;
+    dst.set_lw(i, nl);
+    if (dst_has_w) sc.setE(i, (nl > -CUDART_INF_F) ? __expf(nl) : 0.f);
   }
   const int cl = l + 1;
   if (threadIdx.x == 0) {
@@ -271,7 +368,7 @@ __device__ __forceinline__ void node_backup_warp(const PlanDesc &P, const float 
 template <class M>
 __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red) {
   const int N = P.N;
-  PSet<M> dst = PSet<M>::level(P, 0, 0);
+  const GNode<M> dst = GNode<M>::at(P, 0, 0);
   // log weights of the caller's belief; terminal particles and non-positive weights -> -inf
   float m = -CUDART_INF_F;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -285,7 +382,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
     }
     if (!(lw > -CUDART_INF_F) || M::terminal(s)) lw = -CUDART_INF_F;
     dst.put(i, s);
-    dst.lw[i] = lw;
+    dst.set_lw(i, lw);
     m = fmaxf(m, lw);
   }
   m = block_max(m, red);
@@ -296,16 +393,16 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
   Kahan T;
   T.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float lw = dst.lw[i];
+    const float lw = dst.lw(i);
     if (lw > -CUDART_INF_F) T.add(__expf(lw - m));
   }
   const float lse = m + logf(block_sum(T.value(), red));
   Kahan MX, MY, H;
   MX.init(); MY.init(); H.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float lw = dst.lw[i];
+    const float lw = dst.lw(i);
     const float nl = (lw > -CUDART_INF_F) ? lw - lse : -CUDART_INF_F;
-    dst.lw[i] = nl;
+    dst.set_lw(i, nl);
     const float wn = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
     const typename M::S s = dst.get(i);
     const float2 xy = state_xy<M>(s);
@@ -355,15 +452,16 @@ __device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, 
                             float *red) {
   const DevModel &dm = *P.model;
   const unsigned long long parent = child / (unsigned long long)P.AW;
-  PSet<M> src = PSet<M>::level(P, l, (long long)parent);
-  PSet<M> dst = PSet<M>::level(P, l + 1, (long long)child);
-  build_child<M>(P, dm, l, child, src, dst, smem, smem + P.N, red, false, nullptr);
+  const GNode<M> src = GNode<M>::at(P, l, (long long)parent);
+  const GNode<M> dst = GNode<M>::at(P, l + 1, (long long)child);
+  const ScratchArrays sc{smem, smem + P.N};
+  build_child<M>(P, dm, l, child, src, dst, sc, red, false, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTable st,
                                                 long long total) {
   extern __shared__ float smem[];
-  __shared__ float red[32];
+  __shared__ float red[32 * 5];
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
@@ -380,48 +478,133 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 // ---------------------------------------------------------------------------------------
 // K3: leaf expansion of one level-(D-1) node, fused with its backup.
 // ---------------------------------------------------------------------------------------
+// Compile-time tuning of the leaf loop (results do not depend on them):
+//   VOPP_LEAF_CHUNK      Philox pairs per lane between two rescales of the running sums
+//   VOPP_ROUND_KEYS      1: Philox round keys held in registers for the whole branch
+//   VOPP_LEAF_MINBLOCKS  minimum resident leaf CTAs per SM requested from the compiler
+#ifndef VOPP_LEAF_CHUNK
+#define VOPP_LEAF_CHUNK 4
+#endif
+#ifndef VOPP_ROUND_KEYS
+#define VOPP_ROUND_KEYS 0
+#endif
+#ifndef VOPP_LEAF_MINBLOCKS
+#define VOPP_LEAF_MINBLOCKS 3
+#endif
+constexpr int kLeafChunk = VOPP_LEAF_CHUNK;
+
+// Running max-shifted sums in base 2: S = sum 2^(L - m) and H = sum 2^(L - m) h, compensated.
+struct ShiftedSum {
+  float m;
+  Kahan S, H;
+  __device__ __forceinline__ void init() { m = -CUDART_INF_F; S.init(); H.init(); }
+  // Move the shift to max(m, cm); returns the new shift.
+  __device__ __forceinline__ float shift_to(float cm) {
+    const float nm = fmaxf(m, cm);
+    if (nm > m) {
+      const float f = (m > -CUDART_INF_F) ? ex2(m - nm) : 0.f;
+      S.scale(f);
+      H.scale(f);
+      m = nm;
+    }
+    return m;
+  }
+};
+
+// One leaf branch (slot a*W + k of a level-(D-1) node) by one warp.  The node's particles
+// are in shared memory with base-2 log weights; every lane steps Philox pairs p = lane,
+// lane + 32, ... and keeps running sums over L = lw + log2 Z (child weights, heuristic) and
+// over log2 Z (the proposal normaliser of omega), rescaled once per chunk of pairs.
 template <class M>
-__device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const PSet<M> &nb,
+__device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNode<M> &nb,
                                 int l, unsigned long long node, int slot, float *sm_rb,
                                 float *sm_lo, float *sm_v) {
   const int lane = threadIdx.x & 31, N = P.N, W = P.W;
   const int a = slot / W, k = slot - (slot / W) * W;
+  const float log2g = P.log2_gamma, h_a0 = P.h_a0, h_b0 = P.h_b0;
+  const bool hz = P.h_zero != 0;
   int j;
   const typename M::O o = branch_obs<M>(P, nb, l, a, k, node, dm, j);
 
-  OnlineLSE L1, L0;
-  L1.init(); L0.init();
+#if VOPP_ROUND_KEYS
+  PhiloxKeys K;
+  K.init(P.key0, P.key1);
+#else
+  const uint32_t key0 = P.key0, key1 = P.key1;
+#endif
+  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  const uint32_t c2 = (uint32_t)node, c3 = (uint32_t)(node >> 32);
+  ShiftedSum A1, A0;
+  A1.init();
+  A0.init();
   Kahan R;
   R.init();
   const int npairs = (N + 1) >> 1;
-  for (int p = lane; p < npairs; p += 32) {
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    if (M::kStochastic) w = draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, l, a, k, node);
+  for (int base = lane; base < npairs; base += 32 * kLeafChunk) {
+    float L[2 * kLeafChunk], E[2 * kLeafChunk], Hh[2 * kLeafChunk];
+    float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rsum = 0.f;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int i = 2 * p + e;
-      if (i < N) {
-        typename M::S s = nb.get(i);
-        const float lw = nb.lw[i], wi = nb.w[i];
-        const float r = M::step(s, a, e ? w.z : w.x, e ? w.w : w.y, dm);
-        const float ell = M::loglik(s, a, o, dm);
-        const float h = M::heuristic(s, P);
-        R.add(wi * r);
-        L1.add(lw + ell, h);
-        L0.add(ell);
+    for (int c = 0; c < kLeafChunk; ++c) {
+      const int p = base + 32 * c;
+      L[2 * c] = L[2 * c + 1] = E[2 * c] = E[2 * c + 1] = -CUDART_INF_F;
+      Hh[2 * c] = Hh[2 * c + 1] = 0.f;
+      if (p < npairs) {
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (M::kStochastic) {   // purpose 0 (transition): counter word 0 is the pair index
+#if VOPP_ROUND_KEYS
+          w = philox_rk(make_uint4((uint32_t)p, c1, c2, c3), K);
+#else
+          w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+#endif
+        }
+        typename M::S s0, s1;
+        nb.get_pair(p, s0, s1);
+        const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+        const float r0 = M::step(s0, a, w.x, w.y, dm);
+        const float r1 = M::step(s1, a, w.z, w.w, dm);
+        const float e0 = M::loglik2(s0, a, o, dm), e1 = M::loglik2(s1, a, o, dm);
+        const bool v1 = 2 * p + 1 < N;
+        L[2 * c] = b.x + e0;
+        E[2 * c] = e0;
+        Hh[2 * c] = M::heuristic(s0, log2g, h_a0, h_b0, hz);
+        L[2 * c + 1] = b.y + e1;           // the odd-N pad slot has lw2 = -inf
+        E[2 * c + 1] = v1 ? e1 : -CUDART_INF_F;
+        Hh[2 * c + 1] = M::heuristic(s1, log2g, h_a0, h_b0, hz);
+        rsum = fmaf(b.z, r0, rsum);
+        rsum = fmaf(b.w, r1, rsum);        // pad slot: w = 0
+        cm1 = fmaxf(cm1, fmaxf(L[2 * c], L[2 * c + 1]));
+        cm0 = fmaxf(cm0, fmaxf(E[2 * c], E[2 * c + 1]));
       }
     }
+    const float m1 = A1.shift_to(cm1), m0 = A0.shift_to(cm0);
+    float s1 = 0.f, h1 = 0.f, s0 = 0.f;
+    if (m1 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < 2 * kLeafChunk; ++t) {
+        const float x1 = ex2(L[t] - m1);    // L = -inf gives 0
+        s1 += x1;
+        h1 = fmaf(x1, Hh[t], h1);
+      }
+    }
+    if (m0 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < 2 * kLeafChunk; ++t) s0 += ex2(E[t] - m0);
+    }
+    A1.S.add(s1);
+    A1.H.add(h1);
+    A0.S.add(s0);
+    R.add(rsum);
   }
-  float m1 = L1.m, s1 = L1.s.value(), h1 = L1.h.value();
-  float m0 = L0.m, s0 = L0.s.value(), h0 = 0.f;
-  warp_lse(m1, s1, h1);
-  warp_lse(m0, s0, h0);
+  float m1 = A1.m, s1 = A1.S.value(), h1 = A1.H.value();
+  float m0 = A0.m, s0 = A0.S.value(), h0 = 0.f;
+  warp_lse2(m1, s1, h1);
+  warp_lse2(m0, s0, h0);
   const float rbar = warp_sum(R.value());
   if (lane == 0) {
-    const float lse1 = (s1 > 0.f) ? m1 + logf(s1) : -CUDART_INF_F;
+    const float lse1 = (s1 > 0.f) ? kLn2 * (m1 + lg2(s1)) : -CUDART_INF_F;
     float lom;
     if (P.branch_mode == kEnumerate) lom = lse1;
-    else lom = (lse1 > -CUDART_INF_F) ? logf((float)N) + lse1 - (m0 + logf(s0)) : -CUDART_INF_F;
+    else lom = (lse1 > -CUDART_INF_F) ? __logf((float)N) + lse1 - kLn2 * (m0 + lg2(s0)) : -CUDART_INF_F;
     const float v = (s1 > 0.f) ? h1 / s1 : 0.f;
     sm_rb[slot] = rbar;
     sm_lo[slot] = lom;
@@ -444,29 +627,36 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const PSe
 template <class M>
 __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *smem, float *red) {
   const DevModel &dm = *P.model;
-  const int N = P.N, AW = P.AW, l = P.D - 1;
-  PSet<M> nb = PSet<M>::smem(smem, N);
-  float *sm_rb = smem + (M::kStochastic ? 4 : 3) * N;
+  const int N = P.N, AW = P.AW, l = P.D - 1, npairs = (N + 1) >> 1;
+  const SNode<M> nb = SNode<M>::at(smem, npairs);
+  float *sm_rb = smem + (SNode<M>::kPairBytes / 4) * npairs;
   float *sm_lo = sm_rb + AW, *sm_v = sm_lo + AW;
   __shared__ float2 s_mu;
 
   if (P.leaf_gen) {
     const unsigned long long parent = node / (unsigned long long)AW;
-    PSet<M> src = PSet<M>::level(P, l - 1, (long long)parent);
+    const GNode<M> src = GNode<M>::at(P, l - 1, (long long)parent);
     float2 mu;
-    build_child<M>(P, dm, l - 1, node, src, nb, nb.lw, nb.w, red, true, &mu);
+    build_child<M>(P, dm, l - 1, node, src, nb, ScratchInNode<M>{nb}, red, true, &mu);
     if (threadIdx.x == 0) s_mu = mu;
   } else {
-    PSet<M> src = PSet<M>::level(P, l, (long long)node);
+    const GNode<M> src = GNode<M>::at(P, l, (long long)node);
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       nb.put(i, src.get(i));
-      const float lw = src.lw[i];
-      nb.lw[i] = lw;
-      nb.w[i] = (lw > -CUDART_INF_F) ? __expf(lw) : 0.f;
+      const float lw = src.lw(i);
+      nb.set_lw(i, lw);
+      nb.set_w(i, (lw > -CUDART_INF_F) ? __expf(lw) : 0.f);
     }
     if (threadIdx.x == 0)
       s_mu = (P.pi_mode == kPiNavDist) ? make_float2(P.mu[l][2 * node], P.mu[l][2 * node + 1])
                                        : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) nb.set_lw(i, kLog2e * nb.lw(i));  // base 2
+  if ((N & 1) && threadIdx.x == 0) {   // odd N: the pad slot is a zero-weight copy of particle 0
+    nb.put(N, nb.get(0));
+    nb.set_lw(N, -CUDART_INF_F);
+    nb.set_w(N, 0.f);
   }
   __syncthreads();
 
@@ -487,10 +677,10 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_leaf(const PlanDesc *plans, StageTable st,
+__global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDesc *plans, StageTable st,
                                               long long total) {
-  extern __shared__ float smem[];
-  __shared__ float red[32];
+  extern __shared__ __align__(16) float smem[];
+  __shared__ float red[32 * 5];
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
@@ -641,13 +831,13 @@ __global__ void __launch_bounds__(1024) k_backup_tail(const PlanDesc *plans, Sta
 template <class M>
 __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red, double *dred) {
   const int N = B.N;
-  PSet<M> cur, nxt;
+  GNode<M> cur, nxt;
   if constexpr (M::kStochastic) {
-    cur = PSet<M>{B.x, B.y, B.lw, nullptr};
-    nxt = PSet<M>{B.tx, B.ty, B.tlw, nullptr};
+    cur = GNode<M>{B.x, B.y, B.lw};
+    nxt = GNode<M>{B.tx, B.ty, B.tlw};
   } else {
-    cur.s = B.s; cur.lw = B.lw; cur.w = nullptr;
-    nxt.s = B.ts; nxt.lw = B.tlw; nxt.w = nullptr;
+    cur.s = B.s; cur.lwp = B.lw;
+    nxt.s = B.ts; nxt.lwp = B.tlw;
   }
   typename M::O o;
   if constexpr (M::kStochastic) o = typename M::O{B.obs_f[0], B.obs_f[1]};
@@ -663,9 +853,9 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
       wb = (i & 1) ? w.w : w.y;
     }
     M::step(s, B.action, wa, wb, dm);
-    const float L = cur.lw[i] + M::loglik(s, B.action, o, dm);
+    const float L = cur.lw(i) + M::loglik(s, B.action, o, dm);
     nxt.put(i, s);
-    nxt.lw[i] = L;
+    nxt.set_lw(i, L);
     m = fmaxf(m, L);
   }
   m = block_max(m, red);
@@ -675,13 +865,13 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
   }
   Kahan S;
   S.init();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) S.add(__expf(nxt.lw[i] - m));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) S.add(__expf(nxt.lw(i) - m));
   const float lse = m + logf(block_sum(S.value(), red));
   Kahan Q2;
   Q2.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float nl = nxt.lw[i] - lse;
-    nxt.lw[i] = nl;
+    const float nl = nxt.lw(i) - lse;
+    nxt.set_lw(i, nl);
     const float w = __expf(nl);
     Q2.add(w * w);
   }
@@ -695,7 +885,7 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
     const int chunk = (N + T - 1) / T;
     const int b = tid * chunk, e = min(N, b + chunk);
     double acc = 0.0;
-    for (int i = b; i < e; ++i) acc += (double)__expf(nxt.lw[i]);
+    for (int i = b; i < e; ++i) acc += (double)__expf(nxt.lw(i));
     dred[tid] = acc;
     __syncthreads();
     if (tid == 0) {
@@ -705,7 +895,7 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
     }
     __syncthreads();
     double run = dred[tid];
-    for (int i = b; i < e; ++i) { run += (double)__expf(nxt.lw[i]); B.cdf[i] = run; }
+    for (int i = b; i < e; ++i) { run += (double)__expf(nxt.lw(i)); B.cdf[i] = run; }
     __syncthreads();
     const double total = B.cdf[N - 1];
     const uint4 w = draw(B.key0, B.key1, 0u, kPurposeResample, 0, 0, 0, B.t);
@@ -720,12 +910,12 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
       }
       B.anc[i] = lo;
       cur.put(i, nxt.get(lo));
-      cur.lw[i] = nlw;
+      cur.set_lw(i, nlw);
     }
   } else {
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       cur.put(i, nxt.get(i));
-      cur.lw[i] = nxt.lw[i];
+      cur.set_lw(i, nxt.lw(i));
       B.anc[i] = i;
     }
   }
@@ -751,8 +941,8 @@ __global__ void __launch_bounds__(1024) k_belief(BeliefArgs B) {
 // Host-side launchers.
 // ---------------------------------------------------------------------------------------
 size_t leaf_smem_bytes(int kind, int N, int AW) {
-  const int per = (kind == kNav) ? 16 : 12;
-  return (size_t)per * N + 3 * sizeof(float) * (size_t)AW + 64;
+  const size_t pair = (kind == kNav) ? 32 : 24;
+  return pair * (size_t)((N + 1) / 2) + 3 * sizeof(float) * (size_t)AW + 64;
 }
 size_t expand_smem_bytes(int N) { return 8 * (size_t)N + 64; }
 

@@ -18,7 +18,8 @@ def close(g, o, rtol=RTOL):
     g = np.asarray(g, dtype=np.float64)
     o = np.asarray(o, dtype=np.float64)
     both_inf = np.isneginf(g) & np.isneginf(o)
-    err = np.abs(g - o)
+    with np.errstate(invalid="ignore"):
+        err = np.abs(g - o)
     tol = rtol * np.maximum(np.abs(o), 1.0)
     ok = both_inf | (err <= tol)
     return ok
