@@ -240,6 +240,32 @@ VOPP_API int vopp_agent_get_particles(vopp_agent *agent, void *states, float *lo
 VOPP_API int vopp_agent_num_particles(const vopp_agent *agent);
 VOPP_API void vopp_agent_destroy(vopp_agent *agent);
 
+/* Belief update without any memory allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory when they update a belief
+ * (fixed memory plans of real-time loops, HBM held entirely by another allocator, or code
+ * that cannot afford an allocation's implicit device synchronisation).  It runs the same
+ * SIR kernel as vopp_belief_update, in place, on caller-owned device arrays:
+ *   states       device, in/out: NAV2D float[2n] (x then y), GRID/TOY2 int32[n]
+ *   log_weights  device, in/out: normalised log weights float[n]
+ *   obs          host: NAV2D float[2], GRID/TOY2 int32[1]
+ *   seed, t      the Philox key and time step (counter) of this update
+ *   cuda_stream  stream to run on (cudaStream_t as an integer, 0 = legacy default)
+ *   ancestors    device int32[n] receiving the ancestor indices, or NULL
+ *   ess_out, resampled_out   host, may be NULL
+ * Its working memory is one static device array of about 1.5 MB compiled into the library
+ * (every GPU that loads the library holds it until the process exits), so n is limited to
+ * 65536; larger n returns VOPP_E_INVALID.  The call issues no cudaMalloc / cudaFree and no
+ * allocating library call.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the one array, which keeps the previous call's contents, so
+ * calls that overlap on the GPU (different streams or threads, or concurrent launches)
+ * race: serialise them.  Blocks until the update is done.  VOPP_E_DEGENERATE leaves the
+ * belief unchanged. */
+VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void *states, float *log_weights,
+                                        int32_t n, int32_t action, const void *obs, uint64_t seed,
+                                        uint64_t t, uintptr_t cuda_stream, int32_t *ancestors,
+                                        double *ess_out, int32_t *resampled_out);
+
 /* ---- batches: many uneven plans per launch sequence ----------------------------------- */
 /* Run n independent plans with one launch per stage covering every plan (plans of
  * different models, N, D and W mix freely).  Results equal those of n separate vopp_plan

@@ -627,6 +627,14 @@ void fill_grid_tables(DevModel &d, const vopp_model_desc &m) {
 
 }  // namespace
 
+// Accessors used by entry points defined in other translation units.
+namespace vopp {
+const DevModel *model_device_tables(const vopp_model *m) { return m->dev; }
+int model_kind(const vopp_model *m) { return m->desc.kind; }
+int model_device(const vopp_model *m) { return m->ctx->device; }
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace vopp
+
 // ---------------------------------------------------------------------------------------
 // C ABI.
 // ---------------------------------------------------------------------------------------

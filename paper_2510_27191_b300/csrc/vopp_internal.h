@@ -46,3 +46,12 @@ cudaError_t launch_backup_tail(const PlanDesc *d, const StageTable &st, cudaStre
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
 
 }  // namespace vopp
+
+struct vopp_model;
+namespace vopp {
+const DevModel *model_device_tables(const vopp_model *m);
+int model_kind(const vopp_model *m);
+int model_device(const vopp_model *m);
+int set_error(int code, const char *msg);   // records the thread-local message, returns code
+
+}  // namespace vopp

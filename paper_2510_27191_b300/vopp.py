@@ -103,6 +103,8 @@ def _load():
         "vopp_agent_get_particles": ([vp, vp, vp, vp, u32], ctypes.c_int),
         "vopp_agent_num_particles": ([vp], ctypes.c_int),
         "vopp_agent_destroy": ([vp], None),
+        "vopp_belief_update_noalloc": ([vp, vp, vp, i32, i32, vp, u64, u64, ctypes.c_size_t, vp,
+                                        dp, ctypes.POINTER(i32)], ctypes.c_int),
         "vopp_plan_batch": ([vp, i32, ctypes.POINTER(vopp_plan_request),
                              ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
         "vopp_last_error": ([], ctypes.c_char_p),
@@ -297,6 +299,24 @@ def vopp_agent_get_particles(agent: int, kind: int):
     anc = np.empty(n, dtype=np.int32)
     check(lib.vopp_agent_get_particles(agent, st.ctypes.data, lw.ctypes.data, anc.ctypes.data, 0))
     return st, lw, anc
+
+
+def vopp_belief_update_noalloc(model: int, states, log_weights, action: int, obs, seed: int,
+                               t: int, kind: int, cuda_stream: int = 0, ancestors=None):
+    """In-place SIR update of caller-owned CUDA tensors (states, log_weights) using the
+    library's static scratch; returns (ess, resampled)."""
+    n = log_weights.numel()
+    if kind == VOPP_NAV2D:
+        o = (ctypes.c_float * 2)(float(obs[0]), float(obs[1]))
+    else:
+        o = (ctypes.c_int32 * 1)(int(np.atleast_1d(obs)[0]))
+    ess = ctypes.c_double()
+    res = ctypes.c_int32()
+    check(lib.vopp_belief_update_noalloc(model, states.data_ptr(), log_weights.data_ptr(), n,
+                                         action, o, seed & 0xFFFFFFFFFFFFFFFF, t, cuda_stream,
+                                         None if ancestors is None else ancestors.data_ptr(),
+                                         ctypes.byref(ess), ctypes.byref(res)))
+    return ess.value, bool(res.value)
 
 
 def vopp_agent_destroy(agent: int) -> None:
