@@ -83,8 +83,9 @@ class PlanArgs(ctypes.Structure):
 
 
 class BuResult(ctypes.Structure):
-    _fields_ = [("ess", ctypes.c_double), ("resampled", ctypes.c_int),
-                ("near_ties", ctypes.c_longlong)]
+    _fields_ = [("ess", ctypes.c_double), ("resampled", ctypes.c_int), ("ess_tie", ctypes.c_int),
+                ("near_ties", ctypes.c_longlong), ("ties", _up), ("prop_x", _dp), ("prop_y", _dp),
+                ("prop_s", _ip)]
 
 
 def lib():
@@ -253,12 +254,18 @@ def belief_update(model: Model, lw, action: int, obs, seed: int, t: int, x=None,
     o = np.zeros(2)
     o[:len(np.atleast_1d(obs))] = np.atleast_1d(obs)
     anc = np.zeros(N, dtype=np.int32)
+    ties = np.zeros(N, dtype=np.uint8)
+    px = np.zeros(N) if x is not None else None
+    py = np.zeros(N) if y is not None else None
+    ps = np.zeros(N, dtype=np.int32) if s is not None else None
     r = BuResult()
+    r.ties, r.prop_x, r.prop_y, r.prop_s = _ptr(ties, _up), _ptr(px, _dp), _ptr(py, _dp), _ptr(ps, _ip)
     rc = lib().orc_belief_update(ctypes.byref(model), N, _ptr(x, _dp), _ptr(y, _dp), _ptr(s, _ip),
                                  _ptr(lw, _dp), action, _ptr(o, _dp), seed, t, _ptr(anc, _ip),
                                  ctypes.byref(r))
     return rc, dict(x=x, y=y, s=s, lw=lw, ancestors=anc, ess=r.ess, resampled=bool(r.resampled),
-                    near_ties=r.near_ties)
+                    ess_tie=bool(r.ess_tie), near_ties=r.near_ties, ties=ties.astype(bool),
+                    prop_x=px, prop_y=py, prop_s=ps)
 
 
 def nav_heuristic(x: float, y: float, gamma: float) -> float:

@@ -600,7 +600,11 @@ int orc_plan(const orc_model *m, const double *root_x, const double *root_y,
 typedef struct {
   double ess;
   int resampled;
+  int ess_tie;               /* ESS within 1e-4 N of the resampling threshold N/2 */
   long long near_ties;
+  uint8_t *ties;             /* optional [N]: output position within 1e-5 of a CDF boundary */
+  double *prop_x, *prop_y;   /* optional [N]: propagated states before resampling */
+  int32_t *prop_s;
 } orc_bu_result;
 
 int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *s, double *lw,
@@ -629,7 +633,14 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
   for (int i = 0; i < N; ++i) { nl[i] -= ls; double w = exp(nl[i]); sw2 += w * w; }
   res->ess = 1.0 / sw2;
   res->resampled = res->ess < 0.5 * N;
-  if (fabs(res->ess - 0.5 * N) < 1e-4 * N) ++near;
+  res->ess_tie = fabs(res->ess - 0.5 * N) < 1e-4 * N;
+  if (res->ess_tie) ++near;
+  for (int i = 0; i < N; ++i) {
+    if (res->prop_x) res->prop_x[i] = sp[i].x;
+    if (res->prop_y) res->prop_y[i] = sp[i].y;
+    if (res->prop_s) res->prop_s[i] = sp[i].s;
+    if (res->ties) res->ties[i] = 0;
+  }
 
   if (res->resampled) {
     /* systematic resampling: positions (u0 + i)/N of the total mass, interval search */
@@ -643,7 +654,10 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
       double pos = (u0 + i) / N * cdf[N - 1];
       while (k < N - 1 && !(pos < cdf[k])) ++k;
       ancestors[i] = k;
-      if (fabs(pos - cdf[k]) < 1e-5 || (k > 0 && fabs(pos - cdf[k - 1]) < 1e-5)) ++near;
+      if (fabs(pos - cdf[k]) < 1e-5 || (k > 0 && fabs(pos - cdf[k - 1]) < 1e-5)) {
+        ++near;
+        if (res->ties) res->ties[i] = 1;
+      }
     }
     for (int i = 0; i < N; ++i) {
       pstate a = sp[ancestors[i]];

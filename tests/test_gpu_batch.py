@@ -1,0 +1,144 @@
+"""Batched plans (one launch per stage covering every plan) and the full-size grid plan
+(needs a GPU)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_27191_b300 import workloads as WL
+from tests.parity import Gpu, Spec, action_agrees, assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_specs(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = [WL.NAV2D, WL.GRID, WL.TOY2][i % 3]
+        N = int(rng.integers(1, 700))
+        W = int(rng.integers(1, 4)) + (1 if kind == WL.TOY2 else 0)
+        A = {WL.NAV2D: 4, WL.GRID: 13, WL.TOY2: 2}[kind]
+        D = int(rng.integers(0, 4))
+        while D > 1 and (A * W) ** D * N > 3e6:
+            D -= 1
+        bm = WL.BRANCH_ENUMERATE if (kind == WL.TOY2 and i % 2) else WL.BRANCH_SAMPLE
+        if bm == WL.BRANCH_ENUMERATE:
+            W = max(W, 2)
+        out.append(Spec(kind, N, D, W, eta=float(rng.uniform(0.2, 2.0)), gamma=0.95,
+                        seed=int(rng.integers(1, 2**40)), root_seed=i + 1, branch_mode=bm,
+                        weights="random" if i % 4 == 1 else "uniform"))
+    return out
+
+
+def test_batch_equals_individual_plans_and_oracle():
+    from paper_2510_27191_b300 import vopp as V
+    specs = _mixed_specs(24, 3)
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    models = {}
+    try:
+        reqs, singles = [], []
+        for s in specs:
+            key = (s.kind, s.branch_mode)
+            if key not in models:
+                models[key] = V.vopp_create_model(ctx, V.make_desc(
+                    s.kind, s.branch_mode, rock_x=WL.grid_layout(1)[0] if s.kind == WL.GRID else None,
+                    rock_y=WL.grid_layout(1)[1] if s.kind == WL.GRID else None))
+            s.rock_x, s.rock_y = (WL.grid_layout(1) if s.kind == WL.GRID else (None, None))
+            w = s.root.get("w")
+            reqs.append(dict(model=models[key], states=s.states(),
+                             weights=None if w is None else np.asarray(w, np.float32), n=s.N,
+                             depth=s.D, width=s.W, eta=s.eta, gamma=s.gamma, seed=s.seed, A=s.A))
+        outs, keep = V.vopp_plan_batch(ctx, reqs)
+        for r, s in zip(reqs, specs):
+            singles.append(V.vopp_plan(r["model"], r["states"], r["weights"], s.N, s.D, s.W, s.eta,
+                                       s.gamma, None, s.seed))
+        for i, (a, b, s) in enumerate(zip(outs, singles, specs)):
+            assert a["q"].tolist() == b["q"].tolist(), i
+            assert a["v_root"] == b["v_root"] and a["action"] == b["action"], i
+            orc = s.run_oracle(outputs=False)
+            assert orc["status"] == O.OK
+            assert_close(a["q"], orc["q_root"], f"plan {i} root Q")
+            assert_close([a["v_root"]], [orc["v_root"]], f"plan {i} root V")
+            assert action_agrees(a, orc, s)
+            assert a["particle_steps"] == orc["particle_steps"]
+        del keep
+    finally:
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
+
+
+def test_batch_tree_read_per_plan():
+    from paper_2510_27191_b300 import vopp as V
+    specs = [Spec(WL.NAV2D, 64, 2, 2, seed=1), Spec(WL.GRID, 100, 2, 2, seed=2)]
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    V.vopp_ctx_set_tree_detail(ctx, V.VOPP_TREE_FULL)
+    try:
+        ms = [V.vopp_create_model(ctx, V.make_desc(s.kind, rock_x=s.rock_x, rock_y=s.rock_y))
+              for s in specs]
+        reqs = [dict(model=m, states=s.states(), weights=None, n=s.N, depth=s.D, width=s.W,
+                     eta=s.eta, gamma=s.gamma, seed=s.seed, A=s.A) for m, s in zip(ms, specs)]
+        outs, keep = V.vopp_plan_batch(ctx, reqs)
+        for p, s in enumerate(specs):
+            orc = s.run_oracle()
+            n = (s.A * s.W) ** 2
+            assert_close(V.vopp_tree_read(ctx, V.VOPP_FIELD_V, 2, n, plan=p), orc["V"][2], "V2")
+            np.testing.assert_array_equal(V.vopp_tree_read(ctx, V.VOPP_FIELD_REP, 2, n, plan=p),
+                                          orc["rep"][2])
+        for m in ms:
+            V.vopp_model_destroy(m)
+        del keep
+    finally:
+        V.vopp_ctx_destroy(ctx)
+
+
+def test_config3_grid_sampled_subtrees_bit_exact():
+    """GRID 11x11, 8 rocks, N=2048, depth 5, 13 actions x 3 branches (9.0e7 leaves,
+    1.9e11 particle-steps): three level-3 subtrees against the oracle, integers exact."""
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec.from_plan(WL.CONFIG3)
+    g = Gpu(spec)
+    try:
+        res = g.plan()
+        AW = 39
+        rng = np.random.default_rng(1)
+        for _ in range(3):
+            path = tuple(int(v) for v in rng.integers(0, AW, 3))
+            sub = spec.run_oracle(path=path)
+            assert sub["status"] == O.OK
+            n3 = (path[0] * AW + path[1]) * AW + path[2]
+            assert_close(g.read(V.VOPP_FIELD_V, 3, 1, n3), sub["V"][3], f"V3 {path}")
+            assert_close(g.read(V.VOPP_FIELD_Q, 3, 13, n3 * 13), sub["Q"][3][0], f"Q3 {path}")
+            assert_close(g.read(V.VOPP_FIELD_V, 4, AW, n3 * AW), sub["V"][4], f"V4 {path}")
+            assert_close(g.read(V.VOPP_FIELD_Q, 4, AW * 13, n3 * AW * 13), sub["Q"][4].ravel(),
+                         f"Q4 {path}")
+            assert_close(g.read(V.VOPP_FIELD_RBAR, 4, AW, n3 * AW), sub["rbar"][4], f"rbar4 {path}")
+            assert_close(g.read(V.VOPP_FIELD_LOMEGA, 4, AW, n3 * AW), sub["lomega"][4], f"lom4 {path}")
+            np.testing.assert_array_equal(g.read(V.VOPP_FIELD_REP, 4, AW, n3 * AW), sub["rep"][4])
+            n5 = AW * AW
+            o5 = n3 * n5
+            assert_close(g.read(V.VOPP_FIELD_V, 5, n5, o5), sub["V"][5], f"V5 {path}")
+            assert_close(g.read(V.VOPP_FIELD_RBAR, 5, n5, o5), sub["rbar"][5], f"rbar5 {path}")
+            assert_close(g.read(V.VOPP_FIELD_LOMEGA, 5, n5, o5), sub["lomega"][5], f"lom5 {path}")
+            np.testing.assert_array_equal(g.read(V.VOPP_FIELD_REP, 5, n5, o5), sub["rep"][5])
+            np.testing.assert_array_equal(g.read(V.VOPP_FIELD_OBS, 5, 2 * n5, 2 * o5),
+                                          sub["obs"][5].ravel())
+            # the level-3 particle store (materialised), bit-exact states
+            ps = g.read(V.VOPP_FIELD_PS, 3, 2048, n3 * 2048)
+            sub_d = spec.run_oracle(path=path, dump_levels=3, outputs=False)
+            np.testing.assert_array_equal(ps, sub_d["ps"][3][0])
+            assert_close(g.read(V.VOPP_FIELD_PLW, 3, 2048, n3 * 2048), sub_d["plw"][3][0], "plw3")
+        # root: the FP64 root backup of the level-1 stats (closed form, any size)
+        q1 = np.zeros(13)
+        rb = g.read(V.VOPP_FIELD_RBAR, 1, AW).astype(np.float64).reshape(13, 3)
+        lo = g.read(V.VOPP_FIELD_LOMEGA, 1, AW).astype(np.float64).reshape(13, 3)
+        v1 = g.read(V.VOPP_FIELD_V, 1, AW).astype(np.float64).reshape(13, 3)
+        for a in range(13):
+            om = np.exp(lo[a] - lo[a].max())
+            q1[a] = rb[a].mean() + 0.95 * (om @ v1[a]) / om.sum()
+        assert_close(res["q"], q1, "root Q from level-1 stats")
+        v = 1.0 * np.log(np.mean(np.exp((q1 - q1.max()) / 1.0))) + q1.max()
+        assert_close([res["v_root"]], [v], "root V")
+        assert res["particle_steps"] == WL.CONFIG3.steps
+    finally:
+        g.close()

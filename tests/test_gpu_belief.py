@@ -1,0 +1,100 @@
+"""SIR belief update (Sec. III-B) of the CUDA path vs the FP64 oracle (needs a GPU).
+
+Two updates in a row on an agent: propagated states (NAV2D within 1e-4 max(|x|,1), GRID
+bit-exact), normalised log weights within the same tolerance, ESS, the resampling decision
+and the ancestor indices (exact unless the oracle flags a CDF position or the ESS test
+within 1e-5 of a tie, where FP32 weights may decide differently).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_27191_b300 import workloads as WL
+from tests.parity import assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(kind, N, steps, seed=9, weights="uniform"):
+    """Each step starts the oracle from the GPU's current particles (identical inputs)."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        if kind == WL.NAV2D:
+            x, y, w = WL.nav_root(N, 3, weights)
+            x = (8.0 + 2.0 * (x / 10.0)).astype(np.float32)
+            st = np.concatenate([x, y]).astype(np.float32)
+            desc = V.make_desc(V.VOPP_NAV2D)
+            om = O.make_model(O.NAV2D)
+        else:
+            rx, ry = WL.grid_layout(2)
+            s, w = WL.grid_root(N, 3, weights)
+            st = np.asarray(s, dtype=np.int32)
+            desc = V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry)
+            om = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+        model = V.vopp_create_model(ctx, desc)
+        agent = V.vopp_agent_create(model, st, w, N, seed)
+        resampled_any = False
+        for t, (a, obs) in enumerate(steps):
+            gst0, glw0, _ = V.vopp_agent_get_particles(agent, kind)
+            kw = (dict(x=gst0[:N], y=gst0[N:]) if kind == WL.NAV2D else dict(s=gst0))
+            ess, res = V.vopp_belief_update(agent, a, obs, kind)
+            rc, o = O.belief_update(om, glw0.astype(np.float64), a, obs, seed, t, **kw)
+            assert rc == O.OK
+            gst, glw, ganc = V.vopp_agent_get_particles(agent, kind)
+            assert_close([ess], [o["ess"]], "ESS")
+            if not o["ess_tie"]:
+                assert res == o["resampled"]
+            resampled_any |= res
+            # ancestors: exact away from CDF ties, a neighbouring index at a flagged tie
+            same = ganc == o["ancestors"]
+            assert np.all(same | o["ties"]), np.flatnonzero(~(same | o["ties"]))[:5]
+            assert np.all(np.abs(ganc.astype(np.int64) - o["ancestors"]) <= 1)
+            # every output particle is the propagated state of the ancestor the GPU chose
+            if kind == WL.NAV2D:
+                assert_close(gst[:N], o["prop_x"][ganc], "x")
+                assert_close(gst[N:], o["prop_y"][ganc], "y")
+            else:
+                np.testing.assert_array_equal(gst, o["prop_s"][ganc])
+            lw_ref = o["lw"] if not res else np.full(N, -math.log(N))
+            assert_close(glw, lw_ref, "log weights")
+        V.vopp_agent_destroy(agent)
+        V.vopp_model_destroy(model)
+        return resampled_any
+    finally:
+        V.vopp_ctx_destroy(ctx)
+
+
+def test_nav_belief_update_two_steps():
+    assert _run(WL.NAV2D, 2500, [(0, (8.9, 4.2)), (3, (9.1, 3.0))])
+
+
+def test_nav_belief_update_weighted_no_resample():
+    _run(WL.NAV2D, 777, [(2, (5.0, 5.0))], weights="random")
+
+
+def test_grid_belief_update_two_steps():
+    # repeated senses of rocks 0 and 1 push the ESS below N/2 on the sixth update
+    assert _run(WL.GRID, 4096, [(5, 1), (5, 1), (6, 2), (0, 0), (6, 2), (5, 1)])
+
+
+def test_belief_update_degenerate_is_reported():
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        rx, ry = WL.grid_layout(2)
+        model = V.vopp_create_model(ctx, V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry))
+        st = WL.pack_grid_state(np.zeros(16, dtype=np.int64), rx[0], ry[0])   # rock 0 bad
+        agent = V.vopp_agent_create(model, st, None, 16, 1)
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_belief_update(agent, 5, 1, WL.GRID)      # "good" at distance 0: impossible
+        assert e.value.code == V.VOPP_E_DEGENERATE
+        s2, lw2, _ = V.vopp_agent_get_particles(agent, WL.GRID)
+        np.testing.assert_array_equal(s2, st)
+        np.testing.assert_allclose(lw2, math.log(1 / 16), rtol=1e-6)
+        V.vopp_agent_destroy(agent)
+        V.vopp_model_destroy(model)
+    finally:
+        V.vopp_ctx_destroy(ctx)
