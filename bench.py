@@ -57,6 +57,26 @@ SMS = 148
 LANES_PER_CLK = 128
 
 
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("vopp_kernels.cu", "vopp_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_27191_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def leaf_traffic(workload: str):
+    """DRAM bytes per leaf launch from the committed ncu capture of this workload, or None
+    when there is none or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", f"k_leaf_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d["dram_bytes_per_launch"] if d.get("source_hash") == kernel_source_hash() else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -327,7 +347,8 @@ def main():
                     "d2h_bytes_per_step": int(c2["d2h_bytes"] // max(args.steps, 1))},
             "roofline": {"kernel": "k_leaf", "bound": "alu", "achieved": achieved_ops / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tinstr/s",
-                         "frac": achieved_ops / peak_ops, "traffic": None,
+                         "frac": achieved_ops / peak_ops, "traffic": leaf_traffic(args.workload),
+                         "traffic_unit": "DRAM bytes per launch (ncu capture, profiles/)",
                          "peak_source": f"148 SMs x 128 lanes/clk x {sm_max:.0f} MHz ({pk_src} max clock)",
                          "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
                          "units_per_launch": leaf_steps, "avg_launch_ms": leaf_avg_s * 1e3,
