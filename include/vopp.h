@@ -172,6 +172,8 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 #define VOPP_OPT_LEAF_THREADS 2
 #define VOPP_OPT_GRID_CAP 3
 #define VOPP_OPT_TAIL_MAX_NODES 4
+#define VOPP_OPT_PERSISTENT 5   /* 1: leaf CTAs fill every SM once and pull work items from a
+                                   counter (largest items first); 0 (default): one CTA per item */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
@@ -272,6 +274,44 @@ VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void *states, f
  * calls with the same arguments.  All models must belong to ctx. */
 VOPP_API int vopp_plan_batch(vopp_ctx *ctx, int32_t n, const vopp_plan_request *reqs,
                     vopp_plan_result *outs);
+
+/* ---- serving: continuous batching of plan requests ------------------------------------ */
+typedef struct vopp_server vopp_server;
+typedef struct {
+  uint64_t submitted, completed, rejected;  /* rejected: footprint larger than the budget  */
+  uint64_t batches, batched_plans, max_batch_seen;
+  uint64_t particle_steps;                  /* of completed plans                         */
+  uint64_t pending;                         /* requests waiting for a slot                */
+  uint64_t in_flight_bytes, peak_in_flight_bytes;
+} vopp_server_stats;
+
+/* Start a serving loop on ctx: a worker thread batches queued requests (at most max_batch
+ * per batch) onto n_slots streams whenever a slot is free and the batch's device footprint
+ * fits in hbm_budget_bytes together with the batches already in flight (0 = the context's
+ * budget); batches on different slots overlap on the device, and requests arriving while
+ * others run join the next batch.  Arenas come from the device's stream-ordered memory
+ * pool.  A plan's result does not depend on the batch it ran in.  The worker reads the
+ * context's options and the models; do not destroy a model, agent or the context while
+ * requests that use them are outstanding, and do not update an agent's belief while a
+ * request on that agent is outstanding. */
+VOPP_API int vopp_server_create(vopp_ctx *ctx, int32_t max_batch, int32_t n_slots,
+                                size_t hbm_budget_bytes, vopp_server **out);
+/* Stop accepting work, finish everything queued or in flight, release the server. */
+VOPP_API void vopp_server_destroy(vopp_server *srv);
+/* Queue one plan (non-blocking).  Host inputs are copied at submission; device inputs are
+ * read when the request's batch runs and must stay valid until the ticket completes. */
+VOPP_API int vopp_submit(vopp_server *srv, const vopp_plan_request *req, uint64_t *ticket);
+/* Queue a plan from an agent's device-resident belief (non-blocking). */
+VOPP_API int vopp_submit_agent(vopp_server *srv, vopp_agent *agent, const vopp_plan_params *params,
+                               uint64_t *ticket);
+/* VOPP_E_BUSY while the ticket's plan is queued or running; otherwise the plan's status,
+ * with its result (and submission-to-completion latency in seconds) written and the ticket
+ * released. */
+VOPP_API int vopp_poll(vopp_server *srv, uint64_t ticket, vopp_plan_result *out, double *latency_s);
+/* Like vopp_poll, blocking up to timeout_s seconds (VOPP_E_TIMEOUT if still not done). */
+VOPP_API int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_result *out,
+                       double *latency_s);
+VOPP_API int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out);
 
 VOPP_API const char *vopp_last_error(void);
 /* Library version string. */

@@ -7,7 +7,14 @@
 // materialising expansion per level, the fused leaf expansion, large-level backups and
 // the per-plan tail with the FP64 root -- each launch covering every plan of the batch.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdarg>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -64,15 +71,28 @@ struct TimedLaunch {
 // ---------------------------------------------------------------------------------------
 // Objects.
 // ---------------------------------------------------------------------------------------
+namespace {
+// Resources of one in-flight launch sequence: its stream and a metadata block (plan
+// descriptors, stage tables, results, root copies) in device memory with a pinned mirror.
+struct Slot {
+  cudaStream_t stream = nullptr;
+  char *meta = nullptr;          // device metadata block
+  char *hmeta = nullptr;         // pinned host mirror
+  size_t meta_cap = 0;
+  size_t off_res = 0, off_desc = 0;
+  int n = 0;
+};
+}  // namespace
+
 struct vopp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   char *arena = nullptr;
   size_t arena_cap = 0;
-  char *meta = nullptr;          // device metadata block
-  char *hmeta = nullptr;         // pinned host mirror
-  size_t meta_cap = 0;
+  Slot slot;                     // the synchronous path's slot (stream = ctx stream)
+  int leaf_persistent = 0;       // persistent leaf CTAs pulling work from a counter
+  int sm_count = 148;
   int tree_detail = VOPP_TREE_MINIMAL;
   int leaf_gen = 1;              // generate level D-1 inside the leaf kernel
   int leaf_threads = 128;
@@ -84,7 +104,7 @@ struct vopp_ctx {
   std::vector<TimedLaunch> pending;
   double fam_ms[F_COUNT] = {0};
   unsigned long long fam_n[F_COUNT] = {0};
-  unsigned long long h2d_bytes = 0, d2h_bytes = 0, launches = 0;
+  std::atomic<unsigned long long> h2d_bytes{0}, d2h_bytes{0}, launches{0};
   // last launch, for vopp_tree_read
   std::vector<PlanDesc> last_desc;
   std::vector<int> last_ok;
@@ -226,23 +246,30 @@ int ensure_arena(vopp_ctx *c, size_t bytes) {
   return VOPP_OK;
 }
 
-int ensure_meta(vopp_ctx *c, size_t bytes) {
-  if (bytes <= c->meta_cap) return VOPP_OK;
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  if (c->meta) cudaFree(c->meta);
-  if (c->hmeta) cudaFreeHost(c->hmeta);
-  c->meta = c->hmeta = nullptr;
-  c->meta_cap = 0;
+int ensure_meta(Slot &s, size_t bytes) {
+  if (bytes <= s.meta_cap) return VOPP_OK;
+  CUDA_TRY(cudaStreamSynchronize(s.stream));
+  if (s.meta) cudaFree(s.meta);
+  if (s.hmeta) cudaFreeHost(s.hmeta);
+  s.meta = s.hmeta = nullptr;
+  s.meta_cap = 0;
   const size_t want = align_up(std::max(bytes, (size_t)1 << 16) * 2, 1 << 16);
-  if (cudaMalloc(&c->meta, want) != cudaSuccess) { cudaGetLastError(); return fail(VOPP_E_NOMEM, "meta alloc"); }
-  if (cudaMallocHost(&c->hmeta, want) != cudaSuccess) {
+  if (cudaMalloc(&s.meta, want) != cudaSuccess) { cudaGetLastError(); return fail(VOPP_E_NOMEM, "meta alloc"); }
+  if (cudaMallocHost(&s.hmeta, want) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(c->meta);
-    c->meta = nullptr;
+    cudaFree(s.meta);
+    s.meta = nullptr;
     return fail(VOPP_E_NOMEM, "pinned meta alloc");
   }
-  c->meta_cap = want;
+  s.meta_cap = want;
   return VOPP_OK;
+}
+
+void free_slot(Slot &s) {
+  if (s.meta) cudaFree(s.meta);
+  if (s.hmeta) cudaFreeHost(s.hmeta);
+  s.meta = s.hmeta = nullptr;
+  s.meta_cap = 0;
 }
 
 // ---- timing -----------------------------------------------------------------------------
@@ -302,13 +329,44 @@ struct StageBuild {
   StageTable st{};
 };
 
-int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *statuses) {
-  const int n = (int)jobs.size();
-  // arena
+// CTAs of a persistent leaf launch: every SM filled to the kernel's occupancy.
+int persistent_grid(vopp_ctx *c, size_t smem) {
+  int per_sm = 0;
+  if (leaf_occupancy(c->leaf_threads, smem, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return per_sm * c->sm_count;
+}
+
+// Arena bytes of a batch; assigns each job its offset.
+size_t place_jobs(std::vector<Job> &jobs) {
   size_t arena_bytes = 0;
   for (auto &j : jobs) { j.arena_off = arena_bytes; arena_bytes = align_up(arena_bytes + j.lay.bytes, 256); }
-  int rc = ensure_arena(c, std::max<size_t>(arena_bytes, 256));
-  if (rc) return rc;
+  return std::max<size_t>(arena_bytes, 256);
+}
+
+// Relative cost of one work item of a plan's leaf / expansion stage (for ordering).
+double item_cost(const Job &j, bool leaf) {
+  const double per = (j.shape.kind == kNav) ? 2.0 : 1.0;
+  return per * j.shape.N * (leaf ? (double)(j.shape.AW + 1) : 1.0);
+}
+
+// Plan indices of a stage, most expensive work items first (longest-processing-time order,
+// so that the CTAs dispatched first carry the largest items).
+std::vector<int> lpt_order(const std::vector<Job> &jobs, bool leaf) {
+  std::vector<int> idx(jobs.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    return item_cost(jobs[x], leaf) > item_cost(jobs[y], leaf);
+  });
+  return idx;
+}
+
+// Build the metadata block of a batch in the slot's pinned mirror, upload it and enqueue
+// every launch and the device->host copy of the results on the slot's stream.  Nothing
+// here waits for the device.
+int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, bool timed) {
+  const int n = (int)jobs.size();
+  int rc = VOPP_OK;
+  const std::vector<int> order_leaf = lpt_order(jobs, true), order_exp = lpt_order(jobs, false);
 
   // stages
   std::vector<StageBuild> stages;
@@ -329,7 +387,7 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     s.family = F_EXPAND;
     s.level = l;
     long long acc = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i : order_exp) {
       if (jobs[i].shape.mat_top > l) {
         s.plans.push_back(i);
         s.levels.push_back(l);
@@ -347,7 +405,7 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     s.family = F_LEAF;
     s.level = 0;
     long long acc = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i : order_leaf) {
       if (jobs[i].shape.D >= 1) {
         s.plans.push_back(i);
         s.prefix.push_back(acc);
@@ -412,7 +470,8 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     const size_t k = stages[s].plans.size();
     off = align_up(off + 4 * k, 8);            // plan ids
     off = align_up(off + 8 * (k + 1), 8);      // prefix
-    off = align_up(off + 4 * k, 256);          // levels
+    off = align_up(off + 4 * k, 8);            // levels
+    off = align_up(off + 8, 256);              // work counter (persistent launches)
   }
   std::vector<size_t> root_off(n, kNone);
   for (int i = 0; i < n; ++i) {
@@ -424,10 +483,13 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
       off = align_up(off + sb + wb, 256);
     }
   }
-  rc = ensure_meta(c, off);
+  rc = ensure_meta(sl, off);
   if (rc) return rc;
-  char *H = c->hmeta, *Dm = c->meta;
-  std::memset(H + off_res, 0, sizeof(DevResult) * n);
+  char *H = sl.hmeta, *Dm = sl.meta;
+  std::memset(H, 0, off);
+  sl.off_res = off_res;
+  sl.off_desc = off_desc;
+  sl.n = n;
   PlanDesc *hd = reinterpret_cast<PlanDesc *>(H + off_desc);
   const PlanDesc *dd = reinterpret_cast<const PlanDesc *>(Dm + off_desc);
   for (int i = 0; i < n; ++i) {
@@ -461,7 +523,7 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     P.key0 = (uint32_t)j.p.seed;
     P.key1 = (uint32_t)(j.p.seed >> 32);
     P.model = j.model->dev;
-    char *base = c->arena + j.arena_off;
+    char *base = arena + j.arena_off;
     const PlanLayout &L = j.lay;
     auto fp = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<float *>(base + o); };
     auto ip = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<int *>(base + o); };
@@ -523,36 +585,50 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     } else {
       sb.st.levels = nullptr;
     }
+    o = align_up(o + 4 * k, 8);
+    sb.st.counter = reinterpret_cast<unsigned long long *>(Dm + o);   // zeroed by the upload
     sb.st.n_plans = (int)k;
     sb.st.level = sb.level;
   }
-  CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, c->stream));
+  cudaStream_t stream = sl.stream;
+  CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
   c->h2d_bytes += off;
   c->d2h_bytes += sizeof(DevResult) * n;
   c->launches += stages.size();
 
   for (auto &sb : stages) {
     TimedLaunch tl;
-    timed_begin(c, sb.family, tl);
+    if (timed) timed_begin(c, sb.family, tl);
     cudaError_t e = cudaSuccess;
     switch (sb.family) {
-      case F_ROOT: e = launch_root_prep(dd, sb.st, c->stream); break;
-      case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, c->grid_cap, c->stream); break;
-      case F_LEAF: e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads, c->grid_cap, c->stream); break;
-      case F_BACKUP: e = launch_backup(dd, sb.st, sb.total, c->stream); break;
-      case F_TAIL: e = launch_backup_tail(dd, sb.st, c->stream); break;
+      case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
+      case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, c->grid_cap, stream); break;
+      case F_LEAF:
+        if (!c->leaf_persistent) sb.st.counter = nullptr;
+        e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads,
+                        c->leaf_persistent ? persistent_grid(c, sb.smem) : c->grid_cap, stream);
+        break;
+      case F_BACKUP: e = launch_backup(dd, sb.st, sb.total, stream); break;
+      case F_TAIL: e = launch_backup_tail(dd, sb.st, stream); break;
     }
-    timed_end(c, tl);
+    if (timed) timed_end(c, tl);
     if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
   }
   CUDA_TRY(cudaMemcpyAsync(H + off_res, Dm + off_res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost,
-                           c->stream));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  timed_collect(c);
+                           stream));
+  return VOPP_OK;
+}
 
-  c->last_desc.assign(hd, hd + n);
-  c->last_ok.assign(n, 1);
-  const DevResult *hr = reinterpret_cast<const DevResult *>(H + off_res);
+// Fill the results of a batch whose launches have completed on the slot's stream.
+int collect_results(vopp_ctx *c, const Slot &sl, const std::vector<Job> &jobs,
+                    vopp_plan_result *outs, int *statuses, bool remember) {
+  const int n = (int)jobs.size();
+  const PlanDesc *hd = reinterpret_cast<const PlanDesc *>(sl.hmeta + sl.off_desc);
+  if (remember) {
+    c->last_desc.assign(hd, hd + n);
+    c->last_ok.assign(n, 1);
+  }
+  const DevResult *hr = reinterpret_cast<const DevResult *>(sl.hmeta + sl.off_res);
   int first_err = VOPP_OK;
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
@@ -562,7 +638,7 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
     if (hr[i].status & kStatusDegenerateRoot) {
       st = VOPP_E_DEGENERATE;
       o.action = -1;
-      c->last_ok[i] = 0;
+      if (remember) c->last_ok[i] = 0;
     } else {
       o.action = hr[i].action;
       o.v_root = hr[i].v_root;
@@ -582,6 +658,17 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
   }
   if (first_err == VOPP_E_DEGENERATE) fail(VOPP_E_DEGENERATE, "root belief has zero total weight");
   return first_err;
+}
+
+int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *statuses) {
+  int rc = ensure_arena(c, place_jobs(jobs));
+  if (rc) return rc;
+  c->slot.stream = c->stream;
+  rc = enqueue_jobs(c, c->slot, c->arena, jobs, c->timing);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  timed_collect(c);
+  return collect_results(c, c->slot, jobs, outs, statuses, true);
 }
 
 int make_job(vopp_ctx *c, vopp_model *m, const void *states, const float *weights, int N,
@@ -657,6 +744,10 @@ int vopp_ctx_create(int device, size_t hbm_budget_bytes, uintptr_t cuda_stream, 
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete c; return fail(VOPP_E_CUDA, "cudaMemGetInfo"); }
   c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
+  c->slot.stream = c->stream;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+    c->sm_count = sms;
   *out = c;
   return VOPP_OK;
 }
@@ -666,8 +757,7 @@ void vopp_ctx_destroy(vopp_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->arena) cudaFree(c->arena);
-  if (c->meta) cudaFree(c->meta);
-  if (c->hmeta) cudaFreeHost(c->hmeta);
+  free_slot(c->slot);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -691,6 +781,7 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       if (value < 1) return fail(VOPP_E_INVALID, "grid cap");
       c->grid_cap = (int)std::min<int64_t>(value, 1 << 30);
       return VOPP_OK;
+    case VOPP_OPT_PERSISTENT: c->leaf_persistent = value ? 1 : 0; return VOPP_OK;
     case VOPP_OPT_TAIL_MAX_NODES:
       if (value < 1) return fail(VOPP_E_INVALID, "tail max nodes");
       c->tail_max_nodes = (int)std::min<int64_t>(value, 1 << 20);
@@ -1039,3 +1130,347 @@ int vopp_agent_get_particles(vopp_agent *g, void *states, float *log_weights, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Serving loop: continuous batching of plan requests.
+//
+// Requests wait in a FIFO.  A worker thread forms a batch from the head of the queue
+// whenever a slot is free and the HBM budget admits it, builds the batch's launch sequence
+// on the slot's own stream (arena from the device's stream-ordered pool, released on the
+// same stream after the results are copied back) and moves on; a host callback at the end
+// of the slot's stream wakes the worker, which posts the results.  Batches on different
+// slots run concurrently on the device, and requests that arrive while others run join the
+// next batch.  Each plan's random numbers are keyed by its own seed, so a plan's result does
+// not depend on which batch it joined.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerReq {
+  uint64_t ticket = 0;
+  Job job;
+  std::vector<char> host_states, host_weights;   // copies of host inputs
+  std::vector<float> pi_bar;
+  size_t bytes = 0;
+  double t_submit = 0.0;
+};
+
+struct ServerSlot {
+  Slot slot;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<ServerReq> reqs;
+  std::vector<Job> jobs;
+  bool busy = false;
+  std::atomic<int> complete{0};
+  struct vopp_server *owner = nullptr;
+};
+
+struct Done {
+  int status;
+  vopp_plan_result res;
+  double t_submit, t_done;
+};
+
+}  // namespace
+
+struct vopp_server {
+  vopp_ctx *c = nullptr;
+  int max_batch = 64;
+  size_t budget = 0, in_flight = 0, peak_in_flight = 0;
+  std::vector<ServerSlot *> slots;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::deque<ServerReq> pending;
+  std::unordered_map<uint64_t, Done> done;
+  uint64_t next_ticket = 1;
+  vopp_server_stats stats{};
+  int worker_error = VOPP_OK;
+};
+
+namespace {
+
+// Runs on a CUDA callback thread when a slot's stream reaches the end of its batch.  It
+// takes no lock and makes no CUDA call: the worker may be inside a CUDA call that waits for
+// this very stream while holding the server mutex.  The worker's waits are bounded, so a
+// notification that races with its predicate check only delays it by one wait period.
+void CUDART_CB slot_complete(void *arg) {
+  ServerSlot *s = static_cast<ServerSlot *>(arg);
+  s->complete.store(1);
+  s->owner->cv_work.notify_one();
+}
+
+// Harvest a finished slot (worker thread, lock held).
+void harvest(vopp_server *srv, ServerSlot *s) {
+  const int n = (int)s->jobs.size();
+  std::vector<vopp_plan_result> outs(n);
+  std::vector<int> st(n);
+  collect_results(srv->c, s->slot, s->jobs, outs.data(), st.data(), false);
+  const double t = now_s();
+  for (int i = 0; i < n; ++i) {
+    srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
+    srv->stats.completed += 1;
+    srv->stats.particle_steps += outs[i].particle_steps;
+  }
+  srv->in_flight -= s->arena_bytes;
+  s->arena = nullptr;
+  s->arena_bytes = 0;
+  s->reqs.clear();
+  s->jobs.clear();
+  s->busy = false;
+  s->complete.store(0);
+}
+
+// Start a batch on a free slot from the head of the queue (worker thread, lock held).
+// Returns false when nothing could be started.
+bool start_batch(vopp_server *srv, ServerSlot *s) {
+  std::vector<ServerReq> batch;
+  size_t bytes = 0;
+  while (!srv->pending.empty() && (int)batch.size() < srv->max_batch) {
+    ServerReq &r = srv->pending.front();
+    if (srv->in_flight + bytes + r.bytes > srv->budget) {
+      if (batch.empty() && srv->in_flight == 0) {   // can never fit: refuse it
+        vopp_plan_result z;
+        std::memset(&z, 0, sizeof z);
+        z.action = -1;
+        srv->done[r.ticket] = Done{VOPP_E_BUDGET, z, r.t_submit, now_s()};
+        srv->stats.rejected += 1;
+        srv->pending.pop_front();
+        continue;
+      }
+      break;
+    }
+    bytes += r.bytes;
+    batch.push_back(std::move(r));
+    srv->pending.pop_front();
+  }
+  if (batch.empty()) return false;
+  std::vector<Job> jobs;
+  for (auto &r : batch) {
+    jobs.push_back(r.job);
+    Job &j = jobs.back();
+    if (!r.host_states.empty()) j.states = r.host_states.data();
+    if (!r.host_weights.empty()) j.weights = reinterpret_cast<const float *>(r.host_weights.data());
+    if (!r.pi_bar.empty()) j.p.pi_bar = r.pi_bar.data();
+  }
+  const size_t arena_bytes = place_jobs(jobs);
+  char *arena = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&arena), arena_bytes, s->slot.stream);
+  int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false) : VOPP_E_NOMEM;
+  if (rc == VOPP_OK) {
+    if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
+        cudaLaunchHostFunc(s->slot.stream, slot_complete, s) != cudaSuccess)
+      rc = VOPP_E_CUDA;
+  }
+  if (rc != VOPP_OK) {   // post the failure to every request of the batch
+    cudaGetLastError();
+    if (arena) cudaFreeAsync(arena, s->slot.stream);
+    cudaStreamSynchronize(s->slot.stream);
+    vopp_plan_result z;
+    std::memset(&z, 0, sizeof z);
+    z.action = -1;
+    for (auto &r : batch) srv->done[r.ticket] = Done{rc, z, r.t_submit, now_s()};
+    srv->cv_done.notify_all();
+    return true;
+  }
+  s->arena = arena;
+  s->arena_bytes = arena_bytes;
+  s->reqs = std::move(batch);
+  s->jobs = std::move(jobs);
+  s->busy = true;
+  srv->in_flight += arena_bytes;
+  srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
+  srv->stats.batches += 1;
+  srv->stats.batched_plans += s->reqs.size();
+  srv->stats.max_batch_seen = std::max<uint64_t>(srv->stats.max_batch_seen, s->reqs.size());
+  return true;
+}
+
+void worker_main(vopp_server *srv) {
+  cudaSetDevice(srv->c->device);
+  std::unique_lock<std::mutex> lock(srv->mu);
+  for (;;) {
+    bool harvested = false;
+    for (auto *s : srv->slots)
+      if (s->busy && s->complete.load()) { harvest(srv, s); harvested = true; }
+    if (harvested) srv->cv_done.notify_all();
+    for (auto *s : srv->slots) {
+      if (srv->pending.empty()) break;
+      if (!s->busy) start_batch(srv, s);
+    }
+    int busy = 0;
+    for (auto *s : srv->slots) busy += s->busy;
+    if (srv->stop) {
+      if (busy == 0 && srv->pending.empty()) break;
+      // shutting down: drain the busy slots directly rather than waiting for callbacks
+      for (auto *s : srv->slots) {
+        if (!s->busy) continue;
+        lock.unlock();
+        cudaStreamSynchronize(s->slot.stream);
+        lock.lock();
+        for (int spins = 0; !s->complete.load() && spins < 200000; ++spins) {   // <= ~10 s
+          lock.unlock();   // the callback follows the stream's last operation
+          std::this_thread::sleep_for(std::chrono::microseconds(50));
+          lock.lock();
+        }
+        if (!s->complete.load()) {   // callback never ran: give up on this slot's batch
+          srv->worker_error = VOPP_E_TIMEOUT;
+          s->complete.store(1);
+        }
+      }
+      continue;
+    }
+    srv->cv_work.wait_for(lock, std::chrono::microseconds(200), [&] {
+      if (srv->stop) return true;
+      for (auto *s : srv->slots) if (s->busy && s->complete.load()) return true;
+      if (!srv->pending.empty())
+        for (auto *s : srv->slots) if (!s->busy) return true;
+      return false;
+    });
+  }
+}
+
+int submit_req(vopp_server *srv, ServerReq &&r, uint64_t *ticket) {
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    r.ticket = srv->next_ticket++;
+    r.t_submit = now_s();
+    *ticket = r.ticket;
+    srv->stats.submitted += 1;
+    srv->pending.push_back(std::move(r));
+  }
+  srv->cv_work.notify_one();
+  return VOPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vopp_server_create(vopp_ctx *c, int32_t max_batch, int32_t n_slots, size_t hbm_budget_bytes,
+                       vopp_server **out) {
+  if (!c || !out || max_batch < 1 || n_slots < 1 || n_slots > 16)
+    return fail(VOPP_E_INVALID, "bad server arguments");
+  *out = nullptr;
+  cudaSetDevice(c->device);
+  vopp_server *srv = new (std::nothrow) vopp_server;
+  if (!srv) return fail(VOPP_E_NOMEM, "server alloc");
+  srv->c = c;
+  srv->max_batch = max_batch;
+  srv->budget = hbm_budget_bytes ? hbm_budget_bytes : c->budget;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t thr = ~0ull;   // keep freed arenas in the pool for the next batch
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  for (int i = 0; i < n_slots; ++i) {
+    ServerSlot *s = new (std::nothrow) ServerSlot;
+    if (!s || cudaStreamCreateWithFlags(&s->slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        ensure_meta(s->slot, 1 << 20) != VOPP_OK) {
+      delete s;
+      for (auto *q : srv->slots) { free_slot(q->slot); cudaStreamDestroy(q->slot.stream); delete q; }
+      delete srv;
+      return fail(VOPP_E_NOMEM, "server slot");
+    }
+    s->owner = srv;
+    srv->slots.push_back(s);
+  }
+  srv->worker = std::thread(worker_main, srv);
+  *out = srv;
+  return VOPP_OK;
+}
+
+void vopp_server_destroy(vopp_server *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  if (srv->worker.joinable()) srv->worker.join();
+  for (auto *s : srv->slots) {
+    cudaStreamSynchronize(s->slot.stream);
+    free_slot(s->slot);
+    cudaStreamDestroy(s->slot.stream);
+    delete s;
+  }
+  delete srv;
+}
+
+int vopp_submit(vopp_server *srv, const vopp_plan_request *req, uint64_t *ticket) {
+  if (!srv || !req || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
+  if (!req->model || req->model->ctx != srv->c) return fail(VOPP_E_INVALID, "model of another context");
+  ServerReq r;
+  int rc = make_job(srv->c, req->model, req->root_states, req->root_weights, req->n_particles,
+                    req->params, req->ptr_flags, r.job);
+  if (rc) return rc;
+  if (!(req->ptr_flags & VOPP_PTR_DEVICE)) {
+    const size_t sb = (r.job.shape.kind == kNav ? 8 : 4) * (size_t)r.job.shape.N;
+    r.host_states.assign(static_cast<const char *>(req->root_states),
+                         static_cast<const char *>(req->root_states) + sb);
+    if (req->root_weights)
+      r.host_weights.assign(reinterpret_cast<const char *>(req->root_weights),
+                            reinterpret_cast<const char *>(req->root_weights) + 4 * (size_t)r.job.shape.N);
+  }
+  if (req->params.pi_bar) r.pi_bar.assign(req->params.pi_bar, req->params.pi_bar + req->model->A);
+  r.bytes = r.job.lay.bytes + 256;
+  return submit_req(srv, std::move(r), ticket);
+}
+
+int vopp_submit_agent(vopp_server *srv, vopp_agent *g, const vopp_plan_params *p, uint64_t *ticket) {
+  if (!srv || !g || !p || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
+  if (g->model->ctx != srv->c) return fail(VOPP_E_INVALID, "agent of another context");
+  ServerReq r;
+  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  int rc = make_job(srv->c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, r.job);
+  if (rc) return rc;
+  r.job.log_weights = g->lw;
+  if (p->pi_bar) r.pi_bar.assign(p->pi_bar, p->pi_bar + g->model->A);
+  r.bytes = r.job.lay.bytes + 256;
+  return submit_req(srv, std::move(r), ticket);
+}
+
+static int take_done(vopp_server *srv, uint64_t ticket, vopp_plan_result *out, double *latency) {
+  auto it = srv->done.find(ticket);
+  if (it == srv->done.end()) return VOPP_E_BUSY;
+  const Done d = it->second;
+  srv->done.erase(it);
+  if (out) *out = d.res;
+  if (latency) *latency = d.t_done - d.t_submit;
+  if (d.status) return fail(d.status, "request failed");
+  return VOPP_OK;
+}
+
+int vopp_poll(vopp_server *srv, uint64_t ticket, vopp_plan_result *out, double *latency_s) {
+  if (!srv) return fail(VOPP_E_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  return take_done(srv, ticket, out, latency_s);
+}
+
+int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_result *out,
+              double *latency_s) {
+  if (!srv) return fail(VOPP_E_INVALID, "server is NULL");
+  std::unique_lock<std::mutex> lock(srv->mu);
+  const bool ok = srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                                        [&] { return srv->done.count(ticket) > 0; });
+  if (!ok) return fail(VOPP_E_TIMEOUT, "ticket not completed within the timeout");
+  return take_done(srv, ticket, out, latency_s);
+}
+
+int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out) {
+  if (!srv || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  *out = srv->stats;
+  out->pending = srv->pending.size();
+  out->in_flight_bytes = srv->in_flight;
+  out->peak_in_flight_bytes = srv->peak_in_flight;
+  return VOPP_OK;
+}
+
+}  // extern "C"
+

@@ -90,6 +90,7 @@ struct StageTable {
   const int *plan;            // [n_plans] plan index into the descriptor array
   const long long *prefix;    // [n_plans + 1]
   const int *levels;          // [n_plans] per-plan level (overrides `level` when non-null)
+  unsigned long long *counter;  // persistent launches: next work item (zero at launch)
 };
 
 __device__ __forceinline__ int find_plan(const StageTable &st, long long item) {

@@ -681,7 +681,15 @@ __global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDes
                                               long long total) {
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[32 * 5];
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+  __shared__ long long s_item;
+  long long item = blockIdx.x;
+  if (st.counter) {   // persistent CTAs: take work items in order from a global counter
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(st.counter, 1ull);
+    __syncthreads();
+    item = s_item;
+    __syncthreads();
+  }
+  while (item < total) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
     const unsigned long long node = (unsigned long long)(item - st.prefix[pi]);
@@ -689,6 +697,14 @@ __global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDes
       case kNav: leaf_item<NavModel>(P, node, smem, red); break;
       case kGrid: leaf_item<GridModel>(P, node, smem, red); break;
       default: leaf_item<ToyModel>(P, node, smem, red); break;
+    }
+    if (st.counter) {
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(st.counter, 1ull);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else {
+      item += gridDim.x;
     }
   }
 }
@@ -968,6 +984,12 @@ cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total
   const long long grid = total < grid_cap ? total : grid_cap;
   k_leaf<<<(unsigned)grid, threads, smem, s>>>(d, st, total);
   return cudaGetLastError();
+}
+
+cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf, threads, smem);
 }
 
 cudaError_t launch_backup(const PlanDesc *d, const StageTable &st, long long total_nodes,

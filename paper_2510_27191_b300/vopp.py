@@ -27,6 +27,7 @@ VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 (VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
  VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU) = range(11)
 VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP, VOPP_OPT_TAIL_MAX_NODES = 1, 2, 3, 4
+VOPP_OPT_PERSISTENT = 5
 VOPP_MAX_ACTIONS = 16
 NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
 
@@ -61,6 +62,12 @@ class vopp_plan_params(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("width", ctypes.c_int32), ("eta", ctypes.c_float),
                 ("gamma", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("pi_bar", ctypes.POINTER(ctypes.c_float))]
+
+
+class vopp_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "rejected", "batches", "batched_plans", "max_batch_seen",
+        "particle_steps", "pending", "in_flight_bytes", "peak_in_flight_bytes")]
 
 
 class vopp_plan_request(ctypes.Structure):
@@ -107,6 +114,14 @@ def _load():
                                         dp, ctypes.POINTER(i32)], ctypes.c_int),
         "vopp_plan_batch": ([vp, i32, ctypes.POINTER(vopp_plan_request),
                              ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_server_create": ([vp, i32, i32, ctypes.c_size_t, ctypes.POINTER(vp)], ctypes.c_int),
+        "vopp_server_destroy": ([vp], None),
+        "vopp_submit": ([vp, ctypes.POINTER(vopp_plan_request), ctypes.POINTER(u64)], ctypes.c_int),
+        "vopp_submit_agent": ([vp, vp, ctypes.POINTER(vopp_plan_params), ctypes.POINTER(u64)],
+                              ctypes.c_int),
+        "vopp_poll": ([vp, u64, ctypes.POINTER(vopp_plan_result), dp], ctypes.c_int),
+        "vopp_wait": ([vp, u64, ctypes.c_double, ctypes.POINTER(vopp_plan_result), dp], ctypes.c_int),
+        "vopp_server_get_stats": ([vp, ctypes.POINTER(vopp_server_stats)], ctypes.c_int),
         "vopp_last_error": ([], ctypes.c_char_p),
         "vopp_version": ([], ctypes.c_char_p),
     }
@@ -348,3 +363,65 @@ def vopp_plan_batch(ctx: int, requests: list) -> tuple[list, list]:
 
 def vopp_version() -> str:
     return lib.vopp_version().decode()
+
+
+# ---- serving ---------------------------------------------------------------------------
+def vopp_server_create(ctx: int, max_batch: int = 64, n_slots: int = 2, hbm_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    check(lib.vopp_server_create(ctx, max_batch, n_slots, hbm_budget_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def vopp_server_destroy(srv: int) -> None:
+    lib.vopp_server_destroy(srv)
+
+
+def vopp_submit_agent(srv: int, agent: int, depth: int, width: int, eta: float, gamma: float,
+                      seed: int, pi_bar=None) -> int:
+    p, keep = make_params(depth, width, eta, gamma, seed, pi_bar)
+    t = ctypes.c_uint64()
+    check(lib.vopp_submit_agent(srv, agent, ctypes.byref(p), ctypes.byref(t)))
+    del keep
+    return t.value
+
+
+def vopp_submit(srv: int, model: int, states, weights, n: int, depth: int, width: int, eta: float,
+                gamma: float, seed: int, pi_bar=None) -> int:
+    """Queue one plan; host (numpy) inputs are copied at submission, CUDA tensors must stay
+    alive until the ticket completes."""
+    sp, sdev, k1 = _addr(states)
+    wp, _, k2 = _addr(weights)
+    p, k3 = make_params(depth, width, eta, gamma, seed, pi_bar)
+    r = vopp_plan_request()
+    r.model, r.root_states, r.root_weights, r.n_particles = model, sp, wp, n
+    r.ptr_flags = VOPP_PTR_DEVICE if sdev else 0
+    r.params = p
+    t = ctypes.c_uint64()
+    check(lib.vopp_submit(srv, ctypes.byref(r), ctypes.byref(t)))
+    del k1, k2, k3
+    return t.value
+
+
+def vopp_poll(srv: int, ticket: int, A: int):
+    """None while busy; else (result dict, latency seconds)."""
+    r = vopp_plan_result()
+    lat = ctypes.c_double()
+    rc = lib.vopp_poll(srv, ticket, ctypes.byref(r), ctypes.byref(lat))
+    if rc == VOPP_E_BUSY:
+        return None
+    check(rc)
+    return _result_dict(r, A), lat.value
+
+
+def vopp_wait(srv: int, ticket: int, A: int, timeout_s: float = 10.0):
+    r = vopp_plan_result()
+    lat = ctypes.c_double()
+    check(lib.vopp_wait(srv, ticket, timeout_s, ctypes.byref(r), ctypes.byref(lat)))
+    return _result_dict(r, A), lat.value
+
+
+def vopp_server_get_stats(srv: int) -> dict:
+    st = vopp_server_stats()
+    check(lib.vopp_server_get_stats(srv, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in vopp_server_stats._fields_}
+
