@@ -233,6 +233,9 @@ def main():
     ap.add_argument("--impl", default="vopp", choices=["vopp", "reference"])
     ap.add_argument("--workload", default="nav1024_d4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="skip the batched (512 mixed plans) and served (Poisson requests) legs")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -357,6 +360,20 @@ def main():
             "clocks": clk.summary(),
             "result": {"action": int(last["action"]), "v_root": last["v_root"]},
         }
+        if not args.no_batch_serve:
+            from paper_2510_27191_b300 import loadgen as LG
+            out["batched"] = LG.batch_run(V, ctx)
+            served = {}
+            for rate in (2000.0, 16000.0):
+                for mode in ("served", "plain"):
+                    r = LG.serve_run(V, ctx, seconds=args.serve_seconds, rate=rate, mode=mode,
+                                     drain_factor=2.0)
+                    served[f"{mode}_{int(rate)}"] = {k: r[k] for k in (
+                        "plans_per_s", "particle_steps_per_s", "p50_ms", "p99_ms",
+                        "deadline_misses", "completed", "requests", "unfinished")}
+                    if mode == "served":
+                        served[f"{mode}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
+            out["served"] = served
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(spec)
         print(json.dumps(out))

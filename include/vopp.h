@@ -311,7 +311,15 @@ VOPP_API int vopp_poll(vopp_server *srv, uint64_t ticket, vopp_plan_result *out,
 /* Like vopp_poll, blocking up to timeout_s seconds (VOPP_E_TIMEOUT if still not done). */
 VOPP_API int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_result *out,
                        double *latency_s);
+/* Wait up to timeout_s seconds for the next plan to finish, in completion order; writes its
+ * ticket (and result and latency) and releases it.  Returns the plan's status, or
+ * VOPP_E_TIMEOUT when nothing finished in time. */
+VOPP_API int vopp_wait_any(vopp_server *srv, double timeout_s, uint64_t *ticket,
+                           vopp_plan_result *out, double *latency_s);
 VOPP_API int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out);
+/* paused = 1: keep queueing requests but start no new batch (batches in flight finish);
+ * paused = 0: resume.  Lets a caller release a burst of requests as full batches. */
+VOPP_API int vopp_server_set_paused(vopp_server *srv, int paused);
 
 VOPP_API const char *vopp_last_error(void);
 /* Library version string. */

@@ -7,6 +7,7 @@
 // materialising expansion per level, the fused leaf expansion, large-level backups and
 // the per-plan tail with the FP64 root -- each launch covering every plan of the batch.
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -400,22 +401,38 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     s.total = acc;
     if (acc) stages.push_back(s);
   }
+  // Leaf stage: one launch per shared-memory class (powers of two of the node buffer), so
+  // that small-N plans are not held to the occupancy of the largest node buffer.
   {
-    StageBuild s;
-    s.family = F_LEAF;
-    s.level = 0;
-    long long acc = 0;
-    for (int i : order_leaf) {
+    std::vector<int> classes;
+    for (int i : order_leaf)
       if (jobs[i].shape.D >= 1) {
+        const size_t b = leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW);
+        int cls = 0;
+        while (((size_t)1024 << cls) < b) ++cls;
+        if (std::find(classes.begin(), classes.end(), cls) == classes.end()) classes.push_back(cls);
+      }
+    std::sort(classes.begin(), classes.end(), std::greater<int>());
+    for (int cls : classes) {
+      StageBuild s;
+      s.family = F_LEAF;
+      s.level = 0;
+      long long acc = 0;
+      for (int i : order_leaf) {
+        if (jobs[i].shape.D < 1) continue;
+        const size_t b = leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW);
+        int c2 = 0;
+        while (((size_t)1024 << c2) < b) ++c2;
+        if (c2 != cls) continue;
         s.plans.push_back(i);
         s.prefix.push_back(acc);
         acc += nodes(jobs[i], jobs[i].shape.D - 1);
-        s.smem = std::max(s.smem, leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW));
+        s.smem = std::max(s.smem, b);
       }
+      s.prefix.push_back(acc);
+      s.total = acc;
+      if (acc) stages.push_back(s);
     }
-    s.prefix.push_back(acc);
-    s.total = acc;
-    if (acc) stages.push_back(s);
   }
   std::vector<int> tail_top(n, -1);
   for (int i = 0; i < n; ++i) {
@@ -1186,8 +1203,10 @@ struct vopp_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
+  bool paused = false;          // queue requests without starting batches
   std::deque<ServerReq> pending;
   std::unordered_map<uint64_t, Done> done;
+  std::deque<uint64_t> completion_order;   // tickets in the order their plans finished
   uint64_t next_ticket = 1;
   vopp_server_stats stats{};
   int worker_error = VOPP_OK;
@@ -1214,6 +1233,7 @@ void harvest(vopp_server *srv, ServerSlot *s) {
   const double t = now_s();
   for (int i = 0; i < n; ++i) {
     srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
+    srv->completion_order.push_back(s->reqs[i].ticket);
     srv->stats.completed += 1;
     srv->stats.particle_steps += outs[i].particle_steps;
   }
@@ -1239,6 +1259,7 @@ bool start_batch(vopp_server *srv, ServerSlot *s) {
         std::memset(&z, 0, sizeof z);
         z.action = -1;
         srv->done[r.ticket] = Done{VOPP_E_BUDGET, z, r.t_submit, now_s()};
+        srv->completion_order.push_back(r.ticket);
         srv->stats.rejected += 1;
         srv->pending.pop_front();
         continue;
@@ -1274,7 +1295,10 @@ bool start_batch(vopp_server *srv, ServerSlot *s) {
     vopp_plan_result z;
     std::memset(&z, 0, sizeof z);
     z.action = -1;
-    for (auto &r : batch) srv->done[r.ticket] = Done{rc, z, r.t_submit, now_s()};
+    for (auto &r : batch) {
+      srv->done[r.ticket] = Done{rc, z, r.t_submit, now_s()};
+      srv->completion_order.push_back(r.ticket);
+    }
     srv->cv_done.notify_all();
     return true;
   }
@@ -1300,7 +1324,7 @@ void worker_main(vopp_server *srv) {
       if (s->busy && s->complete.load()) { harvest(srv, s); harvested = true; }
     if (harvested) srv->cv_done.notify_all();
     for (auto *s : srv->slots) {
-      if (srv->pending.empty()) break;
+      if (srv->pending.empty() || (srv->paused && !srv->stop)) break;
       if (!s->busy) start_batch(srv, s);
     }
     int busy = 0;
@@ -1328,7 +1352,7 @@ void worker_main(vopp_server *srv) {
     srv->cv_work.wait_for(lock, std::chrono::microseconds(200), [&] {
       if (srv->stop) return true;
       for (auto *s : srv->slots) if (s->busy && s->complete.load()) return true;
-      if (!srv->pending.empty())
+      if (!srv->pending.empty() && !srv->paused)
         for (auto *s : srv->slots) if (!s->busy) return true;
       return false;
     });
@@ -1460,6 +1484,32 @@ int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_res
                                         [&] { return srv->done.count(ticket) > 0; });
   if (!ok) return fail(VOPP_E_TIMEOUT, "ticket not completed within the timeout");
   return take_done(srv, ticket, out, latency_s);
+}
+
+int vopp_wait_any(vopp_server *srv, double timeout_s, uint64_t *ticket, vopp_plan_result *out,
+                  double *latency_s) {
+  if (!srv || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
+  std::unique_lock<std::mutex> lock(srv->mu);
+  auto ready = [&] {
+    while (!srv->completion_order.empty() && !srv->done.count(srv->completion_order.front()))
+      srv->completion_order.pop_front();   // already taken by vopp_poll / vopp_wait
+    return !srv->completion_order.empty();
+  };
+  if (!srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready))
+    return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
+  *ticket = srv->completion_order.front();
+  srv->completion_order.pop_front();
+  return take_done(srv, *ticket, out, latency_s);
+}
+
+int vopp_server_set_paused(vopp_server *srv, int paused) {
+  if (!srv) return fail(VOPP_E_INVALID, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->paused = paused != 0;
+  }
+  srv->cv_work.notify_one();
+  return VOPP_OK;
 }
 
 int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out) {

@@ -74,7 +74,7 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
 
 def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int = 1024,
               seed: int = 11, mode: str = "served", deadline_s: float = 0.05, max_batch: int = 64,
-              n_slots: int = 3):
+              n_slots: int = 3, drain_factor: float = 3.0):
     """Poisson arrivals at `rate` per second over `n_agents` agents for `seconds`; each
     agent's requests are served in order, a belief update follows every completed plan."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x73657276]))
@@ -84,7 +84,7 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
               for i, ps in enumerate(specs)]
     n_req = rng.poisson(rate * seconds)
     arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
-    who = rng.integers(0, n_agents, n_req)
+    who = [int(v) for v in rng.integers(0, n_agents, n_req)]
     queues = [[] for _ in range(n_agents)]
     busy = np.zeros(n_agents, dtype=bool)
     lat, steps_done, updates = [], 0, 0
@@ -107,6 +107,17 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
         except V.VoppError:
             pass                      # impossible observation: belief left unchanged
 
+    resets = 0
+
+    def reset(i):
+        # every particle of agent i is terminal: its episode is over, start a new one
+        nonlocal resets
+        ps = specs[i]
+        V.vopp_agent_destroy(agents[i])
+        agents[i] = V.vopp_agent_create(models[ps.kind], _root(ps), None, ps.N,
+                                        1000003 * (i + 1) + 17 * resets)
+        resets += 1
+
     def issue(i):
         ps = specs[i]
         plan_count[i] += 1
@@ -121,37 +132,54 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
             queues[who[k]].append(arrivals[k])
             k += 1
         if mode == "served":
-            for i in np.flatnonzero(~busy):
+            for i in map(int, np.flatnonzero(~busy)):
                 if queues[i]:
                     inflight[issue(i)] = (i, queues[i].pop(0))
                     busy[i] = True
             done = []
-            for t, (i, arr) in inflight.items():
-                r = V.vopp_poll(srv, t, specs[i].A)
-                if r is not None:
-                    done.append((t, i, arr, r[0]))
+            while inflight:
+                got = V.vopp_wait_any(srv, 0.0 if (k < n_req or done) else 0.0005)
+                if got is None:
+                    break
+                t, rc, res, _ = got
+                if rc not in (V.VOPP_OK, V.VOPP_E_DEGENERATE):
+                    V.check(rc)
+                i, arr = inflight[t]
+                done.append((t, i, arr, res))
             for t, i, arr, res in done:
                 del inflight[t]
                 lat.append(time.perf_counter() - t0 - arr)
-                steps_done += res["particle_steps"]
-                after_plan(i, res)
+                if res is None:
+                    reset(i)
+                else:
+                    steps_done += res["particle_steps"]
+                    after_plan(i, res)
                 busy[i] = False
         else:
             # plain path: the oldest waiting request runs alone, synchronously
             cand = [(q[0], i) for i, q in enumerate(queues) if q]
             if cand:
                 arr, i = min(cand)
+                i = int(i)
                 queues[i].pop(0)
                 ps = specs[i]
                 plan_count[i] += 1
-                res = V.vopp_agent_plan(agents[i], models[ps.kind], ps.D, ps.W, ps.eta, ps.gamma,
-                                        (i + 1) * 7919 + int(plan_count[i]))
+                try:
+                    res = V.vopp_agent_plan(agents[i], models[ps.kind], ps.D, ps.W, ps.eta,
+                                            ps.gamma, (i + 1) * 7919 + int(plan_count[i]))
+                except V.VoppError as e:
+                    if e.code != V.VOPP_E_DEGENERATE:
+                        raise
+                    res = None
                 lat.append(time.perf_counter() - t0 - arr)
-                steps_done += res["particle_steps"]
-                after_plan(i, res)
+                if res is None:
+                    reset(i)
+                else:
+                    steps_done += res["particle_steps"]
+                    after_plan(i, res)
         if k >= n_req and not inflight and not any(queues):
             break
-        if time.perf_counter() - t0 > seconds * 20 + 60:
+        if time.perf_counter() - t0 > seconds * drain_factor:
             break                                      # overloaded: stop draining
     wall = time.perf_counter() - t0
     stats = V.vopp_server_get_stats(srv) if srv else {}
@@ -163,10 +191,12 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
         V.vopp_model_destroy(m)
     lat = np.array(lat)
     out = {"mode": mode, "requests": int(n_req), "completed": int(len(lat)), "wall_s": wall,
+           "unfinished": int(n_req - len(lat)),
            "plans_per_s": len(lat) / wall, "particle_steps_per_s": steps_done / wall,
            "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
            "deadline_misses": int(np.sum(lat > deadline_s)), "belief_updates": updates,
+           "episodes_restarted": resets,
            "offered_rate": rate, "agents": n_agents, "seconds": seconds}
     if stats:
         out["batches"] = int(stats["batches"])

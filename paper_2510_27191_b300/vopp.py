@@ -122,6 +122,9 @@ def _load():
         "vopp_poll": ([vp, u64, ctypes.POINTER(vopp_plan_result), dp], ctypes.c_int),
         "vopp_wait": ([vp, u64, ctypes.c_double, ctypes.POINTER(vopp_plan_result), dp], ctypes.c_int),
         "vopp_server_get_stats": ([vp, ctypes.POINTER(vopp_server_stats)], ctypes.c_int),
+        "vopp_server_set_paused": ([vp, ctypes.c_int], ctypes.c_int),
+        "vopp_wait_any": ([vp, ctypes.c_double, ctypes.POINTER(u64), ctypes.POINTER(vopp_plan_result),
+                           dp], ctypes.c_int),
         "vopp_last_error": ([], ctypes.c_char_p),
         "vopp_version": ([], ctypes.c_char_p),
     }
@@ -279,7 +282,8 @@ def vopp_agent_create(model: int, states, weights, n: int, seed: int) -> int:
 
 def make_params(depth: int, width: int, eta: float, gamma: float, seed: int, pi_bar=None):
     p = vopp_plan_params()
-    p.depth, p.width, p.eta, p.gamma, p.seed = depth, width, eta, gamma, seed & 0xFFFFFFFFFFFFFFFF
+    p.depth, p.width, p.eta, p.gamma = int(depth), int(width), float(eta), float(gamma)
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     keep = None
     if pi_bar is not None:
         keep = (ctypes.c_float * len(pi_bar))(*[float(v) for v in pi_bar])
@@ -424,4 +428,20 @@ def vopp_server_get_stats(srv: int) -> dict:
     st = vopp_server_stats()
     check(lib.vopp_server_get_stats(srv, ctypes.byref(st)))
     return {n: getattr(st, n) for n, _ in vopp_server_stats._fields_}
+
+
+def vopp_wait_any(srv: int, timeout_s: float = 0.0):
+    """(ticket, status, result-or-None, latency) of the next finished plan, or None when none
+    finished within timeout_s."""
+    t = ctypes.c_uint64()
+    r = vopp_plan_result()
+    lat = ctypes.c_double()
+    rc = lib.vopp_wait_any(srv, timeout_s, ctypes.byref(t), ctypes.byref(r), ctypes.byref(lat))
+    if rc == VOPP_E_TIMEOUT:
+        return None
+    return t.value, rc, (_result_dict(r, VOPP_MAX_ACTIONS) if rc == VOPP_OK else None), lat.value
+
+
+def vopp_server_set_paused(srv: int, paused: bool) -> None:
+    check(lib.vopp_server_set_paused(srv, int(paused)))
 

@@ -28,6 +28,7 @@ def test_served_results_equal_alone_results():
     try:
         specs = WL.draw_mixed_plans(48, 11, 1 << 22)
         agents, tickets, inputs = [], [], []
+        V.vopp_server_set_paused(srv, True)      # queue the whole burst, then release it
         for i, ps in enumerate(specs):
             sp = Spec.from_plan(ps)
             st = sp.states()
@@ -40,11 +41,12 @@ def test_served_results_equal_alone_results():
                                   ps.gamma, ps.seed)
             tickets.append(t)
             inputs.append((ps, st))
+        V.vopp_server_set_paused(srv, False)
         served = [V.vopp_wait(srv, t, {WL.NAV2D: 4, WL.GRID: 13}[ps.kind], 20.0)
                   for t, (ps, _) in zip(tickets, inputs)]
         stats = V.vopp_server_get_stats(srv)
         assert stats["completed"] == 48 and stats["rejected"] == 0
-        assert stats["batches"] < 48          # requests were batched
+        assert stats["batches"] <= 4 and stats["max_batch_seen"] == 16   # batches of <= 16
         for (res, lat), (ps, st) in zip(served, inputs):
             alone = V.vopp_plan(models[ps.kind], st, None, ps.N, ps.D, ps.W, ps.eta, ps.gamma,
                                 None, ps.seed)
