@@ -165,15 +165,14 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
  *                            from level D-2; 0: level D-1 is materialised in HBM first
  *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 128)
  *   VOPP_OPT_GRID_CAP        maximum CTAs of an expansion / leaf launch (grid-stride beyond)
- *   VOPP_OPT_TAIL_MAX_NODES  levels with at most this many nodes are backed up by the
- *                            single-CTA tail kernel (default 2048)
  * Results do not depend on any option. */
 #define VOPP_OPT_LEAF_GEN 1
 #define VOPP_OPT_LEAF_THREADS 2
 #define VOPP_OPT_GRID_CAP 3
-#define VOPP_OPT_TAIL_MAX_NODES 4
 #define VOPP_OPT_PERSISTENT 5   /* 1: leaf CTAs fill every SM once and pull work items from a
                                    counter (largest items first); 0 (default): one CTA per item */
+#define VOPP_OPT_FP64_ROOT 6    /* 1: back the root up in FP64 (VOPP_FLAG_FP64_ROOT); 0 (default):
+                                   FP32 with compensated sums, within the 1e-4 tolerance */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);

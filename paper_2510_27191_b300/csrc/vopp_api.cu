@@ -59,8 +59,8 @@ unsigned long long ipow(unsigned long long b, int e) {
   return r;
 }
 
-const char *kFamilies[] = {"root_prep", "expand", "leaf", "backup", "backup_tail", "belief"};
-enum { F_ROOT = 0, F_EXPAND, F_LEAF, F_BACKUP, F_TAIL, F_BELIEF, F_COUNT };
+const char *kFamilies[] = {"root_prep", "expand", "leaf", "belief"};
+enum { F_ROOT = 0, F_EXPAND, F_LEAF, F_BELIEF, F_COUNT };
 
 struct TimedLaunch {
   int family;
@@ -93,12 +93,12 @@ struct vopp_ctx {
   size_t arena_cap = 0;
   Slot slot;                     // the synchronous path's slot (stream = ctx stream)
   int leaf_persistent = 0;       // persistent leaf CTAs pulling work from a counter
+  int fp64_root = 0;             // root backup in FP64
   int sm_count = 148;
   int tree_detail = VOPP_TREE_MINIMAL;
   int leaf_gen = 1;              // generate level D-1 inside the leaf kernel
   int leaf_threads = 128;
   int grid_cap = 1 << 30;
-  int tail_max_nodes = 2048;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -147,7 +147,7 @@ struct PlanLayout {
   size_t bytes = 0;
   size_t px[kMaxDepth], py[kMaxDepth], plw[kMaxDepth], ps[kMaxDepth];
   size_t rbar[kMaxDepth + 1], lom[kMaxDepth + 1], V[kMaxDepth + 1], Q[kMaxDepth],
-      mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1];
+      mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1], cnt[kMaxDepth];
 };
 
 constexpr size_t kNone = ~(size_t)0;
@@ -170,7 +170,7 @@ PlanShape make_shape(const vopp_model *m, int N, int D, int W, const vopp_ctx *c
 
 PlanLayout make_layout(const PlanShape &s) {
   PlanLayout L;
-  for (int i = 0; i < kMaxDepth; ++i) L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = kNone;
+  for (int i = 0; i < kMaxDepth; ++i) L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = L.cnt[i] = kNone;
   for (int i = 0; i <= kMaxDepth; ++i) L.rbar[i] = L.lom[i] = L.V[i] = L.rep[i] = L.obs[i] = kNone;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -187,6 +187,7 @@ PlanLayout make_layout(const PlanShape &s) {
     if (keep) L.V[l] = take(4 * nodes);
     if (node_level) L.Q[l] = take(4 * nodes * s.A);
     if (node_level && s.pi_mode == kPiNavDist) L.mu[l] = take(8 * nodes);
+    if (l <= s.D - 2) L.cnt[l] = take(4 * nodes);
     if (l >= 1 && keep) { L.rbar[l] = take(4 * nodes); L.lom[l] = take(4 * nodes); }
     if (l >= 1 && keep && s.keep_debug) { L.rep[l] = take(4 * nodes); L.obs[l] = take(8 * nodes); }
   }
@@ -434,49 +435,6 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       if (acc) stages.push_back(s);
     }
   }
-  std::vector<int> tail_top(n, -1);
-  for (int i = 0; i < n; ++i) {
-    const auto &sh = jobs[i].shape;
-    int top = -1;
-    for (int l = sh.D - 2; l >= 1; --l)
-      if ((long long)ipow(sh.AW, l) <= c->tail_max_nodes) { top = l; break; }
-    tail_top[i] = top;
-  }
-  for (int l = maxD - 2; l >= 1; --l) {
-    StageBuild s;
-    s.family = F_BACKUP;
-    s.level = l;
-    long long acc = 0;
-    for (int i = 0; i < n; ++i) {
-      const auto &sh = jobs[i].shape;
-      if (l <= sh.D - 2 && l > tail_top[i]) {
-        s.plans.push_back(i);
-        s.levels.push_back(l);
-        s.prefix.push_back(acc);
-        acc += nodes(jobs[i], l);
-      }
-    }
-    s.prefix.push_back(acc);
-    s.total = acc;
-    if (acc) stages.push_back(s);
-  }
-  {
-    StageBuild s;
-    s.family = F_TAIL;
-    s.level = 0;
-    long long acc = 0;
-    for (int i = 0; i < n; ++i) {
-      if (jobs[i].shape.D >= 1) {
-        s.plans.push_back(i);
-        s.levels.push_back(tail_top[i] < 0 ? 0 : tail_top[i]);
-        s.prefix.push_back(acc++);
-      }
-    }
-    s.prefix.push_back(acc);
-    s.total = acc;
-    if (acc) stages.push_back(s);
-  }
-
   // metadata block: [results n][descs n][stage tables][root copies]
   size_t off = 0;
   const size_t off_res = off; off = align_up(off + sizeof(DevResult) * n, 256);
@@ -519,6 +477,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     P.pi_mode = sh.pi_mode;
     P.h_zero = j.model->desc.h_zero;
     P.leaf_gen = sh.leaf_gen; P.keep_leaf = sh.keep_leaf; P.keep_debug = sh.keep_debug;
+    P.fp64_root = c->fp64_root;
     P.eta = j.p.eta; P.inv_eta = 1.0f / j.p.eta; P.gamma = j.p.gamma;
     P.pi_temp = j.model->desc.pi_temp;
     // reference policy (uniform / fixed / caller override), normalised in double
@@ -547,6 +506,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     for (int l = 0; l < kMaxDepth; ++l) {
       P.px[l] = fp(L.px[l]); P.py[l] = fp(L.py[l]); P.plw[l] = fp(L.plw[l]); P.ps[l] = ip(L.ps[l]);
       P.Q[l] = fp(L.Q[l]); P.mu[l] = fp(L.mu[l]);
+      P.cnt[l] = L.cnt[l] == kNone ? nullptr : reinterpret_cast<unsigned int *>(base + L.cnt[l]);
     }
     for (int l = 0; l <= kMaxDepth; ++l) {
       P.rbar[l] = fp(L.rbar[l]); P.lom[l] = fp(L.lom[l]); P.V[l] = fp(L.V[l]);
@@ -625,8 +585,6 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
         e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads,
                         c->leaf_persistent ? persistent_grid(c, sb.smem) : c->grid_cap, stream);
         break;
-      case F_BACKUP: e = launch_backup(dd, sb.st, sb.total, stream); break;
-      case F_TAIL: e = launch_backup_tail(dd, sb.st, stream); break;
     }
     if (timed) timed_end(c, tl);
     if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -799,10 +757,7 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       c->grid_cap = (int)std::min<int64_t>(value, 1 << 30);
       return VOPP_OK;
     case VOPP_OPT_PERSISTENT: c->leaf_persistent = value ? 1 : 0; return VOPP_OK;
-    case VOPP_OPT_TAIL_MAX_NODES:
-      if (value < 1) return fail(VOPP_E_INVALID, "tail max nodes");
-      c->tail_max_nodes = (int)std::min<int64_t>(value, 1 << 20);
-      return VOPP_OK;
+    case VOPP_OPT_FP64_ROOT: c->fp64_root = value ? 1 : 0; return VOPP_OK;
     default: return fail(VOPP_E_INVALID, "unknown option %d", option);
   }
 }

@@ -61,6 +61,7 @@ struct PlanDesc {
   int leaf_gen;               // 1: level D-1 particles are generated in the leaf kernel
   int keep_leaf;              // store branch stats at level D
   int keep_debug;             // store representatives / observations
+  int fp64_root;              // back the root up in FP64 (else FP32, compensated)
   float eta, inv_eta, gamma, pi_temp;
   float log_pi[kMaxActions];  // uniform / fixed reference policy
   float h_a0, h_b0, log2_gamma;  // NAV2D heuristic: h = a0 + b0 gamma^(m-1)
@@ -80,6 +81,7 @@ struct PlanDesc {
   float *mu[kMaxDepth];       // weighted mean particle (x,y) per node, kPiNavDist only
   int *rep[kMaxDepth + 1];
   float *obs[kMaxDepth + 1];  // 2 floats per child
+  unsigned int *cnt[kMaxDepth];  // per node of levels 0..D-2: children finished (backup climb)
   DevResult *result;
 };
 
@@ -152,11 +154,23 @@ __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, ui
                 k0, k1);
 }
 
+// Two-wide FP32 arithmetic (Blackwell packed f32x2 FMA / ADD / MUL on float2), used to run
+// the two particles of a Philox pair through the same instruction.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).  Built from the float
 // 1 + (x >> 9) 2^-23 in [1, 2) minus (1 - 2^-24); the difference is representable, so the
 // subtraction is exact.
 __device__ __forceinline__ float u01(uint32_t x) {
-  return __uint_as_float((x >> 9) | 0x3F800000u) - 0.999999940395355225f;
+  return __fadd_rn(__uint_as_float((x >> 9) | 0x3F800000u), -0.999999940395355225f);
+}
+__device__ __forceinline__ float2 u01_2(uint32_t a, uint32_t b) {
+  return add2(make_float2(__uint_as_float((a >> 9) | 0x3F800000u),
+                          __uint_as_float((b >> 9) | 0x3F800000u)),
+              bc2(-0.999999940395355225f));
 }
 
 // Hardware base-2 exponential / logarithm (PTX ex2.approx / lg2.approx, flush-to-zero):
@@ -174,31 +188,46 @@ __device__ __forceinline__ float lg2(float x) {
 constexpr float kLog2e = 1.44269504088896341f;
 constexpr float kLn2 = 0.693147180559945309f;
 
-// -ln(u) for u in (0, 1).  Where -ln u > 2^-8 the hardware base-2 logarithm (absolute
+
+// -2 ln(u) for u in (0, 1).  Where -ln u > 2^-8 the hardware base-2 logarithm (absolute
 // error ~2^-22) gives a relative error below 5e-5 that shrinks as u moves away from 1;
-// for u > 1 - 2^-8 the Taylor series -ln(1 - v) = v + v^2/2 + v^3/3 + v^4/4 (v = 1 - u,
-// exact) truncates below v^4 / 5 < 1e-10 relative.
-__device__ __forceinline__ float neg_log_u(float u) {
-  const float v = 1.0f - u;
-  float ser = fmaf(v, 0.25f, 0.33333334f);
-  ser = fmaf(v, ser, 0.5f);
+// for u > 1 - 2^-8 the Taylor series -2 ln(1 - v) = 2 (v + v^2/2 + v^3/3 + v^4/4)
+// (v = 1 - u, exact) truncates below v^4 / 5 < 1e-10 relative.
+__device__ __forceinline__ float neg2_log_u(float u) {
+  const float v = fmaf(u, -1.0f, 1.0f);
+  float ser = fmaf(v, 0.5f, 0.666666687f);
   ser = fmaf(v, ser, 1.0f);
-  ser *= v;
-  const float hw = -kLn2 * lg2(u);
+  ser = fmaf(v, ser, 2.0f);
+  ser = __fmul_rn(ser, v);
+  const float hw = __fmul_rn(-1.38629436f, lg2(u));
   return (v < 0.00390625f) ? ser : hw;
+}
+__device__ __forceinline__ float2 neg2_log_u2(float2 u) {
+  const float2 v = fma2(u, bc2(-1.0f), bc2(1.0f));
+  float2 ser = fma2(v, bc2(0.5f), bc2(0.666666687f));
+  ser = fma2(v, ser, bc2(1.0f));
+  ser = fma2(v, ser, bc2(2.0f));
+  ser = mul2(ser, v);
+  const float2 hw = mul2(bc2(-1.38629436f), make_float2(lg2(u.x), lg2(u.y)));
+  return make_float2((v.x < 0.00390625f) ? ser.x : hw.x, (v.y < 0.00390625f) ? ser.y : hw.y);
 }
 
 // Box-Muller: (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  The angle is taken as
-// t = 2 pi (u2 - 1/2) in (-pi, pi), where the hardware sine / cosine are accurate, and
-// cos(2 pi u2) = -cos t, sin(2 pi u2) = -sin t.
-__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+// t = 2 pi u2 - pi in (-pi, pi), where the hardware sine / cosine are accurate, and
+// cos(2 pi u2) = -cos t, sin(2 pi u2) = -sin t; the returned pair is (-g1, -g2)'s negation
+// folded in: the caller gets r cos t and r sin t and subtracts.
+__device__ __forceinline__ float2 box_muller_neg(uint32_t a, uint32_t b) {
   const float u1 = u01(a), u2 = u01(b);
-  const float s = 2.0f * neg_log_u(u1);
-  const float r = s * rsqrtf(s);
-  const float t = 6.28318531f * (u2 - 0.5f);
+  const float s = neg2_log_u(u1);
+  const float r = __fmul_rn(s, rsqrtf(s));
+  const float t = fmaf(6.28318531f, u2, -3.14159265f);
   float sn, cs;
   __sincosf(t, &sn, &cs);
-  return make_float2(-r * cs, -r * sn);
+  return make_float2(__fmul_rn(r, cs), __fmul_rn(r, sn));   // = (-g1, -g2)
+}
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  const float2 n = box_muller_neg(a, b);
+  return make_float2(-n.x, -n.y);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -305,11 +334,12 @@ __device__ __forceinline__ float block_max(float v, float *red) {
 // ---------------------------------------------------------------------------------------
 struct NavModel {
   static constexpr bool kStochastic = true;
+  static constexpr bool kPairPacked = true;
   struct S { float x, y; };
   struct O { float x, y; };
 
   __device__ __forceinline__ static bool terminal(const S &s) {
-    return s.x * s.x + s.y * s.y <= 0.25f;
+    return fmaf(s.x, s.x, __fmul_rn(s.y, s.y)) <= 0.25f;
   }
   __device__ __forceinline__ static float dx_of(int a) { return (a == 0) ? 1.0f : ((a == 1) ? -1.0f : 0.0f); }
   __device__ __forceinline__ static float dy_of(int a) { return (a == 2) ? 1.0f : ((a == 3) ? -1.0f : 0.0f); }
@@ -317,21 +347,68 @@ struct NavModel {
   // -1 otherwise; terminal states stay put with reward 0.
   __device__ __forceinline__ static float step(S &s, int a, uint32_t wa, uint32_t wb,
                                                const DevModel &) {
-    const bool term = terminal(s);
-    const float2 g = box_muller(wa, wb);
-    const float nx = fminf(fmaxf(fmaf(0.1f, g.x, s.x + dx_of(a)), 0.0f), 10.0f);
-    const float ny = fminf(fmaxf(fmaf(0.1f, g.y, s.y + dy_of(a)), 0.0f), 10.0f);
-    const float r = (nx * nx + ny * ny <= 0.25f) ? 100.0f : -1.0f;
+    const bool term = fmaf(s.x, s.x, __fmul_rn(s.y, s.y)) <= 0.25f;
+    const float2 ng = box_muller_neg(wa, wb);
+    const float nx = fminf(fmaxf(fmaf(-0.1f, ng.x, __fadd_rn(s.x, dx_of(a))), 0.0f), 10.0f);
+    const float ny = fminf(fmaxf(fmaf(-0.1f, ng.y, __fadd_rn(s.y, dy_of(a))), 0.0f), 10.0f);
+    const float r = (fmaf(nx, nx, __fmul_rn(ny, ny)) <= 0.25f) ? 100.0f : -1.0f;
     s.x = term ? s.x : nx;
     s.y = term ? s.y : ny;
     return term ? 0.0f : r;
   }
-  __device__ __forceinline__ static float sigma(float x) { return fmaf(0.5f, fabsf(x - 9.0f), 0.05f); }
+  // The two particles of a Philox pair (x = (x0, x1), y = (y0, y1), words w) stepped with
+  // two-wide arithmetic; same operation sequence as step().  Returns the rewards; terminal
+  // flags of the new states in t0 / t1.
+  __device__ __forceinline__ static float2 step_pair(float2 &x, float2 &y, float dx, float dy,
+                                                     uint4 w, bool &t0, bool &t1) {
+    const float2 rr = fma2(x, x, mul2(y, y));
+    const bool p0 = rr.x <= 0.25f, p1 = rr.y <= 0.25f;
+    const float2 u1 = u01_2(w.x, w.z), u2 = u01_2(w.y, w.w);
+    const float2 sq = neg2_log_u2(u1);
+    const float2 r = mul2(sq, make_float2(rsqrtf(sq.x), rsqrtf(sq.y)));
+    const float2 t = fma2(bc2(6.28318531f), u2, bc2(-3.14159265f));
+    float s0, c0, s1, c1;
+    __sincosf(t.x, &s0, &c0);
+    __sincosf(t.y, &s1, &c1);
+    float2 nx = fma2(bc2(-0.1f), mul2(r, make_float2(c0, c1)), add2(x, bc2(dx)));
+    float2 ny = fma2(bc2(-0.1f), mul2(r, make_float2(s0, s1)), add2(y, bc2(dy)));
+    nx = make_float2(fminf(fmaxf(nx.x, 0.0f), 10.0f), fminf(fmaxf(nx.y, 0.0f), 10.0f));
+    ny = make_float2(fminf(fmaxf(ny.x, 0.0f), 10.0f), fminf(fmaxf(ny.y, 0.0f), 10.0f));
+    const float2 r2 = fma2(nx, nx, mul2(ny, ny));
+    const bool g0 = r2.x <= 0.25f, g1 = r2.y <= 0.25f;
+    x = make_float2(p0 ? x.x : nx.x, p1 ? x.y : nx.y);
+    y = make_float2(p0 ? y.x : ny.x, p1 ? y.y : ny.y);
+    t0 = p0 || g0;
+    t1 = p1 || g1;
+    return make_float2(p0 ? 0.0f : (g0 ? 100.0f : -1.0f), p1 ? 0.0f : (g1 ? 100.0f : -1.0f));
+  }
+  __device__ __forceinline__ static float sigma(float x) {
+    return fmaf(0.5f, fabsf(__fadd_rn(x, -9.0f)), 0.05f);
+  }
   __device__ __forceinline__ static O draw_obs(const S &s, int, uint32_t w0, uint32_t w1,
                                                const DevModel &) {
     const float2 g = box_muller(w0, w1);
     const float sg = sigma(s.x);
     return O{fmaf(sg, g.x, s.x), fmaf(sg, g.y, s.y)};
+  }
+  // Base-2 log-likelihoods of observation o for the two particles of a pair.
+  __device__ __forceinline__ static float2 loglik2_pair(float2 x, float2 y, const O &o) {
+    const float2 dm = add2(x, bc2(-9.0f));
+    const float2 sg = fma2(bc2(0.5f), make_float2(fabsf(dm.x), fabsf(dm.y)), bc2(0.05f));
+    const float2 inv = make_float2(__fdividef(1.0f, sg.x), __fdividef(1.0f, sg.y));
+    const float2 ex = fma2(x, bc2(-1.0f), bc2(o.x)), ey = fma2(y, bc2(-1.0f), bc2(o.y));
+    const float2 d2 = fma2(ex, ex, mul2(ey, ey));
+    return fma2(mul2(bc2(-0.721347520f), d2), mul2(inv, inv),
+                fma2(bc2(-2.0f), make_float2(lg2(sg.x), lg2(sg.y)), bc2(-2.65149613f)));
+  }
+  // Heuristic of the pair; t0 / t1 are the terminal flags of the states.
+  __device__ __forceinline__ static float2 heuristic_pair(float2 x, float2 y, bool t0, bool t1,
+                                                          float log2g, float a0, float b0, bool hz) {
+    float2 m = add2(add2(x, y), bc2(-0.5f));
+    m = make_float2(fmaxf(m.x, 1.0f), fmaxf(m.y, 1.0f));
+    const float2 e = fma2(m, bc2(log2g), bc2(-log2g));
+    const float2 h = fma2(bc2(b0), make_float2(ex2(e.x), ex2(e.y)), bc2(a0));
+    return make_float2((hz || t0) ? 0.0f : h.x, (hz || t1) ? 0.0f : h.y);
   }
   __device__ __forceinline__ static O enum_obs(int k) { return O{(float)k, 0.f}; }
   // log2 N(o; s', sigma(x')^2 I) = log2 e (-|o - s'|^2 / (2 sigma^2)) - 2 log2 sigma
@@ -339,9 +416,9 @@ struct NavModel {
   __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &) {
     const float sg = sigma(s.x);
     const float inv = __fdividef(1.0f, sg);
-    const float dx = o.x - s.x, dy = o.y - s.y;
-    const float d2 = fmaf(dx, dx, dy * dy);
-    return fmaf(-0.721347520f * d2, inv * inv, fmaf(-2.0f, lg2(sg), -2.65149613f));
+    const float ex = fmaf(s.x, -1.0f, o.x), ey = fmaf(s.y, -1.0f, o.y);
+    const float d2 = fmaf(ex, ex, __fmul_rn(ey, ey));
+    return fmaf(__fmul_rn(-0.721347520f, d2), __fmul_rn(inv, inv), fmaf(-2.0f, lg2(sg), -2.65149613f));
   }
   __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
     return kLn2 * loglik2(s, a, o, m);
@@ -350,8 +427,8 @@ struct NavModel {
   // the heuristic is forced to zero, 1 otherwise.
   __device__ __forceinline__ static float heuristic(const S &s, float log2g, float a0, float b0,
                                                     bool hz) {
-    const float m = fmaxf(s.x + s.y - 0.5f, 1.0f);
-    const float h = fmaf(b0, ex2((m - 1.0f) * log2g), a0);
+    const float m = fmaxf(__fadd_rn(__fadd_rn(s.x, s.y), -0.5f), 1.0f);
+    const float h = fmaf(b0, ex2(fmaf(m, log2g, -log2g)), a0);
     return (hz || terminal(s)) ? 0.0f : h;
   }
   __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
@@ -369,6 +446,7 @@ __device__ __forceinline__ int gpack(int rocks, int x, int y, int t) {
 
 struct GridModel {
   static constexpr bool kStochastic = false;
+  static constexpr bool kPairPacked = false;
   struct S { int s; };
   struct O { int o; };
 
@@ -437,6 +515,7 @@ struct GridModel {
 
 struct ToyModel {
   static constexpr bool kStochastic = false;
+  static constexpr bool kPairPacked = false;
   struct S { int s; };
   struct O { int o; };
 

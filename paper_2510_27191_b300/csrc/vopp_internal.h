@@ -41,9 +41,6 @@ cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long tot
 cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
                         int threads, int grid_cap, cudaStream_t s);
 cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_backup(const PlanDesc *d, const StageTable &st, long long total_nodes,
-                          cudaStream_t s);
-cudaError_t launch_backup_tail(const PlanDesc *d, const StageTable &st, cudaStream_t s);
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
 
 }  // namespace vopp

@@ -8,8 +8,8 @@
 //   k_leaf        per level-(D-1) node: build its particle set in shared memory (or load
 //                 it), expand all A*W leaf children without writing particles (weighted
 //                 heuristic mean, branch weights, mean reward), then back the node up
-//   k_backup      Q and V of every node of one level from its children's branch stats
-//   k_backup_tail remaining small levels in one CTA per plan, root level in FP64, action
+//                 and climb: the last child of each parent to finish backs the parent up,
+//                 up to the FP64 root and the action choice (no separate backup launches)
 //   k_belief      SIR belief update tau(b, a, o) of one agent (Sec. III-B)
 //
 // No tensor cores: nothing here is a dense contraction.  The leaf kernel is bound by FP32
@@ -84,6 +84,7 @@ template <> struct SNode<NavModel> {
     s0 = NavModel::S{a.x, a.z};
     s1 = NavModel::S{a.y, a.w};
   }
+  __device__ __forceinline__ float4 A_f4(int p) const { return A[p]; }
   __device__ __forceinline__ float lw(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[i & 1]; }
   __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
   __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
@@ -139,6 +140,10 @@ template <class M> struct ScratchInNode {   // K3: the destination node's lw / w
   __device__ __forceinline__ float getE(int i) const { return n.w(i); }
   __device__ __forceinline__ void setE(int i, float v) const { n.set_w(i, v); }
 };
+
+// The observation of a pair-packed (NAV2D) branch; other models never take that path.
+template <class Obs> __device__ __forceinline__ NavModel::O o_nav(const Obs &) { return NavModel::O{0.f, 0.f}; }
+template <> __device__ __forceinline__ NavModel::O o_nav<NavModel::O>(const NavModel::O &o) { return o; }
 
 template <class M> __device__ __forceinline__ float2 state_xy(const typename M::S &s);
 template <> __device__ __forceinline__ float2 state_xy<NavModel>(const NavModel::S &s) {
@@ -305,6 +310,7 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   }
   const int cl = l + 1;
   if (threadIdx.x == 0) {
+    if (cl <= P.D - 2) P.cnt[cl][child] = 0u;   // completion counter of the new node
     P.rbar[cl][child] = rbar;
     P.lom[cl][child] = lom;
     float2 mu = make_float2(0.f, 0.f);
@@ -325,27 +331,37 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
 }
 
 // ---------------------------------------------------------------------------------------
-// Backup of one node (Alg. 3 lines computing R, W, Q, then Eq. 1 value) from branch stats
-// held in arrays indexed by slot a*W + k.  Executed by the lanes of one warp (a = lane).
+// Backup of one node (Alg. 3: mean reward R, weighted child value W, Q = R + gamma W, then
+// the Eq. 1 value over actions) from branch stats held in arrays indexed by slot a*W + k.
+// Executed by the lanes of one warp (lane = action).  kL2: the arrays are in global memory
+// and written by other CTAs of the running kernel, so they are read through L2 (L1 is not
+// coherent across SMs).  Returns V to every lane; lane a's Q in q_lane.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void node_backup_warp(const PlanDesc &P, const float *rb,
-                                                 const float *lo, const float *vc, float2 mu,
-                                                 float *q_out, float *v_out) {
+template <bool kL2>
+__device__ __forceinline__ float ld_stat(const float *p) {
+  if constexpr (kL2) return __ldcg(p);
+  else return *p;
+}
+
+template <bool kL2>
+__device__ __forceinline__ float node_backup_warp(const PlanDesc &P, const float *rb,
+                                                  const float *lo, const float *vc, float2 mu,
+                                                  float &q_lane) {
   const int lane = threadIdx.x & 31, A = P.A, W = P.W;
   float q = 0.f, z = -CUDART_INF_F;
   if (lane < A) {
     float rs = 0.f, M = -CUDART_INF_F;
     for (int k = 0; k < W; ++k) {
-      rs += rb[lane * W + k];
-      M = fmaxf(M, lo[lane * W + k]);
+      rs += ld_stat<kL2>(rb + lane * W + k);
+      M = fmaxf(M, ld_stat<kL2>(lo + lane * W + k));
     }
     float fut = 0.f;
     if (M > -CUDART_INF_F) {
       Kahan num, den;
       num.init(); den.init();
       for (int k = 0; k < W; ++k) {
-        const float om = __expf(lo[lane * W + k] - M);
-        num.add(om * vc[lane * W + k]);
+        const float om = __expf(ld_stat<kL2>(lo + lane * W + k) - M);
+        num.add(om * ld_stat<kL2>(vc + lane * W + k));
         den.add(om);
       }
       fut = num.value() / den.value();
@@ -354,12 +370,130 @@ __device__ __forceinline__ void node_backup_warp(const PlanDesc &P, const float 
     }
     q = rs / (float)W + P.gamma * fut;
     z = log_pibar(P, mu, lane) + q * P.inv_eta;
-    q_out[lane] = q;
   }
+  q_lane = q;
   const float zm = warp_max(z);
   float e = (lane < A && z > -CUDART_INF_F) ? __expf(z - zm) : 0.f;
   e = warp_sum(e);
-  if (lane == 0) *v_out = P.eta * (zm + logf(e));
+  return P.eta * (zm + __logf(e));
+}
+
+// Root backup from the level-1 branch stats and the Alg. 1 action choice (argmax of
+// Q + eta log pibar, lowest index on ties), in FP32 with compensated sums; the FP64 variant
+// below runs instead when the plan asks for it.  One warp.
+__device__ void root_backup_warp_fp64(const PlanDesc &P);
+__device__ void root_backup_warp(const PlanDesc &P) {
+  if (P.fp64_root) { root_backup_warp_fp64(P); return; }
+  const int lane = threadIdx.x & 31, A = P.A;
+  float2 mu = make_float2(0.f, 0.f);
+  if (P.pi_mode == kPiNavDist) mu = make_float2(__ldcg(P.mu[0]), __ldcg(P.mu[0] + 1));
+  float q;
+  const float v = node_backup_warp<true>(P, P.rbar[1], P.lom[1], P.V[1], mu, q);
+  const float lp = (lane < A) ? log_pibar(P, mu, lane) : -CUDART_INF_F;
+  float sc = (lane < A) ? q + P.eta * lp : -CUDART_INF_F;
+  int best = (lane < A) ? lane : 1 << 30;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
+    const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
+    if (sc2 > sc || (sc2 == sc && b2 < best)) { sc = sc2; best = b2; }
+  }
+  DevResult *R = P.result;
+  if (lane < A) {
+    R->q[lane] = q;
+    R->policy[lane] = __expf(lp + (q - v) * P.inv_eta);
+    P.Q[0][lane] = q;
+  }
+  if (lane == 0) {
+    R->v_root = v;
+    R->action = best;
+    P.V[0][0] = v;
+  }
+}
+
+__device__ void root_backup_warp_fp64(const PlanDesc &P) {
+  const int lane = threadIdx.x & 31, A = P.A, W = P.W;
+  double q = 0.0, z = -CUDART_INF;
+  float2 mu = make_float2(0.f, 0.f);
+  if (P.pi_mode == kPiNavDist) mu = make_float2(__ldcg(P.mu[0]), __ldcg(P.mu[0] + 1));
+  double lp = -CUDART_INF;
+  if (lane < A) {
+    double rs = 0.0;
+    float M = -CUDART_INF_F;
+    for (int k = 0; k < W; ++k) {
+      rs += (double)__ldcg(P.rbar[1] + lane * W + k);
+      M = fmaxf(M, __ldcg(P.lom[1] + lane * W + k));
+    }
+    double fut = 0.0;
+    if (M > -CUDART_INF_F) {
+      double num = 0.0, den = 0.0;
+      for (int k = 0; k < W; ++k) {
+        const double om = exp((double)__ldcg(P.lom[1] + lane * W + k) - (double)M);
+        num += om * (double)__ldcg(P.V[1] + lane * W + k);
+        den += om;
+      }
+      fut = num / den;
+    } else {
+      atomicAdd(&P.result->degenerate, 1u);
+    }
+    q = rs / (double)W + (double)P.gamma * fut;
+    lp = (double)log_pibar(P, mu, lane);
+    z = lp + q / (double)P.eta;
+  }
+  double zm = z;
+  for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+  double e = (lane < A && z > -CUDART_INF) ? exp(z - zm) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  const double v = (double)P.eta * (zm + log(e));
+  double sc = (lane < A) ? q + (double)P.eta * lp : -CUDART_INF;
+  int best = (lane < A) ? lane : 1 << 30;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
+    const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
+    if (sc2 > sc || (sc2 == sc && b2 < best)) { sc = sc2; best = b2; }
+  }
+  DevResult *R = P.result;
+  if (lane < A) {
+    R->q[lane] = q;
+    R->policy[lane] = exp(lp + (q - v) / (double)P.eta);
+    P.Q[0][lane] = (float)q;
+  }
+  if (lane == 0) {
+    R->v_root = v;
+    R->action = best;
+    R->flags |= 2u;
+    P.V[0][0] = (float)v;
+  }
+}
+
+// After node `node` of level l has its Q and V written: the warp signals the parent, and if
+// it is the last of the parent's A*W children to finish, backs the parent up and climbs on.
+// The CTA that finishes last overall backs up the root.  Every climb step fences its writes
+// before signalling and after learning it is the last, so the siblings' results are visible.
+__device__ void climb_warp(const PlanDesc &P, int l, unsigned long long node) {
+  const int lane = threadIdx.x & 31, A = P.A;
+  const unsigned long long AW = (unsigned long long)P.AW;
+  unsigned long long n = node;
+  for (int lev = l; lev > 0; --lev) {
+    __threadfence();
+    const unsigned long long p = n / AW;
+    unsigned int old = 0;
+    if (lane == 0) old = atomicAdd(P.cnt[lev - 1] + p, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != (unsigned int)(AW - 1)) return;
+    __threadfence();
+    if (lev - 1 == 0) {
+      root_backup_warp(P);
+      return;
+    }
+    const unsigned long long c0 = p * AW;
+    float2 mu = make_float2(0.f, 0.f);
+    if (P.pi_mode == kPiNavDist) mu = make_float2(__ldcg(P.mu[lev - 1] + 2 * p), __ldcg(P.mu[lev - 1] + 2 * p + 1));
+    float q;
+    const float v = node_backup_warp<true>(P, P.rbar[lev] + c0, P.lom[lev] + c0, P.V[lev] + c0, mu, q);
+    if (lane < A) P.Q[lev - 1][p * A + lane] = q;
+    if (lane == 0) P.V[lev - 1][p] = v;
+    n = p;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -413,6 +547,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
   const float mx = block_sum(MX.value(), red), my = block_sum(MY.value(), red);
   const float hv = block_sum(H.value(), red);
   if (threadIdx.x == 0) {
+    if (P.D >= 2) P.cnt[0][0] = 0u;
     if (P.mu[0]) { P.mu[0][0] = mx; P.mu[0][1] = my; }
     if (P.D == 0) {
       // depth 0: V = weighted mean heuristic, every Q equal to it, action = argmax pibar
@@ -491,7 +626,11 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 #ifndef VOPP_LEAF_MINBLOCKS
 #define VOPP_LEAF_MINBLOCKS 3
 #endif
+#ifndef VOPP_LEAF_CHUNK_PACKED
+#define VOPP_LEAF_CHUNK_PACKED 4
+#endif
 constexpr int kLeafChunk = VOPP_LEAF_CHUNK;
+constexpr int kLeafChunkPacked = VOPP_LEAF_CHUNK_PACKED;   // pairs per rescale, packed path
 
 // Running max-shifted sums in base 2: S = sum 2^(L - m) and H = sum 2^(L - m) h, compensated.
 struct ShiftedSum {
@@ -540,6 +679,63 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   Kahan R;
   R.init();
   const int npairs = (N + 1) >> 1;
+  if constexpr (M::kPairPacked) {
+    // both particles of a pair through one two-wide instruction stream
+    const float dx = NavModel::dx_of(a), dy = NavModel::dy_of(a);
+    for (int base = lane; base < npairs; base += 32 * kLeafChunkPacked) {
+      float2 L[kLeafChunkPacked], E[kLeafChunkPacked], Hh[kLeafChunkPacked];
+      float2 rsum = make_float2(0.f, 0.f);
+      float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F;
+#pragma unroll
+      for (int c = 0; c < kLeafChunkPacked; ++c) {
+        const int p = base + 32 * c;
+        L[c] = E[c] = bc2(-CUDART_INF_F);
+        Hh[c] = bc2(0.f);
+        if (p < npairs) {
+#if VOPP_ROUND_KEYS
+          const uint4 w = philox_rk(make_uint4((uint32_t)p, c1, c2, c3), K);
+#else
+          const uint4 w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+#endif
+          const float4 xy = nb.A_f4(p);            // (x0, x1, y0, y1)
+          const float4 b = nb.B[p];                // (lw2_0, lw2_1, w_0, w_1)
+          float2 X = make_float2(xy.x, xy.y), Y = make_float2(xy.z, xy.w);
+          bool t0, t1;
+          const float2 r = NavModel::step_pair(X, Y, dx, dy, w, t0, t1);
+          const float2 e = NavModel::loglik2_pair(X, Y, o_nav(o));
+          const bool v1 = 2 * p + 1 < N;
+          L[c] = add2(make_float2(b.x, b.y), e);   // the odd-N pad slot has lw2 = -inf
+          E[c] = make_float2(e.x, v1 ? e.y : -CUDART_INF_F);
+          Hh[c] = NavModel::heuristic_pair(X, Y, t0, t1, log2g, h_a0, h_b0, hz);
+          rsum = fma2(make_float2(b.z, b.w), r, rsum);   // pad slot: w = 0
+          cm1 = fmaxf(cm1, fmaxf(L[c].x, L[c].y));
+          cm0 = fmaxf(cm0, fmaxf(E[c].x, E[c].y));
+        }
+      }
+      const float m1 = A1.shift_to(cm1), m0 = A0.shift_to(cm0);
+      float2 s1 = bc2(0.f), h1 = bc2(0.f), s0 = bc2(0.f);
+      if (m1 > -CUDART_INF_F) {
+#pragma unroll
+        for (int c = 0; c < kLeafChunkPacked; ++c) {
+          const float2 d = add2(L[c], bc2(-m1));
+          const float2 x1 = make_float2(ex2(d.x), ex2(d.y));   // L = -inf gives 0
+          s1 = add2(s1, x1);
+          h1 = fma2(x1, Hh[c], h1);
+        }
+      }
+      if (m0 > -CUDART_INF_F) {
+#pragma unroll
+        for (int c = 0; c < kLeafChunkPacked; ++c) {
+          const float2 d = add2(E[c], bc2(-m0));
+          s0 = add2(s0, make_float2(ex2(d.x), ex2(d.y)));
+        }
+      }
+      A1.S.add(s1.x + s1.y);
+      A1.H.add(h1.x + h1.y);
+      A0.S.add(s0.x + s0.y);
+      R.add(rsum.x + rsum.y);
+    }
+  } else {
   for (int base = lane; base < npairs; base += 32 * kLeafChunk) {
     float L[2 * kLeafChunk], E[2 * kLeafChunk], Hh[2 * kLeafChunk];
     float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rsum = 0.f;
@@ -594,6 +790,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
     A1.H.add(h1);
     A0.S.add(s0);
     R.add(rsum);
+  }
   }
   float m1 = A1.m, s1 = A1.S.value(), h1 = A1.H.value();
   float m0 = A0.m, s0 = A0.S.value(), h0 = 0.f;
@@ -666,13 +863,17 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   __syncthreads();
 
   if (wid == 0) {
-    __shared__ float s_q[kMaxActions];
-    __shared__ float s_v;
-    node_backup_warp(P, sm_rb, sm_lo, sm_v, s_mu, s_q, &s_v);
-    __syncwarp();
+    float q;
+    const float v = node_backup_warp<false>(P, sm_rb, sm_lo, sm_v, s_mu, q);
     const int lane = threadIdx.x & 31;
-    if (lane < P.A) P.Q[l][node * P.A + lane] = s_q[lane];
-    if (lane == 0) P.V[l][node] = s_v;
+    if (lane < P.A) P.Q[l][node * P.A + lane] = q;
+    if (lane == 0) P.V[l][node] = v;
+    if (l == 0) {
+      __threadfence_block();
+      root_backup_warp(P);          // depth 1: this node is the root
+    } else {
+      climb_warp(P, l, node);
+    }
   }
   __syncthreads();
 }
@@ -705,138 +906,6 @@ __global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDes
       __syncthreads();
     } else {
       item += gridDim.x;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// K4: backup of one level (16 lanes per node, lane = action), FP32.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void backup_node16(const PlanDesc &P, int l, unsigned long long n,
-                                              int a, bool valid) {
-  const int A = P.A, W = P.W, AW = P.AW;
-  float q = 0.f, z = -CUDART_INF_F;
-  if (valid && a < A) {
-    const unsigned long long c0 = n * (unsigned long long)AW + (unsigned long long)(a * W);
-    const float *rb = P.rbar[l + 1] + c0, *lo = P.lom[l + 1] + c0, *vc = P.V[l + 1] + c0;
-    float rs = 0.f, M = -CUDART_INF_F;
-    for (int k = 0; k < W; ++k) { rs += rb[k]; M = fmaxf(M, lo[k]); }
-    float fut = 0.f;
-    if (M > -CUDART_INF_F) {
-      Kahan num, den;
-      num.init(); den.init();
-      for (int k = 0; k < W; ++k) {
-        const float om = __expf(lo[k] - M);
-        num.add(om * vc[k]);
-        den.add(om);
-      }
-      fut = num.value() / den.value();
-    } else {
-      atomicAdd(&P.result->degenerate, 1u);
-    }
-    q = rs / (float)W + P.gamma * fut;
-    float2 mu = make_float2(0.f, 0.f);
-    if (P.pi_mode == kPiNavDist) mu = make_float2(P.mu[l][2 * n], P.mu[l][2 * n + 1]);
-    z = log_pibar(P, mu, a) + q * P.inv_eta;
-    P.Q[l][n * A + a] = q;
-  }
-  float zm = z;
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o, 16));
-  float e = (valid && a < A && z > -CUDART_INF_F) ? __expf(z - zm) : 0.f;
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
-  if (valid && a == 0) P.V[l][n] = P.eta * (zm + logf(e));
-}
-
-__global__ void __launch_bounds__(256) k_backup(const PlanDesc *plans, StageTable st,
-                                                long long total_threads) {
-  // whole warps iterate together (the 16-lane shuffles run under a full-warp mask)
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-       t - (threadIdx.x & 31) < total_threads; t += (long long)gridDim.x * blockDim.x) {
-    const long long node_item = t >> 4;
-    const bool valid = t < total_threads;
-    const long long safe = valid ? node_item : ((total_threads - 1) >> 4);
-    const int pi = find_plan(st, safe);
-    const PlanDesc &P = plans[st.plan[pi]];
-    const int l = st.levels ? st.levels[pi] : st.level;
-    backup_node16(P, l, (unsigned long long)(safe - st.prefix[pi]), (int)(t & 15), valid);
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Tail: the plan's small levels top..1 in FP32 (one CTA), then the root in FP64 and the
-// Alg. 1 action choice.
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_backup_tail(const PlanDesc *plans, StageTable st) {
-  const int pi = blockIdx.x;
-  const PlanDesc &P = plans[st.plan[pi]];
-  if (P.result->status & kStatusDegenerateRoot) return;
-  const int top = st.levels ? st.levels[pi] : st.level;
-  for (int l = top; l >= 1; --l) {
-    unsigned long long nodes = 1;
-    for (int i = 0; i < l; ++i) nodes *= (unsigned long long)P.AW;
-    const unsigned long long tasks = nodes * 16ull;
-    for (unsigned long long t = threadIdx.x; t - (threadIdx.x & 31) < tasks; t += blockDim.x) {
-      const bool valid = t < tasks;
-      backup_node16(P, l, valid ? (t >> 4) : 0, (int)(t & 15), valid);
-    }
-    __syncthreads();
-  }
-  // root level in double precision
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x, A = P.A, W = P.W;
-    double q = 0.0, z = -CUDART_INF;
-    float2 mu = make_float2(0.f, 0.f);
-    if (P.pi_mode == kPiNavDist) mu = make_float2(P.mu[0][0], P.mu[0][1]);
-    double lp = -CUDART_INF;
-    if (lane < A) {
-      double rs = 0.0;
-      float M = -CUDART_INF_F;
-      for (int k = 0; k < W; ++k) {
-        rs += (double)P.rbar[1][lane * W + k];
-        M = fmaxf(M, P.lom[1][lane * W + k]);
-      }
-      double fut = 0.0;
-      if (M > -CUDART_INF_F) {
-        double num = 0.0, den = 0.0;
-        for (int k = 0; k < W; ++k) {
-          const double om = exp((double)P.lom[1][lane * W + k] - (double)M);
-          num += om * (double)P.V[1][lane * W + k];
-          den += om;
-        }
-        fut = num / den;
-      } else {
-        atomicAdd(&P.result->degenerate, 1u);
-      }
-      q = rs / (double)W + (double)P.gamma * fut;
-      lp = (double)log_pibar(P, mu, lane);
-      z = lp + q / (double)P.eta;
-    }
-    double zm = z;
-    for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
-    double e = (lane < A && z > -CUDART_INF) ? exp(z - zm) : 0.0;
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    const double v = (double)P.eta * (zm + log(e));
-    // argmax of Q + eta log pibar, lowest index on ties
-    double sc = (lane < A) ? q + (double)P.eta * lp : -CUDART_INF;
-    int best = (lane < A) ? lane : 1 << 30;
-    for (int o = 16; o > 0; o >>= 1) {
-      const double sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
-      const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
-      if (sc2 > sc || (sc2 == sc && b2 < best)) { sc = sc2; best = b2; }
-    }
-    DevResult *R = P.result;
-    if (lane < A) {
-      R->q[lane] = q;
-      R->policy[lane] = exp(lp + (q - v) / (double)P.eta);
-      P.Q[0][lane] = (float)q;
-    }
-    if (lane == 0) {
-      R->v_root = v;
-      R->action = best;
-      R->flags |= 2u;
-      P.V[0][0] = (float)v;
     }
   }
 }
@@ -990,20 +1059,6 @@ cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm) {
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf, threads, smem);
-}
-
-cudaError_t launch_backup(const PlanDesc *d, const StageTable &st, long long total_nodes,
-                          cudaStream_t s) {
-  const long long threads = total_nodes * 16;
-  long long grid = (threads + 255) / 256;
-  if (grid > (1ll << 20)) grid = 1ll << 20;
-  k_backup<<<(unsigned)grid, 256, 0, s>>>(d, st, threads);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_backup_tail(const PlanDesc *d, const StageTable &st, cudaStream_t s) {
-  k_backup_tail<<<st.n_plans, 1024, 0, s>>>(d, st);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s) {

@@ -26,8 +26,9 @@ VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT = 1, 2
 VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 (VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
  VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU) = range(11)
-VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP, VOPP_OPT_TAIL_MAX_NODES = 1, 2, 3, 4
+VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP = 1, 2, 3
 VOPP_OPT_PERSISTENT = 5
+VOPP_OPT_FP64_ROOT = 6
 VOPP_MAX_ACTIONS = 16
 NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
 

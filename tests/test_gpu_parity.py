@@ -66,6 +66,23 @@ def test_caller_pi_bar_overrides_model_policy():
     _full(Spec(WL.NAV2D, 128, 2, 2, pi_mode=WL.PI_NAV_SOFTMAX_DIST, pi_bar=[0.1, 0.2, 0.3, 0.4]))
 
 
+def test_fp64_root_option_agrees():
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(WL.NAV2D, 256, 3, 2, seed=13, eta=0.3)
+    g = Gpu(spec)
+    try:
+        a = g.plan()
+        V.vopp_ctx_set_option(g.ctx, V.VOPP_OPT_FP64_ROOT, 1)
+        b = g.plan()
+        assert b["flags"] & V.VOPP_FLAG_FP64_ROOT and not a["flags"] & V.VOPP_FLAG_FP64_ROOT
+        orc = spec.run_oracle(outputs=False)
+        assert_close(a["q"], orc["q_root"], "FP32 root Q")
+        assert_close(b["q"], orc["q_root"], "FP64 root Q")
+        assert_close([b["v_root"]], [orc["v_root"]], "FP64 root V")
+    finally:
+        g.close()
+
+
 def test_leaf_threads_do_not_change_results():
     spec = Spec(WL.NAV2D, 300, 2, 4, seed=11)
     r1 = Gpu(spec, leaf_threads=256)
