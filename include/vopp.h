@@ -173,6 +173,9 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
                                    counter (largest items first); 0 (default): one CTA per item */
 #define VOPP_OPT_FP64_ROOT 6    /* 1: back the root up in FP64 (VOPP_FLAG_FP64_ROOT); 0 (default):
                                    FP32 with compensated sums, within the 1e-4 tolerance */
+#define VOPP_OPT_GRAPHS 7       /* 1: vopp_plan / vopp_plan_batch capture their launch sequence in
+                                   a CUDA graph and replay it while the batch shape, buffers and
+                                   options repeat (not while per-kernel timing is on) */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
@@ -319,6 +322,22 @@ VOPP_API int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out);
 /* paused = 1: keep queueing requests but start no new batch (batches in flight finish);
  * paused = 0: resume.  Lets a caller release a burst of requests as full batches. */
 VOPP_API int vopp_server_set_paused(vopp_server *srv, int paused);
+
+/* ---- autotuning ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t leaf_threads;      /* chosen threads per leaf CTA (warps = branches processed at once) */
+  int32_t persistent;        /* chosen leaf scheduling: 1 persistent CTAs, 0 one CTA per node   */
+  double best_ms;            /* best time of the representative batch                         */
+  int32_t n_tried;
+  int32_t tried_threads[8], tried_persistent[8];
+  double tried_ms[8];
+} vopp_tune_result;
+/* Time a representative batch (n requests, `reps` timed runs each) under every leaf
+ * configuration -- 64 / 128 / 256 threads per leaf CTA, i.e. 2 / 4 / 8 branches per node in
+ * flight, each with per-node or persistent scheduling -- check that all of them agree
+ * within 1e-4 (they only reorder FP32 sums), and keep the fastest on the context. */
+VOPP_API int vopp_autotune(vopp_ctx *ctx, int32_t n, const vopp_plan_request *reqs, int32_t reps,
+                           vopp_tune_result *out);
 
 VOPP_API const char *vopp_last_error(void);
 /* Library version string. */

@@ -85,8 +85,31 @@ struct Slot {
 };
 }  // namespace
 
+namespace {
+// A captured launch sequence (metadata upload, every kernel, result download) of one batch
+// shape, replayed while the shape, the buffers and the options stay the same.
+struct GraphCache {
+  std::vector<unsigned char> sig;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;   // private stream the sequence is recorded on (the legacy
+                                    // default stream cannot be captured)
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    sig.clear();
+  }
+  void release() {
+    reset();
+    if (capture) cudaStreamDestroy(capture);
+    capture = nullptr;
+  }
+};
+}  // namespace
+
 struct vopp_ctx {
   int device = 0;
+  int use_graphs = 0;            // replay captured launch sequences of repeated shapes
+  GraphCache graph;
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   char *arena = nullptr;
@@ -365,7 +388,8 @@ std::vector<int> lpt_order(const std::vector<Job> &jobs, bool leaf) {
 // Build the metadata block of a batch in the slot's pinned mirror, upload it and enqueue
 // every launch and the device->host copy of the results on the slot's stream.  Nothing
 // here waits for the device.
-int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, bool timed) {
+int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, bool timed,
+                 GraphCache *graph) {
   const int n = (int)jobs.size();
   int rc = VOPP_OK;
   const std::vector<int> order_leaf = lpt_order(jobs, true), order_exp = lpt_order(jobs, false);
@@ -568,29 +592,85 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     sb.st.level = sb.level;
   }
   cudaStream_t stream = sl.stream;
-  CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
   c->h2d_bytes += off;
   c->d2h_bytes += sizeof(DevResult) * n;
   c->launches += stages.size();
-
-  for (auto &sb : stages) {
-    TimedLaunch tl;
-    if (timed) timed_begin(c, sb.family, tl);
-    cudaError_t e = cudaSuccess;
-    switch (sb.family) {
-      case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
-      case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, c->grid_cap, stream); break;
-      case F_LEAF:
-        if (!c->leaf_persistent) sb.st.counter = nullptr;
-        e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads,
-                        c->leaf_persistent ? persistent_grid(c, sb.smem) : c->grid_cap, stream);
-        break;
+  // launch shapes (computed before any capture)
+  std::vector<long long> grids(stages.size());
+  for (size_t k = 0; k < stages.size(); ++k) {
+    StageBuild &sb = stages[k];
+    if (sb.family == F_LEAF) {
+      if (!c->leaf_persistent) sb.st.counter = nullptr;
+      grids[k] = c->leaf_persistent ? persistent_grid(c, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
+    } else if (sb.family == F_EXPAND) {
+      grids[k] = std::min<long long>(sb.total, c->grid_cap);
+    } else {
+      grids[k] = sb.st.n_plans;
     }
-    if (timed) timed_end(c, tl);
-    if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
   }
-  CUDA_TRY(cudaMemcpyAsync(H + off_res, Dm + off_res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost,
-                           stream));
+  auto record = [&](cudaStream_t stream) -> int {
+    CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
+    for (size_t k = 0; k < stages.size(); ++k) {
+      StageBuild &sb = stages[k];
+      TimedLaunch tl;
+      if (timed) timed_begin(c, sb.family, tl);
+      cudaError_t e = cudaSuccess;
+      switch (sb.family) {
+        case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
+        case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, grids[k], stream); break;
+        case F_LEAF: e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
+      }
+      if (timed) timed_end(c, tl);
+      if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaMemcpyAsync(H + off_res, Dm + off_res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost,
+                             stream));
+    return VOPP_OK;
+  };
+  if (!graph || timed) return record(stream);
+
+  // signature of everything the recorded operations depend on
+  std::vector<unsigned char> sig;
+  auto put = [&](const void *p, size_t b) {
+    const unsigned char *q = static_cast<const unsigned char *>(p);
+    sig.insert(sig.end(), q, q + b);
+  };
+  const void *ptrs[3] = {Dm, H, arena};
+  put(ptrs, sizeof ptrs);
+  put(&off, sizeof off);
+  put(&off_res, sizeof off_res);
+  put(&n, sizeof n);
+  put(&c->leaf_threads, sizeof c->leaf_threads);
+  for (size_t k = 0; k < stages.size(); ++k) {
+    const StageBuild &sb = stages[k];
+    put(&sb.family, sizeof sb.family);
+    put(&sb.total, sizeof sb.total);
+    put(&sb.smem, sizeof sb.smem);
+    put(&sb.maxN, sizeof sb.maxN);
+    put(&sb.st, sizeof sb.st);
+    put(&grids[k], sizeof grids[k]);
+  }
+  if (!graph->exec || graph->sig != sig) {
+    graph->reset();
+    if (!graph->capture) CUDA_TRY(cudaStreamCreateWithFlags(&graph->capture, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(graph->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc2 = record(graph->capture);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(graph->capture, &g);
+    if (rc2 != VOPP_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc2 != VOPP_OK ? rc2 : fail(VOPP_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&graph->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      graph->exec = nullptr;
+      return fail(VOPP_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    graph->sig = std::move(sig);
+  }
+  CUDA_TRY(cudaGraphLaunch(graph->exec, stream));
   return VOPP_OK;
 }
 
@@ -639,7 +719,7 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
   int rc = ensure_arena(c, place_jobs(jobs));
   if (rc) return rc;
   c->slot.stream = c->stream;
-  rc = enqueue_jobs(c, c->slot, c->arena, jobs, c->timing);
+  rc = enqueue_jobs(c, c->slot, c->arena, jobs, c->timing, c->use_graphs ? &c->graph : nullptr);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   timed_collect(c);
@@ -720,6 +800,7 @@ int vopp_ctx_create(int device, size_t hbm_budget_bytes, uintptr_t cuda_stream, 
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete c; return fail(VOPP_E_CUDA, "cudaMemGetInfo"); }
   c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
   c->slot.stream = c->stream;
+  if (init_kernel_attributes() != cudaSuccess) { delete c; return fail(VOPP_E_CUDA, "kernel attributes"); }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
     c->sm_count = sms;
@@ -731,6 +812,7 @@ void vopp_ctx_destroy(vopp_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  c->graph.release();
   if (c->arena) cudaFree(c->arena);
   free_slot(c->slot);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -758,6 +840,10 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       return VOPP_OK;
     case VOPP_OPT_PERSISTENT: c->leaf_persistent = value ? 1 : 0; return VOPP_OK;
     case VOPP_OPT_FP64_ROOT: c->fp64_root = value ? 1 : 0; return VOPP_OK;
+    case VOPP_OPT_GRAPHS:
+      c->use_graphs = value ? 1 : 0;
+      if (!c->use_graphs) c->graph.reset();
+      return VOPP_OK;
     default: return fail(VOPP_E_INVALID, "unknown option %d", option);
   }
 }
@@ -919,6 +1005,89 @@ int vopp_plan_batch(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, vopp_
   std::vector<int> st(n);
   int rc = run_jobs(c, jobs, outs, st.data());
   return rc;
+}
+
+int vopp_autotune(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, int32_t reps,
+                  vopp_tune_result *out) {
+  if (!c || !reqs || !out || n < 1 || reps < 1) return fail(VOPP_E_INVALID, "bad autotune arguments");
+  std::vector<Job> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    const vopp_plan_request &r = reqs[i];
+    if (!r.model || r.model->ctx != c) return fail(VOPP_E_INVALID, "request %d: model of another context", i);
+    int rc = make_job(c, r.model, r.root_states, r.root_weights, r.n_particles, r.params, r.ptr_flags, jobs[i]);
+    if (rc) return rc;
+  }
+  cudaSetDevice(c->device);
+  const int threads[3] = {64, 128, 256};
+  const int saved_threads = c->leaf_threads, saved_pers = c->leaf_persistent, saved_timing = c->timing;
+  const bool saved_graphs = c->use_graphs;
+  c->timing = false;
+  c->use_graphs = 0;
+  std::memset(out, 0, sizeof *out);
+  std::vector<vopp_plan_result> ref(n), got(n);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  double best = 1e300;
+  int rc = VOPP_OK, k = 0;
+  for (int pers = 0; pers < 2 && rc == VOPP_OK; ++pers) {
+    for (int t = 0; t < 3 && rc == VOPP_OK; ++t, ++k) {
+      c->leaf_threads = threads[t];
+      c->leaf_persistent = pers;
+      rc = run_jobs(c, jobs, k == 0 ? ref.data() : got.data(), nullptr);   // warm-up
+      if (rc) break;
+      if (k > 0) {   // configurations only reorder FP32 sums: results agree within 1e-4
+        for (int i = 0; i < n; ++i) {
+          const int A = jobs[i].shape.A;
+          double top1 = -1e300, top2 = -1e300;
+          for (int a = 0; a < A; ++a) {
+            const double d = std::fabs(ref[i].q[a] - got[i].q[a]);
+            if (d > 1e-4 * std::max(std::fabs(ref[i].q[a]), 1.0))
+              rc = fail(VOPP_E_CUDA, "configuration changed a value beyond the tolerance");
+            if (ref[i].q[a] > top1) { top2 = top1; top1 = ref[i].q[a]; }
+            else if (ref[i].q[a] > top2) top2 = ref[i].q[a];
+          }
+          if (ref[i].action != got[i].action && top1 - top2 > 1e-4 * std::max(std::fabs(top1), 1.0))
+            rc = fail(VOPP_E_CUDA, "configuration changed a clear action choice");
+        }
+        if (rc) break;
+      }
+      double ms_best = 1e300;
+      for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, c->stream);
+        rc = run_jobs(c, jobs, got.data(), nullptr);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_best = std::min(ms_best, (double)ms);
+        if (rc) break;
+      }
+      out->tried_ms[k] = ms_best;
+      out->tried_threads[k] = threads[t];
+      out->tried_persistent[k] = pers;
+      if (ms_best < best) {
+        best = ms_best;
+        out->leaf_threads = threads[t];
+        out->persistent = pers;
+      }
+    }
+  }
+  out->n_tried = k;
+  out->best_ms = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = saved_timing;
+  c->use_graphs = saved_graphs;
+  if (rc != VOPP_OK) {
+    c->leaf_threads = saved_threads;
+    c->leaf_persistent = saved_pers;
+    return rc;
+  }
+  c->leaf_threads = out->leaf_threads;   // keep the winner for the context
+  c->leaf_persistent = out->persistent;
+  c->graph.reset();
+  return VOPP_OK;
 }
 
 int vopp_tree_read(vopp_ctx *c, int32_t field, int32_t level, uint64_t offset, uint64_t count,
@@ -1237,7 +1406,7 @@ bool start_batch(vopp_server *srv, ServerSlot *s) {
   const size_t arena_bytes = place_jobs(jobs);
   char *arena = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&arena), arena_bytes, s->slot.stream);
-  int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false) : VOPP_E_NOMEM;
+  int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false, nullptr) : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
     if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
         cudaLaunchHostFunc(s->slot.stream, slot_complete, s) != cudaSuccess)

@@ -36,10 +36,11 @@ constexpr size_t kLeafSmemLimit = 200 * 1024;
 size_t leaf_smem_bytes(int kind, int N, int AW);
 size_t expand_smem_bytes(int N);
 cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s);
+cudaError_t init_kernel_attributes();
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
-                          int grid_cap, cudaStream_t s);
+                          long long grid, cudaStream_t s);
 cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                        int threads, int grid_cap, cudaStream_t s);
+                        int threads, long long grid, cudaStream_t s);
 cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
 

@@ -16,6 +16,7 @@
 // / SFU issue (Philox integer multiplies, Box-Muller, log / exp); the others are small.
 #include "vopp_device.cuh"
 #include "vopp_internal.h"
+#include "vopp.h"
 
 namespace vopp {
 
@@ -1036,28 +1037,29 @@ cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream
   return cudaGetLastError();
 }
 
+// Dynamic shared memory ceilings of the kernels that may exceed 48 KB (set once, before any
+// stream capture).
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kLeafSmemLimit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kLeafSmemLimit);
+}
+
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
-                          int grid_cap, cudaStream_t s) {
-  const size_t smem = expand_smem_bytes(maxN);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long long grid = total < grid_cap ? total : grid_cap;
-  k_expand<<<(unsigned)grid, 256, smem, s>>>(d, st, total);
+                          long long grid, cudaStream_t s) {
+  k_expand<<<(unsigned)grid, 256, expand_smem_bytes(maxN), s>>>(d, st, total);
   return cudaGetLastError();
 }
 
 cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                        int threads, int grid_cap, cudaStream_t s) {
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long long grid = total < grid_cap ? total : grid_cap;
+                        int threads, long long grid, cudaStream_t s) {
   k_leaf<<<(unsigned)grid, threads, smem, s>>>(d, st, total);
   return cudaGetLastError();
 }
 
 cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm) {
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf, threads, smem);
 }
 

@@ -30,7 +30,8 @@ def make_models(V, ctx, layout_seed: int = 1):
             WL.GRID: V.vopp_create_model(ctx, V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry))}
 
 
-def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequential: bool = True):
+def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequential: bool = True,
+              autotune: bool = True):
     """Returns a dict with the batched and sequential times (CUDA events around each)."""
     import torch
     specs = WL.draw_mixed_plans(n_plans, seed)
@@ -50,12 +51,14 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
         b.synchronize()
         return a.elapsed_time(b) / 1e3, out
 
+    tune = V.vopp_autotune(ctx, reqs[::8], reps=1) if autotune else None   # tiles from the tuner
     V.vopp_plan_batch(ctx, reqs[:8])          # warm-up
     t_batch = []
     for _ in range(reps):
         t, (outs, keep) = timed(lambda: V.vopp_plan_batch(ctx, reqs))
         t_batch.append(t)
     res = {"plans": n_plans, "particle_steps": steps, "batched_s": min(t_batch),
+           "autotune": tune,
            "batched_particle_steps_per_s": steps / min(t_batch),
            "batched_plans_per_s": n_plans / min(t_batch)}
     if sequential:

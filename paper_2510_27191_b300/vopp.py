@@ -29,6 +29,7 @@ VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP = 1, 2, 3
 VOPP_OPT_PERSISTENT = 5
 VOPP_OPT_FP64_ROOT = 6
+VOPP_OPT_GRAPHS = 7
 VOPP_MAX_ACTIONS = 16
 NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
 
@@ -69,6 +70,13 @@ class vopp_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "rejected", "batches", "batched_plans", "max_batch_seen",
         "particle_steps", "pending", "in_flight_bytes", "peak_in_flight_bytes")]
+
+
+class vopp_tune_result(ctypes.Structure):
+    _fields_ = [("leaf_threads", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("n_tried", ctypes.c_int32),
+                ("tried_threads", ctypes.c_int32 * 8), ("tried_persistent", ctypes.c_int32 * 8),
+                ("tried_ms", ctypes.c_double * 8)]
 
 
 class vopp_plan_request(ctypes.Structure):
@@ -126,6 +134,8 @@ def _load():
         "vopp_server_set_paused": ([vp, ctypes.c_int], ctypes.c_int),
         "vopp_wait_any": ([vp, ctypes.c_double, ctypes.POINTER(u64), ctypes.POINTER(vopp_plan_result),
                            dp], ctypes.c_int),
+        "vopp_autotune": ([vp, i32, ctypes.POINTER(vopp_plan_request), i32,
+                           ctypes.POINTER(vopp_tune_result)], ctypes.c_int),
         "vopp_last_error": ([], ctypes.c_char_p),
         "vopp_version": ([], ctypes.c_char_p),
     }
@@ -445,4 +455,30 @@ def vopp_wait_any(srv: int, timeout_s: float = 0.0):
 
 def vopp_server_set_paused(srv: int, paused: bool) -> None:
     check(lib.vopp_server_set_paused(srv, int(paused)))
+
+
+def _requests(requests):
+    n = len(requests)
+    reqs = (vopp_plan_request * n)()
+    keep = []
+    for i, q in enumerate(requests):
+        sp, sdev, k1 = _addr(q["states"])
+        wp, _, k2 = _addr(q.get("weights"))
+        p, k3 = make_params(q["depth"], q["width"], q["eta"], q["gamma"], q["seed"], q.get("pi_bar"))
+        keep += [k1, k2, k3]
+        reqs[i].model, reqs[i].root_states, reqs[i].root_weights = q["model"], sp, wp
+        reqs[i].n_particles = q["n"]
+        reqs[i].ptr_flags = VOPP_PTR_DEVICE if sdev else 0
+        reqs[i].params = p
+    return reqs, keep
+
+
+def vopp_autotune(ctx: int, requests: list, reps: int = 2) -> dict:
+    reqs, keep = _requests(requests)
+    out = vopp_tune_result()
+    check(lib.vopp_autotune(ctx, len(requests), reqs, reps, ctypes.byref(out)))
+    del keep
+    return dict(leaf_threads=out.leaf_threads, persistent=out.persistent, best_ms=out.best_ms,
+                tried=[(out.tried_threads[i], out.tried_persistent[i], out.tried_ms[i])
+                       for i in range(out.n_tried)])
 

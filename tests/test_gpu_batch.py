@@ -142,3 +142,60 @@ def test_config3_grid_sampled_subtrees_bit_exact():
         assert res["particle_steps"] == WL.CONFIG3.steps
     finally:
         g.close()
+
+
+def test_graph_replay_equals_direct_launches():
+    """With VOPP_OPT_GRAPHS the launch sequence is captured once per shape and replayed; the
+    results equal those of direct launches bit for bit, across seeds and a shape change."""
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(WL.NAV2D, 300, 3, 2, seed=1, pi_mode=WL.PI_NAV_SOFTMAX_DIST)
+    spec2 = Spec(WL.GRID, 128, 3, 2, seed=1)
+    ctx_a = V.vopp_ctx_create(0, 0, 0)
+    ctx_b = V.vopp_ctx_create(0, 0, 0)
+    V.vopp_ctx_set_option(ctx_b, V.VOPP_OPT_GRAPHS, 1)
+    try:
+        ma = V.vopp_create_model(ctx_a, V.make_desc(WL.NAV2D, pi_mode=WL.PI_NAV_SOFTMAX_DIST))
+        mb = V.vopp_create_model(ctx_b, V.make_desc(WL.NAV2D, pi_mode=WL.PI_NAV_SOFTMAX_DIST))
+        ga = V.vopp_create_model(ctx_a, V.make_desc(WL.GRID, rock_x=spec2.rock_x, rock_y=spec2.rock_y))
+        gb = V.vopp_create_model(ctx_b, V.make_desc(WL.GRID, rock_x=spec2.rock_x, rock_y=spec2.rock_y))
+        for seed in (1, 2, 3, 4):
+            for (m1, m2, s) in ((ma, mb, spec), (ga, gb, spec2)):
+                a = V.vopp_plan(m1, s.states(), None, s.N, s.D, s.W, 0.7, 0.95, None, seed)
+                b = V.vopp_plan(m2, s.states(), None, s.N, s.D, s.W, 0.7, 0.95, None, seed)
+                assert a["q"].tolist() == b["q"].tolist() and a["action"] == b["action"]
+        orc = spec.run_oracle(outputs=False)
+        b = V.vopp_plan(mb, spec.states(), None, spec.N, spec.D, spec.W, spec.eta, spec.gamma,
+                        None, spec.seed)
+        assert_close(b["q"], orc["q_root"], "graph-replayed root Q")
+        for m in (ma, mb, ga, gb):
+            V.vopp_model_destroy(m)
+    finally:
+        V.vopp_ctx_destroy(ctx_a)
+        V.vopp_ctx_destroy(ctx_b)
+
+
+def test_autotune_picks_a_configuration_without_changing_results():
+    from paper_2510_27191_b300 import vopp as V
+    specs = _mixed_specs(12, 9)
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        models = {}
+        reqs = []
+        for s in specs:
+            key = (s.kind, s.branch_mode)
+            if key not in models:
+                models[key] = V.vopp_create_model(ctx, V.make_desc(
+                    s.kind, s.branch_mode, rock_x=WL.grid_layout(1)[0] if s.kind == WL.GRID else None,
+                    rock_y=WL.grid_layout(1)[1] if s.kind == WL.GRID else None))
+            reqs.append(dict(model=models[key], states=s.states(), weights=None, n=s.N, depth=s.D,
+                             width=s.W, eta=s.eta, gamma=s.gamma, seed=s.seed, A=s.A))
+        before, k1 = V.vopp_plan_batch(ctx, reqs)
+        tune = V.vopp_autotune(ctx, reqs, reps=1)
+        assert tune["leaf_threads"] in (64, 128, 256) and len(tune["tried"]) == 6
+        after, k2 = V.vopp_plan_batch(ctx, reqs)
+        for a, b in zip(before, after):
+            assert_close(b["q"], a["q"], "Q after tuning")
+        for m in models.values():
+            V.vopp_model_destroy(m)
+    finally:
+        V.vopp_ctx_destroy(ctx)
