@@ -141,6 +141,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's value (the slowest rank's time); the value itself when
+    running alone."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def dist_setup(n_gpus: int):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -297,13 +313,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     counters = V.vopp_ctx_counters(ctx)
-    total_ms = float(sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dist, "cuda")
     units = spec.steps * args.steps * world
-    value = units / (total_ms / 1e3)
+    value = weak_scaling_rate(spec.steps * args.steps, world, total_ms)
     lat = np.array(times)
 
     # roofline of the dominant kernel (the fused leaf expansion), per-kernel events
@@ -326,11 +338,7 @@ def main():
     V.vopp_ctx_reset_kernel_times(ctx)
     e2e_times, _ = timed_pass(pinned.numpy(), args.steps, args.warmup)
     c2 = V.vopp_ctx_counters(ctx)
-    e2e_ms = float(sum(e2e_times))
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(float(sum(e2e_times)), dist, "cuda")
 
     if rank == 0:
         out = {
