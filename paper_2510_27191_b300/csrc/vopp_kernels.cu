@@ -157,6 +157,11 @@ template <> __device__ __forceinline__ float2 state_xy<ToyModel>(const ToyModel:
   return make_float2(0.f, 0.f);
 }
 
+template <class M> __device__ __forceinline__ typename M::S set_xy(typename M::S s, float, float) { return s; }
+template <> __device__ __forceinline__ NavModel::S set_xy<NavModel>(NavModel::S, float x, float y) {
+  return NavModel::S{x, y};
+}
+
 template <class M>
 __device__ __forceinline__ typename M::S load_root(const PlanDesc &P, int i);
 template <> __device__ __forceinline__ NavModel::S load_root<NavModel>(const PlanDesc &P, int i) {
@@ -234,43 +239,65 @@ __device__ __forceinline__ void block_reduce(float (&v)[K], const bool (&is_max)
 
 // ---------------------------------------------------------------------------------------
 // Child construction (Alg. 2: G, observation, weighting) by a whole CTA, one Philox pair
-// per thread iteration.  src: parent particles (level l); dst: the child's particles;
-// sc: two per-particle scratch values between the passes.
+// per thread iteration, in base-2 logs.  src: parent particles (level l, natural log
+// weights); dst: the child's particles; sc: two per-particle scratch values between the
+// passes.  dst_log2: store the child's log weights in base 2 (shared-memory node buffers)
+// rather than natural (level stores); dst_has_w also stores the linear weights.
 // ---------------------------------------------------------------------------------------
 template <class M, class Src, class Dst, class Scr>
 __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
                             unsigned long long child, const Src &src, const Dst &dst,
-                            const Scr &sc, float *red, bool dst_has_w, float2 *mu_out) {
+                            const Scr &sc, float *red, bool dst_has_w, bool dst_log2,
+                            float2 *mu_out) {
   const int N = P.N, AW = P.AW, W = P.W, npairs = (N + 1) >> 1;
   const unsigned long long parent = child / (unsigned long long)AW;
   const int slot = (int)(child - parent * (unsigned long long)AW);
   const int a = slot / W, k = slot - (slot / W) * W;
   int j;
   const typename M::O o = branch_obs<M>(P, src, l, a, k, parent, dm, j);
+  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
 
+  // pass 1: step every particle, log2-likelihood, reward mean; keep L2 = lw2 + ell2, ell2
   Kahan R;
   R.init();
   float m1 = -CUDART_INF_F, m0 = -CUDART_INF_F;
   for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-    const uint4 w = pair_words<M>(P, p, l, a, k, parent);
-    float rp = 0.f;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int i = 2 * p + e;
-      if (i < N) {
-        typename M::S s = src.get(i);
-        const float lw = src.lw(i);
-        const float r = M::step(s, a, e ? w.z : w.x, e ? w.w : w.y, dm);
-        const float ell = M::loglik(s, a, o, dm);
-        const float L = lw + ell;
-        rp += (lw > -CUDART_INF_F) ? __expf(lw) * r : 0.f;
-        dst.put(i, s);
-        sc.setL(i, L);
-        sc.setE(i, ell);
-        m1 = fmaxf(m1, L);
-        m0 = fmaxf(m0, ell);
-      }
+    const int i0 = 2 * p, i1 = 2 * p + 1;
+    const bool v1 = i1 < N;
+    const uint4 w = M::kStochastic
+                        ? philox(make_uint4((uint32_t)p, c1, (uint32_t)parent, (uint32_t)(parent >> 32)),
+                                 P.key0, P.key1)
+                        : make_uint4(0u, 0u, 0u, 0u);
+    const float lw0 = src.lw(i0), lw1 = v1 ? src.lw(i1) : -CUDART_INF_F;
+    float2 r, e;
+    typename M::S s0 = src.get(i0), s1 = v1 ? src.get(i1) : src.get(i0);
+    if constexpr (M::kPairPacked) {
+      float2 X = make_float2(state_xy<M>(s0).x, state_xy<M>(s1).x);
+      float2 Y = make_float2(state_xy<M>(s0).y, state_xy<M>(s1).y);
+      bool t0, t1;
+      r = NavModel::step_pair(X, Y, NavModel::dx_of(a), NavModel::dy_of(a), w, t0, t1);
+      e = NavModel::loglik2_pair(X, Y, o_nav(o));
+      s0 = set_xy<M>(s0, X.x, Y.x);
+      s1 = set_xy<M>(s1, X.y, Y.y);
+    } else {
+      r.x = M::step(s0, a, w.x, w.y, dm);
+      r.y = M::step(s1, a, w.z, w.w, dm);
+      e = make_float2(M::loglik2(s0, a, o, dm), M::loglik2(s1, a, o, dm));
     }
+    const float L0 = fmaf(lw0, kLog2e, e.x), L1 = v1 ? fmaf(lw1, kLog2e, e.y) : -CUDART_INF_F;
+    const float E1 = v1 ? e.y : -CUDART_INF_F;
+    float rp = (lw0 > -CUDART_INF_F) ? ex2(lw0 * kLog2e) * r.x : 0.f;
+    if (lw1 > -CUDART_INF_F) rp = fmaf(ex2(lw1 * kLog2e), r.y, rp);
+    dst.put(i0, s0);
+    sc.setL(i0, L0);
+    sc.setE(i0, e.x);
+    if (v1) {
+      dst.put(i1, s1);
+      sc.setL(i1, L1);
+      sc.setE(i1, E1);
+    }
+    m1 = fmaxf(m1, fmaxf(L0, L1));
+    m0 = fmaxf(m0, fmaxf(e.x, E1));
     R.add(rp);
   }
   {
@@ -280,18 +307,30 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
     m1 = v[0];
     m0 = v[1];
   }
+  // pass 2: shifted sums (compensated per pair) and the weighted mean particle
   Kahan S1, S0, MX, MY;
   S1.init(); S0.init(); MX.init(); MY.init();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float e1 = (m1 > -CUDART_INF_F) ? __expf(sc.getL(i) - m1) : 0.f;
-    const float e0 = (m0 > -CUDART_INF_F) ? __expf(sc.getE(i) - m0) : 0.f;
-    S1.add(e1);
-    S0.add(e0);
-    if (P.pi_mode == kPiNavDist) {
-      const float2 xy = state_xy<M>(dst.get(i));
-      MX.add(e1 * xy.x);
-      MY.add(e1 * xy.y);
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    const int i0 = 2 * p, i1 = 2 * p + 1;
+    const bool v1 = i1 < N;
+    float a1 = 0.f, a0 = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int i = e ? i1 : i0;
+      if (e && !v1) break;
+      const float e1 = (m1 > -CUDART_INF_F) ? ex2(sc.getL(i) - m1) : 0.f;
+      const float e0 = (m0 > -CUDART_INF_F) ? ex2(sc.getE(i) - m0) : 0.f;
+      a1 += e1;
+      a0 += e0;
+      if (P.pi_mode == kPiNavDist) {
+        const float2 xy = state_xy<M>(dst.get(i));
+        ax = fmaf(e1, xy.x, ax);
+        ay = fmaf(e1, xy.y, ay);
+      }
     }
+    S1.add(a1);
+    S0.add(a0);
+    if (P.pi_mode == kPiNavDist) { MX.add(ax); MY.add(ay); }
   }
   float v[5] = {R.value(), S1.value(), S0.value(), MX.value(), MY.value()};
   {
@@ -299,15 +338,16 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
     block_reduce<5>(v, mx, red);
   }
   const float rbar = v[0], s1 = v[1], s0 = v[2], mx = v[3], my = v[4];
-  const float lse1 = (s1 > 0.f) ? m1 + __logf(s1) : -CUDART_INF_F;
+  const float lse2 = (s1 > 0.f) ? m1 + lg2(s1) : -CUDART_INF_F;       // base 2
   float lom;
-  if (P.branch_mode == kEnumerate) lom = lse1;
-  else lom = (lse1 > -CUDART_INF_F) ? __logf((float)N) + lse1 - (m0 + __logf(s0)) : -CUDART_INF_F;
+  if (P.branch_mode == kEnumerate) lom = kLn2 * lse2;
+  else lom = (lse2 > -CUDART_INF_F) ? __logf((float)N) + kLn2 * (lse2 - (m0 + lg2(s0))) : -CUDART_INF_F;
 
+  // pass 3: normalised child log weights (and linear weights)
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float nl = (lse1 > -CUDART_INF_F) ? sc.getL(i) - lse1 : -CUDART_INF_F;
-    dst.set_lw(i, nl);
-    if (dst_has_w) sc.setE(i, (nl > -CUDART_INF_F) ? __expf(nl) : 0.f);
+    const float nl2 = (lse2 > -CUDART_INF_F) ? sc.getL(i) - lse2 : -CUDART_INF_F;
+    dst.set_lw(i, dst_log2 ? nl2 : kLn2 * nl2);
+    if (dst_has_w) sc.setE(i, ex2(nl2));
   }
   const int cl = l + 1;
   if (threadIdx.x == 0) {
@@ -591,7 +631,7 @@ __device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, 
   const GNode<M> src = GNode<M>::at(P, l, (long long)parent);
   const GNode<M> dst = GNode<M>::at(P, l + 1, (long long)child);
   const ScratchArrays sc{smem, smem + P.N};
-  build_child<M>(P, dm, l, child, src, dst, sc, red, false, nullptr);
+  build_child<M>(P, dm, l, child, src, dst, sc, red, false, false, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTable st,
@@ -835,22 +875,20 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
     const unsigned long long parent = node / (unsigned long long)AW;
     const GNode<M> src = GNode<M>::at(P, l - 1, (long long)parent);
     float2 mu;
-    build_child<M>(P, dm, l - 1, node, src, nb, ScratchInNode<M>{nb}, red, true, &mu);
+    build_child<M>(P, dm, l - 1, node, src, nb, ScratchInNode<M>{nb}, red, true, true, &mu);
     if (threadIdx.x == 0) s_mu = mu;
   } else {
     const GNode<M> src = GNode<M>::at(P, l, (long long)node);
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       nb.put(i, src.get(i));
       const float lw = src.lw(i);
-      nb.set_lw(i, lw);
+      nb.set_lw(i, kLog2e * lw);                       // base 2 in shared memory
       nb.set_w(i, (lw > -CUDART_INF_F) ? __expf(lw) : 0.f);
     }
     if (threadIdx.x == 0)
       s_mu = (P.pi_mode == kPiNavDist) ? make_float2(P.mu[l][2 * node], P.mu[l][2 * node + 1])
                                        : make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) nb.set_lw(i, kLog2e * nb.lw(i));  // base 2
   if ((N & 1) && threadIdx.x == 0) {   // odd N: the pad slot is a zero-weight copy of particle 0
     nb.put(N, nb.get(0));
     nb.set_lw(N, -CUDART_INF_F);
