@@ -21,6 +21,18 @@
 namespace vopp {
 
 // ---------------------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel lets the next kernel of the plan start being
+// scheduled right away, and waits for its predecessor's results before reading them.  Both
+// are no-ops for a kernel launched without the programmatic-serialisation attribute.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_release_next() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_prev() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------
 // Particle-set views.
 //   GNode: a node's particles in a global level store (SoA x[N], y[N] / s[N], lw[N]); the
 //          linear weight is exp(lw).
@@ -611,6 +623,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
 
 __global__ void __launch_bounds__(1024) k_root_prep(const PlanDesc *plans, StageTable st) {
   __shared__ float red[32];
+  pdl_release_next();
   const PlanDesc &P = plans[st.plan[blockIdx.x]];
   const DevModel &dm = *P.model;
   switch (P.kind) {
@@ -638,6 +651,8 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
                                                 long long total) {
   extern __shared__ float smem[];
   __shared__ float red[32 * 5];
+  pdl_release_next();
+  pdl_wait_prev();
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
@@ -922,6 +937,8 @@ __global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDes
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[32 * 5];
   __shared__ long long s_item;
+  pdl_release_next();
+  pdl_wait_prev();
   long long item = blockIdx.x;
   if (st.counter) {   // persistent CTAs: take work items in order from a global counter
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(st.counter, 1ull);
@@ -1085,16 +1102,32 @@ cudaError_t init_kernel_attributes() {
                               (int)kLeafSmemLimit);
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled while its
+// predecessor on the stream is still running and waits for it on the device.
+template <typename... Args>
+static cudaError_t launch_pdl(void (*k)(Args...), unsigned grid, unsigned threads, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
                           long long grid, cudaStream_t s) {
-  k_expand<<<(unsigned)grid, 256, expand_smem_bytes(maxN), s>>>(d, st, total);
-  return cudaGetLastError();
+  return launch_pdl(k_expand, (unsigned)grid, 256u, expand_smem_bytes(maxN), s, d, st, total);
 }
 
 cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
                         int threads, long long grid, cudaStream_t s) {
-  k_leaf<<<(unsigned)grid, threads, smem, s>>>(d, st, total);
-  return cudaGetLastError();
+  return launch_pdl(k_leaf, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
 }
 
 cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm) {
