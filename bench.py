@@ -167,7 +167,9 @@ def dist_setup(n_gpus: int):
 
 
 def run_reference(args, spec, rank, world):
-    """FP64 oracle on the host: each step plans one level-1 subtree (1/(A W) of the tree)."""
+    """FP64 oracle on the host cores: each step plans one wave of level-1 subtrees, one per
+    host thread (each 1/(A W) of the tree; the ctypes calls release the interpreter lock)."""
+    import concurrent.futures as cf
     import oracle as O
     if rank != 0:
         return
@@ -176,30 +178,36 @@ def run_reference(args, spec, rank, world):
                      rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None)
     root = _root_arrays(spec)
     AW = spec.A * spec.W
-    steps_per_sample = sum(AW ** l for l in range(1, spec.D)) * spec.N + spec.N
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, min(threads or 1, AW))
+    steps_per_subtree = sum(AW ** l for l in range(1, spec.D)) * spec.N + spec.N
 
-    def sample(i):
-        path = (i % AW,)
+    def subtree(i):
         kw = dict(root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"))
-        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=path,
+        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(i % AW,),
                    outputs=False, **kw)
         return r["particle_steps"]
 
-    for i in range(args.warmup):
-        sample(i)
-    t0 = time.perf_counter()
-    done = 0
-    for i in range(args.steps):
-        done += sample(args.warmup + i)
-    dt = time.perf_counter() - t0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        def sample(i):
+            return sum(ex.map(subtree, range(i * threads, (i + 1) * threads)))
+
+        for i in range(args.warmup):
+            sample(i)
+        t0 = time.perf_counter()
+        done = 0
+        for i in range(args.steps):
+            done += sample(args.warmup + i)
+        dt = time.perf_counter() - t0
     value = done / dt
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": _config(spec, args),
-           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
-                            "sample": f"one level-1 subtree per step ({steps_per_sample} "
-                                      f"particle-steps, 1/{AW} of the plan), single thread"},
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": threads,
+                            "sample": f"{threads} level-1 subtrees per step, one per thread "
+                                      f"({steps_per_subtree} particle-steps each, 1/{AW} of "
+                                      f"the plan)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -221,24 +229,48 @@ def _config(spec, args):
 
 
 def cpu_baseline(spec, budget_s=20.0):
-    """The oracle timed as it stands on the host (one thread) over a bounded sample."""
+    """The oracle timed as it stands on the host over a bounded sample: level-1 subtrees of
+    the same plan (independent, so they spread over the host's cores with one thread per
+    core; the ctypes calls release the interpreter lock).  Reports the all-cores rate, with
+    the single-thread rate beside it."""
+    import concurrent.futures as cf
     import oracle as O
     m = O.make_model(spec.kind, pi_mode=spec.pi_mode, pi_temp=spec.pi_temp,
                      rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
                      rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None)
     root = _root_arrays(spec)
     AW = spec.A * spec.W
+
+    def subtree(n):
+        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(n % AW,),
+                   outputs=False, root_x=root.get("x"), root_y=root.get("y"),
+                   root_s=root.get("s"))
+        return r["particle_steps"]
+
+    # single thread: subtrees one after another for a third of the budget
     t0 = time.perf_counter()
+    done1, n1 = 0, 0
+    while time.perf_counter() - t0 < budget_s / 3 and n1 < AW:
+        done1 += subtree(n1)
+        n1 += 1
+    dt1 = time.perf_counter() - t0
+    # all cores: waves of one subtree per thread, every subtree of the plan at least once
+    # when the budget allows
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, threads or 1)
     done, n = 0, 0
-    while time.perf_counter() - t0 < budget_s and n < AW:
-        r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(n,),
-                   outputs=False, root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"))
-        done += r["particle_steps"]
-        n += 1
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < budget_s * 2 / 3 and n < max(AW, threads):
+            wave = list(range(n, n + threads))
+            done += sum(ex.map(subtree, wave))
+            n += len(wave)
     dt = time.perf_counter() - t0
-    return {"kind": "oracle", "value": done / dt, "unit": UNIT, "cores": 1,
-            "sample": f"{n} of {AW} level-1 subtrees of the same plan ({done} particle-steps), "
-                      f"FP64, single thread, {dt:.1f} s"}
+    return {"kind": "oracle", "value": done / dt, "unit": UNIT, "cores": threads,
+            "single_thread_value": done1 / dt1,
+            "sample": f"{n} level-1 subtrees (of {AW}; indices taken modulo {AW}) of the same "
+                      f"plan, {done} particle-steps, FP64, {threads} threads, {dt:.1f} s; "
+                      f"single thread: {n1} subtrees, {done1} particle-steps, {dt1:.1f} s"}
 
 
 def main():
@@ -340,6 +372,10 @@ def main():
     c2 = V.vopp_ctx_counters(ctx)
     e2e_ms = max_over_ranks(float(sum(e2e_times)), dist, "cuda")
 
+    # issue rates of the leaf kernel's arithmetic, per SM cycle (outside every timed region)
+    pipes = V.vopp_pipe_rates(local)
+    fma_per_clk = pipes.get("fma.rn.f32", (LANES_PER_CLK, 0.0))[0]
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -363,7 +399,11 @@ def main():
                          "peak_source": f"148 SMs x 128 lanes/clk x {sm_max:.0f} MHz ({pk_src} max clock)",
                          "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
                          "units_per_launch": leaf_steps, "avg_launch_ms": leaf_avg_s * 1e3,
-                         "share_of_step": leaf_ms / max(total_kernel_ms, 1e-9)},
+                         "share_of_step": leaf_ms / max(total_kernel_ms, 1e-9),
+                         "frac_of_measured_fp32_issue":
+                             achieved_ops / (SMS * fma_per_clk * sm_max * 1e6)},
+            "pipe_rates": {"unit": "thread ops per SM cycle (microbenchmark, clock64)",
+                           **{k: round(v[0], 3) for k, v in pipes.items()}},
             "kernels_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items() if v[1]},
             "clocks": clk.summary(),
             "result": {"action": int(last["action"]), "v_root": last["v_root"]},

@@ -339,6 +339,22 @@ typedef struct {
 VOPP_API int vopp_autotune(vopp_ctx *ctx, int32_t n, const vopp_plan_request *reqs, int32_t reps,
                            vopp_tune_result *out);
 
+/* ---- measurement aid (no counterpart in the paper) ----------------------------------- */
+/* Issue rate of one arithmetic operation the leaf kernel is built from. */
+typedef struct {
+  char op[32];                          /* PTX operation measured, or "philox4x32-10 call"  */
+  double thread_ops_per_clock_per_sm;   /* per SM cycle (clock64), independent of the clock */
+  double ops_per_second;                /* whole device, at the clock of the moment         */
+  int32_t sms;
+} vopp_pipe_rate;
+/* Microbenchmark: for each of up to max_out operations (FP32 FMA, packed f32x2 FMA, 32-bit
+ * multiply-add (low and high half), three-input XOR, add, ex2, lg2, sin, sqrt, rsqrt, one
+ * Philox4x32-10 call) run 4 CTAs x 256 threads per SM, 8 chains of 4096 steps
+ * per thread, and report the rate.  Fills out[0 .. *n_out-1].  Allocates a few hundred KB
+ * of device memory for the duration of the call and runs on its own stream; VOPP_E_CUDA
+ * on a CUDA failure. */
+VOPP_API int vopp_pipe_rates(int device, vopp_pipe_rate *out, int32_t max_out, int32_t *n_out);
+
 VOPP_API const char *vopp_last_error(void);
 /* Library version string. */
 VOPP_API const char *vopp_version(void);

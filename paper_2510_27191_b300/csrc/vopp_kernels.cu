@@ -932,8 +932,12 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256, VOPP_LEAF_MINBLOCKS) k_leaf(const PlanDesc *plans, StageTable st,
-                                              long long total) {
+#ifdef VOPP_LEAF_MAXNREG
+#define VOPP_LEAF_BOUNDS __maxnreg__(VOPP_LEAF_MAXNREG)
+#else
+#define VOPP_LEAF_BOUNDS __launch_bounds__(256, VOPP_LEAF_MINBLOCKS)
+#endif
+__global__ void VOPP_LEAF_BOUNDS k_leaf(const PlanDesc *plans, StageTable st, long long total) {
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[32 * 5];
   __shared__ long long s_item;

@@ -79,6 +79,11 @@ class vopp_tune_result(ctypes.Structure):
                 ("tried_ms", ctypes.c_double * 8)]
 
 
+class vopp_pipe_rate(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_char * 32), ("thread_ops_per_clock_per_sm", ctypes.c_double),
+                ("ops_per_second", ctypes.c_double), ("sms", ctypes.c_int32)]
+
+
 class vopp_plan_request(ctypes.Structure):
     _fields_ = [("model", ctypes.c_void_p), ("root_states", ctypes.c_void_p),
                 ("root_weights", ctypes.c_void_p), ("n_particles", ctypes.c_int32),
@@ -138,6 +143,7 @@ def _load():
                            ctypes.POINTER(vopp_tune_result)], ctypes.c_int),
         "vopp_last_error": ([], ctypes.c_char_p),
         "vopp_version": ([], ctypes.c_char_p),
+        "vopp_pipe_rates": ([ctypes.c_int, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -378,6 +384,15 @@ def vopp_plan_batch(ctx: int, requests: list) -> tuple[list, list]:
 
 def vopp_version() -> str:
     return lib.vopp_version().decode()
+
+
+def vopp_pipe_rates(device: int = 0) -> dict:
+    """Issue-rate microbenchmark: {op: (thread ops per SM cycle, ops per second)}."""
+    out = (vopp_pipe_rate * 16)()
+    n = ctypes.c_int32()
+    check(lib.vopp_pipe_rates(device, out, 16, ctypes.byref(n)))
+    return {out[i].op.decode(): (out[i].thread_ops_per_clock_per_sm, out[i].ops_per_second)
+            for i in range(n.value)}
 
 
 # ---- serving ---------------------------------------------------------------------------

@@ -1,12 +1,14 @@
 """Serving loop (continuous batching) on the GPU: results alone vs in the mix, admission by
 the HBM budget, overlap of batches (needs a GPU)."""
+import dataclasses
 import time
 
 import numpy as np
 import pytest
 
 from paper_2510_27191_b300 import workloads as WL
-from tests.parity import Spec
+import oracle as O
+from tests.parity import Spec, action_agrees, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -71,8 +73,8 @@ def test_admission_refuses_plans_beyond_the_budget():
         x, y, _ = WL.nav_root(1024, 1)
         st = np.concatenate([x, y]).astype(np.float32)
         big = V.vopp_submit(srv, models[WL.NAV2D], st, None, 1024, 5, 4, 1.0, 0.95, 1)
-        small = [V.vopp_submit(srv, models[WL.NAV2D], st[:2 * 64] if False else
-                               np.concatenate([x[:64], y[:64]]), None, 64, 2, 2, 1.0, 0.95, s)
+        small = [V.vopp_submit(srv, models[WL.NAV2D], np.concatenate([x[:64], y[:64]]), None,
+                               64, 2, 2, 1.0, 0.95, s)
                  for s in range(6)]
         with pytest.raises(V.VoppError) as e:
             V.vopp_wait(srv, big, 4, 20.0)
@@ -87,6 +89,94 @@ def test_admission_refuses_plans_beyond_the_budget():
         assert e.value.code == V.VOPP_E_TIMEOUT
     finally:
         V.vopp_server_destroy(srv)
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
+
+
+def _observation(kind, action, st, lw):
+    """An observation the agent's own belief makes possible: from its heaviest particle (moved
+    by the action's mean displacement for the navigation model; the sensed rock's bit for the
+    grid model, NULL for moves and collect)."""
+    i = int(np.argmax(lw))
+    if kind == WL.NAV2D:
+        n = lw.size
+        d = [(1, 0), (-1, 0), (0, 1), (0, -1)][action]
+        return (float(np.clip(st[i] + d[0], 0, 10)), float(np.clip(st[n + i] + d[1], 0, 10)))
+    if action >= 5:
+        return 1 if (int(st[i]) >> (action - 5)) & 1 else 2
+    return 0
+
+
+def _replay(kind, st, lw, N, D, W, eta, gamma, seed, res, what):
+    """Run the oracle on the particles a request carried and compare the served result."""
+    w = np.exp(lw.astype(np.float64) - float(np.max(lw)))
+    n = lw.size
+    root = (dict(x=st[:n], y=st[n:], w=w) if kind == WL.NAV2D else dict(s=st, w=w))
+    sp = Spec(kind, N, D, W, eta=eta, gamma=gamma, seed=seed, root=root, weights="random")
+    orc = sp.run_oracle(outputs=False)
+    assert orc["status"] == O.OK, what
+    assert_close(res["q"][:sp.A], orc["q_root"], f"{what} root Q")
+    assert_close([res["v_root"]], [orc["v_root"]], f"{what} root V")
+    assert action_agrees(dict(res, q=res["q"][:sp.A]), orc, sp), what
+
+
+def test_tagged_agents_and_sampled_requests_replayed_by_the_oracle():
+    """Eight tagged agents run short episodes through the serving loop (plan, act, observe,
+    belief update) among untagged traffic.  Every plan of a tagged agent is replayed by the
+    oracle from the particles the agent held when the plan was submitted, and so is every
+    eighth untagged request."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    models = _models(V, ctx)
+    srv = V.vopp_server_create(ctx, max_batch=16, n_slots=3)
+    agents = []
+    try:
+        rng = np.random.default_rng(5)
+        for i in range(8):
+            kind = WL.NAV2D if i % 2 == 0 else WL.GRID
+            sp = Spec(kind, 192 + 32 * i, 2, 2, root_seed=40 + i)
+            agents.append((kind, V.vopp_agent_create(models[kind], sp.states(), None, sp.N,
+                                                     900 + i)))
+        untagged = WL.draw_mixed_plans(48, 23, 1 << 20)
+        replayed = 0
+        for step in range(3):
+            # one untagged burst per step, submitted before the tagged agents' plans
+            burst = []
+            for j, ps in enumerate(untagged[16 * step:16 * (step + 1)]):
+                ps = dataclasses.replace(ps, layout_seed=1)   # the served grid model's layout
+                sp = Spec.from_plan(ps)
+                t = V.vopp_submit(srv, models[ps.kind], sp.states(), None, ps.N, ps.D, ps.W,
+                                  ps.eta, ps.gamma, ps.seed)
+                burst.append((t, ps, sp))
+            tagged = []
+            for i, (kind, g) in enumerate(agents):
+                st, lw, _ = V.vopp_agent_get_particles(g, kind)
+                D, W = 2 + (i + step) % 2, 2
+                eta, gamma, seed = float(rng.uniform(0.3, 2.0)), 0.95, 7000 + 10 * i + step
+                t = V.vopp_submit_agent(srv, g, D, W, eta, gamma, seed)
+                tagged.append((t, kind, g, st, lw, D, W, eta, gamma, seed))
+            for t, kind, g, st, lw, D, W, eta, gamma, seed in tagged:
+                res, _ = V.vopp_wait(srv, t, V.VOPP_MAX_ACTIONS, 30.0)
+                _replay(kind, st, lw, lw.size, D, W, eta, gamma, seed, res,
+                        f"tagged agent {g:#x} step {step}")
+                replayed += 1
+                a = res["action"]
+                V.vopp_belief_update(g, a, _observation(kind, a, st, lw), kind)
+            for j, (t, ps, sp) in enumerate(burst):
+                res, _ = V.vopp_wait(srv, t, V.VOPP_MAX_ACTIONS, 30.0)
+                if j % 8 == step % 8:
+                    orc = sp.run_oracle(outputs=False)
+                    assert_close(res["q"][:sp.A], orc["q_root"], f"untagged {j} root Q")
+                    assert_close([res["v_root"]], [orc["v_root"]], f"untagged {j} root V")
+                    assert action_agrees(dict(res, q=res["q"][:sp.A]), orc, sp)
+                    replayed += 1
+        assert replayed == 24 + 6
+        assert V.vopp_server_get_stats(srv)["completed"] == 24 + 48
+    finally:
+        V.vopp_server_destroy(srv)
+        for _, g in agents:
+            V.vopp_agent_destroy(g)
         for m in models.values():
             V.vopp_model_destroy(m)
         V.vopp_ctx_destroy(ctx)
