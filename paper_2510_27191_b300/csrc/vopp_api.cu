@@ -346,6 +346,7 @@ struct Job {
 struct StageBuild {
   int family;
   int level;
+  int kind = -1;              // leaf stages: the model of every plan in the launch
   std::vector<int> plans, levels;
   std::vector<long long> prefix;
   long long total = 0;
@@ -355,9 +356,9 @@ struct StageBuild {
 };
 
 // CTAs of a persistent leaf launch: every SM filled to the kernel's occupancy.
-int persistent_grid(vopp_ctx *c, size_t smem) {
+int persistent_grid(vopp_ctx *c, int kind, size_t smem) {
   int per_sm = 0;
-  if (leaf_occupancy(c->leaf_threads, smem, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (leaf_occupancy(kind, c->leaf_threads, smem, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
   return per_sm * c->sm_count;
 }
 
@@ -426,33 +427,39 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     s.total = acc;
     if (acc) stages.push_back(s);
   }
-  // Leaf stage: one launch per shared-memory class (powers of two of the node buffer), so
-  // that small-N plans are not held to the occupancy of the largest node buffer.
+  // Leaf stage: one launch per model and shared-memory class (powers of two of the node
+  // buffer), so that each model runs its own kernel and small-N plans are not held to the
+  // occupancy of the largest node buffer.
   {
-    std::vector<int> classes;
+    auto leaf_class = [&](const Job &j) {
+      const size_t b = leaf_smem_bytes(j.shape.kind, j.shape.N, j.shape.AW);
+      int cls = 0;
+      while (((size_t)1024 << cls) < b) ++cls;
+      return std::make_pair(cls, j.shape.kind);
+    };
+    std::vector<std::pair<int, int>> classes;
     for (int i : order_leaf)
       if (jobs[i].shape.D >= 1) {
-        const size_t b = leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW);
-        int cls = 0;
-        while (((size_t)1024 << cls) < b) ++cls;
-        if (std::find(classes.begin(), classes.end(), cls) == classes.end()) classes.push_back(cls);
+        const auto key = leaf_class(jobs[i]);
+        if (std::find(classes.begin(), classes.end(), key) == classes.end()) classes.push_back(key);
       }
-    std::sort(classes.begin(), classes.end(), std::greater<int>());
-    for (int cls : classes) {
+    std::sort(classes.begin(), classes.end(), [](const std::pair<int, int> &x,
+                                                 const std::pair<int, int> &y) {
+      return x.first != y.first ? x.first > y.first : x.second < y.second;
+    });
+    for (const auto &key : classes) {
       StageBuild s;
       s.family = F_LEAF;
       s.level = 0;
+      s.kind = key.second;
       long long acc = 0;
       for (int i : order_leaf) {
-        if (jobs[i].shape.D < 1) continue;
-        const size_t b = leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N, jobs[i].shape.AW);
-        int c2 = 0;
-        while (((size_t)1024 << c2) < b) ++c2;
-        if (c2 != cls) continue;
+        if (jobs[i].shape.D < 1 || leaf_class(jobs[i]) != key) continue;
         s.plans.push_back(i);
         s.prefix.push_back(acc);
         acc += nodes(jobs[i], jobs[i].shape.D - 1);
-        s.smem = std::max(s.smem, b);
+        s.smem = std::max(s.smem, leaf_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N,
+                                                  jobs[i].shape.AW));
       }
       s.prefix.push_back(acc);
       s.total = acc;
@@ -601,7 +608,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     StageBuild &sb = stages[k];
     if (sb.family == F_LEAF) {
       if (!c->leaf_persistent) sb.st.counter = nullptr;
-      grids[k] = c->leaf_persistent ? persistent_grid(c, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
+      grids[k] = c->leaf_persistent ? persistent_grid(c, sb.kind, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
     } else if (sb.family == F_EXPAND) {
       grids[k] = std::min<long long>(sb.total, c->grid_cap);
     } else {
@@ -618,7 +625,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       switch (sb.family) {
         case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
         case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, grids[k], stream); break;
-        case F_LEAF: e = launch_leaf(dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
+        case F_LEAF: e = launch_leaf(sb.kind, dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
       }
       if (timed) timed_end(c, tl);
       if (e != cudaSuccess) return fail(VOPP_E_CUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -644,6 +651,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   for (size_t k = 0; k < stages.size(); ++k) {
     const StageBuild &sb = stages[k];
     put(&sb.family, sizeof sb.family);
+    put(&sb.kind, sizeof sb.kind);
     put(&sb.total, sizeof sb.total);
     put(&sb.smem, sizeof sb.smem);
     put(&sb.maxN, sizeof sb.maxN);

@@ -39,9 +39,10 @@ cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream
 cudaError_t init_kernel_attributes();
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
                           long long grid, cudaStream_t s);
-cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                        int threads, long long grid, cudaStream_t s);
-cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm);
+// kind selects the model's leaf kernel (kNav, kGrid, kToy)
+cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
+                        size_t smem, int threads, long long grid, cudaStream_t s);
+cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
 
 }  // namespace vopp

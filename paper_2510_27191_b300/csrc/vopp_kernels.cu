@@ -672,7 +672,8 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 // Compile-time tuning of the leaf loop (results do not depend on them):
 //   VOPP_LEAF_CHUNK      Philox pairs per lane between two rescales of the running sums
 //   VOPP_ROUND_KEYS      1: Philox round keys held in registers for the whole branch
-//   VOPP_LEAF_MINBLOCKS  minimum resident leaf CTAs per SM requested from the compiler
+//   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
+//                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
 #endif
@@ -681,6 +682,9 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 #endif
 #ifndef VOPP_LEAF_MINBLOCKS
 #define VOPP_LEAF_MINBLOCKS 3
+#endif
+#ifndef VOPP_LEAF_GRID_MINBLOCKS
+#define VOPP_LEAF_GRID_MINBLOCKS 4
 #endif
 #ifndef VOPP_LEAF_CHUNK_PACKED
 #define VOPP_LEAF_CHUNK_PACKED 4
@@ -932,12 +936,16 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   __syncthreads();
 }
 
-#ifdef VOPP_LEAF_MAXNREG
-#define VOPP_LEAF_BOUNDS __maxnreg__(VOPP_LEAF_MAXNREG)
-#else
-#define VOPP_LEAF_BOUNDS __launch_bounds__(256, VOPP_LEAF_MINBLOCKS)
-#endif
-__global__ void VOPP_LEAF_BOUNDS k_leaf(const PlanDesc *plans, StageTable st, long long total) {
+// One leaf kernel per model, so that each gets its own register allocation and occupancy;
+// a launch covers the leaf items of every plan of that model in one shared-memory class.
+template <int K> struct LeafModel;
+template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMinBlocks = VOPP_LEAF_MINBLOCKS; };
+template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
+template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
+
+template <int K>
+__global__ void __launch_bounds__(256, LeafModel<K>::kMinBlocks)
+k_leaf(const PlanDesc *plans, StageTable st, long long total) {
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[32 * 5];
   __shared__ long long s_item;
@@ -954,11 +962,7 @@ __global__ void VOPP_LEAF_BOUNDS k_leaf(const PlanDesc *plans, StageTable st, lo
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
     const unsigned long long node = (unsigned long long)(item - st.prefix[pi]);
-    switch (P.kind) {
-      case kNav: leaf_item<NavModel>(P, node, smem, red); break;
-      case kGrid: leaf_item<GridModel>(P, node, smem, red); break;
-      default: leaf_item<ToyModel>(P, node, smem, red); break;
-    }
+    leaf_item<typename LeafModel<K>::type>(P, node, smem, red);
     if (st.counter) {
       if (threadIdx.x == 0) s_item = (long long)atomicAdd(st.counter, 1ull);
       __syncthreads();
@@ -1101,9 +1105,16 @@ cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream
 cudaError_t init_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kLeafSmemLimit);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kLeafSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf<kNav>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf<kGrid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf<kToy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemLimit);
+  return e;
 }
 
 // Launch with programmatic stream serialisation: the kernel may be scheduled while its
@@ -1129,13 +1140,23 @@ cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long tot
   return launch_pdl(k_expand, (unsigned)grid, 256u, expand_smem_bytes(maxN), s, d, st, total);
 }
 
-cudaError_t launch_leaf(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                        int threads, long long grid, cudaStream_t s) {
-  return launch_pdl(k_leaf, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
+                        size_t smem, int threads, long long grid, cudaStream_t s) {
+  switch (kind) {
+    case kNav: return launch_pdl(k_leaf<kNav>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+    case kGrid: return launch_pdl(k_leaf<kGrid>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+    case kToy: return launch_pdl(k_leaf<kToy>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t leaf_occupancy(int threads, size_t smem, int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf, threads, smem);
+cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_sm) {
+  switch (kind) {
+    case kNav: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kNav>, threads, smem);
+    case kGrid: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kGrid>, threads, smem);
+    case kToy: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kToy>, threads, smem);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s) {
