@@ -79,7 +79,8 @@ class PlanArgs(ctypes.Structure):
                 ("action", ctypes.c_int), ("v_root", ctypes.c_double),
                 ("q_root", ctypes.c_double * MAXA), ("policy", ctypes.c_double * MAXA),
                 ("near_threshold", ctypes.c_longlong), ("degenerate", ctypes.c_longlong),
-                ("particle_steps", ctypes.c_longlong)]
+                ("particle_steps", ctypes.c_longlong),
+                ("psi", _dp), ("psi_new_level", ctypes.c_int)]
 
 
 class BuResult(ctypes.Structure):
@@ -184,12 +185,16 @@ def level_offsets(A: int, W: int, D: int, P: int = 0) -> np.ndarray:
 
 def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: int,
          root_x=None, root_y=None, root_s=None, root_w=None, path=(), dump_levels: int = -1,
-         outputs: bool = True):
+         outputs: bool = True, psi=None, psi_new_level: int = 0):
     """Run one full-width plan (or the subtree below ``path``) and return a result dict.
 
     Per-level arrays are returned as lists indexed by level: ``V[l]`` (levels 0..D),
     ``Q[l]`` (levels 0..D-1, shape [n_l, A]), ``rbar/lomega/rep/obs/near[l]`` (levels 1..D,
     indexed by the branch's child node), and the particle dumps ``px/py/plw/ps[l]``.
+
+    ``psi`` (float64, updated in place, one row of A preferences per internal node,
+    concatenated by level) switches the backup to the persistent preference update of
+    Eq. 3; nodes at levels >= ``psi_new_level`` start from eta log pibar.
     """
     A = NUM_ACTIONS[model.kind]
     P = len(path)
@@ -200,6 +205,10 @@ def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: i
     for l, s in enumerate(path):
         io.path[l] = int(s)
     io.dump_levels = dump_levels
+    if psi is not None:
+        assert psi.dtype == np.float64 and psi.flags.c_contiguous and psi.size >= off[D] * A
+        io.psi = _ptr(psi, _dp)
+        io.psi_new_level = int(psi_new_level)
     arrs = {}
     if outputs:
         arrs = dict(V=np.full(tot, np.nan), Q=np.full(tot * A, np.nan), rbar=np.full(tot, np.nan),
@@ -241,6 +250,29 @@ def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: i
         for k in ("px", "py", "ps", "plw"):
             if k in arrs:
                 res[k] = [arrs[k][off[l] * N:off[l + 1] * N].reshape(-1, N) for l in range(nl)]
+    return res
+
+
+def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float, seed: int,
+                 root_x=None, root_y=None, root_s=None, root_w=None):
+    """Anytime iterative deepening (Alg. 1 planning loop): iterations k = 1..K each search
+    the full-width tree of depth k with the same random numbers and back it up with the
+    preference update of Eq. 3 on preferences that persist across iterations (the nodes of
+    level k-1 are new in iteration k).  Returns the last iteration's result dict, with the
+    root preferences ``psi_root`` and the per-iteration root Q values ``q_iters``."""
+    A = NUM_ACTIONS[model.kind]
+    off = level_offsets(A, W, K, 0)
+    psi = np.zeros(int(off[K]) * A)
+    q_iters, res = [], None
+    for k in range(1, K + 1):
+        res = plan(model, N, k, W, eta, gamma, seed, root_x=root_x, root_y=root_y,
+                   root_s=root_s, root_w=root_w, outputs=False, psi=psi, psi_new_level=k - 1)
+        if res["status"] != OK:
+            return res
+        q_iters.append(res["q_root"].copy())
+    res["psi_root"] = psi[:A].copy()
+    res["q_iters"] = q_iters
+    res["psi"] = psi
     return res
 
 

@@ -93,6 +93,12 @@ typedef struct {
   double q_root[ORC_MAXA];
   double policy[ORC_MAXA];
   long long near_threshold, degenerate, particle_steps;
+  /* anytime iterative deepening (Alg. 1 loop, Eq. 3): when psi is set, every internal node
+   * keeps its preferences Psi(n, .) in psi[(off_l + n) * A + a] across calls, and the backup
+   * updates them instead of using the one-pass closed form.  Nodes at levels >=
+   * psi_new_level start from Psi_0 = eta log pibar. */
+  double *psi;             /* [sum_{l<D} n_l * A] or NULL                                   */
+  int psi_new_level;
 } orc_plan_args;
 
 /* ------------------------------------------------------------------------------------ */
@@ -330,6 +336,25 @@ static double belief_value(const double *q, const double *lpi, int A, double eta
   return eta * log_sum_exp(z, A);
 }
 
+/* [L_eta Psi](b) = eta * log sum_a exp(Psi(b,a)/eta)   (Eq. 1 with the temperature eta) */
+static double lse_value(const double *psi, int A, double eta) {
+  double z[ORC_MAXA] = {0};
+  for (int a = 0; a < A; ++a) z[a] = psi[a] / eta;
+  return eta * log_sum_exp(z, A);
+}
+
+/* One preference update of a node (Eq. 3; Alg. 3 steps V_curr, Psi update, V):
+ *   V_curr = L Psi;  Psi <- Psi - V_curr + Q;  returns V = L Psi.
+ * A node that has no preferences yet starts from Psi_0 = eta log pibar. */
+static double preference_update(double *psi, const double *q, const double *lpi, int fresh,
+                                int A, double eta) {
+  if (fresh)
+    for (int a = 0; a < A; ++a) psi[a] = eta * lpi[a];
+  double vcur = lse_value(psi, A, eta);
+  for (int a = 0; a < A; ++a) psi[a] = psi[a] - vcur + q[a];
+  return lse_value(psi, A, eta);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Full-width tree recursion (Alg. 2 forward search, Alg. 3 backup), depth first.          */
 /* ------------------------------------------------------------------------------------ */
@@ -470,7 +495,17 @@ static double expand(orc_tree *t, int l, uint64_t gnode, long long lnode) {
     }
     q[a] = rsum / W + io->gamma * fut;
   }
-  double v = belief_value(q, lpi, A, io->eta);
+  /* Psi of this node: one-pass closed form, or the persistent preferences (anytime mode) */
+  double ps[ORC_MAXA];
+  double v;
+  if (io->psi) {
+    double *pn = io->psi + (t->off[l] + lnode) * A;
+    v = preference_update(pn, q, lpi, l >= io->psi_new_level, A, io->eta);
+    for (int a = 0; a < A; ++a) ps[a] = pn[a];
+  } else {
+    v = belief_value(q, lpi, A, io->eta);
+    for (int a = 0; a < A; ++a) ps[a] = q[a] + io->eta * lpi[a];
+  }
   if (io->Q) for (int a = 0; a < A; ++a) io->Q[(t->off[l] + lnode) * A + a] = q[a];
   if (io->V) io->V[t->off[l] + lnode] = v;
 
@@ -478,10 +513,9 @@ static double expand(orc_tree *t, int l, uint64_t gnode, long long lnode) {
     int best = 0;
     double bs = -INFINITY;
     for (int a = 0; a < A; ++a) {
-      double sc = q[a] + io->eta * lpi[a];
-      if (sc > bs) { bs = sc; best = a; }
+      if (ps[a] > bs) { bs = ps[a]; best = a; }
       io->q_root[a] = q[a];
-      io->policy[a] = exp(lpi[a] + q[a] / io->eta - v / io->eta);
+      io->policy[a] = exp((ps[a] - v) / io->eta);
     }
     io->action = best;
     io->v_root = v;
@@ -537,6 +571,7 @@ int orc_plan(const orc_model *m, const double *root_x, const double *root_y,
     return ORC_E_INVALID;
   for (int l = 0; l < t.P; ++l)
     if (io->path[l] < 0 || io->path[l] >= t.AW) return ORC_E_INVALID;
+  if (io->psi && (t.P > 0 || t.D < 1)) return ORC_E_INVALID;   /* anytime: whole trees, D >= 1 */
   orc_level_offsets(t.A, t.W, t.D, t.P, t.off);
   io->near_threshold = io->degenerate = io->particle_steps = 0;
   io->action = -1;

@@ -19,7 +19,7 @@ from scipy.special import logsumexp
 
 import oracle as O
 from paper_2510_27191_b300 import workloads as WL
-from tests.brute import soft_expectimax
+from tests.brute import porpp_anytime, soft_expectimax
 
 SEEDS = [0x0123456789ABCDEF, 1, 0xFFFFFFFFFFFFFFFF, 0x9E3779B97F4A7C15]
 
@@ -320,6 +320,59 @@ def test_toy2_enumerate_equals_brute_force_soft_expectimax(depth, eta, pi):
     np.testing.assert_allclose(r["q_root"], q, atol=1e-12)
     assert r["action"] == int(np.argmax(q + eta * lpi))
     assert np.exp(lpi + q / eta - v / eta) == pytest.approx(r["policy"], abs=1e-12)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+@pytest.mark.parametrize("eta", [0.1, 1.0, 5.0])
+@pytest.mark.parametrize("pi", [None, (0.7, 0.3)])
+def test_toy2_anytime_equals_brute_force_porpp_iteration(K, eta, pi):
+    """Anytime deepening with persistent preferences (Alg. 1 loop, Eq. 3) on the exact tree:
+    root preferences, value, last Q, policy and action equal the history-keyed brute force."""
+    b0 = np.array([0.6, 0.4])
+    kw = dict(branch_mode=O.ENUMERATE)
+    lpi = np.log([0.5, 0.5])
+    if pi is not None:
+        kw.update(pi_mode=O.PI_FIXED, pi_fixed=pi)
+        lpi = np.log(np.array(pi) / sum(pi))
+    m = O.make_model(O.TOY2, **kw)
+    r = O.plan_anytime(m, 2, K, 2, eta, 0.95, 42, root_s=np.array([0, 1]), root_w=b0)
+    assert r["status"] == O.OK
+    v, psi, q, qs = porpp_anytime(b0, K, eta, 0.95, lpi)
+    assert r["v_root"] == pytest.approx(v, abs=1e-11)
+    np.testing.assert_allclose(r["psi_root"], psi, atol=1e-11)
+    np.testing.assert_allclose(r["q_root"], q, atol=1e-11)
+    for qa, qb in zip(r["q_iters"], qs):
+        np.testing.assert_allclose(qa, qb, atol=1e-11)
+    assert r["action"] == int(np.argmax(psi))
+    np.testing.assert_allclose(r["policy"], np.exp((psi - v) / eta), atol=1e-12)
+    if K == 1:   # one iteration is the one-pass closed form
+        v1, q1 = soft_expectimax(b0, 1, eta, 0.95, lpi)
+        assert v == pytest.approx(v1, abs=1e-12)
+
+
+@pytest.mark.parametrize("kind", [O.NAV2D, O.GRID])
+def test_anytime_two_iterations_closed_form(kind):
+    """After two iterations the root preferences are eta log pibar + Q1 + Q2 - V1, with Q1,
+    V1 the one-pass depth-1 plan and Q2 the one-pass depth-2 root Q (the level-1 nodes are
+    new in the second iteration, so their values are one-pass values)."""
+    N, W, eta, gamma, seed = 48, 2, 0.8, 0.95, 77
+    if kind == O.NAV2D:
+        x, y, _ = WL.nav_root(N, 3)
+        m = O.make_model(O.NAV2D, pi_mode=O.PI_NAV_DIST, pi_temp=2.0)
+        kw = dict(root_x=x, root_y=y)
+    else:
+        s, _ = WL.grid_root(N, 3)
+        rx, ry = WL.grid_layout(1)
+        m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+        kw = dict(root_s=s)
+    r1 = O.plan(m, N, 1, W, eta, gamma, seed, outputs=False, **kw)
+    r2 = O.plan(m, N, 2, W, eta, gamma, seed, outputs=False, **kw)
+    ra = O.plan_anytime(m, N, 2, W, eta, gamma, seed, **kw)
+    lpi = np.log(r1["policy"]) - (r1["q_root"] - r1["v_root"]) / eta   # log pibar of the root
+    expect = eta * lpi + r1["q_root"] + r2["q_root"] - r1["v_root"]
+    np.testing.assert_allclose(ra["psi_root"], expect, rtol=1e-12, atol=1e-10)
+    np.testing.assert_allclose(ra["q_root"], r2["q_root"], rtol=1e-13)
+    assert ra["v_root"] == pytest.approx(eta * logsumexp(expect / eta), rel=1e-12)
 
 
 def test_toy2_small_eta_tends_to_hard_expectimax():
