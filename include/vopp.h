@@ -95,6 +95,8 @@ extern "C" {
 #define VOPP_FIELD_PS 8     /* int32  GRID/TOY2 s[node][N]  materialised levels            */
 #define VOPP_FIELD_PLW 9    /* float  log weight[node][N]   materialised levels            */
 #define VOPP_FIELD_MU 10    /* float  weighted mean particle [node][2] (VOPP_PI_NAV_DIST) */
+#define VOPP_FIELD_PSI 11   /* float  Psi[node][A] persistent preferences, levels 0..D-1,
+                               after vopp_plan_anytime / vopp_agent_plan_anytime only        */
 
 #define VOPP_MAX_ACTIONS 16
 #define VOPP_MAX_DEPTH 8
@@ -212,6 +214,24 @@ VOPP_API int vopp_plan(vopp_model *model, const void *root_states, const float *
               int32_t n_particles, int32_t depth, int32_t width, float eta, float gamma,
               const float *pi_bar, uint64_t seed, uint32_t ptr_flags, vopp_plan_result *out);
 
+/* ---- anytime plan (Alg. 1 planning loop with iterative deepening, Eq. 3) --------------- */
+/* Iterations k = 1, 2, ..., params->depth: iteration k searches the full-width tree of
+ * depth k with the plan's seed -- so a node has the same particles in every iteration --
+ * and backs it up with the preference update of Eq. 3 on preferences Psi(n, .) that persist
+ * across iterations (Alg. 3: V_curr = eta log sum_a exp(Psi/eta); Psi <- Psi - V_curr + Q;
+ * V = eta log sum_a exp(Psi/eta)); the nodes of level k-1 are new in iteration k and start
+ * from Psi_0 = eta log pibar.  Iteration 1 equals vopp_plan at depth 1.  A further
+ * iteration starts while the wall time since the call began is below budget_s (<= 0: no
+ * time limit, run to params->depth); the last iteration may overrun the budget.
+ * out: the last iteration's root Q, V = [L Psi](root), policy softmax(Psi/eta) and action
+ * argmax Psi (lowest index on ties); particle_steps counts the steps actually simulated
+ * (each iteration adds one materialised level, rebuilds the leaf kernel's node level and
+ * expands the leaves).  depth_reached (may be NULL) receives the last iteration's depth.
+ * Arguments, layouts, ownership and errors as vopp_plan; params->depth >= 1. */
+VOPP_API int vopp_plan_anytime(vopp_model *model, const void *root_states, const float *root_weights,
+                               int32_t n_particles, const vopp_plan_params *params, double budget_s,
+                               uint32_t ptr_flags, vopp_plan_result *out, int32_t *depth_reached);
+
 /* Copy `count` elements of a tree field of the most recent plan on this context, starting
  * at element `offset` of that level's array, into dst (host, or device with ptr_flags).
  * Valid until the next plan on the context. */
@@ -231,6 +251,9 @@ VOPP_API int vopp_grid_thresholds(uint64_t *thr, int32_t n);
 VOPP_API int vopp_agent_create(vopp_model *model, const void *states, const float *weights, int32_t n,
                       uint64_t seed, uint32_t ptr_flags, vopp_agent **out);
 VOPP_API int vopp_agent_plan(vopp_agent *agent, const vopp_plan_params *params, vopp_plan_result *out);
+/* vopp_plan_anytime from the agent's particles. */
+VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *params, double budget_s,
+                                     vopp_plan_result *out, int32_t *depth_reached);
 /* tau(b, a, o): propagate every particle under `action` (Philox purpose 3, time step t of
  * the agent), reweight by Z(obs | s', a), resample systematically when ESS < N/2.  obs is a
  * host pointer: NAV2D float[2], GRID/TOY2 int32[1].  On VOPP_E_DEGENERATE (every particle

@@ -254,25 +254,28 @@ def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: i
 
 
 def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float, seed: int,
-                 root_x=None, root_y=None, root_s=None, root_w=None):
+                 root_x=None, root_y=None, root_s=None, root_w=None, outputs: bool = False):
     """Anytime iterative deepening (Alg. 1 planning loop): iterations k = 1..K each search
     the full-width tree of depth k with the same random numbers and back it up with the
     preference update of Eq. 3 on preferences that persist across iterations (the nodes of
-    level k-1 are new in iteration k).  Returns the last iteration's result dict, with the
-    root preferences ``psi_root`` and the per-iteration root Q values ``q_iters``."""
+    level k-1 are new in iteration k).  Returns the last iteration's result dict (with the
+    per-level arrays of ``plan`` when ``outputs``), the root preferences ``psi_root``, the
+    per-iteration root Q values ``q_iters`` and the preferences of every internal node,
+    ``psi_levels[l]`` of shape [n_l, A]."""
     A = NUM_ACTIONS[model.kind]
     off = level_offsets(A, W, K, 0)
     psi = np.zeros(int(off[K]) * A)
     q_iters, res = [], None
     for k in range(1, K + 1):
         res = plan(model, N, k, W, eta, gamma, seed, root_x=root_x, root_y=root_y,
-                   root_s=root_s, root_w=root_w, outputs=False, psi=psi, psi_new_level=k - 1)
+                   root_s=root_s, root_w=root_w, outputs=outputs and k == K, psi=psi,
+                   psi_new_level=k - 1)
         if res["status"] != OK:
             return res
         q_iters.append(res["q_root"].copy())
     res["psi_root"] = psi[:A].copy()
     res["q_iters"] = q_iters
-    res["psi"] = psi
+    res["psi_levels"] = [psi[off[l] * A:off[l + 1] * A].reshape(-1, A) for l in range(K)]
     return res
 
 

@@ -170,7 +170,7 @@ struct PlanLayout {
   size_t bytes = 0;
   size_t px[kMaxDepth], py[kMaxDepth], plw[kMaxDepth], ps[kMaxDepth];
   size_t rbar[kMaxDepth + 1], lom[kMaxDepth + 1], V[kMaxDepth + 1], Q[kMaxDepth],
-      mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1], cnt[kMaxDepth];
+      mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1], cnt[kMaxDepth], psi[kMaxDepth];
 };
 
 constexpr size_t kNone = ~(size_t)0;
@@ -191,9 +191,11 @@ PlanShape make_shape(const vopp_model *m, int N, int D, int W, const vopp_ctx *c
   return s;
 }
 
-PlanLayout make_layout(const PlanShape &s) {
+// psi: also allocate the persistent preferences of every internal level (anytime plans).
+PlanLayout make_layout(const PlanShape &s, bool psi = false) {
   PlanLayout L;
-  for (int i = 0; i < kMaxDepth; ++i) L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = L.cnt[i] = kNone;
+  for (int i = 0; i < kMaxDepth; ++i)
+    L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = L.cnt[i] = L.psi[i] = kNone;
   for (int i = 0; i <= kMaxDepth; ++i) L.rbar[i] = L.lom[i] = L.V[i] = L.rep[i] = L.obs[i] = kNone;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -211,6 +213,7 @@ PlanLayout make_layout(const PlanShape &s) {
     if (node_level) L.Q[l] = take(4 * nodes * s.A);
     if (node_level && s.pi_mode == kPiNavDist) L.mu[l] = take(8 * nodes);
     if (l <= s.D - 2) L.cnt[l] = take(4 * nodes);
+    if (psi && l < s.D) L.psi[l] = take(4 * nodes * s.A);
     if (l >= 1 && keep) { L.rbar[l] = take(4 * nodes); L.lom[l] = take(4 * nodes); }
     if (l >= 1 && keep && s.keep_debug) { L.rep[l] = take(4 * nodes); L.obs[l] = take(8 * nodes); }
   }
@@ -336,6 +339,8 @@ struct Job {
   PlanShape shape;
   PlanLayout lay;
   size_t arena_off;
+  int first_expand = 0;     // levels 1..first_expand are already materialised (anytime)
+  int psi_new_level = 0;    // anytime: levels >= this start from Psi_0
   const void *states;
   const float *weights;
   const float *log_weights;   // device log weights (agents)
@@ -415,7 +420,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     s.level = l;
     long long acc = 0;
     for (int i : order_exp) {
-      if (jobs[i].shape.mat_top > l) {
+      if (jobs[i].shape.mat_top > l && l >= jobs[i].first_expand) {
         s.plans.push_back(i);
         s.levels.push_back(l);
         s.prefix.push_back(acc);
@@ -538,7 +543,9 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       P.px[l] = fp(L.px[l]); P.py[l] = fp(L.py[l]); P.plw[l] = fp(L.plw[l]); P.ps[l] = ip(L.ps[l]);
       P.Q[l] = fp(L.Q[l]); P.mu[l] = fp(L.mu[l]);
       P.cnt[l] = L.cnt[l] == kNone ? nullptr : reinterpret_cast<unsigned int *>(base + L.cnt[l]);
+      P.psi[l] = fp(L.psi[l]);
     }
+    P.psi_new_level = j.psi_new_level;
     for (int l = 0; l <= kMaxDepth; ++l) {
       P.rbar[l] = fp(L.rbar[l]); P.lom[l] = fp(L.lom[l]); P.V[l] = fp(L.V[l]);
       P.rep[l] = ip(L.rep[l]); P.obs[l] = fp(L.obs[l]);
@@ -755,6 +762,56 @@ int make_job(vopp_ctx *c, vopp_model *m, const void *states, const float *weight
   j.log_weights = nullptr;
   j.ptr_flags = ptr_flags;
   j.p = p;
+  return VOPP_OK;
+}
+
+// Anytime planning loop (Alg. 1): iterations k = 1, 2, ... each search the full-width tree
+// of depth k with the plan's keys (so every node keeps its particle set from one iteration
+// to the next) and back it up with the preference update of Eq. 3 on preferences that
+// persist in the arena.  Iteration k materialises only the one level it adds above the leaf
+// kernel's node level; the others are already in place.  The next iteration starts while
+// the elapsed time is below budget_s (<= 0: no time limit) and k < the maximum depth.
+int run_anytime(vopp_ctx *c, Job &base, double budget_s, vopp_plan_result *out, int *depth_out) {
+  const int K = base.p.depth;
+  if (K < 1) return fail(VOPP_E_INVALID, "anytime planning needs a maximum depth >= 1");
+  if (!(budget_s == budget_s)) return fail(VOPP_E_INVALID, "budget is NaN");
+  base.lay = make_layout(base.shape, true);     // the depth-K arrays, shared by every iteration
+  std::vector<Job> jobs(1, base);
+  int rc = ensure_arena(c, place_jobs(jobs));
+  if (rc) return rc;
+  c->slot.stream = c->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const unsigned long long N = (unsigned long long)base.shape.N, AW = base.shape.AW;
+  unsigned long long steps = 0, nodes = 1;
+  int prev_mat = 0, done = 0;
+  vopp_plan_result res;
+  for (int k = 1; k <= K; ++k) {
+    Job &j = jobs[0];
+    j.shape = make_shape(j.model, base.shape.N, k, base.shape.W, c);
+    j.first_expand = prev_mat;
+    j.psi_new_level = k - 1;
+    j.p.depth = k;
+    rc = enqueue_jobs(c, c->slot, c->arena, jobs, c->timing, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    timed_collect(c);
+    rc = collect_results(c, c->slot, jobs, &res, nullptr, true);
+    if (rc) return rc;
+    // particle-steps simulated by this iteration: the newly materialised levels, the node
+    // level the leaf kernel builds in shared memory, and the leaves
+    for (int l = prev_mat + 1; l <= j.shape.mat_top; ++l) steps += ipow(AW, l) * N;
+    if (j.shape.leaf_gen) steps += ipow(AW, k - 1) * N;
+    steps += ipow(AW, k) * N;
+    nodes += ipow(AW, k);
+    prev_mat = j.shape.mat_top;
+    done = k;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (budget_s > 0.0 && el >= budget_s) break;
+  }
+  res.particle_steps = steps;
+  res.nodes = nodes;
+  *out = res;
+  if (depth_out) *depth_out = done;
   return VOPP_OK;
 }
 
@@ -1000,6 +1057,18 @@ int vopp_plan(vopp_model *m, const void *root_states, const float *root_weights,
   return run_jobs(c, jobs, out, nullptr);
 }
 
+int vopp_plan_anytime(vopp_model *m, const void *root_states, const float *root_weights,
+                      int32_t N, const vopp_plan_params *p, double budget_s, uint32_t ptr_flags,
+                      vopp_plan_result *out, int32_t *depth_reached) {
+  if (!m || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = m->ctx;
+  Job j;
+  int rc = make_job(c, m, root_states, root_weights, N, *p, ptr_flags, j);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  return run_anytime(c, j, budget_s, out, depth_reached);
+}
+
 int vopp_plan_batch(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, vopp_plan_result *outs) {
   if (!c || !reqs || !outs || n < 1) return fail(VOPP_E_INVALID, "bad batch arguments");
   std::vector<Job> jobs(n);
@@ -1126,6 +1195,7 @@ int vopp_tree_read_plan(vopp_ctx *c, int32_t plan, int32_t field, int32_t level,
     case VOPP_FIELD_PS: src = lv < kMaxDepth ? P.ps[lv] : nullptr; len = nodes * P.N; break;
     case VOPP_FIELD_PLW: src = lv < kMaxDepth ? P.plw[lv] : nullptr; len = nodes * P.N; break;
     case VOPP_FIELD_MU: src = lv < kMaxDepth ? P.mu[lv] : nullptr; len = 2 * nodes; break;
+    case VOPP_FIELD_PSI: src = lv < kMaxDepth ? P.psi[lv] : nullptr; len = nodes * P.A; break;
     default: return fail(VOPP_E_INVALID, "field %d", field);
   }
   if (!src) return fail(VOPP_E_INVALID, "field %d not kept at level %d", field, level);
@@ -1213,6 +1283,19 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
   jobs[0].log_weights = g->lw;
   cudaSetDevice(c->device);
   return run_jobs(c, jobs, out, nullptr);
+}
+
+int vopp_agent_plan_anytime(vopp_agent *g, const vopp_plan_params *p, double budget_s,
+                            vopp_plan_result *out, int32_t *depth_reached) {
+  if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = g->model->ctx;
+  Job j;
+  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  int rc = make_job(c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, j);
+  if (rc) return rc;
+  j.log_weights = g->lw;
+  cudaSetDevice(c->device);
+  return run_anytime(c, j, budget_s, out, depth_reached);
 }
 
 int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,

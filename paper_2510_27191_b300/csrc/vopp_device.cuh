@@ -81,7 +81,12 @@ struct PlanDesc {
   float *mu[kMaxDepth];       // weighted mean particle (x,y) per node, kPiNavDist only
   int *rep[kMaxDepth + 1];
   float *obs[kMaxDepth + 1];  // 2 floats per child
-  unsigned int *cnt[kMaxDepth];  // per node of levels 0..D-2: children finished (backup climb)
+  unsigned int *cnt[kMaxDepth];  // per node of levels 0..D-2: children finished (backup climb),
+                                 // counted modulo A*W so that later iterations need no reset
+  // anytime iterative deepening: preferences Psi [nodes][A] per internal level that persist
+  // across iterations (null: one-pass closed form); levels >= psi_new_level are new
+  float *psi[kMaxDepth];
+  int psi_new_level;
   DevResult *result;
 };
 

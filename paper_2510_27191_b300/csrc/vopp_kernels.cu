@@ -399,7 +399,8 @@ __device__ __forceinline__ float ld_stat(const float *p) {
 template <bool kL2>
 __device__ __forceinline__ float node_backup_warp(const PlanDesc &P, const float *rb,
                                                   const float *lo, const float *vc, float2 mu,
-                                                  float &q_lane) {
+                                                  float &q_lane, float *psi_node = nullptr,
+                                                  bool fresh = false, float *psi_lane = nullptr) {
   const int lane = threadIdx.x & 31, A = P.A, W = P.W;
   float q = 0.f, z = -CUDART_INF_F;
   if (lane < A) {
@@ -422,9 +423,23 @@ __device__ __forceinline__ float node_backup_warp(const PlanDesc &P, const float
       atomicAdd(&P.result->degenerate, 1u);
     }
     q = rs / (float)W + P.gamma * fut;
-    z = log_pibar(P, mu, lane) + q * P.inv_eta;
+    if (!psi_node) z = log_pibar(P, mu, lane) + q * P.inv_eta;
   }
   q_lane = q;
+  if (psi_node) {
+    // Eq. 3 on persistent preferences: V_curr = L Psi, Psi <- Psi - V_curr + Q, V = L Psi
+    // (a new node starts from Psi_0 = eta log pibar)
+    float ps = -CUDART_INF_F;
+    if (lane < A) ps = fresh ? P.eta * log_pibar(P, mu, lane) : psi_node[lane];
+    const float zc = ps * P.inv_eta;
+    const float zcm = warp_max(zc);
+    const float ec = warp_sum((lane < A && zc > -CUDART_INF_F) ? __expf(zc - zcm) : 0.f);
+    const float vcur = P.eta * (zcm + __logf(ec));
+    const float pn = ps - vcur + q;          // -inf (pibar = 0) stays -inf
+    if (lane < A) psi_node[lane] = pn;
+    if (psi_lane) *psi_lane = pn;
+    z = (lane < A) ? pn * P.inv_eta : -CUDART_INF_F;
+  }
   const float zm = warp_max(z);
   float e = (lane < A && z > -CUDART_INF_F) ? __expf(z - zm) : 0.f;
   e = warp_sum(e);
@@ -440,10 +455,12 @@ __device__ void root_backup_warp(const PlanDesc &P) {
   const int lane = threadIdx.x & 31, A = P.A;
   float2 mu = make_float2(0.f, 0.f);
   if (P.pi_mode == kPiNavDist) mu = make_float2(__ldcg(P.mu[0]), __ldcg(P.mu[0] + 1));
-  float q;
-  const float v = node_backup_warp<true>(P, P.rbar[1], P.lom[1], P.V[1], mu, q);
+  float q, ps = -CUDART_INF_F;
+  const float v = node_backup_warp<true>(P, P.rbar[1], P.lom[1], P.V[1], mu, q, P.psi[0],
+                                         P.psi_new_level <= 0, &ps);
   const float lp = (lane < A) ? log_pibar(P, mu, lane) : -CUDART_INF_F;
-  float sc = (lane < A) ? q + P.eta * lp : -CUDART_INF_F;
+  // Alg. 1: the action maximising Psi (closed form: Q + eta log pibar)
+  float sc = (lane < A) ? (P.psi[0] ? ps : q + P.eta * lp) : -CUDART_INF_F;
   int best = (lane < A) ? lane : 1 << 30;
   for (int o = 16; o > 0; o >>= 1) {
     const float sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
@@ -453,7 +470,7 @@ __device__ void root_backup_warp(const PlanDesc &P) {
   DevResult *R = P.result;
   if (lane < A) {
     R->q[lane] = q;
-    R->policy[lane] = __expf(lp + (q - v) * P.inv_eta);
+    R->policy[lane] = P.psi[0] ? __expf((ps - v) * P.inv_eta) : __expf(lp + (q - v) * P.inv_eta);
     P.Q[0][lane] = q;
   }
   if (lane == 0) {
@@ -492,12 +509,26 @@ __device__ void root_backup_warp_fp64(const PlanDesc &P) {
     lp = (double)log_pibar(P, mu, lane);
     z = lp + q / (double)P.eta;
   }
-  double zm = z;
-  for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
-  double e = (lane < A && z > -CUDART_INF) ? exp(z - zm) : 0.0;
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  const double v = (double)P.eta * (zm + log(e));
-  double sc = (lane < A) ? q + (double)P.eta * lp : -CUDART_INF;
+  auto lse = [&](double x) {     // eta * log sum over the warp's lanes of exp(x), x = Psi/eta
+    double xm = x;
+    for (int o = 16; o > 0; o >>= 1) xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+    double ex = (lane < A && x > -CUDART_INF) ? exp(x - xm) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, o);
+    return (double)P.eta * (xm + log(ex));
+  };
+  double ps = -CUDART_INF;
+  if (P.psi[0]) {   // Eq. 3 on the persistent root preferences
+    if (lane < A)
+      ps = (P.psi_new_level <= 0) ? (double)P.eta * lp : (double)P.psi[0][lane];
+    const double vcur = lse((lane < A) ? ps / (double)P.eta : -CUDART_INF);
+    if (lane < A) {
+      ps = ps - vcur + q;
+      P.psi[0][lane] = (float)ps;
+    }
+    z = (lane < A) ? ps / (double)P.eta : -CUDART_INF;
+  }
+  const double v = lse(z);
+  double sc = (lane < A) ? (P.psi[0] ? ps : q + (double)P.eta * lp) : -CUDART_INF;
   int best = (lane < A) ? lane : 1 << 30;
   for (int o = 16; o > 0; o >>= 1) {
     const double sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
@@ -507,7 +538,7 @@ __device__ void root_backup_warp_fp64(const PlanDesc &P) {
   DevResult *R = P.result;
   if (lane < A) {
     R->q[lane] = q;
-    R->policy[lane] = exp(lp + (q - v) / (double)P.eta);
+    R->policy[lane] = P.psi[0] ? exp((ps - v) / (double)P.eta) : exp(lp + (q - v) / (double)P.eta);
     P.Q[0][lane] = (float)q;
   }
   if (lane == 0) {
@@ -532,7 +563,7 @@ __device__ void climb_warp(const PlanDesc &P, int l, unsigned long long node) {
     unsigned int old = 0;
     if (lane == 0) old = atomicAdd(P.cnt[lev - 1] + p, 1u);
     old = __shfl_sync(0xffffffffu, old, 0);
-    if (old != (unsigned int)(AW - 1)) return;
+    if ((old + 1u) % (unsigned int)AW != 0u) return;
     __threadfence();
     if (lev - 1 == 0) {
       root_backup_warp(P);
@@ -542,7 +573,9 @@ __device__ void climb_warp(const PlanDesc &P, int l, unsigned long long node) {
     float2 mu = make_float2(0.f, 0.f);
     if (P.pi_mode == kPiNavDist) mu = make_float2(__ldcg(P.mu[lev - 1] + 2 * p), __ldcg(P.mu[lev - 1] + 2 * p + 1));
     float q;
-    const float v = node_backup_warp<true>(P, P.rbar[lev] + c0, P.lom[lev] + c0, P.V[lev] + c0, mu, q);
+    float *psi = P.psi[lev - 1] ? P.psi[lev - 1] + p * A : nullptr;
+    const float v = node_backup_warp<true>(P, P.rbar[lev] + c0, P.lom[lev] + c0, P.V[lev] + c0, mu, q,
+                                           psi, lev - 1 >= P.psi_new_level);
     if (lane < A) P.Q[lev - 1][p * A + lane] = q;
     if (lane == 0) P.V[lev - 1][p] = v;
     n = p;
@@ -922,7 +955,10 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
 
   if (wid == 0) {
     float q;
-    const float v = node_backup_warp<false>(P, sm_rb, sm_lo, sm_v, s_mu, q);
+    // (at the root, depth 1, the preferences are updated once, by root_backup_warp)
+    float *psi = (l > 0 && P.psi[l]) ? P.psi[l] + node * P.A : nullptr;
+    const float v = node_backup_warp<false>(P, sm_rb, sm_lo, sm_v, s_mu, q, psi,
+                                            l >= P.psi_new_level);
     const int lane = threadIdx.x & 31;
     if (lane < P.A) P.Q[l][node * P.A + lane] = q;
     if (lane == 0) P.V[l][node] = v;

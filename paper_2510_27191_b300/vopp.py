@@ -25,7 +25,8 @@ VOPP_PTR_DEVICE = 1
 VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT = 1, 2
 VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 (VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
- VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU) = range(11)
+ VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU,
+ VOPP_FIELD_PSI) = range(12)
 VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP = 1, 2, 3
 VOPP_OPT_PERSISTENT = 5
 VOPP_OPT_FP64_ROOT = 6
@@ -144,6 +145,12 @@ def _load():
         "vopp_last_error": ([], ctypes.c_char_p),
         "vopp_version": ([], ctypes.c_char_p),
         "vopp_pipe_rates": ([ctypes.c_int, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "vopp_plan_anytime": ([vp, vp, vp, i32, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
+                               u32, ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
+                              ctypes.c_int),
+        "vopp_agent_plan_anytime": ([vp, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
+                                     ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
+                                    ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -276,6 +283,37 @@ def vopp_plan(model: int, root_states, root_weights, n_particles: int, depth: in
                         seed & 0xFFFFFFFFFFFFFFFF, ptr_flags, ctypes.byref(r)))
     del keep1, keep2
     return _result_dict(r, vopp_model_num_actions(model))
+
+
+def vopp_plan_anytime(model: int, root_states, root_weights, n_particles: int, max_depth: int,
+                      width: int, eta: float, gamma: float, seed: int, budget_s: float = 0.0,
+                      pi_bar=None) -> dict:
+    """Anytime plan (iterative deepening with persistent preferences); the result dict
+    carries ``depth_reached``."""
+    sp, sdev, k1 = _addr(root_states)
+    wp, _, k2 = _addr(root_weights)
+    p, k3 = make_params(max_depth, width, eta, gamma, seed, pi_bar)
+    r = vopp_plan_result()
+    d = ctypes.c_int32()
+    check(lib.vopp_plan_anytime(model, sp, wp, n_particles, ctypes.byref(p), float(budget_s),
+                                VOPP_PTR_DEVICE if sdev else 0, ctypes.byref(r), ctypes.byref(d)))
+    del k1, k2, k3
+    out = _result_dict(r, vopp_model_num_actions(model))
+    out["depth_reached"] = d.value
+    return out
+
+
+def vopp_agent_plan_anytime(agent: int, model: int, max_depth: int, width: int, eta: float,
+                            gamma: float, seed: int, budget_s: float = 0.0, pi_bar=None) -> dict:
+    p, keep = make_params(max_depth, width, eta, gamma, seed, pi_bar)
+    r = vopp_plan_result()
+    d = ctypes.c_int32()
+    check(lib.vopp_agent_plan_anytime(agent, ctypes.byref(p), float(budget_s), ctypes.byref(r),
+                                      ctypes.byref(d)))
+    del keep
+    out = _result_dict(r, vopp_model_num_actions(model))
+    out["depth_reached"] = d.value
+    return out
 
 
 def vopp_tree_read(ctx: int, field: int, level: int, count: int, offset: int = 0, plan: int = 0,
