@@ -279,6 +279,24 @@ def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float,
     return res
 
 
+def env_step(model: Model, state, action: int, seed: int, t: int):
+    """One step of the true state (closed loop, Alg. 1): returns (status, next state,
+    observation, reward, terminal); state is (x, y) for NAV2D, an int for GRID / TOY2."""
+    if model.kind == NAV2D:
+        x, y, s = ctypes.c_double(state[0]), ctypes.c_double(state[1]), ctypes.c_int32(0)
+    else:
+        x, y, s = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(int(state))
+    o = (ctypes.c_double * 2)()
+    r = ctypes.c_double()
+    term = ctypes.c_int()
+    rc = lib().orc_env_step(ctypes.byref(model), ctypes.byref(x), ctypes.byref(y),
+                            ctypes.byref(s), int(action), ctypes.c_uint64(seed & (2**64 - 1)),
+                            ctypes.c_uint64(t), o, ctypes.byref(r), ctypes.byref(term))
+    nxt = (x.value, y.value) if model.kind == NAV2D else s.value
+    obs = (o[0], o[1]) if model.kind == NAV2D else int(o[0])
+    return rc, nxt, obs, r.value, bool(term.value)
+
+
 def belief_update(model: Model, lw, action: int, obs, seed: int, t: int, x=None, y=None, s=None):
     """SIR update in place on float64 copies; returns (status, dict of new arrays)."""
     N = len(lw)

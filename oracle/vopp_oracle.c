@@ -39,6 +39,8 @@
  *   purpose 1: observation draw of a branch (words 0,1 -> noise / sense outcome, word 2 -> j)
  *   purpose 3: belief-update transition of pair idx, c1 = 0, node = time step t
  *   purpose 4: belief-update resampling offset, idx 0, c1 = 0, node = t
+ *   purpose 5: environment transition of the true state, idx 0, c1 = 0, node = t
+ *   purpose 6: environment observation, idx 0, c1 = 0, node = t (words 0,1 as purpose 1)
  *   uniform:   u = (2 (x >> 9) + 1) * 2^-24, exactly representable in FP32 and FP64.
  */
 #include <math.h>
@@ -761,6 +763,28 @@ double orc_nav_loglik(double sx, double sy, double ox, double oy) {
   pstate sp = {sx, sy, 0};
   double o[2] = {ox, oy};
   return model_loglik(&m, &sp, 0, o);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Environment of the closed loop (Alg. 1: execute the action, perceive the observation):  */
+/* the true state steps under the model's own transition and observation processes, with   */
+/* its own random numbers (purposes 5 and 6, node = time step t).                          */
+/* ------------------------------------------------------------------------------------ */
+int orc_env_step(const orc_model *m, double *x, double *y, int32_t *s, int a, uint64_t seed,
+                 uint64_t t, double obs[2], double *reward, int *terminal) {
+  if (a < 0 || a >= orc_num_actions(m->kind)) return ORC_E_INVALID;
+  pstate in = {*x, *y, *s}, out;
+  long long near = 0;
+  uint32_t w[4];
+  draw(seed, 0, 5, 0, 0, 0, t, w);
+  model_step(m, &in, a, w[0], w[1], &out, reward, &near);
+  draw(seed, 0, 6, 0, 0, 0, t, w);
+  model_draw_obs(m, &out, a, w[0], w[1], obs);
+  *terminal = model_is_terminal(m, &out);
+  *x = out.x;
+  *y = out.y;
+  *s = out.s;
+  return ORC_OK;
 }
 
 double orc_belief_value(const double *q, const double *lpi, int A, double eta) {

@@ -541,3 +541,62 @@ def test_belief_update_zero_likelihood_is_degenerate():
     s = WL.pack_grid_state(np.zeros(8, dtype=np.int64), rx[0], ry[0])   # rock 0 bad everywhere
     rc, _ = O.belief_update(m, np.full(8, -math.log(8)), 5, 1, seed=1, t=0, s=s)
     assert rc == O.E_DEGENERATE
+
+
+# ----------------------------------------------------------------------------------------
+# Environment of the closed loop: the true state follows the model's own processes.
+# ----------------------------------------------------------------------------------------
+def test_env_step_nav_noise_is_the_model_noise():
+    """Transition noise N(0, 0.1^2) per axis around s + delta_a, observation noise
+    N(0, sigma_o(x')^2) around s' (sigma_o(x) = 0.5 |x - 9| + 0.05), independent over t."""
+    m = O.make_model(O.NAV2D)
+    dx, dy, ex, ey = [], [], [], []
+    for t in range(3000):
+        rc, (x, y), (ox, oy), r, term = O.env_step(m, (5.0, 5.0), 2, 0xABCDEF, t)
+        assert rc == O.OK and r == -1.0 and not term
+        dx.append((x - 5.0) / 0.1)
+        dy.append((y - 6.0) / 0.1)
+        sg = 0.5 * abs(x - 9.0) + 0.05
+        ex.append((ox - x) / sg)
+        ey.append((oy - y) / sg)
+    for v in (dx, dy, ex, ey):
+        assert stats.kstest(v, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(dx[:-1], dx[1:])[0, 1]) < 0.08       # fresh numbers every step
+    assert abs(np.corrcoef(dx, ex)[0, 1]) < 0.08                 # transition vs observation
+
+
+def test_env_step_nav_goal_and_absorbing():
+    m = O.make_model(O.NAV2D)
+    hits = 0
+    for t in range(400):
+        rc, (x, y), _, r, term = O.env_step(m, (1.05, 0.0), 1, 7, t)   # move -x into the disc
+        if term:
+            hits += 1
+            assert r == 100.0 and x * x + y * y <= 0.25
+            rc, (x2, y2), _, r2, term2 = O.env_step(m, (x, y), 0, 7, t + 1)
+            assert (x2, y2) == (x, y) and r2 == 0.0 and term2      # absorbing
+        else:
+            assert r == -1.0
+    assert hits > 100
+
+
+def test_env_step_grid_sense_accuracy_and_moves():
+    """Sense outcomes are correct with probability acc(d) = 0.5 + 0.5 exp(-d/4); moves are
+    deterministic and exiting east is terminal with +10."""
+    rx, ry = WL.grid_layout(1)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    bits = 0b10110010
+    s0 = int(WL.pack_grid_state(np.array([bits]), 0, 5)[0])
+    for rock in (0, 3, 7):
+        d = math.hypot(rx[rock] - 0, ry[rock] - 5)
+        acc = 0.5 + 0.5 * math.exp(-d / 4.0)
+        good = (bits >> rock) & 1
+        n, ok = 4000, 0
+        for t in range(n):
+            rc, s1, o, r, term = O.env_step(m, s0, 5 + rock, 99, t)
+            assert s1 == s0 and r == 0.0 and not term and o in (1, 2)
+            ok += (o == 1) == bool(good)
+        assert stats.binomtest(ok, n, acc).pvalue > 1e-3
+    s = int(WL.pack_grid_state(np.array([bits]), 10, 5)[0])
+    rc, s1, o, r, term = O.env_step(m, s, 0, 99, 0)
+    assert term and r == 10.0 and o == 0
