@@ -260,6 +260,44 @@ VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *
  * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
 VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out);
+/* ---- closed loop (Alg. 1: plan, execute, perceive, update the belief) ---------------- */
+/* The environment: a true state held on the device as a single particle, stepped by the
+ * model's own transition and observation processes with random numbers of its own (Philox
+ * key = seed; purpose 5 transition words 0,1 and purpose 6 observation words 0,1; node word
+ * = the environment's step count t, starting at 0).  state: host NAV2D float[2] (x, y),
+ * GRID/TOY2 int32[1]; copied at creation.  Paper: Alg. 1 "execute action, perceive
+ * observation"; the paper's environments are simulators of the same models. */
+typedef struct vopp_env vopp_env;
+VOPP_API int vopp_env_create(vopp_model *model, const void *state, uint64_t seed, vopp_env **out);
+/* One step under `action`: obs receives the observation (host NAV2D float[2], GRID/TOY2
+ * int32[1]), reward and terminal (1 when the new state is terminal; terminal states are
+ * absorbing with reward 0) may be NULL.  VOPP_E_INVALID for an action outside [0, A). */
+VOPP_API int vopp_env_step(vopp_env *env, int32_t action, void *obs, float *reward, int32_t *terminal);
+/* Copy the true state to the host (same layout as at creation). */
+VOPP_API int vopp_env_get_state(vopp_env *env, void *state);
+VOPP_API void vopp_env_destroy(vopp_env *env);
+
+typedef struct {
+  int32_t steps;             /* actions executed                                          */
+  int32_t terminated;        /* 1: the true state reached a terminal state                */
+  int32_t status;            /* VOPP_OK, or the error that ended the episode early        */
+  int32_t min_depth;         /* smallest search depth reached by a plan (anytime budgets) */
+  double total_reward;       /* sum_t r_t                                                 */
+  double discounted_return;  /* sum_t gamma^t r_t                                         */
+  uint64_t particle_steps;   /* planning particle-steps over the episode                  */
+  double plan_seconds;       /* wall time spent planning                                  */
+} vopp_episode_result;
+/* Run one episode of at most max_steps: at step t plan from the agent's belief with
+ * params (seed params->seed + t; one full-width plan of params->depth, or with anytime != 0
+ * the anytime plan up to params->depth within budget_s), execute the chosen action in env,
+ * stop if the true state is terminal, else update the belief with the observation
+ * (vopp_belief_update).  actions / rewards: optional host arrays [max_steps].  An error of a
+ * step (e.g. VOPP_E_DEGENERATE: the observation has zero likelihood under every particle)
+ * ends the episode; it is returned and recorded in out->status with the steps done so far. */
+VOPP_API int vopp_run_episode(vopp_agent *agent, vopp_env *env, const vopp_plan_params *params,
+                              int32_t max_steps, int32_t anytime, double budget_s,
+                              vopp_episode_result *out, int32_t *actions, float *rewards);
+
 /* Copy the agent's particles (NAV2D x then y as float[2N]; GRID/TOY2 int32[N]) and
  * normalised log weights out; ancestors (int32[N], may be NULL) of the last update. */
 VOPP_API int vopp_agent_get_particles(vopp_agent *agent, void *states, float *log_weights,

@@ -142,6 +142,15 @@ struct vopp_model {
   int A = 0;
 };
 
+struct vopp_env {
+  vopp_model *model = nullptr;
+  uint64_t seed = 0;
+  unsigned long long t = 0;
+  float *xy = nullptr;                  // NAV2D true state (x, y)
+  int *s = nullptr;                     // GRID / TOY2 true state
+  EnvOut *dout = nullptr, *hout = nullptr;
+};
+
 struct vopp_agent {
   vopp_model *model = nullptr;
   int N = 0;
@@ -1256,6 +1265,122 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
   if (e == cudaSuccess) e = cudaMemcpy(g->lw, lw.data(), 4 * (size_t)n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { vopp_agent_destroy(g); return fail(VOPP_E_CUDA, "agent upload: %s", cudaGetErrorString(e)); }
   *out = g;
+  return VOPP_OK;
+}
+
+// ---- environment and closed loop ------------------------------------------------------
+int vopp_env_create(vopp_model *m, const void *state, uint64_t seed, vopp_env **out) {
+  if (!m || !state || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  *out = nullptr;
+  vopp_ctx *c = m->ctx;
+  cudaSetDevice(c->device);
+  vopp_env *e = new (std::nothrow) vopp_env;
+  if (!e) return fail(VOPP_E_NOMEM, "env alloc");
+  e->model = m;
+  e->seed = seed;
+  const bool nav = m->desc.kind == VOPP_NAV2D;
+  cudaError_t ce = nav ? cudaMalloc(&e->xy, 2 * sizeof(float)) : cudaMalloc(&e->s, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMalloc(&e->dout, sizeof(EnvOut));
+  if (ce == cudaSuccess) ce = cudaMallocHost(&e->hout, sizeof(EnvOut));
+  if (ce == cudaSuccess)
+    ce = nav ? cudaMemcpy(e->xy, state, 2 * sizeof(float), cudaMemcpyHostToDevice)
+             : cudaMemcpy(e->s, state, sizeof(int), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    vopp_env_destroy(e);
+    return fail(VOPP_E_NOMEM, "env buffers: %s", cudaGetErrorString(ce));
+  }
+  *out = e;
+  return VOPP_OK;
+}
+
+int vopp_env_step(vopp_env *e, int32_t action, void *obs, float *reward, int32_t *terminal) {
+  if (!e || !obs) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_model *m = e->model;
+  if (action < 0 || action >= m->A) return fail(VOPP_E_INVALID, "action %d", action);
+  vopp_ctx *c = m->ctx;
+  cudaSetDevice(c->device);
+  EnvArgs E;
+  std::memset(&E, 0, sizeof E);
+  E.kind = m->desc.kind;
+  E.action = action;
+  E.key0 = (uint32_t)e->seed;
+  E.key1 = (uint32_t)(e->seed >> 32);
+  E.t = e->t;
+  E.xy = e->xy;
+  E.s = e->s;
+  E.model = m->dev;
+  E.out = e->dout;
+  cudaError_t ce = launch_env(E, c->stream);
+  c->launches += 1;
+  if (ce != cudaSuccess) return fail(VOPP_E_CUDA, "env launch: %s", cudaGetErrorString(ce));
+  CUDA_TRY(cudaMemcpyAsync(e->hout, e->dout, sizeof(EnvOut), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (E.kind == kNav) {
+    static_cast<float *>(obs)[0] = e->hout->obs[0];
+    static_cast<float *>(obs)[1] = e->hout->obs[1];
+  } else {
+    *static_cast<int32_t *>(obs) = e->hout->obs_i;
+  }
+  if (reward) *reward = e->hout->reward;
+  if (terminal) *terminal = e->hout->terminal;
+  e->t += 1;
+  return VOPP_OK;
+}
+
+int vopp_env_get_state(vopp_env *e, void *state) {
+  if (!e || !state) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = e->model->ctx;
+  cudaSetDevice(c->device);
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (e->model->desc.kind == VOPP_NAV2D) CUDA_TRY(cudaMemcpy(state, e->xy, 2 * sizeof(float), cudaMemcpyDeviceToHost));
+  else CUDA_TRY(cudaMemcpy(state, e->s, sizeof(int), cudaMemcpyDeviceToHost));
+  return VOPP_OK;
+}
+
+void vopp_env_destroy(vopp_env *e) {
+  if (!e) return;
+  if (e->model) cudaStreamSynchronize(e->model->ctx->stream);
+  cudaFree(e->xy); cudaFree(e->s); cudaFree(e->dout);
+  if (e->hout) cudaFreeHost(e->hout);
+  delete e;
+}
+
+int vopp_run_episode(vopp_agent *g, vopp_env *e, const vopp_plan_params *p, int32_t max_steps,
+                     int32_t anytime, double budget_s, vopp_episode_result *out,
+                     int32_t *actions, float *rewards) {
+  if (!g || !e || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  if (g->model != e->model) return fail(VOPP_E_INVALID, "agent and environment use different models");
+  if (max_steps < 0) return fail(VOPP_E_INVALID, "max_steps %d", max_steps);
+  std::memset(out, 0, sizeof *out);
+  double disc = 1.0;
+  for (int t = 0; t < max_steps; ++t) {
+    vopp_plan_params pt = *p;
+    pt.seed = p->seed + (uint64_t)t;
+    vopp_plan_result r;
+    const auto t0 = std::chrono::steady_clock::now();
+    int32_t depth = pt.depth;
+    int rc = anytime ? vopp_agent_plan_anytime(g, &pt, budget_s, &r, &depth)
+                     : vopp_agent_plan(g, &pt, &r);
+    out->plan_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc) { out->status = rc; return rc; }
+    out->particle_steps += r.particle_steps;
+    if (t == 0 || depth < out->min_depth) out->min_depth = depth;
+    float obs[2] = {0.f, 0.f};
+    float rew = 0.f;
+    int32_t term = 0;
+    rc = vopp_env_step(e, r.action, obs, &rew, &term);
+    if (rc) { out->status = rc; return rc; }
+    if (actions) actions[t] = r.action;
+    if (rewards) rewards[t] = rew;
+    out->steps = t + 1;
+    out->total_reward += rew;
+    out->discounted_return += disc * rew;
+    disc *= (double)p->gamma;
+    if (term) { out->terminated = 1; break; }
+    rc = vopp_belief_update(g, r.action, obs, nullptr, nullptr);
+    if (rc) { out->status = rc; return rc; }
+  }
   return VOPP_OK;
 }
 

@@ -22,7 +22,7 @@ constexpr int kPiUniform = 0, kPiFixed = 1, kPiNavDist = 2;
 
 // Philox purposes (high byte of counter word 0).
 constexpr uint32_t kPurposeTransition = 0, kPurposeObservation = 1, kPurposeBeliefStep = 3,
-                   kPurposeResample = 4;
+                   kPurposeResample = 4, kPurposeEnvStep = 5, kPurposeEnvObs = 6;
 
 // Device status bits.
 constexpr uint32_t kStatusDegenerateRoot = 1u;

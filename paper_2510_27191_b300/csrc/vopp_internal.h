@@ -31,6 +31,24 @@ struct BeliefArgs {
   BeliefOut *out;
 };
 
+struct EnvOut {
+  float obs[2];     // NAV2D observation
+  int obs_i;        // GRID / TOY2 observation
+  float reward;
+  int terminal;
+};
+
+// One step of the closed loop's true state (a single particle on the device).
+struct EnvArgs {
+  int kind, action;
+  uint32_t key0, key1;
+  unsigned long long t;        // environment time step (Philox node word)
+  float *xy;                   // NAV2D state (x, y)
+  int *s;                      // GRID / TOY2 state
+  const DevModel *model;
+  EnvOut *out;
+};
+
 // Dynamic shared memory a leaf CTA may use (B300: 227 KB per block, kept below it).
 constexpr size_t kLeafSmemLimit = 200 * 1024;
 size_t leaf_smem_bytes(int kind, int N, int AW);
@@ -44,6 +62,7 @@ cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long 
                         size_t smem, int threads, long long grid, cudaStream_t s);
 cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
+cudaError_t launch_env(const EnvArgs &E, cudaStream_t s);
 
 }  // namespace vopp
 

@@ -1123,6 +1123,47 @@ __global__ void __launch_bounds__(1024) k_belief(BeliefArgs B) {
 }
 
 // ---------------------------------------------------------------------------------------
+// K7: one environment step of the closed loop (Alg. 1: execute the action, perceive the
+// observation).  The true state steps under the model's own transition and observation
+// processes with random numbers of its own: Philox purpose 5 (transition words 0,1) and 6
+// (observation words 0,1), node word = the environment's time step.
+// ---------------------------------------------------------------------------------------
+template <class M>
+__device__ void env_step(const EnvArgs &E) {
+  const DevModel &dm = *E.model;
+  typename M::S s;
+  if constexpr (M::kStochastic) s = typename M::S{E.xy[0], E.xy[1]};
+  else s = typename M::S{E.s[0]};
+  const uint4 w = draw(E.key0, E.key1, 0u, kPurposeEnvStep, 0, 0, 0, E.t);
+  const float r = M::step(s, E.action, w.x, w.y, dm);
+  const uint4 v = draw(E.key0, E.key1, 0u, kPurposeEnvObs, 0, 0, 0, E.t);
+  const typename M::O o = M::draw_obs(s, E.action, v.x, v.y, dm);
+  if constexpr (M::kStochastic) {
+    E.xy[0] = s.x;
+    E.xy[1] = s.y;
+    E.out->obs[0] = o.x;
+    E.out->obs[1] = o.y;
+    E.out->obs_i = 0;
+  } else {
+    E.s[0] = s.s;
+    E.out->obs[0] = (float)o.o;
+    E.out->obs[1] = 0.f;
+    E.out->obs_i = o.o;
+  }
+  E.out->reward = r;
+  E.out->terminal = M::terminal(s) ? 1 : 0;
+}
+
+__global__ void k_env(EnvArgs E) {
+  if (threadIdx.x != 0) return;
+  switch (E.kind) {
+    case kNav: env_step<NavModel>(E); break;
+    case kGrid: env_step<GridModel>(E); break;
+    default: env_step<ToyModel>(E); break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------------------
 size_t leaf_smem_bytes(int kind, int N, int AW) {
@@ -1193,6 +1234,11 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
     case kToy: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kToy>, threads, smem);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_env(const EnvArgs &E, cudaStream_t s) {
+  k_env<<<1, 32, 0, s>>>(E);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s) {

@@ -85,6 +85,13 @@ class vopp_pipe_rate(ctypes.Structure):
                 ("ops_per_second", ctypes.c_double), ("sms", ctypes.c_int32)]
 
 
+class vopp_episode_result(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("terminated", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("min_depth", ctypes.c_int32),
+                ("total_reward", ctypes.c_double), ("discounted_return", ctypes.c_double),
+                ("particle_steps", ctypes.c_uint64), ("plan_seconds", ctypes.c_double)]
+
+
 class vopp_plan_request(ctypes.Structure):
     _fields_ = [("model", ctypes.c_void_p), ("root_states", ctypes.c_void_p),
                 ("root_weights", ctypes.c_void_p), ("n_particles", ctypes.c_int32),
@@ -148,6 +155,12 @@ def _load():
         "vopp_plan_anytime": ([vp, vp, vp, i32, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
                                u32, ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
                               ctypes.c_int),
+        "vopp_env_create": ([vp, vp, u64, ctypes.POINTER(vp)], ctypes.c_int),
+        "vopp_env_step": ([vp, i32, vp, fp, ctypes.POINTER(i32)], ctypes.c_int),
+        "vopp_env_get_state": ([vp, vp], ctypes.c_int),
+        "vopp_env_destroy": ([vp], None),
+        "vopp_run_episode": ([vp, vp, ctypes.POINTER(vopp_plan_params), i32, i32, ctypes.c_double,
+                              ctypes.POINTER(vopp_episode_result), vp, vp], ctypes.c_int),
         "vopp_agent_plan_anytime": ([vp, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
                                      ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
                                     ctypes.c_int),
@@ -391,6 +404,52 @@ def vopp_belief_update_noalloc(model: int, states, log_weights, action: int, obs
                                          None if ancestors is None else ancestors.data_ptr(),
                                          ctypes.byref(ess), ctypes.byref(res)))
     return ess.value, bool(res.value)
+
+
+# ---- closed loop -------------------------------------------------------------------------
+def vopp_env_create(model: int, state, seed: int, kind: int) -> int:
+    """state: (x, y) for NAV2D, an int for GRID / TOY2 (kind: the model's kind)."""
+    st = (np.asarray(state, dtype=np.float32).reshape(2) if kind == VOPP_NAV2D
+          else np.asarray([int(state)], dtype=np.int32))
+    h = ctypes.c_void_p()
+    check(lib.vopp_env_create(model, st.ctypes.data, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h)))
+    return h.value
+
+
+def vopp_env_step(env: int, action: int, kind: int):
+    """(observation, reward, terminal) of one step; observation (x, y) or an int."""
+    o = np.zeros(2, dtype=np.float32) if kind == VOPP_NAV2D else np.zeros(1, dtype=np.int32)
+    r = ctypes.c_float()
+    t = ctypes.c_int32()
+    check(lib.vopp_env_step(env, int(action), o.ctypes.data, ctypes.byref(r), ctypes.byref(t)))
+    obs = (float(o[0]), float(o[1])) if kind == VOPP_NAV2D else int(o[0])
+    return obs, r.value, bool(t.value)
+
+
+def vopp_env_get_state(env: int, kind: int):
+    o = np.zeros(2, dtype=np.float32) if kind == VOPP_NAV2D else np.zeros(1, dtype=np.int32)
+    check(lib.vopp_env_get_state(env, o.ctypes.data))
+    return (float(o[0]), float(o[1])) if kind == VOPP_NAV2D else int(o[0])
+
+
+def vopp_env_destroy(env: int) -> None:
+    lib.vopp_env_destroy(env)
+
+
+def vopp_run_episode(agent: int, env: int, depth: int, width: int, eta: float, gamma: float,
+                     seed: int, max_steps: int, anytime: bool = False, budget_s: float = 0.0):
+    """Closed loop: (result dict, actions, rewards); the dict carries the status instead of
+    raising when an error ends the episode early."""
+    p, keep = make_params(depth, width, eta, gamma, seed)
+    r = vopp_episode_result()
+    acts = np.full(max_steps, -1, dtype=np.int32)
+    rews = np.zeros(max_steps, dtype=np.float32)
+    rc = lib.vopp_run_episode(agent, env, ctypes.byref(p), int(max_steps), int(bool(anytime)),
+                              float(budget_s), ctypes.byref(r), acts.ctypes.data, rews.ctypes.data)
+    del keep
+    res = {n: getattr(r, n) for n, _ in vopp_episode_result._fields_}
+    res["rc"] = rc
+    return res, acts[:r.steps], rews[:r.steps]
 
 
 def vopp_agent_destroy(agent: int) -> None:
