@@ -397,14 +397,16 @@ struct NavModel {
     return O{fmaf(sg, g.x, s.x), fmaf(sg, g.y, s.y)};
   }
   // Base-2 log-likelihoods of observation o for the two particles of a pair.
+  // 1/sigma^2 comes from the same logarithm, 2^(-2 log2 sigma): one ex2 instead of a
+  // reciprocal and a product.
   __device__ __forceinline__ static float2 loglik2_pair(float2 x, float2 y, const O &o) {
     const float2 dm = add2(x, bc2(-9.0f));
     const float2 sg = fma2(bc2(0.5f), make_float2(fabsf(dm.x), fabsf(dm.y)), bc2(0.05f));
-    const float2 inv = make_float2(__fdividef(1.0f, sg.x), __fdividef(1.0f, sg.y));
+    const float2 t = mul2(bc2(-2.0f), make_float2(lg2(sg.x), lg2(sg.y)));   // -2 log2 sigma
+    const float2 is2 = make_float2(ex2(t.x), ex2(t.y));                   // 1 / sigma^2
     const float2 ex = fma2(x, bc2(-1.0f), bc2(o.x)), ey = fma2(y, bc2(-1.0f), bc2(o.y));
     const float2 d2 = fma2(ex, ex, mul2(ey, ey));
-    return fma2(mul2(bc2(-0.721347520f), d2), mul2(inv, inv),
-                fma2(bc2(-2.0f), make_float2(lg2(sg.x), lg2(sg.y)), bc2(-2.65149613f)));
+    return fma2(mul2(bc2(-0.721347520f), d2), is2, add2(t, bc2(-2.65149613f)));
   }
   // Heuristic of the pair; t0 / t1 are the terminal flags of the states.
   __device__ __forceinline__ static float2 heuristic_pair(float2 x, float2 y, bool t0, bool t1,
@@ -420,10 +422,11 @@ struct NavModel {
   //                                 - log2(2 pi)
   __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &) {
     const float sg = sigma(s.x);
-    const float inv = __fdividef(1.0f, sg);
+    const float t = __fmul_rn(-2.0f, lg2(sg));      // -2 log2 sigma
+    const float is2 = ex2(t);                       // 1 / sigma^2
     const float ex = fmaf(s.x, -1.0f, o.x), ey = fmaf(s.y, -1.0f, o.y);
     const float d2 = fmaf(ex, ex, __fmul_rn(ey, ey));
-    return fmaf(__fmul_rn(-0.721347520f, d2), __fmul_rn(inv, inv), fmaf(-2.0f, lg2(sg), -2.65149613f));
+    return fmaf(__fmul_rn(-0.721347520f, d2), is2, __fadd_rn(t, -2.65149613f));
   }
   __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
     return kLn2 * loglik2(s, a, o, m);

@@ -46,6 +46,20 @@ def test_nav_small_full_tree(N, D, W, leaf_gen):
     _full(Spec(WL.NAV2D, N, D, W, eta=0.7, seed=3, root_seed=N), leaf_gen=leaf_gen)
 
 
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_nav_weight_far_from_likelihood(D):
+    """Almost all weight on one particle far from where the other particles (and so the
+    branch observations) lie, those carrying 1e-30 each: the weighted sums of the leaf
+    branches are dominated by terms far below the likelihood maximum, the case the leaf
+    kernel sums in the exact log-domain form."""
+    N = 64
+    rng = np.random.default_rng(12)
+    x = np.concatenate([[9.0], 8.8 + 0.3 * rng.random(N - 1)]).astype(np.float32)
+    y = np.concatenate([[1.0], 4.0 + 2.0 * rng.random(N - 1)]).astype(np.float32)
+    w = np.concatenate([[1.0], np.full(N - 1, 1e-30)]).astype(np.float32)
+    _full(Spec(WL.NAV2D, N, D, 2, eta=0.6, seed=17, root=dict(x=x, y=y, w=w)))
+
+
 def test_nav_nav_dist_policy_and_weights():
     _full(Spec(WL.NAV2D, 200, 3, 2, eta=0.5, seed=9, pi_mode=WL.PI_NAV_SOFTMAX_DIST,
                weights="sparse", root_seed=4))
