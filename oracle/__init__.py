@@ -279,6 +279,63 @@ def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float,
     return res
 
 
+class EpisodeArgs(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("O", ctypes.c_int),
+                ("eta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("cap", ctypes.c_int),
+                ("parent_an", _ip), ("depth", _ip),
+                ("psi", _dp), ("V", _dp), ("C", _dp), ("Ws", _dp), ("Hs", _dp),
+                ("N", ctypes.POINTER(ctypes.c_int64)), ("Nl", ctypes.POINTER(ctypes.c_int64)),
+                ("child", _ip),
+                ("n_nodes", ctypes.c_int), ("action", ctypes.c_int), ("v_root", ctypes.c_double),
+                ("q_root", ctypes.c_double * MAXA), ("policy", ctypes.c_double * MAXA),
+                ("particle_steps", ctypes.c_longlong), ("near_decisions", ctypes.c_longlong),
+                ("near_threshold", ctypes.c_longlong)]
+
+
+NUM_OBS = {NAV2D: 0, GRID: 3, TOY2: 2}
+
+
+def plan_episodes(model: Model, M: int, K: int, eta: float, gamma: float, seed: int,
+                  root_x=None, root_y=None, root_s=None, root_w=None, cap: int = 0):
+    """Episode mode (Alg. 1-3 as printed): K planning iterations of M sampled episodes, the
+    tree grown by first visits, visit-weighted backups of the persistent preferences.
+    Returns the root result and the tree arrays (``parent_an``, ``depth``, ``psi``, ``V``,
+    ``C``, ``N``, ``Nl``, ``Hs`` trimmed to the node count)."""
+    A = NUM_ACTIONS[model.kind]
+    O = NUM_OBS[model.kind]
+    Np = len(root_x) if root_x is not None else len(root_s)
+    cap = cap or M * K * (K + 1) // 2 + 1
+    arr = dict(parent_an=np.zeros(cap, np.int32), depth=np.zeros(cap, np.int32),
+               psi=np.zeros(cap * A), V=np.zeros(cap), C=np.zeros(cap * A), Ws=np.zeros(cap * A),
+               Hs=np.zeros(cap), N=np.zeros(cap * A, np.int64), Nl=np.zeros(cap, np.int64),
+               child=np.zeros(max(cap * A * O, 1), np.int32))
+    io = EpisodeArgs()
+    io.M, io.K, io.O, io.eta, io.gamma, io.seed, io.cap = M, K, O, eta, gamma, seed & (2**64 - 1), cap
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    io.parent_an, io.depth = _ptr(arr["parent_an"], _ip), _ptr(arr["depth"], _ip)
+    io.psi, io.V, io.C = _ptr(arr["psi"], _dp), _ptr(arr["V"], _dp), _ptr(arr["C"], _dp)
+    io.Ws, io.Hs = _ptr(arr["Ws"], _dp), _ptr(arr["Hs"], _dp)
+    io.N, io.Nl = _ptr(arr["N"], i64), _ptr(arr["Nl"], i64)
+    io.child = _ptr(arr["child"], _ip)
+    rx = None if root_x is None else np.ascontiguousarray(root_x, dtype=np.float64)
+    ry = None if root_y is None else np.ascontiguousarray(root_y, dtype=np.float64)
+    rs = None if root_s is None else np.ascontiguousarray(root_s, dtype=np.int32)
+    rw = None if root_w is None else np.ascontiguousarray(root_w, dtype=np.float64)
+    rc = lib().orc_plan_episodes(ctypes.byref(model), _ptr(rx, _dp), _ptr(ry, _dp),
+                                 _ptr(rs, _ip), _ptr(rw, _dp), Np, ctypes.byref(io))
+    n = io.n_nodes
+    res = dict(status=rc, action=io.action, v_root=io.v_root, q_root=np.array(io.q_root[:A]),
+               policy=np.array(io.policy[:A]), n_nodes=n, particle_steps=io.particle_steps,
+               near_decisions=io.near_decisions, near_threshold=io.near_threshold)
+    for k in ("parent_an", "depth", "V", "Hs", "Nl"):
+        res[k] = arr[k][:n].copy()
+    for k in ("psi", "C", "N"):
+        res[k] = arr[k][:n * A].reshape(n, A).copy()
+    res["psi_root"] = res["psi"][0].copy() if n else None
+    return res
+
+
 def env_step(model: Model, state, action: int, seed: int, t: int):
     """One step of the true state (closed loop, Alg. 1): returns (status, next state,
     observation, reward, terminal); state is (x, y) for NAV2D, an int for GRID / TOY2."""

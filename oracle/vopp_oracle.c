@@ -41,6 +41,9 @@
  *   purpose 4: belief-update resampling offset, idx 0, c1 = 0, node = t
  *   purpose 5: environment transition of the true state, idx 0, c1 = 0, node = t
  *   purpose 6: environment observation, idx 0, c1 = 0, node = t (words 0,1 as purpose 1)
+ *   episode mode (iteration k as the node word, episode e as idx, depth d as level):
+ *   purpose 7: root state sample (word 0), 8: action sample (word 0), 9: transition
+ *   (words 0,1), 10: observation (words 0,1)
  *   uniform:   u = (2 (x >> 9) + 1) * 2^-24, exactly representable in FP32 and FP64.
  */
 #include <math.h>
@@ -763,6 +766,205 @@ double orc_nav_loglik(double sx, double sy, double ox, double oy) {
   pstate sp = {sx, sy, 0};
   double o[2] = {ox, oy};
   return model_loglik(&m, &sp, 0, o);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Episode mode (Alg. 1-3 as printed): every planning iteration k = 1, 2, ... samples M     */
+/* episodes from the root belief and runs them to depth D_max = k, each step sampling an   */
+/* action from softmax(Psi(b,.)/eta), simulating G, adding the reward and a visit to the  */
+/* action node and moving to the child belief of the observation (created on first visit; */
+/* continuous observations always create one); episodes that reach a terminal state stop */
+/* (FilterTerminals).  The backup (Alg. 3) then aggregates the leaves' heuristics and,     */
+/* for d = D_max..1, forms Q of every action node at depth d-1 from its mean reward and   */
+/* the visit-weighted values of its children (normalised by the action's own visits) and  */
+/* applies V_curr = L Psi, Psi <- Psi - V_curr + Q, V = L Psi to every belief at d-1.     */
+/* Actions without a visit enter the update with Q = 0 (the dense tensor's default).      */
+/* Node ids are assigned in creation order: iteration, depth step, episode.               */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+  /* inputs */
+  int M, K, O;             /* episodes per iteration, iterations (= max depth), |O| (0: continuous) */
+  double eta, gamma;
+  uint64_t seed;
+  int cap;                 /* belief-node capacity of the arrays below                    */
+  /* tree arrays, capacity cap (per action node: [cap * A]; child table: [cap * A * O]) */
+  int32_t *parent_an;      /* parent action node b * A + a (-1 at the root)                */
+  int32_t *depth;
+  double *psi, *V, *C, *Ws, *Hs;
+  int64_t *N, *Nl;
+  int32_t *child;
+  /* results */
+  int n_nodes, action;
+  double v_root;
+  double q_root[ORC_MAXA], policy[ORC_MAXA];
+  long long particle_steps, near_decisions, near_threshold;
+} orc_episode_args;
+
+/* index of the first cumulative entry above u; flags u within tol of a boundary */
+static int sample_cdf(const double *cdf, int n, double u, double tol, long long *near) {
+  int i = 0;
+  while (i < n - 1 && !(u < cdf[i])) ++i;
+  if (fabs(u - cdf[i]) < tol || (i > 0 && fabs(u - cdf[i - 1]) < tol)) ++*near;
+  return i;
+}
+
+static void ep_new_node(orc_episode_args *io, int A, int id, int parent_an, int d,
+                        const double *lpi) {
+  io->parent_an[id] = parent_an;
+  io->depth[id] = d;
+  io->V[id] = 0.0;
+  io->Hs[id] = 0.0;
+  io->Nl[id] = 0;
+  for (int a = 0; a < A; ++a) {
+    io->psi[(long long)id * A + a] = io->eta * lpi[a];
+    io->C[(long long)id * A + a] = 0.0;
+    io->N[(long long)id * A + a] = 0;
+    for (int o = 0; o < io->O; ++o) io->child[((long long)id * A + a) * io->O + o] = -1;
+  }
+}
+
+int orc_plan_episodes(const orc_model *m, const double *root_x, const double *root_y,
+                      const int32_t *root_s, const double *root_w, int Np,
+                      orc_episode_args *io) {
+  const int A = orc_num_actions(m->kind), M = io->M, K = io->K;
+  if (Np < 1 || M < 1 || K < 1 || K > ORC_MAXD || !(io->eta > 0.0) || !(io->gamma > 0.0) ||
+      !(io->gamma < 1.0) || m->pi_mode == ORC_PI_NAV_DIST || io->cap < 1)
+    return ORC_E_INVALID;
+  if ((m->kind == ORC_NAV2D) != (io->O == 0)) return ORC_E_INVALID;
+  double lpi[ORC_MAXA];
+  log_pibar(m, NULL, NULL, 0, lpi);
+  pstate *root = (pstate *)calloc((size_t)Np, sizeof(pstate));
+  double *cdf = (double *)calloc((size_t)Np, sizeof(double));
+  pstate *S = (pstate *)calloc((size_t)M, sizeof(pstate));
+  int *B = (int *)calloc((size_t)M, sizeof(int)), *alive = (int *)calloc((size_t)M, sizeof(int));
+  int rc = (root && cdf && S && B && alive) ? ORC_OK : ORC_E_NOMEM;
+  io->n_nodes = 0;
+  io->particle_steps = io->near_decisions = io->near_threshold = 0;
+  io->action = -1;
+  io->v_root = NAN;
+  if (rc == ORC_OK) {
+    /* root belief: normalised weights, terminal particles weight 0 (as the full-width plan) */
+    double tot = 0.0;
+    for (int i = 0; i < Np; ++i) {
+      root[i].x = root_x ? root_x[i] : 0.0;
+      root[i].y = root_y ? root_y[i] : 0.0;
+      root[i].s = root_s ? root_s[i] : 0;
+      double w = root_w ? root_w[i] : 1.0;
+      if (w < 0.0) rc = ORC_E_INVALID;
+      if (model_is_terminal(m, &root[i])) w = 0.0;
+      cdf[i] = w;
+      tot += w;
+    }
+    if (rc == ORC_OK && !(tot > 0.0)) rc = ORC_E_DEGENERATE;
+    double acc = 0.0;
+    for (int i = 0; i < Np && rc == ORC_OK; ++i) { acc += cdf[i] / tot; cdf[i] = acc; }
+  }
+  if (rc == ORC_OK) {
+    ep_new_node(io, A, 0, -1, 0, lpi);
+    io->n_nodes = 1;
+  }
+  for (int k = 1; k <= K && rc == ORC_OK; ++k) {
+    /* SampleStatesFromBelief */
+    for (int e = 0; e < M; ++e) {
+      uint32_t w[4];
+      draw(io->seed, (uint32_t)e, 7, 0, 0, 0, (uint64_t)k, w);
+      int i = sample_cdf(cdf, Np, orc_uniform(w[0]), 1e-12, &io->near_decisions);
+      S[e] = root[i];
+      B[e] = 0;
+      alive[e] = 1;
+    }
+    /* Search (Alg. 2) */
+    for (int d = 0; d < k && rc == ORC_OK; ++d) {
+      for (int e = 0; e < M && rc == ORC_OK; ++e) {
+        if (!alive[e]) continue;
+        const int b = B[e];
+        double z[ORC_MAXA], pc[ORC_MAXA], mx = -INFINITY, sum = 0.0;
+        for (int a = 0; a < A; ++a) {
+          z[a] = io->psi[(long long)b * A + a] / io->eta;
+          if (z[a] > mx) mx = z[a];
+        }
+        for (int a = 0; a < A; ++a) { pc[a] = exp(z[a] - mx); sum += pc[a]; }
+        double run = 0.0;
+        for (int a = 0; a < A; ++a) { run += pc[a] / sum; pc[a] = run; }
+        uint32_t w[4];
+        draw(io->seed, (uint32_t)e, 8, (uint32_t)d, 0, 0, (uint64_t)k, w);
+        const int a = sample_cdf(pc, A, orc_uniform(w[0]), 1e-5, &io->near_decisions);
+        pstate sp;
+        double r, o[2];
+        draw(io->seed, (uint32_t)e, 9, (uint32_t)d, 0, 0, (uint64_t)k, w);
+        model_step(m, &S[e], a, w[0], w[1], &sp, &r, &io->near_threshold);
+        draw(io->seed, (uint32_t)e, 10, (uint32_t)d, 0, 0, (uint64_t)k, w);
+        model_draw_obs(m, &sp, a, w[0], w[1], o);
+        const long long an = (long long)b * A + a;
+        io->C[an] += r;
+        io->N[an] += 1;
+        io->particle_steps += 1;
+        if (model_is_terminal(m, &sp)) { alive[e] = 0; continue; }   /* FilterTerminals */
+        int nb;
+        if (io->O > 0) {
+          const long long slot = an * io->O + (long long)o[0];
+          nb = io->child[slot];
+          if (nb < 0) {
+            if (io->n_nodes >= io->cap) { rc = ORC_E_NOMEM; break; }
+            nb = io->n_nodes++;
+            ep_new_node(io, A, nb, (int)an, d + 1, lpi);
+            io->child[slot] = nb;
+          }
+        } else {
+          if (io->n_nodes >= io->cap) { rc = ORC_E_NOMEM; break; }
+          nb = io->n_nodes++;
+          ep_new_node(io, A, nb, (int)an, d + 1, lpi);
+        }
+        B[e] = nb;
+        S[e] = sp;
+      }
+    }
+    if (rc != ORC_OK) break;
+    /* leaves: ValueHeuristic aggregated per leaf belief */
+    for (int e = 0; e < M; ++e) {
+      if (!alive[e]) continue;
+      io->Hs[B[e]] += model_heuristic(m, &S[e], io->gamma);
+      io->Nl[B[e]] += 1;
+    }
+    /* Backup (Alg. 3) */
+    for (int n = 0; n < io->n_nodes; ++n)
+      if (io->depth[n] == k) io->V[n] = io->Nl[n] > 0 ? io->Hs[n] / (double)io->Nl[n] : 0.0;
+    for (int d = k; d >= 1; --d) {
+      for (long long x = 0; x < (long long)io->n_nodes * A; ++x) io->Ws[x] = 0.0;
+      for (int n = 0; n < io->n_nodes; ++n) {
+        if (io->depth[n] != d) continue;
+        double visits = 0.0;
+        if (d == k) visits = (double)io->Nl[n];
+        else for (int a = 0; a < A; ++a) visits += (double)io->N[(long long)n * A + a];
+        io->Ws[io->parent_an[n]] += visits * io->V[n];
+      }
+      for (int n = 0; n < io->n_nodes; ++n) {
+        if (io->depth[n] != d - 1) continue;
+        double q[ORC_MAXA], *ps = io->psi + (long long)n * A;
+        for (int a = 0; a < A; ++a) {
+          const long long an = (long long)n * A + a;
+          q[a] = io->N[an] > 0 ? io->C[an] / (double)io->N[an] +
+                                     io->gamma * io->Ws[an] / (double)io->N[an]
+                               : 0.0;
+        }
+        const double vcur = lse_value(ps, A, io->eta);
+        for (int a = 0; a < A; ++a) ps[a] = ps[a] - vcur + q[a];
+        io->V[n] = lse_value(ps, A, io->eta);
+        if (n == 0)
+          for (int a = 0; a < A; ++a) io->q_root[a] = q[a];
+      }
+    }
+  }
+  if (rc == ORC_OK) {
+    const double *ps = io->psi;
+    int best = 0;
+    for (int a = 0; a < A; ++a) if (ps[a] > ps[best]) best = a;
+    io->action = best;
+    io->v_root = io->V[0];
+    for (int a = 0; a < A; ++a) io->policy[a] = exp((ps[a] - io->V[0]) / io->eta);
+  }
+  free(root); free(cdf); free(S); free(B); free(alive);
+  return rc;
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -19,7 +19,7 @@ from scipy.special import logsumexp
 
 import oracle as O
 from paper_2510_27191_b300 import workloads as WL
-from tests.brute import porpp_anytime, soft_expectimax
+from tests.brute import episode_mode_reference, porpp_anytime, soft_expectimax
 
 SEEDS = [0x0123456789ABCDEF, 1, 0xFFFFFFFFFFFFFFFF, 0x9E3779B97F4A7C15]
 
@@ -600,3 +600,85 @@ def test_env_step_grid_sense_accuracy_and_moves():
     s = int(WL.pack_grid_state(np.array([bits]), 10, 5)[0])
     rc, s1, o, r, term = O.env_step(m, s, 0, 99, 0)
     assert term and r == 10.0 and o == 0
+
+
+# ----------------------------------------------------------------------------------------
+# Episode mode (Alg. 1-3 as printed) against an independent dict-keyed implementation.
+# ----------------------------------------------------------------------------------------
+def _philox_words(seed):
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    return lambda idx, purpose, level, node: O.philox(
+        (idx | (purpose << 24), level, node & 0xFFFFFFFF, node >> 32), key)
+
+
+def _compare_episode_trees(r, nodes, steps, A):
+    assert r["status"] == O.OK and r["near_decisions"] == 0
+    assert r["n_nodes"] == len(nodes) and r["particle_steps"] == steps
+    for i, n in enumerate(nodes):
+        par = -1 if n["parent"] is None else n["parent"][0] * A + n["parent"][1]
+        assert r["parent_an"][i] == par and r["depth"][i] == n["depth"], i
+        assert r["N"][i].tolist() == n["N"].tolist(), i
+        np.testing.assert_allclose(r["C"][i], n["C"], rtol=1e-13, atol=1e-12)
+        np.testing.assert_allclose(r["psi"][i], n["psi"], rtol=1e-11, atol=1e-10)
+        assert r["V"][i] == pytest.approx(n["V"], rel=1e-11, abs=1e-10)
+    psi = nodes[0]["psi"]
+    assert r["action"] == int(np.argmax(psi))
+    np.testing.assert_allclose(r["policy"], np.exp((psi - nodes[0]["V"]) / r["eta"]), atol=1e-12)
+
+
+@pytest.mark.parametrize("K,M,eta", [(1, 40, 1.0), (3, 64, 0.5), (4, 30, 2.0)])
+def test_episode_mode_toy2_equals_independent_implementation(K, M, eta):
+    T = lambda s, a: (1 - s) if a == 1 else s
+    R = lambda s, a: -0.1 if a == 1 else (1.0 if s == 0 else -1.0)
+    thr = int(math.floor(0.85 * 4294967296.0))
+    m = O.make_model(O.TOY2, pi_mode=O.PI_FIXED, pi_fixed=(0.6, 0.4))
+    states = [0, 1, 1, 0, 1]
+    w = [0.3, 0.1, 0.2, 0.25, 0.15]
+    seed = 0xC0FFEE
+    r = O.plan_episodes(m, M, K, eta, 0.9, seed, root_s=np.array(states), root_w=np.array(w))
+    r["eta"] = eta
+    nodes, steps = episode_mode_reference(
+        m, 2, 2, states, w, M, K, eta, 0.9, seed, np.log([0.6, 0.4]),
+        step=lambda s, a, w0, w1: (T(s, a), R(s, a)),
+        draw_obs=lambda s, a, w0, w1: s if w0 < thr else 1 - s,
+        terminal=lambda s: False, heuristic=lambda s: 0.0, philox_words=_philox_words(seed))
+    _compare_episode_trees(r, nodes, steps, 2)
+
+
+def test_episode_mode_grid_equals_independent_implementation():
+    rx, ry = WL.grid_layout(1)
+    m = O.make_model(O.GRID, rock_x=rx, rock_y=ry)
+    s0, _ = WL.grid_root(24, 5)
+    # start two cells from the east edge so that exits (terminal episodes) occur
+    s0 = WL.pack_grid_state(np.asarray(s0) & 0xFF, 9, 5)
+    gamma, seed = 0.95, 31337
+    term = lambda s: bool((int(s) >> 16) & 1)
+    r = O.plan_episodes(m, 48, 3, 1.0, gamma, seed, root_s=s0)
+    r["eta"] = 1.0
+
+    def step(s, a, w0, w1):
+        s2, rew = O.grid_step(m, int(s), a)
+        return s2, rew
+
+    nodes, steps = episode_mode_reference(
+        m, 13, 3, [int(v) for v in s0], np.ones(len(s0)), 48, 3, 1.0, gamma, seed,
+        np.full(13, -math.log(13)), step=step,
+        draw_obs=lambda s, a, w0, w1: O.grid_draw_obs(m, int(s), a, w0),
+        terminal=term,
+        heuristic=lambda s: 0.0 if term(s) else 10.0 * gamma ** (10 - ((int(s) >> 8) & 0xF)),
+        philox_words=_philox_words(seed))
+    _compare_episode_trees(r, nodes, steps, 13)
+    assert any(n["N"].sum() > 0 for n in nodes[1:])
+
+
+def test_episode_mode_one_iteration_root_q_is_the_empirical_mean_reward():
+    """K = 1: Q(root, a) is the mean reward of the episodes that chose a (no children at
+    depth 1 carry value into it beyond the leaf heuristic, zero here), and Psi = eta log
+    pibar + Q for the visited actions, eta log pibar for the others."""
+    m = O.make_model(O.TOY2, h_zero=True)
+    states = np.array([0, 1])
+    r = O.plan_episodes(m, 2000, 1, 1.0, 0.9, 5, root_s=states, root_w=np.array([0.7, 0.3]))
+    q = r["q_root"]
+    assert q[0] == pytest.approx(0.7 * 1.0 + 0.3 * -1.0, abs=0.06)   # E[R(s, stay)]
+    assert q[1] == pytest.approx(-0.1, abs=1e-12)
+    np.testing.assert_allclose(r["psi_root"], np.log(0.5) + q, atol=1e-12)
