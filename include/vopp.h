@@ -232,6 +232,49 @@ VOPP_API int vopp_plan_anytime(vopp_model *model, const void *root_states, const
                                int32_t n_particles, const vopp_plan_params *params, double budget_s,
                                uint32_t ptr_flags, vopp_plan_result *out, int32_t *depth_reached);
 
+/* ---- episode mode (Alg. 1-3 as printed) ---------------------------------------------- */
+/* Planning iterations k = 1, 2, ..., max_depth (D_max = k): sample `episodes` root states
+ * from the belief (Philox purpose 7; episode e, iteration k), run every episode to depth k
+ * -- action a ~ softmax(Psi(b,.)/eta) (purpose 8), G (transition purpose 9, observation
+ * purpose 10, depth d as the level word), reward and visit added to action node (b, a), the
+ * episode ends at a terminal state, else moves to the child belief of its observation,
+ * created on first visit (a continuous NAV2D observation always creates one) -- then
+ * aggregate the leaf heuristics and back up (Alg. 3) for d = k..1: W(b,a) = sum over the
+ * children of visits x V (normaliser: the action's own visits, so terminated episodes add no
+ * future value), Q = C/N + gamma W/N (0 for an action without visits), and every belief at
+ * depth d-1: V_curr = eta log sum exp(Psi/eta), Psi <- Psi - V_curr + Q, V = L Psi.  A new
+ * belief starts from Psi_0 = eta log pibar (uniform or fixed policy; the distance softmax
+ * needs per-node particle sets and is refused with VOPP_E_INVALID).  Another iteration
+ * starts while the wall time is below budget_s (<= 0: none).  Node ids follow creation
+ * order (iteration, depth, episode); the tree lives until the next episode-mode plan on the
+ * context (vopp_episode_tree_read).  out: action argmax Psi(root), v_root = V(root), q =
+ * the root's last Q, policy softmax(Psi(root)/eta), particle_steps = generative-model calls,
+ * nodes = beliefs.  Errors: VOPP_E_INVALID (arguments), VOPP_E_NOMEM (device buffers, or
+ * more beliefs than max_nodes), VOPP_E_DEGENERATE (root weights sum to 0). */
+typedef struct {
+  int32_t episodes;    /* M, episodes per planning iteration, 1 .. 2^24                   */
+  int32_t max_depth;   /* iterations = maximum depth, 1 .. VOPP_MAX_DEPTH                 */
+  float eta;           /* temperature (> 0)                                               */
+  float gamma;         /* discount in (0,1)                                               */
+  uint64_t seed;       /* Philox key                                                      */
+  int32_t max_nodes;   /* belief capacity; 0: M * D * (D + 1) / 2 + 1 (always enough)     */
+} vopp_episode_params;
+VOPP_API int vopp_plan_episodes(vopp_model *model, const void *root_states, const float *root_weights,
+                                int32_t n_particles, const vopp_episode_params *params, double budget_s,
+                                uint32_t ptr_flags, vopp_plan_result *out, int32_t *depth_reached,
+                                int32_t *n_nodes);
+/* Fields of the last episode-mode tree (vopp_episode_tree_read), indexed by belief id. */
+#define VOPP_EP_PARENT 0   /* int32  parent action node b*A + a, -1 at the root              */
+#define VOPP_EP_DEPTH 1    /* int32  depth                                                   */
+#define VOPP_EP_PSI 2      /* double Psi[node][A]                                            */
+#define VOPP_EP_V 3        /* double V[node]                                                 */
+#define VOPP_EP_REWARD 4   /* double C[node][A], reward sum of the action node               */
+#define VOPP_EP_VISITS 5   /* uint64 N[node][A], visits of the action node                   */
+/* Copy `count` elements from element `offset` of a field of the context's last episode-mode
+ * tree to host memory dst. */
+VOPP_API int vopp_episode_tree_read(vopp_ctx *ctx, int32_t field, uint64_t offset, uint64_t count,
+                                    void *dst);
+
 /* Copy `count` elements of a tree field of the most recent plan on this context, starting
  * at element `offset` of that level's array, into dst (host, or device with ptr_flags).
  * Valid until the next plan on the context. */
@@ -251,6 +294,9 @@ VOPP_API int vopp_grid_thresholds(uint64_t *thr, int32_t n);
 VOPP_API int vopp_agent_create(vopp_model *model, const void *states, const float *weights, int32_t n,
                       uint64_t seed, uint32_t ptr_flags, vopp_agent **out);
 VOPP_API int vopp_agent_plan(vopp_agent *agent, const vopp_plan_params *params, vopp_plan_result *out);
+/* vopp_plan_episodes from the agent's particles and log weights. */
+VOPP_API int vopp_agent_plan_episodes(vopp_agent *agent, const vopp_episode_params *params, double budget_s,
+                                      vopp_plan_result *out, int32_t *depth_reached, int32_t *n_nodes);
 /* vopp_plan_anytime from the agent's particles. */
 VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *params, double budget_s,
                                      vopp_plan_result *out, int32_t *depth_reached);

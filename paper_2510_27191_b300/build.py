@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libvopp.so")
-SOURCES = ["vopp_api.cu", "vopp_kernels.cu", "vopp_noalloc.cu", "vopp_pipes.cu"]
+SOURCES = ["vopp_api.cu", "vopp_kernels.cu", "vopp_noalloc.cu", "vopp_pipes.cu", "vopp_episodes.cu"]
 HEADERS = ["vopp_device.cuh", "vopp_internal.h"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-shared",

@@ -132,6 +132,7 @@ struct vopp_ctx {
   // last launch, for vopp_tree_read
   std::vector<PlanDesc> last_desc;
   std::vector<int> last_ok;
+  EpisodeStore *episodes = nullptr;   // buffers of the last episode-mode plan
 };
 
 struct vopp_model {
@@ -849,6 +850,11 @@ const DevModel *model_device_tables(const vopp_model *m) { return m->dev; }
 int model_kind(const vopp_model *m) { return m->desc.kind; }
 int model_device(const vopp_model *m) { return m->ctx->device; }
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+const vopp_model_desc &model_desc(const vopp_model *m) { return m->desc; }
+vopp_ctx *model_ctx(const vopp_model *m) { return m->ctx; }
+cudaStream_t model_stream(const vopp_model *m) { return m->ctx->stream; }
+cudaStream_t ctx_stream(const vopp_ctx *c) { return c->stream; }
+EpisodeStore *&ctx_episode_store(vopp_ctx *c) { return c->episodes; }
 }  // namespace vopp
 
 // ---------------------------------------------------------------------------------------
@@ -887,6 +893,7 @@ void vopp_ctx_destroy(vopp_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   c->graph.release();
+  free_episode_store(c->episodes);
   if (c->arena) cudaFree(c->arena);
   free_slot(c->slot);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -1421,6 +1428,14 @@ int vopp_agent_plan_anytime(vopp_agent *g, const vopp_plan_params *p, double bud
   j.log_weights = g->lw;
   cudaSetDevice(c->device);
   return run_anytime(c, j, budget_s, out, depth_reached);
+}
+
+int vopp_agent_plan_episodes(vopp_agent *g, const vopp_episode_params *p, double budget_s,
+                             vopp_plan_result *out, int32_t *depth_reached, int32_t *n_nodes) {
+  if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  vopp::EpisodeInputs in{states, nullptr, g->lw, g->N, VOPP_PTR_DEVICE};
+  return vopp::run_plan_episodes(g->model, in, *p, budget_s, out, depth_reached, n_nodes);
 }
 
 int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "vopp.h"
 #include "vopp_device.cuh"
 
 namespace vopp {
@@ -67,10 +68,31 @@ cudaError_t launch_env(const EnvArgs &E, cudaStream_t s);
 }  // namespace vopp
 
 struct vopp_model;
+struct vopp_ctx;
 namespace vopp {
 const DevModel *model_device_tables(const vopp_model *m);
 int model_kind(const vopp_model *m);
 int model_device(const vopp_model *m);
+const vopp_model_desc &model_desc(const vopp_model *m);
+vopp_ctx *model_ctx(const vopp_model *m);
+cudaStream_t model_stream(const vopp_model *m);
+cudaStream_t ctx_stream(const vopp_ctx *c);
 int set_error(int code, const char *msg);   // records the thread-local message, returns code
+
+// Episode mode (vopp_episodes.cu): buffers of a context's last episode-mode plan.
+struct EpisodeStore;
+EpisodeStore *&ctx_episode_store(vopp_ctx *c);
+void free_episode_store(EpisodeStore *s);
+struct EpisodeInputs {
+  const void *states;         // NAV2D float[2N] (x then y), GRID / TOY2 int32[N]
+  const float *weights;       // linear weights or null (uniform)
+  const float *log_weights;   // device log weights (agents) or null
+  int N;
+  uint32_t ptr_flags;
+};
+int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode_params &p,
+                      double budget_s, vopp_plan_result *out, int32_t *depth_reached,
+                      int32_t *n_nodes);
+int episode_tree_read(vopp_ctx *c, int32_t field, uint64_t offset, uint64_t count, void *dst);
 
 }  // namespace vopp

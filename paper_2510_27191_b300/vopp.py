@@ -92,6 +92,15 @@ class vopp_episode_result(ctypes.Structure):
                 ("particle_steps", ctypes.c_uint64), ("plan_seconds", ctypes.c_double)]
 
 
+class vopp_episode_params(ctypes.Structure):
+    _fields_ = [("episodes", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("eta", ctypes.c_float), ("gamma", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("max_nodes", ctypes.c_int32)]
+
+
+(VOPP_EP_PARENT, VOPP_EP_DEPTH, VOPP_EP_PSI, VOPP_EP_V, VOPP_EP_REWARD, VOPP_EP_VISITS) = range(6)
+
+
 class vopp_plan_request(ctypes.Structure):
     _fields_ = [("model", ctypes.c_void_p), ("root_states", ctypes.c_void_p),
                 ("root_weights", ctypes.c_void_p), ("n_particles", ctypes.c_int32),
@@ -155,6 +164,13 @@ def _load():
         "vopp_plan_anytime": ([vp, vp, vp, i32, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
                                u32, ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
                               ctypes.c_int),
+        "vopp_plan_episodes": ([vp, vp, vp, i32, ctypes.POINTER(vopp_episode_params), ctypes.c_double,
+                                u32, ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32)], ctypes.c_int),
+        "vopp_agent_plan_episodes": ([vp, ctypes.POINTER(vopp_episode_params), ctypes.c_double,
+                                      ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32)], ctypes.c_int),
+        "vopp_episode_tree_read": ([vp, i32, u64, u64, vp], ctypes.c_int),
         "vopp_env_create": ([vp, vp, u64, ctypes.POINTER(vp)], ctypes.c_int),
         "vopp_env_step": ([vp, i32, vp, fp, ctypes.POINTER(i32)], ctypes.c_int),
         "vopp_env_get_state": ([vp, vp], ctypes.c_int),
@@ -404,6 +420,52 @@ def vopp_belief_update_noalloc(model: int, states, log_weights, action: int, obs
                                          None if ancestors is None else ancestors.data_ptr(),
                                          ctypes.byref(ess), ctypes.byref(res)))
     return ess.value, bool(res.value)
+
+
+# ---- episode mode ------------------------------------------------------------------------
+def _episode_params(episodes, max_depth, eta, gamma, seed, max_nodes=0):
+    p = vopp_episode_params()
+    p.episodes, p.max_depth, p.eta, p.gamma = int(episodes), int(max_depth), float(eta), float(gamma)
+    p.seed, p.max_nodes = int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_nodes)
+    return p
+
+
+def vopp_plan_episodes(model: int, root_states, root_weights, n_particles: int, episodes: int,
+                       max_depth: int, eta: float, gamma: float, seed: int,
+                       budget_s: float = 0.0, max_nodes: int = 0) -> dict:
+    """Episode mode; the result dict carries ``depth_reached`` and ``n_nodes``."""
+    sp, sdev, k1 = _addr(root_states)
+    wp, _, k2 = _addr(root_weights)
+    p = _episode_params(episodes, max_depth, eta, gamma, seed, max_nodes)
+    r = vopp_plan_result()
+    d, n = ctypes.c_int32(), ctypes.c_int32()
+    check(lib.vopp_plan_episodes(model, sp, wp, n_particles, ctypes.byref(p), float(budget_s),
+                                 VOPP_PTR_DEVICE if sdev else 0, ctypes.byref(r), ctypes.byref(d),
+                                 ctypes.byref(n)))
+    del k1, k2
+    out = _result_dict(r, vopp_model_num_actions(model))
+    out["depth_reached"], out["n_nodes"] = d.value, n.value
+    return out
+
+
+def vopp_agent_plan_episodes(agent: int, model: int, episodes: int, max_depth: int, eta: float,
+                             gamma: float, seed: int, budget_s: float = 0.0) -> dict:
+    p = _episode_params(episodes, max_depth, eta, gamma, seed)
+    r = vopp_plan_result()
+    d, n = ctypes.c_int32(), ctypes.c_int32()
+    check(lib.vopp_agent_plan_episodes(agent, ctypes.byref(p), float(budget_s), ctypes.byref(r),
+                                       ctypes.byref(d), ctypes.byref(n)))
+    out = _result_dict(r, vopp_model_num_actions(model))
+    out["depth_reached"], out["n_nodes"] = d.value, n.value
+    return out
+
+
+def vopp_episode_tree_read(ctx: int, field: int, count: int, offset: int = 0) -> np.ndarray:
+    dtype = {VOPP_EP_PARENT: np.int32, VOPP_EP_DEPTH: np.int32,
+             VOPP_EP_VISITS: np.uint64}.get(field, np.float64)
+    out = np.empty(count, dtype=dtype)
+    check(lib.vopp_episode_tree_read(ctx, field, offset, count, out.ctypes.data))
+    return out
 
 
 # ---- closed loop -------------------------------------------------------------------------
