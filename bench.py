@@ -273,6 +273,77 @@ def cpu_baseline(spec, budget_s=20.0):
                       f"single thread: {n1} subtrees, {done1} particle-steps, {dt1:.1f} s"}
 
 
+def modes_run(V, ctx, spec, dev_states):
+    """The other planning modes on the same device: anytime deepening of the workload's plan
+    (to its depth, and under 2 ms and 50 ms budgets), episode mode at 60,000 parallel
+    episodes (the paper's largest batch) on both models, and one closed-loop grid episode."""
+    import torch
+    out = {}
+    rx, ry = WL.grid_layout(spec.layout_seed)
+    model = V.vopp_create_model(ctx, V.make_desc(spec.kind, pi_mode=spec.pi_mode,
+                                                 pi_temp=spec.pi_temp,
+                                                 rock_x=rx if spec.kind == WL.GRID else None,
+                                                 rock_y=ry if spec.kind == WL.GRID else None))
+
+    def timed(fn, reps=3):
+        fn()
+        ts, r = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)), r
+
+    t, r = timed(lambda: V.vopp_plan_anytime(model, dev_states, None, spec.N, spec.D, spec.W,
+                                             spec.eta, spec.gamma, spec.seed))
+    out["anytime"] = {"max_depth": spec.D, "depth_reached": r["depth_reached"], "ms": 1e3 * t,
+                      "particle_steps": r["particle_steps"],
+                      "particle_steps_per_s": r["particle_steps"] / t}
+    for budget in (0.002, 0.05):   # the next iteration starts while under budget (Alg. 1)
+        t, r = timed(lambda: V.vopp_plan_anytime(model, dev_states, None, spec.N, spec.D + 2,
+                                                 spec.W, spec.eta, spec.gamma, spec.seed,
+                                                 budget_s=budget))
+        out[f"anytime_budget_{int(budget * 1e3)}ms"] = {
+            "max_depth": spec.D + 2, "depth_reached": r["depth_reached"], "ms": 1e3 * t,
+            "particle_steps": r["particle_steps"]}
+    V.vopp_model_destroy(model)
+    eps = {}
+    rx, ry = WL.grid_layout(1)
+    for name, kind in (("grid", WL.GRID), ("nav", WL.NAV2D)):
+        m = V.vopp_create_model(ctx, V.make_desc(kind, rock_x=rx if kind == WL.GRID else None,
+                                                 rock_y=ry if kind == WL.GRID else None))
+        if kind == WL.GRID:
+            st, _ = WL.grid_root(2048, 1)
+            st = torch.from_numpy(st.astype(np.int32)).cuda()
+        else:
+            x, y, _ = WL.nav_root(2048, 1)
+            st = torch.from_numpy(np.concatenate([x, y]).astype(np.float32)).cuda()
+        t, r = timed(lambda: V.vopp_plan_episodes(m, st, None, 2048, 60000, 6, 1.0, 0.95, 5))
+        eps[name] = {"episodes": 60000, "depth_reached": r["depth_reached"], "ms": 1e3 * t,
+                     "nodes": r["n_nodes"], "model_steps": r["particle_steps"],
+                     "model_steps_per_s": r["particle_steps"] / t}
+        V.vopp_model_destroy(m)
+    out["episodes"] = eps
+    m = V.vopp_create_model(ctx, V.make_desc(WL.GRID, rock_x=rx, rock_y=ry))
+    st, _ = WL.grid_root(1024, 2)
+    g = V.vopp_agent_create(m, st.astype(np.int32), None, 1024, 2)
+    env = V.vopp_env_create(m, int(WL.pack_grid_state(np.array([0b10110101]), *WL.GRID_START)[0]),
+                            9, WL.GRID)
+    t0 = time.perf_counter()
+    ep, acts, rews = V.vopp_run_episode(g, env, 4, 3, 1.0, 0.95, 100, 60)
+    dt = time.perf_counter() - t0
+    out["closed_loop_grid"] = {"steps": ep["steps"], "terminated": ep["terminated"],
+                               "discounted_return": ep["discounted_return"],
+                               "plan_depth": 4, "particles": 1024, "wall_s": dt,
+                               "plan_s": ep["plan_seconds"], "status": ep["status"]}
+    V.vopp_env_destroy(env)
+    V.vopp_agent_destroy(g)
+    V.vopp_model_destroy(m)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,7 +353,8 @@ def main():
     ap.add_argument("--workload", default="nav1024_d4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-serve", action="store_true",
-                    help="skip the batched (512 mixed plans) and served (Poisson requests) legs")
+                    help="skip the batched (512 mixed plans), served (Poisson requests) and "
+                         "other-mode (anytime, episodes, closed loop) legs")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
@@ -422,6 +494,8 @@ def main():
                     if mode == "served":
                         served[f"{mode}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
             out["served"] = served
+        if not args.no_batch_serve:
+            out["modes"] = modes_run(V, ctx, spec, dev_states)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(spec)
         print(json.dumps(out))
