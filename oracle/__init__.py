@@ -31,11 +31,11 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 MAXA = 16
 MAXD = 8
-NAV2D, GRID, TOY2 = 0, 1, 2
+NAV2D, GRID, TOY2, CROWD = 0, 1, 2, 3
 SAMPLE, ENUMERATE = 0, 1
 PI_UNIFORM, PI_FIXED, PI_NAV_DIST = 0, 1, 2
 OK, E_INVALID, E_NOMEM, E_DEGENERATE = 0, -1, -2, -6
-NUM_ACTIONS = {NAV2D: 4, GRID: 13, TOY2: 2}
+NUM_ACTIONS = {NAV2D: 4, GRID: 13, TOY2: 2, CROWD: 5}
 
 _lock = threading.Lock()
 _lib = None
@@ -80,13 +80,14 @@ class PlanArgs(ctypes.Structure):
                 ("q_root", ctypes.c_double * MAXA), ("policy", ctypes.c_double * MAXA),
                 ("near_threshold", ctypes.c_longlong), ("degenerate", ctypes.c_longlong),
                 ("particle_steps", ctypes.c_longlong),
-                ("psi", _dp), ("psi_new_level", ctypes.c_int)]
+                ("psi", _dp), ("psi_new_level", ctypes.c_int),
+                ("root_pf", _dp), ("ppf", _dp)]
 
 
 class BuResult(ctypes.Structure):
     _fields_ = [("ess", ctypes.c_double), ("resampled", ctypes.c_int), ("ess_tie", ctypes.c_int),
                 ("near_ties", ctypes.c_longlong), ("ties", _up), ("prop_x", _dp), ("prop_y", _dp),
-                ("prop_s", _ip)]
+                ("prop_s", _ip), ("pf", _dp)]
 
 
 def lib():
@@ -99,6 +100,10 @@ def lib():
             L.orc_uniform.argtypes = [ctypes.c_uint32]
             L.orc_uniform.restype = ctypes.c_double
             L.orc_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _dp, _dp]
+            L.orc_crowd_loglik.argtypes = [ctypes.c_int32, ctypes.c_int]
+            L.orc_crowd_loglik.restype = ctypes.c_double
+            L.orc_crowd_heuristic.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_double]
+            L.orc_crowd_heuristic.restype = ctypes.c_double
             L.orc_grid_acc.argtypes = [ctypes.c_int]
             L.orc_grid_acc.restype = ctypes.c_double
             L.orc_grid_threshold.argtypes = [ctypes.c_int]
@@ -185,12 +190,15 @@ def level_offsets(A: int, W: int, D: int, P: int = 0) -> np.ndarray:
 
 def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: int,
          root_x=None, root_y=None, root_s=None, root_w=None, path=(), dump_levels: int = -1,
-         outputs: bool = True, psi=None, psi_new_level: int = 0):
+         outputs: bool = True, psi=None, psi_new_level: int = 0, root_pf=None):
     """Run one full-width plan (or the subtree below ``path``) and return a result dict.
 
     Per-level arrays are returned as lists indexed by level: ``V[l]`` (levels 0..D),
     ``Q[l]`` (levels 0..D-1, shape [n_l, A]), ``rbar/lomega/rep/obs/near[l]`` (levels 1..D,
     indexed by the branch's child node), and the particle dumps ``px/py/plw/ps[l]``.
+
+    CROWD: root_x / root_y are the robot, root_s the flags and ``root_pf`` [12, N] the people
+    (rows 2q, 2q+1 = person q's x, y); the dumps add ``ppf`` [nodes, 12, N].
 
     ``psi`` (float64, updated in place, one row of A preferences per internal node,
     concatenated by level) switches the backup to the persistent preference update of
@@ -219,18 +227,23 @@ def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: i
         io.obs, io.rep, io.near = _ptr(arrs["obs"], _dp), _ptr(arrs["rep"], _ip), _ptr(arrs["near"], _up)
     if dump_levels >= 0:
         dtot = int(off[min(dump_levels, D) + 1]) * N
-        if model.kind == NAV2D:
+        if model.kind in (NAV2D, CROWD):
             arrs["px"], arrs["py"] = np.zeros(dtot), np.zeros(dtot)
             io.px, io.py = _ptr(arrs["px"], _dp), _ptr(arrs["py"], _dp)
-        else:
+        if model.kind != NAV2D:
             arrs["ps"] = np.zeros(dtot, dtype=np.int32)
             io.ps = _ptr(arrs["ps"], _ip)
+        if model.kind == CROWD:
+            arrs["ppf"] = np.zeros(dtot * 12)
+            io.ppf = _ptr(arrs["ppf"], _dp)
         arrs["plw"] = np.zeros(dtot)
         io.plw = _ptr(arrs["plw"], _dp)
     rx = None if root_x is None else np.ascontiguousarray(root_x, dtype=np.float64)
     ry = None if root_y is None else np.ascontiguousarray(root_y, dtype=np.float64)
     rs = None if root_s is None else np.ascontiguousarray(root_s, dtype=np.int32)
     rw = None if root_w is None else np.ascontiguousarray(root_w, dtype=np.float64)
+    rpf = None if root_pf is None else np.ascontiguousarray(root_pf, dtype=np.float64).ravel()
+    io.root_pf = _ptr(rpf, _dp)
     rc = lib().orc_plan(ctypes.byref(model), _ptr(rx, _dp), _ptr(ry, _dp), _ptr(rs, _ip),
                         _ptr(rw, _dp), ctypes.byref(io))
     res = dict(status=rc, action=io.action, v_root=io.v_root,
@@ -250,11 +263,15 @@ def plan(model: Model, N: int, D: int, W: int, eta: float, gamma: float, seed: i
         for k in ("px", "py", "ps", "plw"):
             if k in arrs:
                 res[k] = [arrs[k][off[l] * N:off[l + 1] * N].reshape(-1, N) for l in range(nl)]
+        if "ppf" in arrs:
+            res["ppf"] = [arrs["ppf"][off[l] * N * 12:off[l + 1] * N * 12].reshape(-1, 12, N)
+                          for l in range(nl)]
     return res
 
 
 def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float, seed: int,
-                 root_x=None, root_y=None, root_s=None, root_w=None, outputs: bool = False):
+                 root_x=None, root_y=None, root_s=None, root_w=None, outputs: bool = False,
+                 root_pf=None):
     """Anytime iterative deepening (Alg. 1 planning loop): iterations k = 1..K each search
     the full-width tree of depth k with the same random numbers and back it up with the
     preference update of Eq. 3 on preferences that persist across iterations (the nodes of
@@ -269,7 +286,7 @@ def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float,
     for k in range(1, K + 1):
         res = plan(model, N, k, W, eta, gamma, seed, root_x=root_x, root_y=root_y,
                    root_s=root_s, root_w=root_w, outputs=outputs and k == K, psi=psi,
-                   psi_new_level=k - 1)
+                   psi_new_level=k - 1, root_pf=root_pf)
         if res["status"] != OK:
             return res
         q_iters.append(res["q_root"].copy())
@@ -282,7 +299,7 @@ def plan_anytime(model: Model, N: int, K: int, W: int, eta: float, gamma: float,
 class EpisodeArgs(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("O", ctypes.c_int),
                 ("eta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("cap", ctypes.c_int),
+                ("cap", ctypes.c_int), ("root_pf", _dp),
                 ("parent_an", _ip), ("depth", _ip),
                 ("psi", _dp), ("V", _dp), ("C", _dp), ("Ws", _dp), ("Hs", _dp),
                 ("N", ctypes.POINTER(ctypes.c_int64)), ("Nl", ctypes.POINTER(ctypes.c_int64)),
@@ -293,11 +310,12 @@ class EpisodeArgs(ctypes.Structure):
                 ("near_threshold", ctypes.c_longlong)]
 
 
-NUM_OBS = {NAV2D: 0, GRID: 3, TOY2: 2}
+NUM_OBS = {NAV2D: 0, GRID: 3, TOY2: 2, CROWD: 64}
 
 
 def plan_episodes(model: Model, M: int, K: int, eta: float, gamma: float, seed: int,
-                  root_x=None, root_y=None, root_s=None, root_w=None, cap: int = 0):
+                  root_x=None, root_y=None, root_s=None, root_w=None, cap: int = 0,
+                  root_pf=None):
     """Episode mode (Alg. 1-3 as printed): K planning iterations of M sampled episodes, the
     tree grown by first visits, visit-weighted backups of the persistent preferences.
     Returns the root result and the tree arrays (``parent_an``, ``depth``, ``psi``, ``V``,
@@ -322,6 +340,8 @@ def plan_episodes(model: Model, M: int, K: int, eta: float, gamma: float, seed: 
     ry = None if root_y is None else np.ascontiguousarray(root_y, dtype=np.float64)
     rs = None if root_s is None else np.ascontiguousarray(root_s, dtype=np.int32)
     rw = None if root_w is None else np.ascontiguousarray(root_w, dtype=np.float64)
+    rpf = None if root_pf is None else np.ascontiguousarray(root_pf, dtype=np.float64).ravel()
+    io.root_pf = _ptr(rpf, _dp)
     rc = lib().orc_plan_episodes(ctypes.byref(model), _ptr(rx, _dp), _ptr(ry, _dp),
                                  _ptr(rs, _ip), _ptr(rw, _dp), Np, ctypes.byref(io))
     n = io.n_nodes
@@ -338,24 +358,38 @@ def plan_episodes(model: Model, M: int, K: int, eta: float, gamma: float, seed: 
 
 def env_step(model: Model, state, action: int, seed: int, t: int):
     """One step of the true state (closed loop, Alg. 1): returns (status, next state,
-    observation, reward, terminal); state is (x, y) for NAV2D, an int for GRID / TOY2."""
+    observation, reward, terminal); state is (x, y) for NAV2D, an int for GRID / TOY2 and
+    (x, y, flags, people[12]) for CROWD."""
+    pf = None
     if model.kind == NAV2D:
         x, y, s = ctypes.c_double(state[0]), ctypes.c_double(state[1]), ctypes.c_int32(0)
+    elif model.kind == CROWD:
+        x, y, s = ctypes.c_double(state[0]), ctypes.c_double(state[1]), ctypes.c_int32(int(state[2]))
+        pf = np.ascontiguousarray(state[3], dtype=np.float64).copy()
     else:
         x, y, s = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(int(state))
     o = (ctypes.c_double * 2)()
     r = ctypes.c_double()
     term = ctypes.c_int()
     rc = lib().orc_env_step(ctypes.byref(model), ctypes.byref(x), ctypes.byref(y),
-                            ctypes.byref(s), int(action), ctypes.c_uint64(seed & (2**64 - 1)),
-                            ctypes.c_uint64(t), o, ctypes.byref(r), ctypes.byref(term))
-    nxt = (x.value, y.value) if model.kind == NAV2D else s.value
+                            ctypes.byref(s), _ptr(pf, _dp), int(action),
+                            ctypes.c_uint64(seed & (2**64 - 1)), ctypes.c_uint64(t), o,
+                            ctypes.byref(r), ctypes.byref(term))
+    if model.kind == NAV2D:
+        nxt = (x.value, y.value)
+    elif model.kind == CROWD:
+        nxt = (x.value, y.value, s.value, pf)
+    else:
+        nxt = s.value
     obs = (o[0], o[1]) if model.kind == NAV2D else int(o[0])
     return rc, nxt, obs, r.value, bool(term.value)
 
 
-def belief_update(model: Model, lw, action: int, obs, seed: int, t: int, x=None, y=None, s=None):
-    """SIR update in place on float64 copies; returns (status, dict of new arrays)."""
+def belief_update(model: Model, lw, action: int, obs, seed: int, t: int, x=None, y=None, s=None,
+                  pf=None):
+    """SIR update in place on float64 copies; returns (status, dict of new arrays).  CROWD:
+    x, y the robot, s the flags, pf [12, N] the people."""
+    pf = None if pf is None else np.array(pf, dtype=np.float64).reshape(12, -1).copy()
     N = len(lw)
     lw = np.array(lw, dtype=np.float64)
     x = None if x is None else np.array(x, dtype=np.float64)
@@ -370,12 +404,21 @@ def belief_update(model: Model, lw, action: int, obs, seed: int, t: int, x=None,
     ps = np.zeros(N, dtype=np.int32) if s is not None else None
     r = BuResult()
     r.ties, r.prop_x, r.prop_y, r.prop_s = _ptr(ties, _up), _ptr(px, _dp), _ptr(py, _dp), _ptr(ps, _ip)
+    r.pf = _ptr(pf, _dp)
     rc = lib().orc_belief_update(ctypes.byref(model), N, _ptr(x, _dp), _ptr(y, _dp), _ptr(s, _ip),
                                  _ptr(lw, _dp), action, _ptr(o, _dp), seed, t, _ptr(anc, _ip),
                                  ctypes.byref(r))
     return rc, dict(x=x, y=y, s=s, lw=lw, ancestors=anc, ess=r.ess, resampled=bool(r.resampled),
                     ess_tie=bool(r.ess_tie), near_ties=r.near_ties, ties=ties.astype(bool),
-                    prop_x=px, prop_y=py, prop_s=ps)
+                    prop_x=px, prop_y=py, prop_s=ps, pf=pf)
+
+
+def crowd_loglik(flags: int, obs: int) -> float:
+    return lib().orc_crowd_loglik(int(flags), int(obs))
+
+
+def crowd_heuristic(y: float, flags: int, gamma: float) -> float:
+    return lib().orc_crowd_heuristic(float(y), int(flags), float(gamma))
 
 
 def nav_heuristic(x: float, y: float, gamma: float) -> float:

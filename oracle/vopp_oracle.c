@@ -56,7 +56,7 @@
 #define ORC_MAXROCKS 8
 #define ORC_MAXW 64
 
-enum { ORC_NAV2D = 0, ORC_GRID = 1, ORC_TOY2 = 2 };
+enum { ORC_NAV2D = 0, ORC_GRID = 1, ORC_TOY2 = 2, ORC_CROWD = 3 };
 enum { ORC_SAMPLE = 0, ORC_ENUMERATE = 1 };
 enum { ORC_PI_UNIFORM = 0, ORC_PI_FIXED = 1, ORC_PI_NAV_DIST = 2 };
 enum { ORC_OK = 0, ORC_E_INVALID = -1, ORC_E_NOMEM = -2, ORC_E_DEGENERATE = -6 };
@@ -104,6 +104,10 @@ typedef struct {
    * psi_new_level start from Psi_0 = eta log pibar. */
   double *psi;             /* [sum_{l<D} n_l * A] or NULL                                   */
   int psi_new_level;
+  /* CROWD: root people coordinates [12][N] (px_q = row 2q, py_q = row 2q + 1); dumps of the
+   * people coordinates [sum_{l<=dump} n_l][12][N] (robot in px/py, flags in ps) */
+  const double *root_pf;
+  double *ppf;
 } orc_plan_args;
 
 /* ------------------------------------------------------------------------------------ */
@@ -127,16 +131,21 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-static void draw(uint64_t seed, uint32_t idx, uint32_t purpose, uint32_t level, uint32_t action,
-                 uint32_t branch, uint64_t node, uint32_t out[4]) {
+static void draw_j(uint64_t seed, uint32_t idx, uint32_t purpose, uint32_t level, uint32_t action,
+                   uint32_t branch, uint32_t call, uint64_t node, uint32_t out[4]) {
   uint32_t ctr[4], key[2];
   ctr[0] = idx | (purpose << 24);
-  ctr[1] = level | (action << 8) | (branch << 16);
+  ctr[1] = level | (action << 8) | (branch << 16) | (call << 24);
   ctr[2] = (uint32_t)node;
   ctr[3] = (uint32_t)(node >> 32);
   key[0] = (uint32_t)seed;
   key[1] = (uint32_t)(seed >> 32);
   orc_philox4x32_10(ctr, key, out);
+}
+
+static void draw(uint64_t seed, uint32_t idx, uint32_t purpose, uint32_t level, uint32_t action,
+                 uint32_t branch, uint64_t node, uint32_t out[4]) {
+  draw_j(seed, idx, purpose, level, action, branch, 0, node, out);
 }
 
 double orc_uniform(uint32_t x) { return (2.0 * (double)(x >> 9) + 1.0) * (1.0 / 16777216.0); }
@@ -164,10 +173,20 @@ static double log_sum_exp(const double *v, int n) {
 /* ------------------------------------------------------------------------------------ */
 /* The three generative models G(s,a) -> (s', o, r) (Sec. III-B).                         */
 /* ------------------------------------------------------------------------------------ */
-int orc_num_actions(int kind) { return kind == ORC_NAV2D ? 4 : kind == ORC_GRID ? 13 : 2; }
-static int num_obs(int kind) { return kind == ORC_NAV2D ? 0 : kind == ORC_GRID ? 3 : 2; }
+int orc_num_actions(int kind) {
+  return kind == ORC_NAV2D ? 4 : kind == ORC_GRID ? 13 : kind == ORC_CROWD ? 5 : 2;
+}
+static int num_obs(int kind) {
+  return kind == ORC_NAV2D ? 0 : kind == ORC_GRID ? 3 : kind == ORC_CROWD ? 64 : 2;
+}
 
-typedef struct { double x, y; int32_t s; } pstate;
+/* particle state: NAV2D (x, y); GRID / TOY2 s; CROWD robot (x, y), people (px, py), s = flags */
+#define CR_N 6
+typedef struct { double x, y; int32_t s; double px[CR_N], py[CR_N]; } pstate;
+
+/* Counter of a particle's random numbers (CROWD draws several Philox calls per step; call j
+ * sits in bits 24-31 of the second counter word, which the other models leave 0). */
+typedef struct { uint64_t seed; uint32_t idx, purpose, level, action, branch; uint64_t node; } orc_ctr;
 
 /* NAV2D: (x,y) in [0,10]^2, goal disc of radius 0.5 at the origin is absorbing. */
 static const double NAV_DX[4] = {1.0, -1.0, 0.0, 0.0};
@@ -202,9 +221,109 @@ static int grid_d2(const orc_model *m, int32_t s, int rock) {
   return dx * dx + dy * dy;
 }
 
-/* One transition step.  words: the two Philox words of this particle (NAV2D only). */
+/* CROWD (Sec. IV, CrowdNav): a robot in a 50 x 40 m hall and the CR_N nearest people, each
+ * curious or shy (hidden).  Actions 0 NORTH, 1 EAST, 2 SOUTH, 3 WEST (1 m), 4 YELL.  Every
+ * person moves by N(0, 0.05^2) noise per axis; a person within 4 m of the robot's new
+ * position reacts with probability 0.9 -- curious toward it by 0.3 m (never past it), shy
+ * away by 0.8 m -- and under YELL every such person backs away by 2 m instead.  People stay
+ * in the hall; the robot is held by the east, west and south walls and leaves through the
+ * north border (y >= 40: +1000, terminal).  Reward -1 per step, -25 for YELL, -200 per
+ * person within 0.5 m after the step.  Observation: per person, whether the distance to
+ * the robot's new position decreased, each bit flipped with probability q = floor(0.1 2^32)
+ * / 2^32.  Flags: bits 0-5 traits (1 = curious), 8-13 the true "came closer" bits, 16
+ * terminal. */
+#define CR_W 50.0
+#define CR_H 40.0
+#define CR_RNEAR 4.0
+#define CR_VCUR 0.3
+#define CR_VSHY 0.8
+#define CR_VBACK 2.0
+#define CR_SIGP 0.05
+#define CR_RBUMP 0.5
+static const double CR_DX[5] = {0.0, 1.0, 0.0, -1.0, 0.0};
+static const double CR_DY[5] = {1.0, 0.0, -1.0, 0.0, 0.0};
+static const uint32_t CR_REACT_THR = 3865470566u;   /* floor(0.9 * 2^32) */
+static const uint32_t CR_FLIP_THR = 429496729u;     /* floor(0.1 * 2^32) */
+#define CR_TERM(s) (((s) >> 16) & 1)
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static void crowd_step(const pstate *in, int a, const orc_ctr *c, pstate *out, double *reward) {
+  *out = *in;
+  if (CR_TERM(in->s)) { *reward = 0.0; return; }
+  uint32_t w[5][4];
+  for (uint32_t j = 0; j < 5; ++j)
+    draw_j(c->seed, c->idx, c->purpose, c->level, c->action, c->branch, j, c->node, w[j]);
+  double r = -1.0 + (a == 4 ? -25.0 : 0.0);
+  const double nx = clampd(in->x + CR_DX[a], 0.0, CR_W), ny = in->y + CR_DY[a] < 0.0 ? 0.0 : in->y + CR_DY[a];
+  out->x = nx;
+  out->y = ny;
+  const int traits = in->s & 0x3F;
+  int closer = 0;
+  const int exited = ny >= CR_H;
+  for (int i = 0; i < CR_N; ++i) {
+    double px = in->px[i], py = in->py[i];
+    const double d0 = hypot(px - nx, py - ny);
+    if (d0 < CR_RNEAR && d0 > 0.0) {
+      const double ux = (px - nx) / d0, uy = (py - ny) / d0;   /* away from the robot */
+      const uint32_t wr = i < 4 ? w[3][i] : w[4][i - 4];
+      if (a == 4) {
+        px += CR_VBACK * ux; py += CR_VBACK * uy;
+      } else if (wr < CR_REACT_THR) {
+        if ((traits >> i) & 1) {
+          const double st = d0 < CR_VCUR ? d0 : CR_VCUR;
+          px -= st * ux; py -= st * uy;
+        } else {
+          px += CR_VSHY * ux; py += CR_VSHY * uy;
+        }
+      }
+    }
+    double g1, g2;
+    orc_box_muller(w[i / 2][2 * (i % 2)], w[i / 2][2 * (i % 2) + 1], &g1, &g2);
+    px = clampd(px + CR_SIGP * g1, 0.0, CR_W);
+    py = clampd(py + CR_SIGP * g2, 0.0, CR_H);
+    const double d1 = hypot(px - nx, py - ny);
+    if (d1 < d0) closer |= 1 << i;
+    if (!exited && d1 < CR_RBUMP) r -= 200.0;
+    out->px[i] = px;
+    out->py[i] = py;
+  }
+  if (exited) r += 1000.0;
+  out->s = traits | (closer << 8) | (exited << 16);
+  *reward = r;
+}
+
+/* observation bits: word k of the branch's calls decides the flip of bit k */
+static int crowd_draw_obs(const pstate *sp, const orc_ctr *c) {
+  uint32_t w0[4], w1[4];
+  draw_j(c->seed, c->idx, c->purpose, c->level, c->action, c->branch, 0, c->node, w0);
+  draw_j(c->seed, c->idx, c->purpose, c->level, c->action, c->branch, 1, c->node, w1);
+  const uint32_t u[CR_N] = {w0[0], w0[1], w0[3], w1[0], w1[1], w1[2]};
+  int o = 0;
+  for (int i = 0; i < CR_N; ++i) {
+    int bit = (sp->s >> (8 + i)) & 1;
+    if (u[i] < CR_FLIP_THR) bit ^= 1;
+    o |= bit << i;
+  }
+  return o;
+}
+
+static double crowd_loglik(const pstate *sp, int o) {
+  const double q = (double)CR_FLIP_THR / 4294967296.0;
+  double l = 0.0;
+  for (int i = 0; i < CR_N; ++i)
+    l += (((sp->s >> (8 + i)) & 1) == ((o >> i) & 1)) ? log(1.0 - q) : log(q);
+  return l;
+}
+
+/* One transition step.  wa, wb: the two Philox words of this particle (NAV2D); c: the
+ * counter of the particle's own calls (CROWD). */
 static void model_step(const orc_model *m, const pstate *in, int a, uint32_t wa, uint32_t wb,
-                       pstate *out, double *reward, long long *near) {
+                       const orc_ctr *c, pstate *out, double *reward, long long *near) {
+  if (m->kind == ORC_CROWD) {
+    crowd_step(in, a, c, out, reward);
+    return;
+  }
   if (m->kind == ORC_NAV2D) {
     if (nav_terminal(in->x, in->y)) { *out = *in; *reward = 0.0; return; }
     double g1, g2;
@@ -245,7 +364,12 @@ static void model_step(const orc_model *m, const pstate *in, int a, uint32_t wa,
 /* o ~ Z(. | s', a) drawn with Philox words (w0,w1).  NAV2D fills o[0..1]; discrete models
  * store the observation index in o[0]. */
 static void model_draw_obs(const orc_model *m, const pstate *sp, int a, uint32_t w0, uint32_t w1,
-                           double o[2]) {
+                           const orc_ctr *c, double o[2]) {
+  if (m->kind == ORC_CROWD) {
+    o[0] = (double)crowd_draw_obs(sp, c);
+    o[1] = 0.0;
+    return;
+  }
   if (m->kind == ORC_NAV2D) {
     double g3, g4, sg = nav_sigma(sp->x);
     orc_box_muller(w0, w1, &g3, &g4);
@@ -267,6 +391,11 @@ static void model_draw_obs(const orc_model *m, const pstate *sp, int a, uint32_t
 
 /* log Z(o | s', a); -inf where the observation is impossible. */
 static double model_loglik(const orc_model *m, const pstate *sp, int a, const double o[2]) {
+  if (m->kind == ORC_CROWD) {
+    const int oi = (int)o[0];
+    if (oi < 0 || oi > 63) return -INFINITY;
+    return crowd_loglik(sp, oi);
+  }
   if (m->kind == ORC_NAV2D) {
     double sg = nav_sigma(sp->x);
     double dx = o[0] - sp->x, dy = o[1] - sp->y;
@@ -299,6 +428,12 @@ static double model_heuristic(const orc_model *m, const pstate *s, double gamma)
   } else if (m->kind == ORC_GRID) {
     if (G_TERM(s->s)) return 0.0;
     return 10.0 * pow(gamma, (double)(10 - G_X(s->s)));
+  } else if (m->kind == ORC_CROWD) {
+    if (CR_TERM(s->s)) return 0.0;
+    double steps = CR_H - s->y;              /* 1 m moves north to the border (continuous) */
+    if (steps < 1.0) steps = 1.0;
+    double gk = pow(gamma, steps - 1.0);
+    return -(1.0 - gk) / (1.0 - gamma) + 1000.0 * gk;
   }
   return 0.0;
 }
@@ -306,6 +441,7 @@ static double model_heuristic(const orc_model *m, const pstate *s, double gamma)
 static int model_is_terminal(const orc_model *m, const pstate *s) {
   if (m->kind == ORC_NAV2D) return nav_terminal(s->x, s->y);
   if (m->kind == ORC_GRID) return G_TERM(s->s);
+  if (m->kind == ORC_CROWD) return CR_TERM(s->s);
   return 0;
 }
 
@@ -388,6 +524,11 @@ static void dump_particles(orc_tree *t, int l, long long lnode) {
     if (io->py) io->py[base + i] = t->lev[l][i].y;
     if (io->ps) io->ps[base + i] = t->lev[l][i].s;
     if (io->plw) io->plw[base + i] = t->lw[l][i];
+    if (io->ppf)
+      for (int q = 0; q < CR_N; ++q) {
+        io->ppf[(base * 12) + (2 * q) * t->N + i] = t->lev[l][i].px[q];
+        io->ppf[(base * 12) + (2 * q + 1) * t->N + i] = t->lev[l][i].py[q];
+      }
   }
 }
 
@@ -406,7 +547,8 @@ static void make_child(orc_tree *t, int l, uint64_t gnode, int a, int k, long lo
     uint32_t w[4] = {0, 0, 0, 0};
     if (m->kind == ORC_NAV2D) draw(io->seed, (uint32_t)(i / 2), 0, l, a, k, gnode, w);
     uint32_t wa = (i & 1) ? w[2] : w[0], wb = (i & 1) ? w[3] : w[1];
-    model_step(m, &par[i], a, wa, wb, &ch[i], &t->rew[i], &near);
+    const orc_ctr c = {io->seed, (uint32_t)i, 0, (uint32_t)l, (uint32_t)a, (uint32_t)k, gnode};
+    model_step(m, &par[i], a, wa, wb, &c, &ch[i], &t->rew[i], &near);
   }
   io->particle_steps += N;
 
@@ -417,7 +559,8 @@ static void make_child(orc_tree *t, int l, uint64_t gnode, int a, int k, long lo
     uint32_t w[4];
     draw(io->seed, 0, 1, l, a, k, gnode, w);
     j = (int)(((uint64_t)w[2] * (uint64_t)N) >> 32);
-    model_draw_obs(m, &ch[j], a, w[0], w[1], o);
+    const orc_ctr c = {io->seed, 0, 1, (uint32_t)l, (uint32_t)a, (uint32_t)k, gnode};
+    model_draw_obs(m, &ch[j], a, w[0], w[1], &c, o);
   } else {
     o[0] = (double)k;
     o[1] = 0.0;
@@ -599,6 +742,11 @@ int orc_plan(const orc_model *m, const double *root_x, const double *root_y,
       root[i].x = root_x ? root_x[i] : 0.0;
       root[i].y = root_y ? root_y[i] : 0.0;
       root[i].s = root_s ? root_s[i] : 0;
+      if (io->root_pf)
+        for (int q = 0; q < CR_N; ++q) {
+          root[i].px[q] = io->root_pf[(2 * q) * t.N + i];
+          root[i].py[q] = io->root_pf[(2 * q + 1) * t.N + i];
+        }
     }
     long long near = 0;
     rc = root_prep(m, root, root_w, t.N, t.lev[0], t.lw[0], &near);
@@ -645,11 +793,14 @@ typedef struct {
   uint8_t *ties;             /* optional [N]: output position within 1e-5 of a CDF boundary */
   double *prop_x, *prop_y;   /* optional [N]: propagated states before resampling */
   int32_t *prop_s;
+  double *pf;                /* CROWD people coordinates [12][N] (px_q = row 2q, py_q = 2q+1),
+                                updated like x, y, s; NULL for the other models */
 } orc_bu_result;
 
 int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *s, double *lw,
                       int action, const double *obs, uint64_t seed, uint64_t t_step,
                       int32_t *ancestors, orc_bu_result *res) {
+  double *pf = res->pf;
   if (N < 1 || action < 0 || action >= orc_num_actions(m->kind)) return ORC_E_INVALID;
   pstate *sp = (pstate *)calloc((size_t)N, sizeof(pstate));
   double *nl = (double *)calloc((size_t)N, sizeof(double));
@@ -661,10 +812,12 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
   /* propagate every particle through T, reweight by Z(o | s', a) */
   for (int i = 0; i < N; ++i) {
     pstate in = {x ? x[i] : 0.0, y ? y[i] : 0.0, s ? s[i] : 0};
+    if (pf) for (int q = 0; q < CR_N; ++q) { in.px[q] = pf[(2 * q) * N + i]; in.py[q] = pf[(2 * q + 1) * N + i]; }
     uint32_t w[4] = {0, 0, 0, 0};
     if (m->kind == ORC_NAV2D) draw(seed, (uint32_t)(i / 2), 3, 0, 0, 0, t_step, w);
     double r;
-    model_step(m, &in, action, (i & 1) ? w[2] : w[0], (i & 1) ? w[3] : w[1], &sp[i], &r, &near);
+    const orc_ctr c = {seed, (uint32_t)i, 3, 0, 0, 0, t_step};
+    model_step(m, &in, action, (i & 1) ? w[2] : w[0], (i & 1) ? w[3] : w[1], &c, &sp[i], &r, &near);
     nl[i] = lw[i] + model_loglik(m, &sp[i], action, o);
   }
   double ls = log_sum_exp(nl, N);
@@ -704,6 +857,7 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
       if (x) x[i] = a.x;
       if (y) y[i] = a.y;
       if (s) s[i] = a.s;
+      if (pf) for (int q = 0; q < CR_N; ++q) { pf[(2 * q) * N + i] = a.px[q]; pf[(2 * q + 1) * N + i] = a.py[q]; }
       lw[i] = -log((double)N);
     }
   } else {
@@ -711,6 +865,7 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
       if (x) x[i] = sp[i].x;
       if (y) y[i] = sp[i].y;
       if (s) s[i] = sp[i].s;
+      if (pf) for (int q = 0; q < CR_N; ++q) { pf[(2 * q) * N + i] = sp[i].px[q]; pf[(2 * q + 1) * N + i] = sp[i].py[q]; }
       lw[i] = nl[i];
       if (ancestors) ancestors[i] = i;
     }
@@ -721,6 +876,24 @@ int orc_belief_update(const orc_model *m, int N, double *x, double *y, int32_t *
 }
 
 /* Exposed pieces for the oracle's own pins. */
+double orc_crowd_loglik(int32_t flags, int o) {
+  pstate sp;
+  memset(&sp, 0, sizeof sp);
+  sp.s = flags;
+  return crowd_loglik(&sp, o);
+}
+
+double orc_crowd_heuristic(double y, int32_t flags, double gamma) {
+  orc_model m;
+  memset(&m, 0, sizeof m);
+  m.kind = ORC_CROWD;
+  pstate s;
+  memset(&s, 0, sizeof s);
+  s.y = y;
+  s.s = flags;
+  return model_heuristic(&m, &s, gamma);
+}
+
 double orc_nav_heuristic(double x, double y, double gamma) {
   orc_model m;
   memset(&m, 0, sizeof m);
@@ -731,7 +904,7 @@ double orc_nav_heuristic(double x, double y, double gamma) {
 int orc_grid_step(const orc_model *m, int32_t s, int a, int32_t *out, double *reward) {
   pstate in = {0.0, 0.0, s}, o;
   long long near = 0;
-  model_step(m, &in, a, 0, 0, &o, reward, &near);
+  model_step(m, &in, a, 0, 0, NULL, &o, reward, &near);
   *out = o.s;
   return ORC_OK;
 }
@@ -745,7 +918,7 @@ double orc_grid_loglik(const orc_model *m, int32_t s, int a, int obs) {
 int orc_grid_draw_obs(const orc_model *m, int32_t s, int a, uint32_t w0) {
   pstate sp = {0.0, 0.0, s};
   double o[2];
-  model_draw_obs(m, &sp, a, w0, 0, o);
+  model_draw_obs(m, &sp, a, w0, 0, NULL, o);
   return (int)o[0];
 }
 
@@ -755,7 +928,7 @@ void orc_nav_step(double x, double y, int a, uint32_t wa, uint32_t wb, double *o
   memset(&m, 0, sizeof m);
   pstate in = {x, y, 0}, o;
   long long near = 0;
-  model_step(&m, &in, a, wa, wb, &o, reward, &near);
+  model_step(&m, &in, a, wa, wb, NULL, &o, reward, &near);
   *ox = o.x;
   *oy = o.y;
 }
@@ -787,6 +960,7 @@ typedef struct {
   double eta, gamma;
   uint64_t seed;
   int cap;                 /* belief-node capacity of the arrays below                    */
+  const double *root_pf;   /* CROWD root people coordinates [12][Np], or NULL             */
   /* tree arrays, capacity cap (per action node: [cap * A]; child table: [cap * A * O]) */
   int32_t *parent_an;      /* parent action node b * A + a (-1 at the root)                */
   int32_t *depth;
@@ -849,6 +1023,11 @@ int orc_plan_episodes(const orc_model *m, const double *root_x, const double *ro
       root[i].x = root_x ? root_x[i] : 0.0;
       root[i].y = root_y ? root_y[i] : 0.0;
       root[i].s = root_s ? root_s[i] : 0;
+      if (io->root_pf)
+        for (int q = 0; q < CR_N; ++q) {
+          root[i].px[q] = io->root_pf[(2 * q) * Np + i];
+          root[i].py[q] = io->root_pf[(2 * q + 1) * Np + i];
+        }
       double w = root_w ? root_w[i] : 1.0;
       if (w < 0.0) rc = ORC_E_INVALID;
       if (model_is_terminal(m, &root[i])) w = 0.0;
@@ -892,9 +1071,11 @@ int orc_plan_episodes(const orc_model *m, const double *root_x, const double *ro
         pstate sp;
         double r, o[2];
         draw(io->seed, (uint32_t)e, 9, (uint32_t)d, 0, 0, (uint64_t)k, w);
-        model_step(m, &S[e], a, w[0], w[1], &sp, &r, &io->near_threshold);
+        const orc_ctr cs = {io->seed, (uint32_t)e, 9, (uint32_t)d, 0, 0, (uint64_t)k};
+        model_step(m, &S[e], a, w[0], w[1], &cs, &sp, &r, &io->near_threshold);
         draw(io->seed, (uint32_t)e, 10, (uint32_t)d, 0, 0, (uint64_t)k, w);
-        model_draw_obs(m, &sp, a, w[0], w[1], o);
+        const orc_ctr co = {io->seed, (uint32_t)e, 10, (uint32_t)d, 0, 0, (uint64_t)k};
+        model_draw_obs(m, &sp, a, w[0], w[1], &co, o);
         const long long an = (long long)b * A + a;
         io->C[an] += r;
         io->N[an] += 1;
@@ -972,16 +1153,19 @@ int orc_plan_episodes(const orc_model *m, const double *root_x, const double *ro
 /* the true state steps under the model's own transition and observation processes, with   */
 /* its own random numbers (purposes 5 and 6, node = time step t).                          */
 /* ------------------------------------------------------------------------------------ */
-int orc_env_step(const orc_model *m, double *x, double *y, int32_t *s, int a, uint64_t seed,
-                 uint64_t t, double obs[2], double *reward, int *terminal) {
+int orc_env_step(const orc_model *m, double *x, double *y, int32_t *s, double *pf, int a,
+                 uint64_t seed, uint64_t t, double obs[2], double *reward, int *terminal) {
   if (a < 0 || a >= orc_num_actions(m->kind)) return ORC_E_INVALID;
   pstate in = {*x, *y, *s}, out;
+  if (pf) for (int q = 0; q < CR_N; ++q) { in.px[q] = pf[2 * q]; in.py[q] = pf[2 * q + 1]; }
   long long near = 0;
   uint32_t w[4];
   draw(seed, 0, 5, 0, 0, 0, t, w);
-  model_step(m, &in, a, w[0], w[1], &out, reward, &near);
+  const orc_ctr cs = {seed, 0, 5, 0, 0, 0, t}, co = {seed, 0, 6, 0, 0, 0, t};
+  model_step(m, &in, a, w[0], w[1], &cs, &out, reward, &near);
   draw(seed, 0, 6, 0, 0, 0, t, w);
-  model_draw_obs(m, &out, a, w[0], w[1], obs);
+  model_draw_obs(m, &out, a, w[0], w[1], &co, obs);
+  if (pf) for (int q = 0; q < CR_N; ++q) { pf[2 * q] = out.px[q]; pf[2 * q + 1] = out.py[q]; }
   *terminal = model_is_terminal(m, &out);
   *x = out.x;
   *y = out.y;

@@ -7,8 +7,8 @@ sharing any of the method.
 
 The workloads stand in for the paper's benchmark problems (Sec. IV: MARS, Navigation,
 CrowdNav), whose maps and code are not available: a continuous 2-D navigation problem
-(NAV2D), a RockSample-like discrete grid-sensing problem (GRID) and a two-state test
-problem (TOY2).  All numbers come from numpy's PCG64 generator seeded explicitly.
+(NAV2D), a RockSample-like discrete grid-sensing problem (GRID), a two-state test
+problem (TOY2) and a crowd-navigation problem shaped like the paper's CrowdNav (CROWD).  All numbers come from numpy's PCG64 generator seeded explicitly.
 """
 from __future__ import annotations
 
@@ -17,9 +17,10 @@ import math
 
 import numpy as np
 
-NAV2D, GRID, TOY2 = 0, 1, 2
-KIND_NAMES = {NAV2D: "nav2d", GRID: "grid", TOY2: "toy2"}
-NUM_ACTIONS = {NAV2D: 4, GRID: 13, TOY2: 2}
+NAV2D, GRID, TOY2, CROWD = 0, 1, 2, 3
+KIND_NAMES = {NAV2D: "nav2d", GRID: "grid", TOY2: "toy2", CROWD: "crowd"}
+NUM_ACTIONS = {NAV2D: 4, GRID: 13, TOY2: 2, CROWD: 5}
+CROWD_PEOPLE = 6
 
 BRANCH_SAMPLE, BRANCH_ENUMERATE = 0, 1
 PI_UNIFORM, PI_FIXED, PI_NAV_SOFTMAX_DIST = 0, 1, 2
@@ -75,6 +76,36 @@ def toy2_root_sampled(n: int, seed: int, b0=(0.6, 0.4)):
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x746F79]))
     s = (rng.uniform(size=n) >= b0[0]).astype(np.int32)
     return s, np.full(n, 1.0 / n, dtype=np.float32)
+
+
+def crowd_root(n: int, seed: int, p_curious: float = 0.5, weights: str = "uniform",
+               robot=(25.0, 0.5)):
+    """Root belief for CROWD: the robot on the southern border, the six nearest people at
+    positions known to every particle (drawn within 8 m ahead of the robot), and per particle
+    each person's hidden trait, curious with probability p_curious.  Returns dict(x, y, s,
+    pf, w): robot x, y [N], flags s [N] (bits 0-5 traits), people pf [12, N] (rows 2q, 2q+1
+    = person q's x, y), weights."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x63726F77]))
+    px = np.clip(robot[0] + rng.uniform(-6.0, 6.0, size=CROWD_PEOPLE), 0.0, 50.0)
+    py = np.clip(robot[1] + rng.uniform(0.5, 8.0, size=CROWD_PEOPLE), 0.0, 40.0)
+    traits = (rng.uniform(size=(n, CROWD_PEOPLE)) < p_curious).astype(np.int64)
+    s = (traits << np.arange(CROWD_PEOPLE)).sum(axis=1).astype(np.int32)
+    pf = np.empty((2 * CROWD_PEOPLE, n), dtype=np.float32)
+    pf[0::2] = px.astype(np.float32)[:, None]
+    pf[1::2] = py.astype(np.float32)[:, None]
+    x = np.full(n, robot[0], dtype=np.float32)
+    y = np.full(n, robot[1], dtype=np.float32)
+    return dict(x=x, y=y, s=s, pf=pf, w=_weights(rng, n, weights))
+
+
+def pack_crowd_states(root: dict) -> np.ndarray:
+    """The C ABI's CROWD root layout: 15 rows of N 32-bit words -- robot x, robot y, the 12
+    people coordinates (float32), then the int32 flags."""
+    n = len(root["x"])
+    out = np.empty((15, n), dtype=np.float32)
+    out[0], out[1], out[2:14] = root["x"], root["y"], root["pf"]
+    out[14] = np.asarray(root["s"], dtype=np.int32).view(np.float32)
+    return out.ravel()
 
 
 def _weights(rng, n, kind):

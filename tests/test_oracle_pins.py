@@ -682,3 +682,112 @@ def test_episode_mode_one_iteration_root_q_is_the_empirical_mean_reward():
     assert q[0] == pytest.approx(0.7 * 1.0 + 0.3 * -1.0, abs=0.06)   # E[R(s, stay)]
     assert q[1] == pytest.approx(-0.1, abs=1e-12)
     np.testing.assert_allclose(r["psi_root"], np.log(0.5) + q, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# CROWD model (the paper's CrowdNav as a synthetic model), through the environment step.
+# ----------------------------------------------------------------------------------------
+def _crowd_state(robot, people, traits=0, flags_extra=0):
+    pf = np.zeros(12)
+    for q, (px, py) in enumerate(people):
+        pf[2 * q], pf[2 * q + 1] = px, py
+    return (robot[0], robot[1], traits | flags_extra, pf)
+
+
+def test_crowd_yell_backs_nearby_people_away_and_costs_25():
+    m = O.make_model(O.CROWD)
+    people = [(26.0, 10.0), (25.0, 12.5), (22.0, 10.0), (31.0, 10.0), (25.0, 16.0), (40.0, 30.0)]
+    for t in range(50):
+        rc, (x, y, f, pf), o, r, term = O.env_step(m, _crowd_state((25.0, 10.0), people, 0b101010),
+                                                   4, 11, t)
+        assert rc == O.OK and (x, y) == (25.0, 10.0) and not term
+        for q, (px, py) in enumerate(people):
+            d0 = math.hypot(px - 25.0, py - 10.0)
+            d1 = math.hypot(pf[2 * q] - 25.0, pf[2 * q + 1] - 10.0)
+            expect = d0 + 2.0 if d0 < 4.0 else d0      # nearby: 2 m straight away
+            assert abs(d1 - expect) < 0.3, (q, d0, d1)
+            assert ((f >> (8 + q)) & 1) == (d1 < d0)    # the "came closer" bit
+        assert r == -26.0                               # step and YELL, nobody within 0.5 m
+        assert f & 0x3F == 0b101010                     # traits never change
+
+
+@pytest.mark.parametrize("curious", [0, 1])
+def test_crowd_trait_reaction_probability_and_speed(curious):
+    """A person 2 m from the robot reacts with probability 0.9: curious 0.3 m toward it,
+    shy 0.8 m away; otherwise only the N(0, 0.05^2) noise moves them."""
+    m = O.make_model(O.CROWD)
+    people = [(27.0, 10.0)] + [(45.0, 35.0)] * 5
+    n, moved = 4000, 0
+    for t in range(n):
+        # robot moves EAST from (24, 10) to (25, 10): the person is then 2 m away
+        _, (x, y, f, pf), _, r, _ = O.env_step(m, _crowd_state((24.0, 10.0), people, curious), 1, 3, t)
+        assert (x, y) == (25.0, 10.0)
+        step = math.hypot(pf[0] - 25.0, pf[1] - 10.0) - 2.0
+        target = -0.3 if curious else 0.8
+        if abs(step - target) < 0.25:
+            moved += 1
+        else:
+            assert abs(step) < 0.25, step
+    assert stats.binomtest(moved, n, 0.9).pvalue > 1e-3
+
+
+def test_crowd_noise_of_distant_people_is_gaussian():
+    m = O.make_model(O.CROWD)
+    people = [(40.0, 30.0), (10.0, 30.0), (45.0, 5.0), (5.0, 20.0), (30.0, 35.0), (15.0, 38.0)]
+    zs = []
+    for t in range(800):
+        _, (_, _, _, pf), _, _, _ = O.env_step(m, _crowd_state((25.0, 10.0), people), 0, 21, t)
+        for q, (px, py) in enumerate(people):
+            zs += [(pf[2 * q] - px) / 0.05, (pf[2 * q + 1] - py) / 0.05]
+    assert stats.kstest(zs, "norm").pvalue > 1e-3
+
+
+def test_crowd_exit_bump_and_walls():
+    m = O.make_model(O.CROWD)
+    far = [(45.0, 5.0)] * 6
+    _, (x, y, f, _), _, r, term = O.env_step(m, _crowd_state((25.0, 39.5), far), 0, 1, 0)
+    assert term and y == 40.5 and r == 999.0 and (f >> 16) & 1
+    _, st2, _, r2, term2 = O.env_step(m, (x, y, f, np.zeros(12)), 0, 1, 1)
+    assert term2 and r2 == 0.0 and st2[:3] == (x, y, f)       # absorbing
+    _, (x, y, _, _), _, _, _ = O.env_step(m, _crowd_state((0.0, 0.0), far), 3, 1, 0)   # west wall
+    assert (x, y) == (0.0, 0.0)
+    _, (x, y, _, _), _, _, _ = O.env_step(m, _crowd_state((0.0, 0.0), far), 2, 1, 0)   # south wall
+    assert (x, y) == (0.0, 0.0)
+    # a shy person 0.3 m from the robot's new position stays within 0.5 m unless it reacts
+    bumps = 0
+    for t in range(400):
+        _, _, _, r, _ = O.env_step(m, _crowd_state((24.0, 10.0), [(25.2, 10.0)] + far[:5]), 1, 5, t)
+        assert r in (-1.0, -201.0)
+        bumps += r == -201.0
+    assert stats.binomtest(bumps, 400, 0.1).pvalue > 1e-3      # no reaction: 10 %
+
+
+def test_crowd_observation_model():
+    """Each bit reports 'came closer' and is flipped with probability q = floor(0.1 2^32)/2^32;
+    the likelihood is a distribution over the 64 observations."""
+    q = math.floor(0.1 * 2**32) / 2**32
+    for flags in (0, 0x3F00, 0x1500, 0x2A3F):
+        tot = sum(math.exp(O.crowd_loglik(flags, o)) for o in range(64))
+        assert tot == pytest.approx(1.0, abs=1e-12)
+        assert O.crowd_loglik(flags, (flags >> 8) & 0x3F) == pytest.approx(6 * math.log(1 - q))
+    m = O.make_model(O.CROWD)
+    people = [(26.0, 10.0), (25.0, 12.0), (22.0, 10.0), (45.0, 30.0), (10.0, 30.0), (40.0, 20.0)]
+    n, agree = 3000, np.zeros(6)
+    for t in range(n):
+        _, (_, _, f, _), o, _, _ = O.env_step(m, _crowd_state((25.0, 10.0), people), 4, 8, t)
+        agree += [((o >> i) & 1) == ((f >> (8 + i)) & 1) for i in range(6)]
+    for i in range(6):
+        assert stats.binomtest(int(agree[i]), n, 1 - q).pvalue > 1e-3
+
+
+def test_crowd_heuristic_is_the_straight_line_return():
+    gamma = 0.97
+    for y in (0.5, 12.25, 30.0, 39.2):
+        steps = max(1.0, 40.0 - y)
+        k = int(steps)
+        if steps == k:
+            expect = sum(-gamma ** t for t in range(k - 1)) + 1000.0 * gamma ** (k - 1)
+            assert O.crowd_heuristic(y, 0, gamma) == pytest.approx(expect, rel=1e-12)
+        gk = gamma ** (steps - 1)
+        assert O.crowd_heuristic(y, 0, gamma) == pytest.approx(-(1 - gk) / (1 - gamma) + 1000 * gk)
+    assert O.crowd_heuristic(10.0, 1 << 16, gamma) == 0.0
