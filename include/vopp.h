@@ -65,6 +65,15 @@ extern "C" {
 #define VOPP_NAV2D 0 /* continuous 2-D navigation, state (x,y) in [0,10]^2, 4 actions     */
 #define VOPP_GRID 1  /* 11x11 grid sensing, packed int32 state, 13 actions, obs {0,1,2}  */
 #define VOPP_TOY2 2  /* 2 states, 2 actions, 2 observations (test model)                  */
+#define VOPP_CROWD 3 /* crowd navigation shaped like the paper's CrowdNav (Sec. IV): robot in
+                        a 50 x 40 m hall with its 6 nearest people, each curious or shy
+                        (hidden); 5 actions (NORTH, EAST, SOUTH, WEST, YELL); 64 observations
+                        (per person: came closer, each bit flipped with probability 0.1);
+                        gamma 0.97 in the paper.  Particle layout: 15 rows of N 32-bit words
+                        -- robot x, robot y, people x0 y0 ... x5 y5 (float32), then int32
+                        flags (bits 0-5 traits, 1 = curious; 8-13 "came closer"; 16
+                        terminal).  ENUMERATE branches and the distance-softmax policy are
+                        not available. */
 
 #define VOPP_BRANCH_SAMPLE 0    /* o_k drawn from a uniformly chosen representative      */
 #define VOPP_BRANCH_ENUMERATE 1 /* branch k is observation k (discrete models, W >= |O|) */
@@ -97,6 +106,8 @@ extern "C" {
 #define VOPP_FIELD_MU 10    /* float  weighted mean particle [node][2] (VOPP_PI_NAV_DIST) */
 #define VOPP_FIELD_PSI 11   /* float  Psi[node][A] persistent preferences, levels 0..D-1,
                                after vopp_plan_anytime / vopp_agent_plan_anytime only        */
+#define VOPP_FIELD_PF 12    /* float  CROWD people [node][12][N] (rows x0 y0 .. x5 y5),
+                               materialised levels (robot in PX / PY, flags in PS)           */
 
 #define VOPP_MAX_ACTIONS 16
 #define VOPP_MAX_DEPTH 8
@@ -111,7 +122,7 @@ typedef struct vopp_agent vopp_agent;
 /* Model description.  The POMDP 8-tuple of Sec. II-A fixed by kind; layout fields apply
  * to VOPP_GRID (rock cells, all distinct, none on the start cell (0,5)). */
 typedef struct {
-  int32_t kind;        /* VOPP_NAV2D | VOPP_GRID | VOPP_TOY2                               */
+  int32_t kind;        /* VOPP_NAV2D | VOPP_GRID | VOPP_TOY2 | VOPP_CROWD                  */
   int32_t branch_mode; /* VOPP_BRANCH_SAMPLE | VOPP_BRANCH_ENUMERATE                      */
   int32_t pi_mode;     /* VOPP_PI_UNIFORM | VOPP_PI_FIXED | VOPP_PI_NAV_DIST                */
   int32_t h_zero;      /* 1: leaf heuristic forced to 0                                    */

@@ -229,8 +229,11 @@ static int grid_d2(const orc_model *m, int32_t s, int rock) {
  * in the hall; the robot is held by the east, west and south walls and leaves through the
  * north border (y >= 40: +1000, terminal).  Reward -1 per step, -25 for YELL, -200 per
  * person within 0.5 m after the step.  Observation: per person, whether the distance to
- * the robot's new position decreased, each bit flipped with probability q = floor(0.1 2^32)
- * / 2^32.  Flags: bits 0-5 traits (1 = curious), 8-13 the true "came closer" bits, 16
+ * the robot's new position decreased -- taken from the person's displacement d as
+ * d.(d + 2(p - r)) < 0, which is that comparison away from the walls and stays the same in
+ * FP32 and FP64 except within 1e-7 of a tie -- each bit flipped with probability
+ * q = floor(0.1 2^32) / 2^32.  Near-threshold events (reaction radius, bump radius, closer
+ * ties) are counted like NAV2D's goal test.  Flags: bits 0-5 traits (1 = curious), 8-13 the true "came closer" bits, 16
  * terminal. */
 #define CR_W 50.0
 #define CR_H 40.0
@@ -248,7 +251,8 @@ static const uint32_t CR_FLIP_THR = 429496729u;     /* floor(0.1 * 2^32) */
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-static void crowd_step(const pstate *in, int a, const orc_ctr *c, pstate *out, double *reward) {
+static void crowd_step(const pstate *in, int a, const orc_ctr *c, pstate *out, double *reward,
+                       long long *near) {
   *out = *in;
   if (CR_TERM(in->s)) { *reward = 0.0; return; }
   uint32_t w[5][4];
@@ -262,31 +266,39 @@ static void crowd_step(const pstate *in, int a, const orc_ctr *c, pstate *out, d
   int closer = 0;
   const int exited = ny >= CR_H;
   for (int i = 0; i < CR_N; ++i) {
-    double px = in->px[i], py = in->py[i];
-    const double d0 = hypot(px - nx, py - ny);
+    const double px = in->px[i], py = in->py[i];
+    const double ex = px - nx, ey = py - ny;        /* robot (new position) to the person */
+    const double d0 = sqrt(ex * ex + ey * ey);
+    double mx = 0.0, my = 0.0;                       /* the person's reaction */
     if (d0 < CR_RNEAR && d0 > 0.0) {
-      const double ux = (px - nx) / d0, uy = (py - ny) / d0;   /* away from the robot */
+      const double ux = ex / d0, uy = ey / d0;       /* away from the robot */
       const uint32_t wr = i < 4 ? w[3][i] : w[4][i - 4];
       if (a == 4) {
-        px += CR_VBACK * ux; py += CR_VBACK * uy;
+        mx = CR_VBACK * ux; my = CR_VBACK * uy;
       } else if (wr < CR_REACT_THR) {
         if ((traits >> i) & 1) {
           const double st = d0 < CR_VCUR ? d0 : CR_VCUR;
-          px -= st * ux; py -= st * uy;
+          mx = -st * ux; my = -st * uy;
         } else {
-          px += CR_VSHY * ux; py += CR_VSHY * uy;
+          mx = CR_VSHY * ux; my = CR_VSHY * uy;
         }
       }
     }
+    if (fabs(d0 - CR_RNEAR) < 1e-4) ++*near;
     double g1, g2;
     orc_box_muller(w[i / 2][2 * (i % 2)], w[i / 2][2 * (i % 2) + 1], &g1, &g2);
-    px = clampd(px + CR_SIGP * g1, 0.0, CR_W);
-    py = clampd(py + CR_SIGP * g2, 0.0, CR_H);
-    const double d1 = hypot(px - nx, py - ny);
-    if (d1 < d0) closer |= 1 << i;
+    const double dx = mx + CR_SIGP * g1, dy = my + CR_SIGP * g2;   /* displacement */
+    /* came closer: |p + d - r| < |p - r|, i.e. d.(d + 2(p - r)) < 0 (from the displacement,
+     * before the walls clamp the position) */
+    const double cl = dx * (dx + 2.0 * ex) + dy * (dy + 2.0 * ey);
+    if (cl < 0.0) closer |= 1 << i;
+    if (fabs(cl) < 1e-7) ++*near;
+    const double qx = clampd(px + dx, 0.0, CR_W), qy = clampd(py + dy, 0.0, CR_H);
+    const double d1 = hypot(qx - nx, qy - ny);
     if (!exited && d1 < CR_RBUMP) r -= 200.0;
-    out->px[i] = px;
-    out->py[i] = py;
+    if (!exited && fabs(d1 - CR_RBUMP) < 1e-4) ++*near;
+    out->px[i] = qx;
+    out->py[i] = qy;
   }
   if (exited) r += 1000.0;
   out->s = traits | (closer << 8) | (exited << 16);
@@ -321,7 +333,7 @@ static double crowd_loglik(const pstate *sp, int o) {
 static void model_step(const orc_model *m, const pstate *in, int a, uint32_t wa, uint32_t wb,
                        const orc_ctr *c, pstate *out, double *reward, long long *near) {
   if (m->kind == ORC_CROWD) {
-    crowd_step(in, a, c, out, reward);
+    crowd_step(in, a, c, out, reward, near);
     return;
   }
   if (m->kind == ORC_NAV2D) {

@@ -147,8 +147,10 @@ struct vopp_env {
   vopp_model *model = nullptr;
   uint64_t seed = 0;
   unsigned long long t = 0;
-  float *xy = nullptr;                  // NAV2D true state (x, y)
-  int *s = nullptr;                     // GRID / TOY2 true state
+  float *blk = nullptr;                 // the true state (one particle of the root layout)
+  float *xy = nullptr;                  // NAV2D / CROWD robot (x, y)
+  int *s = nullptr;                     // GRID / TOY2 state, CROWD flags
+  float *pf = nullptr;                  // CROWD people
   EnvOut *dout = nullptr, *hout = nullptr;
 };
 
@@ -161,6 +163,8 @@ struct vopp_agent {
   int *s = nullptr;                     // GRID / TOY2
   float *txy = nullptr, *tlw = nullptr;
   int *ts = nullptr;
+  float *pf = nullptr, *tpf = nullptr;  // CROWD people [12][N]
+  float *blk = nullptr, *tblk = nullptr;  // the state store (rows as the root layout)
   double *cdf = nullptr;
   int *anc = nullptr;
   BeliefOut *dout = nullptr, *hout = nullptr;
@@ -178,12 +182,15 @@ struct PlanShape {
 
 struct PlanLayout {
   size_t bytes = 0;
-  size_t px[kMaxDepth], py[kMaxDepth], plw[kMaxDepth], ps[kMaxDepth];
+  size_t px[kMaxDepth], py[kMaxDepth], plw[kMaxDepth], ps[kMaxDepth], pf[kMaxDepth];
   size_t rbar[kMaxDepth + 1], lom[kMaxDepth + 1], V[kMaxDepth + 1], Q[kMaxDepth],
       mu[kMaxDepth], rep[kMaxDepth + 1], obs[kMaxDepth + 1], cnt[kMaxDepth], psi[kMaxDepth];
 };
 
 constexpr size_t kNone = ~(size_t)0;
+
+// 32-bit words per particle of the caller's root states (and of an agent's store).
+size_t root_words(int kind) { return kind == kNav ? 2 : (kind == kCrowd ? 15 : 1); }
 
 PlanShape make_shape(const vopp_model *m, int N, int D, int W, const vopp_ctx *ctx) {
   PlanShape s{};
@@ -205,14 +212,15 @@ PlanShape make_shape(const vopp_model *m, int N, int D, int W, const vopp_ctx *c
 PlanLayout make_layout(const PlanShape &s, bool psi = false) {
   PlanLayout L;
   for (int i = 0; i < kMaxDepth; ++i)
-    L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.Q[i] = L.mu[i] = L.cnt[i] = L.psi[i] = kNone;
+    L.px[i] = L.py[i] = L.plw[i] = L.ps[i] = L.pf[i] = L.Q[i] = L.mu[i] = L.cnt[i] = L.psi[i] = kNone;
   for (int i = 0; i <= kMaxDepth; ++i) L.rbar[i] = L.lom[i] = L.V[i] = L.rep[i] = L.obs[i] = kNone;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   for (int l = 0; l <= s.mat_top; ++l) {
     const size_t n = (size_t)ipow(s.AW, l) * (size_t)s.N;
-    if (s.kind == kNav) { L.px[l] = take(4 * n); L.py[l] = take(4 * n); }
-    else L.ps[l] = take(4 * n);
+    if (s.kind == kNav || s.kind == kCrowd) { L.px[l] = take(4 * n); L.py[l] = take(4 * n); }
+    if (s.kind != kNav) L.ps[l] = take(4 * n);
+    if (s.kind == kCrowd) L.pf[l] = take(48 * n);
     L.plw[l] = take(4 * n);
   }
   for (int l = 0; l <= s.D; ++l) {
@@ -499,7 +507,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     const Job &j = jobs[i];
     if (!(j.ptr_flags & VOPP_PTR_DEVICE) && j.states) {
       root_off[i] = off;
-      const size_t sb = (j.shape.kind == kNav ? 8 : 4) * (size_t)j.shape.N;
+      const size_t sb = root_words(j.shape.kind) * 4 * (size_t)j.shape.N;
       const size_t wb = j.weights ? 4 * (size_t)j.shape.N : 0;
       off = align_up(off + sb + wb, 256);
     }
@@ -540,7 +548,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     }
     const double g = j.p.gamma;
     P.h_a0 = (float)(-1.0 / (1.0 - g));
-    P.h_b0 = (float)(100.0 + 1.0 / (1.0 - g));
+    P.h_b0 = (float)((sh.kind == kCrowd ? 1000.0 : 100.0) + 1.0 / (1.0 - g));
     P.log2_gamma = (float)std::log2(g);
     P.key0 = (uint32_t)j.p.seed;
     P.key1 = (uint32_t)(j.p.seed >> 32);
@@ -551,6 +559,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     auto ip = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<int *>(base + o); };
     for (int l = 0; l < kMaxDepth; ++l) {
       P.px[l] = fp(L.px[l]); P.py[l] = fp(L.py[l]); P.plw[l] = fp(L.plw[l]); P.ps[l] = ip(L.ps[l]);
+      P.pf[l] = fp(L.pf[l]);
       P.Q[l] = fp(L.Q[l]); P.mu[l] = fp(L.mu[l]);
       P.cnt[l] = L.cnt[l] == kNone ? nullptr : reinterpret_cast<unsigned int *>(base + L.cnt[l]);
       P.psi[l] = fp(L.psi[l]);
@@ -565,25 +574,28 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     if (j.log_weights) {
       P.root_lw = j.log_weights;
     }
-    if (j.ptr_flags & VOPP_PTR_DEVICE || !j.states) {
-      if (sh.kind == kNav) {
-        P.root_x = static_cast<const float *>(j.states);
+    // root states: NAV2D rows x, y; GRID / TOY2 one row s; CROWD rows x, y, 12 people, flags
+    auto set_root = [&](const char *base) {
+      if (sh.kind == kNav || sh.kind == kCrowd) {
+        P.root_x = reinterpret_cast<const float *>(base);
         P.root_y = P.root_x + sh.N;
-      } else {
-        P.root_s = static_cast<const int *>(j.states);
       }
+      if (sh.kind == kCrowd) {
+        P.root_pf = P.root_x + 2 * (size_t)sh.N;
+        P.root_s = reinterpret_cast<const int *>(P.root_x + 14 * (size_t)sh.N);
+      } else if (sh.kind != kNav) {
+        P.root_s = reinterpret_cast<const int *>(base);
+      }
+    };
+    if (j.ptr_flags & VOPP_PTR_DEVICE || !j.states) {
+      set_root(static_cast<const char *>(j.states));
       P.root_w = j.weights;
     } else {
       char *hb = H + root_off[i];
       const char *db = Dm + root_off[i];
-      const size_t sb = (sh.kind == kNav ? 8 : 4) * (size_t)sh.N;
+      const size_t sb = root_words(sh.kind) * 4 * (size_t)sh.N;
       std::memcpy(hb, j.states, sb);
-      if (sh.kind == kNav) {
-        P.root_x = reinterpret_cast<const float *>(db);
-        P.root_y = P.root_x + sh.N;
-      } else {
-        P.root_s = reinterpret_cast<const int *>(db);
-      }
+      set_root(db);
       if (j.weights) {
         std::memcpy(hb + sb, j.weights, 4 * (size_t)sh.N);
         P.root_w = reinterpret_cast<const float *>(db + sb);
@@ -973,7 +985,7 @@ int vopp_plan_footprint(const vopp_model *m, int32_t N, int32_t D, int32_t W, si
 int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
   if (!c || !d || !out) return fail(VOPP_E_INVALID, "NULL argument");
   *out = nullptr;
-  if (d->kind < VOPP_NAV2D || d->kind > VOPP_TOY2) return fail(VOPP_E_INVALID, "kind %d", d->kind);
+  if (d->kind < VOPP_NAV2D || d->kind > VOPP_CROWD) return fail(VOPP_E_INVALID, "kind %d", d->kind);
   if (d->branch_mode != VOPP_BRANCH_SAMPLE && d->branch_mode != VOPP_BRANCH_ENUMERATE)
     return fail(VOPP_E_INVALID, "branch_mode");
   if (d->branch_mode == VOPP_BRANCH_ENUMERATE && d->kind == VOPP_NAV2D)
@@ -982,7 +994,7 @@ int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
     return fail(VOPP_E_INVALID, "pi_mode");
   if (d->pi_mode == VOPP_PI_NAV_DIST && (d->kind != VOPP_NAV2D || !(d->pi_temp > 0.f)))
     return fail(VOPP_E_INVALID, "NAV_DIST needs NAV2D and pi_temp > 0");
-  const int A = d->kind == VOPP_NAV2D ? 4 : d->kind == VOPP_GRID ? 13 : 2;
+  const int A = d->kind == VOPP_NAV2D ? 4 : d->kind == VOPP_GRID ? 13 : d->kind == VOPP_CROWD ? 5 : 2;
   if (d->pi_mode == VOPP_PI_FIXED) {
     double s = 0.0;
     for (int a = 0; a < A; ++a) {
@@ -1009,7 +1021,7 @@ int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
   std::memset(&h, 0, sizeof h);
   h.kind = d->kind;
   h.A = A;
-  h.n_obs = d->kind == VOPP_NAV2D ? 0 : (d->kind == VOPP_GRID ? 3 : 2);
+  h.n_obs = d->kind == VOPP_NAV2D ? 0 : (d->kind == VOPP_GRID ? 3 : (d->kind == VOPP_CROWD ? 64 : 2));
   h.branch_mode = d->branch_mode;
   h.pi_mode = d->pi_mode;
   h.h_zero = d->h_zero;
@@ -1212,6 +1224,7 @@ int vopp_tree_read_plan(vopp_ctx *c, int32_t plan, int32_t field, int32_t level,
     case VOPP_FIELD_PLW: src = lv < kMaxDepth ? P.plw[lv] : nullptr; len = nodes * P.N; break;
     case VOPP_FIELD_MU: src = lv < kMaxDepth ? P.mu[lv] : nullptr; len = 2 * nodes; break;
     case VOPP_FIELD_PSI: src = lv < kMaxDepth ? P.psi[lv] : nullptr; len = nodes * P.A; break;
+    case VOPP_FIELD_PF: src = lv < kMaxDepth ? P.pf[lv] : nullptr; len = nodes * 12 * P.N; break;
     default: return fail(VOPP_E_INVALID, "field %d", field);
   }
   if (!src) return fail(VOPP_E_INVALID, "field %d not kept at level %d", field, level);
@@ -1258,8 +1271,27 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
   g->seed = seed;
   bool ok = true;
   auto al = [&](void **p, size_t b) { if (ok && cudaMalloc(p, b) != cudaSuccess) { cudaGetLastError(); ok = false; } };
-  if (nav) { al((void **)&g->xy, 8 * (size_t)n); al((void **)&g->txy, 8 * (size_t)n); }
-  else { al((void **)&g->s, 4 * (size_t)n); al((void **)&g->ts, 4 * (size_t)n); }
+  const int kind = m->desc.kind;
+  const size_t words = root_words(kind);
+  float *blk = nullptr, *tblk = nullptr;      // root_words(kind) rows of n words
+  al((void **)&blk, 4 * words * (size_t)n);
+  al((void **)&tblk, 4 * words * (size_t)n);
+  if (ok) {
+    if (nav || kind == kCrowd) { g->xy = blk; g->txy = tblk; }
+    if (kind == kCrowd) {
+      g->pf = blk + 2 * (size_t)n; g->tpf = tblk + 2 * (size_t)n;
+      g->s = reinterpret_cast<int *>(blk + 14 * (size_t)n);
+      g->ts = reinterpret_cast<int *>(tblk + 14 * (size_t)n);
+    } else if (!nav) {
+      g->s = reinterpret_cast<int *>(blk);
+      g->ts = reinterpret_cast<int *>(tblk);
+    }
+    g->blk = blk;
+    g->tblk = tblk;
+  } else {
+    cudaFree(blk);
+    cudaFree(tblk);
+  }
   al((void **)&g->lw, 4 * (size_t)n);
   al((void **)&g->tlw, 4 * (size_t)n);
   al((void **)&g->cdf, 8 * (size_t)n);
@@ -1268,7 +1300,7 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
   if (ok && cudaMallocHost((void **)&g->hout, sizeof(BeliefOut)) != cudaSuccess) { cudaGetLastError(); ok = false; }
   if (!ok) { vopp_agent_destroy(g); return fail(VOPP_E_NOMEM, "agent device alloc"); }
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = nav ? cudaMemcpy(g->xy, states, 8 * (size_t)n, k) : cudaMemcpy(g->s, states, 4 * (size_t)n, k);
+  cudaError_t e = cudaMemcpy(g->blk, states, 4 * words * (size_t)n, k);
   if (e == cudaSuccess) e = cudaMemcpy(g->lw, lw.data(), 4 * (size_t)n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { vopp_agent_destroy(g); return fail(VOPP_E_CUDA, "agent upload: %s", cudaGetErrorString(e)); }
   *out = g;
@@ -1285,13 +1317,17 @@ int vopp_env_create(vopp_model *m, const void *state, uint64_t seed, vopp_env **
   if (!e) return fail(VOPP_E_NOMEM, "env alloc");
   e->model = m;
   e->seed = seed;
-  const bool nav = m->desc.kind == VOPP_NAV2D;
-  cudaError_t ce = nav ? cudaMalloc(&e->xy, 2 * sizeof(float)) : cudaMalloc(&e->s, sizeof(int));
+  const int kind = m->desc.kind;
+  const size_t words = root_words(kind);     // the state as one particle of the root layout
+  cudaError_t ce = cudaMalloc(&e->blk, 4 * words);
+  if (ce == cudaSuccess) {
+    if (kind == kNav || kind == kCrowd) e->xy = e->blk;
+    if (kind == kCrowd) { e->pf = e->blk + 2; e->s = reinterpret_cast<int *>(e->blk + 14); }
+    else if (kind != kNav) e->s = reinterpret_cast<int *>(e->blk);
+  }
   if (ce == cudaSuccess) ce = cudaMalloc(&e->dout, sizeof(EnvOut));
   if (ce == cudaSuccess) ce = cudaMallocHost(&e->hout, sizeof(EnvOut));
-  if (ce == cudaSuccess)
-    ce = nav ? cudaMemcpy(e->xy, state, 2 * sizeof(float), cudaMemcpyHostToDevice)
-             : cudaMemcpy(e->s, state, sizeof(int), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(e->blk, state, 4 * words, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
     cudaGetLastError();
     vopp_env_destroy(e);
@@ -1316,6 +1352,7 @@ int vopp_env_step(vopp_env *e, int32_t action, void *obs, float *reward, int32_t
   E.t = e->t;
   E.xy = e->xy;
   E.s = e->s;
+  E.pf = e->pf;
   E.model = m->dev;
   E.out = e->dout;
   cudaError_t ce = launch_env(E, c->stream);
@@ -1340,15 +1377,14 @@ int vopp_env_get_state(vopp_env *e, void *state) {
   vopp_ctx *c = e->model->ctx;
   cudaSetDevice(c->device);
   CUDA_TRY(cudaStreamSynchronize(c->stream));
-  if (e->model->desc.kind == VOPP_NAV2D) CUDA_TRY(cudaMemcpy(state, e->xy, 2 * sizeof(float), cudaMemcpyDeviceToHost));
-  else CUDA_TRY(cudaMemcpy(state, e->s, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(state, e->blk, 4 * root_words(e->model->desc.kind), cudaMemcpyDeviceToHost));
   return VOPP_OK;
 }
 
 void vopp_env_destroy(vopp_env *e) {
   if (!e) return;
   if (e->model) cudaStreamSynchronize(e->model->ctx->stream);
-  cudaFree(e->xy); cudaFree(e->s); cudaFree(e->dout);
+  cudaFree(e->blk); cudaFree(e->dout);
   if (e->hout) cudaFreeHost(e->hout);
   delete e;
 }
@@ -1394,7 +1430,7 @@ int vopp_run_episode(vopp_agent *g, vopp_env *e, const vopp_plan_params *p, int3
 void vopp_agent_destroy(vopp_agent *g) {
   if (!g) return;
   if (g->model) cudaStreamSynchronize(g->model->ctx->stream);
-  cudaFree(g->xy); cudaFree(g->txy); cudaFree(g->s); cudaFree(g->ts);
+  cudaFree(g->blk); cudaFree(g->tblk);
   cudaFree(g->lw); cudaFree(g->tlw); cudaFree(g->cdf); cudaFree(g->anc); cudaFree(g->dout);
   if (g->hout) cudaFreeHost(g->hout);
   delete g;
@@ -1409,7 +1445,7 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
   if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = g->model->ctx;
   std::vector<Job> jobs(1);
-  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  const void *states = g->blk;
   int rc = make_job(c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, jobs[0]);
   if (rc) return rc;
   jobs[0].log_weights = g->lw;
@@ -1422,7 +1458,7 @@ int vopp_agent_plan_anytime(vopp_agent *g, const vopp_plan_params *p, double bud
   if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = g->model->ctx;
   Job j;
-  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  const void *states = g->blk;
   int rc = make_job(c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, j);
   if (rc) return rc;
   j.log_weights = g->lw;
@@ -1433,7 +1469,7 @@ int vopp_agent_plan_anytime(vopp_agent *g, const vopp_plan_params *p, double bud
 int vopp_agent_plan_episodes(vopp_agent *g, const vopp_episode_params *p, double budget_s,
                              vopp_plan_result *out, int32_t *depth_reached, int32_t *n_nodes) {
   if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
-  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  const void *states = g->blk;
   vopp::EpisodeInputs in{states, nullptr, g->lw, g->N, VOPP_PTR_DEVICE};
   return vopp::run_plan_episodes(g->model, in, *p, budget_s, out, depth_reached, n_nodes);
 }
@@ -1453,13 +1489,16 @@ int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *e
   B.key0 = (uint32_t)g->seed;
   B.key1 = (uint32_t)(g->seed >> 32);
   B.t = g->t;
-  if (B.kind == kNav) {
+  if (B.kind == kNav || B.kind == kCrowd) {
     B.x = g->xy; B.y = g->xy + g->N; B.tx = g->txy; B.ty = g->txy + g->N;
+  }
+  if (B.kind == kNav) {
     const float *o = static_cast<const float *>(obs);
     B.obs_f[0] = o[0];
     B.obs_f[1] = o[1];
   } else {
     B.s = g->s; B.ts = g->ts;
+    B.pf = g->pf; B.tpf = g->tpf;
     B.obs_i = *static_cast<const int32_t *>(obs);
   }
   B.lw = g->lw;
@@ -1491,10 +1530,8 @@ int vopp_agent_get_particles(vopp_agent *g, void *states, float *log_weights, in
   vopp_ctx *c = g->model->ctx;
   const cudaMemcpyKind k = (ptr_flags & VOPP_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t n = (size_t)g->N;
-  if (states) {
-    if (g->model->desc.kind == VOPP_NAV2D) CUDA_TRY(cudaMemcpyAsync(states, g->xy, 8 * n, k, c->stream));
-    else CUDA_TRY(cudaMemcpyAsync(states, g->s, 4 * n, k, c->stream));
-  }
+  if (states)
+    CUDA_TRY(cudaMemcpyAsync(states, g->blk, 4 * root_words(g->model->desc.kind) * n, k, c->stream));
   if (log_weights) CUDA_TRY(cudaMemcpyAsync(log_weights, g->lw, 4 * n, k, c->stream));
   if (ancestors) CUDA_TRY(cudaMemcpyAsync(ancestors, g->anc, 4 * n, k, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1805,7 +1842,7 @@ int vopp_submit_agent(vopp_server *srv, vopp_agent *g, const vopp_plan_params *p
   if (!srv || !g || !p || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
   if (g->model->ctx != srv->c) return fail(VOPP_E_INVALID, "agent of another context");
   ServerReq r;
-  const void *states = g->model->desc.kind == VOPP_NAV2D ? (const void *)g->xy : (const void *)g->s;
+  const void *states = g->blk;
   int rc = make_job(srv->c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, r.job);
   if (rc) return rc;
   r.job.log_weights = g->lw;

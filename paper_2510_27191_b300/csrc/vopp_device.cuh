@@ -16,7 +16,7 @@ constexpr int kMaxDepth = 8;
 constexpr int kMaxActions = 16;
 constexpr int kMaxAW = 256;           // actions x branches per node
 constexpr int kGridD2 = 256;          // squared agent-rock distances 0..221 (table padded)
-constexpr int kNav = 0, kGrid = 1, kToy = 2;
+constexpr int kNav = 0, kGrid = 1, kToy = 2, kCrowd = 3;
 constexpr int kSample = 0, kEnumerate = 1;
 constexpr int kPiUniform = 0, kPiFixed = 1, kPiNavDist = 2;
 
@@ -64,7 +64,7 @@ struct PlanDesc {
   int fp64_root;              // back the root up in FP64 (else FP32, compensated)
   float eta, inv_eta, gamma, pi_temp;
   float log_pi[kMaxActions];  // uniform / fixed reference policy
-  float h_a0, h_b0, log2_gamma;  // NAV2D heuristic: h = a0 + b0 gamma^(m-1)
+  float h_a0, h_b0, log2_gamma;  // NAV2D / CROWD heuristic: h = a0 + b0 gamma^(m-1)
   uint32_t key0, key1;
   const DevModel *model;
   // root input (device copy or caller device pointer)
@@ -72,9 +72,11 @@ struct PlanDesc {
   const int *root_s;
   const float *root_w;        // linear weights (or null = uniform)
   const float *root_lw;       // log weights (agents); overrides root_w when set
+  const float *root_pf;       // CROWD people [12][N] (rows 2q, 2q+1 = person q's x, y)
   // particle stores per level (levels 0 .. D-1, only those materialised)
   float *px[kMaxDepth], *py[kMaxDepth], *plw[kMaxDepth];
   int *ps[kMaxDepth];
+  float *pf[kMaxDepth];       // CROWD people [node][12][N]
   // per-node / per-child arrays
   float *rbar[kMaxDepth + 1], *lom[kMaxDepth + 1], *V[kMaxDepth + 1];
   float *Q[kMaxDepth];
@@ -525,6 +527,7 @@ struct ToyModel {
   static constexpr bool kStochastic = false;
   static constexpr bool kPairPacked = false;
   struct S { int s; };
+
   struct O { int o; };
 
   __device__ __forceinline__ static bool terminal(const S &) { return false; }
@@ -551,5 +554,149 @@ struct ToyModel {
   __device__ __forceinline__ static float heuristic(const S &, const PlanDesc &) { return 0.0f; }
   __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
 };
+
+// ---------------------------------------------------------------------------------------
+// CROWD: the paper's CrowdNav problem (Sec. IV) as a synthetic model.  A robot in a 50 x 40 m
+// hall and the six nearest people, each curious or shy (hidden).  Actions 0 NORTH, 1 EAST,
+// 2 SOUTH, 3 WEST (1 m; the east, west and south walls hold the robot), 4 YELL.  Every person
+// moves by N(0, 0.05^2) noise per axis; a person within 4 m of the robot's new position
+// reacts with probability 0.9 -- curious 0.3 m toward it (never past it), shy 0.8 m away --
+// and under YELL every such person backs away 2 m instead.  Reward -1 per step, -25 for
+// YELL, -200 per person within 0.5 m after the step, +1000 on leaving north (terminal).
+// Observation: per person whether it came closer to the robot's new position, read from its
+// displacement d as d.(d + 2(p - r)) < 0, each bit flipped with probability
+// floor(0.1 2^32) / 2^32.  A step draws its own five Philox calls (call index in bits 24-31
+// of the second counter word); flags: bits 0-5 traits (1 = curious), 8-13 the true
+// "came closer" bits, 16 terminal.
+// ---------------------------------------------------------------------------------------
+struct DrawCtx {                 // the counter words a self-drawing model step uses
+  uint32_t k0, k1, purpose, c1;  // c1 = level | action << 8 | branch << 16
+  unsigned long long node;
+};
+
+struct CrowdModel {
+  static constexpr bool kStochastic = false;
+  static constexpr bool kPairPacked = false;
+  static constexpr bool kSelfDraw = true;
+  static constexpr int kPeople = 6;
+  struct S { float x, y; float px[6], py[6]; int f; };
+  struct O { int o; };
+  static constexpr uint32_t kReactThr = 3865470566u;   // floor(0.9 2^32)
+  static constexpr uint32_t kFlipThr = 429496729u;     // floor(0.1 2^32)
+
+  __device__ __forceinline__ static bool terminal(const S &s) { return (s.f >> 16) & 1; }
+  __device__ __forceinline__ static uint4 words(const DrawCtx &c, uint32_t idx, uint32_t j) {
+    return philox(make_uint4(idx | (c.purpose << 24), c.c1 | (j << 24), (uint32_t)c.node,
+                             (uint32_t)(c.node >> 32)), c.k0, c.k1);
+  }
+  __device__ static float step_drawn(S &s, int a, const DrawCtx &c, uint32_t idx) {
+    if (terminal(s)) return 0.0f;
+    uint4 w[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w[j] = words(c, idx, (uint32_t)j);
+    const float dxa = (a == 1) ? 1.0f : ((a == 3) ? -1.0f : 0.0f);
+    const float dya = (a == 0) ? 1.0f : ((a == 2) ? -1.0f : 0.0f);
+    const float nx = fminf(fmaxf(__fadd_rn(s.x, dxa), 0.0f), 50.0f);
+    const float ny = fmaxf(__fadd_rn(s.y, dya), 0.0f);
+    const bool exited = ny >= 40.0f;
+    float r = (a == 4) ? -26.0f : -1.0f;
+    const int traits = s.f & 0x3F;
+    int closer = 0;
+#pragma unroll
+    for (int i = 0; i < kPeople; ++i) {
+      const float ex = __fsub_rn(s.px[i], nx), ey = __fsub_rn(s.py[i], ny);
+      const float d0 = __fsqrt_rn(fmaf(ex, ex, __fmul_rn(ey, ey)));
+      float mx = 0.0f, my = 0.0f;
+      if (d0 < 4.0f && d0 > 0.0f) {
+        const float ux = __fdiv_rn(ex, d0), uy = __fdiv_rn(ey, d0);
+        const uint32_t wr = (i < 4) ? (&w[3].x)[i] : (&w[4].x)[i - 4];
+        if (a == 4) {
+          mx = 2.0f * ux; my = 2.0f * uy;
+        } else if (wr < kReactThr) {
+          if ((traits >> i) & 1) {
+            const float st = fminf(d0, 0.3f);
+            mx = -st * ux; my = -st * uy;
+          } else {
+            mx = 0.8f * ux; my = 0.8f * uy;
+          }
+        }
+      }
+      const uint4 wb = w[i >> 1];
+      const float2 g = (i & 1) ? box_muller(wb.z, wb.w) : box_muller(wb.x, wb.y);
+      const float ddx = fmaf(0.05f, g.x, mx), ddy = fmaf(0.05f, g.y, my);
+      const float cl = fmaf(ddx, fmaf(2.0f, ex, ddx), __fmul_rn(ddy, fmaf(2.0f, ey, ddy)));
+      if (cl < 0.0f) closer |= 1 << i;
+      const float qx = fminf(fmaxf(__fadd_rn(s.px[i], ddx), 0.0f), 50.0f);
+      const float qy = fminf(fmaxf(__fadd_rn(s.py[i], ddy), 0.0f), 40.0f);
+      const float fx = __fsub_rn(qx, nx), fy = __fsub_rn(qy, ny);
+      const float d1 = __fsqrt_rn(fmaf(fx, fx, __fmul_rn(fy, fy)));
+      if (!exited && d1 < 0.5f) r -= 200.0f;
+      s.px[i] = qx;
+      s.py[i] = qy;
+    }
+    s.x = nx;
+    s.y = ny;
+    s.f = traits | (closer << 8) | (exited ? (1 << 16) : 0);
+    return exited ? r + 1000.0f : r;
+  }
+  // w0: the first observation call of counter (idx, c) (words 0, 1, 3 decide bits 0-2; word 2
+  // picks a branch's representative); the second call decides bits 3-5.
+  __device__ static O draw_obs_drawn(const S &s, const uint4 &w0, const DrawCtx &c, uint32_t idx) {
+    const uint4 w1 = words(c, idx, 1u);
+    const uint32_t u[6] = {w0.x, w0.y, w0.w, w1.x, w1.y, w1.z};
+    int o = 0;
+#pragma unroll
+    for (int i = 0; i < kPeople; ++i) {
+      int bit = (s.f >> (8 + i)) & 1;
+      if (u[i] < kFlipThr) bit ^= 1;
+      o |= bit << i;
+    }
+    return O{o};
+  }
+  __device__ __forceinline__ static O enum_obs(int k) { return O{k}; }
+  // log2 Z(o | s') = sum over people of log2(1 - q) on agreement, log2 q otherwise
+  __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &) {
+    if (o.o < 0 || o.o > 63) return -CUDART_INF_F;
+    const int agree = 6 - __popc(((s.f >> 8) ^ o.o) & 0x3F);
+    return (float)agree * -0.152003093f + (float)(6 - agree) * -3.32192809f;
+  }
+  __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
+    return kLn2 * loglik2(s, a, o, m);
+  }
+  // h = a0 + b0 gamma^(m-1), m = max(1, 40 - y) unit moves north; 0 at terminal states
+  __device__ __forceinline__ static float heuristic(const S &s, float log2g, float a0, float b0,
+                                                    bool hz) {
+    const float m = fmaxf(__fsub_rn(40.0f, s.y), 1.0f);
+    const float h = fmaf(b0, ex2(fmaf(m, log2g, -log2g)), a0);
+    return (hz || terminal(s)) ? 0.0f : h;
+  }
+  __device__ __forceinline__ static float heuristic(const S &s, const PlanDesc &P) {
+    return heuristic(s, P.log2_gamma, P.h_a0, P.h_b0, P.h_zero != 0);
+  }
+  __device__ __forceinline__ static float2 obs_f2(const O &o) { return make_float2((float)o.o, 0.f); }
+};
+
+// Whether a model's step draws its own Philox calls (CROWD) or takes two words of the
+// pair call of its particle (the others).
+template <class M> struct SelfDraw { static constexpr bool value = false; };
+template <> struct SelfDraw<CrowdModel> { static constexpr bool value = true; };
+
+// Transition of particle i: from the pair words pw (words 0,1 for even i, 2,3 for odd i) or,
+// for a self-drawing model, from its own calls under counter c with idx = i.
+template <class M>
+__device__ __forceinline__ float step_particle(typename M::S &s, int a, const uint4 &pw, int i,
+                                              const DrawCtx &c, const DevModel &dm) {
+  if constexpr (SelfDraw<M>::value) return M::step_drawn(s, a, c, (uint32_t)i);
+  else return M::step(s, a, (i & 1) ? pw.z : pw.x, (i & 1) ? pw.w : pw.y, dm);
+}
+// Observation from the first observation call w of counter (idx, c) (and, for a
+// self-drawing model, further calls of it).
+template <class M>
+__device__ __forceinline__ typename M::O obs_particle(const typename M::S &s, int a,
+                                                      const uint4 &w, const DrawCtx &c,
+                                                      uint32_t idx, const DevModel &dm) {
+  if constexpr (SelfDraw<M>::value) return M::draw_obs_drawn(s, w, c, idx);
+  else return M::draw_obs(s, a, w.x, w.y, dm);
+}
 
 }  // namespace vopp

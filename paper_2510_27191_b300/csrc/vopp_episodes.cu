@@ -50,9 +50,10 @@ struct EpDesc {
   const int *rs;
   const float *rw;            // linear weights or null
   const float *rlw;           // log weights (agents) or null
+  const float *rpf;           // CROWD root people [12][Np]
   double *cdf;                // [Np]
   // episodes
-  float *ex, *ey;
+  float *ex, *ey, *epf;       // NAV2D / CROWD robot, CROWD people [12][M]
   int *es, *eb, *alive, *eslot, *ean;
   // tree
   int *parent_an, *depth;
@@ -76,18 +77,47 @@ namespace {
 
 template <class M>
 __device__ __forceinline__ typename M::S ep_load(const EpDesc &P, int e) {
-  if constexpr (M::kStochastic) return typename M::S{P.ex[e], P.ey[e]};
-  else return typename M::S{P.es[e]};
+  if constexpr (SelfDraw<M>::value) {
+    typename M::S s;
+    s.x = P.ex[e];
+    s.y = P.ey[e];
+    for (int q = 0; q < 6; ++q) { s.px[q] = P.epf[(2 * q) * P.M + e]; s.py[q] = P.epf[(2 * q + 1) * P.M + e]; }
+    s.f = P.es[e];
+    return s;
+  } else if constexpr (M::kStochastic) {
+    return typename M::S{P.ex[e], P.ey[e]};
+  } else {
+    return typename M::S{P.es[e]};
+  }
 }
 template <class M>
 __device__ __forceinline__ void ep_store(const EpDesc &P, int e, const typename M::S &s) {
-  if constexpr (M::kStochastic) { P.ex[e] = s.x; P.ey[e] = s.y; }
-  else P.es[e] = s.s;
+  if constexpr (SelfDraw<M>::value) {
+    P.ex[e] = s.x;
+    P.ey[e] = s.y;
+    for (int q = 0; q < 6; ++q) { P.epf[(2 * q) * P.M + e] = s.px[q]; P.epf[(2 * q + 1) * P.M + e] = s.py[q]; }
+    P.es[e] = s.f;
+  } else if constexpr (M::kStochastic) {
+    P.ex[e] = s.x;
+    P.ey[e] = s.y;
+  } else {
+    P.es[e] = s.s;
+  }
 }
 template <class M>
 __device__ __forceinline__ typename M::S ep_root(const EpDesc &P, int i) {
-  if constexpr (M::kStochastic) return typename M::S{P.rx[i], P.ry[i]};
-  else return typename M::S{P.rs[i]};
+  if constexpr (SelfDraw<M>::value) {
+    typename M::S s;
+    s.x = P.rx[i];
+    s.y = P.ry[i];
+    for (int q = 0; q < 6; ++q) { s.px[q] = P.rpf[(2 * q) * P.Np + i]; s.py[q] = P.rpf[(2 * q + 1) * P.Np + i]; }
+    s.f = P.rs[i];
+    return s;
+  } else if constexpr (M::kStochastic) {
+    return typename M::S{P.rx[i], P.ry[i]};
+  } else {
+    return typename M::S{P.rs[i]};
+  }
 }
 
 // Root CDF in FP64 (terminal particles weigh 0) and the root node.  One CTA.
@@ -151,6 +181,7 @@ __global__ void __launch_bounds__(1024) k_ep_prepare(EpDesc P) {
   switch (P.kind) {
     case kNav: ep_prepare<NavModel>(P, part); break;
     case kGrid: ep_prepare<GridModel>(P, part); break;
+    case kCrowd: ep_prepare<CrowdModel>(P, part); break;
     default: ep_prepare<ToyModel>(P, part); break;
   }
 }
@@ -176,6 +207,7 @@ __global__ void k_ep_start(EpDesc P, unsigned long long k) {
   switch (P.kind) {
     case kNav: ep_start<NavModel>(P, e, k); break;
     case kGrid: ep_start<GridModel>(P, e, k); break;
+    case kCrowd: ep_start<CrowdModel>(P, e, k); break;
     default: ep_start<ToyModel>(P, e, k); break;
   }
 }
@@ -200,9 +232,14 @@ __device__ void ep_step(const EpDesc &P, int e, int d, unsigned long long k) {
   }
   typename M::S s = ep_load<M>(P, e);
   const uint4 ws = draw(P.key0, P.key1, (uint32_t)e, kPurposeEpStep, (uint32_t)d, 0, 0, k);
-  const float r = M::step(s, act, ws.x, ws.y, *P.model);
+  // pair-drawn models take words 0,1 of the episode's call (index 0 of the pair); a
+  // self-drawing model keys its own calls by the episode
+  const int si = SelfDraw<M>::value ? e : 0;
+  const float r = step_particle<M>(s, act, ws, si, DrawCtx{P.key0, P.key1, kPurposeEpStep, (uint32_t)d, k},
+                                   *P.model);
   const uint4 wo = draw(P.key0, P.key1, (uint32_t)e, kPurposeEpObs, (uint32_t)d, 0, 0, k);
-  const typename M::O o = M::draw_obs(s, act, wo.x, wo.y, *P.model);
+  const typename M::O o = obs_particle<M>(s, act, wo, DrawCtx{P.key0, P.key1, kPurposeEpObs, (uint32_t)d, k},
+                                          (uint32_t)e, *P.model);
   const long long an = (long long)b * A + act;
   atomicAdd(P.C + an, (double)r);
   atomicAdd(P.N + an, 1ull);
@@ -228,6 +265,7 @@ __global__ void k_ep_step(EpDesc P, int d, unsigned long long k) {
   switch (P.kind) {
     case kNav: ep_step<NavModel>(P, e, d, k); break;
     case kGrid: ep_step<GridModel>(P, e, d, k); break;
+    case kCrowd: ep_step<CrowdModel>(P, e, d, k); break;
     default: ep_step<ToyModel>(P, e, d, k); break;
   }
 }
@@ -318,6 +356,7 @@ __global__ void k_ep_leaf(EpDesc P) {
   switch (P.kind) {
     case kNav: ep_leaf<NavModel>(P, e); break;
     case kGrid: ep_leaf<GridModel>(P, e); break;
+    case kCrowd: ep_leaf<CrowdModel>(P, e); break;
     default: ep_leaf<ToyModel>(P, e); break;
   }
 }
@@ -403,7 +442,7 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   const vopp_model_desc &desc = model_desc(m);
   const int A = vopp_model_num_actions(m);
   const int kind = desc.kind;
-  const int O = kind == kGrid ? 3 : (kind == kToy ? 2 : 0);
+  const int O = kind == kGrid ? 3 : (kind == kToy ? 2 : (kind == kCrowd ? 64 : 0));
   if (!out) return set_error(VOPP_E_INVALID, "vopp_plan_episodes: out is NULL");
   if (in.N < 1 || in.N > VOPP_MAX_PARTICLES) return set_error(VOPP_E_INVALID, "n_particles outside [1, 65536]");
   if (!in.states) return set_error(VOPP_E_INVALID, "root_states is NULL");
@@ -427,10 +466,12 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   const size_t Np = (size_t)in.N;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
-  const bool nav = kind == kNav;
-  const size_t o_rx = take(nav ? 4 * Np : 0), o_ry = take(nav ? 4 * Np : 0);
+  const bool nav = kind == kNav, crowd = kind == kCrowd, xy = nav || crowd;
+  const size_t o_rx = take(xy ? 4 * Np : 0), o_ry = take(xy ? 4 * Np : 0);
   const size_t o_rs = take(nav ? 0 : 4 * Np), o_rw = take(4 * Np), o_cdf = take(8 * Np);
-  const size_t o_ex = take(nav ? 4 * M : 0), o_ey = take(nav ? 4 * M : 0), o_es = take(nav ? 0 : 4 * M);
+  const size_t o_rpf = take(crowd ? 48 * Np : 0);
+  const size_t o_ex = take(xy ? 4 * M : 0), o_ey = take(xy ? 4 * M : 0), o_es = take(nav ? 0 : 4 * M);
+  const size_t o_epf = take(crowd ? 48 * M : 0);
   const size_t o_eb = take(4 * M), o_alive = take(4 * M), o_eslot = take(4 * M), o_ean = take(4 * M);
   const size_t o_par = take(4 * cap), o_dep = take(4 * cap);
   const size_t o_psi = take(8 * cap * A), o_V = take(8 * cap), o_C = take(8 * cap * A);
@@ -457,7 +498,7 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   const double g = p.gamma;
   P.log2g = (float)std::log2(g);
   P.h_a0 = (float)(-1.0 / (1.0 - g));
-  P.h_b0 = (float)(100.0 + 1.0 / (1.0 - g));
+  P.h_b0 = (float)((kind == kCrowd ? 1000.0 : 100.0) + 1.0 / (1.0 - g));
   P.h_zero = desc.h_zero;
   P.key0 = (uint32_t)p.seed;
   P.key1 = (uint32_t)(p.seed >> 32);
@@ -474,7 +515,20 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   auto u64 = [&](size_t o) { return reinterpret_cast<unsigned long long *>(B + o); };
   const bool dev = in.ptr_flags & VOPP_PTR_DEVICE;
   cudaError_t e = cudaSuccess;
-  if (nav) {
+  if (crowd) {   // 15 rows of N words: robot x, y, 12 people coordinates, flags
+    const float *w = static_cast<const float *>(in.states);
+    if (!dev) {
+      e = cudaMemcpyAsync(f(o_rx), in.states, 4 * Np, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(f(o_ry), w + Np, 4 * Np, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(f(o_rpf), w + 2 * Np, 48 * Np, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(i32(o_rs), w + 14 * Np, 4 * Np, cudaMemcpyHostToDevice, st);
+      w = nullptr;
+    }
+    P.rx = w ? w : f(o_rx);
+    P.ry = w ? w + Np : f(o_ry);
+    P.rpf = w ? w + 2 * Np : f(o_rpf);
+    P.rs = w ? reinterpret_cast<const int *>(w + 14 * Np) : i32(o_rs);
+  } else if (nav) {
     if (dev) {
       P.rx = static_cast<const float *>(in.states);
       P.ry = P.rx + in.N;
@@ -504,7 +558,7 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
     }
   }
   P.cdf = f64(o_cdf);
-  P.ex = f(o_ex); P.ey = f(o_ey); P.es = i32(o_es);
+  P.ex = f(o_ex); P.ey = f(o_ey); P.es = i32(o_es); P.epf = f(o_epf);
   P.eb = i32(o_eb); P.alive = i32(o_alive); P.eslot = i32(o_eslot); P.ean = i32(o_ean);
   P.parent_an = i32(o_par); P.depth = i32(o_dep);
   P.psi = f64(o_psi); P.V = f64(o_V); P.C = f64(o_C); P.Ws = f64(o_Ws); P.Hs = f64(o_Hs);

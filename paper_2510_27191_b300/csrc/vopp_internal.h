@@ -24,6 +24,7 @@ struct BeliefArgs {
   int *s;                      // current belief (GRID / TOY2)
   float *tx, *ty, *tlw;        // propagated particles (scratch)
   int *ts;
+  float *pf, *tpf;             // CROWD people [12][N] (current, propagated)
   double *cdf;                 // [N] scratch
   int *anc;                    // [N] ancestors of the update
   float obs_f[2];
@@ -44,8 +45,9 @@ struct EnvArgs {
   int kind, action;
   uint32_t key0, key1;
   unsigned long long t;        // environment time step (Philox node word)
-  float *xy;                   // NAV2D state (x, y)
-  int *s;                      // GRID / TOY2 state
+  float *xy;                   // NAV2D / CROWD robot (x, y)
+  int *s;                      // GRID / TOY2 state, CROWD flags
+  float *pf;                   // CROWD people (x, y) x 6
   const DevModel *model;
   EnvOut *out;
 };

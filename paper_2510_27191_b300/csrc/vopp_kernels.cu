@@ -75,6 +75,34 @@ template <> struct GNode<ToyModel> : GNodeInt<ToyModel> {
   }
 };
 
+template <> struct GNode<CrowdModel> {
+  float *x, *y, *pf, *lwp;
+  int *f;
+  int N;
+  __device__ static GNode at(const PlanDesc &P, int l, long long node) {
+    const long long b = node * P.N;
+    return GNode{P.px[l] + b, P.py[l] + b, P.pf[l] + 12 * b, P.plw[l] + b, P.ps[l] + b, P.N};
+  }
+  __device__ __forceinline__ CrowdModel::S get(int i) const {
+    CrowdModel::S s;
+    s.x = x[i];
+    s.y = y[i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { s.px[q] = pf[(2 * q) * N + i]; s.py[q] = pf[(2 * q + 1) * N + i]; }
+    s.f = f[i];
+    return s;
+  }
+  __device__ __forceinline__ void put(int i, const CrowdModel::S &s) const {
+    x[i] = s.x;
+    y[i] = s.y;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { pf[(2 * q) * N + i] = s.px[q]; pf[(2 * q + 1) * N + i] = s.py[q]; }
+    f[i] = s.f;
+  }
+  __device__ __forceinline__ float lw(int i) const { return lwp[i]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { lwp[i] = v; }
+};
+
 template <class M> struct SNode;
 template <> struct SNode<NavModel> {
   float4 *A, *B;
@@ -138,6 +166,43 @@ template <> struct SNode<ToyModel> : SNodeInt<ToyModel> {
   }
 };
 
+// CROWD in shared memory: {lw0,lw1,w0,w1} per pair, then 15 rows of 2*npairs words (robot
+// x, y, the 12 people coordinates, the flags).
+template <> struct SNode<CrowdModel> {
+  float4 *B;
+  float *F;
+  int n2;
+  static constexpr int kPairBytes = 16 + 2 * 15 * 4;
+  __device__ static SNode at(float *base, int npairs) {
+    float4 *b = reinterpret_cast<float4 *>(base);
+    return SNode{b, reinterpret_cast<float *>(b + npairs), 2 * npairs};
+  }
+  __device__ __forceinline__ CrowdModel::S get(int i) const {
+    CrowdModel::S s;
+    s.x = F[i];
+    s.y = F[n2 + i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { s.px[q] = F[(2 + 2 * q) * n2 + i]; s.py[q] = F[(3 + 2 * q) * n2 + i]; }
+    s.f = __float_as_int(F[14 * n2 + i]);
+    return s;
+  }
+  __device__ __forceinline__ void put(int i, const CrowdModel::S &s) const {
+    F[i] = s.x;
+    F[n2 + i] = s.y;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { F[(2 + 2 * q) * n2 + i] = s.px[q]; F[(3 + 2 * q) * n2 + i] = s.py[q]; }
+    F[14 * n2 + i] = __int_as_float(s.f);
+  }
+  __device__ __forceinline__ void get_pair(int p, CrowdModel::S &s0, CrowdModel::S &s1) const {
+    s0 = get(2 * p);
+    s1 = get(2 * p + 1);
+  }
+  __device__ __forceinline__ float lw(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[i & 1]; }
+  __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
+  __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
+  __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+};
+
 // Scratch for the two per-particle values a child build keeps between its passes.
 struct ScratchArrays {           // K2: dynamic shared memory, N floats each
   float *L, *E;
@@ -168,6 +233,9 @@ template <> __device__ __forceinline__ float2 state_xy<GridModel>(const GridMode
 template <> __device__ __forceinline__ float2 state_xy<ToyModel>(const ToyModel::S &) {
   return make_float2(0.f, 0.f);
 }
+template <> __device__ __forceinline__ float2 state_xy<CrowdModel>(const CrowdModel::S &s) {
+  return make_float2(s.x, s.y);
+}
 
 template <class M> __device__ __forceinline__ typename M::S set_xy(typename M::S s, float, float) { return s; }
 template <> __device__ __forceinline__ NavModel::S set_xy<NavModel>(NavModel::S, float x, float y) {
@@ -184,6 +252,15 @@ template <> __device__ __forceinline__ GridModel::S load_root<GridModel>(const P
 }
 template <> __device__ __forceinline__ ToyModel::S load_root<ToyModel>(const PlanDesc &P, int i) {
   return ToyModel::S{P.root_s[i]};
+}
+template <> __device__ __forceinline__ CrowdModel::S load_root<CrowdModel>(const PlanDesc &P, int i) {
+  CrowdModel::S s;
+  s.x = P.root_x[i];
+  s.y = P.root_y[i];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) { s.px[q] = P.root_pf[(2 * q) * P.N + i]; s.py[q] = P.root_pf[(2 * q + 1) * P.N + i]; }
+  s.f = P.root_s[i];
+  return s;
 }
 
 // Transition Philox words of particle pair p of branch (l, node, a, k).
@@ -205,8 +282,9 @@ __device__ __forceinline__ typename M::O branch_obs(const PlanDesc &P, const Src
   j = (int)(((unsigned long long)w.z * (unsigned long long)P.N) >> 32);
   typename M::S sj = src.get(j);
   const uint4 t = pair_words<M>(P, j >> 1, l, a, k, node);
-  M::step(sj, a, (j & 1) ? t.z : t.x, (j & 1) ? t.w : t.y, dm);
-  return M::draw_obs(sj, a, w.x, w.y, dm);
+  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  step_particle<M>(sj, a, t, j, DrawCtx{P.key0, P.key1, kPurposeTransition, c1, node}, dm);
+  return obs_particle<M>(sj, a, w, DrawCtx{P.key0, P.key1, kPurposeObservation, c1, node}, 0u, dm);
 }
 
 // log pibar(a | node) for a < A (computed by every calling thread).
@@ -292,8 +370,9 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       s0 = set_xy<M>(s0, X.x, Y.x);
       s1 = set_xy<M>(s1, X.y, Y.y);
     } else {
-      r.x = M::step(s0, a, w.x, w.y, dm);
-      r.y = M::step(s1, a, w.z, w.w, dm);
+      const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, parent};
+      r.x = step_particle<M>(s0, a, w, i0, dc, dm);
+      r.y = step_particle<M>(s1, a, w, i1, dc, dm);
       e = make_float2(M::loglik2(s0, a, o, dm), M::loglik2(s1, a, o, dm));
     }
     const float L0 = fmaf(lw0, kLog2e, e.x), L1 = v1 ? fmaf(lw1, kLog2e, e.y) : -CUDART_INF_F;
@@ -662,6 +741,7 @@ __global__ void __launch_bounds__(1024) k_root_prep(const PlanDesc *plans, Stage
   switch (P.kind) {
     case kNav: root_prep_plan<NavModel>(P, dm, red); break;
     case kGrid: root_prep_plan<GridModel>(P, dm, red); break;
+    case kCrowd: root_prep_plan<CrowdModel>(P, dm, red); break;
     default: root_prep_plan<ToyModel>(P, dm, red); break;
   }
 }
@@ -694,6 +774,7 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
     switch (P.kind) {
       case kNav: expand_item<NavModel>(P, l, child, smem, red); break;
       case kGrid: expand_item<GridModel>(P, l, child, smem, red); break;
+      case kCrowd: expand_item<CrowdModel>(P, l, child, smem, red); break;
       default: expand_item<ToyModel>(P, l, child, smem, red); break;
     }
   }
@@ -849,8 +930,9 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
         typename M::S s0, s1;
         nb.get_pair(p, s0, s1);
         const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
-        const float r0 = M::step(s0, a, w.x, w.y, dm);
-        const float r1 = M::step(s1, a, w.z, w.w, dm);
+        const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, node};
+        const float r0 = step_particle<M>(s0, a, w, 2 * p, dc, dm);
+        const float r1 = step_particle<M>(s1, a, w, 2 * p + 1, dc, dm);
         const float e0 = M::loglik2(s0, a, o, dm), e1 = M::loglik2(s1, a, o, dm);
         const bool v1 = 2 * p + 1 < N;
         L[2 * c] = b.x + e0;
@@ -978,6 +1060,7 @@ template <int K> struct LeafModel;
 template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMinBlocks = VOPP_LEAF_MINBLOCKS; };
 template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
 template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
+template <> struct LeafModel<kCrowd> { using type = CrowdModel; static constexpr int kMinBlocks = 2; };
 
 template <int K>
 __global__ void __launch_bounds__(256, LeafModel<K>::kMinBlocks)
@@ -1017,7 +1100,10 @@ template <class M>
 __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red, double *dred) {
   const int N = B.N;
   GNode<M> cur, nxt;
-  if constexpr (M::kStochastic) {
+  if constexpr (SelfDraw<M>::value) {
+    cur = GNode<M>{B.x, B.y, B.pf, B.lw, B.s, N};
+    nxt = GNode<M>{B.tx, B.ty, B.tpf, B.tlw, B.ts, N};
+  } else if constexpr (M::kStochastic) {
     cur = GNode<M>{B.x, B.y, B.lw};
     nxt = GNode<M>{B.tx, B.ty, B.tlw};
   } else {
@@ -1031,13 +1117,10 @@ __device__ void belief_plan(const BeliefArgs &B, const DevModel &dm, float *red,
   float m = -CUDART_INF_F;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     typename M::S s = cur.get(i);
-    uint32_t wa = 0, wb = 0;
-    if (M::kStochastic) {
-      const uint4 w = draw(B.key0, B.key1, (uint32_t)(i >> 1), kPurposeBeliefStep, 0, 0, 0, B.t);
-      wa = (i & 1) ? w.z : w.x;
-      wb = (i & 1) ? w.w : w.y;
-    }
-    M::step(s, B.action, wa, wb, dm);
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (M::kStochastic)
+      w = draw(B.key0, B.key1, (uint32_t)(i >> 1), kPurposeBeliefStep, 0, 0, 0, B.t);
+    step_particle<M>(s, B.action, w, i, DrawCtx{B.key0, B.key1, kPurposeBeliefStep, 0u, B.t}, dm);
     const float L = cur.lw(i) + M::loglik(s, B.action, o, dm);
     nxt.put(i, s);
     nxt.set_lw(i, L);
@@ -1118,6 +1201,7 @@ __global__ void __launch_bounds__(1024) k_belief(BeliefArgs B) {
   switch (B.kind) {
     case kNav: belief_plan<NavModel>(B, dm, red, dred); break;
     case kGrid: belief_plan<GridModel>(B, dm, red, dred); break;
+    case kCrowd: belief_plan<CrowdModel>(B, dm, red, dred); break;
     default: belief_plan<ToyModel>(B, dm, red, dred); break;
   }
 }
@@ -1132,13 +1216,30 @@ template <class M>
 __device__ void env_step(const EnvArgs &E) {
   const DevModel &dm = *E.model;
   typename M::S s;
-  if constexpr (M::kStochastic) s = typename M::S{E.xy[0], E.xy[1]};
-  else s = typename M::S{E.s[0]};
+  if constexpr (SelfDraw<M>::value) {
+    s.x = E.xy[0];
+    s.y = E.xy[1];
+    for (int q = 0; q < 12; ++q) (q & 1 ? s.py : s.px)[q >> 1] = E.pf[q];
+    s.f = E.s[0];
+  } else if constexpr (M::kStochastic) {
+    s = typename M::S{E.xy[0], E.xy[1]};
+  } else {
+    s = typename M::S{E.s[0]};
+  }
   const uint4 w = draw(E.key0, E.key1, 0u, kPurposeEnvStep, 0, 0, 0, E.t);
-  const float r = M::step(s, E.action, w.x, w.y, dm);
+  const float r = step_particle<M>(s, E.action, w, 0, DrawCtx{E.key0, E.key1, kPurposeEnvStep, 0u, E.t}, dm);
   const uint4 v = draw(E.key0, E.key1, 0u, kPurposeEnvObs, 0, 0, 0, E.t);
-  const typename M::O o = M::draw_obs(s, E.action, v.x, v.y, dm);
-  if constexpr (M::kStochastic) {
+  const typename M::O o =
+      obs_particle<M>(s, E.action, v, DrawCtx{E.key0, E.key1, kPurposeEnvObs, 0u, E.t}, 0u, dm);
+  if constexpr (SelfDraw<M>::value) {
+    E.xy[0] = s.x;
+    E.xy[1] = s.y;
+    for (int q = 0; q < 12; ++q) E.pf[q] = (q & 1 ? s.py : s.px)[q >> 1];
+    E.s[0] = s.f;
+    E.out->obs[0] = (float)o.o;
+    E.out->obs[1] = 0.f;
+    E.out->obs_i = o.o;
+  } else if constexpr (M::kStochastic) {
     E.xy[0] = s.x;
     E.xy[1] = s.y;
     E.out->obs[0] = o.x;
@@ -1159,6 +1260,7 @@ __global__ void k_env(EnvArgs E) {
   switch (E.kind) {
     case kNav: env_step<NavModel>(E); break;
     case kGrid: env_step<GridModel>(E); break;
+    case kCrowd: env_step<CrowdModel>(E); break;
     default: env_step<ToyModel>(E); break;
   }
 }
@@ -1167,7 +1269,7 @@ __global__ void k_env(EnvArgs E) {
 // Host-side launchers.
 // ---------------------------------------------------------------------------------------
 size_t leaf_smem_bytes(int kind, int N, int AW) {
-  const size_t pair = (kind == kNav) ? 32 : 24;
+  const size_t pair = (kind == kNav) ? 32 : (kind == kCrowd ? SNode<CrowdModel>::kPairBytes : 24);
   return pair * (size_t)((N + 1) / 2) + 3 * sizeof(float) * (size_t)AW + 64;
 }
 size_t expand_smem_bytes(int N) { return 8 * (size_t)N + 64; }
@@ -1190,6 +1292,9 @@ cudaError_t init_kernel_attributes() {
                              (int)kLeafSmemLimit);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf<kToy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf<kCrowd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kLeafSmemLimit);
   return e;
 }
@@ -1223,6 +1328,7 @@ cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long 
     case kNav: return launch_pdl(k_leaf<kNav>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kGrid: return launch_pdl(k_leaf<kGrid>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kToy: return launch_pdl(k_leaf<kToy>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+    case kCrowd: return launch_pdl(k_leaf<kCrowd>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1232,6 +1338,7 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
     case kNav: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kNav>, threads, smem);
     case kGrid: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kGrid>, threads, smem);
     case kToy: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kToy>, threads, smem);
+    case kCrowd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kCrowd>, threads, smem);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libvopp.so")
 
 VOPP_OK, VOPP_E_INVALID, VOPP_E_NOMEM, VOPP_E_BUDGET = 0, -1, -2, -3
 VOPP_E_CUDA, VOPP_E_TIMEOUT, VOPP_E_DEGENERATE, VOPP_E_BUSY = -4, -5, -6, -7
-VOPP_NAV2D, VOPP_GRID, VOPP_TOY2 = 0, 1, 2
+VOPP_NAV2D, VOPP_GRID, VOPP_TOY2, VOPP_CROWD = 0, 1, 2, 3
 VOPP_BRANCH_SAMPLE, VOPP_BRANCH_ENUMERATE = 0, 1
 VOPP_PI_UNIFORM, VOPP_PI_FIXED, VOPP_PI_NAV_DIST = 0, 1, 2
 VOPP_PTR_DEVICE = 1
@@ -26,7 +26,7 @@ VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT = 1, 2
 VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 (VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
  VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU,
- VOPP_FIELD_PSI) = range(12)
+ VOPP_FIELD_PSI, VOPP_FIELD_PF) = range(13)
 VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP = 1, 2, 3
 VOPP_OPT_PERSISTENT = 5
 VOPP_OPT_FP64_ROOT = 6
@@ -395,9 +395,17 @@ def vopp_belief_update(agent: int, action: int, obs, kind: int):
     return ess.value, bool(res.value)
 
 
+def _state_words(kind: int) -> int:
+    return {VOPP_NAV2D: 2, VOPP_CROWD: 15}.get(kind, 1)
+
+
 def vopp_agent_get_particles(agent: int, kind: int):
+    """(states, log weights, ancestors of the last update); states in the root layout
+    (NAV2D float32 [2N]; GRID / TOY2 int32 [N]; CROWD float32 [15N], the last row int32
+    flags)."""
     n = check(lib.vopp_agent_num_particles(agent))
-    st = np.empty(2 * n, dtype=np.float32) if kind == VOPP_NAV2D else np.empty(n, dtype=np.int32)
+    st = (np.empty(_state_words(kind) * n, dtype=np.float32) if kind in (VOPP_NAV2D, VOPP_CROWD)
+          else np.empty(n, dtype=np.int32))
     lw = np.empty(n, dtype=np.float32)
     anc = np.empty(n, dtype=np.int32)
     check(lib.vopp_agent_get_particles(agent, st.ctypes.data, lw.ctypes.data, anc.ctypes.data, 0))
@@ -469,10 +477,22 @@ def vopp_episode_tree_read(ctx: int, field: int, count: int, offset: int = 0) ->
 
 
 # ---- closed loop -------------------------------------------------------------------------
+def _env_state(state, kind):
+    if kind == VOPP_NAV2D:
+        return np.asarray(state, dtype=np.float32).reshape(2)
+    if kind == VOPP_CROWD:   # (x, y, flags, people[12])
+        st = np.empty(15, dtype=np.float32)
+        st[0], st[1] = state[0], state[1]
+        st[2:14] = np.asarray(state[3], dtype=np.float32).reshape(12)
+        st[14:15] = np.asarray([int(state[2])], dtype=np.int32).view(np.float32)
+        return st
+    return np.asarray([int(state)], dtype=np.int32)
+
+
 def vopp_env_create(model: int, state, seed: int, kind: int) -> int:
-    """state: (x, y) for NAV2D, an int for GRID / TOY2 (kind: the model's kind)."""
-    st = (np.asarray(state, dtype=np.float32).reshape(2) if kind == VOPP_NAV2D
-          else np.asarray([int(state)], dtype=np.int32))
+    """state: (x, y) for NAV2D, an int for GRID / TOY2, (x, y, flags, people[12]) for CROWD
+    (kind: the model's kind)."""
+    st = _env_state(state, kind)
     h = ctypes.c_void_p()
     check(lib.vopp_env_create(model, st.ctypes.data, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h)))
     return h.value
@@ -489,9 +509,14 @@ def vopp_env_step(env: int, action: int, kind: int):
 
 
 def vopp_env_get_state(env: int, kind: int):
-    o = np.zeros(2, dtype=np.float32) if kind == VOPP_NAV2D else np.zeros(1, dtype=np.int32)
+    o = np.zeros(_state_words(kind), dtype=np.float32 if kind != VOPP_GRID and kind != VOPP_TOY2
+                 else np.int32)
     check(lib.vopp_env_get_state(env, o.ctypes.data))
-    return (float(o[0]), float(o[1])) if kind == VOPP_NAV2D else int(o[0])
+    if kind == VOPP_NAV2D:
+        return (float(o[0]), float(o[1]))
+    if kind == VOPP_CROWD:
+        return (float(o[0]), float(o[1]), int(o[14:15].view(np.int32)[0]), o[2:14].copy())
+    return int(o[0])
 
 
 def vopp_env_destroy(env: int) -> None:

@@ -11,7 +11,7 @@ from paper_2510_27191_b300 import workloads as WL
 # (relative 1e-4, measured in reward units below magnitude 1).
 RTOL = 1e-4
 
-KIND_A = {WL.NAV2D: 4, WL.GRID: 13, WL.TOY2: 2}
+KIND_A = {WL.NAV2D: 4, WL.GRID: 13, WL.TOY2: 2, WL.CROWD: 5}
 
 
 def close(g, o, rtol=RTOL):
@@ -55,6 +55,8 @@ class Spec:
         elif kind == WL.GRID:
             s, w = WL.grid_root(N, root_seed, weights)
             self.root = dict(s=s, w=w)
+        elif kind == WL.CROWD:
+            self.root = WL.crowd_root(N, root_seed, weights=weights)
         else:
             s, w = WL.toy2_root_sampled(N, root_seed)
             self.root = dict(s=s, w=None if weights == "uniform" else w)
@@ -66,6 +68,8 @@ class Spec:
                     layout_seed=ps.layout_seed, root_seed=ps.root_seed, **kw)
 
     def states(self):
+        if self.kind == WL.CROWD:
+            return WL.pack_crowd_states(self.root)
         if self.kind == WL.NAV2D:
             return np.concatenate([self.root["x"], self.root["y"]]).astype(np.float32)
         return np.asarray(self.root["s"], dtype=np.int32)
@@ -87,6 +91,11 @@ class Spec:
         if self.kind == WL.NAV2D:
             return O.plan(m, self.N, self.D, self.W, self.eta, self.gamma, self.seed,
                           root_x=self.root["x"], root_y=self.root["y"], root_w=w, path=path,
+                          dump_levels=dump_levels, outputs=outputs)
+        if self.kind == WL.CROWD:
+            return O.plan(m, self.N, self.D, self.W, self.eta, self.gamma, self.seed,
+                          root_x=self.root["x"], root_y=self.root["y"], root_s=self.root["s"],
+                          root_pf=self.root["pf"], root_w=w, path=path,
                           dump_levels=dump_levels, outputs=outputs)
         return O.plan(m, self.N, self.D, self.W, self.eta, self.gamma, self.seed,
                       root_s=self.root["s"], root_w=w, path=path, dump_levels=dump_levels,
@@ -169,21 +178,25 @@ def compare_full_tree(spec: Spec, gpu: Gpu, res: dict, orc: dict, materialised_t
             if spec.kind == WL.NAV2D:
                 assert_close(obs, orc["obs"][l], f"obs[{l}]", np.repeat(keep[l], 2).reshape(n, 2))
             else:
-                np.testing.assert_array_equal(obs, orc["obs"][l], err_msg=f"obs[{l}]")
+                np.testing.assert_array_equal(obs[keep[l]], orc["obs"][l][keep[l]], err_msg=f"obs[{l}]")
     if check_particles:
         for l in range(0, materialised_top + 1):
             n = AW ** l
             kp = np.repeat(keep[l], N).reshape(n, N)
             lw = gpu.read(V.VOPP_FIELD_PLW, l, n * N).reshape(n, N)
             assert_close(lw, orc["plw"][l], f"plw[{l}]", kp)
-            if spec.kind == WL.NAV2D:
+            if spec.kind in (WL.NAV2D, WL.CROWD):
                 px = gpu.read(V.VOPP_FIELD_PX, l, n * N).reshape(n, N)
                 py = gpu.read(V.VOPP_FIELD_PY, l, n * N).reshape(n, N)
                 assert_close(px, orc["px"][l], f"px[{l}]", kp)
                 assert_close(py, orc["py"][l], f"py[{l}]", kp)
-            else:
+            if spec.kind != WL.NAV2D:
                 ps = gpu.read(V.VOPP_FIELD_PS, l, n * N).reshape(n, N)
-                np.testing.assert_array_equal(ps, orc["ps"][l], err_msg=f"ps[{l}]")
+                np.testing.assert_array_equal(ps[kp], orc["ps"][l][kp], err_msg=f"ps[{l}]")
+            if spec.kind == WL.CROWD:
+                pf = gpu.read(V.VOPP_FIELD_PF, l, n * 12 * N).reshape(n, 12, N)
+                assert_close(pf, orc["ppf"][l], f"people[{l}]",
+                             np.repeat(kp[:, None, :], 12, axis=1))
     # root
     assert_close(res["q"], orc["q_root"], "root Q")
     assert_close([res["v_root"]], [orc["v_root"]], "root V")
