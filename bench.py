@@ -47,12 +47,15 @@ WORKLOADS = {
     # smaller grid plan (depth 4) used for kernel profiles
     "grid2048_d4": WL.PlanSpec(kind=WL.GRID, N=2048, D=4, W=3, eta=1.0, gamma=0.95, seed=1,
                                layout_seed=1, root_seed=1),
+    # crowd navigation shaped like the paper's CrowdNav (gamma 0.97), wide particle state
+    "crowd1024_d4": WL.PlanSpec(kind=WL.CROWD, N=1024, D=4, W=2, eta=1.0, gamma=0.97, seed=1,
+                                layout_seed=1, root_seed=1),
 }
 
 # Leaf-kernel roofline: issue-bound FP32/INT/SFU arithmetic.  Algorithmic instruction count
 # per particle-step of the fused leaf step (counted in the design notes) and the issue peak
 # of the B300: 148 SMs x 4 schedulers x 32 lanes per clock at the maximum SM clock.
-ALG_INSTR_PER_STEP = {WL.NAV2D: 106.0, WL.GRID: 52.0, WL.TOY2: 40.0}
+ALG_INSTR_PER_STEP = {WL.NAV2D: 106.0, WL.GRID: 52.0, WL.TOY2: 40.0, WL.CROWD: 420.0}
 SMS = 148
 LANES_PER_CLK = 128
 
@@ -183,7 +186,8 @@ def run_reference(args, spec, rank, world):
     steps_per_subtree = sum(AW ** l for l in range(1, spec.D)) * spec.N + spec.N
 
     def subtree(i):
-        kw = dict(root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"))
+        kw = dict(root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"),
+                  root_pf=root.get("pf"))
         r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(i % AW,),
                    outputs=False, **kw)
         return r["particle_steps"]
@@ -216,8 +220,20 @@ def _root_arrays(spec):
     if spec.kind == WL.NAV2D:
         x, y, _ = WL.nav_root(spec.N, spec.root_seed)
         return dict(x=x, y=y)
+    if spec.kind == WL.CROWD:
+        r = WL.crowd_root(spec.N, spec.root_seed)
+        return dict(x=r["x"], y=r["y"], s=r["s"], pf=r["pf"])
     s, _ = WL.grid_root(spec.N, spec.root_seed)
     return dict(s=s)
+
+
+def _host_states(spec, root):
+    """The C ABI's root layout of the workload's particles."""
+    if spec.kind == WL.NAV2D:
+        return np.concatenate([root["x"], root["y"]]).astype(np.float32)
+    if spec.kind == WL.CROWD:
+        return WL.pack_crowd_states(root)
+    return root["s"].astype(np.int32)
 
 
 def _config(spec, args):
@@ -244,7 +260,7 @@ def cpu_baseline(spec, budget_s=20.0):
     def subtree(n):
         r = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, spec.seed, path=(n % AW,),
                    outputs=False, root_x=root.get("x"), root_y=root.get("y"),
-                   root_s=root.get("s"))
+                   root_s=root.get("s"), root_pf=root.get("pf"))
         return r["particle_steps"]
 
     # single thread: subtrees one after another for a third of the budget
@@ -326,6 +342,14 @@ def modes_run(V, ctx, spec, dev_states):
                      "model_steps_per_s": r["particle_steps"] / t}
         V.vopp_model_destroy(m)
     out["episodes"] = eps
+    cs = WORKLOADS["crowd1024_d4"]
+    mc = V.vopp_create_model(ctx, V.make_desc(WL.CROWD))
+    cst = torch.from_numpy(_host_states(cs, _root_arrays(cs))).cuda()
+    t, r = timed(lambda: V.vopp_plan(mc, cst, None, cs.N, cs.D, cs.W, cs.eta, cs.gamma, None, cs.seed))
+    out["crowd1024_d4"] = {"ms": 1e3 * t, "particle_steps": r["particle_steps"],
+                           "particle_steps_per_s": r["particle_steps"] / t,
+                           "state_bytes_per_particle": 60}
+    V.vopp_model_destroy(mc)
     m = V.vopp_create_model(ctx, V.make_desc(WL.GRID, rock_x=rx, rock_y=ry))
     st, _ = WL.grid_root(1024, 2)
     g = V.vopp_agent_create(m, st.astype(np.int32), None, 1024, 2)
@@ -377,8 +401,7 @@ def main():
                                                  rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
                                                  rock_y=WL.grid_layout(spec.layout_seed)[1] if spec.kind == WL.GRID else None))
     root = _root_arrays(spec)
-    host_states = (np.concatenate([root["x"], root["y"]]).astype(np.float32) if spec.kind == WL.NAV2D
-                   else root["s"].astype(np.int32))
+    host_states = _host_states(spec, root)
     dev_states = torch.from_numpy(host_states).cuda()
     pinned = torch.from_numpy(host_states).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
