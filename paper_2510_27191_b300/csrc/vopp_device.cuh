@@ -589,7 +589,7 @@ struct CrowdModel {
     return philox(make_uint4(idx | (c.purpose << 24), c.c1 | (j << 24), (uint32_t)c.node,
                              (uint32_t)(c.node >> 32)), c.k0, c.k1);
   }
-  __device__ static float step_drawn(S &s, int a, const DrawCtx &c, uint32_t idx) {
+  __device__ __forceinline__ static float step_drawn(S &s, int a, const DrawCtx &c, uint32_t idx) {
     if (terminal(s)) return 0.0f;
     uint4 w[5];
 #pragma unroll
@@ -604,11 +604,14 @@ struct CrowdModel {
     int closer = 0;
 #pragma unroll
     for (int i = 0; i < kPeople; ++i) {
+      // distances are compared squared; the direction uses one reciprocal square root
       const float ex = __fsub_rn(s.px[i], nx), ey = __fsub_rn(s.py[i], ny);
-      const float d0 = __fsqrt_rn(fmaf(ex, ex, __fmul_rn(ey, ey)));
+      const float q0 = fmaf(ex, ex, __fmul_rn(ey, ey));
       float mx = 0.0f, my = 0.0f;
-      if (d0 < 4.0f && d0 > 0.0f) {
-        const float ux = __fdiv_rn(ex, d0), uy = __fdiv_rn(ey, d0);
+      if (q0 < 16.0f && q0 > 0.0f) {
+        const float inv = rsqrtf(q0);
+        const float d0 = q0 * inv;
+        const float ux = ex * inv, uy = ey * inv;
         const uint32_t wr = (i < 4) ? (&w[3].x)[i] : (&w[4].x)[i - 4];
         if (a == 4) {
           mx = 2.0f * ux; my = 2.0f * uy;
@@ -629,8 +632,7 @@ struct CrowdModel {
       const float qx = fminf(fmaxf(__fadd_rn(s.px[i], ddx), 0.0f), 50.0f);
       const float qy = fminf(fmaxf(__fadd_rn(s.py[i], ddy), 0.0f), 40.0f);
       const float fx = __fsub_rn(qx, nx), fy = __fsub_rn(qy, ny);
-      const float d1 = __fsqrt_rn(fmaf(fx, fx, __fmul_rn(fy, fy)));
-      if (!exited && d1 < 0.5f) r -= 200.0f;
+      if (!exited && fmaf(fx, fx, __fmul_rn(fy, fy)) < 0.25f) r -= 200.0f;
       s.px[i] = qx;
       s.py[i] = qy;
     }
