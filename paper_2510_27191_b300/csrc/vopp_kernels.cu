@@ -787,7 +787,8 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 //   VOPP_LEAF_CHUNK      Philox pairs per lane between two rescales of the running sums
 //   VOPP_ROUND_KEYS      1: Philox round keys held in registers for the whole branch
 //   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
-//                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2)
+//                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2;
+//                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
 #endif
@@ -799,6 +800,9 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTabl
 #endif
 #ifndef VOPP_LEAF_GRID_MINBLOCKS
 #define VOPP_LEAF_GRID_MINBLOCKS 4
+#endif
+#ifndef VOPP_LEAF_CROWD_MINBLOCKS
+#define VOPP_LEAF_CROWD_MINBLOCKS 1
 #endif
 #ifndef VOPP_LEAF_CHUNK_PACKED
 #define VOPP_LEAF_CHUNK_PACKED 4
@@ -910,11 +914,14 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
       R.add(rsum.x + rsum.y);
     }
   } else {
-  for (int base = lane; base < npairs; base += 32 * kLeafChunk) {
-    float L[2 * kLeafChunk], E[2 * kLeafChunk], Hh[2 * kLeafChunk];
+  // a self-drawing model's step is long: one pair per chunk keeps the unrolled loop small
+  // enough for the instruction cache
+  constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
+  for (int base = lane; base < npairs; base += 32 * kCh) {
+    float L[2 * kCh], E[2 * kCh], Hh[2 * kCh];
     float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rsum = 0.f;
 #pragma unroll
-    for (int c = 0; c < kLeafChunk; ++c) {
+    for (int c = 0; c < kCh; ++c) {
       const int p = base + 32 * c;
       L[2 * c] = L[2 * c + 1] = E[2 * c] = E[2 * c + 1] = -CUDART_INF_F;
       Hh[2 * c] = Hh[2 * c + 1] = 0.f;
@@ -951,7 +958,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
     float s1 = 0.f, h1 = 0.f, s0 = 0.f;
     if (m1 > -CUDART_INF_F) {
 #pragma unroll
-      for (int t = 0; t < 2 * kLeafChunk; ++t) {
+      for (int t = 0; t < 2 * kCh; ++t) {
         const float x1 = ex2(L[t] - m1);    // L = -inf gives 0
         s1 += x1;
         h1 = fmaf(x1, Hh[t], h1);
@@ -959,7 +966,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
     }
     if (m0 > -CUDART_INF_F) {
 #pragma unroll
-      for (int t = 0; t < 2 * kLeafChunk; ++t) s0 += ex2(E[t] - m0);
+      for (int t = 0; t < 2 * kCh; ++t) s0 += ex2(E[t] - m0);
     }
     A1.S.add(s1);
     A1.H.add(h1);
@@ -1060,7 +1067,7 @@ template <int K> struct LeafModel;
 template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMinBlocks = VOPP_LEAF_MINBLOCKS; };
 template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
 template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
-template <> struct LeafModel<kCrowd> { using type = CrowdModel; static constexpr int kMinBlocks = 2; };
+template <> struct LeafModel<kCrowd> { using type = CrowdModel; static constexpr int kMinBlocks = VOPP_LEAF_CROWD_MINBLOCKS; };
 
 template <int K>
 __global__ void __launch_bounds__(256, LeafModel<K>::kMinBlocks)
