@@ -16,9 +16,11 @@
 // dense child table [b][a][o], so AppendBeliefs is one compare-and-claim per episode instead
 // of a hash lookup).  New nodes of a depth step are numbered by one scan over the episodes in
 // episode order, so the tree is the same on every run and node ids equal the oracle's.
-// Reward sums, visit counts, heuristic sums and the whole backup are FP64: the sampled
-// decisions of later iterations read Psi, and FP64 keeps them away from rounding-order
-// effects of the atomics; the simulation itself is the FP32 model code of the plans.
+// Reward sums, visit counts, heuristic sums and the backup's accumulations are FP64: the
+// sampled decisions of later iterations read Psi, and FP64 keeps them away from the
+// rounding-order effects of the atomics; the simulation itself is the FP32 model code of the
+// plans, and the exponentials and logarithm of the softmax and log-sum-exp are FP32 (terms
+// <= 1, sums in [1, A]).
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -39,7 +41,7 @@ constexpr int kClaimBase = 1 << 30;   // claim of a child slot by episode e: e -
 
 struct EpDesc {
   int kind, A, O, M, Np, cap;
-  double eta, gamma;
+  double eta, gamma, inv_eta;
   float log2g, h_a0, h_b0;
   int h_zero;
   uint32_t key0, key1;
@@ -62,6 +64,10 @@ struct EpDesc {
   int *child;
   // counters: [0] nodes, [1] error, [2] first new node of the last step, [3] new nodes
   int *ctr;
+  int K;                      // iterations (= maximum depth)
+  int2 *ranges;               // [(K+1) * K]: beliefs of depth d created in iteration j
+  int *pre, *bsum;            // assignment scratch: prefix within the block, block sums
+  int nblk;                   // blocks of the episode kernels
   unsigned long long *steps;
   double *result;             // [2 + 2A]: action, V(root), Q(root)[A], policy[A]
 };
@@ -74,6 +80,21 @@ struct EpisodeStore {
 };
 
 namespace {
+
+// Warp-aggregated atomic adds: the active lanes that target the same index add their values
+// in lane order and one lane issues the atomic (many episodes share the shallow nodes).
+__device__ __forceinline__ void agg_add(double *base, long long key, double v) {
+  const unsigned act = __activemask();
+  const unsigned m = __match_any_sync(act, key);
+  double tot = 0.0;
+  for (unsigned b = m; b; b &= b - 1) tot += __shfl_sync(m, v, __ffs(b) - 1);
+  if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(base + key, tot);
+}
+__device__ __forceinline__ void agg_count(unsigned long long *base, long long key) {
+  const unsigned act = __activemask();
+  const unsigned m = __match_any_sync(act, key);
+  if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(base + key, (unsigned long long)__popc(m));
+}
 
 template <class M>
 __device__ __forceinline__ typename M::S ep_load(const EpDesc &P, int e) {
@@ -159,9 +180,12 @@ __device__ void ep_prepare(const EpDesc &P, double *part) {
   const double tot = part[T];
   double run = part[t];
   for (int i = b; i < e; ++i) { run += weight(i); P.cdf[i] = run / tot; }
+  for (int x = t; x < (P.K + 1) * P.K; x += T) P.ranges[x] = make_int2(0, 0);
+  __syncthreads();
   if (t == 0) {
     if (!(tot > 0.0)) P.ctr[1] = 2;     // degenerate root
     P.ctr[0] = 1;
+    P.ranges[0] = make_int2(0, 1);      // depth 0: the root
     P.parent_an[0] = -1;
     P.depth[0] = 0;
     P.V[0] = 0.0;
@@ -218,16 +242,19 @@ __device__ void ep_step(const EpDesc &P, int e, int d, unsigned long long k) {
   if (!P.alive[e]) return;
   const int A = P.A, b = P.eb[e];
   // a ~ softmax(Psi(b,.)/eta), inverse CDF in FP64 (first a with u < cumulative)
+  // (the softmax runs in FP32 from the FP64 preferences: its error, ~1e-7 of the total, lies
+  // far inside the 1e-5 band in which a sampled decision is treated as a tie)
   const double *ps = P.psi + (long long)b * A;
-  double z[kMaxActions], mx = -CUDART_INF, sum = 0.0;
-  for (int a = 0; a < A; ++a) { z[a] = ps[a] / P.eta; mx = fmax(mx, z[a]); }
-  for (int a = 0; a < A; ++a) { z[a] = exp(z[a] - mx); sum += z[a]; }
+  double zm = -CUDART_INF;
+  for (int a = 0; a < A; ++a) zm = fmax(zm, ps[a] * P.inv_eta);
+  float z[kMaxActions], sum = 0.f;
+  for (int a = 0; a < A; ++a) { z[a] = __expf((float)(ps[a] * P.inv_eta - zm)); sum += z[a]; }
   const uint4 wa = draw(P.key0, P.key1, (uint32_t)e, kPurposeEpAction, (uint32_t)d, 0, 0, k);
-  const double u = (double)u01(wa.x);
+  const float u = u01(wa.x), inv = 1.0f / sum;
   int act = A - 1;
-  double run = 0.0;
+  float run = 0.f;
   for (int a = 0; a < A; ++a) {
-    run += z[a] / sum;
+    run = fmaf(z[a], inv, run);
     if (u < run) { act = a; break; }
   }
   typename M::S s = ep_load<M>(P, e);
@@ -241,9 +268,9 @@ __device__ void ep_step(const EpDesc &P, int e, int d, unsigned long long k) {
   const typename M::O o = obs_particle<M>(s, act, wo, DrawCtx{P.key0, P.key1, kPurposeEpObs, (uint32_t)d, k},
                                           (uint32_t)e, *P.model);
   const long long an = (long long)b * A + act;
-  atomicAdd(P.C + an, (double)r);
-  atomicAdd(P.N + an, 1ull);
-  atomicAdd(P.steps, 1ull);
+  agg_add(P.C, an, (double)r);
+  agg_count(P.N, an);
+  agg_count(P.steps, 0);
   ep_store<M>(P, e, s);
   P.ean[e] = (int)an;
   if (M::terminal(s)) {             // FilterTerminals
@@ -270,20 +297,38 @@ __global__ void k_ep_step(EpDesc P, int d, unsigned long long k) {
   }
 }
 
-// AppendBeliefs: number the new beliefs of this step in episode order (one CTA, chunked
-// scan), publish them in the child table and move every live episode to its child.
-__global__ void __launch_bounds__(1024) k_ep_assign(EpDesc P, int d) {
+// AppendBeliefs: the new beliefs of a depth step are numbered in episode order by a scan
+// over the episodes' creator flags (block prefixes, one CTA over the block sums), then
+// published in the child table, and every live episode moves to its child.
+__device__ __forceinline__ bool ep_creator(const EpDesc &P, int e) {
+  if (e >= P.M || !P.alive[e]) return false;
+  return P.O == 0 || P.child[P.eslot[e]] == e - kClaimBase;
+}
+
+__global__ void __launch_bounds__(256) k_ep_flags(EpDesc P) {
+  __shared__ int wsum[8];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f = ep_creator(P, e) ? 1 : 0;
+  int incl = f;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  int woff = 0;
+  for (int w = 0; w < wid; ++w) woff += wsum[w];
+  if (e < P.M) P.pre[e] = woff + incl - f;
+  if (threadIdx.x == blockDim.x - 1) P.bsum[blockIdx.x] = woff + incl;
+}
+
+__global__ void __launch_bounds__(1024) k_ep_scan(EpDesc P, int d, int k) {
   __shared__ int wsum[32];
-  __shared__ int s_total, s_base, s_ok;
-  const int T = blockDim.x, t = threadIdx.x, M = P.M;
-  const int chunk = (M + T - 1) / T, b = t * chunk, e_end = min(M, b + chunk);
-  auto creator = [&](int e) -> bool {
-    if (!P.alive[e]) return false;
-    return P.O == 0 || P.child[P.eslot[e]] == e - kClaimBase;
-  };
+  __shared__ int s_base, s_total, s_ok;
+  const int T = blockDim.x, t = threadIdx.x, nb = P.nblk;
+  const int chunk = (nb + T - 1) / T, b = t * chunk, e_end = min(nb, b + chunk);
   int cnt = 0;
-  for (int e = b; e < e_end; ++e) cnt += creator(e) ? 1 : 0;
-  // block exclusive scan of the per-thread counts
+  for (int i = b; i < e_end; ++i) cnt += P.bsum[i];
   const int lane = t & 31, wid = t >> 5;
   int incl = cnt;
   for (int o = 1; o < 32; o <<= 1) {
@@ -301,25 +346,33 @@ __global__ void __launch_bounds__(1024) k_ep_assign(EpDesc P, int d) {
     if (!s_ok) P.ctr[1] = 1;       // capacity exceeded
   }
   __syncthreads();
-  if (!s_ok) return;
-  int id = s_base + wsum[wid] + incl - cnt;
-  for (int e = b; e < e_end; ++e) {
-    if (!creator(e)) continue;
-    P.parent_an[id] = P.ean[e];
-    P.depth[id] = d + 1;
-    if (P.O > 0) P.child[P.eslot[e]] = id;
-    else P.eb[e] = id;
-    ++id;
-  }
-  __syncthreads();
-  if (P.O > 0)
-    for (int e = b; e < e_end; ++e)
-      if (P.alive[e]) P.eb[e] = P.child[P.eslot[e]];
-  if (t == 0) {
+  int run = s_base + wsum[wid] + incl - cnt;
+  for (int i = b; i < e_end; ++i) { const int v = P.bsum[i]; P.bsum[i] = run; run += v; }
+  if (t == 0 && s_ok) {
     P.ctr[2] = s_base;
     P.ctr[3] = s_total;
     P.ctr[0] = s_base + s_total;
+    P.ranges[(d + 1) * P.K + (k - 1)] = make_int2(s_base, s_total);
+  } else if (t == 0) {
+    P.ctr[2] = s_base;
+    P.ctr[3] = 0;
   }
+}
+
+__global__ void __launch_bounds__(256) k_ep_publish(EpDesc P, int d) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P.ctr[1] != 0 || !ep_creator(P, e)) return;
+  const int id = P.bsum[blockIdx.x] + P.pre[e];
+  P.parent_an[id] = P.ean[e];
+  P.depth[id] = d + 1;
+  if (P.O > 0) P.child[P.eslot[e]] = id;
+  else P.eb[e] = id;
+}
+
+__global__ void __launch_bounds__(256) k_ep_advance(EpDesc P) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P.M || P.ctr[1] != 0 || !P.alive[e]) return;
+  P.eb[e] = P.child[P.eslot[e]];
 }
 
 // Fields of the beliefs created by the last assign: Psi_0 = eta log pibar, empty action
@@ -346,8 +399,8 @@ template <class M>
 __device__ void ep_leaf(const EpDesc &P, int e) {
   if (!P.alive[e]) return;
   const float h = M::heuristic(ep_load<M>(P, e), P.log2g, P.h_a0, P.h_b0, P.h_zero != 0);
-  atomicAdd(P.Hs + P.eb[e], (double)h);
-  atomicAdd(P.Nl + P.eb[e], 1ull);
+  agg_add(P.Hs, P.eb[e], (double)h);
+  agg_count(P.Nl, P.eb[e]);
 }
 
 __global__ void k_ep_leaf(EpDesc P) {
@@ -361,19 +414,43 @@ __global__ void k_ep_leaf(EpDesc P) {
   }
 }
 
-__global__ void k_ep_zero_ws(EpDesc P) {
-  const long long n = (long long)P.ctr[0] * P.A;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
-       x += (long long)gridDim.x * blockDim.x)
-    P.Ws[x] = 0.0;
+// Beliefs of depth dep created up to iteration k, as one index space over the ranges.
+struct DepthRanges {
+  int2 r[kMaxDepth];
+  int n, total;
+  __device__ DepthRanges(const EpDesc &P, int dep, int k) : n(0), total(0) {
+    for (int j = 0; j < k && j < kMaxDepth; ++j) {
+      const int2 v = P.ranges[dep * P.K + j];
+      if (v.y > 0) { r[n++] = v; total += v.y; }
+    }
+  }
+  __device__ __forceinline__ int node(int x) const {
+    for (int j = 0; j < n; ++j) {
+      if (x < r[j].y) return r[j].x + x;
+      x -= r[j].y;
+    }
+    return -1;
+  }
+};
+
+// Ws of the action nodes of the beliefs at depth d-1 back to zero.
+__global__ void k_ep_zero_ws(EpDesc P, int d, int k) {
+  const DepthRanges R(P, d - 1, k);
+  const long long tot = (long long)R.total * P.A;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int n = R.node((int)(x / P.A));
+    P.Ws[(long long)n * P.A + (int)(x % P.A)] = 0.0;
+  }
 }
 
 // W of the action nodes above depth d: sum over their children of visits x V (leaves of
 // this iteration, d = D_max, take V = heuristic mean and their leaf visits).
 __global__ void k_ep_scatter(EpDesc P, int d, int dmax) {
-  const int nn = P.ctr[0], A = P.A;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
-    if (P.depth[n] != d) continue;
+  const DepthRanges R(P, d, dmax);
+  const int A = P.A;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < R.total; x += gridDim.x * blockDim.x) {
+    const int n = R.node(x);
     double visits;
     if (d == dmax) {
       visits = (double)P.Nl[n];
@@ -382,34 +459,46 @@ __global__ void k_ep_scatter(EpDesc P, int d, int dmax) {
       visits = 0.0;
       for (int a = 0; a < A; ++a) visits += (double)P.N[(long long)n * A + a];
     }
-    atomicAdd(P.Ws + P.parent_an[n], visits * P.V[n]);
+    agg_add(P.Ws, P.parent_an[n], visits * P.V[n]);
   }
 }
 
-__device__ __forceinline__ double ep_lse(const double *psi, int A, double eta) {
+// eta log sum_a exp(Psi_a / eta): the shifted terms (each <= 1) are exponentiated and the
+// sum (in [1, A]) logged in FP32, the shift kept in FP64 (absolute error ~1e-7 eta, the same
+// on every run).
+__device__ __forceinline__ double ep_lse(const double *psi, int A, double eta, double inv_eta) {
   double m = -CUDART_INF;
-  for (int a = 0; a < A; ++a) m = fmax(m, psi[a] / eta);
+  for (int a = 0; a < A; ++a) m = fmax(m, psi[a] * inv_eta);
   if (!(m > -CUDART_INF)) return -CUDART_INF;
-  double s = 0.0;
-  for (int a = 0; a < A; ++a) s += exp(psi[a] / eta - m);
-  return eta * (m + log(s));
+  float s = 0.f;
+  for (int a = 0; a < A; ++a) s += __expf((float)(psi[a] * inv_eta - m));
+  return eta * (m + (double)__logf(s));
+}
+
+// 1 / n for a visit count: FP32 reciprocal refined by one Newton-Raphson step in FP64
+// (r <- r (2 - n r) doubles the correct bits, ~1e-14 relative).
+__device__ __forceinline__ double ep_recip(unsigned long long cnt) {
+  const double n = (double)cnt;
+  const double r = (double)__frcp_rn((float)n);
+  return r * fma(-n, r, 2.0);
 }
 
 // Preference update of every belief at depth d-1 (Alg. 3: Q, V_curr, Psi, V).
-__global__ void k_ep_update(EpDesc P, int d) {
-  const int nn = P.ctr[0], A = P.A;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
-    if (P.depth[n] != d - 1) continue;
+__global__ void k_ep_update(EpDesc P, int d, int k) {
+  const DepthRanges R(P, d - 1, k);
+  const int A = P.A;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < R.total; x += gridDim.x * blockDim.x) {
+    const int n = R.node(x);
     double q[kMaxActions];
     for (int a = 0; a < A; ++a) {
       const long long an = (long long)n * A + a;
       const unsigned long long cnt = P.N[an];
-      q[a] = cnt ? P.C[an] / (double)cnt + P.gamma * P.Ws[an] / (double)cnt : 0.0;
+      q[a] = cnt ? (P.C[an] + P.gamma * P.Ws[an]) * ep_recip(cnt) : 0.0;
     }
     double *ps = P.psi + (long long)n * A;
-    const double vcur = ep_lse(ps, A, P.eta);
+    const double vcur = ep_lse(ps, A, P.eta, P.inv_eta);
     for (int a = 0; a < A; ++a) ps[a] = ps[a] - vcur + q[a];
-    P.V[n] = ep_lse(ps, A, P.eta);
+    P.V[n] = ep_lse(ps, A, P.eta, P.inv_eta);
     if (n == 0)
       for (int a = 0; a < A; ++a) P.result[2 + a] = q[a];
   }
@@ -477,6 +566,8 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   const size_t o_psi = take(8 * cap * A), o_V = take(8 * cap), o_C = take(8 * cap * A);
   const size_t o_Ws = take(8 * cap * A), o_Hs = take(8 * cap), o_N = take(8 * cap * A), o_Nl = take(8 * cap);
   const size_t o_child = take(4 * cap * A * (O > 0 ? O : 1));
+  const size_t nblk = (size_t)((M + 255) / 256);
+  const size_t o_ranges = take(8 * (size_t)(K + 1) * K), o_pre = take(4 * M), o_bsum = take(4 * nblk);
   const size_t o_ctr = take(64), o_steps = take(8), o_res = take(8 * (2 + 2 * kMaxActions));
   const size_t bytes = off;
   cudaSetDevice(model_device(m));
@@ -494,7 +585,7 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   EpDesc &P = store->d;
   std::memset(&P, 0, sizeof P);
   P.kind = kind; P.A = A; P.O = O; P.M = (int)M; P.Np = in.N; P.cap = (int)cap;
-  P.eta = p.eta; P.gamma = p.gamma;
+  P.eta = p.eta; P.gamma = p.gamma; P.inv_eta = 1.0 / (double)p.eta;
   const double g = p.gamma;
   P.log2g = (float)std::log2(g);
   P.h_a0 = (float)(-1.0 / (1.0 - g));
@@ -564,6 +655,11 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
   P.psi = f64(o_psi); P.V = f64(o_V); P.C = f64(o_C); P.Ws = f64(o_Ws); P.Hs = f64(o_Hs);
   P.N = u64(o_N); P.Nl = u64(o_Nl); P.child = i32(o_child);
   P.ctr = i32(o_ctr); P.steps = u64(o_steps); P.result = f64(o_res);
+  P.K = (int)K;
+  P.ranges = reinterpret_cast<int2 *>(B + o_ranges);
+  P.pre = i32(o_pre);
+  P.bsum = i32(o_bsum);
+  P.nblk = (int)nblk;
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_ctr, 0, 64, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_steps, 0, 8, st);
   if (e != cudaSuccess) return set_error(VOPP_E_CUDA, cudaGetErrorString(e));
@@ -577,14 +673,17 @@ int run_plan_episodes(vopp_model *m, const EpisodeInputs &in, const vopp_episode
     k_ep_start<<<eg, 256, 0, st>>>(P, (unsigned long long)k);
     for (int d = 0; d < k; ++d) {
       k_ep_step<<<eg, 256, 0, st>>>(P, d, (unsigned long long)k);
-      k_ep_assign<<<1, 1024, 0, st>>>(P, d);
+      k_ep_flags<<<eg, 256, 0, st>>>(P);
+      k_ep_scan<<<1, 1024, 0, st>>>(P, d, k);
+      k_ep_publish<<<eg, 256, 0, st>>>(P, d);
+      if (O > 0) k_ep_advance<<<eg, 256, 0, st>>>(P);
       k_ep_init_nodes<<<ng, 256, 0, st>>>(P);
     }
     k_ep_leaf<<<eg, 256, 0, st>>>(P);
     for (int d = k; d >= 1; --d) {
-      k_ep_zero_ws<<<ng, 256, 0, st>>>(P);
+      k_ep_zero_ws<<<ng, 256, 0, st>>>(P, d, k);
       k_ep_scatter<<<ng, 256, 0, st>>>(P, d, k);
-      k_ep_update<<<ng, 256, 0, st>>>(P, d);
+      k_ep_update<<<ng, 256, 0, st>>>(P, d, k);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hctr, P.ctr, sizeof hctr, cudaMemcpyDeviceToHost, st);
