@@ -367,16 +367,17 @@ VOPP_API void vopp_agent_destroy(vopp_agent *agent);
  * (fixed memory plans of real-time loops, HBM held entirely by another allocator, or code
  * that cannot afford an allocation's implicit device synchronisation).  It runs the same
  * SIR kernel as vopp_belief_update, in place, on caller-owned device arrays:
- *   states       device, in/out: NAV2D float[2n] (x then y), GRID/TOY2 int32[n]
+ *   states       device, in/out: NAV2D float[2n] (x then y), GRID/TOY2 int32[n], CROWD
+ *                15 rows of n words (robot x, y, 12 people coordinates, int32 flags)
  *   log_weights  device, in/out: normalised log weights float[n]
- *   obs          host: NAV2D float[2], GRID/TOY2 int32[1]
+ *   obs          host: NAV2D float[2], GRID/TOY2/CROWD int32[1]
  *   seed, t      the Philox key and time step (counter) of this update
  *   cuda_stream  stream to run on (cudaStream_t as an integer, 0 = legacy default)
  *   ancestors    device int32[n] receiving the ancestor indices, or NULL
  *   ess_out, resampled_out   host, may be NULL
  * Its working memory is one static device array of about 1.5 MB compiled into the library
  * (every GPU that loads the library holds it until the process exits), so n is limited to
- * 65536; larger n returns VOPP_E_INVALID.  The call issues no cudaMalloc / cudaFree and no
+ * 65536 (CROWD, with 60-byte states: 20,000); larger n returns VOPP_E_INVALID.  The call issues no cudaMalloc / cudaFree and no
  * allocating library call.  The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture.  All calls share the one array, which keeps the previous call's contents, so

@@ -8,6 +8,7 @@
 // arrays the caller owns, and takes the kernel's working memory (propagated particles,
 // the FP64 CDF, ancestors, the status word) from one fixed device array compiled into the
 // library instead of from an allocator.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -18,9 +19,10 @@ namespace {
 
 // Largest particle count the static scratch serves, and the scratch itself: per particle
 // 8 B propagated state, 4 B log weight, 8 B CDF entry, 4 B ancestor; plus the status word.
+// CROWD's 60-byte states fit fewer particles (kNoAllocScratchBytes / 76, about 20,000).
 constexpr int kNoAllocMaxParticles = 65536;
 constexpr size_t kNoAllocScratchBytes =
-    (size_t)kNoAllocMaxParticles * (8 + 4 + 8 + 4) + 256;
+    (size_t)kNoAllocMaxParticles * (8 + 4 + 8 + 4) + 256 * 5;
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -62,11 +64,17 @@ extern "C" VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void
                                                    double *ess_out, int32_t *resampled_out) {
   if (!model || !states || !log_weights || !obs)
     return vopp::set_error(VOPP_E_INVALID, "NULL argument");
-  if (n < 1 || n > kNoAllocMaxParticles)
-    return vopp::set_error(VOPP_E_INVALID,
-                           "n outside [1, 65536], the capacity of the static scratch");
   const int kind = vopp::model_kind(model);
-  const int A = kind == VOPP_NAV2D ? 4 : (kind == VOPP_GRID ? 13 : 2);
+  // 32-bit words per particle state (the root layout): NAV2D 2, CROWD 15, GRID / TOY2 1
+  const size_t words = kind == VOPP_NAV2D ? 2 : (kind == VOPP_CROWD ? 15 : 1);
+  const size_t per = 4 * words + 4 + 8 + 4;
+  const int nmax = (int)std::min<size_t>((size_t)kNoAllocMaxParticles,
+                                         (kNoAllocScratchBytes - 256 * 5) / per);
+  if (n < 1 || n > nmax)
+    return vopp::set_error(VOPP_E_INVALID,
+                           "n outside [1, the capacity of the static scratch] (65536 particles; "
+                           "CROWD: 20,000)");
+  const int A = kind == VOPP_NAV2D ? 4 : (kind == VOPP_GRID ? 13 : (kind == VOPP_CROWD ? 5 : 2));
   if (action < 0 || action >= A) return vopp::set_error(VOPP_E_INVALID, "action out of range");
   const int device = vopp::model_device(model);
   void *base = nullptr;
@@ -78,7 +86,7 @@ extern "C" VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void
   // carve the static array: propagated states | log weights | CDF | ancestors | status
   char *p = static_cast<char *>(base);
   const size_t N = (size_t)n;
-  char *t_states = p;           p += up256(8 * N);
+  char *t_states = p;           p += up256(4 * words * N);
   float *t_lw = reinterpret_cast<float *>(p);  p += up256(4 * N);
   double *cdf = reinterpret_cast<double *>(p); p += up256(8 * N);
   int *anc = reinterpret_cast<int *>(p);       p += up256(4 * N);
@@ -99,6 +107,12 @@ extern "C" VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void
     const float *o = static_cast<const float *>(obs);
     B.obs_f[0] = o[0];
     B.obs_f[1] = o[1];
+  } else if (kind == VOPP_CROWD) {   // rows: x, y, 12 people coordinates, flags
+    float *st = static_cast<float *>(states);
+    float *tst = reinterpret_cast<float *>(t_states);
+    B.x = st; B.y = st + n; B.pf = st + 2 * N; B.s = reinterpret_cast<int *>(st + 14 * N);
+    B.tx = tst; B.ty = tst + n; B.tpf = tst + 2 * N; B.ts = reinterpret_cast<int *>(tst + 14 * N);
+    B.obs_i = *static_cast<const int32_t *>(obs);
   } else {
     B.s = static_cast<int *>(states);
     B.ts = reinterpret_cast<int *>(t_states);

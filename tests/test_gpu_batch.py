@@ -199,3 +199,41 @@ def test_autotune_picks_a_configuration_without_changing_results():
             V.vopp_model_destroy(m)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_batch_with_crowd_plans_equals_individual_plans_and_oracle():
+    """CROWD plans (their own leaf kernel and shared-memory class) batched with the other
+    models: every result equals the plan run alone bit for bit and the oracle within the
+    tolerance."""
+    from paper_2510_27191_b300 import vopp as V
+    specs = [Spec(WL.CROWD, 64, 2, 2, eta=0.8, gamma=0.97, seed=31, root_seed=1),
+             Spec(WL.NAV2D, 300, 2, 3, eta=0.6, seed=32, root_seed=2),
+             Spec(WL.CROWD, 150, 1, 4, eta=1.2, gamma=0.97, seed=33, root_seed=3, weights="random"),
+             Spec(WL.GRID, 200, 2, 2, seed=34, root_seed=4),
+             Spec(WL.CROWD, 33, 3, 1, eta=0.5, gamma=0.97, seed=35, root_seed=5)]
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    models = {}
+    try:
+        reqs = []
+        for s in specs:
+            if s.kind not in models:
+                models[s.kind] = V.vopp_create_model(ctx, V.make_desc(s.kind, rock_x=s.rock_x,
+                                                                      rock_y=s.rock_y))
+            w = s.root.get("w")
+            reqs.append(dict(model=models[s.kind], states=s.states(),
+                             weights=None if w is None else np.asarray(w, np.float32), n=s.N,
+                             depth=s.D, width=s.W, eta=s.eta, gamma=s.gamma, seed=s.seed, A=s.A))
+        outs, keep = V.vopp_plan_batch(ctx, reqs)
+        for i, (r, s) in enumerate(zip(reqs, specs)):
+            alone = V.vopp_plan(r["model"], r["states"], r["weights"], s.N, s.D, s.W, s.eta,
+                                s.gamma, None, s.seed)
+            assert outs[i]["q"].tolist() == alone["q"].tolist(), i
+            orc = s.run_oracle(outputs=False)
+            assert orc["status"] == O.OK
+            assert_close(outs[i]["q"], orc["q_root"], f"plan {i} root Q")
+            assert action_agrees(outs[i], orc, s)
+        del keep
+    finally:
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)

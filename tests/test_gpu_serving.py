@@ -180,3 +180,42 @@ def test_tagged_agents_and_sampled_requests_replayed_by_the_oracle():
         for m in models.values():
             V.vopp_model_destroy(m)
         V.vopp_ctx_destroy(ctx)
+
+
+def test_served_crowd_requests_equal_alone():
+    """CROWD requests and agents through the serving loop, mixed with navigation requests."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    mc = V.vopp_create_model(ctx, V.make_desc(V.VOPP_CROWD))
+    mn = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
+    srv = V.vopp_server_create(ctx, max_batch=8, n_slots=2)
+    try:
+        V.vopp_server_set_paused(srv, True)
+        sub = []
+        for i in range(6):
+            if i % 2 == 0:
+                st = WL.pack_crowd_states(WL.crowd_root(96 + 16 * i, 20 + i))
+                n, m, A = 96 + 16 * i, mc, 5
+            else:
+                x, y, _ = WL.nav_root(128, 20 + i)
+                st, n, m, A = np.concatenate([x, y]).astype(np.float32), 128, mn, 4
+            if i == 4:
+                g = V.vopp_agent_create(mc, st, None, n, 7)
+                t = V.vopp_submit_agent(srv, g, 2, 2, 1.0, 0.97, 100 + i)
+            else:
+                g = None
+                t = V.vopp_submit(srv, m, st, None, n, 2, 2, 1.0, 0.97, 100 + i)
+            sub.append((t, m, st, n, A, g, 100 + i))
+        V.vopp_server_set_paused(srv, False)
+        for t, m, st, n, A, g, seed in sub:
+            res, _ = V.vopp_wait(srv, t, A, 20.0)
+            alone = V.vopp_plan(m, st, None, n, 2, 2, 1.0, 0.97, None, seed)
+            assert res["q"].tolist() == alone["q"].tolist() and res["action"] == alone["action"]
+            if g is not None:
+                V.vopp_agent_destroy(g)
+    finally:
+        V.vopp_server_destroy(srv)
+        V.vopp_model_destroy(mc)
+        V.vopp_model_destroy(mn)
+        V.vopp_ctx_destroy(ctx)
+

@@ -76,3 +76,34 @@ def test_noalloc_update_matches_agent_update_twice(kind):
         V.vopp_model_destroy(model)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_no_alloc_crowd_update_equals_agent_update():
+    """CROWD particles (15 words each) through the allocation-free update equal the agent's
+    update from the same particles, seed and step; beyond the scratch's CROWD capacity the
+    call is refused."""
+    import torch
+    from paper_2510_27191_b300 import vopp as V
+    from paper_2510_27191_b300 import workloads as WL
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        m = V.vopp_create_model(ctx, V.make_desc(V.VOPP_CROWD))
+        N = 700
+        st = WL.pack_crowd_states(WL.crowd_root(N, 3, robot=(25.0, 3.0)))
+        g = V.vopp_agent_create(m, st, None, N, 21)
+        V.vopp_belief_update(g, 4, 0b000101, V.VOPP_CROWD)
+        ga, glw, _ = V.vopp_agent_get_particles(g, V.VOPP_CROWD)
+        dst = torch.from_numpy(st.copy()).cuda()
+        dlw = torch.full((N,), -float(np.log(N)), dtype=torch.float32, device="cuda")
+        V.vopp_belief_update_noalloc(m, dst, dlw, 4, 0b000101, 21, 0, V.VOPP_CROWD)
+        assert dst.cpu().numpy().tolist() == ga.tolist()
+        assert dlw.cpu().numpy().tolist() == glw.tolist()
+        big = torch.zeros(15 * 30000, dtype=torch.float32, device="cuda")
+        bw = torch.zeros(30000, dtype=torch.float32, device="cuda")
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_belief_update_noalloc(m, big, bw, 0, 0, 1, 0, V.VOPP_CROWD)
+        assert e.value.code == V.VOPP_E_INVALID
+        V.vopp_agent_destroy(g)
+        V.vopp_model_destroy(m)
+    finally:
+        V.vopp_ctx_destroy(ctx)
