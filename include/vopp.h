@@ -101,7 +101,7 @@ extern "C" {
 #define VOPP_FIELD_OBS 5    /* float  observation[child][2] levels 1..D (FULL)             */
 #define VOPP_FIELD_PX 6     /* float  NAV2D x[node][N]      materialised levels            */
 #define VOPP_FIELD_PY 7     /* float  NAV2D y[node][N]      materialised levels            */
-#define VOPP_FIELD_PS 8     /* int32  GRID/TOY2 s[node][N]  materialised levels            */
+#define VOPP_FIELD_PS 8     /* int32  GRID/TOY2 s, CROWD flags [node][N], materialised     */
 #define VOPP_FIELD_PLW 9    /* float  log weight[node][N]   materialised levels            */
 #define VOPP_FIELD_MU 10    /* float  weighted mean particle [node][2] (VOPP_PI_NAV_DIST) */
 #define VOPP_FIELD_PSI 11   /* float  Psi[node][A] persistent preferences, levels 0..D-1,
@@ -158,7 +158,8 @@ typedef struct {
 /* One plan of a batch: root particles (host or device per ptr_flags) plus parameters. */
 typedef struct {
   vopp_model *model;
-  const void *root_states;  /* NAV2D: float[2N] (x[0..N-1] then y[0..N-1]); GRID/TOY2: int32[N] */
+  const void *root_states;  /* NAV2D: float[2N] (x[0..N-1] then y[0..N-1]); GRID/TOY2: int32[N];
+                               CROWD: 15 rows of N words (see VOPP_CROWD)                   */
   const float *root_weights;/* [N] or NULL for uniform                                    */
   int32_t n_particles;
   uint32_t ptr_flags;
@@ -214,7 +215,8 @@ VOPP_API void vopp_model_destroy(vopp_model *model);
 VOPP_API int vopp_model_num_actions(const vopp_model *model);
 
 /* ---- one plan (Alg. 1 with one full-width search and one backup) ---------------------- */
-/* root_states: NAV2D float[2N] (x then y), GRID/TOY2 int32[N]; root_weights: [N] or NULL.
+/* root_states: NAV2D float[2N] (x then y), GRID/TOY2 int32[N], CROWD 15 rows of N words
+ * (robot x, y, 12 people coordinates, int32 flags); root_weights: [N] or NULL.
  * Weights must be >= 0; particles that are terminal at the root get weight 0; zero total
  * weight returns VOPP_E_DEGENERATE.  pi_bar: [A] host weights or NULL (model's policy).
  * Errors: VOPP_E_INVALID for depth < 0 or > VOPP_MAX_DEPTH, width < 1, N < 1 or
@@ -313,7 +315,7 @@ VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *
                                      vopp_plan_result *out, int32_t *depth_reached);
 /* tau(b, a, o): propagate every particle under `action` (Philox purpose 3, time step t of
  * the agent), reweight by Z(obs | s', a), resample systematically when ESS < N/2.  obs is a
- * host pointer: NAV2D float[2], GRID/TOY2 int32[1].  On VOPP_E_DEGENERATE (every particle
+ * host pointer: NAV2D float[2], GRID/TOY2/CROWD int32[1].  On VOPP_E_DEGENERATE (every particle
  * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
 VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out);
@@ -322,11 +324,12 @@ VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *o
  * model's own transition and observation processes with random numbers of its own (Philox
  * key = seed; purpose 5 transition words 0,1 and purpose 6 observation words 0,1; node word
  * = the environment's step count t, starting at 0).  state: host NAV2D float[2] (x, y),
- * GRID/TOY2 int32[1]; copied at creation.  Paper: Alg. 1 "execute action, perceive
+ * GRID/TOY2 int32[1], CROWD 15 words (one particle of the root layout); copied at
+ * creation.  Paper: Alg. 1 "execute action, perceive
  * observation"; the paper's environments are simulators of the same models. */
 typedef struct vopp_env vopp_env;
 VOPP_API int vopp_env_create(vopp_model *model, const void *state, uint64_t seed, vopp_env **out);
-/* One step under `action`: obs receives the observation (host NAV2D float[2], GRID/TOY2
+/* One step under `action`: obs receives the observation (host NAV2D float[2], GRID/TOY2/CROWD
  * int32[1]), reward and terminal (1 when the new state is terminal; terminal states are
  * absorbing with reward 0) may be NULL.  VOPP_E_INVALID for an action outside [0, A). */
 VOPP_API int vopp_env_step(vopp_env *env, int32_t action, void *obs, float *reward, int32_t *terminal);
@@ -355,7 +358,8 @@ VOPP_API int vopp_run_episode(vopp_agent *agent, vopp_env *env, const vopp_plan_
                               int32_t max_steps, int32_t anytime, double budget_s,
                               vopp_episode_result *out, int32_t *actions, float *rewards);
 
-/* Copy the agent's particles (NAV2D x then y as float[2N]; GRID/TOY2 int32[N]) and
+/* Copy the agent's particles (NAV2D x then y as float[2N]; GRID/TOY2 int32[N]; CROWD 15 rows
+ * of N words) and
  * normalised log weights out; ancestors (int32[N], may be NULL) of the last update. */
 VOPP_API int vopp_agent_get_particles(vopp_agent *agent, void *states, float *log_weights,
                              int32_t *ancestors, uint32_t ptr_flags);

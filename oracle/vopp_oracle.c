@@ -3,7 +3,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls this file;
  * only the tests, the package's smoke check and the benchmark's CPU-baseline leg do.  It
- * shares no source with the CUDA library: the Philox generator, the three models, the
+ * shares no source with the CUDA library: the Philox generator, the four models, the
  * tree recursion and the backup are all written out again here, in double precision, as
  * plain loops in the order the paper gives them.
  *
@@ -709,7 +709,8 @@ void orc_level_offsets(int A, int W, int D, int P, long long *off) {
 
 /*
  * One plan (Alg. 1 with a single full-width search episode and one backup pass).
- * root_x/root_y: NAV2D particle coordinates; root_s: GRID/TOY2 states; root_w: weights or
+ * root_x/root_y: NAV2D particle coordinates (CROWD robot); root_s: GRID/TOY2 states (CROWD
+ * flags; people in io->root_pf); root_w: weights or
  * NULL for uniform.  Returns ORC_OK, ORC_E_INVALID, ORC_E_NOMEM or ORC_E_DEGENERATE.
  */
 int orc_plan(const orc_model *m, const double *root_x, const double *root_y,

@@ -297,7 +297,8 @@ def _result_dict(r: vopp_plan_result, A: int) -> dict:
 
 def vopp_plan(model: int, root_states, root_weights, n_particles: int, depth: int, width: int,
               eta: float, gamma: float, pi_bar=None, seed: int = 0, ptr_flags: int | None = None) -> dict:
-    """root_states: NAV2D float32[2N] (x then y), GRID/TOY2 int32[N]; numpy (host) or torch
+    """root_states: NAV2D float32[2N] (x then y), GRID/TOY2 int32[N], CROWD the 15-row layout
+    (workloads.pack_crowd_states); numpy (host) or torch
     CUDA tensors (device).  Returns the vopp_plan_result as a dict."""
     sp, sdev, keep1 = _addr(root_states)
     wp, wdev, keep2 = _addr(root_weights)
