@@ -1548,11 +1548,15 @@ int vopp_agent_get_particles(vopp_agent *g, void *states, float *log_weights, in
 // Requests wait in a FIFO.  A worker thread forms a batch from the head of the queue
 // whenever a slot is free and the HBM budget admits it, builds the batch's launch sequence
 // on the slot's own stream (arena from the device's stream-ordered pool, released on the
-// same stream after the results are copied back) and moves on; a host callback at the end
-// of the slot's stream wakes the worker, which posts the results.  Batches on different
-// slots run concurrently on the device, and requests that arrive while others run join the
-// next batch.  Each plan's random numbers are keyed by its own seed, so a plan's result does
-// not depend on which batch it joined.
+// same stream after the results are copied back) and records an event after it.  While any
+// batch is in flight the worker polls the slots' events and the queue (yielding the CPU
+// between polls), so a finished batch is posted and a new request is started within
+// microseconds; with nothing in flight it sleeps on a condition variable.  The server mutex
+// guards only the queue, the results and the counters: the worker releases it around its
+// CUDA calls, so callers that submit or collect are never held up by a launch.  Batches on
+// different slots run concurrently on the device, and requests that arrive while others run
+// join the next batch.  Each plan's random numbers are keyed by its own seed, so a plan's
+// result does not depend on which batch it joined.
 // ---------------------------------------------------------------------------------------
 namespace {
 
@@ -1569,15 +1573,15 @@ struct ServerReq {
   double t_submit = 0.0;
 };
 
+// Slot state is touched by the worker thread only.
 struct ServerSlot {
   Slot slot;
+  cudaEvent_t done_ev = nullptr;   // recorded after the batch's last operation
   char *arena = nullptr;
   size_t arena_bytes = 0;
   std::vector<ServerReq> reqs;
   std::vector<Job> jobs;
   bool busy = false;
-  std::atomic<int> complete{0};
-  struct vopp_server *owner = nullptr;
 };
 
 struct Done {
@@ -1608,28 +1612,43 @@ struct vopp_server {
 
 namespace {
 
-// Runs on a CUDA callback thread when a slot's stream reaches the end of its batch.  It
-// takes no lock and makes no CUDA call: the worker may be inside a CUDA call that waits for
-// this very stream while holding the server mutex.  The worker's waits are bounded, so a
-// notification that races with its predicate check only delays it by one wait period.
-void CUDART_CB slot_complete(void *arg) {
-  ServerSlot *s = static_cast<ServerSlot *>(arg);
-  s->complete.store(1);
-  s->owner->cv_work.notify_one();
+// Batches of at most this many particle-steps (about a fifth of a millisecond of leaf work
+// for the navigation model) count as small for the choice of stream priority.
+constexpr double kSmallBatchSteps = 3.0e7;
+
+vopp_plan_result failed_result() {
+  vopp_plan_result z;
+  std::memset(&z, 0, sizeof z);
+  z.action = -1;
+  return z;
 }
 
-// Harvest a finished slot (worker thread, lock held).
-void harvest(vopp_server *srv, ServerSlot *s) {
-  const int n = (int)s->jobs.size();
-  std::vector<vopp_plan_result> outs(n);
-  std::vector<int> st(n);
-  collect_results(srv->c, s->slot, s->jobs, outs.data(), st.data(), false);
+// Post a status for every request of a batch (lock held).
+void post_failure(vopp_server *srv, std::vector<ServerReq> &batch, int rc) {
   const double t = now_s();
-  for (int i = 0; i < n; ++i) {
-    srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
-    srv->completion_order.push_back(s->reqs[i].ticket);
-    srv->stats.completed += 1;
-    srv->stats.particle_steps += outs[i].particle_steps;
+  for (auto &r : batch) {
+    srv->done[r.ticket] = Done{rc, failed_result(), r.t_submit, t};
+    srv->completion_order.push_back(r.ticket);
+  }
+}
+
+// Post the results of a finished slot (lock held).  The results are in the slot's pinned
+// mirror: the stream copied them back before the slot's event.
+void harvest(vopp_server *srv, ServerSlot *s, bool ok) {
+  const int n = (int)s->jobs.size();
+  if (ok) {
+    std::vector<vopp_plan_result> outs(n);
+    std::vector<int> st(n);
+    collect_results(srv->c, s->slot, s->jobs, outs.data(), st.data(), false);
+    const double t = now_s();
+    for (int i = 0; i < n; ++i) {
+      srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
+      srv->completion_order.push_back(s->reqs[i].ticket);
+      srv->stats.completed += 1;
+      srv->stats.particle_steps += outs[i].particle_steps;
+    }
+  } else {
+    post_failure(srv, s->reqs, VOPP_E_CUDA);
   }
   srv->in_flight -= s->arena_bytes;
   s->arena = nullptr;
@@ -1637,22 +1656,18 @@ void harvest(vopp_server *srv, ServerSlot *s) {
   s->reqs.clear();
   s->jobs.clear();
   s->busy = false;
-  s->complete.store(0);
 }
 
-// Start a batch on a free slot from the head of the queue (worker thread, lock held).
-// Returns false when nothing could be started.
-bool start_batch(vopp_server *srv, ServerSlot *s) {
+// Take a batch from the head of the queue within the budget and reserve its bytes (lock
+// held).  A request that could never fit is refused at once.
+std::vector<ServerReq> take_batch(vopp_server *srv, size_t *bytes_out) {
   std::vector<ServerReq> batch;
   size_t bytes = 0;
   while (!srv->pending.empty() && (int)batch.size() < srv->max_batch) {
     ServerReq &r = srv->pending.front();
     if (srv->in_flight + bytes + r.bytes > srv->budget) {
       if (batch.empty() && srv->in_flight == 0) {   // can never fit: refuse it
-        vopp_plan_result z;
-        std::memset(&z, 0, sizeof z);
-        z.action = -1;
-        srv->done[r.ticket] = Done{VOPP_E_BUDGET, z, r.t_submit, now_s()};
+        srv->done[r.ticket] = Done{VOPP_E_BUDGET, failed_result(), r.t_submit, now_s()};
         srv->completion_order.push_back(r.ticket);
         srv->stats.rejected += 1;
         srv->pending.pop_front();
@@ -1664,7 +1679,13 @@ bool start_batch(vopp_server *srv, ServerSlot *s) {
     batch.push_back(std::move(r));
     srv->pending.pop_front();
   }
-  if (batch.empty()) return false;
+  srv->in_flight += bytes;
+  *bytes_out = bytes;
+  return batch;
+}
+
+// Enqueue a batch on a slot's stream (worker thread, lock NOT held).
+int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch) {
   std::vector<Job> jobs;
   for (auto &r : batch) {
     jobs.push_back(r.job);
@@ -1679,77 +1700,127 @@ bool start_batch(vopp_server *srv, ServerSlot *s) {
   int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false, nullptr) : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
     if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
-        cudaLaunchHostFunc(s->slot.stream, slot_complete, s) != cudaSuccess)
+        cudaEventRecord(s->done_ev, s->slot.stream) != cudaSuccess)
       rc = VOPP_E_CUDA;
   }
-  if (rc != VOPP_OK) {   // post the failure to every request of the batch
+  if (rc != VOPP_OK) {
     cudaGetLastError();
     if (arena) cudaFreeAsync(arena, s->slot.stream);
     cudaStreamSynchronize(s->slot.stream);
-    vopp_plan_result z;
-    std::memset(&z, 0, sizeof z);
-    z.action = -1;
-    for (auto &r : batch) {
-      srv->done[r.ticket] = Done{rc, z, r.t_submit, now_s()};
-      srv->completion_order.push_back(r.ticket);
-    }
-    srv->cv_done.notify_all();
-    return true;
+    return rc;
   }
   s->arena = arena;
-  s->arena_bytes = arena_bytes;
-  s->reqs = std::move(batch);
   s->jobs = std::move(jobs);
-  s->busy = true;
-  srv->in_flight += arena_bytes;
-  srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
-  srv->stats.batches += 1;
-  srv->stats.batched_plans += s->reqs.size();
-  srv->stats.max_batch_seen = std::max<uint64_t>(srv->stats.max_batch_seen, s->reqs.size());
-  return true;
+  return VOPP_OK;
 }
+
+// Particle-steps of a batch (the leaf work dominates a plan's time).
+double batch_steps(const std::vector<ServerReq> &batch) {
+  double t = 0.0;
+  for (const auto &r : batch) {
+    const PlanShape &sh = r.job.shape;
+    double lvl = (double)sh.N;
+    for (int l = 1; l <= sh.D; ++l) { lvl *= sh.AW; t += lvl; }
+  }
+  return t;
+}
+
+// A free slot for a batch, or null.  Slot 0's stream has the device's highest priority:
+// small batches take it first (their CTAs are then dispatched ahead of the queued CTAs of
+// large plans already running on other slots), large batches take it last.
+ServerSlot *pick_slot(vopp_server *srv, const std::vector<ServerReq> &batch) {
+  const int n = (int)srv->slots.size();
+  const bool small = batch_steps(batch) <= kSmallBatchSteps;
+  for (int i = 0; i < n; ++i) {
+    ServerSlot *s = srv->slots[small ? i : n - 1 - i];
+    if (!s->busy) return s;
+  }
+  return nullptr;
+}
+
+// Completion state of a busy slot: 1 finished, 0 running, -1 failed.
+int slot_state(ServerSlot *s) {
+  const cudaError_t q = cudaEventQuery(s->done_ev);
+  if (q == cudaSuccess) return 1;
+  if (q == cudaErrorNotReady) return 0;
+  cudaGetLastError();
+  return -1;
+}
+
+// After the last batch finishes the worker keeps polling this long before it sleeps, so
+// that a request arriving soon after starts without a thread wake-up.
+constexpr double kSpinIdle = 250e-6;
 
 void worker_main(vopp_server *srv) {
   cudaSetDevice(srv->c->device);
   std::unique_lock<std::mutex> lock(srv->mu);
+  double idle_since = now_s();
   for (;;) {
-    bool harvested = false;
-    for (auto *s : srv->slots)
-      if (s->busy && s->complete.load()) { harvest(srv, s); harvested = true; }
-    if (harvested) srv->cv_done.notify_all();
+    bool posted = false;
     for (auto *s : srv->slots) {
-      if (srv->pending.empty() || (srv->paused && !srv->stop)) break;
-      if (!s->busy) start_batch(srv, s);
+      if (!s->busy) continue;
+      const int st = slot_state(s);
+      if (st != 0) { harvest(srv, s, st > 0); posted = true; }
     }
+    for (;;) {
+      if (srv->pending.empty() || (srv->paused && !srv->stop)) break;
+      bool any_free = false;
+      for (auto *q : srv->slots) any_free |= !q->busy;
+      if (!any_free) break;
+      const size_t refused_before = srv->completion_order.size();
+      size_t bytes = 0;
+      std::vector<ServerReq> batch = take_batch(srv, &bytes);
+      posted |= srv->completion_order.size() != refused_before;
+      if (batch.empty()) break;                 // the head waits for budget to free up
+      ServerSlot *s = pick_slot(srv, batch);
+      s->busy = true;
+      lock.unlock();
+      const int rc = launch_batch(srv, s, batch);
+      lock.lock();
+      if (rc != VOPP_OK) {                      // post the failure to every request
+        srv->in_flight -= bytes;
+        post_failure(srv, batch, rc);
+        s->busy = false;
+        posted = true;
+        continue;
+      }
+      s->arena_bytes = bytes;                   // the reservation is released at harvest
+      s->reqs = std::move(batch);
+      srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
+      srv->stats.batches += 1;
+      srv->stats.batched_plans += s->reqs.size();
+      srv->stats.max_batch_seen = std::max<uint64_t>(srv->stats.max_batch_seen, s->reqs.size());
+    }
+    if (posted) srv->cv_done.notify_all();
     int busy = 0;
     for (auto *s : srv->slots) busy += s->busy;
     if (srv->stop) {
       if (busy == 0 && srv->pending.empty()) break;
-      // shutting down: drain the busy slots directly rather than waiting for callbacks
+      // shutting down: wait (bounded) for the busy slots rather than polling at full rate
       for (auto *s : srv->slots) {
         if (!s->busy) continue;
         lock.unlock();
-        cudaStreamSynchronize(s->slot.stream);
-        lock.lock();
-        for (int spins = 0; !s->complete.load() && spins < 200000; ++spins) {   // <= ~10 s
-          lock.unlock();   // the callback follows the stream's last operation
+        int st = 0;
+        for (int spins = 0; (st = slot_state(s)) == 0 && spins < 200000; ++spins)   // <= ~10 s
           std::this_thread::sleep_for(std::chrono::microseconds(50));
-          lock.lock();
-        }
-        if (!s->complete.load()) {   // callback never ran: give up on this slot's batch
-          srv->worker_error = VOPP_E_TIMEOUT;
-          s->complete.store(1);
-        }
+        lock.lock();
+        if (st == 0) srv->worker_error = VOPP_E_TIMEOUT;   // gave up on this batch
+        harvest(srv, s, st > 0);
       }
+      srv->cv_done.notify_all();
       continue;
     }
-    srv->cv_work.wait_for(lock, std::chrono::microseconds(200), [&] {
-      if (srv->stop) return true;
-      for (auto *s : srv->slots) if (s->busy && s->complete.load()) return true;
-      if (!srv->pending.empty() && !srv->paused)
-        for (auto *s : srv->slots) if (!s->busy) return true;
-      return false;
-    });
+    if (busy || now_s() - idle_since < kSpinIdle) {
+      // batches in flight, or only just idle: poll again after letting callers in
+      lock.unlock();
+      std::this_thread::yield();
+      lock.lock();
+    } else {
+      srv->cv_work.wait_for(lock, std::chrono::milliseconds(1), [&] {
+        return srv->stop || (!srv->pending.empty() && !srv->paused);
+      });
+    }
+    if (busy) idle_since = now_s();
   }
 }
 
@@ -1788,14 +1859,27 @@ int vopp_server_create(vopp_ctx *c, int32_t max_batch, int32_t n_slots, size_t h
   }
   for (int i = 0; i < n_slots; ++i) {
     ServerSlot *s = new (std::nothrow) ServerSlot;
-    if (!s || cudaStreamCreateWithFlags(&s->slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio_lo = 0, prio_hi = 0;   // numerically lower = higher priority
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (!s || cudaStreamCreateWithPriority(&s->slot.stream, cudaStreamNonBlocking,
+                                           i == 0 ? prio_hi : prio_lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess ||
         ensure_meta(s->slot, 1 << 20) != VOPP_OK) {
+      if (s) {
+        if (s->done_ev) cudaEventDestroy(s->done_ev);
+        free_slot(s->slot);
+        if (s->slot.stream) cudaStreamDestroy(s->slot.stream);
+      }
       delete s;
-      for (auto *q : srv->slots) { free_slot(q->slot); cudaStreamDestroy(q->slot.stream); delete q; }
+      for (auto *q : srv->slots) {
+        free_slot(q->slot);
+        cudaEventDestroy(q->done_ev);
+        cudaStreamDestroy(q->slot.stream);
+        delete q;
+      }
       delete srv;
       return fail(VOPP_E_NOMEM, "server slot");
     }
-    s->owner = srv;
     srv->slots.push_back(s);
   }
   srv->worker = std::thread(worker_main, srv);
@@ -1814,6 +1898,7 @@ void vopp_server_destroy(vopp_server *srv) {
   for (auto *s : srv->slots) {
     cudaStreamSynchronize(s->slot.stream);
     free_slot(s->slot);
+    cudaEventDestroy(s->done_ev);
     cudaStreamDestroy(s->slot.stream);
     delete s;
   }

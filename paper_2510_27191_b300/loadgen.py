@@ -129,61 +129,80 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
 
     t0 = time.perf_counter()
     k = 0
-    while True:
-        now = time.perf_counter() - t0
-        while k < n_req and arrivals[k] <= now:
-            queues[who[k]].append(arrivals[k])
-            k += 1
-        if mode == "served":
-            for i in map(int, np.flatnonzero(~busy)):
-                if queues[i]:
-                    inflight[issue(i)] = (i, queues[i].pop(0))
+    if mode == "served":
+        # event-driven: a request is submitted the moment it arrives (or, if its agent has a
+        # plan in flight, the moment that plan's belief update is done); between events the
+        # loop polls for completions and arrivals
+        def finish(t, rc, res):
+            if rc not in (V.VOPP_OK, V.VOPP_E_DEGENERATE):
+                V.check(rc)
+            i, arr = inflight.pop(t)
+            lat.append(time.perf_counter() - t0 - arr)
+            nonlocal_steps[0] += res["particle_steps"] if res is not None else 0
+            if res is None:
+                reset(i)
+            else:
+                after_plan(i, res)
+            busy[i] = False
+            if queues[i]:
+                inflight[issue(i)] = (i, queues[i].pop(0))
+                busy[i] = True
+
+        nonlocal_steps = [0]
+        while True:
+            now = time.perf_counter() - t0
+            while k < n_req and arrivals[k] <= now:
+                i = who[k]
+                if busy[i]:
+                    queues[i].append(arrivals[k])
+                else:
+                    inflight[issue(i)] = (i, arrivals[k])
                     busy[i] = True
-            done = []
-            while inflight:
-                got = V.vopp_wait_any(srv, 0.0 if (k < n_req or done) else 0.0005)
+                k += 1
+            if k >= n_req and not inflight:
+                break
+            if now > seconds * drain_factor:
+                break                                  # overloaded: stop draining
+            # poll: a completion or an arrival is picked up within microseconds (a blocking
+            # wait would add a thread wake-up to every request)
+            got = V.vopp_wait_any(srv, 0.0) if inflight else None
+            if got is None:
+                if not inflight and k < n_req:
+                    while time.perf_counter() - t0 < arrivals[k]:
+                        pass                           # idle until the next arrival
+                continue
+            finish(got[0], got[1], got[2])
+            while inflight:                            # everything else already finished
+                got = V.vopp_wait_any(srv, 0.0)
                 if got is None:
                     break
-                t, rc, res, _ = got
-                if rc not in (V.VOPP_OK, V.VOPP_E_DEGENERATE):
-                    V.check(rc)
-                i, arr = inflight[t]
-                done.append((t, i, arr, res))
-            for t, i, arr, res in done:
-                del inflight[t]
-                lat.append(time.perf_counter() - t0 - arr)
-                if res is None:
-                    reset(i)
-                else:
-                    steps_done += res["particle_steps"]
-                    after_plan(i, res)
-                busy[i] = False
-        else:
-            # plain path: the oldest waiting request runs alone, synchronously
-            cand = [(q[0], i) for i, q in enumerate(queues) if q]
-            if cand:
-                arr, i = min(cand)
-                i = int(i)
-                queues[i].pop(0)
-                ps = specs[i]
-                plan_count[i] += 1
-                try:
-                    res = V.vopp_agent_plan(agents[i], models[ps.kind], ps.D, ps.W, ps.eta,
-                                            ps.gamma, (i + 1) * 7919 + int(plan_count[i]))
-                except V.VoppError as e:
-                    if e.code != V.VOPP_E_DEGENERATE:
-                        raise
-                    res = None
-                lat.append(time.perf_counter() - t0 - arr)
-                if res is None:
-                    reset(i)
-                else:
-                    steps_done += res["particle_steps"]
-                    after_plan(i, res)
-        if k >= n_req and not inflight and not any(queues):
-            break
-        if time.perf_counter() - t0 > seconds * drain_factor:
-            break                                      # overloaded: stop draining
+                finish(got[0], got[1], got[2])
+        steps_done = nonlocal_steps[0]
+    else:
+        # plain path: requests run alone, synchronously, in arrival order (an agent's earlier
+        # request has always finished, with its belief update, before its next one starts)
+        while k < n_req:
+            while time.perf_counter() - t0 < arrivals[k]:
+                pass                                   # idle until the next arrival
+            i, arr = who[k], arrivals[k]
+            k += 1
+            ps = specs[i]
+            plan_count[i] += 1
+            try:
+                res = V.vopp_agent_plan(agents[i], models[ps.kind], ps.D, ps.W, ps.eta,
+                                        ps.gamma, (i + 1) * 7919 + int(plan_count[i]))
+            except V.VoppError as e:
+                if e.code != V.VOPP_E_DEGENERATE:
+                    raise
+                res = None
+            lat.append(time.perf_counter() - t0 - arr)
+            if res is None:
+                reset(i)
+            else:
+                steps_done += res["particle_steps"]
+                after_plan(i, res)
+            if time.perf_counter() - t0 > seconds * drain_factor:
+                break                                  # overloaded: stop draining
     wall = time.perf_counter() - t0
     stats = V.vopp_server_get_stats(srv) if srv else {}
     if srv:
