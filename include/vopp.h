@@ -87,6 +87,8 @@ extern "C" {
 /* result flags */
 #define VOPP_FLAG_DEGENERATE_BRANCH 1u /* some action had sum_k omega_k = 0 (future := 0) */
 #define VOPP_FLAG_FP64_ROOT 2u         /* the root backup ran in FP64                     */
+#define VOPP_FLAG_REUSED 4u            /* the plan continued a kept subtree (agents with
+                                          subtree reuse, vopp_agent_set_reuse)             */
 
 /* tree detail kept on the device after a plan (vopp_ctx_set_tree_detail) */
 #define VOPP_TREE_MINIMAL 0 /* only what the backup needs                                 */
@@ -142,7 +144,9 @@ typedef struct {
   uint64_t particle_steps;           /* sum_{l=1..D} (A W)^l N generative-model steps      */
   uint64_t nodes;                    /* belief nodes in the tree, root included            */
   uint32_t degenerate_actions;       /* actions whose branch weights all vanished          */
-  uint32_t reserved;
+  uint32_t reused_levels;            /* with VOPP_FLAG_REUSED: materialised levels below the
+                                        root copied from the kept subtree instead of
+                                        expanded again (else 0)                            */
 } vopp_plan_result;
 
 /* Per-plan parameters (used by agents, batches and the serving queue). */
@@ -189,7 +193,11 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
                                    FP32 with compensated sums, within the 1e-4 tolerance */
 #define VOPP_OPT_GRAPHS 7       /* 1: vopp_plan / vopp_plan_batch capture their launch sequence in
                                    a CUDA graph and replay it while the batch shape, buffers and
-                                   options repeat (not while per-kernel timing is on) */
+                                   options repeat (not while per-kernel timing is on, and not for
+                                   batches that keep or continue agents' trees) */
+#define VOPP_OPT_REUSE_COPY 8   /* 1 (default): a plan that continues a kept subtree copies its
+                                   materialised levels; 0: it expands them again under the same
+                                   keys (the same result; for checking the copies) */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
@@ -319,6 +327,35 @@ VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *
  * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
 VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out);
+/* Subtree reuse (enable = 1; 0 turns it off and releases what the agent keeps).  The
+ * paper rebuilds its tree at every step (Alg. 1); with reuse on, an agent keeps what its
+ * last plan expanded and builds on it:
+ *   - vopp_agent_plan / vopp_submit_agent keep the plan's tree on the device (its own
+ *     memory from the stream-ordered pool, outside any server's in-flight budget) until the
+ *     agent's next plan or belief update;
+ *   - vopp_belief_update(a, o) looks for a root branch (a, k) of the kept tree whose sampled
+ *     observation equals o exactly (lowest k; discrete observations match, continuous ones
+ *     practically never do).  If there is one and the tree's level 1 is materialised (depth
+ *     >= 3), that child's particle set and normalised log weights become the belief as the
+ *     tree holds them (no propagation, no resampling; *ess_out = -1, *resampled_out = 0, the
+ *     time step still advances) and its materialised subtree is kept; otherwise the SIR
+ *     update runs and nothing is kept;
+ *   - the agent's plans from an adopted belief continue that subtree, with the same width W
+ *     and as long as the keys stay in range (key level + depth <= 255, node indices below
+ *     2^64): they draw their random numbers as the nodes they are in the kept tree (the
+ *     kept tree's seed, not params->seed), take the root as it stands (terminal particles
+ *     keep their weight: they add no reward or value), and copy the materialised levels the
+ *     subtree already has instead of expanding them (VOPP_FLAG_REUSED, reused_levels).  A
+ *     reused plan therefore equals the subtree below the adopted branches of one tree that
+ *     is that much deeper, and every reused plan from the same belief is the same plan.
+ * Anytime and episode-mode plans of the agent neither keep nor continue trees. */
+VOPP_API int vopp_agent_set_reuse(vopp_agent *agent, int32_t enable);
+/* After a belief update: the adopted branch a*W + k (or -1 when the SIR update ran), the
+ * materialised levels of the kept subtree (root included, 0 if none) and the key level of
+ * its root (the depth of the adopted node in the tree its keys belong to).  Any pointer may
+ * be NULL. */
+VOPP_API int vopp_agent_reuse_info(const vopp_agent *agent, int32_t *adopted_slot,
+                                   int32_t *kept_levels, int32_t *key_level);
 /* ---- closed loop (Alg. 1: plan, execute, perceive, update the belief) ---------------- */
 /* The environment: a true state held on the device as a single particle, stepped by the
  * model's own transition and observation processes with random numbers of its own (Philox

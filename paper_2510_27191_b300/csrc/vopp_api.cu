@@ -122,6 +122,7 @@ struct vopp_ctx {
   int leaf_gen = 1;              // generate level D-1 inside the leaf kernel
   int leaf_threads = 128;
   int grid_cap = 1 << 30;
+  int reuse_copy = 1;            // plans continuing a kept subtree copy its levels (else recompute)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -154,11 +155,18 @@ struct vopp_env {
   EnvOut *dout = nullptr, *hout = nullptr;
 };
 
+struct KeptTree;   // a plan's tree kept on the device for subtree reuse (below)
+
 struct vopp_agent {
   vopp_model *model = nullptr;
   int N = 0;
   uint64_t seed = 0;
   unsigned long long t = 0;
+  // subtree reuse (vopp_agent_set_reuse): the last plan's tree, kept until the next plan or
+  // belief update, and the subtree adopted by the last belief update, kept until the next
+  int reuse = 0;
+  KeptTree *tree = nullptr, *sub = nullptr;
+  int adopted_slot = -1;                // branch a*W + k adopted by the last update, or -1
   float *xy = nullptr, *lw = nullptr;   // NAV2D: xy[2N] (x then y)
   int *s = nullptr;                     // GRID / TOY2
   float *txy = nullptr, *tlw = nullptr;
@@ -178,6 +186,7 @@ namespace {
 struct PlanShape {
   int kind, A, W, AW, N, D, pi_mode;
   int leaf_gen, keep_leaf, keep_debug, mat_top;
+  int keep_obs;      // store the branch observations of every materialised level (kept trees)
 };
 
 struct PlanLayout {
@@ -234,6 +243,7 @@ PlanLayout make_layout(const PlanShape &s, bool psi = false) {
     if (psi && l < s.D) L.psi[l] = take(4 * nodes * s.A);
     if (l >= 1 && keep) { L.rbar[l] = take(4 * nodes); L.lom[l] = take(4 * nodes); }
     if (l >= 1 && keep && s.keep_debug) { L.rep[l] = take(4 * nodes); L.obs[l] = take(8 * nodes); }
+    if (l >= 1 && l <= s.mat_top && s.keep_obs && L.obs[l] == kNone) L.obs[l] = take(8 * nodes);
   }
   L.bytes = off;
   return L;
@@ -352,6 +362,23 @@ void timed_collect(vopp_ctx *c) {
 // ---------------------------------------------------------------------------------------
 // One launch sequence for a set of plans.
 // ---------------------------------------------------------------------------------------
+}  // namespace
+
+// A tree kept on the device for subtree reuse: its memory (from the stream-ordered pool),
+// its shape and layout, and the Philox key schedule its nodes were drawn with (key = seed,
+// key level of its root, key node index of its root at that level).
+struct KeptTree {
+  char *mem = nullptr;
+  size_t bytes = 0;
+  PlanShape shape{};
+  PlanLayout lay{};
+  uint64_t seed = 0;
+  int lvl_off = 0;
+  unsigned long long root_idx = 0;
+};
+
+namespace {
+
 struct Job {
   const vopp_model *model;
   PlanShape shape;
@@ -364,6 +391,12 @@ struct Job {
   const float *log_weights;   // device log weights (agents)
   uint32_t ptr_flags;
   vopp_plan_params p;
+  // subtree reuse
+  vopp_agent *agent = nullptr;      // agent that keeps this plan's tree (own arena)
+  char *own_arena = nullptr;        // the plan's memory when its tree is kept
+  const KeptTree *reuse_src = nullptr;   // adopted subtree this plan continues
+  int lvl_off = 0, reuse_root = 0;
+  unsigned long long root_idx = 0;
 };
 
 struct StageBuild {
@@ -388,7 +421,10 @@ int persistent_grid(vopp_ctx *c, int kind, size_t smem) {
 // Arena bytes of a batch; assigns each job its offset.
 size_t place_jobs(std::vector<Job> &jobs) {
   size_t arena_bytes = 0;
-  for (auto &j : jobs) { j.arena_off = arena_bytes; arena_bytes = align_up(arena_bytes + j.lay.bytes, 256); }
+  for (auto &j : jobs) {
+    j.arena_off = arena_bytes;
+    if (!j.agent) arena_bytes = align_up(arena_bytes + j.lay.bytes, 256);   // kept trees: own memory
+  }
   return std::max<size_t>(arena_bytes, 256);
 }
 
@@ -409,6 +445,47 @@ std::vector<int> lpt_order(const std::vector<Job> &jobs, bool leaf) {
     return item_cost(jobs[x], leaf) > item_cost(jobs[y], leaf);
   });
   return idx;
+}
+
+// A device-to-device copy of a kept subtree's arrays into a plan's arena (src == nullptr:
+// zero dst instead).
+struct CopyOp {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+
+// Materialised levels a plan continuing a kept subtree takes from it (0: the root only).
+int reuse_top(const vopp_ctx *c, const Job &j) {
+  return c->reuse_copy ? std::min(j.reuse_src->shape.mat_top, j.shape.mat_top) : 0;
+}
+
+// The copies that put a kept subtree's levels 0..reuse_top into a plan's arena `base`:
+// particle stores, branch statistics, observations and mean particles, and zeroed
+// completion counters (the kernels that would have written them do not run).
+void reuse_copies(const vopp_ctx *c, const Job &j, char *base, std::vector<CopyOp> &ops) {
+  const KeptTree &t = *j.reuse_src;
+  const PlanLayout &L = j.lay, &S = t.lay;
+  const size_t N = (size_t)j.shape.N;
+  const int top = reuse_top(c, j);
+  auto add = [&](size_t d, size_t s, size_t bytes) {
+    if (d != kNone && s != kNone) ops.push_back(CopyOp{base + d, t.mem + s, bytes});
+  };
+  for (int l = 0; l <= top; ++l) {
+    const size_t nodes = (size_t)ipow(j.shape.AW, l), n = nodes * N;
+    add(L.px[l], S.px[l], 4 * n);
+    add(L.py[l], S.py[l], 4 * n);
+    add(L.ps[l], S.ps[l], 4 * n);
+    add(L.pf[l], S.pf[l], 48 * n);
+    add(L.plw[l], S.plw[l], 4 * n);
+    if (l == 0) continue;
+    add(L.rbar[l], S.rbar[l], 4 * nodes);
+    add(L.lom[l], S.lom[l], 4 * nodes);
+    add(L.obs[l], S.obs[l], 8 * nodes);
+    add(L.rep[l], S.rep[l], 4 * nodes);
+    add(L.mu[l], S.mu[l], 8 * nodes);
+    if (L.cnt[l] != kNone) ops.push_back(CopyOp{base + L.cnt[l], nullptr, 4 * nodes});
+  }
 }
 
 // Build the metadata block of a batch in the slot's pinned mirror, upload it and enqueue
@@ -523,7 +600,10 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   sl.n = n;
   PlanDesc *hd = reinterpret_cast<PlanDesc *>(H + off_desc);
   const PlanDesc *dd = reinterpret_cast<const PlanDesc *>(Dm + off_desc);
+  std::vector<CopyOp> copies;     // kept subtrees into the arenas of the plans that continue them
+  bool kept = false;              // some plan keeps its tree (its memory is not the arena's)
   for (int i = 0; i < n; ++i) {
+    kept |= jobs[i].own_arena != nullptr;
     const Job &j = jobs[i];
     const PlanShape &sh = j.shape;
     PlanDesc P;
@@ -555,7 +635,12 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     P.key0 = (uint32_t)j.p.seed;
     P.key1 = (uint32_t)(j.p.seed >> 32);
     P.model = j.model->dev;
-    char *base = arena + j.arena_off;
+    P.lvl_off = j.lvl_off;
+    P.reuse_root = j.reuse_root;
+    for (int l = 0; l <= kMaxDepth; ++l)
+      P.node_off[l] = (l <= sh.D) ? j.root_idx * ipow(sh.AW, l) : 0ull;
+    char *base = j.own_arena ? j.own_arena : arena + j.arena_off;
+    if (j.reuse_src) reuse_copies(c, j, base, copies);
     const PlanLayout &L = j.lay;
     auto fp = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<float *>(base + o); };
     auto ip = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<int *>(base + o); };
@@ -648,6 +733,10 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   }
   auto record = [&](cudaStream_t stream) -> int {
     CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
+    for (const CopyOp &op : copies) {
+      if (op.src) CUDA_TRY(cudaMemcpyAsync(op.dst, op.src, op.bytes, cudaMemcpyDeviceToDevice, stream));
+      else CUDA_TRY(cudaMemsetAsync(op.dst, 0, op.bytes, stream));
+    }
     for (size_t k = 0; k < stages.size(); ++k) {
       StageBuild &sb = stages[k];
       TimedLaunch tl;
@@ -665,7 +754,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
                              stream));
     return VOPP_OK;
   };
-  if (!graph || timed) return record(stream);
+  // batches that continue or keep agents' trees touch memory outside the arena: not replayed
+  if (!graph || timed || kept || !copies.empty()) return record(stream);
 
   // signature of everything the recorded operations depend on
   std::vector<unsigned char> sig;
@@ -740,6 +830,10 @@ int collect_results(vopp_ctx *c, const Slot &sl, const std::vector<Job> &jobs,
     }
     o.flags = hr[i].flags | (hr[i].degenerate ? VOPP_FLAG_DEGENERATE_BRANCH : 0u);
     o.degenerate_actions = hr[i].degenerate;
+    if (j.reuse_src) {
+      o.flags |= VOPP_FLAG_REUSED;
+      o.reused_levels = (uint32_t)reuse_top(c, j);
+    }
     unsigned long long steps = 0, nodes_total = 1;
     for (int l = 1; l <= j.shape.D; ++l) {
       steps += ipow(j.shape.AW, l) * (unsigned long long)j.shape.N;
@@ -752,6 +846,151 @@ int collect_results(vopp_ctx *c, const Slot &sl, const std::vector<Job> &jobs,
   }
   if (first_err == VOPP_E_DEGENERATE) fail(VOPP_E_DEGENERATE, "root belief has zero total weight");
   return first_err;
+}
+
+// ---- subtree reuse ----------------------------------------------------------------------
+void free_kept(KeptTree *&t, cudaStream_t s) {
+  if (!t) return;
+  if (t->mem) cudaFreeAsync(t->mem, s);
+  delete t;
+  t = nullptr;
+}
+
+// The Philox counter of every node of a depth-D tree rooted at key level lvl_off, key node
+// root_idx fits: levels below 256 (8 bits) and node indices root_idx (A W)^l + n < 2^64.
+bool keys_fit(int lvl_off, unsigned long long root_idx, int AW, int D) {
+  if (lvl_off + D > 255) return false;
+  unsigned __int128 span = 1;
+  for (int l = 0; l < D; ++l) span *= (unsigned)AW;
+  return ((unsigned __int128)root_idx + 1) * span <= ((unsigned __int128)1 << 64);
+}
+
+// An agent plan with subtree reuse on keeps its tree (own memory, observations of every
+// materialised level), and continues the adopted subtree when the agent has one that fits
+// (same width, keys within range): its keys, its root as it stands, its levels.
+void attach_reuse(vopp_agent *g, Job &j) {
+  j.agent = g;
+  j.shape.keep_obs = 1;
+  const KeptTree *sb = g->sub;
+  if (sb && sb->shape.W == j.shape.W && sb->shape.N == j.shape.N &&
+      keys_fit(sb->lvl_off, sb->root_idx, j.shape.AW, j.shape.D)) {
+    j.reuse_src = sb;
+    j.lvl_off = sb->lvl_off;
+    j.root_idx = sb->root_idx;
+    j.reuse_root = 1;
+    j.p.seed = sb->seed;
+    j.first_expand = j.model->ctx->reuse_copy ? std::min(sb->shape.mat_top, j.shape.mat_top) : 0;
+  }
+  j.lay = make_layout(j.shape);
+}
+
+// After an agent's plan: its tree replaces the agent's kept tree (or is released if the
+// plan failed).
+void keep_tree(vopp_agent *g, Job &j, bool ok, cudaStream_t s) {
+  free_kept(g->tree, s);
+  if (!ok || !j.own_arena) {
+    if (j.own_arena) cudaFreeAsync(j.own_arena, s);
+    j.own_arena = nullptr;
+    return;
+  }
+  KeptTree *t = new KeptTree;
+  t->mem = j.own_arena;
+  t->bytes = j.lay.bytes;
+  t->shape = j.shape;
+  t->lay = j.lay;
+  t->seed = j.p.seed;
+  t->lvl_off = j.lvl_off;
+  t->root_idx = j.root_idx;
+  g->tree = t;
+  j.own_arena = nullptr;
+}
+
+// Adopt child `slot` (= a W + k) of the kept tree's root: its particle set becomes the
+// agent's belief and its materialised subtree (levels 1..mat_top of the tree, the child's
+// nodes, contiguous at every level) is copied into a compact store keyed as it was.
+int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
+  const KeptTree &t = *g->tree;
+  const int AW = t.shape.AW;
+  const size_t N = (size_t)t.shape.N;
+  PlanShape sh = t.shape;
+  sh.D = t.shape.D - 1;
+  sh.mat_top = t.shape.mat_top - 1;
+  sh.keep_leaf = sh.keep_debug = 0;
+  sh.keep_obs = 1;
+  KeptTree *sb = new (std::nothrow) KeptTree;
+  if (!sb) return fail(VOPP_E_NOMEM, "subtree alloc");
+  sb->shape = sh;
+  sb->lay = make_layout(sh);
+  sb->bytes = sb->lay.bytes;
+  sb->seed = t.seed;
+  sb->lvl_off = t.lvl_off + 1;
+  sb->root_idx = t.root_idx * (unsigned long long)AW + (unsigned long long)slot;
+  if (cudaMallocAsync(reinterpret_cast<void **>(&sb->mem), sb->bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    delete sb;
+    return fail(VOPP_E_NOMEM, "subtree device alloc");
+  }
+  const PlanLayout &S = t.lay, &L = sb->lay;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](size_t d, size_t src, size_t elem_off, size_t elem_bytes, size_t bytes) {
+    if (e == cudaSuccess && d != kNone && src != kNone)
+      e = cudaMemcpyAsync(sb->mem + d, t.mem + src + elem_off * elem_bytes, bytes,
+                          cudaMemcpyDeviceToDevice, s);
+  };
+  for (int l = 0; l <= sh.mat_top; ++l) {
+    const size_t nodes = (size_t)ipow(AW, l), first = (size_t)slot * nodes;   // first node there
+    cp(L.px[l], S.px[l + 1], first * N, 4, 4 * nodes * N);
+    cp(L.py[l], S.py[l + 1], first * N, 4, 4 * nodes * N);
+    cp(L.ps[l], S.ps[l + 1], first * N, 4, 4 * nodes * N);
+    cp(L.pf[l], S.pf[l + 1], first * N, 48, 48 * nodes * N);
+    cp(L.plw[l], S.plw[l + 1], first * N, 4, 4 * nodes * N);
+    if (l == 0) continue;
+    cp(L.rbar[l], S.rbar[l + 1], first, 4, 4 * nodes);
+    cp(L.lom[l], S.lom[l + 1], first, 4, 4 * nodes);
+    cp(L.obs[l], S.obs[l + 1], first, 8, 8 * nodes);
+    cp(L.mu[l], S.mu[l + 1], first, 8, 8 * nodes);
+  }
+  // the agent's belief: the adopted node's particles in the agent's row layout
+  auto cpa = [&](void *d, size_t src, size_t elem_bytes, size_t rows) {
+    if (e == cudaSuccess && src != kNone)
+      e = cudaMemcpyAsync(d, t.mem + src + (size_t)slot * N * elem_bytes, rows * 4 * N,
+                          cudaMemcpyDeviceToDevice, s);
+  };
+  const int kind = t.shape.kind;
+  if (kind == kNav || kind == kCrowd) { cpa(g->xy, S.px[1], 4, 1); cpa(g->xy + N, S.py[1], 4, 1); }
+  if (kind == kCrowd) cpa(g->pf, S.pf[1], 48, 12);
+  if (kind != kNav) cpa(g->s, S.ps[1], 4, 1);
+  cpa(g->lw, S.plw[1], 4, 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(sb->mem, s);
+    delete sb;
+    return fail(VOPP_E_CUDA, "subtree copy: %s", cudaGetErrorString(e));
+  }
+  free_kept(g->sub, s);
+  g->sub = sb;
+  return VOPP_OK;
+}
+
+// The kept tree's branch (action, k) whose sampled observation equals obs (lowest k), as
+// slot action W + k, or -1.  Only a tree whose level 1 is materialised can be adopted.
+int matching_branch(vopp_agent *g, int action, const float *obs_f, int obs_i, cudaStream_t s) {
+  const KeptTree *t = g->tree;
+  if (!t || t->shape.mat_top < 1 || t->lay.obs[1] == kNone) return -1;
+  const int W = t->shape.W;
+  std::vector<float> ob(2 * (size_t)W);
+  if (cudaMemcpyAsync(ob.data(), t->mem + t->lay.obs[1] + 8 * (size_t)action * W, 8 * (size_t)W,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  for (int k = 0; k < W; ++k) {
+    const bool eq = (t->shape.kind == kNav) ? (ob[2 * k] == obs_f[0] && ob[2 * k + 1] == obs_f[1])
+                                            : ((int)ob[2 * k] == obs_i);
+    if (eq) return action * W + k;
+  }
+  return -1;
 }
 
 int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *statuses) {
@@ -939,6 +1178,7 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       c->use_graphs = value ? 1 : 0;
       if (!c->use_graphs) c->graph.reset();
       return VOPP_OK;
+    case VOPP_OPT_REUSE_COPY: c->reuse_copy = value ? 1 : 0; return VOPP_OK;
     default: return fail(VOPP_E_INVALID, "unknown option %d", option);
   }
 }
@@ -1431,7 +1671,12 @@ int vopp_run_episode(vopp_agent *g, vopp_env *e, const vopp_plan_params *p, int3
 
 void vopp_agent_destroy(vopp_agent *g) {
   if (!g) return;
-  if (g->model) cudaStreamSynchronize(g->model->ctx->stream);
+  if (g->model) {
+    cudaStream_t s = g->model->ctx->stream;
+    free_kept(g->tree, s);
+    free_kept(g->sub, s);
+    cudaStreamSynchronize(s);
+  }
   cudaFree(g->blk); cudaFree(g->tblk);
   cudaFree(g->lw); cudaFree(g->tlw); cudaFree(g->cdf); cudaFree(g->anc); cudaFree(g->dout);
   if (g->hout) cudaFreeHost(g->hout);
@@ -1452,7 +1697,37 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
   if (rc) return rc;
   jobs[0].log_weights = g->lw;
   cudaSetDevice(c->device);
-  return run_jobs(c, jobs, out, nullptr);
+  if (!g->reuse) return run_jobs(c, jobs, out, nullptr);
+  Job &j = jobs[0];
+  attach_reuse(g, j);
+  if (cudaMallocAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(VOPP_E_NOMEM, "plan memory for the kept tree");
+  }
+  rc = run_jobs(c, jobs, out, nullptr);
+  keep_tree(g, j, rc == VOPP_OK, c->stream);
+  return rc;
+}
+
+int vopp_agent_set_reuse(vopp_agent *g, int32_t enable) {
+  if (!g) return fail(VOPP_E_INVALID, "agent is NULL");
+  g->reuse = enable != 0;
+  if (!g->reuse) {
+    cudaStream_t s = g->model->ctx->stream;
+    free_kept(g->tree, s);
+    free_kept(g->sub, s);
+    g->adopted_slot = -1;
+  }
+  return VOPP_OK;
+}
+
+int vopp_agent_reuse_info(const vopp_agent *g, int32_t *adopted_slot, int32_t *kept_levels,
+                          int32_t *key_level) {
+  if (!g) return fail(VOPP_E_INVALID, "agent is NULL");
+  if (adopted_slot) *adopted_slot = g->sub ? g->adopted_slot : -1;
+  if (kept_levels) *kept_levels = g->sub ? g->sub->shape.mat_top + 1 : 0;
+  if (key_level) *key_level = g->sub ? g->sub->lvl_off : 0;
+  return VOPP_OK;
 }
 
 int vopp_agent_plan_anytime(vopp_agent *g, const vopp_plan_params *p, double budget_s,
@@ -1502,6 +1777,25 @@ int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *e
     B.s = g->s; B.ts = g->ts;
     B.pf = g->pf; B.tpf = g->tpf;
     B.obs_i = *static_cast<const int32_t *>(obs);
+  }
+  if (g->reuse) {
+    // subtree reuse: a kept tree's branch of this action that sampled this very observation
+    // becomes the belief (its particle set, as the tree holds it), and its subtree is kept
+    const int slot = matching_branch(g, action, B.obs_f, B.obs_i, c->stream);
+    free_kept(g->sub, c->stream);
+    g->adopted_slot = -1;
+    if (slot >= 0) {
+      const int rc = adopt_subtree(g, slot, c->stream);
+      free_kept(g->tree, c->stream);
+      if (rc) return rc;
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+      g->adopted_slot = slot;
+      g->t += 1;
+      if (ess_out) *ess_out = -1.0;
+      if (resampled_out) *resampled_out = 0;
+      return VOPP_OK;
+    }
+    free_kept(g->tree, c->stream);
   }
   B.lw = g->lw;
   B.tlw = g->tlw;
@@ -1640,6 +1934,8 @@ void harvest(vopp_server *srv, ServerSlot *s, bool ok) {
     std::vector<vopp_plan_result> outs(n);
     std::vector<int> st(n);
     collect_results(srv->c, s->slot, s->jobs, outs.data(), st.data(), false);
+    for (int i = 0; i < n; ++i)   // agents with subtree reuse keep their plan's tree
+      if (s->jobs[i].agent) keep_tree(s->jobs[i].agent, s->jobs[i], st[i] == VOPP_OK, s->slot.stream);
     const double t = now_s();
     for (int i = 0; i < n; ++i) {
       srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
@@ -1648,6 +1944,8 @@ void harvest(vopp_server *srv, ServerSlot *s, bool ok) {
       srv->stats.particle_steps += outs[i].particle_steps;
     }
   } else {
+    for (auto &j : s->jobs)
+      if (j.agent) keep_tree(j.agent, j, false, s->slot.stream);
     post_failure(srv, s->reqs, VOPP_E_CUDA);
   }
   srv->in_flight -= s->arena_bytes;
@@ -1697,6 +1995,9 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
   const size_t arena_bytes = place_jobs(jobs);
   char *arena = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&arena), arena_bytes, s->slot.stream);
+  for (auto &j : jobs)   // plans whose agents keep their trees get memory of their own
+    if (e == cudaSuccess && j.agent)
+      e = cudaMallocAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, s->slot.stream);
   int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false, nullptr) : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
     if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
@@ -1706,6 +2007,8 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
   if (rc != VOPP_OK) {
     cudaGetLastError();
     if (arena) cudaFreeAsync(arena, s->slot.stream);
+    for (auto &j : jobs)
+      if (j.own_arena) cudaFreeAsync(j.own_arena, s->slot.stream);
     cudaStreamSynchronize(s->slot.stream);
     return rc;
   }
@@ -1933,6 +2236,7 @@ int vopp_submit_agent(vopp_server *srv, vopp_agent *g, const vopp_plan_params *p
   int rc = make_job(srv->c, g->model, states, nullptr, g->N, *p, VOPP_PTR_DEVICE, r.job);
   if (rc) return rc;
   r.job.log_weights = g->lw;
+  if (g->reuse) attach_reuse(g, r.job);   // the worker allocates the kept tree's memory
   if (p->pi_bar) r.pi_bar.assign(p->pi_bar, p->pi_bar + g->model->A);
   r.bytes = r.job.lay.bytes + 256;
   return submit_req(srv, std::move(r), ticket);

@@ -89,8 +89,23 @@ struct PlanDesc {
   // across iterations (null: one-pass closed form); levels >= psi_new_level are new
   float *psi[kMaxDepth];
   int psi_new_level;
+  // Subtree reuse: a plan that continues a kept subtree keys its random numbers as the
+  // nodes they are in the tree it continues (level l + lvl_off, index node + node_off[l],
+  // node_off[l] = root index there x (A W)^l), and its root is that tree's node as it
+  // stands (reuse_root: level 0 already holds its particles and normalised log weights).
+  int lvl_off, reuse_root;
+  unsigned long long node_off[kMaxDepth + 1];
   DevResult *result;
 };
+
+// Philox counter words of tree level l and node `node` of a plan (see PlanDesc).
+__device__ __forceinline__ uint32_t key_level(const PlanDesc &P, int l) {
+  return (uint32_t)(l + P.lvl_off);
+}
+__device__ __forceinline__ unsigned long long key_node(const PlanDesc &P, int l,
+                                                       unsigned long long node) {
+  return node + P.node_off[l];
+}
 
 // A launch covers work items of several plans: plan i owns items [prefix[i], prefix[i+1]).
 struct StageTable {

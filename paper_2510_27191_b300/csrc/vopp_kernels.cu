@@ -268,7 +268,8 @@ template <class M>
 __device__ __forceinline__ uint4 pair_words(const PlanDesc &P, int p, int l, int a, int k,
                                             unsigned long long node) {
   if (!M::kStochastic) return make_uint4(0u, 0u, 0u, 0u);
-  return draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, l, a, k, node);
+  return draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, key_level(P, l), a, k,
+              key_node(P, l, node));
 }
 
 // The branch observation of (l, node, a, k): enumerated, or drawn from the representative
@@ -278,13 +279,14 @@ __device__ __forceinline__ typename M::O branch_obs(const PlanDesc &P, const Src
                                                     int k, unsigned long long node,
                                                     const DevModel &dm, int &j) {
   if (P.branch_mode == kEnumerate) { j = -1; return M::enum_obs(k); }
-  const uint4 w = draw(P.key0, P.key1, 0u, kPurposeObservation, l, a, k, node);
+  const unsigned long long kn = key_node(P, l, node);
+  const uint4 w = draw(P.key0, P.key1, 0u, kPurposeObservation, key_level(P, l), a, k, kn);
   j = (int)(((unsigned long long)w.z * (unsigned long long)P.N) >> 32);
   typename M::S sj = src.get(j);
   const uint4 t = pair_words<M>(P, j >> 1, l, a, k, node);
-  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
-  step_particle<M>(sj, a, t, j, DrawCtx{P.key0, P.key1, kPurposeTransition, c1, node}, dm);
-  return obs_particle<M>(sj, a, w, DrawCtx{P.key0, P.key1, kPurposeObservation, c1, node}, 0u, dm);
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  step_particle<M>(sj, a, t, j, DrawCtx{P.key0, P.key1, kPurposeTransition, c1, kn}, dm);
+  return obs_particle<M>(sj, a, w, DrawCtx{P.key0, P.key1, kPurposeObservation, c1, kn}, 0u, dm);
 }
 
 // log pibar(a | node) for a < A (computed by every calling thread).
@@ -345,7 +347,8 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   const int a = slot / W, k = slot - (slot / W) * W;
   int j;
   const typename M::O o = branch_obs<M>(P, src, l, a, k, parent, dm, j);
-  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  const unsigned long long kn = key_node(P, l, parent);
 
   // pass 1: step every particle, log2-likelihood, reward mean; keep L2 = lw2 + ell2, ell2
   Kahan R;
@@ -355,7 +358,7 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
     const int i0 = 2 * p, i1 = 2 * p + 1;
     const bool v1 = i1 < N;
     const uint4 w = M::kStochastic
-                        ? philox(make_uint4((uint32_t)p, c1, (uint32_t)parent, (uint32_t)(parent >> 32)),
+                        ? philox(make_uint4((uint32_t)p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)),
                                  P.key0, P.key1)
                         : make_uint4(0u, 0u, 0u, 0u);
     const float lw0 = src.lw(i0), lw1 = v1 ? src.lw(i1) : -CUDART_INF_F;
@@ -370,7 +373,7 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       s0 = set_xy<M>(s0, X.x, Y.x);
       s1 = set_xy<M>(s1, X.y, Y.y);
     } else {
-      const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, parent};
+      const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, kn};
       r.x = step_particle<M>(s0, a, w, i0, dc, dm);
       r.y = step_particle<M>(s1, a, w, i1, dc, dm);
       e = make_float2(M::loglik2(s0, a, o, dm), M::loglik2(s1, a, o, dm));
@@ -452,8 +455,8 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       P.mu[cl][2 * child + 1] = mu.y;
     }
     if (mu_out) *mu_out = mu;
-    if (P.keep_debug) {
-      P.rep[cl][child] = j;
+    if (P.rep[cl]) P.rep[cl][child] = j;
+    if (P.obs[cl]) {   // full detail, or the level-1 observations a kept tree needs
       const float2 of = M::obs_f2(o);
       P.obs[cl][2 * child] = of.x;
       P.obs[cl][2 * child + 1] = of.y;
@@ -668,9 +671,16 @@ template <class M>
 __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red) {
   const int N = P.N;
   const GNode<M> dst = GNode<M>::at(P, 0, 0);
-  // log weights of the caller's belief; terminal particles and non-positive weights -> -inf
+  // log weights of the caller's belief; terminal particles and non-positive weights -> -inf.
+  // A reused root (a node of a kept tree) is taken as it stands: its particles and
+  // normalised log weights are already in the level-0 store, terminal particles included
+  // (they keep the weight they had inside that tree, where they add no reward or value).
   float m = -CUDART_INF_F;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    if (P.reuse_root) {
+      m = fmaxf(m, dst.lw(i));
+      continue;
+    }
     const typename M::S s = load_root<M>(P, i);
     float lw;
     if (P.root_lw) {
@@ -695,13 +705,14 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
     const float lw = dst.lw(i);
     if (lw > -CUDART_INF_F) T.add(__expf(lw - m));
   }
-  const float lse = m + logf(block_sum(T.value(), red));
+  const float tsum = block_sum(T.value(), red);
+  const float lse = P.reuse_root ? 0.f : m + logf(tsum);
   Kahan MX, MY, H;
   MX.init(); MY.init(); H.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float lw = dst.lw(i);
     const float nl = (lw > -CUDART_INF_F) ? lw - lse : -CUDART_INF_F;
-    dst.set_lw(i, nl);
+    if (!P.reuse_root) dst.set_lw(i, nl);
     const float wn = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
     const typename M::S s = dst.get(i);
     const float2 xy = state_xy<M>(s);
@@ -849,8 +860,9 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
 #else
   const uint32_t key0 = P.key0, key1 = P.key1;
 #endif
-  const uint32_t c1 = (uint32_t)l | ((uint32_t)a << 8) | ((uint32_t)k << 16);
-  const uint32_t c2 = (uint32_t)node, c3 = (uint32_t)(node >> 32);
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  const unsigned long long kn = key_node(P, l, node);
+  const uint32_t c2 = (uint32_t)kn, c3 = (uint32_t)(kn >> 32);
   ShiftedSum A1, A0;
   A1.init();
   A0.init();
@@ -937,7 +949,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
         typename M::S s0, s1;
         nb.get_pair(p, s0, s1);
         const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
-        const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, node};
+        const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, kn};
         const float r0 = step_particle<M>(s0, a, w, 2 * p, dc, dm);
         const float r1 = step_particle<M>(s1, a, w, 2 * p + 1, dc, dm);
         const float e0 = M::loglik2(s0, a, o, dm), e1 = M::loglik2(s1, a, o, dm);

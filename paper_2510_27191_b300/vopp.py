@@ -22,7 +22,7 @@ VOPP_NAV2D, VOPP_GRID, VOPP_TOY2, VOPP_CROWD = 0, 1, 2, 3
 VOPP_BRANCH_SAMPLE, VOPP_BRANCH_ENUMERATE = 0, 1
 VOPP_PI_UNIFORM, VOPP_PI_FIXED, VOPP_PI_NAV_DIST = 0, 1, 2
 VOPP_PTR_DEVICE = 1
-VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT = 1, 2
+VOPP_FLAG_DEGENERATE_BRANCH, VOPP_FLAG_FP64_ROOT, VOPP_FLAG_REUSED = 1, 2, 4
 VOPP_TREE_MINIMAL, VOPP_TREE_FULL = 0, 1
 (VOPP_FIELD_V, VOPP_FIELD_Q, VOPP_FIELD_RBAR, VOPP_FIELD_LOMEGA, VOPP_FIELD_REP, VOPP_FIELD_OBS,
  VOPP_FIELD_PX, VOPP_FIELD_PY, VOPP_FIELD_PS, VOPP_FIELD_PLW, VOPP_FIELD_MU,
@@ -31,6 +31,7 @@ VOPP_OPT_LEAF_GEN, VOPP_OPT_LEAF_THREADS, VOPP_OPT_GRID_CAP = 1, 2, 3
 VOPP_OPT_PERSISTENT = 5
 VOPP_OPT_FP64_ROOT = 6
 VOPP_OPT_GRAPHS = 7
+VOPP_OPT_REUSE_COPY = 8
 VOPP_MAX_ACTIONS = 16
 NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
 
@@ -58,7 +59,7 @@ class vopp_plan_result(ctypes.Structure):
                 ("v_root", ctypes.c_double), ("q", ctypes.c_double * VOPP_MAX_ACTIONS),
                 ("policy", ctypes.c_double * VOPP_MAX_ACTIONS),
                 ("particle_steps", ctypes.c_uint64), ("nodes", ctypes.c_uint64),
-                ("degenerate_actions", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("degenerate_actions", ctypes.c_uint32), ("reused_levels", ctypes.c_uint32)]
 
 
 class vopp_plan_params(ctypes.Structure):
@@ -180,6 +181,9 @@ def _load():
         "vopp_agent_plan_anytime": ([vp, ctypes.POINTER(vopp_plan_params), ctypes.c_double,
                                      ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
                                     ctypes.c_int),
+        "vopp_agent_set_reuse": ([vp, i32], ctypes.c_int),
+        "vopp_agent_reuse_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -292,7 +296,7 @@ def _addr(a):
 def _result_dict(r: vopp_plan_result, A: int) -> dict:
     return dict(action=r.action, flags=r.flags, v_root=r.v_root, q=np.array(r.q[:A]),
                 policy=np.array(r.policy[:A]), particle_steps=r.particle_steps, nodes=r.nodes,
-                degenerate_actions=r.degenerate_actions)
+                degenerate_actions=r.degenerate_actions, reused_levels=r.reused_levels)
 
 
 def vopp_plan(model: int, root_states, root_weights, n_particles: int, depth: int, width: int,
@@ -398,6 +402,17 @@ def vopp_belief_update(agent: int, action: int, obs, kind: int):
 
 def _state_words(kind: int) -> int:
     return {VOPP_NAV2D: 2, VOPP_CROWD: 15}.get(kind, 1)
+
+
+def vopp_agent_set_reuse(agent: int, enable: bool = True) -> None:
+    check(lib.vopp_agent_set_reuse(agent, int(enable)))
+
+
+def vopp_agent_reuse_info(agent: int) -> dict:
+    """adopted_slot (a*W + k, or -1 after an SIR update), kept_levels, key_level."""
+    a, k, lv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(lib.vopp_agent_reuse_info(agent, ctypes.byref(a), ctypes.byref(k), ctypes.byref(lv)))
+    return dict(adopted_slot=a.value, kept_levels=k.value, key_level=lv.value)
 
 
 def vopp_agent_get_particles(agent: int, kind: int):
