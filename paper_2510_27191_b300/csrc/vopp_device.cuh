@@ -130,14 +130,25 @@ __device__ __forceinline__ int find_plan(const StageTable &st, long long item) {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter words:
 //   c0 = idx | purpose << 24, c1 = level | action << 8 | branch << 16, (c2, c3) = node.
 // ---------------------------------------------------------------------------------------
+#ifndef VOPP_PHILOX_WIDE
+#define VOPP_PHILOX_WIDE 1
+#endif
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
+#if VOPP_PHILOX_WIDE
+    // each round's two 32x32 -> 64-bit products as single wide multiplies
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                   (uint32_t)p0);
+#else
     const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
     const uint32_t lo0 = 0xD2511F53u * c.x;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
     const uint32_t lo1 = 0xCD9E8D57u * c.z;
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+#endif
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -205,6 +216,13 @@ __device__ __forceinline__ float ex2(float x) {
 __device__ __forceinline__ float lg2(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// max(a, b, c) in one instruction (three-input max of sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float y;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
   return y;
 }
 constexpr float kLog2e = 1.44269504088896341f;
@@ -419,18 +437,23 @@ struct NavModel {
   __device__ __forceinline__ static float2 loglik2_pair(float2 x, float2 y, const O &o) {
     const float2 dm = add2(x, bc2(-9.0f));
     const float2 sg = fma2(bc2(0.5f), make_float2(fabsf(dm.x), fabsf(dm.y)), bc2(0.05f));
-    const float2 t = mul2(bc2(-2.0f), make_float2(lg2(sg.x), lg2(sg.y)));   // -2 log2 sigma
-    const float2 is2 = make_float2(ex2(t.x), ex2(t.y));                   // 1 / sigma^2
+    const float2 lg = make_float2(lg2(sg.x), lg2(sg.y));
+    // -2 log2 sigma - log2(2 pi), and log2(log2(e) / 2) - 2 log2 sigma whose 2^ is
+    // log2(e) / (2 sigma^2), the factor of -|o - s'|^2
+    const float2 t = fma2(lg, bc2(-2.0f), bc2(-2.65149613f));
+    const float2 f = fma2(lg, bc2(-2.0f), bc2(-0.471233627f));
+    const float2 is2 = make_float2(-ex2(f.x), -ex2(f.y));
     const float2 ex = fma2(x, bc2(-1.0f), bc2(o.x)), ey = fma2(y, bc2(-1.0f), bc2(o.y));
     const float2 d2 = fma2(ex, ex, mul2(ey, ey));
-    return fma2(mul2(bc2(-0.721347520f), d2), is2, add2(t, bc2(-2.65149613f)));
+    return fma2(d2, is2, t);
   }
   // Heuristic of the pair; t0 / t1 are the terminal flags of the states.
   __device__ __forceinline__ static float2 heuristic_pair(float2 x, float2 y, bool t0, bool t1,
                                                           float log2g, float a0, float b0, bool hz) {
-    float2 m = add2(add2(x, y), bc2(-0.5f));
-    m = make_float2(fmaxf(m.x, 1.0f), fmaxf(m.y, 1.0f));
-    const float2 e = fma2(m, bc2(log2g), bc2(-log2g));
+    // m - 1 = max(x + y - 1/2, 1) - 1 = max(x + y, 3/2) - 3/2
+    float2 m = add2(x, y);
+    m = make_float2(fmaxf(m.x, 1.5f), fmaxf(m.y, 1.5f));
+    const float2 e = fma2(m, bc2(log2g), bc2(-1.5f * log2g));
     const float2 h = fma2(bc2(b0), make_float2(ex2(e.x), ex2(e.y)), bc2(a0));
     return make_float2((hz || t0) ? 0.0f : h.x, (hz || t1) ? 0.0f : h.y);
   }

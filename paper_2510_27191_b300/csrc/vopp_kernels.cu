@@ -263,27 +263,27 @@ template <> __device__ __forceinline__ CrowdModel::S load_root<CrowdModel>(const
   return s;
 }
 
-// Transition Philox words of particle pair p of branch (l, node, a, k).
+// Transition Philox words of particle pair p of branch (a, k) of the node with key node
+// index kn at level l (kn = key_node(P, l, node)).
 template <class M>
 __device__ __forceinline__ uint4 pair_words(const PlanDesc &P, int p, int l, int a, int k,
-                                            unsigned long long node) {
+                                            unsigned long long kn) {
   if (!M::kStochastic) return make_uint4(0u, 0u, 0u, 0u);
-  return draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, key_level(P, l), a, k,
-              key_node(P, l, node));
+  return draw(P.key0, P.key1, (uint32_t)p, kPurposeTransition, key_level(P, l), a, k, kn);
 }
 
-// The branch observation of (l, node, a, k): enumerated, or drawn from the representative
-// particle j = floor(u N / 2^32) after its own transition.
+// The branch observation of branch (a, k) of the node with key node index kn at level l:
+// enumerated, or drawn from the representative particle j = floor(u N / 2^32) after its
+// own transition.
 template <class M, class Src>
 __device__ __forceinline__ typename M::O branch_obs(const PlanDesc &P, const Src &src, int l, int a,
-                                                    int k, unsigned long long node,
+                                                    int k, unsigned long long kn,
                                                     const DevModel &dm, int &j) {
   if (P.branch_mode == kEnumerate) { j = -1; return M::enum_obs(k); }
-  const unsigned long long kn = key_node(P, l, node);
   const uint4 w = draw(P.key0, P.key1, 0u, kPurposeObservation, key_level(P, l), a, k, kn);
   j = (int)(((unsigned long long)w.z * (unsigned long long)P.N) >> 32);
   typename M::S sj = src.get(j);
-  const uint4 t = pair_words<M>(P, j >> 1, l, a, k, node);
+  const uint4 t = pair_words<M>(P, j >> 1, l, a, k, kn);
   const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
   step_particle<M>(sj, a, t, j, DrawCtx{P.key0, P.key1, kPurposeTransition, c1, kn}, dm);
   return obs_particle<M>(sj, a, w, DrawCtx{P.key0, P.key1, kPurposeObservation, c1, kn}, 0u, dm);
@@ -346,9 +346,9 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   const int slot = (int)(child - parent * (unsigned long long)AW);
   const int a = slot / W, k = slot - (slot / W) * W;
   int j;
-  const typename M::O o = branch_obs<M>(P, src, l, a, k, parent, dm, j);
-  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
   const unsigned long long kn = key_node(P, l, parent);
+  const typename M::O o = branch_obs<M>(P, src, l, a, k, kn, dm, j);
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
 
   // pass 1: step every particle, log2-likelihood, reward mean; keep L2 = lw2 + ell2, ell2
   Kahan R;
@@ -771,7 +771,7 @@ __device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, 
   build_child<M>(P, dm, l, child, src, dst, sc, red, false, false, nullptr);
 }
 
-__global__ void __launch_bounds__(256) k_expand(const PlanDesc *plans, StageTable st,
+__global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageTable st,
                                                 long long total) {
   extern __shared__ float smem[];
   __shared__ float red[32 * 5];
@@ -852,7 +852,8 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   const float log2g = P.log2_gamma, h_a0 = P.h_a0, h_b0 = P.h_b0;
   const bool hz = P.h_zero != 0;
   int j;
-  const typename M::O o = branch_obs<M>(P, nb, l, a, k, node, dm, j);
+  const unsigned long long kn = key_node(P, l, node);
+  const typename M::O o = branch_obs<M>(P, nb, l, a, k, kn, dm, j);
 
 #if VOPP_ROUND_KEYS
   PhiloxKeys K;
@@ -861,7 +862,6 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   const uint32_t key0 = P.key0, key1 = P.key1;
 #endif
   const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
-  const unsigned long long kn = key_node(P, l, node);
   const uint32_t c2 = (uint32_t)kn, c3 = (uint32_t)(kn >> 32);
   ShiftedSum A1, A0;
   A1.init();
@@ -898,8 +898,8 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
           E[c] = make_float2(e.x, v1 ? e.y : -CUDART_INF_F);
           Hh[c] = NavModel::heuristic_pair(X, Y, t0, t1, log2g, h_a0, h_b0, hz);
           rsum = fma2(make_float2(b.z, b.w), r, rsum);   // pad slot: w = 0
-          cm1 = fmaxf(cm1, fmaxf(L[c].x, L[c].y));
-          cm0 = fmaxf(cm0, fmaxf(E[c].x, E[c].y));
+          cm1 = fmax3(cm1, L[c].x, L[c].y);
+          cm0 = fmax3(cm0, E[c].x, E[c].y);
         }
       }
       const float m1 = A1.shift_to(cm1), m0 = A0.shift_to(cm0);
