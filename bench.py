@@ -507,13 +507,16 @@ def main():
             from paper_2510_27191_b300 import loadgen as LG
             out["batched"] = LG.batch_run(V, ctx)
             served = {}
+            # served: continuous batching, batched belief updates, agents with subtree reuse;
+            # plain: one synchronous plan per request, then its own belief update
             for rate in (2000.0, 16000.0):
                 for mode in ("served", "plain"):
                     r = LG.serve_run(V, ctx, seconds=args.serve_seconds, rate=rate, mode=mode,
-                                     drain_factor=2.0)
+                                     drain_factor=2.0, reuse=(mode == "served"))
                     served[f"{mode}_{int(rate)}"] = {k: r[k] for k in (
                         "plans_per_s", "particle_steps_per_s", "p50_ms", "p99_ms",
-                        "deadline_misses", "completed", "requests", "unfinished")}
+                        "deadline_misses", "completed", "requests", "unfinished",
+                        "subtree_reuse", "reused_plans")}
                     if mode == "served":
                         served[f"{mode}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
             out["served"] = served

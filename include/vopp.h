@@ -312,6 +312,12 @@ VOPP_API int vopp_tree_read_plan(vopp_ctx *ctx, int32_t plan, int32_t field, int
 VOPP_API int vopp_grid_thresholds(uint64_t *thr, int32_t n);
 
 /* ---- agents: device-resident beliefs with the SIR update (Sec. III-B) ---------------- */
+/* An agent holds n weighted particles (states as for vopp_plan's root, weights linear or
+ * NULL = uniform, host or device per ptr_flags) on the device, with its own Philox key
+ * (seed) and time step for its belief updates.  Its device memory comes from the device's
+ * stream-ordered pool on the context's stream, so creating or destroying an agent does not
+ * synchronise the device (a serving loop keeps running while agents come and go); do not
+ * destroy an agent while a request on it is outstanding. */
 VOPP_API int vopp_agent_create(vopp_model *model, const void *states, const float *weights, int32_t n,
                       uint64_t seed, uint32_t ptr_flags, vopp_agent **out);
 VOPP_API int vopp_agent_plan(vopp_agent *agent, const vopp_plan_params *params, vopp_plan_result *out);
@@ -327,6 +333,22 @@ VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *
  * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
 VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out);
+/* tau(b, a, o) for n agents of ctx at once: each agent is updated exactly as
+ * vopp_belief_update would update it (subtree reuse included), the SIR updates of all of
+ * them in one launch (one CTA per agent, the same arithmetic and reduction order, so the
+ * particles, weights, ancestors, ESS and resampling decisions are bit-identical to n single
+ * calls).  agents[i] (each at most once), actions[i] and obs[i] (a host pointer, as for
+ * vopp_belief_update) describe update i; status_out[i] receives its status (VOPP_OK, or
+ * VOPP_E_DEGENERATE with that agent's belief unchanged), ess_out[i] / resampled_out[i] (may
+ * be NULL) its ESS (-1 for an adopted subtree) and resampling flag.  Returns VOPP_OK when
+ * every update succeeded, else the first failing status; VOPP_E_INVALID (nothing updated)
+ * for bad arguments, an agent of another context or an agent listed twice.  Serving loops
+ * use it to update every agent whose plan just finished with one launch and one
+ * synchronisation. */
+VOPP_API int vopp_belief_update_batch(vopp_ctx *ctx, int32_t n, vopp_agent *const *agents,
+                                      const int32_t *actions, const void *const *obs,
+                                      double *ess_out, int32_t *resampled_out,
+                                      int32_t *status_out);
 /* Subtree reuse (enable = 1; 0 turns it off and releases what the agent keeps).  The
  * paper rebuilds its tree at every step (Alg. 1); with reuse on, an agent keeps what its
  * last plan expanded and builds on it:

@@ -53,6 +53,7 @@ int fail(int code, const char *fmt, ...) {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+
 unsigned long long ipow(unsigned long long b, int e) {
   unsigned long long r = 1;
   for (int i = 0; i < e; ++i) r *= b;
@@ -134,6 +135,9 @@ struct vopp_ctx {
   std::vector<PlanDesc> last_desc;
   std::vector<int> last_ok;
   EpisodeStore *episodes = nullptr;   // buffers of the last episode-mode plan
+  // the library's stream-ordered pool (server arenas, kept trees, agents): memory stays in
+  // it once allocated, and it never makes one stream wait for another to reuse memory
+  cudaMemPool_t pool = nullptr;
 };
 
 struct vopp_model {
@@ -175,7 +179,8 @@ struct vopp_agent {
   float *blk = nullptr, *tblk = nullptr;  // the state store (rows as the root layout)
   double *cdf = nullptr;
   int *anc = nullptr;
-  BeliefOut *dout = nullptr, *hout = nullptr;
+  BeliefOut *dout = nullptr;
+  BeliefOut hout{};                     // host copy of the last update's outcome
 };
 
 // ---------------------------------------------------------------------------------------
@@ -925,7 +930,8 @@ int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
   sb->seed = t.seed;
   sb->lvl_off = t.lvl_off + 1;
   sb->root_idx = t.root_idx * (unsigned long long)AW + (unsigned long long)slot;
-  if (cudaMallocAsync(reinterpret_cast<void **>(&sb->mem), sb->bytes, s) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&sb->mem), sb->bytes, g->model->ctx->pool, s) !=
+      cudaSuccess) {
     cudaGetLastError();
     delete sb;
     return fail(VOPP_E_NOMEM, "subtree device alloc");
@@ -1134,6 +1140,23 @@ int vopp_ctx_create(int device, size_t hbm_budget_bytes, uintptr_t cuda_stream, 
   c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
   c->slot.stream = c->stream;
   if (init_kernel_attributes() != cudaSuccess) { delete c; return fail(VOPP_E_CUDA, "kernel attributes"); }
+  {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    uint64_t keep = ~0ull;   // never return memory to the driver between allocations
+    int no = 0;              // reuse memory only when its free has completed: no cross-stream waits
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->pool) cudaMemPoolDestroy(c->pool);
+      delete c;
+      return fail(VOPP_E_CUDA, "memory pool");
+    }
+  }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
     c->sm_count = sms;
@@ -1150,6 +1173,7 @@ void vopp_ctx_destroy(vopp_ctx *c) {
   if (c->arena) cudaFree(c->arena);
   free_slot(c->slot);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->pool) cudaMemPoolDestroy(c->pool);   // released once its last allocation is freed
   delete c;
 }
 
@@ -1512,7 +1536,12 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
   g->N = n;
   g->seed = seed;
   bool ok = true;
-  auto al = [&](void **p, size_t b) { if (ok && cudaMalloc(p, b) != cudaSuccess) { cudaGetLastError(); ok = false; } };
+  // agent memory comes from the stream-ordered pool: creating or destroying an agent never
+  // synchronises the device (a serving loop keeps running while agents come and go)
+  cudaStream_t cs = c->stream;
+  auto al = [&](void **p, size_t b) {
+    if (ok && cudaMallocFromPoolAsync(p, b, c->pool, cs) != cudaSuccess) { cudaGetLastError(); ok = false; }
+  };
   const int kind = m->desc.kind;
   const size_t words = root_words(kind);
   float *blk = nullptr, *tblk = nullptr;      // root_words(kind) rows of n words
@@ -1531,19 +1560,19 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
     g->blk = blk;
     g->tblk = tblk;
   } else {
-    cudaFree(blk);
-    cudaFree(tblk);
+    if (blk) cudaFreeAsync(blk, cs);
+    if (tblk) cudaFreeAsync(tblk, cs);
   }
   al((void **)&g->lw, 4 * (size_t)n);
   al((void **)&g->tlw, 4 * (size_t)n);
   al((void **)&g->cdf, 8 * (size_t)n);
   al((void **)&g->anc, 4 * (size_t)n);
   al((void **)&g->dout, sizeof(BeliefOut));
-  if (ok && cudaMallocHost((void **)&g->hout, sizeof(BeliefOut)) != cudaSuccess) { cudaGetLastError(); ok = false; }
   if (!ok) { vopp_agent_destroy(g); return fail(VOPP_E_NOMEM, "agent device alloc"); }
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = cudaMemcpy(g->blk, states, 4 * words * (size_t)n, k);
-  if (e == cudaSuccess) e = cudaMemcpy(g->lw, lw.data(), 4 * (size_t)n, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpyAsync(g->blk, states, 4 * words * (size_t)n, k, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->lw, lw.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);   // lw is a local buffer
   if (e != cudaSuccess) { vopp_agent_destroy(g); return fail(VOPP_E_CUDA, "agent upload: %s", cudaGetErrorString(e)); }
   *out = g;
   return VOPP_OK;
@@ -1671,15 +1700,14 @@ int vopp_run_episode(vopp_agent *g, vopp_env *e, const vopp_plan_params *p, int3
 
 void vopp_agent_destroy(vopp_agent *g) {
   if (!g) return;
-  if (g->model) {
+  if (g->model) {   // stream-ordered frees: no device-wide synchronisation
     cudaStream_t s = g->model->ctx->stream;
     free_kept(g->tree, s);
     free_kept(g->sub, s);
-    cudaStreamSynchronize(s);
+    for (void *p : {(void *)g->blk, (void *)g->tblk, (void *)g->lw, (void *)g->tlw,
+                    (void *)g->cdf, (void *)g->anc, (void *)g->dout})
+      if (p) cudaFreeAsync(p, s);
   }
-  cudaFree(g->blk); cudaFree(g->tblk);
-  cudaFree(g->lw); cudaFree(g->tlw); cudaFree(g->cdf); cudaFree(g->anc); cudaFree(g->dout);
-  if (g->hout) cudaFreeHost(g->hout);
   delete g;
 }
 
@@ -1700,7 +1728,8 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
   if (!g->reuse) return run_jobs(c, jobs, out, nullptr);
   Job &j = jobs[0];
   attach_reuse(g, j);
-  if (cudaMallocAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, c->stream) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, c->pool, c->stream) !=
+      cudaSuccess) {
     cudaGetLastError();
     return fail(VOPP_E_NOMEM, "plan memory for the kept tree");
   }
@@ -1751,13 +1780,14 @@ int vopp_agent_plan_episodes(vopp_agent *g, const vopp_episode_params *p, double
   return vopp::run_plan_episodes(g->model, in, *p, budget_s, out, depth_reached, n_nodes);
 }
 
-int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,
-                       int32_t *resampled_out) {
-  if (!g || !obs) return fail(VOPP_E_INVALID, "NULL argument");
-  vopp_model *m = g->model;
-  if (action < 0 || action >= m->A) return fail(VOPP_E_INVALID, "action %d", action);
-  vopp_ctx *c = m->ctx;
-  cudaSetDevice(c->device);
+}  // extern "C"
+
+namespace {
+
+// The SIR kernel's arguments for agent g under (action, obs); obs is a host pointer (NAV2D
+// float[2], other models int32[1]).  The result goes to `out` (device).
+BeliefArgs belief_args(vopp_agent *g, int32_t action, const void *obs, BeliefOut *out) {
+  const vopp_model *m = g->model;
   BeliefArgs B;
   std::memset(&B, 0, sizeof B);
   B.kind = m->desc.kind;
@@ -1778,31 +1808,57 @@ int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *e
     B.pf = g->pf; B.tpf = g->tpf;
     B.obs_i = *static_cast<const int32_t *>(obs);
   }
-  if (g->reuse) {
-    // subtree reuse: a kept tree's branch of this action that sampled this very observation
-    // becomes the belief (its particle set, as the tree holds it), and its subtree is kept
-    const int slot = matching_branch(g, action, B.obs_f, B.obs_i, c->stream);
-    free_kept(g->sub, c->stream);
-    g->adopted_slot = -1;
-    if (slot >= 0) {
-      const int rc = adopt_subtree(g, slot, c->stream);
-      free_kept(g->tree, c->stream);
-      if (rc) return rc;
-      CUDA_TRY(cudaStreamSynchronize(c->stream));
-      g->adopted_slot = slot;
-      g->t += 1;
-      if (ess_out) *ess_out = -1.0;
-      if (resampled_out) *resampled_out = 0;
-      return VOPP_OK;
-    }
-    free_kept(g->tree, c->stream);
-  }
   B.lw = g->lw;
   B.tlw = g->tlw;
   B.cdf = g->cdf;
   B.anc = g->anc;
   B.model = m->dev;
-  B.out = g->dout;
+  B.out = out;
+  return B;
+}
+
+// Subtree reuse at a belief update: adopt the matching branch of the kept tree (slot >= 0,
+// its subtree kept) or release what the agent kept (slot < 0: the SIR update follows).
+int reuse_update(vopp_agent *g, int slot, cudaStream_t s) {
+  free_kept(g->sub, s);
+  g->adopted_slot = -1;
+  if (slot < 0) {
+    free_kept(g->tree, s);
+    return VOPP_OK;
+  }
+  const int rc = adopt_subtree(g, slot, s);
+  free_kept(g->tree, s);
+  if (rc) return rc;
+  g->adopted_slot = slot;
+  return VOPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,
+                       int32_t *resampled_out) {
+  if (!g || !obs) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_model *m = g->model;
+  if (action < 0 || action >= m->A) return fail(VOPP_E_INVALID, "action %d", action);
+  vopp_ctx *c = m->ctx;
+  cudaSetDevice(c->device);
+  BeliefArgs B = belief_args(g, action, obs, g->dout);
+  if (g->reuse) {
+    // subtree reuse: a kept tree's branch of this action that sampled this very observation
+    // becomes the belief (its particle set, as the tree holds it), and its subtree is kept
+    const int slot = matching_branch(g, action, B.obs_f, B.obs_i, c->stream);
+    const int rc = reuse_update(g, slot, c->stream);
+    if (rc) return rc;
+    if (slot >= 0) {
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+      g->t += 1;
+      if (ess_out) *ess_out = -1.0;
+      if (resampled_out) *resampled_out = 0;
+      return VOPP_OK;
+    }
+  }
   TimedLaunch tl;
   timed_begin(c, F_BELIEF, tl);
   cudaError_t e = launch_belief(B, c->stream);
@@ -1810,13 +1866,129 @@ int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *e
   c->d2h_bytes += sizeof(BeliefOut);
   timed_end(c, tl);
   if (e != cudaSuccess) return fail(VOPP_E_CUDA, "belief launch: %s", cudaGetErrorString(e));
-  CUDA_TRY(cudaMemcpyAsync(g->hout, g->dout, sizeof(BeliefOut), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(&g->hout, g->dout, sizeof(BeliefOut), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   timed_collect(c);
-  if (g->hout->status) return fail(VOPP_E_DEGENERATE, "observation has zero likelihood under every particle");
-  if (ess_out) *ess_out = g->hout->ess;
-  if (resampled_out) *resampled_out = g->hout->resampled;
+  if (g->hout.status) return fail(VOPP_E_DEGENERATE, "observation has zero likelihood under every particle");
+  if (ess_out) *ess_out = g->hout.ess;
+  if (resampled_out) *resampled_out = g->hout.resampled;
   g->t += 1;
+  return VOPP_OK;
+}
+
+int vopp_belief_update_batch(vopp_ctx *c, int32_t n, vopp_agent *const *agents,
+                             const int32_t *actions, const void *const *obs, double *ess_out,
+                             int32_t *resampled_out, int32_t *status_out) {
+  if (!c || n < 0) return fail(VOPP_E_INVALID, "bad batch arguments");
+  if (n == 0) return VOPP_OK;
+  if (!agents || !actions || !obs || !status_out) return fail(VOPP_E_INVALID, "NULL argument");
+  {
+    std::vector<const vopp_agent *> seen(agents, agents + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(VOPP_E_INVALID, "an agent appears twice in the batch");
+  }
+  for (int i = 0; i < n; ++i) {
+    const vopp_agent *g = agents[i];
+    if (!g || !obs[i]) return fail(VOPP_E_INVALID, "NULL agent or observation at %d", i);
+    if (g->model->ctx != c) return fail(VOPP_E_INVALID, "agent %d belongs to another context", i);
+    if (actions[i] < 0 || actions[i] >= g->model->A) return fail(VOPP_E_INVALID, "action %d at %d", actions[i], i);
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t s = c->stream;
+  std::vector<BeliefArgs> args(n);
+  for (int i = 0; i < n; ++i) args[i] = belief_args(agents[i], actions[i], obs[i], nullptr);
+
+  // subtree reuse: the kept trees' level-1 observations of the agents' actions, one copy
+  // each and one synchronisation for all, then adoptions
+  std::vector<int> slot(n, -1);
+  {
+    std::vector<int> asked;
+    std::vector<float> ob;
+    std::vector<size_t> at(n, 0);
+    for (int i = 0; i < n; ++i) {
+      const KeptTree *t = agents[i]->reuse ? agents[i]->tree : nullptr;
+      if (!t || t->shape.mat_top < 1 || t->lay.obs[1] == kNone) continue;
+      at[i] = ob.size();
+      ob.resize(ob.size() + 2 * (size_t)t->shape.W);
+      asked.push_back(i);
+    }
+    for (int i : asked) {
+      const KeptTree *t = agents[i]->tree;
+      CUDA_TRY(cudaMemcpyAsync(ob.data() + at[i], t->mem + t->lay.obs[1] + 8 * (size_t)actions[i] * t->shape.W,
+                               8 * (size_t)t->shape.W, cudaMemcpyDeviceToHost, s));
+    }
+    if (!asked.empty()) CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i : asked) {
+      const KeptTree *t = agents[i]->tree;
+      for (int k = 0; k < t->shape.W; ++k) {
+        const float *o = ob.data() + at[i] + 2 * k;
+        const bool eq = (t->shape.kind == kNav) ? (o[0] == args[i].obs_f[0] && o[1] == args[i].obs_f[1])
+                                                : ((int)o[0] == args[i].obs_i);
+        if (eq) { slot[i] = actions[i] * t->shape.W + k; break; }
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      status_out[i] = VOPP_OK;
+      if (!agents[i]->reuse) continue;
+      const int rc = reuse_update(agents[i], slot[i], s);
+      if (rc) { status_out[i] = rc; slot[i] = -2; }   // failed adoption: no update
+    }
+  }
+
+  // SIR for every other agent: one CTA each in one launch
+  std::vector<int> sir;
+  for (int i = 0; i < n; ++i) if (slot[i] == -1) sir.push_back(i);
+  const int ns = (int)sir.size();
+  std::vector<BeliefOut> hres(ns);
+  if (ns > 0) {
+    char *mem = nullptr;
+    const size_t res_off = align_up(sizeof(BeliefArgs) * ns, 256);
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&mem), res_off + sizeof(BeliefOut) * ns, c->pool, s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return fail(VOPP_E_NOMEM, "batch arguments");
+    }
+    BeliefArgs *dargs = reinterpret_cast<BeliefArgs *>(mem);
+    BeliefOut *dres = reinterpret_cast<BeliefOut *>(mem + res_off);
+    std::vector<BeliefArgs> sargs(ns);
+    for (int q = 0; q < ns; ++q) { sargs[q] = args[sir[q]]; sargs[q].out = dres + q; }
+    TimedLaunch tl;
+    timed_begin(c, F_BELIEF, tl);
+    cudaError_t e = cudaMemcpyAsync(dargs, sargs.data(), sizeof(BeliefArgs) * ns, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_belief_batch(dargs, ns, s);
+    timed_end(c, tl);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hres.data(), dres, sizeof(BeliefOut) * ns, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(mem, s);
+    c->launches += 1;
+    c->h2d_bytes += sizeof(BeliefArgs) * ns;
+    c->d2h_bytes += sizeof(BeliefOut) * ns;
+    if (e != cudaSuccess) return fail(VOPP_E_CUDA, "batched belief update: %s", cudaGetErrorString(e));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  timed_collect(c);
+  for (int i = 0; i < n; ++i) {
+    if (ess_out) ess_out[i] = 0.0;
+    if (resampled_out) resampled_out[i] = 0;
+    if (slot[i] >= 0) {                    // adopted
+      agents[i]->t += 1;
+      if (ess_out) ess_out[i] = -1.0;
+    }
+  }
+  int first = VOPP_OK;
+  for (int q = 0; q < ns; ++q) {
+    const int i = sir[q];
+    if (hres[q].status) {
+      status_out[i] = VOPP_E_DEGENERATE;
+    } else {
+      agents[i]->t += 1;
+      if (ess_out) ess_out[i] = hres[q].ess;
+      if (resampled_out) resampled_out[i] = hres[q].resampled;
+    }
+  }
+  for (int i = 0; i < n; ++i) if (status_out[i] && !first) first = status_out[i];
+  if (first) return fail(first, "belief update failed for some agents (see status_out)");
   return VOPP_OK;
 }
 
@@ -1895,10 +2067,13 @@ struct vopp_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
+  std::atomic<bool> stop_flag{false};   // stop, readable without the lock
   bool paused = false;          // queue requests without starting batches
   std::deque<ServerReq> pending;
+  std::atomic<size_t> n_pending{0};   // pending.size(), readable without the lock
   std::unordered_map<uint64_t, Done> done;
   std::deque<uint64_t> completion_order;   // tickets in the order their plans finished
+  std::atomic<size_t> n_order{0};          // completion_order.size(), readable without the lock
   uint64_t next_ticket = 1;
   vopp_server_stats stats{};
   int worker_error = VOPP_OK;
@@ -1924,30 +2099,48 @@ void post_failure(vopp_server *srv, std::vector<ServerReq> &batch, int rc) {
     srv->done[r.ticket] = Done{rc, failed_result(), r.t_submit, t};
     srv->completion_order.push_back(r.ticket);
   }
+  srv->n_order.store(srv->completion_order.size());
 }
 
-// Post the results of a finished slot (lock held).  The results are in the slot's pinned
-// mirror: the stream copied them back before the slot's event.
-void harvest(vopp_server *srv, ServerSlot *s, bool ok) {
+// A finished slot's outcomes, gathered without the lock (worker thread): the results are
+// in the slot's pinned mirror (the stream copied them back before the slot's event), and
+// agents that keep their trees take their plan's memory.
+struct Harvest {
+  std::vector<std::pair<uint64_t, Done>> done;
+  unsigned long long steps = 0;
+  int completed = 0;
+};
+Harvest gather(vopp_server *srv, ServerSlot *s, bool ok) {
+  Harvest h;
   const int n = (int)s->jobs.size();
+  const double t = now_s();
   if (ok) {
     std::vector<vopp_plan_result> outs(n);
     std::vector<int> st(n);
     collect_results(srv->c, s->slot, s->jobs, outs.data(), st.data(), false);
-    for (int i = 0; i < n; ++i)   // agents with subtree reuse keep their plan's tree
-      if (s->jobs[i].agent) keep_tree(s->jobs[i].agent, s->jobs[i], st[i] == VOPP_OK, s->slot.stream);
-    const double t = now_s();
     for (int i = 0; i < n; ++i) {
-      srv->done[s->reqs[i].ticket] = Done{st[i], outs[i], s->reqs[i].t_submit, t};
-      srv->completion_order.push_back(s->reqs[i].ticket);
-      srv->stats.completed += 1;
-      srv->stats.particle_steps += outs[i].particle_steps;
+      if (s->jobs[i].agent) keep_tree(s->jobs[i].agent, s->jobs[i], st[i] == VOPP_OK, s->slot.stream);
+      h.done.emplace_back(s->reqs[i].ticket, Done{st[i], outs[i], s->reqs[i].t_submit, t});
+      h.steps += outs[i].particle_steps;
     }
+    h.completed = n;
   } else {
     for (auto &j : s->jobs)
       if (j.agent) keep_tree(j.agent, j, false, s->slot.stream);
-    post_failure(srv, s->reqs, VOPP_E_CUDA);
+    for (auto &r : s->reqs) h.done.emplace_back(r.ticket, Done{VOPP_E_CUDA, failed_result(), r.t_submit, t});
   }
+  return h;
+}
+
+// Post a gathered slot and free the slot (lock held).
+void post(vopp_server *srv, ServerSlot *s, Harvest &h) {
+  for (auto &d : h.done) {
+    srv->done[d.first] = d.second;
+    srv->completion_order.push_back(d.first);
+  }
+  srv->n_order.store(srv->completion_order.size());
+  srv->stats.completed += h.completed;
+  srv->stats.particle_steps += h.steps;
   srv->in_flight -= s->arena_bytes;
   s->arena = nullptr;
   s->arena_bytes = 0;
@@ -1967,6 +2160,7 @@ std::vector<ServerReq> take_batch(vopp_server *srv, size_t *bytes_out) {
       if (batch.empty() && srv->in_flight == 0) {   // can never fit: refuse it
         srv->done[r.ticket] = Done{VOPP_E_BUDGET, failed_result(), r.t_submit, now_s()};
         srv->completion_order.push_back(r.ticket);
+        srv->n_order.store(srv->completion_order.size());
         srv->stats.rejected += 1;
         srv->pending.pop_front();
         continue;
@@ -1978,6 +2172,7 @@ std::vector<ServerReq> take_batch(vopp_server *srv, size_t *bytes_out) {
     srv->pending.pop_front();
   }
   srv->in_flight += bytes;
+  srv->n_pending.store(srv->pending.size());
   *bytes_out = bytes;
   return batch;
 }
@@ -1994,10 +2189,12 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
   }
   const size_t arena_bytes = place_jobs(jobs);
   char *arena = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&arena), arena_bytes, s->slot.stream);
+  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&arena), arena_bytes, srv->c->pool,
+                                          s->slot.stream);
   for (auto &j : jobs)   // plans whose agents keep their trees get memory of their own
     if (e == cudaSuccess && j.agent)
-      e = cudaMallocAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, s->slot.stream);
+      e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, srv->c->pool,
+                                  s->slot.stream);
   int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false, nullptr) : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
     if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
@@ -2056,15 +2253,29 @@ constexpr double kSpinIdle = 250e-6;
 
 void worker_main(vopp_server *srv) {
   cudaSetDevice(srv->c->device);
-  std::unique_lock<std::mutex> lock(srv->mu);
   double idle_since = now_s();
+  std::vector<ServerSlot *> fin;
+  std::vector<Harvest> hv;
   for (;;) {
-    bool posted = false;
+    // finished slots: polled and gathered without the lock (slot state is this thread's)
+    fin.clear();
+    hv.clear();
     for (auto *s : srv->slots) {
       if (!s->busy) continue;
       const int st = slot_state(s);
-      if (st != 0) { harvest(srv, s, st > 0); posted = true; }
+      if (st != 0) { fin.push_back(s); hv.push_back(gather(srv, s, st > 0)); }
     }
+    int busy_now = 0;
+    for (auto *s : srv->slots) busy_now += s->busy;
+    if (fin.empty() && busy_now > 0 && (srv->n_pending.load() == 0 || busy_now == (int)srv->slots.size()) &&
+        !srv->stop_flag.load()) {
+      std::this_thread::yield();   // nothing to post or start: poll again without the lock
+      idle_since = now_s();
+      continue;
+    }
+    std::unique_lock<std::mutex> lock(srv->mu);
+    bool posted = !fin.empty();
+    for (size_t i = 0; i < fin.size(); ++i) post(srv, fin[i], hv[i]);
     for (;;) {
       if (srv->pending.empty() || (srv->paused && !srv->stop)) break;
       bool any_free = false;
@@ -2087,7 +2298,7 @@ void worker_main(vopp_server *srv) {
         posted = true;
         continue;
       }
-      s->arena_bytes = bytes;                   // the reservation is released at harvest
+      s->arena_bytes = bytes;                   // the reservation is released at post
       s->reqs = std::move(batch);
       srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
       srv->stats.batches += 1;
@@ -2100,24 +2311,26 @@ void worker_main(vopp_server *srv) {
     if (srv->stop) {
       if (busy == 0 && srv->pending.empty()) break;
       // shutting down: wait (bounded) for the busy slots rather than polling at full rate
+      lock.unlock();
       for (auto *s : srv->slots) {
         if (!s->busy) continue;
-        lock.unlock();
         int st = 0;
         for (int spins = 0; (st = slot_state(s)) == 0 && spins < 200000; ++spins)   // <= ~10 s
           std::this_thread::sleep_for(std::chrono::microseconds(50));
+        Harvest h = gather(srv, s, st > 0);
         lock.lock();
         if (st == 0) srv->worker_error = VOPP_E_TIMEOUT;   // gave up on this batch
-        harvest(srv, s, st > 0);
+        post(srv, s, h);
+        lock.unlock();
       }
+      lock.lock();
       srv->cv_done.notify_all();
       continue;
     }
     if (busy || now_s() - idle_since < kSpinIdle) {
-      // batches in flight, or only just idle: poll again after letting callers in
+      // batches in flight, or only just idle: poll again, without holding the lock
       lock.unlock();
       std::this_thread::yield();
-      lock.lock();
     } else {
       srv->cv_work.wait_for(lock, std::chrono::milliseconds(1), [&] {
         return srv->stop || (!srv->pending.empty() && !srv->paused);
@@ -2135,6 +2348,7 @@ int submit_req(vopp_server *srv, ServerReq &&r, uint64_t *ticket) {
     *ticket = r.ticket;
     srv->stats.submitted += 1;
     srv->pending.push_back(std::move(r));
+    srv->n_pending.store(srv->pending.size());
   }
   srv->cv_work.notify_one();
   return VOPP_OK;
@@ -2155,11 +2369,6 @@ int vopp_server_create(vopp_ctx *c, int32_t max_batch, int32_t n_slots, size_t h
   srv->c = c;
   srv->max_batch = max_batch;
   srv->budget = hbm_budget_bytes ? hbm_budget_bytes : c->budget;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
-    uint64_t thr = ~0ull;   // keep freed arenas in the pool for the next batch
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
   for (int i = 0; i < n_slots; ++i) {
     ServerSlot *s = new (std::nothrow) ServerSlot;
     int prio_lo = 0, prio_hi = 0;   // numerically lower = higher priority
@@ -2195,6 +2404,7 @@ void vopp_server_destroy(vopp_server *srv) {
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     srv->stop = true;
+    srv->stop_flag.store(true);
   }
   srv->cv_work.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
@@ -2263,8 +2473,11 @@ int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_res
               double *latency_s) {
   if (!srv) return fail(VOPP_E_INVALID, "server is NULL");
   std::unique_lock<std::mutex> lock(srv->mu);
-  const bool ok = srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
-                                        [&] { return srv->done.count(ticket) > 0; });
+  auto ready = [&] { return srv->done.count(ticket) > 0; };
+  // a zero timeout only looks (a timed wait would still sleep for the kernel's timer slack)
+  const bool ok = timeout_s > 0.0
+                      ? srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready)
+                      : ready();
   if (!ok) return fail(VOPP_E_TIMEOUT, "ticket not completed within the timeout");
   return take_done(srv, ticket, out, latency_s);
 }
@@ -2272,16 +2485,24 @@ int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_res
 int vopp_wait_any(vopp_server *srv, double timeout_s, uint64_t *ticket, vopp_plan_result *out,
                   double *latency_s) {
   if (!srv || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
+  // a zero-timeout poll with nothing finished answers without the lock, so that a caller
+  // polling in a loop never holds up the worker
+  if (!(timeout_s > 0.0) && srv->n_order.load() == 0)
+    return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
   std::unique_lock<std::mutex> lock(srv->mu);
   auto ready = [&] {
     while (!srv->completion_order.empty() && !srv->done.count(srv->completion_order.front()))
       srv->completion_order.pop_front();   // already taken by vopp_poll / vopp_wait
+    srv->n_order.store(srv->completion_order.size());
     return !srv->completion_order.empty();
   };
-  if (!srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready))
-    return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
+  const bool ok = timeout_s > 0.0
+                      ? srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready)
+                      : ready();   // a zero timeout only looks
+  if (!ok) return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
   *ticket = srv->completion_order.front();
   srv->completion_order.pop_front();
+  srv->n_order.store(srv->completion_order.size());
   return take_done(srv, *ticket, out, latency_s);
 }
 

@@ -65,6 +65,8 @@ cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long 
                         size_t smem, int threads, long long grid, cudaStream_t s);
 cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
+// n updates, args in device memory (one CTA each, the same arithmetic as launch_belief)
+cudaError_t launch_belief_batch(const BeliefArgs *d_args, int n, cudaStream_t s);
 cudaError_t launch_env(const EnvArgs &E, cudaStream_t s);
 
 }  // namespace vopp

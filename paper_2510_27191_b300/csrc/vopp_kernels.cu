@@ -1225,6 +1225,21 @@ __global__ void __launch_bounds__(1024) k_belief(BeliefArgs B) {
   }
 }
 
+// Belief updates of many agents in one launch: CTA b updates agent b exactly as k_belief
+// would (same block size, same reduction order).
+__global__ void __launch_bounds__(1024) k_belief_batch(const BeliefArgs *args) {
+  __shared__ float red[32];
+  __shared__ double dred[1025];
+  const BeliefArgs &B = args[blockIdx.x];
+  const DevModel &dm = *B.model;
+  switch (B.kind) {
+    case kNav: belief_plan<NavModel>(B, dm, red, dred); break;
+    case kGrid: belief_plan<GridModel>(B, dm, red, dred); break;
+    case kCrowd: belief_plan<CrowdModel>(B, dm, red, dred); break;
+    default: belief_plan<ToyModel>(B, dm, red, dred); break;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // K7: one environment step of the closed loop (Alg. 1: execute the action, perceive the
 // observation).  The true state steps under the model's own transition and observation
@@ -1369,6 +1384,12 @@ cudaError_t launch_env(const EnvArgs &E, cudaStream_t s) {
 
 cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s) {
   k_belief<<<1, 1024, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_belief_batch(const BeliefArgs *d_args, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_belief_batch<<<n, 1024, 0, s>>>(d_args);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@ Only argument marshalling and timing happen here; every plan runs in libvopp's k
 """
 from __future__ import annotations
 
+import gc
 import time
 
 import numpy as np
@@ -77,14 +78,24 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
 
 def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int = 1024,
               seed: int = 11, mode: str = "served", deadline_s: float = 0.05, max_batch: int = 64,
-              n_slots: int = 3, drain_factor: float = 3.0):
+              n_slots: int = 3, drain_factor: float = 3.0, reuse: bool = False):
     """Poisson arrivals at `rate` per second over `n_agents` agents for `seconds`; each
-    agent's requests are served in order, a belief update follows every completed plan."""
+    agent's requests are served in order, a belief update follows every completed plan.
+    Served mode updates the agents of all plans that finished together in one batched call;
+    reuse: agents keep their trees (subtree reuse)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x73657276]))
     specs = WL.draw_mixed_plans(n_agents, seed, WL.SERVE_CAP_STEPS)
     models = make_models(V, ctx)
-    agents = [V.vopp_agent_create(models[ps.kind], _root(ps), None, ps.N, 1000003 * (i + 1))
-              for i, ps in enumerate(specs)]
+
+    def new_agent(i, salt=0):
+        ps = specs[i]
+        g = V.vopp_agent_create(models[ps.kind], _root(ps), None, ps.N, 1000003 * (i + 1) + salt)
+        if reuse:
+            V.vopp_agent_set_reuse(g, True)
+        return g
+
+    agents = [new_agent(i) for i in range(n_agents)]
+    reused = 0
     n_req = rng.poisson(rate * seconds)
     arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
     who = [int(v) for v in rng.integers(0, n_agents, n_req)]
@@ -117,8 +128,7 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
         nonlocal resets
         ps = specs[i]
         V.vopp_agent_destroy(agents[i])
-        agents[i] = V.vopp_agent_create(models[ps.kind], _root(ps), None, ps.N,
-                                        1000003 * (i + 1) + 17 * resets)
+        agents[i] = new_agent(i, 17 * resets)
         resets += 1
 
     def issue(i):
@@ -127,26 +137,43 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
         seed_i = (i + 1) * 7919 + int(plan_count[i])
         return V.vopp_submit_agent(srv, agents[i], ps.D, ps.W, ps.eta, ps.gamma, seed_i)
 
+    # the timed loop runs with Python's cyclic garbage collector off (its pauses would show
+    # up as request latency); reference counting still frees everything the loop drops
+    gc_was_on = gc.isenabled()
+    gc.disable()
     t0 = time.perf_counter()
     k = 0
     if mode == "served":
         # event-driven: a request is submitted the moment it arrives (or, if its agent has a
         # plan in flight, the moment that plan's belief update is done); between events the
         # loop polls for completions and arrivals
-        def finish(t, rc, res):
-            if rc not in (V.VOPP_OK, V.VOPP_E_DEGENERATE):
-                V.check(rc)
-            i, arr = inflight.pop(t)
-            lat.append(time.perf_counter() - t0 - arr)
-            nonlocal_steps[0] += res["particle_steps"] if res is not None else 0
-            if res is None:
-                reset(i)
-            else:
-                after_plan(i, res)
-            busy[i] = False
-            if queues[i]:
-                inflight[issue(i)] = (i, queues[i].pop(0))
-                busy[i] = True
+        def finish(done):
+            """Completed plans: latencies, one batched belief update, next requests."""
+            nonlocal updates, reused
+            upd, freed = [], []
+            for t, rc, res in done:
+                if rc not in (V.VOPP_OK, V.VOPP_E_DEGENERATE):
+                    V.check(rc)
+                i, arr = inflight.pop(t)
+                freed.append(i)
+                lat.append(time.perf_counter() - t0 - arr)
+                if res is None:
+                    reset(i)
+                else:
+                    nonlocal_steps[0] += res["particle_steps"]
+                    reused += bool(res["flags"] & V.VOPP_FLAG_REUSED)
+                    a = max(int(res["action"]), 0)
+                    upd.append((i, a, obs_for(specs[i], a)))
+            if upd:
+                st, _, _ = V.vopp_belief_update_batch(
+                    ctx, [agents[i] for i, _, _ in upd], [a for _, a, _ in upd],
+                    [o for _, _, o in upd], [specs[i].kind for i, _, _ in upd])
+                updates += int(np.sum(st == V.VOPP_OK))   # impossible observation: unchanged
+            for i in freed:
+                busy[i] = False
+                if queues[i]:
+                    inflight[issue(i)] = (i, queues[i].pop(0))
+                    busy[i] = True
 
         nonlocal_steps = [0]
         while True:
@@ -171,12 +198,13 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
                     while time.perf_counter() - t0 < arrivals[k]:
                         pass                           # idle until the next arrival
                 continue
-            finish(got[0], got[1], got[2])
-            while inflight:                            # everything else already finished
+            done = [got[:3]]
+            while len(done) < len(inflight):           # everything else already finished
                 got = V.vopp_wait_any(srv, 0.0)
                 if got is None:
                     break
-                finish(got[0], got[1], got[2])
+                done.append(got[:3])
+            finish(done)
         steps_done = nonlocal_steps[0]
     else:
         # plain path: requests run alone, synchronously, in arrival order (an agent's earlier
@@ -200,10 +228,13 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
                 reset(i)
             else:
                 steps_done += res["particle_steps"]
+                reused += bool(res["flags"] & V.VOPP_FLAG_REUSED)
                 after_plan(i, res)
             if time.perf_counter() - t0 > seconds * drain_factor:
                 break                                  # overloaded: stop draining
     wall = time.perf_counter() - t0
+    if gc_was_on:
+        gc.enable()
     stats = V.vopp_server_get_stats(srv) if srv else {}
     if srv:
         V.vopp_server_destroy(srv)
@@ -218,6 +249,7 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
            "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
            "deadline_misses": int(np.sum(lat > deadline_s)), "belief_updates": updates,
+           "reused_plans": int(reused), "subtree_reuse": bool(reuse),
            "episodes_restarted": resets,
            "offered_rate": rate, "agents": n_agents, "seconds": seconds}
     if stats:

@@ -182,6 +182,9 @@ def _load():
                                      ctypes.POINTER(vopp_plan_result), ctypes.POINTER(i32)],
                                     ctypes.c_int),
         "vopp_agent_set_reuse": ([vp, i32], ctypes.c_int),
+        "vopp_belief_update_batch": ([vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                      ctypes.POINTER(vp), dp, ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32)], ctypes.c_int),
         "vopp_agent_reuse_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)], ctypes.c_int),
     }
@@ -402,6 +405,35 @@ def vopp_belief_update(agent: int, action: int, obs, kind: int):
 
 def _state_words(kind: int) -> int:
     return {VOPP_NAV2D: 2, VOPP_CROWD: 15}.get(kind, 1)
+
+
+def vopp_belief_update_batch(ctx: int, agents, actions, obs, kinds):
+    """Update agents[i] with (actions[i], obs[i]) for every i in one call (kinds[i]: the
+    agent's model kind, which fixes the observation's type).  Returns (status, ess,
+    resampled) arrays; a failing update shows in its status, not as an exception."""
+    n = len(agents)
+    keep = []
+    ptrs = (ctypes.c_void_p * n)()
+    for i, (o, k) in enumerate(zip(obs, kinds)):
+        if k == VOPP_NAV2D:
+            b = (ctypes.c_float * 2)(float(o[0]), float(o[1]))
+        else:
+            b = (ctypes.c_int32 * 1)(int(np.atleast_1d(o)[0]))
+        keep.append(b)
+        ptrs[i] = ctypes.cast(b, ctypes.c_void_p)
+    ags = (ctypes.c_void_p * n)(*agents)
+    acts = (ctypes.c_int32 * n)(*[int(a) for a in actions])
+    ess = np.zeros(n, dtype=np.float64)
+    res = np.zeros(n, dtype=np.int32)
+    st = np.zeros(n, dtype=np.int32)
+    rc = lib.vopp_belief_update_batch(ctx, n, ags, acts, ptrs,
+                                      ess.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      res.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc not in (VOPP_OK, VOPP_E_DEGENERATE):
+        check(rc)
+    del keep
+    return st, ess, res.astype(bool)
 
 
 def vopp_agent_set_reuse(agent: int, enable: bool = True) -> None:

@@ -98,3 +98,65 @@ def test_belief_update_degenerate_is_reported():
         V.vopp_model_destroy(model)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_batched_update_equals_single_updates():
+    """vopp_belief_update_batch over mixed agents (NAV2D and GRID, several N, one agent with
+    an impossible observation, one with subtree reuse that adopts) equals the same updates
+    made one by one, bit for bit, and leaves the failing agent's belief unchanged."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        rx, ry = WL.grid_layout(2)
+        nav = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
+        grid = V.vopp_create_model(ctx, V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry))
+        specs = []          # (kind, model, states, N, action, obs, reuse)
+        for i, n in enumerate((128, 1000, 4096)):
+            x, y, _ = WL.nav_root(n, 10 + i)
+            specs.append((WL.NAV2D, nav, np.concatenate([x, y]).astype(np.float32), n, i % 4,
+                          (2.0 + i, 3.0), False))
+        for i, n in enumerate((256, 2048)):
+            s, _ = WL.grid_root(n, 20 + i)
+            specs.append((WL.GRID, grid, np.asarray(s, np.int32), n, 5 + i, 1 + i, False))
+        s, _ = WL.grid_root(300, 30)
+        specs.append((WL.GRID, grid, np.asarray(s, np.int32), 300, 0, 1, False))  # move: obs 1 impossible
+        s, _ = WL.grid_root(512, 31)
+        specs.append((WL.GRID, grid, np.asarray(s, np.int32), 512, 2, 0, True))   # reuse: adopts
+
+        def make():
+            out = []
+            for j, (kind, model, st, n, a, o, reuse) in enumerate(specs):
+                g = V.vopp_agent_create(model, st, None, n, 500 + j)
+                if reuse:
+                    V.vopp_agent_set_reuse(g, True)
+                    V.vopp_agent_plan(g, model, 3, 2, 1.0, 0.95, 8)
+                out.append(g)
+            return out
+
+        single, batched = make(), make()
+        st_single = []
+        for g, (kind, model, st, n, a, o, reuse) in zip(single, specs):
+            try:
+                ess, res = V.vopp_belief_update(g, a, o, kind)
+                st_single.append((V.VOPP_OK, ess, res))
+            except V.VoppError as e:
+                st_single.append((e.code, 0.0, False))
+        status, ess, res = V.vopp_belief_update_batch(ctx, batched, [p[4] for p in specs],
+                                                      [p[5] for p in specs], [p[0] for p in specs])
+        for j, (g1, g2, sp) in enumerate(zip(single, batched, specs)):
+            assert status[j] == st_single[j][0], j
+            if status[j] == V.VOPP_OK:
+                assert ess[j] == st_single[j][1] and res[j] == st_single[j][2], j
+            p1, p2 = V.vopp_agent_get_particles(g1, sp[0]), V.vopp_agent_get_particles(g2, sp[0])
+            for a1, a2 in zip(p1[:2], p2[:2]):
+                np.testing.assert_array_equal(a1, a2)
+            if status[j] == V.VOPP_OK and ess[j] > 0:
+                np.testing.assert_array_equal(p1[2], p2[2])
+        assert status[5] == V.VOPP_E_DEGENERATE
+        assert ess[6] == -1.0 and V.vopp_agent_reuse_info(batched[6])["adopted_slot"] >= 0
+        for g in single + batched:
+            V.vopp_agent_destroy(g)
+        V.vopp_model_destroy(nav)
+        V.vopp_model_destroy(grid)
+    finally:
+        V.vopp_ctx_destroy(ctx)
