@@ -241,7 +241,8 @@ def _config(spec, args):
                         f"eta={spec.eta} gamma={spec.gamma} pi={'softmax(-dist/2)' if spec.pi_mode == WL.PI_NAV_SOFTMAX_DIST else 'uniform'}",
             "particle_steps_per_plan": spec.steps, "leaves": (spec.A * spec.W) ** spec.D,
             "root_particles": spec.N, "depth": spec.D, "branches": spec.A * spec.W,
-            "l2": "flushed before every step (256 MB write)", "parallelism": f"replicas{args.gpus}"}
+            "l2": "flushed before every step (256 MB write)",
+            "parallelism": f"replicas{args.gpus if args else 1}"}
 
 
 def cpu_baseline(spec, budget_s=20.0):
@@ -287,6 +288,56 @@ def cpu_baseline(spec, budget_s=20.0):
             "sample": f"{n} level-1 subtrees (of {AW}; indices taken modulo {AW}) of the same "
                       f"plan, {done} particle-steps, FP64, {threads} threads, {dt:.1f} s; "
                       f"single thread: {n1} subtrees, {done1} particle-steps, {dt1:.1f} s"}
+
+
+def config_leg(V, ctx, name, steps, warmup=1):
+    """One configured workload at full size on this context: event-timed plans (L2 flushed
+    before each), then the same plans with per-kernel events for its leaf kernel's roofline."""
+    import torch
+    spec = WORKLOADS[name]
+    rx, ry = WL.grid_layout(spec.layout_seed)
+    model = V.vopp_create_model(ctx, V.make_desc(spec.kind, pi_mode=spec.pi_mode,
+                                                 pi_temp=spec.pi_temp,
+                                                 rock_x=rx if spec.kind == WL.GRID else None,
+                                                 rock_y=ry if spec.kind == WL.GRID else None))
+    states = torch.from_numpy(_host_states(spec, _root_arrays(spec))).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(n):
+        ts = []
+        for i in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            V.vopp_plan(model, states, None, spec.N, spec.D, spec.W, spec.eta, spec.gamma, None,
+                        spec.seed + i)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    run(warmup)
+    ts = run(steps)
+    V.vopp_ctx_set_timing(ctx, True)
+    V.vopp_ctx_reset_kernel_times(ctx)
+    run(steps)
+    kt = V.vopp_ctx_kernel_times(ctx)
+    V.vopp_ctx_set_timing(ctx, False)
+    V.vopp_model_destroy(model)
+    leaf_ms, leaf_n = kt["leaf"]
+    leaf_s = leaf_ms / max(leaf_n, 1) / 1e3
+    AW = spec.A * spec.W
+    leaf_steps = (AW ** spec.D + (AW ** (spec.D - 1) if spec.D >= 2 else 0)) * spec.N
+    pk, _ = peaks()
+    peak_ops = SMS * LANES_PER_CLK * float(pk.get("sm_max_mhz", 2032.0)) * 1e6
+    ms = float(np.median(ts))
+    return {"workload": _config(spec, None)["workload"], "plans": steps,
+            "ms_per_plan": ms, "particle_steps": spec.steps,
+            "particle_steps_per_s": spec.steps / (ms / 1e3),
+            "leaf": {"avg_launch_ms": leaf_s * 1e3, "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
+                     "frac": ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_s / peak_ops,
+                     "share_of_plan": leaf_ms / max(sum(v[0] for v in kt.values()), 1e-9)}}
 
 
 def modes_run(V, ctx, spec, dev_states):
@@ -522,6 +573,9 @@ def main():
             out["served"] = served
         if not args.no_batch_serve:
             out["modes"] = modes_run(V, ctx, spec, dev_states)
+            # the other single-plan configurations at full size (C1, C3)
+            out["configs"] = {"nav256_d3": config_leg(V, ctx, "nav256_d3", 20, 3),
+                              "grid2048_d5": config_leg(V, ctx, "grid2048_d5", 3, 1)}
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(spec)
         print(json.dumps(out))

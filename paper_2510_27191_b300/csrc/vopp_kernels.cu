@@ -14,6 +14,8 @@
 //
 // No tensor cores: nothing here is a dense contraction.  The leaf kernel is bound by FP32
 // / SFU issue (Philox integer multiplies, Box-Muller, log / exp); the others are small.
+#include <type_traits>
+
 #include "vopp_device.cuh"
 #include "vopp_internal.h"
 #include "vopp.h"
@@ -843,6 +845,18 @@ struct ShiftedSum {
 // are in shared memory with base-2 log weights; every lane steps Philox pairs p = lane,
 // lane + 32, ... and keeps running sums over L = lw + log2 Z (child weights, heuristic) and
 // over log2 Z (the proposal normaliser of omega), rescaled once per chunk of pairs.
+// GRID: the leaf heuristic per column x (it depends on x alone), filled by each leaf CTA
+// with the same arithmetic as GridModel::heuristic.
+__shared__ float s_grid_h[16];
+
+// The leaf heuristic (GRID: from the CTA's column table).
+template <class M>
+__device__ __forceinline__ float leaf_heuristic(const typename M::S &s, float log2g, float a0,
+                                                float b0, bool hz) {
+  if constexpr (std::is_same<M, GridModel>::value) return (hz || gterm(s.s)) ? 0.0f : s_grid_h[gx(s.s)];
+  else return M::heuristic(s, log2g, a0, b0, hz);
+}
+
 template <class M>
 __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNode<M> &nb,
                                 int l, unsigned long long node, int slot, float *sm_rb,
@@ -956,10 +970,10 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
         const bool v1 = 2 * p + 1 < N;
         L[2 * c] = b.x + e0;
         E[2 * c] = e0;
-        Hh[2 * c] = M::heuristic(s0, log2g, h_a0, h_b0, hz);
+        Hh[2 * c] = leaf_heuristic<M>(s0, log2g, h_a0, h_b0, hz);
         L[2 * c + 1] = b.y + e1;           // the odd-N pad slot has lw2 = -inf
         E[2 * c + 1] = v1 ? e1 : -CUDART_INF_F;
-        Hh[2 * c + 1] = M::heuristic(s1, log2g, h_a0, h_b0, hz);
+        Hh[2 * c + 1] = leaf_heuristic<M>(s1, log2g, h_a0, h_b0, hz);
         rsum = fmaf(b.z, r0, rsum);
         rsum = fmaf(b.w, r1, rsum);        // pad slot: w = 0
         cm1 = fmaxf(cm1, fmaxf(L[2 * c], L[2 * c + 1]));
@@ -1023,6 +1037,12 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   float *sm_rb = smem + (SNode<M>::kPairBytes / 4) * npairs;
   float *sm_lo = sm_rb + AW, *sm_v = sm_lo + AW;
   __shared__ float2 s_mu;
+  if constexpr (std::is_same<M, GridModel>::value) {
+    if (threadIdx.x < 16) {   // read after the node build's barriers
+      const GridModel::S col{gpack(0, threadIdx.x & 15, 0, 0)};
+      s_grid_h[threadIdx.x] = GridModel::heuristic(col, P.log2_gamma, P.h_a0, P.h_b0, false);
+    }
+  }
 
   if (P.leaf_gen) {
     const unsigned long long parent = node / (unsigned long long)AW;
