@@ -245,11 +245,13 @@ def _config(spec, args):
             "parallelism": f"replicas{args.gpus if args else 1}"}
 
 
-def cpu_baseline(spec, budget_s=20.0):
+def cpu_baseline(spec, budget_s=20.0, gpu=None):
     """The oracle timed as it stands on the host over a bounded sample: level-1 subtrees of
     the same plan (independent, so they spread over the host's cores with one thread per
     core; the ctypes calls release the interpreter lock).  Reports the all-cores rate, with
-    the single-thread rate beside it."""
+    the single-thread rate beside it.  The single-thread sample is the whole plan of the
+    GPU's last timed seed when it fits a third of the budget (gpu = (result, seed)); the
+    GPU result's error against it is reported as `accuracy`."""
     import concurrent.futures as cf
     import oracle as O
     m = O.make_model(spec.kind, pi_mode=spec.pi_mode, pi_temp=spec.pi_temp,
@@ -264,12 +266,31 @@ def cpu_baseline(spec, budget_s=20.0):
                    root_s=root.get("s"), root_pf=root.get("pf"))
         return r["particle_steps"]
 
-    # single thread: subtrees one after another for a third of the budget
+    # single thread: the whole plan of the GPU's last timed seed if it fits a third of the
+    # budget (about 1e7 FP64 particle-steps/s on one core), else subtrees one after another
+    accuracy, whole = None, gpu is not None and spec.steps <= 1e7 * budget_s / 3
     t0 = time.perf_counter()
     done1, n1 = 0, 0
-    while time.perf_counter() - t0 < budget_s / 3 and n1 < AW:
-        done1 += subtree(n1)
-        n1 += 1
+    if whole:
+        res, seed = gpu
+        o = O.plan(m, spec.N, spec.D, spec.W, spec.eta, spec.gamma, seed, outputs=False,
+                   root_x=root.get("x"), root_y=root.get("y"), root_s=root.get("s"),
+                   root_pf=root.get("pf"))
+        done1, n1 = o["particle_steps"], AW
+        q_o, q_g = np.asarray(o["q_root"], dtype=np.float64), np.asarray(res["q"], dtype=np.float64)
+        rel = lambda g, r: np.abs(g - r) / np.maximum(np.abs(r), 1.0)
+        top = np.sort(q_o)[::-1]
+        accuracy = {"oracle": f"FP64, seed {seed}, whole plan", "tolerance": 1e-4,
+                    "max_err_q_root": float(rel(q_g, q_o).max()),
+                    "err_v_root": float(rel(np.float64(res["v_root"]), np.float64(o["v_root"]))),
+                    "action": int(res["action"]), "oracle_action": int(o["action"]),
+                    "action_match": int(res["action"]) == int(o["action"]),
+                    "oracle_top2_q_gap": float(top[0] - top[1]) if len(top) > 1 else None,
+                    "near_threshold_particles": int(o["near_threshold"])}
+    else:
+        while time.perf_counter() - t0 < budget_s / 3 and n1 < AW:
+            done1 += subtree(n1)
+            n1 += 1
     dt1 = time.perf_counter() - t0
     # all cores: waves of one subtree per thread, every subtree of the plan at least once
     # when the budget allows
@@ -287,7 +308,9 @@ def cpu_baseline(spec, budget_s=20.0):
             "single_thread_value": done1 / dt1,
             "sample": f"{n} level-1 subtrees (of {AW}; indices taken modulo {AW}) of the same "
                       f"plan, {done} particle-steps, FP64, {threads} threads, {dt:.1f} s; "
-                      f"single thread: {n1} subtrees, {done1} particle-steps, {dt1:.1f} s"}
+                      f"single thread: " + (f"the whole plan" if whole else f"{n1} subtrees") +
+                      f", {done1} particle-steps, {dt1:.1f} s",
+            "accuracy": accuracy}
 
 
 def config_leg(V, ctx, name, steps, warmup=1):
@@ -431,6 +454,9 @@ def main():
                     help="skip the batched (512 mixed plans), served (Poisson requests) and "
                          "other-mode (anytime, episodes, closed loop) legs")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every plan's kernels one by one instead of replaying the "
+                         "captured CUDA graph of the plan's shape")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -447,6 +473,9 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     ctx = V.vopp_ctx_create(local, 0, stream.cuda_stream)
+    # plans of one shape replay one captured CUDA graph (metadata upload, every kernel, result
+    # copy): the per-plan host work is a memcpy into pinned memory and one graph launch
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, 0 if args.no_graphs else 1)
     model = V.vopp_create_model(ctx, V.make_desc(spec.kind, pi_mode=spec.pi_mode,
                                                  pi_temp=spec.pi_temp,
                                                  rock_x=WL.grid_layout(spec.layout_seed)[0] if spec.kind == WL.GRID else None,
@@ -518,6 +547,10 @@ def main():
     c2 = V.vopp_ctx_counters(ctx)
     e2e_ms = max_over_ranks(float(sum(e2e_times)), dist, "cuda")
 
+    # the other legs mix plan shapes: one captured graph per context would be re-captured at
+    # every shape change, so they launch stage by stage
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, 0)
+
     # issue rates of the leaf kernel's arithmetic, per SM cycle (outside every timed region)
     pipes = V.vopp_pipe_rates(local)
     fma_per_clk = pipes.get("fma.rn.f32", (LANES_PER_CLK, 0.0))[0]
@@ -528,7 +561,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded root particles; no datasets)",
-            "config": _config(spec, args),
+            "config": {**_config(spec, args),
+                       "launch": "stream launches" if args.no_graphs else "CUDA graph replay"},
             "plans_per_s": args.steps * world / (total_ms / 1e3),
             "nodes_per_s": (sum(AW ** l for l in range(spec.D + 1))) * args.steps * world / (total_ms / 1e3),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -577,7 +611,8 @@ def main():
             out["configs"] = {"nav256_d3": config_leg(V, ctx, "nav256_d3", 20, 3),
                               "grid2048_d5": config_leg(V, ctx, "grid2048_d5", 3, 1)}
         if not args.no_cpu_baseline and world == 1:
-            out["cpu_baseline"] = cpu_baseline(spec)
+            last_seed = seeds[(args.warmup + args.steps - 1) % len(seeds)]
+            out["cpu_baseline"] = cpu_baseline(spec, gpu=(last, last_seed))
         print(json.dumps(out))
     V.vopp_model_destroy(model)
     V.vopp_ctx_destroy(ctx)
