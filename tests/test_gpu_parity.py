@@ -223,3 +223,44 @@ def test_config2_root_and_sampled_subtrees():
             del n3
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("kind,W", [(WL.NAV2D, 1), (WL.GRID, 1)])
+def test_largest_particle_count_matches_oracle(kind, W):
+    """The largest N a plan accepts (bounded by the leaf kernel's shared-memory node buffer):
+    found through the ABI by bisection on depth-0 plans, then a depth-2 plan at that N
+    against the oracle; N + 1 particles are refused with VOPP_E_INVALID."""
+    from paper_2510_27191_b300 import vopp as V
+
+    def accepted(n, g):
+        st = Spec(kind, n, 0, W, root_seed=5).states()
+        try:
+            V.vopp_plan(g.model, st, None, n, 0, W, 1.0, 0.95, None, 1)
+            return True
+        except V.VoppError as e:
+            assert e.code == V.VOPP_E_INVALID
+            return False
+
+    g = Gpu(Spec(kind, 16, 0, W))
+    try:
+        lo, hi = 1024, 70000           # accepted(lo), not accepted(hi)
+        assert accepted(lo, g) and not accepted(hi, g)
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            lo, hi = (mid, hi) if accepted(mid, g) else (lo, mid)
+        n_max = lo
+        assert n_max >= 8192
+    finally:
+        g.close()
+    spec = Spec(kind, n_max, 2, W, seed=3, root_seed=5)
+    g = Gpu(spec)
+    try:
+        res = g.plan()
+        orc = spec.run_oracle(outputs=False)
+        assert_close(res["q"], orc["q_root"], f"root Q at N={n_max}")
+        assert_close([res["v_root"]], [orc["v_root"]], f"root V at N={n_max}")
+        top = np.sort(np.asarray(orc["q_root"]))[::-1]
+        if top[0] - top[1] > 1e-4 * max(abs(top[0]), 1.0):
+            assert res["action"] == orc["action"]
+    finally:
+        g.close()
