@@ -2248,8 +2248,9 @@ int slot_state(ServerSlot *s) {
 }
 
 // After the last batch finishes the worker keeps polling this long before it sleeps, so
-// that a request arriving soon after starts without a thread wake-up.
-constexpr double kSpinIdle = 250e-6;
+// that a request arriving soon after starts without a thread wake-up (at a few thousand
+// requests per second the worker then never sleeps: a serving process gives it a core).
+constexpr double kSpinIdle = 2e-3;
 
 void worker_main(vopp_server *srv) {
   cudaSetDevice(srv->c->device);
