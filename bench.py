@@ -250,7 +250,7 @@ def cpu_baseline(spec, budget_s=20.0, gpu=None):
     the same plan (independent, so they spread over the host's cores with one thread per
     core; the ctypes calls release the interpreter lock).  Reports the all-cores rate, with
     the single-thread rate beside it.  The single-thread sample is the whole plan of the
-    GPU's last timed seed when it fits a third of the budget (gpu = (result, seed)); the
+    GPU's last timed seed when it fits half the budget (gpu = (result, seed)); the
     GPU result's error against it is reported as `accuracy`."""
     import concurrent.futures as cf
     import oracle as O
@@ -266,9 +266,9 @@ def cpu_baseline(spec, budget_s=20.0, gpu=None):
                    root_s=root.get("s"), root_pf=root.get("pf"))
         return r["particle_steps"]
 
-    # single thread: the whole plan of the GPU's last timed seed if it fits a third of the
-    # budget (about 1e7 FP64 particle-steps/s on one core), else subtrees one after another
-    accuracy, whole = None, gpu is not None and spec.steps <= 1e7 * budget_s / 3
+    # single thread: the whole plan of the GPU's last timed seed if it fits half the budget
+    # (about 1e7 FP64 particle-steps/s on one core), else subtrees one after another
+    accuracy, whole = None, gpu is not None and spec.steps <= 1e7 * budget_s / 2
     t0 = time.perf_counter()
     done1, n1 = 0, 0
     if whole:
