@@ -311,31 +311,17 @@ __device__ __forceinline__ float log_pibar(const PlanDesc &P, float2 mu, int a) 
   return za - zm - __logf(s);
 }
 
-// Several block-wide reductions at once (sum or max per slot); `red` holds >= 32*K floats.
-template <int K>
-__device__ __forceinline__ void block_reduce(float (&v)[K], const bool (&is_max)[K], float *red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = is_max[k] ? warp_max(v[k]) : warp_sum(v[k]);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float t = (lane < nw) ? red[k * 32 + lane] : (is_max[k] ? -CUDART_INF_F : 0.f);
-    v[k] = is_max[k] ? warp_max(t) : warp_sum(t);
-  }
-  __syncthreads();
-}
+// Philox pairs per thread between two rescales of a child build's running sums.
+constexpr int kBuildChunk = 2;
+// Floats of the block-reduction buffer a child build needs (7 per-warp values, 32 warps).
+constexpr int kRedFloats = 32 * 7;
 
 // ---------------------------------------------------------------------------------------
 // Child construction (Alg. 2: G, observation, weighting) by a whole CTA, one Philox pair
 // per thread iteration, in base-2 logs.  src: parent particles (level l, natural log
 // weights); dst: the child's particles; sc: two per-particle scratch values between the
-// passes.  dst_log2: store the child's log weights in base 2 (shared-memory node buffers)
+// passes; red: kRedFloats floats of shared memory.  dst_log2: store the child's log weights
+// in base 2 (shared-memory node buffers)
 // rather than natural (level stores); dst_has_w also stores the linear weights.
 // ---------------------------------------------------------------------------------------
 template <class M, class Src, class Dst, class Scr>
@@ -352,86 +338,131 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   const typename M::O o = branch_obs<M>(P, src, l, a, k, kn, dm, j);
   const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
 
-  // pass 1: step every particle, log2-likelihood, reward mean; keep L2 = lw2 + ell2, ell2
-  Kahan R;
-  R.init();
+  // pass 1: step every particle, log2-likelihood, reward mean; keep L2 = lw2 + ell2 for the
+  // normalisation, and fold L2 (child weights, mean particle) and ell2 (the proposal
+  // normaliser of omega) into per-thread running max-shifted sums, one rescale per chunk of
+  // kBuildChunk pairs (then one block-wide merge instead of a second pass and a reduction)
+  const bool want_mu = P.pi_mode == kPiNavDist;
+  Kahan R, S1, S0, MX, MY;
+  R.init(); S1.init(); S0.init(); MX.init(); MY.init();
   float m1 = -CUDART_INF_F, m0 = -CUDART_INF_F;
-  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-    const int i0 = 2 * p, i1 = 2 * p + 1;
-    const bool v1 = i1 < N;
-    const uint4 w = M::kStochastic
-                        ? philox(make_uint4((uint32_t)p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)),
-                                 P.key0, P.key1)
-                        : make_uint4(0u, 0u, 0u, 0u);
-    const float lw0 = src.lw(i0), lw1 = v1 ? src.lw(i1) : -CUDART_INF_F;
-    float2 r, e;
-    typename M::S s0 = src.get(i0), s1 = v1 ? src.get(i1) : src.get(i0);
-    if constexpr (M::kPairPacked) {
-      float2 X = make_float2(state_xy<M>(s0).x, state_xy<M>(s1).x);
-      float2 Y = make_float2(state_xy<M>(s0).y, state_xy<M>(s1).y);
-      bool t0, t1;
-      r = NavModel::step_pair(X, Y, NavModel::dx_of(a), NavModel::dy_of(a), w, t0, t1);
-      e = NavModel::loglik2_pair(X, Y, o_nav(o));
-      s0 = set_xy<M>(s0, X.x, Y.x);
-      s1 = set_xy<M>(s1, X.y, Y.y);
-    } else {
-      const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, kn};
-      r.x = step_particle<M>(s0, a, w, i0, dc, dm);
-      r.y = step_particle<M>(s1, a, w, i1, dc, dm);
-      e = make_float2(M::loglik2(s0, a, o, dm), M::loglik2(s1, a, o, dm));
-    }
-    const float L0 = fmaf(lw0, kLog2e, e.x), L1 = v1 ? fmaf(lw1, kLog2e, e.y) : -CUDART_INF_F;
-    const float E1 = v1 ? e.y : -CUDART_INF_F;
-    float rp = (lw0 > -CUDART_INF_F) ? ex2(lw0 * kLog2e) * r.x : 0.f;
-    if (lw1 > -CUDART_INF_F) rp = fmaf(ex2(lw1 * kLog2e), r.y, rp);
-    dst.put(i0, s0);
-    sc.setL(i0, L0);
-    sc.setE(i0, e.x);
-    if (v1) {
-      dst.put(i1, s1);
-      sc.setL(i1, L1);
-      sc.setE(i1, E1);
-    }
-    m1 = fmaxf(m1, fmaxf(L0, L1));
-    m0 = fmaxf(m0, fmaxf(e.x, E1));
-    R.add(rp);
-  }
-  {
-    float v[2] = {m1, m0};
-    const bool mx[2] = {true, true};
-    block_reduce<2>(v, mx, red);
-    m1 = v[0];
-    m0 = v[1];
-  }
-  // pass 2: shifted sums (compensated per pair) and the weighted mean particle
-  Kahan S1, S0, MX, MY;
-  S1.init(); S0.init(); MX.init(); MY.init();
-  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-    const int i0 = 2 * p, i1 = 2 * p + 1;
-    const bool v1 = i1 < N;
-    float a1 = 0.f, a0 = 0.f, ax = 0.f, ay = 0.f;
+  for (int base = threadIdx.x; base < npairs; base += blockDim.x * kBuildChunk) {
+    float Lc[2 * kBuildChunk], Ec[2 * kBuildChunk], Xc[2 * kBuildChunk], Yc[2 * kBuildChunk];
+    float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rp = 0.f;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int i = e ? i1 : i0;
-      if (e && !v1) break;
-      const float e1 = (m1 > -CUDART_INF_F) ? ex2(sc.getL(i) - m1) : 0.f;
-      const float e0 = (m0 > -CUDART_INF_F) ? ex2(sc.getE(i) - m0) : 0.f;
-      a1 += e1;
-      a0 += e0;
-      if (P.pi_mode == kPiNavDist) {
-        const float2 xy = state_xy<M>(dst.get(i));
-        ax = fmaf(e1, xy.x, ax);
-        ay = fmaf(e1, xy.y, ay);
+    for (int c = 0; c < kBuildChunk; ++c) {
+      const int p = base + c * blockDim.x;
+      Lc[2 * c] = Lc[2 * c + 1] = Ec[2 * c] = Ec[2 * c + 1] = -CUDART_INF_F;
+      Xc[2 * c] = Xc[2 * c + 1] = Yc[2 * c] = Yc[2 * c + 1] = 0.f;
+      if (p < npairs) {
+        const int i0 = 2 * p, i1 = 2 * p + 1;
+        const bool v1 = i1 < N;
+        const uint4 w = M::kStochastic
+                            ? philox(make_uint4((uint32_t)p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)),
+                                     P.key0, P.key1)
+                            : make_uint4(0u, 0u, 0u, 0u);
+        const float lw0 = src.lw(i0), lw1 = v1 ? src.lw(i1) : -CUDART_INF_F;
+        float2 r, e;
+        typename M::S s0 = src.get(i0), s1 = v1 ? src.get(i1) : src.get(i0);
+        if constexpr (M::kPairPacked) {
+          float2 X = make_float2(state_xy<M>(s0).x, state_xy<M>(s1).x);
+          float2 Y = make_float2(state_xy<M>(s0).y, state_xy<M>(s1).y);
+          bool t0, t1;
+          r = NavModel::step_pair(X, Y, NavModel::dx_of(a), NavModel::dy_of(a), w, t0, t1);
+          e = NavModel::loglik2_pair(X, Y, o_nav(o));
+          s0 = set_xy<M>(s0, X.x, Y.x);
+          s1 = set_xy<M>(s1, X.y, Y.y);
+        } else {
+          const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, kn};
+          r.x = step_particle<M>(s0, a, w, i0, dc, dm);
+          r.y = step_particle<M>(s1, a, w, i1, dc, dm);
+          e = make_float2(M::loglik2(s0, a, o, dm), M::loglik2(s1, a, o, dm));
+        }
+        const float L0 = fmaf(lw0, kLog2e, e.x), L1 = v1 ? fmaf(lw1, kLog2e, e.y) : -CUDART_INF_F;
+        const float E1 = v1 ? e.y : -CUDART_INF_F;
+        if (lw0 > -CUDART_INF_F) rp = fmaf(ex2(lw0 * kLog2e), r.x, rp);
+        if (lw1 > -CUDART_INF_F) rp = fmaf(ex2(lw1 * kLog2e), r.y, rp);
+        dst.put(i0, s0);
+        sc.setL(i0, L0);
+        if (v1) {
+          dst.put(i1, s1);
+          sc.setL(i1, L1);
+        }
+        Lc[2 * c] = L0;
+        Lc[2 * c + 1] = L1;
+        Ec[2 * c] = e.x;
+        Ec[2 * c + 1] = E1;
+        if (want_mu) {
+          const float2 q0 = state_xy<M>(s0), q1 = state_xy<M>(s1);
+          Xc[2 * c] = q0.x; Yc[2 * c] = q0.y;
+          Xc[2 * c + 1] = q1.x; Yc[2 * c + 1] = q1.y;
+        }
+        cm1 = fmax3(cm1, L0, L1);
+        cm0 = fmax3(cm0, e.x, E1);
       }
     }
-    S1.add(a1);
-    S0.add(a0);
-    if (P.pi_mode == kPiNavDist) { MX.add(ax); MY.add(ay); }
+    // move the shifts to the chunk's maxima, then add the chunk's shifted terms
+    if (cm1 > m1) {
+      const float f = (m1 > -CUDART_INF_F) ? ex2(m1 - cm1) : 0.f;
+      S1.scale(f); MX.scale(f); MY.scale(f);
+      m1 = cm1;
+    }
+    if (cm0 > m0) {
+      const float f = (m0 > -CUDART_INF_F) ? ex2(m0 - cm0) : 0.f;
+      S0.scale(f);
+      m0 = cm0;
+    }
+    float a1 = 0.f, a0 = 0.f, ax = 0.f, ay = 0.f;
+    if (m1 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < 2 * kBuildChunk; ++t) {
+        const float x1 = ex2(Lc[t] - m1);   // L = -inf gives 0
+        a1 += x1;
+        ax = fmaf(x1, Xc[t], ax);
+        ay = fmaf(x1, Yc[t], ay);
+      }
+    }
+    if (m0 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < 2 * kBuildChunk; ++t) a0 += ex2(Ec[t] - m0);
+    }
+    S1.add(a1); S0.add(a0); R.add(rp);
+    if (want_mu) { MX.add(ax); MY.add(ay); }
   }
-  float v[5] = {R.value(), S1.value(), S0.value(), MX.value(), MY.value()};
+  // block-wide merge: each warp merges its lanes' shifted sums at the warp's largest shift,
+  // then every warp merges the warps' partial sums the same way (identically in every warp)
+  float v[5];
   {
-    const bool mx[5] = {false, false, false, false, false};
-    block_reduce<5>(v, mx, red);
+    float w1 = m1, w0 = m0, sv1 = S1.value(), sx = MX.value(), sy = MY.value(), sv0 = S0.value();
+    warp_lse2(w1, sv1, sx);
+    float dummy = 0.f;
+    warp_lse2(w0, sv0, dummy);
+    sy *= (m1 > -CUDART_INF_F) ? ex2(m1 - w1) : 0.f;    // MY in the warp's S1 frame
+    sy = warp_sum(sy);
+    const float rw = warp_sum(R.value());
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();                                    // red may still be read by a caller
+    if (lane == 0) {
+      red[wid] = w1; red[32 + wid] = sv1; red[64 + wid] = sx; red[96 + wid] = sy;
+      red[128 + wid] = w0; red[160 + wid] = sv0; red[192 + wid] = rw;
+    }
+    __syncthreads();
+    float b1 = -CUDART_INF_F, bs1 = 0.f, bx = 0.f, by = 0.f, b0 = -CUDART_INF_F, bs0 = 0.f, br = 0.f;
+    if (lane < nw) {
+      b1 = red[lane]; bs1 = red[32 + lane]; bx = red[64 + lane]; by = red[96 + lane];
+      b0 = red[128 + lane]; bs0 = red[160 + lane]; br = red[192 + lane];
+    }
+    const float b1_own = b1;
+    warp_lse2(b1, bs1, bx);
+    by *= (b1_own > -CUDART_INF_F) ? ex2(b1_own - b1) : 0.f;
+    by = warp_sum(by);
+    float dummy2 = 0.f;
+    warp_lse2(b0, bs0, dummy2);
+    br = warp_sum(br);
+    m1 = b1;
+    m0 = b0;
+    v[0] = br; v[1] = bs1; v[2] = bs0; v[3] = bx; v[4] = by;
+    __syncthreads();                                    // red is free again
   }
   const float rbar = v[0], s1 = v[1], s0 = v[2], mx = v[3], my = v[4];
   const float lse2 = (s1 > 0.f) ? m1 + lg2(s1) : -CUDART_INF_F;       // base 2
@@ -776,7 +807,7 @@ __device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, 
 __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageTable st,
                                                 long long total) {
   extern __shared__ float smem[];
-  __shared__ float red[32 * 5];
+  __shared__ float red[kRedFloats];
   pdl_release_next();
   pdl_wait_prev();
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
@@ -1105,7 +1136,7 @@ template <int K>
 __global__ void __launch_bounds__(256, LeafModel<K>::kMinBlocks)
 k_leaf(const PlanDesc *plans, StageTable st, long long total) {
   extern __shared__ __align__(16) float smem[];
-  __shared__ float red[32 * 5];
+  __shared__ float red[kRedFloats];
   __shared__ long long s_item;
   pdl_release_next();
   pdl_wait_prev();
