@@ -160,3 +160,34 @@ def test_batched_update_equals_single_updates():
         V.vopp_model_destroy(grid)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_batched_update_rejects_bad_batches_without_updating():
+    """An agent listed twice, or an agent of another context, makes the whole batch
+    VOPP_E_INVALID with no belief touched."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    ctx2 = V.vopp_ctx_create(0, 0, 0)
+    try:
+        nav = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
+        nav2 = V.vopp_create_model(ctx2, V.make_desc(V.VOPP_NAV2D))
+        x, y, _ = WL.nav_root(64, 3)
+        st = np.concatenate([x, y]).astype(np.float32)
+        g1 = V.vopp_agent_create(nav, st, None, 64, 1)
+        g2 = V.vopp_agent_create(nav2, st, None, 64, 2)
+        before = V.vopp_agent_get_particles(g1, WL.NAV2D)
+        for agents in ([g1, g1], [g1, g2]):
+            with pytest.raises(V.VoppError) as e:
+                V.vopp_belief_update_batch(ctx, agents, [0] * len(agents),
+                                           [(5.0, 5.0)] * len(agents), [WL.NAV2D] * len(agents))
+            assert e.value.code == V.VOPP_E_INVALID
+        after = V.vopp_agent_get_particles(g1, WL.NAV2D)
+        for a, b in zip(before[:2], after[:2]):
+            np.testing.assert_array_equal(a, b)
+        V.vopp_agent_destroy(g1)
+        V.vopp_agent_destroy(g2)
+        V.vopp_model_destroy(nav)
+        V.vopp_model_destroy(nav2)
+    finally:
+        V.vopp_ctx_destroy(ctx)
+        V.vopp_ctx_destroy(ctx2)

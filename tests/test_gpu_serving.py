@@ -219,3 +219,42 @@ def test_served_crowd_requests_equal_alone():
         V.vopp_model_destroy(mn)
         V.vopp_ctx_destroy(ctx)
 
+
+
+def test_agents_come_and_go_while_plans_run():
+    """Agents created and destroyed (device memory from the stream-ordered pool, no device
+    synchronisation) while the server runs other agents' plans leave those plans' results
+    unchanged; the zero-timeout poll answers while they run."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    models = _models(V, ctx)
+    srv = V.vopp_server_create(ctx, max_batch=8, n_slots=3)
+    try:
+        specs = WL.draw_mixed_plans(24, 5, 1 << 24)
+        agents = [V.vopp_agent_create(models[ps.kind], Spec.from_plan(ps).states(), None, ps.N,
+                                      900 + i) for i, ps in enumerate(specs)]
+        tickets = [V.vopp_submit_agent(srv, g, ps.D, ps.W, ps.eta, ps.gamma, ps.seed)
+                   for g, ps in zip(agents, specs)]
+        churn = 0
+        while V.vopp_server_get_stats(srv)["completed"] < len(tickets) and churn < 200:
+            ps = specs[churn % len(specs)]
+            g = V.vopp_agent_create(models[ps.kind], Spec.from_plan(ps).states(), None, ps.N, 7)
+            V.vopp_agent_destroy(g)
+            churn += 1
+        got = {}
+        while len(got) < len(tickets):
+            r = V.vopp_wait_any(srv, 20.0)
+            assert r is not None and r[1] == V.VOPP_OK
+            got[r[0]] = r[2]
+        assert V.vopp_wait_any(srv, 0.0) is None          # nothing left: answers at once
+        for t, g, ps in zip(tickets, agents, specs):
+            alone = V.vopp_agent_plan(g, models[ps.kind], ps.D, ps.W, ps.eta, ps.gamma, ps.seed)
+            assert got[t]["q"][:len(alone["q"])].tolist() == alone["q"].tolist()
+            assert got[t]["action"] == alone["action"]
+        for g in agents:
+            V.vopp_agent_destroy(g)
+    finally:
+        V.vopp_server_destroy(srv)
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
