@@ -207,3 +207,33 @@ def test_unmatched_observation_falls_back_to_the_sir_update():
         V.vopp_model_destroy(model)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_shallow_tree_or_width_change_plans_afresh():
+    """A depth-2 tree keeps no level-1 particle sets, so even a matching observation runs the
+    SIR update; after an adoption, a plan of another width does not continue the subtree: it
+    plans afresh from the adopted particles (equal, within tolerance, to vopp_plan from them
+    with that seed)."""
+    from paper_2510_27191_b300 import vopp as V
+    rx, ry, s = _grid()
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        model = V.vopp_create_model(ctx, V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry))
+        g = V.vopp_agent_create(model, s, None, N, 31)
+        V.vopp_agent_set_reuse(g, True)
+        V.vopp_agent_plan(g, model, 2, W, ETA, GAMMA, 3)
+        ess, _ = V.vopp_belief_update(g, 2, 0, WL.GRID)          # move N: NULL matches
+        assert ess > 0.0 and V.vopp_agent_reuse_info(g)["adopted_slot"] == -1
+        V.vopp_agent_plan(g, model, 3, W, ETA, GAMMA, 4)
+        ess, _ = V.vopp_belief_update(g, 2, 0, WL.GRID)
+        assert ess == -1.0 and V.vopp_agent_reuse_info(g)["adopted_slot"] >= 0
+        r = V.vopp_agent_plan(g, model, 3, W - 1, ETA, GAMMA, 5)  # another width: fresh
+        assert not (r["flags"] & 4) and r["reused_levels"] == 0
+        st, lw, _ = V.vopp_agent_get_particles(g, WL.GRID)
+        w = np.exp(lw.astype(np.float64) - lw.max()).astype(np.float32)
+        ref = V.vopp_plan(model, st, w, N, 3, W - 1, ETA, GAMMA, None, 5)
+        assert_close(r["q"], ref["q"], "fresh plan after a width change")
+        V.vopp_agent_destroy(g)
+        V.vopp_model_destroy(model)
+    finally:
+        V.vopp_ctx_destroy(ctx)
