@@ -221,6 +221,15 @@ template <class M> struct ScratchInNode {   // K3: the destination node's lw / w
   __device__ __forceinline__ void setE(int i, float v) const { n.set_w(i, v); }
 };
 
+// A branch observation from its two-float form (obs_f2): NAV2D (x, y); the discrete models'
+// index is exact in the first float.
+template <class M> __device__ __forceinline__ typename M::O obs_from_f2(float2 f) {
+  return typename M::O{(int)f.x};
+}
+template <> __device__ __forceinline__ NavModel::O obs_from_f2<NavModel>(float2 f) {
+  return NavModel::O{f.x, f.y};
+}
+
 // The observation of a pair-packed (NAV2D) branch; other models never take that path.
 template <class Obs> __device__ __forceinline__ NavModel::O o_nav(const Obs &) { return NavModel::O{0.f, 0.f}; }
 template <> __device__ __forceinline__ NavModel::O o_nav<NavModel::O>(const NavModel::O &o) { return o; }
@@ -888,17 +897,20 @@ __device__ __forceinline__ float leaf_heuristic(const typename M::S &s, float lo
   else return M::heuristic(s, log2g, a0, b0, hz);
 }
 
+// The branch's sampled observation and representative come from the CTA's table (sm_ox,
+// sm_oy, sm_rep), computed once per node.
 template <class M>
 __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNode<M> &nb,
                                 int l, unsigned long long node, int slot, float *sm_rb,
-                                float *sm_lo, float *sm_v) {
+                                float *sm_lo, float *sm_v, const float *sm_ox,
+                                const float *sm_oy, const int *sm_rep) {
   const int lane = threadIdx.x & 31, N = P.N, W = P.W;
   const int a = slot / W, k = slot - (slot / W) * W;
   const float log2g = P.log2_gamma, h_a0 = P.h_a0, h_b0 = P.h_b0;
   const bool hz = P.h_zero != 0;
-  int j;
   const unsigned long long kn = key_node(P, l, node);
-  const typename M::O o = branch_obs<M>(P, nb, l, a, k, kn, dm, j);
+  const int j = sm_rep[slot];
+  const typename M::O o = obs_from_f2<M>(make_float2(sm_ox[slot], sm_oy[slot]));
 
 #if VOPP_ROUND_KEYS
   PhiloxKeys K;
@@ -1100,9 +1112,26 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   }
   __syncthreads();
 
+  // every branch's sampled observation and representative, one thread per branch (a
+  // warp-uniform serial computation otherwise repeated by all 32 lanes of a branch's warp)
+  float *sm_ox = sm_v + AW, *sm_oy = sm_ox + AW;
+  int *sm_rep = reinterpret_cast<int *>(sm_oy + AW);
+  {
+    const unsigned long long kn = key_node(P, l, node);
+    for (int slot = threadIdx.x; slot < AW; slot += blockDim.x) {
+      const int a = slot / P.W, k = slot - a * P.W;
+      int j;
+      const float2 of = M::obs_f2(branch_obs<M>(P, nb, l, a, k, kn, dm, j));
+      sm_ox[slot] = of.x;
+      sm_oy[slot] = of.y;
+      sm_rep[slot] = j;
+    }
+  }
+  __syncthreads();
+
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int slot = wid; slot < AW; slot += nw)
-    leaf_child_warp<M>(P, dm, nb, l, node, slot, sm_rb, sm_lo, sm_v);
+    leaf_child_warp<M>(P, dm, nb, l, node, slot, sm_rb, sm_lo, sm_v, sm_ox, sm_oy, sm_rep);
   __syncthreads();
 
   if (wid == 0) {
@@ -1355,7 +1384,9 @@ __global__ void k_env(EnvArgs E) {
 // ---------------------------------------------------------------------------------------
 size_t leaf_smem_bytes(int kind, int N, int AW) {
   const size_t pair = (kind == kNav) ? 32 : (kind == kCrowd ? SNode<CrowdModel>::kPairBytes : 24);
-  return pair * (size_t)((N + 1) / 2) + 3 * sizeof(float) * (size_t)AW + 64;
+  // node pairs; per branch: r̄, log ω, V, and the sampled observation (2 floats) with its
+  // representative
+  return pair * (size_t)((N + 1) / 2) + 6 * sizeof(float) * (size_t)AW + 64;
 }
 size_t expand_smem_bytes(int N) { return 8 * (size_t)N + 64; }
 
