@@ -242,14 +242,20 @@ __device__ __forceinline__ float neg2_log_u(float u) {
   const float hw = __fmul_rn(-1.38629436f, lg2(u));
   return (v < 0.00390625f) ? ser : hw;
 }
+// Two at once; the series is evaluated only when one of the two needs it (about one pair in
+// 128), so the common case is the hardware logarithm and a product.
 __device__ __forceinline__ float2 neg2_log_u2(float2 u) {
-  const float2 v = fma2(u, bc2(-1.0f), bc2(1.0f));
-  float2 ser = fma2(v, bc2(0.5f), bc2(0.666666687f));
-  ser = fma2(v, ser, bc2(1.0f));
-  ser = fma2(v, ser, bc2(2.0f));
-  ser = mul2(ser, v);
-  const float2 hw = mul2(bc2(-1.38629436f), make_float2(lg2(u.x), lg2(u.y)));
-  return make_float2((v.x < 0.00390625f) ? ser.x : hw.x, (v.y < 0.00390625f) ? ser.y : hw.y);
+  float2 r = mul2(bc2(-1.38629436f), make_float2(lg2(u.x), lg2(u.y)));
+  const bool nx = u.x > 0.99609375f, ny = u.y > 0.99609375f;   // v = 1 - u < 2^-8
+  if (nx || ny) {
+    const float2 v = fma2(u, bc2(-1.0f), bc2(1.0f));
+    float2 ser = fma2(v, bc2(0.5f), bc2(0.666666687f));
+    ser = fma2(v, ser, bc2(1.0f));
+    ser = fma2(v, ser, bc2(2.0f));
+    ser = mul2(ser, v);
+    r = make_float2(nx ? ser.x : r.x, ny ? ser.y : r.y);
+  }
+  return r;
 }
 
 // Box-Muller: (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  The angle is taken as
