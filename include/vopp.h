@@ -181,7 +181,8 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 /* Tuning options (vopp_ctx_set_option):
  *   VOPP_OPT_LEAF_GEN        1 (default): the leaf kernel builds level D-1 in shared memory
  *                            from level D-2; 0: level D-1 is materialised in HBM first
- *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 128)
+ *   VOPP_OPT_LEAF_THREADS    threads per leaf CTA, multiple of 32 in [32, 256] (default 128;
+ *                            CROWD leaf CTAs always have 160: five warps for its 5 W branches)
  *   VOPP_OPT_GRID_CAP        maximum CTAs of an expansion / leaf launch (grid-stride beyond)
  * Results do not depend on any option. */
 #define VOPP_OPT_LEAF_GEN 1

@@ -52,6 +52,10 @@ struct EnvArgs {
   EnvOut *out;
 };
 
+// CROWD leaf CTAs have five warps whatever the leaf-threads option: the model's A W = 5 W
+// branches then divide evenly among them.
+constexpr int kCrowdLeafThreads = 160;
+
 // Dynamic shared memory a leaf CTA may use (B300: 227 KB per block, kept below it).
 constexpr size_t kLeafSmemLimit = 200 * 1024;
 size_t leaf_smem_bytes(int kind, int N, int AW);

@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageT
 //   VOPP_ROUND_KEYS      1: Philox round keys held in registers for the whole branch
 //   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
 //                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2;
-//                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD)
+//                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD, whose CTAs have 160 threads)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
 #endif
@@ -855,7 +855,7 @@ __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageT
 #define VOPP_LEAF_GRID_MINBLOCKS 4
 #endif
 #ifndef VOPP_LEAF_CROWD_MINBLOCKS
-#define VOPP_LEAF_CROWD_MINBLOCKS 1
+#define VOPP_LEAF_CROWD_MINBLOCKS 3
 #endif
 #ifndef VOPP_LEAF_CHUNK_PACKED
 #define VOPP_LEAF_CHUNK_PACKED 4
@@ -1162,7 +1162,7 @@ template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int
 template <> struct LeafModel<kCrowd> { using type = CrowdModel; static constexpr int kMinBlocks = VOPP_LEAF_CROWD_MINBLOCKS; };
 
 template <int K>
-__global__ void __launch_bounds__(256, LeafModel<K>::kMinBlocks)
+__global__ void __launch_bounds__(K == kCrowd ? kCrowdLeafThreads : 256, LeafModel<K>::kMinBlocks)
 k_leaf(const PlanDesc *plans, StageTable st, long long total) {
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[kRedFloats];
@@ -1444,7 +1444,7 @@ cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long 
     case kNav: return launch_pdl(k_leaf<kNav>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kGrid: return launch_pdl(k_leaf<kGrid>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kToy: return launch_pdl(k_leaf<kToy>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
-    case kCrowd: return launch_pdl(k_leaf<kCrowd>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
+    case kCrowd: return launch_pdl(k_leaf<kCrowd>, (unsigned)grid, (unsigned)kCrowdLeafThreads, smem, s, d, st, total);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1454,7 +1454,7 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
     case kNav: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kNav>, threads, smem);
     case kGrid: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kGrid>, threads, smem);
     case kToy: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kToy>, threads, smem);
-    case kCrowd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kCrowd>, threads, smem);
+    case kCrowd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kCrowd>, kCrowdLeafThreads, smem);
     default: return cudaErrorInvalidValue;
   }
 }
