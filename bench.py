@@ -596,6 +596,7 @@ def main():
         if not args.no_batch_serve:
             from paper_2510_27191_b300 import loadgen as LG
             out["batched"] = LG.batch_run(V, ctx)
+            out["batched_small"] = LG.small_batch_run(V, ctx)
             served = {}
             # served: continuous batching, batched belief updates, agents with subtree reuse;
             # plain: one synchronous plan per request, then its own belief update

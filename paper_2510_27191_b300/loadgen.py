@@ -76,6 +76,47 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
     return res
 
 
+def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3):
+    """n_plans small navigation plans (N=256, depth 3, 4x4 branches: the latency-bound shape)
+    with different seeds and roots, one batch against one plan at a time (CUDA events)."""
+    import torch
+    model = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
+    ps = WL.CONFIG1
+    roots = []
+    for i in range(n_plans):
+        x, y, _ = WL.nav_root(ps.N, 100 + i)
+        roots.append(torch.from_numpy(np.concatenate([x, y]).astype(np.float32)).cuda())
+    reqs = [dict(model=model, states=r, weights=None, n=ps.N, depth=ps.D, width=ps.W,
+                 eta=ps.eta, gamma=ps.gamma, seed=1000 + i, A=4) for i, r in enumerate(roots)]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    def seq():
+        return [V.vopp_plan(q["model"], q["states"], None, q["n"], q["depth"], q["width"],
+                            q["eta"], q["gamma"], None, q["seed"]) for q in reqs]
+
+    V.vopp_plan_batch(ctx, reqs[:8])
+    seq()
+    t_b = min(timed(lambda: V.vopp_plan_batch(ctx, reqs))[0] for _ in range(reps))
+    outs, _ = V.vopp_plan_batch(ctx, reqs)
+    t_s, singles = min((timed(seq) for _ in range(reps)), key=lambda r: r[0])
+    same = all(a["q"].tolist() == b["q"].tolist() for a, b in zip(outs, singles))
+    V.vopp_model_destroy(model)
+    steps = float(ps.steps) * n_plans
+    return {"plans": n_plans, "workload": "nav2d N=256 D=3 A=4 W=4 (different roots and seeds)",
+            "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+            "batched_plans_per_s": n_plans / t_b, "sequential_plans_per_s": n_plans / t_s,
+            "batched_particle_steps_per_s": steps / t_b, "batched_equals_sequential": bool(same)}
+
+
 def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int = 1024,
               seed: int = 11, mode: str = "served", deadline_s: float = 0.05, max_batch: int = 64,
               n_slots: int = 3, drain_factor: float = 3.0, reuse: bool = False):
