@@ -2268,11 +2268,19 @@ void worker_main(vopp_server *srv) {
     }
     int busy_now = 0;
     for (auto *s : srv->slots) busy_now += s->busy;
-    if (fin.empty() && busy_now > 0 && (srv->n_pending.load() == 0 || busy_now == (int)srv->slots.size()) &&
-        !srv->stop_flag.load()) {
-      std::this_thread::yield();   // nothing to post or start: poll again without the lock
-      idle_since = now_s();
-      continue;
+    if (fin.empty() && !srv->stop_flag.load()) {
+      // nothing to post; nothing to start either (no request, or every slot busy): poll
+      // again without the lock, in flight or within the idle polling window
+      const size_t queued = srv->n_pending.load();
+      if (busy_now > 0 && (queued == 0 || busy_now == (int)srv->slots.size())) {
+        std::this_thread::yield();
+        idle_since = now_s();
+        continue;
+      }
+      if (busy_now == 0 && queued == 0 && now_s() - idle_since < kSpinIdle) {
+        std::this_thread::yield();
+        continue;
+      }
     }
     std::unique_lock<std::mutex> lock(srv->mu);
     bool posted = !fin.empty();
