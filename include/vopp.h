@@ -334,7 +334,7 @@ VOPP_API int vopp_agent_plan_anytime(vopp_agent *agent, const vopp_plan_params *
  * has zero likelihood) the belief is left unchanged.  ess_out / resampled_out may be NULL. */
 VOPP_API int vopp_belief_update(vopp_agent *agent, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out);
-/* tau(b, a, o) for n agents of ctx at once: each agent is updated exactly as
+/* tau(b, a, o) (Sec. III-B) for n agents of ctx at once: each agent is updated exactly as
  * vopp_belief_update would update it (subtree reuse included), the SIR updates of all of
  * them in one launch (one CTA per agent, the same arithmetic and reduction order, so the
  * particles, weights, ancestors, ESS and resampling decisions are bit-identical to n single

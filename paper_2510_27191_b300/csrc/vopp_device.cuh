@@ -130,51 +130,16 @@ __device__ __forceinline__ int find_plan(const StageTable &st, long long item) {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter words:
 //   c0 = idx | purpose << 24, c1 = level | action << 8 | branch << 16, (c2, c3) = node.
 // ---------------------------------------------------------------------------------------
-#ifndef VOPP_PHILOX_WIDE
-#define VOPP_PHILOX_WIDE 1
-#endif
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-#if VOPP_PHILOX_WIDE
     // each round's two 32x32 -> 64-bit products as single wide multiplies
     const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
     const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
     c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
                    (uint32_t)p0);
-#else
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-#endif
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
-// Round keys of Philox4x32-10 for one key: rk[2r], rk[2r+1] = (k0, k1) + r (W0, W1).
-struct PhiloxKeys {
-  uint32_t k[20];
-  __device__ __forceinline__ void init(uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-      k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-    }
-  }
-};
-
-__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys &K) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
   }
   return c;
 }

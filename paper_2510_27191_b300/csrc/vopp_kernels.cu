@@ -838,15 +838,11 @@ __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageT
 // ---------------------------------------------------------------------------------------
 // Compile-time tuning of the leaf loop (results do not depend on them):
 //   VOPP_LEAF_CHUNK      Philox pairs per lane between two rescales of the running sums
-//   VOPP_ROUND_KEYS      1: Philox round keys held in registers for the whole branch
 //   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
 //                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2;
 //                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD, whose CTAs have 160 threads)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
-#endif
-#ifndef VOPP_ROUND_KEYS
-#define VOPP_ROUND_KEYS 0
 #endif
 #ifndef VOPP_LEAF_MINBLOCKS
 #define VOPP_LEAF_MINBLOCKS 3
@@ -912,12 +908,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   const int j = sm_rep[slot];
   const typename M::O o = obs_from_f2<M>(make_float2(sm_ox[slot], sm_oy[slot]));
 
-#if VOPP_ROUND_KEYS
-  PhiloxKeys K;
-  K.init(P.key0, P.key1);
-#else
   const uint32_t key0 = P.key0, key1 = P.key1;
-#endif
   const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
   const uint32_t c2 = (uint32_t)kn, c3 = (uint32_t)(kn >> 32);
   ShiftedSum A1, A0;
@@ -939,11 +930,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
         L[c] = E[c] = bc2(-CUDART_INF_F);
         Hh[c] = bc2(0.f);
         if (p < npairs) {
-#if VOPP_ROUND_KEYS
-          const uint4 w = philox_rk(make_uint4((uint32_t)p, c1, c2, c3), K);
-#else
           const uint4 w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
-#endif
           const float4 xy = nb.A_f4(p);            // (x0, x1, y0, y1)
           const float4 b = nb.B[p];                // (lw2_0, lw2_1, w_0, w_1)
           float2 X = make_float2(xy.x, xy.y), Y = make_float2(xy.z, xy.w);
@@ -997,11 +984,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
       if (p < npairs) {
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (M::kStochastic) {   // purpose 0 (transition): counter word 0 is the pair index
-#if VOPP_ROUND_KEYS
-          w = philox_rk(make_uint4((uint32_t)p, c1, c2, c3), K);
-#else
           w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
-#endif
         }
         typename M::S s0, s1;
         nb.get_pair(p, s0, s1);
