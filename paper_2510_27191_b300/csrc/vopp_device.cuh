@@ -328,6 +328,21 @@ __device__ __forceinline__ float block_sum(float v, float *red) {
   return t;
 }
 
+// Four block-wide sums at once (every thread gets them).  `red` holds >= 128 floats.
+__device__ __forceinline__ void block_sum4(float (&v)[4], float *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[32 * k + wid] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = warp_sum((lane < nw) ? red[32 * k + lane] : 0.f);
+}
+
 __device__ __forceinline__ float block_max(float v, float *red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_max(v);

@@ -741,29 +741,32 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
     if (threadIdx.x == 0) P.result->status |= kStatusDegenerateRoot;
     return;
   }
-  Kahan T;
-  T.init();
+  // one pass for the normaliser and the (unnormalised) weighted means of the position and
+  // (depth 0) the heuristic, one block reduction for the four sums
+  Kahan T, MX, MY, H;
+  T.init(); MX.init(); MY.init(); H.init();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float lw = dst.lw(i);
-    if (lw > -CUDART_INF_F) T.add(__expf(lw - m));
-  }
-  const float tsum = block_sum(T.value(), red);
-  const float lse = P.reuse_root ? 0.f : m + logf(tsum);
-  Kahan MX, MY, H;
-  MX.init(); MY.init(); H.init();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float lw = dst.lw(i);
-    const float nl = (lw > -CUDART_INF_F) ? lw - lse : -CUDART_INF_F;
-    if (!P.reuse_root) dst.set_lw(i, nl);
-    const float wn = (nl > -CUDART_INF_F) ? __expf(nl) : 0.f;
+    if (!(lw > -CUDART_INF_F)) continue;
+    const float e = __expf(lw - m);
     const typename M::S s = dst.get(i);
     const float2 xy = state_xy<M>(s);
-    MX.add(wn * xy.x);
-    MY.add(wn * xy.y);
-    if (P.D == 0) H.add(wn * M::heuristic(s, P));
+    T.add(e);
+    MX.add(e * xy.x);
+    MY.add(e * xy.y);
+    if (P.D == 0) H.add(e * M::heuristic(s, P));
   }
-  const float mx = block_sum(MX.value(), red), my = block_sum(MY.value(), red);
-  const float hv = block_sum(H.value(), red);
+  float sums[4] = {T.value(), MX.value(), MY.value(), H.value()};
+  block_sum4(sums, red);
+  const float tsum = sums[0];
+  const float mx = sums[1] / tsum, my = sums[2] / tsum, hv = sums[3] / tsum;
+  if (!P.reuse_root) {   // normalised log weights (a reused root's are already)
+    const float lse = m + logf(tsum);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const float lw = dst.lw(i);
+      if (lw > -CUDART_INF_F) dst.set_lw(i, lw - lse);
+    }
+  }
   if (threadIdx.x == 0) {
     if (P.D >= 2) P.cnt[0][0] = 0u;
     if (P.mu[0]) { P.mu[0][0] = mx; P.mu[0][1] = my; }
@@ -787,7 +790,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
 }
 
 __global__ void __launch_bounds__(1024) k_root_prep(const PlanDesc *plans, StageTable st) {
-  __shared__ float red[32];
+  __shared__ float red[128];
   pdl_release_next();
   const PlanDesc &P = plans[st.plan[blockIdx.x]];
   const DevModel &dm = *P.model;
