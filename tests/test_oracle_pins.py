@@ -791,3 +791,35 @@ def test_crowd_heuristic_is_the_straight_line_return():
         gk = gamma ** (steps - 1)
         assert O.crowd_heuristic(y, 0, gamma) == pytest.approx(-(1 - gk) / (1 - gamma) + 1000 * gk)
     assert O.crowd_heuristic(10.0, 1 << 16, gamma) == 0.0
+
+
+def test_toy2_matches_the_hand_derived_closed_form():
+    """The oracle's TOY2 plans (ENUMERATE branches, two weighted root particles) equal the
+    hand derivation in tests/golden/toy2_closed_form.txt (Alg. 3 and Eq. 1 written out for
+    depth 1 and 2), and the fixture's numbers equal its own formulas."""
+    import math
+    path = os.path.join(os.path.dirname(__file__), "golden", "toy2_closed_form.txt")
+    rows = [list(map(float, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 6
+    g = 0.95
+
+    def v1(b, eta):
+        return eta * math.log((math.exp((b[0] - b[1]) / eta) + math.exp(-0.1 / eta)) / 2)
+
+    m = O.make_model(O.TOY2, branch_mode=O.ENUMERATE)
+    for depth, eta, q_stay, q_flip, v in rows:
+        # the fixture against its formulas
+        if depth == 1:
+            qs, qf = 0.2, -0.1
+        else:
+            qs = 0.2 + g * (0.57 * v1((0.51 / 0.57, 0.06 / 0.57), eta) + 0.43 * v1((0.09 / 0.43, 0.34 / 0.43), eta))
+            qf = -0.1 + g * (0.43 * v1((0.34 / 0.43, 0.09 / 0.43), eta) + 0.57 * v1((0.06 / 0.57, 0.51 / 0.57), eta))
+        vv = eta * math.log((math.exp(qs / eta) + math.exp(qf / eta)) / 2)
+        assert abs(qs - q_stay) < 1e-11 and abs(qf - q_flip) < 1e-11 and abs(vv - v) < 1e-11
+        # the oracle against the fixture
+        r = O.plan(m, 2, int(depth), 2, eta, g, 7, root_s=np.array([0, 1], np.int32),
+                   root_w=np.array([0.6, 0.4]), outputs=False)
+        assert r["status"] == O.OK
+        np.testing.assert_allclose(r["q_root"], [q_stay, q_flip], rtol=0, atol=1e-11)
+        assert abs(r["v_root"] - v) < 1e-11
+        assert r["action"] == 0
