@@ -502,17 +502,26 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   int rc = VOPP_OK;
   const std::vector<int> order_leaf = lpt_order(jobs, true), order_exp = lpt_order(jobs, false);
 
-  // stages
+  // stages.  A plan whose first stage is the level-0 expansion lets that stage prepare its
+  // root (one launch fewer on its critical path), unless it continues a kept subtree or its
+  // root does not fit the expansion's shared memory.
   std::vector<StageBuild> stages;
   auto nodes = [](const Job &j, int l) { return (long long)ipow(j.shape.AW, l); };
+  std::vector<char> fused(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    fused[i] = j.shape.mat_top >= 1 && j.first_expand == 0 && !j.reuse_root &&
+               expand_fused_smem_bytes(j.shape.kind, j.shape.N) <= kLeafSmemLimit;
+  }
   {
     StageBuild s;
     s.family = F_ROOT;
     s.level = 0;
-    for (int i = 0; i < n; ++i) { s.plans.push_back(i); s.prefix.push_back(i); }
-    s.prefix.push_back(n);
-    s.total = n;
-    stages.push_back(s);
+    for (int i = 0; i < n; ++i)
+      if (!fused[i]) { s.prefix.push_back((long long)s.plans.size()); s.plans.push_back(i); }
+    s.prefix.push_back((long long)s.plans.size());
+    s.total = (long long)s.plans.size();
+    if (s.total) stages.push_back(s);
   }
   int max_mat = 0, maxD = 0;
   for (auto &j : jobs) { max_mat = std::max(max_mat, j.shape.mat_top); maxD = std::max(maxD, j.shape.D); }
@@ -528,6 +537,9 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
         s.prefix.push_back(acc);
         acc += nodes(jobs[i], l + 1);
         s.maxN = std::max(s.maxN, jobs[i].shape.N);
+        s.smem = std::max(s.smem, (l == 0 && fused[i])
+                                      ? expand_fused_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N)
+                                      : expand_smem_bytes(jobs[i].shape.N));
       }
     }
     s.prefix.push_back(acc);
@@ -642,6 +654,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     P.model = j.model->dev;
     P.lvl_off = j.lvl_off;
     P.reuse_root = j.reuse_root;
+    P.root_fused = fused[i];
     for (int l = 0; l <= kMaxDepth; ++l)
       P.node_off[l] = (l <= sh.D) ? j.root_idx * ipow(sh.AW, l) : 0ull;
     char *base = j.own_arena ? j.own_arena : arena + j.arena_off;
@@ -749,7 +762,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       cudaError_t e = cudaSuccess;
       switch (sb.family) {
         case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
-        case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.maxN, grids[k], stream); break;
+        case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.smem, grids[k], stream); break;
         case F_LEAF: e = launch_leaf(sb.kind, dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
       }
       if (timed) timed_end(c, tl);

@@ -95,6 +95,8 @@ struct PlanDesc {
   // stands (reuse_root: level 0 already holds its particles and normalised log weights).
   int lvl_off, reuse_root;
   unsigned long long node_off[kMaxDepth + 1];
+  // the level-0 expansion prepares the root itself (no separate root preparation launch)
+  int root_fused;
   DevResult *result;
 };
 

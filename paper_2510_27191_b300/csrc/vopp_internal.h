@@ -60,9 +60,11 @@ constexpr int kCrowdLeafThreads = 160;
 constexpr size_t kLeafSmemLimit = 200 * 1024;
 size_t leaf_smem_bytes(int kind, int N, int AW);
 size_t expand_smem_bytes(int N);
+// an expansion stage whose level-0 items prepare the root themselves (PlanDesc::root_fused)
+size_t expand_fused_smem_bytes(int kind, int N);
 cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s);
 cudaError_t init_kernel_attributes();
-cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
+cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
                           long long grid, cudaStream_t s);
 // kind selects the model's leaf kernel (kNav, kGrid, kToy)
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,

@@ -710,9 +710,9 @@ __device__ void climb_warp(const PlanDesc &P, int l, unsigned long long node) {
 // K1: root preparation (one CTA per plan).
 // ---------------------------------------------------------------------------------------
 template <class M>
-__device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red) {
+__device__ void root_prepare(const PlanDesc &P, const DevModel &dm, const GNode<M> &dst, float *red,
+                             bool outputs) {
   const int N = P.N;
-  const GNode<M> dst = GNode<M>::at(P, 0, 0);
   // log weights of the caller's belief; terminal particles and non-positive weights -> -inf.
   // A reused root (a node of a kept tree) is taken as it stands: its particles and
   // normalised log weights are already in the level-0 store, terminal particles included
@@ -738,7 +738,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
   }
   m = block_max(m, red);
   if (!(m > -CUDART_INF_F)) {
-    if (threadIdx.x == 0) P.result->status |= kStatusDegenerateRoot;
+    if (threadIdx.x == 0 && outputs) P.result->status |= kStatusDegenerateRoot;
     return;
   }
   // one pass for the normaliser and the (unnormalised) weighted means of the position and
@@ -767,7 +767,7 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
       if (lw > -CUDART_INF_F) dst.set_lw(i, lw - lse);
     }
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && outputs) {
     if (P.D >= 2) P.cnt[0][0] = 0u;
     if (P.mu[0]) { P.mu[0][0] = mx; P.mu[0][1] = my; }
     if (P.D == 0) {
@@ -787,6 +787,11 @@ __device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red
       P.V[0][0] = hv;
     }
   }
+}
+
+template <class M>
+__device__ void root_prep_plan(const PlanDesc &P, const DevModel &dm, float *red) {
+  root_prepare<M>(P, dm, GNode<M>::at(P, 0, 0), red, true);
 }
 
 __global__ void __launch_bounds__(1024) k_root_prep(const PlanDesc *plans, StageTable st) {
@@ -816,6 +821,61 @@ __device__ void expand_item(const PlanDesc &P, int l, unsigned long long child, 
   build_child<M>(P, dm, l, child, src, dst, sc, red, false, false, nullptr);
 }
 
+// A node's particles laid out like a level store (GNode) in shared memory from `b`: NAV2D
+// x, y, lw; GRID / TOY2 s, lw; CROWD x, y, the people [12][N], lw, flags (root_node_words(kind)
+// 32-bit words per particle).
+template <class M> __device__ GNode<M> smem_node(float *b, int N);
+template <> __device__ GNode<NavModel> smem_node<NavModel>(float *b, int N) {
+  return GNode<NavModel>{b, b + N, b + 2 * N};
+}
+template <> __device__ GNode<GridModel> smem_node<GridModel>(float *b, int N) {
+  GNode<GridModel> r;
+  r.s = reinterpret_cast<int *>(b);
+  r.lwp = b + N;
+  return r;
+}
+template <> __device__ GNode<ToyModel> smem_node<ToyModel>(float *b, int N) {
+  GNode<ToyModel> r;
+  r.s = reinterpret_cast<int *>(b);
+  r.lwp = b + N;
+  return r;
+}
+template <> __device__ GNode<CrowdModel> smem_node<CrowdModel>(float *b, int N) {
+  return GNode<CrowdModel>{b, b + N, b + 2 * N, b + 14 * N, reinterpret_cast<int *>(b + 15 * N), N};
+}
+
+// A level-1 child of a plan whose root preparation rides in this stage: the CTA prepares
+// the root itself into shared memory (every child's CTA does, so no launch waits for a
+// separate root kernel), the CTA of child 0 also writes the level-0 store and the root's
+// outputs, and the child is built from the shared-memory root.
+template <class M>
+__device__ void expand_root_item(const PlanDesc &P, unsigned long long child, float *smem,
+                                 float *red) {
+  const DevModel &dm = *P.model;
+  const int N = P.N;
+  const GNode<M> root = smem_node<M>(smem + 2 * N, N);
+  const bool first = child == 0;
+  root_prepare<M>(P, dm, root, red, first);
+  __syncthreads();
+  if (first) {
+    const GNode<M> g = GNode<M>::at(P, 0, 0);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      g.put(i, root.get(i));
+      g.set_lw(i, root.lw(i));
+    }
+  }
+  const GNode<M> dst = GNode<M>::at(P, 1, (long long)child);
+  const ScratchArrays sc{smem, smem + N};
+  build_child<M>(P, dm, 0, child, root, dst, sc, red, false, false, nullptr);
+}
+
+template <class M>
+__device__ void expand_any(const PlanDesc &P, int l, unsigned long long child, float *smem,
+                           float *red) {
+  if (l == 0 && P.root_fused) expand_root_item<M>(P, child, smem, red);
+  else expand_item<M>(P, l, child, smem, red);
+}
+
 __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageTable st,
                                                 long long total) {
   extern __shared__ float smem[];
@@ -828,10 +888,10 @@ __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageT
     const int l = st.levels ? st.levels[pi] : st.level;
     const unsigned long long child = (unsigned long long)(item - st.prefix[pi]);
     switch (P.kind) {
-      case kNav: expand_item<NavModel>(P, l, child, smem, red); break;
-      case kGrid: expand_item<GridModel>(P, l, child, smem, red); break;
-      case kCrowd: expand_item<CrowdModel>(P, l, child, smem, red); break;
-      default: expand_item<ToyModel>(P, l, child, smem, red); break;
+      case kNav: expand_any<NavModel>(P, l, child, smem, red); break;
+      case kGrid: expand_any<GridModel>(P, l, child, smem, red); break;
+      case kCrowd: expand_any<CrowdModel>(P, l, child, smem, red); break;
+      default: expand_any<ToyModel>(P, l, child, smem, red); break;
     }
   }
 }
@@ -1375,6 +1435,10 @@ size_t leaf_smem_bytes(int kind, int N, int AW) {
   return pair * (size_t)((N + 1) / 2) + 6 * sizeof(float) * (size_t)AW + 64;
 }
 size_t expand_smem_bytes(int N) { return 8 * (size_t)N + 64; }
+size_t root_node_words(int kind) { return kind == kNav ? 3 : (kind == kCrowd ? 16 : 2); }
+size_t expand_fused_smem_bytes(int kind, int N) {
+  return expand_smem_bytes(N) + 4 * root_node_words(kind) * (size_t)N;
+}
 
 cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s) {
   k_root_prep<<<st.n_plans, 1024, 0, s>>>(d, st);
@@ -1419,9 +1483,9 @@ static cudaError_t launch_pdl(void (*k)(Args...), unsigned grid, unsigned thread
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, int maxN,
+cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
                           long long grid, cudaStream_t s) {
-  return launch_pdl(k_expand, (unsigned)grid, 256u, expand_smem_bytes(maxN), s, d, st, total);
+  return launch_pdl(k_expand, (unsigned)grid, 256u, smem, s, d, st, total);
 }
 
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
