@@ -388,6 +388,7 @@ VOPP_API int vopp_agent_reuse_info(const vopp_agent *agent, int32_t *adopted_slo
  * creation.  Paper: Alg. 1 "execute action, perceive
  * observation"; the paper's environments are simulators of the same models. */
 typedef struct vopp_env vopp_env;
+/* Create an environment of `model` at `state` (see above); destroy with vopp_env_destroy. */
 VOPP_API int vopp_env_create(vopp_model *model, const void *state, uint64_t seed, vopp_env **out);
 /* One step under `action`: obs receives the observation (host NAV2D float[2], GRID/TOY2/CROWD
  * int32[1]), reward and terminal (1 when the new state is terminal; terminal states are
@@ -541,6 +542,8 @@ typedef struct {
  * on a CUDA failure. */
 VOPP_API int vopp_pipe_rates(int device, vopp_pipe_rate *out, int32_t max_out, int32_t *n_out);
 
+/* The message of the last failing call on the calling thread (thread-local; valid until that
+ * thread's next failing call). */
 VOPP_API const char *vopp_last_error(void);
 /* Library version string. */
 VOPP_API const char *vopp_version(void);
