@@ -487,30 +487,35 @@ struct GridModel {
   struct O { int o; };
 
   __device__ __forceinline__ static bool terminal(const S &s) { return gterm(s.s) != 0; }
+  // The branch on the action is the same for a whole leaf branch; inside each action the
+  // per-particle cases (terminal, exit, rock) are selects, not branches.
   __device__ __forceinline__ static float step(S &st, int a, uint32_t, uint32_t,
                                                const DevModel &m) {
     const int s = st.s;
-    if (gterm(s)) return 0.0f;
-    int x = gx(s), y = gy(s), rocks = s & 0xFF;
+    const bool term = gterm(s) != 0;
+    const int x = gx(s), y = gy(s), rocks = s & 0xFF;
+    int ns;
     float r = 0.0f;
     if (a == 0) {
-      if (x == 10) { st.s = gpack(rocks, 11, y, 1); return 10.0f; }
-      x += 1;
+      const bool exit_e = x == 10;
+      ns = exit_e ? gpack(rocks, 11, y, 1) : gpack(rocks, x + 1, y, 0);
+      r = exit_e ? 10.0f : 0.0f;
     } else if (a == 1) {
-      x = (x > 0) ? x - 1 : x;
+      ns = gpack(rocks, (x > 0) ? x - 1 : x, y, 0);
     } else if (a == 2) {
-      y = (y < 10) ? y + 1 : y;
+      ns = gpack(rocks, x, (y < 10) ? y + 1 : y, 0);
     } else if (a == 3) {
-      y = (y > 0) ? y - 1 : y;
+      ns = gpack(rocks, x, (y > 0) ? y - 1 : y, 0);
     } else if (a == 4) {
-      const int rk = (x <= 10) ? m.rock_at[x + 11 * y] : -1;
-      if (rk >= 0) {
-        if ((rocks >> rk) & 1) { r = 10.0f; rocks &= ~(1 << rk); }
-        else r = -10.0f;
-      }
+      const int rk = (!term && x <= 10) ? m.rock_at[x + 11 * y] : -1;
+      const bool on = rk >= 0, good = on && ((rocks >> (rk & 7)) & 1);
+      r = on ? (good ? 10.0f : -10.0f) : 0.0f;
+      ns = gpack(good ? (rocks & ~(1 << (rk & 7))) : rocks, x, y, 0);
+    } else {
+      ns = s;
     }
-    st.s = gpack(rocks, x, y, 0);
-    return r;
+    st.s = term ? s : ns;
+    return term ? 0.0f : r;
   }
   __device__ __forceinline__ static int d2(const S &s, int rk, const DevModel &m) {
     const int dx = gx(s.s) - m.rock_x[rk], dy = gy(s.s) - m.rock_y[rk];
