@@ -638,23 +638,17 @@ struct CrowdModel {
       // distances are compared squared; the direction uses one reciprocal square root
       const float ex = __fsub_rn(s.px[i], nx), ey = __fsub_rn(s.py[i], ny);
       const float q0 = fmaf(ex, ex, __fmul_rn(ey, ey));
-      float mx = 0.0f, my = 0.0f;
-      if (q0 < 16.0f && q0 > 0.0f) {
-        const float inv = rsqrtf(q0);
-        const float d0 = q0 * inv;
-        const float ux = ex * inv, uy = ey * inv;
-        const uint32_t wr = (i < 4) ? (&w[3].x)[i] : (&w[4].x)[i - 4];
-        if (a == 4) {
-          mx = 2.0f * ux; my = 2.0f * uy;
-        } else if (wr < kReactThr) {
-          if ((traits >> i) & 1) {
-            const float st = fminf(d0, 0.3f);
-            mx = -st * ux; my = -st * uy;
-          } else {
-            mx = 0.8f * ux; my = 0.8f * uy;
-          }
-        }
-      }
+      // the reaction (selects, not per-particle branches): YELL pushes a nearby person 2 m
+      // away; otherwise with probability 0.9 a curious one steps toward the robot (at most
+      // 0.3 m, never past it), a shy one 0.8 m away
+      const bool near = q0 < 16.0f && q0 > 0.0f;
+      const float inv = rsqrtf(near ? q0 : 1.0f);
+      const float d0 = q0 * inv;
+      const float ux = ex * inv, uy = ey * inv;
+      const uint32_t wr = (i < 4) ? (&w[3].x)[i] : (&w[4].x)[i - 4];
+      const bool react = near && (a == 4 || wr < kReactThr);
+      const float sp = (a == 4) ? 2.0f : (((traits >> i) & 1) ? -fminf(d0, 0.3f) : 0.8f);
+      const float mx = react ? sp * ux : 0.0f, my = react ? sp * uy : 0.0f;
       const uint4 wb = w[i >> 1];
       const float2 g = (i & 1) ? box_muller(wb.z, wb.w) : box_muller(wb.x, wb.y);
       const float ddx = fmaf(0.05f, g.x, mx), ddy = fmaf(0.05f, g.y, my);
