@@ -1111,6 +1111,8 @@ void fill_grid_tables(DevModel &d, const vopp_model_desc &m) {
     d.l1macc[d2] = (acc < 1.0) ? (float)std::log(1.0 - acc) : -INFINITY;
     d.lacc2[d2] = (float)std::log2(acc);
     d.l1macc2[d2] = (acc < 1.0) ? (float)std::log2(1.0 - acc) : -INFINITY;
+    d.pacc[d2] = (float)acc;
+    d.p1macc[d2] = (float)(1.0 - acc);
   }
 }
 
@@ -1311,6 +1313,8 @@ int vopp_create_model(vopp_ctx *c, const vopp_model_desc *d, vopp_model **out) {
   h.toy_lw = (float)std::log(0.15);
   h.toy_lc2 = (float)std::log2(0.85);
   h.toy_lw2 = (float)std::log2(0.15);
+  h.toy_pc = 0.85f;
+  h.toy_pw = 0.15f;
   cudaSetDevice(c->device);
   if (cudaMalloc(&m->dev, sizeof(DevModel)) != cudaSuccess) {
     cudaGetLastError();

@@ -39,9 +39,11 @@ struct DevModel {
   unsigned long long thr[kGridD2];      // GRID: floor(acc(d2) 2^32), acc(0) -> 2^32
   float lacc[kGridD2], l1macc[kGridD2]; // GRID: log acc, log(1 - acc)   (-inf at acc = 1)
   float lacc2[kGridD2], l1macc2[kGridD2]; // the same in base 2
+  float pacc[kGridD2], p1macc[kGridD2]; // GRID: acc, 1 - acc
   unsigned long long toy_thr;           // TOY2: floor(0.85 2^32)
   float toy_lc, toy_lw;                 // TOY2: log 0.85, log 0.15
   float toy_lc2, toy_lw2;               // TOY2: log2 0.85, log2 0.15
+  float toy_pc, toy_pw;                 // TOY2: 0.85, 0.15
 };
 
 struct DevResult {
@@ -183,6 +185,13 @@ __device__ __forceinline__ float ex2(float x) {
 __device__ __forceinline__ float lg2(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Hardware reciprocal (PTX rcp.approx, flush-to-zero).
+__device__ __forceinline__ float rcpa(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -435,6 +444,21 @@ struct NavModel {
     const float2 d2 = fma2(ex, ex, mul2(ey, ey));
     return fma2(d2, is2, t);
   }
+  // The likelihoods of observation o for the two particles of a pair in linear form, up to
+  // one factor common to all particles: with c = log2(e) / 2 and pk = c / sigma^2,
+  // Z(o | s') = 2^(-|o - s'|^2 pk) pk / (2 pi c).  The factor 1 / (2 pi c) is dropped.
+  // sigma / sqrt(c) comes from one fused multiply-add, pk from one reciprocal.
+  __device__ __forceinline__ static float2 zlin_pair(float2 x, float2 y, const O &o) {
+    const float2 dm = add2(x, bc2(-9.0f));
+    const float2 sc = fma2(bc2(0.588705011f), make_float2(fabsf(dm.x), fabsf(dm.y)),
+                           bc2(0.0588705011f));          // (0.5 |x - 9| + 0.05) / sqrt(c)
+    const float2 s2 = mul2(sc, sc);
+    const float2 pk = make_float2(rcpa(s2.x), rcpa(s2.y));
+    const float2 ex = fma2(x, bc2(-1.0f), bc2(o.x)), ey = fma2(y, bc2(-1.0f), bc2(o.y));
+    const float2 d2 = fma2(ex, ex, mul2(ey, ey));
+    const float2 q = mul2(d2, make_float2(-pk.x, -pk.y));
+    return mul2(make_float2(ex2(q.x), ex2(q.y)), pk);
+  }
   // Heuristic of the pair; t0 / t1 are the terminal flags of the states.
   __device__ __forceinline__ static float2 heuristic_pair(float2 x, float2 y, bool t0, bool t1,
                                                           float log2g, float a0, float b0, bool hz) {
@@ -544,6 +568,14 @@ struct GridModel {
     const int dd = d2(s, rk, m);
     return ((o.o == 1) == (bit == 1)) ? m.lacc2[dd] : m.l1macc2[dd];
   }
+  // Z(o | s') itself
+  __device__ __forceinline__ static float zlin(const S &s, int a, const O &o, const DevModel &m) {
+    if (a < 5) return (o.o == 0) ? 1.0f : 0.0f;
+    if (o.o != 1 && o.o != 2) return 0.0f;
+    const int rk = a - 5, bit = (s.s >> rk) & 1;
+    const int dd = d2(s, rk, m);
+    return ((o.o == 1) == (bit == 1)) ? m.pacc[dd] : m.p1macc[dd];
+  }
   __device__ __forceinline__ static float heuristic(const S &s, float log2g, float, float, bool hz) {
     const float h = 10.0f * ex2((float)(10 - gx(s.s)) * log2g);
     return (hz || gterm(s.s)) ? 0.0f : h;
@@ -580,6 +612,10 @@ struct ToyModel {
   __device__ __forceinline__ static float loglik2(const S &s, int, const O &o, const DevModel &m) {
     if (o.o != 0 && o.o != 1) return -CUDART_INF_F;
     return (o.o == s.s) ? m.toy_lc2 : m.toy_lw2;
+  }
+  __device__ __forceinline__ static float zlin(const S &s, int, const O &o, const DevModel &m) {
+    if (o.o != 0 && o.o != 1) return 0.0f;
+    return (o.o == s.s) ? m.toy_pc : m.toy_pw;
   }
   __device__ __forceinline__ static float heuristic(const S &, float, float, float, bool) { return 0.0f; }
   __device__ __forceinline__ static float heuristic(const S &, const PlanDesc &) { return 0.0f; }
@@ -686,6 +722,10 @@ struct CrowdModel {
     if (o.o < 0 || o.o > 63) return -CUDART_INF_F;
     const int agree = 6 - __popc(((s.f >> 8) ^ o.o) & 0x3F);
     return (float)agree * -0.152003093f + (float)(6 - agree) * -3.32192809f;
+  }
+  // Z(o | s') = 2^(log2 Z), at least 2^-20 for a valid observation
+  __device__ __forceinline__ static float zlin(const S &s, int a, const O &o, const DevModel &m) {
+    return ex2(loglik2(s, a, o, m));
   }
   __device__ __forceinline__ static float loglik(const S &s, int a, const O &o, const DevModel &m) {
     return kLn2 * loglik2(s, a, o, m);

@@ -916,11 +916,12 @@ __global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageT
 #ifndef VOPP_LEAF_CROWD_MINBLOCKS
 #define VOPP_LEAF_CROWD_MINBLOCKS 3
 #endif
-#ifndef VOPP_LEAF_CHUNK_PACKED
-#define VOPP_LEAF_CHUNK_PACKED 4
-#endif
 constexpr int kLeafChunk = VOPP_LEAF_CHUNK;
-constexpr int kLeafChunkPacked = VOPP_LEAF_CHUNK_PACKED;   // pairs per rescale, packed path
+#ifndef VOPP_LEAF_CHUNK_LIN
+#define VOPP_LEAF_CHUNK_LIN 4
+#endif
+constexpr int kLeafChunkLin = VOPP_LEAF_CHUNK_LIN;   // pairs per compensated add, linear sums
+constexpr int kLeafChunkLog = 1;                     // pairs per rescale, log-domain sums
 
 // Running max-shifted sums in base 2: S = sum 2^(L - m) and H = sum 2^(L - m) h, compensated.
 struct ShiftedSum {
@@ -956,23 +957,19 @@ __device__ __forceinline__ float leaf_heuristic(const typename M::S &s, float lo
   else return M::heuristic(s, log2g, a0, b0, hz);
 }
 
-// The branch's sampled observation and representative come from the CTA's table (sm_ox,
-// sm_oy, sm_rep), computed once per node.
+// Leaf sums of one branch, log domain: S1 = sum 2^(L - m1) with L = lw2 + log2 Z and a
+// running shift m1, S0 = sum 2^(log2 Z - m0) with its own shift, H = sum 2^(L - m1) h, and
+// the reward mean.  Exact in relative terms however small the weights: the path for
+// enumerated observations, and for the rare branch whose linear sums are too small.
 template <class M>
-__device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNode<M> &nb,
-                                int l, unsigned long long node, int slot, float *sm_rb,
-                                float *sm_lo, float *sm_v, const float *sm_ox,
-                                const float *sm_oy, const int *sm_rep) {
-  const int lane = threadIdx.x & 31, N = P.N, W = P.W;
-  const int a = slot / W, k = slot - (slot / W) * W;
+__device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel &dm,
+                                           const SNode<M> &nb, int a, uint32_t c1,
+                                           unsigned long long kn, const typename M::O o,
+                                           float &rbar_out, float &lom_out, float &v_out) {
+  const int lane = threadIdx.x & 31, N = P.N;
   const float log2g = P.log2_gamma, h_a0 = P.h_a0, h_b0 = P.h_b0;
   const bool hz = P.h_zero != 0;
-  const unsigned long long kn = key_node(P, l, node);
-  const int j = sm_rep[slot];
-  const typename M::O o = obs_from_f2<M>(make_float2(sm_ox[slot], sm_oy[slot]));
-
   const uint32_t key0 = P.key0, key1 = P.key1;
-  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
   const uint32_t c2 = (uint32_t)kn, c3 = (uint32_t)(kn >> 32);
   ShiftedSum A1, A0;
   A1.init();
@@ -983,12 +980,12 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   if constexpr (M::kPairPacked) {
     // both particles of a pair through one two-wide instruction stream
     const float dx = NavModel::dx_of(a), dy = NavModel::dy_of(a);
-    for (int base = lane; base < npairs; base += 32 * kLeafChunkPacked) {
-      float2 L[kLeafChunkPacked], E[kLeafChunkPacked], Hh[kLeafChunkPacked];
+    for (int base = lane; base < npairs; base += 32 * kLeafChunkLog) {
+      float2 L[kLeafChunkLog], E[kLeafChunkLog], Hh[kLeafChunkLog];
       float2 rsum = make_float2(0.f, 0.f);
       float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F;
 #pragma unroll
-      for (int c = 0; c < kLeafChunkPacked; ++c) {
+      for (int c = 0; c < kLeafChunkLog; ++c) {
         const int p = base + 32 * c;
         L[c] = E[c] = bc2(-CUDART_INF_F);
         Hh[c] = bc2(0.f);
@@ -1013,7 +1010,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
       float2 s1 = bc2(0.f), h1 = bc2(0.f), s0 = bc2(0.f);
       if (m1 > -CUDART_INF_F) {
 #pragma unroll
-        for (int c = 0; c < kLeafChunkPacked; ++c) {
+        for (int c = 0; c < kLeafChunkLog; ++c) {
           const float2 d = add2(L[c], bc2(-m1));
           const float2 x1 = make_float2(ex2(d.x), ex2(d.y));   // L = -inf gives 0
           s1 = add2(s1, x1);
@@ -1022,7 +1019,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
       }
       if (m0 > -CUDART_INF_F) {
 #pragma unroll
-        for (int c = 0; c < kLeafChunkPacked; ++c) {
+        for (int c = 0; c < kLeafChunkLog; ++c) {
           const float2 d = add2(E[c], bc2(-m0));
           s0 = add2(s0, make_float2(ex2(d.x), ex2(d.y)));
         }
@@ -1035,7 +1032,7 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   } else {
   // a self-drawing model's step is long: one pair per chunk keeps the unrolled loop small
   // enough for the instruction cache
-  constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
+  constexpr int kCh = 1;
   for (int base = lane; base < npairs; base += 32 * kCh) {
     float L[2 * kCh], E[2 * kCh], Hh[2 * kCh];
     float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rsum = 0.f;
@@ -1094,12 +1091,127 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   warp_lse2(m1, s1, h1);
   warp_lse2(m0, s0, h0);
   const float rbar = warp_sum(R.value());
+  const float lse1 = (s1 > 0.f) ? kLn2 * (m1 + lg2(s1)) : -CUDART_INF_F;
+  if (P.branch_mode == kEnumerate) lom_out = lse1;
+  else lom_out = (lse1 > -CUDART_INF_F) ? __logf((float)N) + lse1 - kLn2 * (m0 + lg2(s0)) : -CUDART_INF_F;
+  v_out = (s1 > 0.f) ? h1 / s1 : 0.f;
+  rbar_out = rbar;
+}
+
+// Linear sums of sampled-observation branches: z_i = Z(o | s'_i) up to a factor common to
+// the branch (the model's zlin), S0 = sum z_i, S1 = sum w_i z_i, H = sum w_i z_i h_i, so
+// that omega = N S1 / S0 and V = H / S1 need neither a logarithm per particle nor a running
+// maximum.  The weights w_i are the node's normalised linear weights.  A particle whose z_i
+// or w_i z_i flushes to zero loses at most 2^-126 x 288.5 (the largest z) of a sum, N x that
+// over the branch, far below 2^-64: when S1 is at least 2^-64 the sums are exact to FP32
+// rounding; otherwise (false returned, the same in every lane) the caller recomputes the
+// branch in the log domain.
+constexpr float kLinMinS1 = 5.42101086e-20f;   // 2^-64
+template <class M>
+__device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel &dm,
+                                              const SNode<M> &nb, int a, uint32_t c1,
+                                              unsigned long long kn, const typename M::O o,
+                                              float &rbar_out, float &lom_out, float &v_out) {
+  const int lane = threadIdx.x & 31, N = P.N;
+  const float log2g = P.log2_gamma, h_a0 = P.h_a0, h_b0 = P.h_b0;
+  const bool hz = P.h_zero != 0;
+  const uint32_t key0 = P.key0, key1 = P.key1;
+  const uint32_t c2 = (uint32_t)kn, c3 = (uint32_t)(kn >> 32);
+  Kahan S0, S1, H, R;
+  S0.init();
+  S1.init();
+  H.init();
+  R.init();
+  const int npairs = (N + 1) >> 1;
+  if constexpr (M::kPairPacked) {
+    const float dx = NavModel::dx_of(a), dy = NavModel::dy_of(a);
+    for (int base = lane; base < npairs; base += 32 * kLeafChunkLin) {
+      float2 s0 = bc2(0.f), s1 = bc2(0.f), h1 = bc2(0.f), rs = bc2(0.f);
+#pragma unroll
+      for (int c = 0; c < kLeafChunkLin; ++c) {
+        const int p = base + 32 * c;
+        if (p < npairs) {
+          const uint4 w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+          const float4 xy = nb.A_f4(p);            // (x0, x1, y0, y1)
+          const float4 b = nb.B[p];                // (lw2_0, lw2_1, w_0, w_1)
+          float2 X = make_float2(xy.x, xy.y), Y = make_float2(xy.z, xy.w);
+          bool t0, t1;
+          const float2 r = NavModel::step_pair(X, Y, dx, dy, w, t0, t1);
+          float2 z = NavModel::zlin_pair(X, Y, o_nav(o));
+          z.y = (2 * p + 1 < N) ? z.y : 0.f;       // the odd-N pad slot
+          const float2 wt = make_float2(b.z, b.w); // pad slot: w = 0
+          const float2 hh = NavModel::heuristic_pair(X, Y, t0, t1, log2g, h_a0, h_b0, hz);
+          const float2 wz = mul2(wt, z);
+          s0 = add2(s0, z);
+          s1 = add2(s1, wz);
+          h1 = fma2(wz, hh, h1);
+          rs = fma2(wt, r, rs);
+        }
+      }
+      S0.add(s0.x + s0.y);
+      S1.add(s1.x + s1.y);
+      H.add(h1.x + h1.y);
+      R.add(rs.x + rs.y);
+    }
+  } else {
+    constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
+    for (int base = lane; base < npairs; base += 32 * kCh) {
+      float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCh; ++c) {
+        const int p = base + 32 * c;
+        if (p < npairs) {
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          if (M::kStochastic) w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+          typename M::S x0, x1;
+          nb.get_pair(p, x0, x1);
+          const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+          const DrawCtx dc{key0, key1, kPurposeTransition, c1, kn};
+          const float r0 = step_particle<M>(x0, a, w, 2 * p, dc, dm);
+          const float r1 = step_particle<M>(x1, a, w, 2 * p + 1, dc, dm);
+          const float z0 = M::zlin(x0, a, o, dm);
+          const float z1 = (2 * p + 1 < N) ? M::zlin(x1, a, o, dm) : 0.f;
+          const float wz0 = b.z * z0, wz1 = b.w * z1;   // pad slot: w = 0
+          s0 += z0 + z1;
+          s1 += wz0 + wz1;
+          h1 = fmaf(wz0, leaf_heuristic<M>(x0, log2g, h_a0, h_b0, hz), h1);
+          h1 = fmaf(wz1, leaf_heuristic<M>(x1, log2g, h_a0, h_b0, hz), h1);
+          rs = fmaf(b.z, r0, rs);
+          rs = fmaf(b.w, r1, rs);
+        }
+      }
+      S0.add(s0);
+      S1.add(s1);
+      H.add(h1);
+      R.add(rs);
+    }
+  }
+  const float s1 = warp_sum(S1.value());
+  if (!(s1 >= kLinMinS1)) return false;
+  const float s0 = warp_sum(S0.value()), h1 = warp_sum(H.value());
+  rbar_out = warp_sum(R.value());
+  lom_out = __logf((float)N) + kLn2 * (lg2(s1) - lg2(s0));
+  v_out = h1 / s1;
+  return true;
+}
+
+// The branch's sampled observation and representative come from the CTA's table (sm_ox,
+// sm_oy, sm_rep), computed once per node.
+template <class M>
+__device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNode<M> &nb,
+                                int l, unsigned long long node, int slot, float *sm_rb,
+                                float *sm_lo, float *sm_v, const float *sm_ox,
+                                const float *sm_oy, const int *sm_rep) {
+  const int lane = threadIdx.x & 31, W = P.W;
+  const int a = slot / W, k = slot - (slot / W) * W;
+  const unsigned long long kn = key_node(P, l, node);
+  const int j = sm_rep[slot];
+  const typename M::O o = obs_from_f2<M>(make_float2(sm_ox[slot], sm_oy[slot]));
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  float rbar, lom, v;
+  if (P.branch_mode == kEnumerate || !leaf_sums_lin<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v))
+    leaf_sums_log<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v);
   if (lane == 0) {
-    const float lse1 = (s1 > 0.f) ? kLn2 * (m1 + lg2(s1)) : -CUDART_INF_F;
-    float lom;
-    if (P.branch_mode == kEnumerate) lom = lse1;
-    else lom = (lse1 > -CUDART_INF_F) ? __logf((float)N) + lse1 - kLn2 * (m0 + lg2(s0)) : -CUDART_INF_F;
-    const float v = (s1 > 0.f) ? h1 / s1 : 0.f;
     sm_rb[slot] = rbar;
     sm_lo[slot] = lom;
     sm_v[slot] = v;
