@@ -226,6 +226,10 @@ VOPP_API int vopp_model_num_actions(const vopp_model *model);
 /* ---- one plan (Alg. 1 with one full-width search and one backup) ---------------------- */
 /* root_states: NAV2D float[2N] (x then y), GRID/TOY2 int32[N], CROWD 15 rows of N words
  * (robot x, y, 12 people coordinates, int32 flags); root_weights: [N] or NULL.
+ * A GRID state is packed: bits 0-7 rock bits, 8-11 x in 0..11 (11 = exited), 12-15 y in
+ * 0..10, bit 16 terminal, bits 17-31 clear.  Host states outside that are rejected
+ * (VOPP_E_INVALID, also by vopp_agent_create and vopp_env_create); a device buffer is not
+ * read on the host, and its out-of-range fields are clamped on load.
  * Weights must be >= 0; particles that are terminal at the root get weight 0; zero total
  * weight returns VOPP_E_DEGENERATE.  pi_bar: [A] host weights or NULL (model's policy).
  * Errors: VOPP_E_INVALID for depth < 0 or > VOPP_MAX_DEPTH, width < 1, N < 1 or

@@ -1023,11 +1023,25 @@ int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *s
   return collect_results(c, c->slot, jobs, outs, statuses, true);
 }
 
+// GRID states as the kernels take them: bits 0-7 rocks, x (bits 8-11) in 0..11 with 11 =
+// exited, y (bits 12-15) in 0..10, bit 16 terminal, bits 17-31 clear.
+int check_grid_states(const vopp_model *m, const void *states, int n) {
+  if (m->desc.kind != VOPP_GRID) return VOPP_OK;
+  const int32_t *s = static_cast<const int32_t *>(states);
+  for (int i = 0; i < n; ++i) {
+    const int32_t v = s[i];
+    if ((v & ~0x1FFFF) != 0 || ((v >> 8) & 0xF) > 11 || ((v >> 12) & 0xF) > 10)
+      return fail(VOPP_E_INVALID, "grid state %d (0x%x) is not a packed state", i, (unsigned)v);
+  }
+  return VOPP_OK;
+}
+
 int make_job(vopp_ctx *c, vopp_model *m, const void *states, const float *weights, int N,
              const vopp_plan_params &p, uint32_t ptr_flags, Job &j) {
   int rc = validate_plan_args(m, N, p.depth, p.width, p.eta, p.gamma, p.pi_bar);
   if (rc) return rc;
   if (!states) return fail(VOPP_E_INVALID, "root_states is NULL");
+  if (!(ptr_flags & VOPP_PTR_DEVICE) && (rc = check_grid_states(m, states, N))) return rc;
   if (weights && !(ptr_flags & VOPP_PTR_DEVICE)) {
     double s = 0.0;
     for (int i = 0; i < N; ++i) {
@@ -1111,8 +1125,8 @@ void fill_grid_tables(DevModel &d, const vopp_model_desc &m) {
     d.l1macc[d2] = (acc < 1.0) ? (float)std::log(1.0 - acc) : -INFINITY;
     d.lacc2[d2] = (float)std::log2(acc);
     d.l1macc2[d2] = (acc < 1.0) ? (float)std::log2(1.0 - acc) : -INFINITY;
-    d.pacc[d2] = (float)acc;
-    d.p1macc[d2] = (float)(1.0 - acc);
+    d.pz[d2] = (float)acc;
+    d.pz[kGridD2 + d2] = (float)(1.0 - acc);
   }
 }
 
@@ -1543,6 +1557,17 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
     s += wi;
   }
   if (!(s > 0.0)) return fail(VOPP_E_DEGENERATE, "weights sum to 0");
+  if (m->desc.kind == VOPP_GRID) {
+    std::vector<int32_t> stmp;
+    const void *sh = states;
+    if (dev) {
+      stmp.resize(n);
+      CUDA_TRY(cudaMemcpy(stmp.data(), states, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+      sh = stmp.data();
+    }
+    const int rc = check_grid_states(m, sh, n);
+    if (rc) return rc;
+  }
   for (int i = 0; i < n; ++i) {
     const double wi = w ? w[i] : 1.0;
     lw[i] = wi > 0.0 ? (float)std::log(wi / s) : -INFINITY;
@@ -1599,6 +1624,7 @@ int vopp_agent_create(vopp_model *m, const void *states, const float *weights, i
 int vopp_env_create(vopp_model *m, const void *state, uint64_t seed, vopp_env **out) {
   if (!m || !state || !out) return fail(VOPP_E_INVALID, "NULL argument");
   *out = nullptr;
+  if (const int rc = check_grid_states(m, state, 1)) return rc;
   vopp_ctx *c = m->ctx;
   cudaSetDevice(c->device);
   vopp_env *e = new (std::nothrow) vopp_env;

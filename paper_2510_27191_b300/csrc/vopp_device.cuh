@@ -39,7 +39,7 @@ struct DevModel {
   unsigned long long thr[kGridD2];      // GRID: floor(acc(d2) 2^32), acc(0) -> 2^32
   float lacc[kGridD2], l1macc[kGridD2]; // GRID: log acc, log(1 - acc)   (-inf at acc = 1)
   float lacc2[kGridD2], l1macc2[kGridD2]; // the same in base 2
-  float pacc[kGridD2], p1macc[kGridD2]; // GRID: acc, 1 - acc
+  float pz[2 * kGridD2];                 // GRID: acc, then 1 - acc
   unsigned long long toy_thr;           // TOY2: floor(0.85 2^32)
   float toy_lc, toy_lw;                 // TOY2: log 0.85, log 0.15
   float toy_lc2, toy_lw2;               // TOY2: log2 0.85, log2 0.15
@@ -512,31 +512,31 @@ struct GridModel {
 
   __device__ __forceinline__ static bool terminal(const S &s) { return gterm(s.s) != 0; }
   // The branch on the action is the same for a whole leaf branch; inside each action the
-  // per-particle cases (terminal, exit, rock) are selects, not branches.
+  // per-particle cases (terminal, exit, rock) are selects, not branches.  A non-terminal
+  // state has bit 16 clear and x <= 10, so a move changes one field by one without a carry
+  // (the exit sets x = 11 and the terminal bit together).
   __device__ __forceinline__ static float step(S &st, int a, uint32_t, uint32_t,
                                                const DevModel &m) {
     const int s = st.s;
     const bool term = gterm(s) != 0;
-    const int x = gx(s), y = gy(s), rocks = s & 0xFF;
-    int ns;
+    const int x = gx(s), y = gy(s);
+    int ns = s;
     float r = 0.0f;
     if (a == 0) {
       const bool exit_e = x == 10;
-      ns = exit_e ? gpack(rocks, 11, y, 1) : gpack(rocks, x + 1, y, 0);
+      ns = s + (exit_e ? 0x10100 : 0x100);
       r = exit_e ? 10.0f : 0.0f;
     } else if (a == 1) {
-      ns = gpack(rocks, (x > 0) ? x - 1 : x, y, 0);
+      ns = (x > 0) ? s - 0x100 : s;
     } else if (a == 2) {
-      ns = gpack(rocks, x, (y < 10) ? y + 1 : y, 0);
+      ns = (y < 10) ? s + 0x1000 : s;
     } else if (a == 3) {
-      ns = gpack(rocks, x, (y > 0) ? y - 1 : y, 0);
+      ns = (y > 0) ? s - 0x1000 : s;
     } else if (a == 4) {
       const int rk = (!term && x <= 10) ? m.rock_at[x + 11 * y] : -1;
-      const bool on = rk >= 0, good = on && ((rocks >> (rk & 7)) & 1);
+      const bool on = rk >= 0, good = on && ((s >> (rk & 7)) & 1);
       r = on ? (good ? 10.0f : -10.0f) : 0.0f;
-      ns = gpack(good ? (rocks & ~(1 << (rk & 7))) : rocks, x, y, 0);
-    } else {
-      ns = s;
+      ns = good ? (s & ~(1 << (rk & 7))) : s;
     }
     st.s = term ? s : ns;
     return term ? 0.0f : r;
@@ -568,13 +568,13 @@ struct GridModel {
     const int dd = d2(s, rk, m);
     return ((o.o == 1) == (bit == 1)) ? m.lacc2[dd] : m.l1macc2[dd];
   }
-  // Z(o | s') itself
+  // Z(o | s') itself: one load from the [agree, disagree][d^2] table
   __device__ __forceinline__ static float zlin(const S &s, int a, const O &o, const DevModel &m) {
     if (a < 5) return (o.o == 0) ? 1.0f : 0.0f;
     if (o.o != 1 && o.o != 2) return 0.0f;
-    const int rk = a - 5, bit = (s.s >> rk) & 1;
-    const int dd = d2(s, rk, m);
-    return ((o.o == 1) == (bit == 1)) ? m.pacc[dd] : m.p1macc[dd];
+    const int rk = a - 5;
+    const int miss = ((s.s >> rk) & 1) ^ (o.o == 1 ? 1 : 0);   // reading != the rock's bit
+    return m.pz[miss * kGridD2 + d2(s, rk, m)];
   }
   __device__ __forceinline__ static float heuristic(const S &s, float log2g, float, float, bool hz) {
     const float h = 10.0f * ex2((float)(10 - gx(s.s)) * log2g);

@@ -259,7 +259,10 @@ template <> __device__ __forceinline__ NavModel::S load_root<NavModel>(const Pla
   return NavModel::S{P.root_x[i], P.root_y[i]};
 }
 template <> __device__ __forceinline__ GridModel::S load_root<GridModel>(const PlanDesc &P, int i) {
-  return GridModel::S{P.root_s[i]};
+  // Host states are checked by the library; a device buffer's out-of-range fields are
+  // clamped (x <= 11, y <= 10, bits 17-31 cleared) so that every table index stays in range.
+  const int s = P.root_s[i];
+  return GridModel::S{(s & 0x100FF) | (min(gx(s), 11) << 8) | (min(gy(s), 10) << 12)};
 }
 template <> __device__ __forceinline__ ToyModel::S load_root<ToyModel>(const PlanDesc &P, int i) {
   return ToyModel::S{P.root_s[i]};
@@ -948,12 +951,13 @@ struct ShiftedSum {
 // GRID: the leaf heuristic per column x (it depends on x alone), filled by each leaf CTA
 // with the same arithmetic as GridModel::heuristic.
 __shared__ float s_grid_h[16];
+__shared__ float s_grid_z[2 * kGridD2];   // GRID leaf: Z by (disagree, d^2), from the model
 
 // The leaf heuristic (GRID: from the CTA's column table).
 template <class M>
 __device__ __forceinline__ float leaf_heuristic(const typename M::S &s, float log2g, float a0,
                                                 float b0, bool hz) {
-  if constexpr (std::is_same<M, GridModel>::value) return (hz || gterm(s.s)) ? 0.0f : s_grid_h[gx(s.s)];
+  if constexpr (std::is_same<M, GridModel>::value) return s_grid_h[gx(s.s)];
   else return M::heuristic(s, log2g, a0, b0, hz);
 }
 
@@ -1098,6 +1102,91 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
   rbar_out = rbar;
 }
 
+// GRID leaf branches other than collect, with the action's case decided once per branch.
+// A sense action keeps every state and earns 0, so only Z (from the shared-memory table by
+// d^2 and agreement) and h are per particle; a move changes one 4-bit field of the packed
+// state by one unless the field is at its blocking range [lo, hi] (east at x = 10 exits
+// instead: x = 11 and the terminal bit, +10).  The same states and rewards as
+// GridModel::step, which the collect action and the other kernels use.
+__device__ __forceinline__ void grid_branch_sums(const PlanDesc &P, const DevModel &dm,
+                                                 const SNode<GridModel> &nb, int a,
+                                                 GridModel::O o, Kahan &S0, Kahan &S1,
+                                                 Kahan &H, Kahan &R) {
+  const int lane = threadIdx.x & 31, N = P.N, npairs = (N + 1) >> 1;
+  constexpr int kCh = kLeafChunk;
+  if (a >= 5) {
+    const int rk = a - 5, rx = dm.rock_x[rk], ry = dm.rock_y[rk];
+    const int flip = (o.o == 1) ? 1 : 0;
+    const float zs = (o.o == 1 || o.o == 2) ? 1.0f : 0.0f;   // another reading: Z = 0
+    for (int base = lane; base < npairs; base += 32 * kCh) {
+      float s0 = 0.f, s1 = 0.f, h1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCh; ++c) {
+        const int p = base + 32 * c;
+        if (p < npairs) {
+          const int2 st = nb.A[p];
+          const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+          const int x0 = gx(st.x), x1 = gx(st.y);
+          const int dx0 = x0 - rx, dy0 = gy(st.x) - ry, dx1 = x1 - rx, dy1 = gy(st.y) - ry;
+          const int m0 = ((st.x >> rk) & 1) ^ flip, m1 = ((st.y >> rk) & 1) ^ flip;
+          const float z0 = zs * s_grid_z[m0 * kGridD2 + dx0 * dx0 + dy0 * dy0];
+          const float zr = zs * s_grid_z[m1 * kGridD2 + dx1 * dx1 + dy1 * dy1];
+          const float z1 = (2 * p + 1 < N) ? zr : 0.f;
+          const float wz0 = b.z * z0, wz1 = b.w * z1;   // pad slot: w = 0
+          s0 += z0 + z1;
+          s1 += wz0 + wz1;
+          h1 = fmaf(wz0, s_grid_h[x0], h1);
+          h1 = fmaf(wz1, s_grid_h[x1], h1);
+        }
+      }
+      S0.add(s0);
+      S1.add(s1);
+      H.add(h1);
+    }
+    return;                                  // R stays 0: a sense action earns nothing
+  }
+  // a = 0 E, 1 W, 2 N, 3 S
+  const int shift = (a < 2) ? 8 : 12;
+  const int lo = (a == 0 || a == 2) ? 10 : 0, span = (a == 2) ? 5 : 0;   // N: y >= 10 blocks
+  const int delta = (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000;
+  const int at_lim = (a == 0) ? 0x10100 : 0;
+  const float r_lim = (a == 0) ? 10.0f : 0.0f;
+  const float zc = (o.o == 0) ? 1.0f : 0.0f;  // a move's observation is NULL
+  for (int base = lane; base < npairs; base += 32 * kCh) {
+    float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
+#pragma unroll
+    for (int c = 0; c < kCh; ++c) {
+      const int p = base + 32 * c;
+      if (p < npairs) {
+        const int2 st = nb.A[p];
+        const float4 b = nb.B[p];
+        int ns[2];
+        float r[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int sv = i ? st.y : st.x;
+          const bool term = gterm(sv) != 0;
+          const bool blk = (unsigned)(((sv >> shift) & 0xF) - lo) <= (unsigned)span;
+          ns[i] = term ? sv : sv + (blk ? at_lim : delta);
+          r[i] = (term || !blk) ? 0.0f : r_lim;
+        }
+        const float z1 = (2 * p + 1 < N) ? zc : 0.f;
+        const float wz0 = b.z * zc, wz1 = b.w * z1;
+        s0 += zc + z1;
+        s1 += wz0 + wz1;
+        h1 = fmaf(wz0, s_grid_h[gx(ns[0])], h1);
+        h1 = fmaf(wz1, s_grid_h[gx(ns[1])], h1);
+        rs = fmaf(b.z, r[0], rs);
+        rs = fmaf(b.w, r[1], rs);
+      }
+    }
+    S0.add(s0);
+    S1.add(s1);
+    H.add(h1);
+    R.add(rs);
+  }
+}
+
 // Linear sums of sampled-observation branches: z_i = Z(o | s'_i) up to a factor common to
 // the branch (the model's zlin), S0 = sum z_i, S1 = sum w_i z_i, H = sum w_i z_i h_i, so
 // that omega = N S1 / S0 and V = H / S1 need neither a logarithm per particle nor a running
@@ -1153,6 +1242,8 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
       H.add(h1.x + h1.y);
       R.add(rs.x + rs.y);
     }
+  } else if (std::is_same<M, GridModel>::value && a != 4) {
+    if constexpr (std::is_same<M, GridModel>::value) grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R);
   } else {
     constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
     for (int base = lane; base < npairs; base += 32 * kCh) {
@@ -1239,9 +1330,14 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   float *sm_lo = sm_rb + AW, *sm_v = sm_lo + AW;
   __shared__ float2 s_mu;
   if constexpr (std::is_same<M, GridModel>::value) {
-    if (threadIdx.x < 16) {   // read after the node build's barriers
-      const GridModel::S col{gpack(0, threadIdx.x & 15, 0, 0)};
-      s_grid_h[threadIdx.x] = GridModel::heuristic(col, P.log2_gamma, P.h_a0, P.h_b0, false);
+    // the heuristic by column; x = 11 (exited) is the terminal column, 0 like a forced-zero
+    // heuristic (a terminal state with x <= 10 exists only at the root, with weight 0)
+    for (int i = threadIdx.x; i < 2 * kGridD2; i += blockDim.x) s_grid_z[i] = dm.pz[i];
+    if (threadIdx.x < 16) {   // both tables are read after the node build's barriers
+      const int x = threadIdx.x;
+      const GridModel::S col{gpack(0, x, 0, 0)};
+      s_grid_h[x] = (x <= 10 && P.h_zero == 0)
+                        ? GridModel::heuristic(col, P.log2_gamma, P.h_a0, P.h_b0, false) : 0.0f;
     }
   }
 

@@ -189,6 +189,35 @@ def test_invalid_arguments_are_rejected():
         g.close()
 
 
+def test_invalid_grid_states_are_rejected():
+    """A GRID state is bits 0-7 rocks, x in 0..11 (bits 8-11), y in 0..10 (bits 12-15) and
+    the terminal bit 16: host states outside that are refused by plans, agents and
+    environments."""
+    from paper_2510_27191_b300 import vopp as V
+    rx, ry = WL.grid_layout(1)
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        m = V.vopp_create_model(ctx, V.make_desc(WL.GRID, rock_x=rx, rock_y=ry))
+        good = int(WL.pack_grid_state(np.array([0x55]), 3, 4)[0])
+        ok = np.full(8, good, np.int32)
+        V.vopp_plan(m, ok, None, 8, 2, 2, 1.0, 0.9, None, 1)
+        for bad in (good | (1 << 17), (good & ~0xF00) | (12 << 8), (good & ~0xF000) | (11 << 12)):
+            st = ok.copy()
+            st[5] = bad
+            with pytest.raises(V.VoppError) as e:
+                V.vopp_plan(m, st, None, 8, 2, 2, 1.0, 0.9, None, 1)
+            assert e.value.code == V.VOPP_E_INVALID
+            with pytest.raises(V.VoppError) as e:
+                V.vopp_agent_create(m, st, None, 8, 3)
+            assert e.value.code == V.VOPP_E_INVALID
+            with pytest.raises(V.VoppError) as e:
+                V.vopp_env_create(m, bad, 3, WL.GRID)
+            assert e.value.code == V.VOPP_E_INVALID
+        V.vopp_model_destroy(m)
+    finally:
+        V.vopp_ctx_destroy(ctx)
+
+
 def test_config2_root_and_sampled_subtrees():
     """NAV2D, N=1024, depth 4, 4x4 branches, eta 0.5, distance-softmax reference policy:
     root Q/V against the full oracle; every node of three sampled level-2 subtrees."""
