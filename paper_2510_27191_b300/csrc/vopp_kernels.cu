@@ -952,6 +952,7 @@ struct ShiftedSum {
 // with the same arithmetic as GridModel::heuristic.
 __shared__ float s_grid_h[16];
 __shared__ float s_grid_z[2 * kGridD2];   // GRID leaf: Z by (disagree, d^2), from the model
+__shared__ int s_grid_rock[121];          // GRID leaf: rock index of cell x + 11 y, or -1
 
 // The leaf heuristic (GRID: from the CTA's column table).
 template <class M>
@@ -1102,12 +1103,12 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
   rbar_out = rbar;
 }
 
-// GRID leaf branches other than collect, with the action's case decided once per branch.
-// A sense action keeps every state and earns 0, so only Z (from the shared-memory table by
-// d^2 and agreement) and h are per particle; a move changes one 4-bit field of the packed
-// state by one unless the field is at its blocking range [lo, hi] (east at x = 10 exits
-// instead: x = 11 and the terminal bit, +10).  The same states and rewards as
-// GridModel::step, which the collect action and the other kernels use.
+// GRID leaf branches, with the action's case decided once per branch.  A sense action
+// keeps every state and earns 0, so only Z (from the shared-memory table by d^2 and
+// agreement) and h are per particle; a move changes one 4-bit field of the packed state by
+// one unless the field is at its blocking range [lo, hi] (east at x = 10 exits instead:
+// x = 11 and the terminal bit, +10); collect keeps the cell and reads its rock.  The same
+// states and rewards as GridModel::step, which the other kernels use.
 __device__ __forceinline__ void grid_branch_sums(const PlanDesc &P, const DevModel &dm,
                                                  const SNode<GridModel> &nb, int a,
                                                  GridModel::O o, Kahan &S0, Kahan &S1,
@@ -1144,6 +1145,43 @@ __device__ __forceinline__ void grid_branch_sums(const PlanDesc &P, const DevMod
       H.add(h1);
     }
     return;                                  // R stays 0: a sense action earns nothing
+  }
+  if (a == 4) {   // collect: x and y stay, a rock under the agent pays +10 (good) or -10
+    const float zc = (o.o == 0) ? 1.0f : 0.0f;
+    for (int base = lane; base < npairs; base += 32 * kCh) {
+      float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCh; ++c) {
+        const int p = base + 32 * c;
+        if (p < npairs) {
+          const int2 st = nb.A[p];
+          const float4 b = nb.B[p];
+          float r[2], hv[2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int sv = i ? st.y : st.x;
+            const int x = gx(sv);
+            const int rk = (gterm(sv) == 0 && x <= 10) ? s_grid_rock[x + 11 * gy(sv)] : -1;
+            const bool good = rk >= 0 && ((sv >> (rk & 7)) & 1);
+            r[i] = (rk >= 0) ? (good ? 10.0f : -10.0f) : 0.0f;
+            hv[i] = s_grid_h[x];
+          }
+          const float z1 = (2 * p + 1 < N) ? zc : 0.f;
+          const float wz0 = b.z * zc, wz1 = b.w * z1;
+          s0 += zc + z1;
+          s1 += wz0 + wz1;
+          h1 = fmaf(wz0, hv[0], h1);
+          h1 = fmaf(wz1, hv[1], h1);
+          rs = fmaf(b.z, r[0], rs);
+          rs = fmaf(b.w, r[1], rs);
+        }
+      }
+      S0.add(s0);
+      S1.add(s1);
+      H.add(h1);
+      R.add(rs);
+    }
+    return;
   }
   // a = 0 E, 1 W, 2 N, 3 S
   const int shift = (a < 2) ? 8 : 12;
@@ -1242,7 +1280,7 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
       H.add(h1.x + h1.y);
       R.add(rs.x + rs.y);
     }
-  } else if (std::is_same<M, GridModel>::value && a != 4) {
+  } else if (std::is_same<M, GridModel>::value) {
     if constexpr (std::is_same<M, GridModel>::value) grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R);
   } else {
     constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
@@ -1333,6 +1371,7 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
     // the heuristic by column; x = 11 (exited) is the terminal column, 0 like a forced-zero
     // heuristic (a terminal state with x <= 10 exists only at the root, with weight 0)
     for (int i = threadIdx.x; i < 2 * kGridD2; i += blockDim.x) s_grid_z[i] = dm.pz[i];
+    for (int i = threadIdx.x; i < 121; i += blockDim.x) s_grid_rock[i] = dm.rock_at[i];
     if (threadIdx.x < 16) {   // both tables are read after the node build's barriers
       const int x = threadIdx.x;
       const GridModel::S col{gpack(0, x, 0, 0)};
