@@ -55,12 +55,12 @@ WORKLOADS = {
 # Leaf-kernel roofline: issue-bound FP32/INT/SFU arithmetic.  Algorithmic operations per
 # particle-step of the fused leaf step, counted operation by operation: NAV2D 83 (Philox 22,
 # Box-Muller 14, transition 18, likelihood in linear form 11, heuristic 7, the linear sums
-# with their compensation 8.5, loads 2), GRID 19.5 (no Philox; averaged over the 13 actions:
-# a sense step 19, a move 21, collect 18), TOY2 16, CROWD 525 (five Philox calls 220, six
+# with their compensation 8.5, loads 2), GRID 18.5 (no Philox; averaged over the 13 actions:
+# a sense step 18, a move 19, collect 19), TOY2 16, CROWD 525 (five Philox calls 220, six
 # Box-Muller pairs 84, the six people's reactions, moves and tests 180, robot, likelihood,
 # heuristic, sums and loads 41); and the issue peak of the B300: 148 SMs x 4 schedulers x
 # 32 lanes per clock at the maximum SM clock.
-ALG_INSTR_PER_STEP = {WL.NAV2D: 83.0, WL.GRID: 19.5, WL.TOY2: 16.0, WL.CROWD: 525.0}
+ALG_INSTR_PER_STEP = {WL.NAV2D: 83.0, WL.GRID: 18.5, WL.TOY2: 16.0, WL.CROWD: 525.0}
 SMS = 148
 LANES_PER_CLK = 128
 

@@ -1106,123 +1106,105 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
 // GRID leaf branches, with the action's case decided once per branch.  A sense action
 // keeps every state and earns 0, so only Z (from the shared-memory table by d^2 and
 // agreement) and h are per particle; a move changes one 4-bit field of the packed state by
-// one unless the field is at its blocking range [lo, hi] (east at x = 10 exits instead:
-// x = 11 and the terminal bit, +10); collect keeps the cell and reads its rock.  The same
-// states and rewards as GridModel::step, which the other kernels use.
-__device__ __forceinline__ void grid_branch_sums(const PlanDesc &P, const DevModel &dm,
-                                                 const SNode<GridModel> &nb, int a,
-                                                 GridModel::O o, Kahan &S0, Kahan &S1,
-                                                 Kahan &H, Kahan &R) {
-  const int lane = threadIdx.x & 31, N = P.N, npairs = (N + 1) >> 1;
+// one unless the field is at its blocking range [lo, lo + span] (east at x = 10 exits
+// instead: x = 11 and the terminal bit, +10); collect keeps the cell and reads its rock.  The
+// same states and rewards as GridModel::step, which the other kernels use.  A move's or
+// collect's reading is NULL (Z = 1) and a sense reading good or bad; any other reading has
+// Z = 0 everywhere and is left to the log-domain path (false returned).
+struct GridSense { int rk, rx, ry, flip; };
+struct GridMove { int shift, lo, span, delta, at_lim; float r_lim; };
+struct GridSums { float s0, s1, h1, rs; };
+
+__device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense &g, GridSums &t) {
+  const int x = gx(sv), dx = x - g.rx, dy = gy(sv) - g.ry;
+  const int miss = ((sv >> g.rk) & 1) ^ g.flip;
+  const float z = s_grid_z[miss * kGridD2 + dx * dx + dy * dy];
+  const float wz = w * z;
+  t.s0 += z;
+  t.s1 += wz;
+  t.h1 = fmaf(wz, s_grid_h[x], t.h1);
+}
+__device__ __forceinline__ void grid_move_one(int sv, float w, const GridMove &g, GridSums &t) {
+  const bool term = gterm(sv) != 0;
+  const bool blk = (unsigned)(((sv >> g.shift) & 0xF) - g.lo) <= (unsigned)g.span;
+  const int ns = term ? sv : sv + (blk ? g.at_lim : g.delta);
+  const float r = (term || !blk) ? 0.0f : g.r_lim;
+  t.s0 += 1.0f;
+  t.s1 += w;
+  t.h1 = fmaf(w, s_grid_h[gx(ns)], t.h1);
+  t.rs = fmaf(w, r, t.rs);
+}
+__device__ __forceinline__ void grid_collect_one(int sv, float w, GridSums &t) {
+  const int x = gx(sv);
+  const int rk = (gterm(sv) == 0 && x <= 10) ? s_grid_rock[x + 11 * gy(sv)] : -1;
+  const bool good = rk >= 0 && ((sv >> (rk & 7)) & 1);
+  const float r = (rk >= 0) ? (good ? 10.0f : -10.0f) : 0.0f;
+  t.s0 += 1.0f;
+  t.s1 += w;
+  t.h1 = fmaf(w, s_grid_h[x], t.h1);
+  t.rs = fmaf(w, r, t.rs);
+}
+
+// Every whole pair through `one` (chunks of kLeafChunk pairs per lane between compensated
+// adds), then the last particle of an odd N (no pad particle is stepped).
+template <class F>
+__device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F one, Kahan &S0,
+                                           Kahan &S1, Kahan &H, Kahan &R) {
+  const int lane = threadIdx.x & 31, nfull = N >> 1;
   constexpr int kCh = kLeafChunk;
-  if (a >= 5) {
-    const int rk = a - 5, rx = dm.rock_x[rk], ry = dm.rock_y[rk];
-    const int flip = (o.o == 1) ? 1 : 0;
-    const float zs = (o.o == 1 || o.o == 2) ? 1.0f : 0.0f;   // another reading: Z = 0
-    for (int base = lane; base < npairs; base += 32 * kCh) {
-      float s0 = 0.f, s1 = 0.f, h1 = 0.f;
-#pragma unroll
-      for (int c = 0; c < kCh; ++c) {
-        const int p = base + 32 * c;
-        if (p < npairs) {
-          const int2 st = nb.A[p];
-          const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
-          const int x0 = gx(st.x), x1 = gx(st.y);
-          const int dx0 = x0 - rx, dy0 = gy(st.x) - ry, dx1 = x1 - rx, dy1 = gy(st.y) - ry;
-          const int m0 = ((st.x >> rk) & 1) ^ flip, m1 = ((st.y >> rk) & 1) ^ flip;
-          const float z0 = zs * s_grid_z[m0 * kGridD2 + dx0 * dx0 + dy0 * dy0];
-          const float zr = zs * s_grid_z[m1 * kGridD2 + dx1 * dx1 + dy1 * dy1];
-          const float z1 = (2 * p + 1 < N) ? zr : 0.f;
-          const float wz0 = b.z * z0, wz1 = b.w * z1;   // pad slot: w = 0
-          s0 += z0 + z1;
-          s1 += wz0 + wz1;
-          h1 = fmaf(wz0, s_grid_h[x0], h1);
-          h1 = fmaf(wz1, s_grid_h[x1], h1);
-        }
-      }
-      S0.add(s0);
-      S1.add(s1);
-      H.add(h1);
-    }
-    return;                                  // R stays 0: a sense action earns nothing
-  }
-  if (a == 4) {   // collect: x and y stay, a rock under the agent pays +10 (good) or -10
-    const float zc = (o.o == 0) ? 1.0f : 0.0f;
-    for (int base = lane; base < npairs; base += 32 * kCh) {
-      float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
-#pragma unroll
-      for (int c = 0; c < kCh; ++c) {
-        const int p = base + 32 * c;
-        if (p < npairs) {
-          const int2 st = nb.A[p];
-          const float4 b = nb.B[p];
-          float r[2], hv[2];
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int sv = i ? st.y : st.x;
-            const int x = gx(sv);
-            const int rk = (gterm(sv) == 0 && x <= 10) ? s_grid_rock[x + 11 * gy(sv)] : -1;
-            const bool good = rk >= 0 && ((sv >> (rk & 7)) & 1);
-            r[i] = (rk >= 0) ? (good ? 10.0f : -10.0f) : 0.0f;
-            hv[i] = s_grid_h[x];
-          }
-          const float z1 = (2 * p + 1 < N) ? zc : 0.f;
-          const float wz0 = b.z * zc, wz1 = b.w * z1;
-          s0 += zc + z1;
-          s1 += wz0 + wz1;
-          h1 = fmaf(wz0, hv[0], h1);
-          h1 = fmaf(wz1, hv[1], h1);
-          rs = fmaf(b.z, r[0], rs);
-          rs = fmaf(b.w, r[1], rs);
-        }
-      }
-      S0.add(s0);
-      S1.add(s1);
-      H.add(h1);
-      R.add(rs);
-    }
-    return;
-  }
-  // a = 0 E, 1 W, 2 N, 3 S
-  const int shift = (a < 2) ? 8 : 12;
-  const int lo = (a == 0 || a == 2) ? 10 : 0, span = (a == 2) ? 5 : 0;   // N: y >= 10 blocks
-  const int delta = (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000;
-  const int at_lim = (a == 0) ? 0x10100 : 0;
-  const float r_lim = (a == 0) ? 10.0f : 0.0f;
-  const float zc = (o.o == 0) ? 1.0f : 0.0f;  // a move's observation is NULL
-  for (int base = lane; base < npairs; base += 32 * kCh) {
-    float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
+  for (int base = lane; base < nfull; base += 32 * kCh) {
+    GridSums t{0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int c = 0; c < kCh; ++c) {
       const int p = base + 32 * c;
-      if (p < npairs) {
+      if (p < nfull) {
         const int2 st = nb.A[p];
-        const float4 b = nb.B[p];
-        int ns[2];
-        float r[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int sv = i ? st.y : st.x;
-          const bool term = gterm(sv) != 0;
-          const bool blk = (unsigned)(((sv >> shift) & 0xF) - lo) <= (unsigned)span;
-          ns[i] = term ? sv : sv + (blk ? at_lim : delta);
-          r[i] = (term || !blk) ? 0.0f : r_lim;
-        }
-        const float z1 = (2 * p + 1 < N) ? zc : 0.f;
-        const float wz0 = b.z * zc, wz1 = b.w * z1;
-        s0 += zc + z1;
-        s1 += wz0 + wz1;
-        h1 = fmaf(wz0, s_grid_h[gx(ns[0])], h1);
-        h1 = fmaf(wz1, s_grid_h[gx(ns[1])], h1);
-        rs = fmaf(b.z, r[0], rs);
-        rs = fmaf(b.w, r[1], rs);
+        const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+        one(st.x, b.z, t);
+        one(st.y, b.w, t);
       }
     }
-    S0.add(s0);
-    S1.add(s1);
-    H.add(h1);
-    R.add(rs);
+    S0.add(t.s0);
+    S1.add(t.s1);
+    H.add(t.h1);
+    R.add(t.rs);
   }
+  if ((N & 1) && lane == 0) {
+    GridSums t{0.f, 0.f, 0.f, 0.f};
+    one(nb.A[nfull].x, nb.B[nfull].z, t);
+    S0.add(t.s0);
+    S1.add(t.s1);
+    H.add(t.h1);
+    R.add(t.rs);
+  }
+}
+
+__device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevModel &dm,
+                                                 const SNode<GridModel> &nb, int a,
+                                                 GridModel::O o, Kahan &S0, Kahan &S1,
+                                                 Kahan &H, Kahan &R) {
+  const int N = P.N;
+  if (a >= 5) {
+    if (o.o != 1 && o.o != 2) return false;
+    const int rk = a - 5;
+    const GridSense g{rk, dm.rock_x[rk], dm.rock_y[rk], (o.o == 1) ? 1 : 0};
+    grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
+               S0, S1, H, R);                 // R stays 0: a sense action earns nothing
+    return true;
+  }
+  if (o.o != 0) return false;
+  if (a == 4) {
+    grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_collect_one(sv, w, t); },
+               S0, S1, H, R);
+    return true;
+  }
+  // a = 0 E, 1 W, 2 N, 3 S; N is blocked at y >= 10
+  const GridMove g{(a < 2) ? 8 : 12, (a == 0 || a == 2) ? 10 : 0, (a == 2) ? 5 : 0,
+                   (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000,
+                   (a == 0) ? 0x10100 : 0, (a == 0) ? 10.0f : 0.0f};
+  grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_move_one(sv, w, g, t); },
+             S0, S1, H, R);
+  return true;
 }
 
 // Linear sums of sampled-observation branches: z_i = Z(o | s'_i) up to a factor common to
@@ -1281,7 +1263,9 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
       R.add(rs.x + rs.y);
     }
   } else if (std::is_same<M, GridModel>::value) {
-    if constexpr (std::is_same<M, GridModel>::value) grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R);
+    if constexpr (std::is_same<M, GridModel>::value) {
+      if (!grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R)) return false;
+    }
   } else {
     constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
     for (int base = lane; base < npairs; base += 32 * kCh) {
