@@ -924,6 +924,19 @@ constexpr int kLeafChunk = VOPP_LEAF_CHUNK;
 #define VOPP_LEAF_CHUNK_LIN 4
 #endif
 constexpr int kLeafChunkLin = VOPP_LEAF_CHUNK_LIN;   // pairs per compensated add, linear sums
+#ifndef VOPP_GRID_CHUNK
+#define VOPP_GRID_CHUNK 1
+#endif
+constexpr int kGridChunk = VOPP_GRID_CHUNK;          // pairs per compensated add, GRID loops
+#ifndef VOPP_LOG_COLD_GRID
+#define VOPP_LOG_COLD_GRID 1
+#endif
+#ifndef VOPP_LOG_COLD_NAV
+#define VOPP_LOG_COLD_NAV 1
+#endif
+template <class M> struct kLogCold { static constexpr bool value = false; };
+template <> struct kLogCold<GridModel> { static constexpr bool value = VOPP_LOG_COLD_GRID != 0; };
+template <> struct kLogCold<NavModel> { static constexpr bool value = VOPP_LOG_COLD_NAV != 0; };
 constexpr int kLeafChunkLog = 1;                     // pairs per rescale, log-domain sums
 
 // Running max-shifted sums in base 2: S = sum 2^(L - m) and H = sum 2^(L - m) h, compensated.
@@ -1145,13 +1158,20 @@ __device__ __forceinline__ void grid_collect_one(int sv, float w, GridSums &t) {
   t.rs = fmaf(w, r, t.rs);
 }
 
-// Every whole pair through `one` (chunks of kLeafChunk pairs per lane between compensated
-// adds), then the last particle of an odd N (no pad particle is stepped).
-template <class F>
+// Every whole pair through `one` (chunks of kGridChunk pairs per lane between compensated
+// adds), then the last particle of an odd N (no pad particle is stepped).  kR: sum the
+// rewards (a sense branch's are all 0).
+template <bool kR, class F>
 __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F one, Kahan &S0,
                                            Kahan &S1, Kahan &H, Kahan &R) {
   const int lane = threadIdx.x & 31, nfull = N >> 1;
-  constexpr int kCh = kLeafChunk;
+  constexpr int kCh = kGridChunk;
+  auto fold = [&](const GridSums &t) {
+    S0.add(t.s0);
+    S1.add(t.s1);
+    H.add(t.h1);
+    if (kR) R.add(t.rs);
+  };
   for (int base = lane; base < nfull; base += 32 * kCh) {
     GridSums t{0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -1164,18 +1184,12 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
         one(st.y, b.w, t);
       }
     }
-    S0.add(t.s0);
-    S1.add(t.s1);
-    H.add(t.h1);
-    R.add(t.rs);
+    fold(t);
   }
   if ((N & 1) && lane == 0) {
     GridSums t{0.f, 0.f, 0.f, 0.f};
     one(nb.A[nfull].x, nb.B[nfull].z, t);
-    S0.add(t.s0);
-    S1.add(t.s1);
-    H.add(t.h1);
-    R.add(t.rs);
+    fold(t);
   }
 }
 
@@ -1188,23 +1202,33 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
     if (o.o != 1 && o.o != 2) return false;
     const int rk = a - 5;
     const GridSense g{rk, dm.rock_x[rk], dm.rock_y[rk], (o.o == 1) ? 1 : 0};
-    grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
-               S0, S1, H, R);                 // R stays 0: a sense action earns nothing
+    grid_pairs<false>(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
+                      S0, S1, H, R);    // R stays 0: a sense action earns nothing
     return true;
   }
   if (o.o != 0) return false;
   if (a == 4) {
-    grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_collect_one(sv, w, t); },
-               S0, S1, H, R);
+    grid_pairs<true>(nb, N, [&](int sv, float w, GridSums &t) { grid_collect_one(sv, w, t); },
+                     S0, S1, H, R);
     return true;
   }
   // a = 0 E, 1 W, 2 N, 3 S; N is blocked at y >= 10
   const GridMove g{(a < 2) ? 8 : 12, (a == 0 || a == 2) ? 10 : 0, (a == 2) ? 5 : 0,
                    (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000,
                    (a == 0) ? 0x10100 : 0, (a == 0) ? 10.0f : 0.0f};
-  grid_pairs(nb, N, [&](int sv, float w, GridSums &t) { grid_move_one(sv, w, g, t); },
-             S0, S1, H, R);
+  grid_pairs<true>(nb, N, [&](int sv, float w, GridSums &t) { grid_move_one(sv, w, g, t); },
+                   S0, S1, H, R);
   return true;
+}
+
+// The log-domain sums out of line, for kernels whose hot loop should keep the instruction
+// cache to itself.
+template <class M>
+__device__ __noinline__ void leaf_sums_log_cold(const PlanDesc &P, const DevModel &dm,
+                                                const SNode<M> &nb, int a, uint32_t c1,
+                                                unsigned long long kn, const typename M::O o,
+                                                float &rbar_out, float &lom_out, float &v_out) {
+  leaf_sums_log<M>(P, dm, nb, a, c1, kn, o, rbar_out, lom_out, v_out);
 }
 
 // Linear sums of sampled-observation branches: z_i = Z(o | s'_i) up to a factor common to
@@ -1322,8 +1346,10 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
   const typename M::O o = obs_from_f2<M>(make_float2(sm_ox[slot], sm_oy[slot]));
   const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
   float rbar, lom, v;
-  if (P.branch_mode == kEnumerate || !leaf_sums_lin<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v))
-    leaf_sums_log<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v);
+  if (P.branch_mode == kEnumerate || !leaf_sums_lin<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v)) {
+    if constexpr (kLogCold<M>::value) leaf_sums_log_cold<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v);
+    else leaf_sums_log<M>(P, dm, nb, a, c1, kn, o, rbar, lom, v);
+  }
   if (lane == 0) {
     sm_rb[slot] = rbar;
     sm_lo[slot] = lom;
