@@ -924,6 +924,10 @@ constexpr int kLeafChunk = VOPP_LEAF_CHUNK;
 #define VOPP_LEAF_CHUNK_LIN 4
 #endif
 constexpr int kLeafChunkLin = VOPP_LEAF_CHUNK_LIN;   // pairs per compensated add, linear sums
+#ifndef VOPP_SELF_CHUNK
+#define VOPP_SELF_CHUNK 1
+#endif
+constexpr int kSelfChunk = VOPP_SELF_CHUNK;          // particles per compensated add, CROWD
 #ifndef VOPP_GRID_CHUNK
 #define VOPP_GRID_CHUNK 1
 #endif
@@ -1289,6 +1293,32 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
   } else if (std::is_same<M, GridModel>::value) {
     if constexpr (std::is_same<M, GridModel>::value) {
       if (!grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R)) return false;
+    }
+  } else if (SelfDraw<M>::value) {
+    // a self-drawing step is long and needs no pair words: one particle per loop body (the
+    // instruction cache), kSelfChunk particles per lane between compensated adds
+    const DrawCtx dc{key0, key1, kPurposeTransition, c1, kn};
+    for (int base = lane; base < N; base += 32 * kSelfChunk) {
+      float s0 = 0.f, s1 = 0.f, h1 = 0.f, rs = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < kSelfChunk; ++c) {
+        const int i = base + 32 * c;
+        if (i < N) {
+          typename M::S x = nb.get(i);
+          const float wi = nb.w(i);
+          const float r = step_particle<M>(x, a, make_uint4(0u, 0u, 0u, 0u), i, dc, dm);
+          const float z = M::zlin(x, a, o, dm);
+          const float wz = wi * z;
+          s0 += z;
+          s1 += wz;
+          h1 = fmaf(wz, leaf_heuristic<M>(x, log2g, h_a0, h_b0, hz), h1);
+          rs = fmaf(wi, r, rs);
+        }
+      }
+      S0.add(s0);
+      S1.add(s1);
+      H.add(h1);
+      R.add(rs);
     }
   } else {
     constexpr int kCh = SelfDraw<M>::value ? 1 : kLeafChunk;
