@@ -363,7 +363,7 @@ def config_leg(V, ctx, name, steps, warmup=1):
     return {"workload": _config(spec, None)["workload"], "plans": steps,
             "ms_per_plan": ms, "particle_steps": spec.steps,
             "particle_steps_per_s": spec.steps / (ms / 1e3),
-            "leaf": {"avg_launch_ms": leaf_s * 1e3, "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
+            "leaf": {"avg_launch_ms": leaf_s * 1e3, "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:g} instr per particle-step",
                      "frac": ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_s / peak_ops,
                      "share_of_plan": leaf_ms / max(sum(v[0] for v in kt.values()), 1e-9)}}
 
@@ -582,7 +582,7 @@ def main():
                          "frac": achieved_ops / peak_ops, "traffic": leaf_traffic(args.workload),
                          "traffic_unit": "DRAM bytes per launch (ncu capture, profiles/)",
                          "peak_source": f"148 SMs x 128 lanes/clk x {sm_max:.0f} MHz ({pk_src} max clock)",
-                         "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:.0f} instr per particle-step",
+                         "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:g} instr per particle-step",
                          "units_per_launch": leaf_steps, "avg_launch_ms": leaf_avg_s * 1e3,
                          "share_of_step": leaf_ms / max(total_kernel_ms, 1e-9),
                          "frac_of_measured_fp32_issue":
