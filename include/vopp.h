@@ -189,7 +189,10 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 #define VOPP_OPT_LEAF_THREADS 2
 #define VOPP_OPT_GRID_CAP 3
 #define VOPP_OPT_PERSISTENT 5   /* 1: leaf CTAs fill every SM once and pull work items from a
-                                   counter (largest items first); 0 (default): one CTA per item */
+                                   counter (largest items first); 0: one CTA per item; 2
+                                   (default): per model, persistent for GRID and TOY2 (the
+                                   grid leaf's many short items), one CTA per item for NAV2D
+                                   and CROWD; other values: VOPP_E_INVALID */
 #define VOPP_OPT_FP64_ROOT 6    /* 1: back the root up in FP64 (VOPP_FLAG_FP64_ROOT); 0 (default):
                                    FP32 with compensated sums, within the 1e-4 tolerance */
 #define VOPP_OPT_GRAPHS 7       /* 1: vopp_plan / vopp_plan_batch capture their launch sequence in

@@ -116,7 +116,8 @@ struct vopp_ctx {
   char *arena = nullptr;
   size_t arena_cap = 0;
   Slot slot;                     // the synchronous path's slot (stream = ctx stream)
-  int leaf_persistent = 0;       // persistent leaf CTAs pulling work from a counter
+  int leaf_persistent = 2;       // persistent leaf CTAs pulling work from a counter: 0 never,
+                                 // 1 always, 2 per model (GRID and TOY2)
   int fp64_root = 0;             // root backup in FP64
   int sm_count = 148;
   int tree_detail = VOPP_TREE_MINIMAL;
@@ -741,8 +742,10 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   for (size_t k = 0; k < stages.size(); ++k) {
     StageBuild &sb = stages[k];
     if (sb.family == F_LEAF) {
-      if (!c->leaf_persistent) sb.st.counter = nullptr;
-      grids[k] = c->leaf_persistent ? persistent_grid(c, sb.kind, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
+      const bool pers = (c->leaf_persistent == 2) ? (sb.kind == kGrid || sb.kind == kToy)
+                                                  : c->leaf_persistent != 0;
+      if (!pers) sb.st.counter = nullptr;
+      grids[k] = pers ? persistent_grid(c, sb.kind, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
     } else if (sb.family == F_EXPAND) {
       grids[k] = std::min<long long>(sb.total, c->grid_cap);
     } else {
@@ -1225,7 +1228,10 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       if (value < 1) return fail(VOPP_E_INVALID, "grid cap");
       c->grid_cap = (int)std::min<int64_t>(value, 1 << 30);
       return VOPP_OK;
-    case VOPP_OPT_PERSISTENT: c->leaf_persistent = value ? 1 : 0; return VOPP_OK;
+    case VOPP_OPT_PERSISTENT:
+      if (value < 0 || value > 2) return fail(VOPP_E_INVALID, "persistent option %lld", (long long)value);
+      c->leaf_persistent = (int)value;
+      return VOPP_OK;
     case VOPP_OPT_FP64_ROOT: c->fp64_root = value ? 1 : 0; return VOPP_OK;
     case VOPP_OPT_GRAPHS:
       c->use_graphs = value ? 1 : 0;

@@ -108,6 +108,34 @@ def test_leaf_threads_do_not_change_results():
     assert_close(b["q"], a["q"], "Q across leaf CTA sizes")
 
 
+@pytest.mark.parametrize("kind,N,D,W", [(WL.NAV2D, 300, 3, 2), (WL.GRID, 257, 3, 2)])
+def test_persistent_leaf_option_does_not_change_results(kind, N, D, W):
+    """Leaf CTAs per item (0), persistent CTAs pulling items from a counter (1) and the
+    per-model default (2: persistent for GRID) give bit-identical trees; other values are
+    rejected."""
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(kind, N, D, W, seed=13, root_seed=5)
+    out = []
+    for pers in (0, 1, 2):
+        g = Gpu(spec, detail=V.VOPP_TREE_FULL)
+        try:
+            V.vopp_ctx_set_option(g.ctx, V.VOPP_OPT_PERSISTENT, pers)
+            res = g.plan()
+            out.append((res, [g.read(V.VOPP_FIELD_V, l, (spec.A * W) ** l) for l in range(D + 1)]))
+            if pers == 2:
+                for bad in (-1, 3):
+                    with pytest.raises(V.VoppError) as e:
+                        V.vopp_ctx_set_option(g.ctx, V.VOPP_OPT_PERSISTENT, bad)
+                    assert e.value.code == V.VOPP_E_INVALID
+        finally:
+            g.close()
+    for res, levels in out[1:]:
+        np.testing.assert_array_equal(res["q"], out[0][0]["q"])
+        assert res["v_root"] == out[0][0]["v_root"] and res["action"] == out[0][0]["action"]
+        for a, b in zip(levels, out[0][1]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_device_inputs_equal_host_inputs():
     spec = Spec(WL.NAV2D, 500, 2, 3, weights="random", seed=2)
     g = Gpu(spec)
