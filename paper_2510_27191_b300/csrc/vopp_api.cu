@@ -409,6 +409,7 @@ struct StageBuild {
   int family;
   int level;
   int kind = -1;              // leaf stages: the model of every plan in the launch
+  bool long_step = false;     // expansion stages: a CROWD plan (five Philox calls per step)
   std::vector<int> plans, levels;
   std::vector<long long> prefix;
   long long total = 0;
@@ -538,6 +539,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
         s.prefix.push_back(acc);
         acc += nodes(jobs[i], l + 1);
         s.maxN = std::max(s.maxN, jobs[i].shape.N);
+        if (jobs[i].shape.kind == kCrowd) s.long_step = true;
         s.smem = std::max(s.smem, (l == 0 && fused[i])
                                       ? expand_fused_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N)
                                       : expand_smem_bytes(jobs[i].shape.N));
@@ -765,7 +767,12 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       cudaError_t e = cudaSuccess;
       switch (sb.family) {
         case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
-        case F_EXPAND: e = launch_expand(dd, sb.st, sb.total, sb.smem, grids[k], stream); break;
+        case F_EXPAND:
+          // a level of long steps with at most one CTA per SM takes wider CTAs (fewer
+          // particles per thread on its critical path; measured faster for CROWD only)
+          e = launch_expand(dd, sb.st, sb.total, sb.smem, grids[k],
+                            sb.long_step && grids[k] <= c->sm_count, stream);
+          break;
         case F_LEAF: e = launch_leaf(sb.kind, dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
       }
       if (timed) timed_end(c, tl);
@@ -794,6 +801,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     const StageBuild &sb = stages[k];
     put(&sb.family, sizeof sb.family);
     put(&sb.kind, sizeof sb.kind);
+    put(&sb.long_step, sizeof sb.long_step);
     put(&sb.total, sizeof sb.total);
     put(&sb.smem, sizeof sb.smem);
     put(&sb.maxN, sizeof sb.maxN);

@@ -64,8 +64,9 @@ size_t expand_smem_bytes(int N);
 size_t expand_fused_smem_bytes(int kind, int N);
 cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream_t s);
 cudaError_t init_kernel_attributes();
+// wide: the stage has at most one CTA per SM (wider CTAs, fewer particles per thread)
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                          long long grid, cudaStream_t s);
+                          long long grid, bool wide, cudaStream_t s);
 // kind selects the model's leaf kernel (kNav, kGrid, kToy)
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
                         size_t smem, int threads, long long grid, cudaStream_t s);

@@ -879,8 +879,16 @@ __device__ void expand_any(const PlanDesc &P, int l, unsigned long long child, f
   else expand_item<M>(P, l, child, smem, red);
 }
 
-__global__ void __launch_bounds__(256, 2) k_expand(const PlanDesc *plans, StageTable st,
-                                                long long total) {
+// 256-thread CTAs (two per SM); a level that the host marks wide (long steps, at most one
+// CTA per SM) takes kExpandWide threads per CTA, fewer particles per thread on its critical
+// path.
+#ifndef VOPP_EXPAND_WIDE
+#define VOPP_EXPAND_WIDE 512
+#endif
+constexpr int kExpandWide = VOPP_EXPAND_WIDE;
+template <int T>
+__global__ void __launch_bounds__(T, (T <= 256) ? 2 : 1) k_expand(const PlanDesc *plans, StageTable st,
+                                                              long long total) {
   extern __shared__ float smem[];
   __shared__ float red[kRedFloats];
   pdl_release_next();
@@ -1735,8 +1743,11 @@ cudaError_t launch_root_prep(const PlanDesc *d, const StageTable &st, cudaStream
 // Dynamic shared memory ceilings of the kernels that may exceed 48 KB (set once, before any
 // stream capture).
 cudaError_t init_kernel_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_expand<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kLeafSmemLimit);
+  if (e == cudaSuccess && kExpandWide > 256)
+    e = cudaFuncSetAttribute(k_expand<kExpandWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemLimit);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf<kNav>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kLeafSmemLimit);
@@ -1771,8 +1782,10 @@ static cudaError_t launch_pdl(void (*k)(Args...), unsigned grid, unsigned thread
 }
 
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
-                          long long grid, cudaStream_t s) {
-  return launch_pdl(k_expand, (unsigned)grid, 256u, smem, s, d, st, total);
+                          long long grid, bool wide, cudaStream_t s) {
+  if (kExpandWide > 256 && wide)
+    return launch_pdl(k_expand<kExpandWide>, (unsigned)grid, (unsigned)kExpandWide, smem, s, d, st, total);
+  return launch_pdl(k_expand<256>, (unsigned)grid, 256u, smem, s, d, st, total);
 }
 
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
