@@ -60,6 +60,26 @@ def test_nav_weight_far_from_likelihood(D):
     _full(Spec(WL.NAV2D, N, D, 2, eta=0.6, seed=17, root=dict(x=x, y=y, w=w)))
 
 
+@pytest.mark.parametrize("seed,D", [(1, 1), (4, 2)])
+def test_grid_branch_below_the_linear_range(seed, D):
+    """The agent stands on rock 0, where sensing is exact (acc = 1); every particle but one
+    says the rock is bad, the last (weight 1e-30) that it is good.  A rock-0 sense branch
+    whose representative is that particle reads "good": Z = 0 for all the others, so
+    S1 / S0 = e^-73, below the linear sums' 2^-64 floor, and the leaf recomputes the branch
+    in the log domain (the oracle confirms such a branch is in the tree)."""
+    rx, ry = WL.grid_layout(1)
+    N = 64
+    bits = np.zeros(N, np.int64)
+    bits[-1] = 1
+    s = WL.pack_grid_state(bits, rx[0], ry[0]).astype(np.int32)
+    w = np.ones(N, np.float32)
+    w[-1] = 1e-30
+    spec = Spec(WL.GRID, N, D, 3, seed=seed, root=dict(s=s, w=w))
+    res, orc = _full(spec)
+    lo = np.asarray(orc["lomega"][D]) - np.log(N)
+    assert np.nanmin(lo[np.isfinite(lo)]) < -64 * np.log(2.0)
+
+
 def test_nav_nav_dist_policy_and_weights():
     _full(Spec(WL.NAV2D, 200, 3, 2, eta=0.5, seed=9, pi_mode=WL.PI_NAV_SOFTMAX_DIST,
                weights="sparse", root_seed=4))
