@@ -11,7 +11,9 @@ eta = 0.5, gamma = 0.95, distance-softmax reference policy of temperature 2.  In
 synthetic and seeded; the root particles are resident in HBM when the timed region starts.
 
 `value` is particle-steps/s over the device-timed steps (CUDA events on the library's
-stream around each plan, L2 flushed before each step by writing 256 MB).  `e2e` repeats the
+stream: the start event before the plan, the end event right after vopp_plan_submit has
+enqueued it, so the interval is the plan on the device; L2 flushed before each step by
+writing 256 MB).  `e2e` repeats the
 measurement through the same C ABI with host root buffers (host->device copy of the inputs
 and device->host copy of the result inside the timed region).  N > 1 runs independent
 plans per rank (different seeds; no collective on the data path) and reports the
@@ -338,9 +340,10 @@ def config_leg(V, ctx, name, steps, warmup=1):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            V.vopp_plan(model, states, None, spec.N, spec.D, spec.W, spec.eta, spec.gamma, None,
-                        spec.seed + i)
-            b.record(stream)
+            V.vopp_plan_submit(model, states, None, spec.N, spec.D, spec.W, spec.eta, spec.gamma,
+                               None, spec.seed + i)
+            b.record(stream)                 # the plan's device time (see timed_pass)
+            V.vopp_plan_finish(ctx)
             b.synchronize()
             ts.append(a.elapsed_time(b))
         return ts
@@ -496,15 +499,26 @@ def main():
         return V.vopp_plan(model, states, None, spec.N, spec.D, spec.W, spec.eta, spec.gamma,
                            None, seed)
 
-    def timed_pass(states, n_steps, seed0):
+    def timed_pass(states, n_steps, seed0, device_timed=False):
+        """device_timed: the end event is recorded as soon as the plan is enqueued
+        (vopp_plan_submit), so the time is the plan's on the device; otherwise after the
+        synchronous vopp_plan returns (its stream synchronisation and result collection on
+        the host included, as a caller of vopp_plan sees it)."""
         times, res = [], None
         for i in range(n_steps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
+            seed = seeds[(seed0 + i) % len(seeds)]
             a.record(stream)
-            res = plan(states, seeds[(seed0 + i) % len(seeds)])
-            b.record(stream)
+            if device_timed:
+                V.vopp_plan_submit(model, states, None, spec.N, spec.D, spec.W, spec.eta,
+                                   spec.gamma, None, seed)
+                b.record(stream)
+                res = V.vopp_plan_finish(ctx)
+            else:
+                res = plan(states, seed)
+                b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
         return times, res
@@ -518,7 +532,7 @@ def main():
     V.vopp_ctx_reset_kernel_times(ctx)
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
-        times, last = timed_pass(dev_states, args.steps, args.warmup)
+        times, last = timed_pass(dev_states, args.steps, args.warmup, device_timed=True)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if dist:

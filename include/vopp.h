@@ -243,6 +243,21 @@ VOPP_API int vopp_plan(vopp_model *model, const void *root_states, const float *
               int32_t n_particles, int32_t depth, int32_t width, float eta, float gamma,
               const float *pi_bar, uint64_t seed, uint32_t ptr_flags, vopp_plan_result *out);
 
+/* vopp_plan in two halves, for callers that overlap host work with the plan or time it on
+ * the device: vopp_plan_submit checks the arguments and enqueues the whole plan on the
+ * context's stream (same arguments and errors as vopp_plan; host inputs are copied before it
+ * returns, device inputs must stay valid until vopp_plan_finish); vopp_plan_finish waits for
+ * it and fills *out exactly as vopp_plan would.  One submitted plan per context: while it is
+ * pending, vopp_plan_submit, every plan call, tree reads, autotuning and option changes on
+ * the context return VOPP_E_BUSY; vopp_plan_finish with nothing pending returns
+ * VOPP_E_INVALID; vopp_ctx_destroy waits for a pending plan. */
+VOPP_API int vopp_plan_submit(vopp_model *model, const void *root_states, const float *root_weights,
+                              int32_t n_particles, int32_t depth, int32_t width, float eta,
+                              float gamma, const float *pi_bar, uint64_t seed, uint32_t ptr_flags);
+VOPP_API int vopp_plan_finish(vopp_ctx *ctx, vopp_plan_result *out);
+/* The context a model was created in (NULL for NULL). */
+VOPP_API vopp_ctx *vopp_model_ctx(const vopp_model *model);
+
 /* ---- anytime plan (Alg. 1 planning loop with iterative deepening, Eq. 3) --------------- */
 /* Iterations k = 1, 2, ..., params->depth: iteration k searches the full-width tree of
  * depth k with the plan's seed -- so a node has the same particles in every iteration --

@@ -105,6 +105,7 @@ struct GraphCache {
     capture = nullptr;
   }
 };
+struct Job;   // one plan of a launch sequence (below)
 }  // namespace
 
 struct vopp_ctx {
@@ -116,6 +117,8 @@ struct vopp_ctx {
   char *arena = nullptr;
   size_t arena_cap = 0;
   Slot slot;                     // the synchronous path's slot (stream = ctx stream)
+  bool plan_pending = false;     // vopp_plan_submit enqueued a plan; vopp_plan_finish collects
+  std::vector<Job> pending_jobs;
   int leaf_persistent = 2;       // persistent leaf CTAs pulling work from a counter: 0 never,
                                  // 1 always, 2 per model (GRID and TOY2)
   int fp64_root = 0;             // root backup in FP64
@@ -1023,7 +1026,15 @@ int matching_branch(vopp_agent *g, int action, const float *obs_f, int obs_i, cu
   return -1;
 }
 
+// Calls that use the context's arena, stream order or last-plan record wait for a plan
+// that vopp_plan_submit left pending to be collected first.
+int check_not_pending(const vopp_ctx *c) {
+  return c->plan_pending ? fail(VOPP_E_BUSY, "a submitted plan is pending: call vopp_plan_finish")
+                         : VOPP_OK;
+}
+
 int run_jobs(vopp_ctx *c, std::vector<Job> &jobs, vopp_plan_result *outs, int *statuses) {
+  if (const int busy = check_not_pending(c)) return busy;
   int rc = ensure_arena(c, place_jobs(jobs));
   if (rc) return rc;
   c->slot.stream = c->stream;
@@ -1079,6 +1090,7 @@ int make_job(vopp_ctx *c, vopp_model *m, const void *states, const float *weight
 // kernel's node level; the others are already in place.  The next iteration starts while
 // the elapsed time is below budget_s (<= 0: no time limit) and k < the maximum depth.
 int run_anytime(vopp_ctx *c, Job &base, double budget_s, vopp_plan_result *out, int *depth_out) {
+  if (const int busy = check_not_pending(c)) return busy;
   const int K = base.p.depth;
   if (K < 1) return fail(VOPP_E_INVALID, "anytime planning needs a maximum depth >= 1");
   if (!(budget_s == budget_s)) return fail(VOPP_E_INVALID, "budget is NaN");
@@ -1220,12 +1232,14 @@ void vopp_ctx_destroy(vopp_ctx *c) {
 int vopp_ctx_set_tree_detail(vopp_ctx *c, int detail) {
   if (!c || (detail != VOPP_TREE_MINIMAL && detail != VOPP_TREE_FULL))
     return fail(VOPP_E_INVALID, "bad tree detail");
+  if (const int busy = check_not_pending(c)) return busy;
   c->tree_detail = detail;
   return VOPP_OK;
 }
 
 int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
   if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  if (const int busy = check_not_pending(c)) return busy;
   switch (option) {
     case VOPP_OPT_LEAF_GEN: c->leaf_gen = value ? 1 : 0; return VOPP_OK;
     case VOPP_OPT_LEAF_THREADS:
@@ -1252,6 +1266,7 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
 
 int vopp_ctx_set_timing(vopp_ctx *c, int enable) {
   if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
+  if (const int busy = check_not_pending(c)) return busy;
   c->timing = enable != 0;
   return VOPP_OK;
 }
@@ -1396,6 +1411,41 @@ int vopp_plan(vopp_model *m, const void *root_states, const float *root_weights,
   return run_jobs(c, jobs, out, nullptr);
 }
 
+int vopp_plan_submit(vopp_model *m, const void *root_states, const float *root_weights,
+                     int32_t N, int32_t depth, int32_t width, float eta, float gamma,
+                     const float *pi_bar, uint64_t seed, uint32_t ptr_flags) {
+  if (!m) return fail(VOPP_E_INVALID, "NULL argument");
+  vopp_ctx *c = m->ctx;
+  if (const int busy = check_not_pending(c)) return busy;
+  vopp_plan_params p{depth, width, eta, gamma, seed, pi_bar};
+  std::vector<Job> jobs(1);
+  int rc = make_job(c, m, root_states, root_weights, N, p, ptr_flags, jobs[0]);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  rc = ensure_arena(c, place_jobs(jobs));
+  if (rc) return rc;
+  c->slot.stream = c->stream;
+  rc = enqueue_jobs(c, c->slot, c->arena, jobs, c->timing, c->use_graphs ? &c->graph : nullptr);
+  if (rc) return rc;
+  c->pending_jobs = std::move(jobs);
+  c->plan_pending = true;
+  return VOPP_OK;
+}
+
+vopp_ctx *vopp_model_ctx(const vopp_model *m) { return m ? m->ctx : nullptr; }
+
+int vopp_plan_finish(vopp_ctx *c, vopp_plan_result *out) {
+  if (!c || !out) return fail(VOPP_E_INVALID, "NULL argument");
+  if (!c->plan_pending) return fail(VOPP_E_INVALID, "no submitted plan");
+  c->plan_pending = false;
+  cudaSetDevice(c->device);
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  timed_collect(c);
+  const int rc = collect_results(c, c->slot, c->pending_jobs, out, nullptr, true);
+  c->pending_jobs.clear();
+  return rc;
+}
+
 int vopp_plan_anytime(vopp_model *m, const void *root_states, const float *root_weights,
                       int32_t N, const vopp_plan_params *p, double budget_s, uint32_t ptr_flags,
                       vopp_plan_result *out, int32_t *depth_reached) {
@@ -1426,6 +1476,7 @@ int vopp_plan_batch(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, vopp_
 int vopp_autotune(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, int32_t reps,
                   vopp_tune_result *out) {
   if (!c || !reqs || !out || n < 1 || reps < 1) return fail(VOPP_E_INVALID, "bad autotune arguments");
+  if (const int busy = check_not_pending(c)) return busy;
   std::vector<Job> jobs(n);
   for (int i = 0; i < n; ++i) {
     const vopp_plan_request &r = reqs[i];
@@ -1514,6 +1565,7 @@ int vopp_tree_read(vopp_ctx *c, int32_t field, int32_t level, uint64_t offset, u
 int vopp_tree_read_plan(vopp_ctx *c, int32_t plan, int32_t field, int32_t level, uint64_t offset,
                         uint64_t count, void *dst, uint32_t ptr_flags) {
   if (!c || !dst) return fail(VOPP_E_INVALID, "NULL argument");
+  if (const int busy = check_not_pending(c)) return busy;
   if (plan < 0 || plan >= (int)c->last_desc.size()) return fail(VOPP_E_INVALID, "no such plan");
   const PlanDesc &P = c->last_desc[plan];
   if (level < 0 || level > P.D) return fail(VOPP_E_INVALID, "level %d", level);

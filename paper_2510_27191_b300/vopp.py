@@ -133,6 +133,10 @@ def _load():
         "vopp_grid_thresholds": ([ctypes.POINTER(u64), i32], ctypes.c_int),
         "vopp_plan": ([vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, fp, u64, u32,
                        ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_plan_submit": ([vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, fp, u64,
+                              u32], ctypes.c_int),
+        "vopp_plan_finish": ([vp, ctypes.POINTER(vopp_plan_result)], ctypes.c_int),
+        "vopp_model_ctx": ([vp], vp),
         "vopp_tree_read": ([vp, i32, i32, u64, u64, vp, u32], ctypes.c_int),
         "vopp_tree_read_plan": ([vp, i32, i32, i32, u64, u64, vp, u32], ctypes.c_int),
         "vopp_agent_create": ([vp, vp, vp, i32, u64, u32, ctypes.POINTER(vp)], ctypes.c_int),
@@ -320,6 +324,39 @@ def vopp_plan(model: int, root_states, root_weights, n_particles: int, depth: in
                         seed & 0xFFFFFFFFFFFFFFFF, ptr_flags, ctypes.byref(r)))
     del keep1, keep2
     return _result_dict(r, vopp_model_num_actions(model))
+
+
+_PENDING = {}   # ctx -> (number of actions, buffers kept alive until vopp_plan_finish)
+
+
+def vopp_plan_submit(model: int, root_states, root_weights, n_particles: int, depth: int,
+                     width: int, eta: float, gamma: float, pi_bar=None, seed: int = 0,
+                     ptr_flags: int | None = None) -> None:
+    """Enqueue a plan on its context's stream (vopp_plan's arguments); collect it with
+    vopp_plan_finish(ctx)."""
+    sp, sdev, keep1 = _addr(root_states)
+    wp, wdev, keep2 = _addr(root_weights)
+    if ptr_flags is None:
+        ptr_flags = VOPP_PTR_DEVICE if sdev else 0
+    pib = None
+    if pi_bar is not None:
+        pib = (ctypes.c_float * len(pi_bar))(*[float(v) for v in pi_bar])
+    check(lib.vopp_plan_submit(model, sp, wp, n_particles, depth, width, eta, gamma,
+                               ctypes.cast(pib, ctypes.POINTER(ctypes.c_float)) if pib is not None else None,
+                               seed & 0xFFFFFFFFFFFFFFFF, ptr_flags))
+    ctx = lib.vopp_model_ctx(model)
+    _PENDING[ctx] = (vopp_model_num_actions(model), (root_states, root_weights, keep1, keep2))
+
+
+def vopp_plan_finish(ctx: int) -> dict:
+    """Wait for the context's submitted plan; its vopp_plan_result as a dict."""
+    r = vopp_plan_result()
+    A, _ = _PENDING.get(ctx, (0, None))
+    try:
+        check(lib.vopp_plan_finish(ctx, ctypes.byref(r)))
+    finally:
+        _PENDING.pop(ctx, None)
+    return _result_dict(r, A)
 
 
 def vopp_plan_anytime(model: int, root_states, root_weights, n_particles: int, max_depth: int,

@@ -156,6 +156,39 @@ def test_persistent_leaf_option_does_not_change_results(kind, N, D, W):
             np.testing.assert_array_equal(a, b)
 
 
+def test_submit_and_finish_equal_the_synchronous_plan():
+    """vopp_plan_submit + vopp_plan_finish give vopp_plan's result bit for bit; while the
+    submitted plan is pending, plans, tree reads and option changes on its context are
+    refused (VOPP_E_BUSY); finishing twice is an error; a context destroyed with a plan
+    pending waits for it."""
+    from paper_2510_27191_b300 import vopp as V
+    spec = Spec(WL.NAV2D, 300, 3, 2, seed=21)
+    g = Gpu(spec)
+    try:
+        st = spec.states()
+        args = (300, 3, 2, spec.eta, spec.gamma, None, 5)
+        a = V.vopp_plan(g.model, st, None, *args)
+        V.vopp_plan_submit(g.model, st, None, *args)
+        busy = (lambda: V.vopp_plan_submit(g.model, st, None, *args),
+                lambda: V.vopp_plan(g.model, st, None, *args),
+                lambda: V.vopp_ctx_set_option(g.ctx, V.VOPP_OPT_GRAPHS, 0),
+                lambda: V.vopp_tree_read(g.ctx, V.VOPP_FIELD_V, 1, 4))
+        for call in busy:
+            with pytest.raises(V.VoppError) as e:
+                call()
+            assert e.value.code == V.VOPP_E_BUSY
+        b = V.vopp_plan_finish(g.ctx)
+        np.testing.assert_array_equal(b["q"], a["q"])
+        assert (b["v_root"], b["action"], b["flags"], b["particle_steps"]) == \
+            (a["v_root"], a["action"], a["flags"], a["particle_steps"])
+        with pytest.raises(V.VoppError) as e:
+            V.vopp_plan_finish(g.ctx)
+        assert e.value.code == V.VOPP_E_INVALID
+        V.vopp_plan_submit(g.model, st, None, *args)      # left pending for close()
+    finally:
+        g.close()
+
+
 def test_device_inputs_equal_host_inputs():
     spec = Spec(WL.NAV2D, 500, 2, 3, weights="random", seed=2)
     g = Gpu(spec)
