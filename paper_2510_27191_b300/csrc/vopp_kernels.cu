@@ -910,8 +910,14 @@ __global__ void __launch_bounds__(T, (T <= 256) ? 2 : 1) k_expand(const PlanDesc
 // ---------------------------------------------------------------------------------------
 // K3: leaf expansion of one level-(D-1) node, fused with its backup.
 // ---------------------------------------------------------------------------------------
-// Compile-time tuning of the leaf loop (results do not depend on them):
-//   VOPP_LEAF_CHUNK      Philox pairs per lane between two rescales of the running sums
+// Compile-time tuning of the leaf loop (results do not depend on them beyond the rounding
+// order of the compensated sums):
+//   VOPP_LEAF_CHUNK      pairs per lane between two compensated adds of the generic loops
+//                        (TOY2; the log-domain path's rescales)
+//   VOPP_LEAF_CHUNK_LIN  pairs per lane between two compensated adds, NAV2D linear sums
+//   VOPP_GRID_CHUNK      the same for the GRID branch loops (sense, move, collect)
+//   VOPP_SELF_CHUNK      particles per lane between two compensated adds, CROWD
+//   VOPP_LOG_COLD_NAV / VOPP_LOG_COLD_GRID  1: the log-domain fallback is an out-of-line call
 //   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
 //                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2;
 //                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD, whose CTAs have 160 threads)
