@@ -918,17 +918,17 @@ __global__ void __launch_bounds__(T, (T <= 256) ? 2 : 1) k_expand(const PlanDesc
 //   VOPP_GRID_CHUNK      the same for the GRID branch loops (sense, move, collect)
 //   VOPP_SELF_CHUNK      particles per lane between two compensated adds, CROWD
 //   VOPP_LOG_COLD_NAV / VOPP_LOG_COLD_GRID  1: the log-domain fallback is an out-of-line call
-//   VOPP_LEAF_MINBLOCKS  minimum resident 256-thread leaf CTAs per SM requested from the
-//                        compiler for the NAV2D kernel (VOPP_LEAF_GRID_MINBLOCKS: GRID, TOY2;
-//                        VOPP_LEAF_CROWD_MINBLOCKS: CROWD, whose CTAs have 160 threads)
+//   VOPP_LEAF_NAV_MAXREG registers per thread of the NAV2D leaf kernel (72: seven 128-thread
+//                        CTAs per SM); VOPP_LEAF_GRID_MAXREG: GRID and TOY2 (64);
+//                        VOPP_LEAF_CROWD_MINBLOCKS: resident 160-thread CROWD CTAs per SM (3)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
 #endif
-#ifndef VOPP_LEAF_MINBLOCKS
-#define VOPP_LEAF_MINBLOCKS 3
+#ifndef VOPP_LEAF_NAV_MAXREG
+#define VOPP_LEAF_NAV_MAXREG 72
 #endif
-#ifndef VOPP_LEAF_GRID_MINBLOCKS
-#define VOPP_LEAF_GRID_MINBLOCKS 4
+#ifndef VOPP_LEAF_GRID_MAXREG
+#define VOPP_LEAF_GRID_MAXREG 64
 #endif
 #ifndef VOPP_LEAF_CROWD_MINBLOCKS
 #define VOPP_LEAF_CROWD_MINBLOCKS 3
@@ -1503,14 +1503,14 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
 // One leaf kernel per model, so that each gets its own register allocation and occupancy;
 // a launch covers the leaf items of every plan of that model in one shared-memory class.
 template <int K> struct LeafModel;
-template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMinBlocks = VOPP_LEAF_MINBLOCKS; };
-template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
-template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMinBlocks = VOPP_LEAF_GRID_MINBLOCKS; };
-template <> struct LeafModel<kCrowd> { using type = CrowdModel; static constexpr int kMinBlocks = VOPP_LEAF_CROWD_MINBLOCKS; };
+template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMaxReg = VOPP_LEAF_NAV_MAXREG; };
+template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMaxReg = VOPP_LEAF_GRID_MAXREG; };
+template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMaxReg = VOPP_LEAF_GRID_MAXREG; };
+template <> struct LeafModel<kCrowd> { using type = CrowdModel; };
 
 template <int K>
-__global__ void __launch_bounds__(K == kCrowd ? kCrowdLeafThreads : 256, LeafModel<K>::kMinBlocks)
-k_leaf(const PlanDesc *plans, StageTable st, long long total) {
+__device__ __forceinline__ void leaf_kernel_body(const PlanDesc *plans, const StageTable &st,
+                                                 long long total) {
   extern __shared__ __align__(16) float smem[];
   __shared__ float red[kRedFloats];
   __shared__ long long s_item;
@@ -1537,6 +1537,17 @@ k_leaf(const PlanDesc *plans, StageTable st, long long total) {
       item += gridDim.x;
     }
   }
+}
+
+// NAV2D, GRID, TOY2: a register cap per model; CROWD: its 160-thread CTAs, three per SM
+template <int K>
+__global__ void __maxnreg__(LeafModel<K>::kMaxReg)
+k_leaf(const PlanDesc *plans, StageTable st, long long total) {
+  leaf_kernel_body<K>(plans, st, total);
+}
+__global__ void __launch_bounds__(kCrowdLeafThreads, VOPP_LEAF_CROWD_MINBLOCKS)
+k_leaf_crowd(const PlanDesc *plans, StageTable st, long long total) {
+  leaf_kernel_body<kCrowd>(plans, st, total);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1764,7 +1775,7 @@ cudaError_t init_kernel_attributes() {
     e = cudaFuncSetAttribute(k_leaf<kToy>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kLeafSmemLimit);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_leaf<kCrowd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_leaf_crowd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kLeafSmemLimit);
   return e;
 }
@@ -1800,7 +1811,7 @@ cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long 
     case kNav: return launch_pdl(k_leaf<kNav>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kGrid: return launch_pdl(k_leaf<kGrid>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
     case kToy: return launch_pdl(k_leaf<kToy>, (unsigned)grid, (unsigned)threads, smem, s, d, st, total);
-    case kCrowd: return launch_pdl(k_leaf<kCrowd>, (unsigned)grid, (unsigned)kCrowdLeafThreads, smem, s, d, st, total);
+    case kCrowd: return launch_pdl(k_leaf_crowd, (unsigned)grid, (unsigned)kCrowdLeafThreads, smem, s, d, st, total);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1810,7 +1821,7 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
     case kNav: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kNav>, threads, smem);
     case kGrid: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kGrid>, threads, smem);
     case kToy: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kToy>, threads, smem);
-    case kCrowd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf<kCrowd>, kCrowdLeafThreads, smem);
+    case kCrowd: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_leaf_crowd, kCrowdLeafThreads, smem);
     default: return cudaErrorInvalidValue;
   }
 }
