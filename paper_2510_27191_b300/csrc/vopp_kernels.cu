@@ -324,7 +324,7 @@ __device__ __forceinline__ float log_pibar(const PlanDesc &P, float2 mu, int a) 
 }
 
 // Philox pairs per thread between two rescales of a child build's running sums.
-constexpr int kBuildChunk = 2;
+constexpr int kBuildChunk = 1;
 // Floats of the block-reduction buffer a child build needs (7 per-warp values, 32 warps).
 constexpr int kRedFloats = 32 * 7;
 
