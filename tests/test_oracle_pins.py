@@ -823,3 +823,106 @@ def test_toy2_matches_the_hand_derived_closed_form():
         np.testing.assert_allclose(r["q_root"], [q_stay, q_flip], rtol=0, atol=1e-11)
         assert abs(r["v_root"] - v) < 1e-11
         assert r["action"] == 0
+
+
+# ----------------------------------------------------------------------------------------
+# Distance-softmax reference policy (Sec. III-A; the large navigation workload's pi0).
+# ----------------------------------------------------------------------------------------
+_DIST_CASES = {
+    "A": ([(3.0, 4.0)] * 5, [1.0] * 5),
+    "B": ([(2.0, 6.0), (8.0, 2.0)], [1.0, 3.0]),
+    "C": ([(9.75, 0.5), (9.5, 0.75)], [1.0, 1.0]),
+    "E": ([(0.1, 0.2), (4.0, 1.0)], [1.0, 1.0]),
+}
+
+
+def _dist_fixture():
+    path = os.path.join(os.path.dirname(__file__), "golden", "nav_dist_pibar.txt")
+    rows = []
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            f = ln.split()
+            rows.append((f[0], float(f[1]), np.array(list(map(float, f[2:6])))))
+    assert len(rows) == 5
+    return rows
+
+
+def _dist_softmax_by_hand(mu, T):
+    """softmax_a(-|clamp(mu + delta_a, 0, 10)| / T), written out per action."""
+    moves = ((1.0, 0.0), (-1.0, 0.0), (0.0, 1.0), (0.0, -1.0))
+    z = []
+    for dx, dy in moves:
+        cx = min(max(mu[0] + dx, 0.0), 10.0)
+        cy = min(max(mu[1] + dy, 0.0), 10.0)
+        z.append(-math.sqrt(cx * cx + cy * cy) / T)
+    e = [math.exp(v - max(z)) for v in z]
+    return np.array(e) / sum(e)
+
+
+def test_dist_pibar_fixture_matches_its_formulas():
+    """The fixture's numbers equal softmax(-|clamp(mu + delta_a)| / T) at the means its
+    header derives by hand (weighted, terminal particles excluded at the root)."""
+    means = {"A": (3.0, 4.0), "B": (6.5, 3.0), "C": (9.625, 0.625), "E": (4.0, 1.0)}
+    for case, T, pib in _dist_fixture():
+        np.testing.assert_allclose(_dist_softmax_by_hand(means[case], T), pib, rtol=0, atol=1e-14)
+
+
+def _dist_root(case, N):
+    pts, ws = _DIST_CASES[case]
+    reps = N // len(pts)
+    x = np.repeat([p[0] for p in pts], reps).astype(np.float32)
+    y = np.repeat([p[1] for p in pts], reps).astype(np.float32)
+    w = np.repeat(ws, reps)
+    return x, y, w
+
+
+@pytest.mark.parametrize("row", range(5))
+def test_dist_pibar_depth0_policy_is_the_hand_derived_softmax(row):
+    """A depth-0 plan returns pibar itself: the fixture's values to 1e-12.  A wrong mean
+    weighting (case B), a missing clamp (case C), a temperature multiplied instead of divided
+    (cases B at T = 2 and 0.5) or a terminal particle kept in the root mean (case E) fails."""
+    case, T, pib = _dist_fixture()[row]
+    x, y, w = _dist_root(case, 4 if case != "A" else 5)
+    m = O.make_model(O.NAV2D, pi_mode=O.PI_NAV_DIST, pi_temp=T)
+    r = O.plan(m, len(x), 0, 2, 1.0, 0.95, 3, root_x=x, root_y=y, root_w=w, outputs=False)
+    assert r["status"] == O.OK
+    np.testing.assert_allclose(r["policy"], pib, rtol=1e-12, atol=0)
+    assert r["action"] == int(np.argmax(pib))
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("row", [1, 3])
+def test_dist_pibar_enters_the_root_backup(depth, row):
+    """In a plan with depth >= 1 the root's V and policy use the same pibar (Eq. 1):
+    log pibar = log pi* - (Q - V) / eta recovers the fixture's values."""
+    case, T, pib = _dist_fixture()[row]
+    x, y, w = _dist_root(case, 8)
+    eta = 0.5
+    m = O.make_model(O.NAV2D, pi_mode=O.PI_NAV_DIST, pi_temp=T)
+    r = O.plan(m, len(x), depth, 2, eta, 0.95, 11, root_x=x, root_y=y, root_w=w, outputs=False)
+    assert r["status"] == O.OK
+    lpi = np.log(r["policy"]) - (r["q_root"] - r["v_root"]) / eta
+    np.testing.assert_allclose(np.exp(lpi), pib, rtol=1e-11, atol=0)
+    assert r["action"] == int(np.argmax(r["q_root"] + eta * np.log(pib)))
+
+
+def test_dist_pibar_of_inner_nodes_uses_their_weighted_mean():
+    """Every level-1 node's V equals eta log sum_a pibar(a|n) exp(Q(n,a)/eta) with pibar
+    recomputed here from that node's own particles and (non-uniform) weights."""
+    N, D, W, eta, T = 40, 2, 3, 0.7, 2.0
+    x, y, _ = WL.nav_root(N, 21)
+    m = O.make_model(O.NAV2D, pi_mode=O.PI_NAV_DIST, pi_temp=T)
+    r = O.plan(m, N, D, W, eta, 0.95, 9, root_x=x, root_y=y, dump_levels=1)
+    assert r["status"] == O.OK
+    px, py, plw = r["px"][1], r["py"][1], r["plw"][1]
+    assert px.shape == (4 * W, N)
+    spread = 0.0
+    for n in range(4 * W):
+        w = np.exp(plw[n])
+        w = w / w.sum()
+        spread = max(spread, float(plw[n].max() - plw[n].min()))
+        mu = (float(w @ px[n]), float(w @ py[n]))
+        pib = _dist_softmax_by_hand(mu, T)
+        v = eta * logsumexp(np.log(pib) + r["Q"][1][n] / eta)
+        assert r["V"][1][n] == pytest.approx(v, rel=1e-12, abs=1e-12)
+    assert spread > 1.0      # the weights are far from uniform, so the weighting matters
