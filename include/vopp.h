@@ -464,13 +464,18 @@ VOPP_API void vopp_agent_destroy(vopp_agent *agent);
  *   ess_out, resampled_out   host, may be NULL
  * Its working memory is one static device array of about 1.5 MB compiled into the library
  * (every GPU that loads the library holds it until the process exits), so n is limited to
- * 65536 (CROWD, with 60-byte states: 20,000); larger n returns VOPP_E_INVALID.  The call issues no cudaMalloc / cudaFree and no
- * allocating library call.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  All calls share the one array, which keeps the previous call's contents, so
- * calls that overlap on the GPU (different streams or threads, or concurrent launches)
- * race: serialise them.  Blocks until the update is done.  VOPP_E_DEGENERATE leaves the
- * belief unchanged. */
+ * 65536 (CROWD, with 60-byte states: 20695); larger n returns VOPP_E_INVALID.  states,
+ * log_weights and ancestors must be device memory of the model's GPU (checked with
+ * cudaPointerGetAttributes; VOPP_E_INVALID otherwise); their sizes cannot be checked here,
+ * so they must hold n particles as laid out above.  The call issues no cudaMalloc /
+ * cudaFree and no allocating library call.  The first call on a device does a one-time
+ * set-up: it looks the array's device address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the one
+ * array, which keeps the previous call's contents, so calls that overlap on the GPU
+ * (different streams or threads, or concurrent launches) race: serialise them.  The call
+ * reads the kernel's status word back and waits on cuda_stream, so it returns after the
+ * update is done; the caller's current device is left as it was.  VOPP_E_DEGENERATE
+ * leaves the belief unchanged. */
 VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void *states, float *log_weights,
                                         int32_t n, int32_t action, const void *obs, uint64_t seed,
                                         uint64_t t, uintptr_t cuda_stream, int32_t *ancestors,

@@ -766,6 +766,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     for (size_t k = 0; k < stages.size(); ++k) {
       StageBuild &sb = stages[k];
       TimedLaunch tl;
+      vopp::NvtxRange nvtx_range(sb.family == F_ROOT ? "k_root_prep" :
+                                 (sb.family == F_EXPAND ? "k_expand" : "k_leaf"));
       if (timed) timed_begin(c, sb.family, tl);
       cudaError_t e = cudaSuccess;
       switch (sb.family) {
@@ -1401,6 +1403,7 @@ int vopp_grid_thresholds(uint64_t *thr, int32_t n) {
 int vopp_plan(vopp_model *m, const void *root_states, const float *root_weights, int32_t N,
               int32_t depth, int32_t width, float eta, float gamma, const float *pi_bar,
               uint64_t seed, uint32_t ptr_flags, vopp_plan_result *out) {
+  vopp::NvtxRange nvtx_range("vopp_plan");
   if (!m || !out) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = m->ctx;
   vopp_plan_params p{depth, width, eta, gamma, seed, pi_bar};
@@ -1414,6 +1417,7 @@ int vopp_plan(vopp_model *m, const void *root_states, const float *root_weights,
 int vopp_plan_submit(vopp_model *m, const void *root_states, const float *root_weights,
                      int32_t N, int32_t depth, int32_t width, float eta, float gamma,
                      const float *pi_bar, uint64_t seed, uint32_t ptr_flags) {
+  vopp::NvtxRange nvtx_range("vopp_plan_submit");
   if (!m) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = m->ctx;
   if (const int busy = check_not_pending(c)) return busy;
@@ -1435,6 +1439,7 @@ int vopp_plan_submit(vopp_model *m, const void *root_states, const float *root_w
 vopp_ctx *vopp_model_ctx(const vopp_model *m) { return m ? m->ctx : nullptr; }
 
 int vopp_plan_finish(vopp_ctx *c, vopp_plan_result *out) {
+  vopp::NvtxRange nvtx_range("vopp_plan_finish");
   if (!c || !out) return fail(VOPP_E_INVALID, "NULL argument");
   if (!c->plan_pending) return fail(VOPP_E_INVALID, "no submitted plan");
   c->plan_pending = false;
@@ -1449,6 +1454,7 @@ int vopp_plan_finish(vopp_ctx *c, vopp_plan_result *out) {
 int vopp_plan_anytime(vopp_model *m, const void *root_states, const float *root_weights,
                       int32_t N, const vopp_plan_params *p, double budget_s, uint32_t ptr_flags,
                       vopp_plan_result *out, int32_t *depth_reached) {
+  vopp::NvtxRange nvtx_range("vopp_plan_anytime");
   if (!m || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = m->ctx;
   Job j;
@@ -1459,6 +1465,7 @@ int vopp_plan_anytime(vopp_model *m, const void *root_states, const float *root_
 }
 
 int vopp_plan_batch(vopp_ctx *c, int32_t n, const vopp_plan_request *reqs, vopp_plan_result *outs) {
+  vopp::NvtxRange nvtx_range("vopp_plan_batch");
   if (!c || !reqs || !outs || n < 1) return fail(VOPP_E_INVALID, "bad batch arguments");
   std::vector<Job> jobs(n);
   for (int i = 0; i < n; ++i) {
@@ -1826,6 +1833,7 @@ int vopp_agent_num_particles(const vopp_agent *g) {
 }
 
 int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *out) {
+  vopp::NvtxRange nvtx_range("vopp_agent_plan");
   if (!g || !p || !out) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_ctx *c = g->model->ctx;
   std::vector<Job> jobs(1);
@@ -1948,6 +1956,7 @@ extern "C" {
 
 int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *ess_out,
                        int32_t *resampled_out) {
+  vopp::NvtxRange nvtx_range("vopp_belief_update");
   if (!g || !obs) return fail(VOPP_E_INVALID, "NULL argument");
   vopp_model *m = g->model;
   if (action < 0 || action >= m->A) return fail(VOPP_E_INVALID, "action %d", action);
@@ -1988,6 +1997,7 @@ int vopp_belief_update(vopp_agent *g, int32_t action, const void *obs, double *e
 int vopp_belief_update_batch(vopp_ctx *c, int32_t n, vopp_agent *const *agents,
                              const int32_t *actions, const void *const *obs, double *ess_out,
                              int32_t *resampled_out, int32_t *status_out) {
+  vopp::NvtxRange nvtx_range("vopp_belief_update_batch");
   if (!c || n < 0) return fail(VOPP_E_INVALID, "bad batch arguments");
   if (n == 0) return VOPP_OK;
   if (!agents || !actions || !obs || !status_out) return fail(VOPP_E_INVALID, "NULL argument");

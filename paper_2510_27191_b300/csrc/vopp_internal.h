@@ -4,11 +4,22 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "vopp.h"
 #include "vopp_device.cuh"
 
 namespace vopp {
+
+// NVTX range for the lifetime of a scope: a profiler (Nsight Systems, ncu's NVTX filters)
+// shows each plan, batch, belief update and kernel launch as a named range; without a tool
+// attached a push/pop costs a branch.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct BeliefOut {
   int status;       // 0 ok, 1 degenerate (every particle has zero likelihood)

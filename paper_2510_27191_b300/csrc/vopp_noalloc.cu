@@ -9,6 +9,7 @@
 // the FP64 CDF, ancestors, the status word) from one fixed device array compiled into the
 // library instead of from an allocator.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -19,7 +20,7 @@ namespace {
 
 // Largest particle count the static scratch serves, and the scratch itself: per particle
 // 8 B propagated state, 4 B log weight, 8 B CDF entry, 4 B ancestor; plus the status word.
-// CROWD's 60-byte states fit fewer particles (kNoAllocScratchBytes / 76, about 20,000).
+// CROWD's 60-byte states fit fewer particles: (kNoAllocScratchBytes - 5 * 256) / 76 = 20695.
 constexpr int kNoAllocMaxParticles = 65536;
 constexpr size_t kNoAllocScratchBytes =
     (size_t)kNoAllocMaxParticles * (8 + 4 + 8 + 4) + 256 * 5;
@@ -54,6 +55,31 @@ int scratch_address(int device, void **out) {
 
 inline size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Restores the calling thread's current device when it goes out of scope.
+struct DeviceGuard {
+  int prev = 0;
+  bool ok = false;
+  DeviceGuard() { ok = cudaGetDevice(&prev) == cudaSuccess; }
+  ~DeviceGuard() { if (ok) cudaSetDevice(prev); }
+};
+
+// VOPP_OK when p is device (or managed) memory that `device` owns; VOPP_E_INVALID otherwise.
+int check_device_array(const void *p, int device, const char *name) {
+  cudaPointerAttributes at;
+  std::memset(&at, 0, sizeof at);
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the (non-sticky) error so that later calls do not see it
+    return vopp::set_error(VOPP_E_INVALID, name);
+  }
+  const bool on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (!on_device || at.device != device) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "%s is not device memory of the model's GPU %d", name, device);
+    return vopp::set_error(VOPP_E_INVALID, msg);
+  }
+  return VOPP_OK;
+}
+
 }  // namespace
 
 extern "C" VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void *states,
@@ -73,14 +99,22 @@ extern "C" VOPP_API int vopp_belief_update_noalloc(const vopp_model *model, void
   if (n < 1 || n > nmax)
     return vopp::set_error(VOPP_E_INVALID,
                            "n outside [1, the capacity of the static scratch] (65536 particles; "
-                           "CROWD: 20,000)");
+                           "CROWD: 20695)");
   const int A = kind == VOPP_NAV2D ? 4 : (kind == VOPP_GRID ? 13 : (kind == VOPP_CROWD ? 5 : 2));
   if (action < 0 || action >= A) return vopp::set_error(VOPP_E_INVALID, "action out of range");
   const int device = vopp::model_device(model);
   void *base = nullptr;
   int rc = scratch_address(device, &base);
   if (rc) return rc;
-  if (cudaSetDevice(device) != cudaSuccess) return vopp::set_error(VOPP_E_CUDA, "cudaSetDevice failed");
+  // the caller's particle arrays must be device memory of the model's GPU: a host or
+  // another GPU's pointer would be written by the kernel (nothing is allocated to check)
+  if ((rc = check_device_array(states, device, "states")) ||
+      (rc = check_device_array(log_weights, device, "log_weights")) ||
+      (ancestors && (rc = check_device_array(ancestors, device, "ancestors"))))
+    return rc;
+  DeviceGuard guard;   // the caller's current device is restored on every return below
+  if (!guard.ok || cudaSetDevice(device) != cudaSuccess)
+    return vopp::set_error(VOPP_E_CUDA, "cudaSetDevice failed");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
 
   // carve the static array: propagated states | log weights | CDF | ancestors | status

@@ -500,8 +500,30 @@ def vopp_agent_get_particles(agent: int, kind: int):
 def vopp_belief_update_noalloc(model: int, states, log_weights, action: int, obs, seed: int,
                                t: int, kind: int, cuda_stream: int = 0, ancestors=None):
     """In-place SIR update of caller-owned CUDA tensors (states, log_weights) using the
-    library's static scratch; returns (ess, resampled)."""
+    library's static scratch; returns (ess, resampled).
+
+    The kernel writes every one of n = log_weights.numel() particles, so the tensors are
+    checked here first (the C entry point sees only pointers): contiguous CUDA tensors on
+    one device, log_weights float32, states of 4-byte elements holding exactly the model's
+    words per particle times n, ancestors int32 with at least n entries."""
+    import torch
+    words = {VOPP_NAV2D: 2, VOPP_CROWD: 15}.get(kind, 1)
     n = log_weights.numel()
+    tensors = [("states", states), ("log_weights", log_weights)]
+    if ancestors is not None:
+        tensors.append(("ancestors", ancestors))
+    for name, t in tensors:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.device != log_weights.device:
+            raise ValueError(f"{name} is on {t.device}, log_weights on {log_weights.device}")
+    if log_weights.dtype != torch.float32:
+        raise ValueError("log_weights must be float32")
+    if states.element_size() != 4 or states.numel() != words * n:
+        raise ValueError(f"states must hold {words} 4-byte words per particle ({words * n}), "
+                         f"got {states.numel()} of {states.element_size()} bytes")
+    if ancestors is not None and (ancestors.dtype != torch.int32 or ancestors.numel() < n):
+        raise ValueError(f"ancestors must be int32 with at least {n} entries")
     if kind == VOPP_NAV2D:
         o = (ctypes.c_float * 2)(float(obs[0]), float(obs[1]))
     else:

@@ -7,6 +7,7 @@ allocates its scratch at agent creation) on two updates in a row, within the val
 tolerance of the parity tests (|a - b| <= 1e-4 max(|b|, 1); integers exact).  This file is
 collected last so that a failure here cannot hide any other test's result.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -66,6 +67,15 @@ def test_noalloc_update_matches_agent_update_twice(kind):
             else:
                 np.testing.assert_array_equal(states.cpu().numpy(), st_a)
             assert _close(lw.cpu().numpy(), lw_a)
+        # host arrays are refused by the entry point itself (cudaPointerGetAttributes),
+        # before any device work, and the caller's current device is left as it was
+        host = np.zeros(2 * N, dtype=np.float32)
+        hlw = np.zeros(N, dtype=np.float32)
+        o = (ctypes.c_float * 2)(1.0, 1.0)
+        rc = V.lib.vopp_belief_update_noalloc(model, host.ctypes.data, hlw.ctypes.data, N, 0, o,
+                                              1, 0, 0, None, None, None)
+        assert rc == V.VOPP_E_INVALID
+        assert torch.cuda.current_device() == 0
         # sizes beyond the static scratch are refused before any device work
         big = torch.zeros(65537, dtype=torch.float32, device="cuda")
         big_states = torch.zeros(2 * 65537, dtype=torch.float32, device="cuda")
