@@ -87,6 +87,33 @@ def leaf_traffic(workload: str):
     return d["dram_bytes_per_launch"] if d.get("source_hash") == kernel_source_hash() else None
 
 
+# Bytes per particle of a materialised level store: NAV2D x, y, log w; GRID / TOY2 packed
+# state, log w; CROWD robot x, y, flags, 12 people coordinates, log w.
+STORE_BYTES = {WL.NAV2D: 12, WL.GRID: 8, WL.TOY2: 8, WL.CROWD: 64}
+
+
+def expand_alg_bytes(spec, level: int) -> int:
+    """Algorithmic DRAM bytes of the expansion launch that writes `level`: every child's
+    particle store (written), every parent's store (read once), and 12 B of statistics per
+    child (mean reward, branch weight, completion counter)."""
+    AW = spec.A * spec.W
+    per = STORE_BYTES[spec.kind] * spec.N
+    return (AW ** level + AW ** (level - 1)) * per + 12 * AW ** level
+
+
+def expand_traffic(workload: str, level: int):
+    """DRAM bytes of that launch from the committed ncu capture, or None when there is none
+    or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", f"k_expand_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash() or d.get("level") != level:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -360,15 +387,31 @@ def config_leg(V, ctx, name, steps, warmup=1):
     leaf_s = leaf_ms / max(leaf_n, 1) / 1e3
     AW = spec.A * spec.W
     leaf_steps = (AW ** spec.D + (AW ** (spec.D - 1) if spec.D >= 2 else 0)) * spec.N
-    pk, _ = peaks()
+    pk, pk_src = peaks()
     peak_ops = SMS * LANES_PER_CLK * float(pk.get("sm_max_mhz", 2032.0)) * 1e6
     ms = float(np.median(ts))
-    return {"workload": _config(spec, None)["workload"], "plans": steps,
-            "ms_per_plan": ms, "particle_steps": spec.steps,
-            "particle_steps_per_s": spec.steps / (ms / 1e3),
-            "leaf": {"avg_launch_ms": leaf_s * 1e3, "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:g} instr per particle-step",
-                     "frac": ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_s / peak_ops,
-                     "share_of_plan": leaf_ms / max(sum(v[0] for v in kt.values()), 1e-9)}}
+    fam_total = sum(v[0] for k, v in kt.items() if not k.startswith("expand_to_"))
+    out = {"workload": _config(spec, None)["workload"], "plans": steps,
+           "ms_per_plan": ms, "particle_steps": spec.steps,
+           "particle_steps_per_s": spec.steps / (ms / 1e3),
+           "leaf": {"avg_launch_ms": leaf_s * 1e3, "per_unit": f"{ALG_INSTR_PER_STEP[spec.kind]:g} instr per particle-step",
+                    "frac": ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_s / peak_ops,
+                    "share_of_plan": leaf_ms / max(fam_total, 1e-9)}}
+    # the deepest materialised level's expansion (K2): HBM-bound, algorithmic bytes = the
+    # child particle stores written + the parent stores read + the per-child statistics
+    deep = spec.D - 2
+    if deep >= 1 and kt.get(f"expand_to_l{deep}", (0.0, 0))[1]:
+        ems, en = kt[f"expand_to_l{deep}"]
+        e_s = ems / en / 1e3
+        nbytes = expand_alg_bytes(spec, deep)
+        out["expand"] = {"kernel": "k_expand", "level": deep, "bound": "hbm",
+                         "avg_launch_ms": e_s * 1e3, "alg_bytes_per_launch": nbytes,
+                         "achieved": nbytes / e_s / 1e9, "peak": float(pk["hbm_gbs"]),
+                         "unit": "GB/s", "frac": nbytes / e_s / 1e9 / float(pk["hbm_gbs"]),
+                         "peak_source": f"{pk_src} STREAM-style copy",
+                         "traffic": expand_traffic(name, deep),
+                         "share_of_plan": ems / max(fam_total, 1e-9)}
+    return out
 
 
 def modes_run(V, ctx, spec, dev_states):
@@ -558,7 +601,7 @@ def main():
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
     peak_ops = SMS * LANES_PER_CLK * sm_max * 1e6
     achieved_ops = ALG_INSTR_PER_STEP[spec.kind] * leaf_steps / leaf_avg_s
-    total_kernel_ms = sum(v[0] for v in kt.values())
+    total_kernel_ms = sum(v[0] for k, v in kt.items() if not k.startswith("expand_to_"))
 
     # end to end through the C ABI with host buffers
     V.vopp_ctx_reset_kernel_times(ctx)
@@ -580,8 +623,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded root particles; no datasets)",
-            "config": {**_config(spec, args),
-                       "launch": "stream launches" if args.no_graphs else "CUDA graph replay"},
+            "config": _config(spec, args),
+            "launch": "stream launches" if args.no_graphs else "CUDA graph replay",
             "plans_per_s": args.steps * world / (total_ms / 1e3),
             "nodes_per_s": (sum(AW ** l for l in range(spec.D + 1))) * args.steps * world / (total_ms / 1e3),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -630,6 +673,11 @@ def main():
             # the other single-plan configurations at full size (C1, C3)
             out["configs"] = {"nav256_d3": config_leg(V, ctx, "nav256_d3", 20, 3),
                               "grid2048_d5": config_leg(V, ctx, "grid2048_d5", 3, 1)}
+            if "expand" in out["configs"]["grid2048_d5"]:
+                # the materialising kernel's HBM roofline, on the workload that writes the
+                # most (GridSense N=2048 D=5: level 3 is 0.97 GB)
+                out["roofline_expand"] = {"workload": "grid2048_d5",
+                                          **out["configs"]["grid2048_d5"]["expand"]}
         if not args.no_cpu_baseline and world == 1:
             last_seed = seeds[(args.warmup + args.steps - 1) % len(seeds)]
             out["cpu_baseline"] = cpu_baseline(spec, gpu=(last, last_seed))

@@ -205,7 +205,9 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
-/* Per-kernel-family accumulated device time (ms) and launch counts since the last reset.
+/* Per-kernel-family accumulated device time (ms) and launch counts since the last reset:
+ * root_prep, expand, leaf, belief, then expand_to_l1 .. expand_to_l8 (the expansion
+ * launches that wrote that level, also counted under expand).
  * names[i] receives a static string; arrays hold at least *n entries on input; *n is set
  * to the number of families written. */
 VOPP_API int vopp_ctx_kernel_times(vopp_ctx *ctx, const char **names, double *ms, uint64_t *launches,

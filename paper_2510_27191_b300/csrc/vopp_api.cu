@@ -60,11 +60,18 @@ unsigned long long ipow(unsigned long long b, int e) {
   return r;
 }
 
-const char *kFamilies[] = {"root_prep", "expand", "leaf", "belief"};
+// Timed kernel families; an expansion launch also counts under the level it writes
+// ("expand_to_l<l>", every plan of the launch expanding into level l).
+const char *kFamilies[] = {"root_prep", "expand", "leaf", "belief",
+                           "expand_to_l1", "expand_to_l2", "expand_to_l3", "expand_to_l4",
+                           "expand_to_l5", "expand_to_l6", "expand_to_l7", "expand_to_l8"};
 enum { F_ROOT = 0, F_EXPAND, F_LEAF, F_BELIEF, F_COUNT };
+constexpr int F_ALL = F_COUNT + kMaxDepth;
+static_assert(sizeof(kFamilies) / sizeof(kFamilies[0]) == F_ALL, "one name per timed family");
 
 struct TimedLaunch {
   int family;
+  int level;           // expansions: the parent level (the launch writes level + 1)
   cudaEvent_t a, b;
 };
 
@@ -132,8 +139,8 @@ struct vopp_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<TimedLaunch> pending;
-  double fam_ms[F_COUNT] = {0};
-  unsigned long long fam_n[F_COUNT] = {0};
+  double fam_ms[F_ALL] = {0};
+  unsigned long long fam_n[F_ALL] = {0};
   std::atomic<unsigned long long> h2d_bytes{0}, d2h_bytes{0}, launches{0};
   // last launch, for vopp_tree_read
   std::vector<PlanDesc> last_desc;
@@ -338,8 +345,9 @@ void free_slot(Slot &s) {
 }
 
 // ---- timing -----------------------------------------------------------------------------
-void timed_begin(vopp_ctx *c, int fam, TimedLaunch &t) {
+void timed_begin(vopp_ctx *c, int fam, TimedLaunch &t, int level = -1) {
   t.family = fam;
+  t.level = level;
   t.a = t.b = nullptr;
   if (!c->timing) return;
   while (c->ev_pool.size() < c->ev_used + 2) {
@@ -362,6 +370,10 @@ void timed_collect(vopp_ctx *c) {
     if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
       c->fam_ms[t.family] += ms;
       c->fam_n[t.family] += 1;
+      if (t.family == F_EXPAND && t.level >= 0 && t.level < kMaxDepth) {
+        c->fam_ms[F_COUNT + t.level] += ms;
+        c->fam_n[F_COUNT + t.level] += 1;
+      }
     }
   }
   c->pending.clear();
@@ -411,7 +423,8 @@ struct Job {
 struct StageBuild {
   int family;
   int level;
-  int kind = -1;              // leaf stages: the model of every plan in the launch
+  int kind = -1;              // leaf and vectorised expansion stages: the model of every plan
+  int vec_width = 0;          // vectorised expansions: particles per thread unit (0: generic)
   bool long_step = false;     // expansion stages: a CROWD plan (five Philox calls per step)
   std::vector<int> plans, levels;
   std::vector<long long> prefix;
@@ -530,27 +543,55 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   }
   int max_mat = 0, maxD = 0;
   for (auto &j : jobs) { max_mat = std::max(max_mat, j.shape.mat_top); maxD = std::max(maxD, j.shape.D); }
+  // Expansion stages, per level: vectorised launches for NAV2D, GRID and TOY2 plans (a fused
+  // root preparation excepted), one per model and vector width (the widest of 4, 2, 1 that
+  // divides the plan's N: a plan's particle-to-lane mapping, and so its rounding, depends
+  // on nothing but the plan), and one generic launch for the rest (CROWD, the level-0
+  // expansions that prepare their roots, levels of fewer than kExpandVecMinChildren nodes,
+  // where one CTA per child is faster).  Work items are the level's children.
   for (int l = 0; l < max_mat; ++l) {
-    StageBuild s;
-    s.family = F_EXPAND;
-    s.level = l;
-    long long acc = 0;
-    for (int i : order_exp) {
-      if (jobs[i].shape.mat_top > l && l >= jobs[i].first_expand) {
+    auto takes = [&](int i) { return jobs[i].shape.mat_top > l && l >= jobs[i].first_expand; };
+    auto vec_class = [&](int i) {   // (model, vector width), or (-1, 0) for the generic kernel
+      const int kd = jobs[i].shape.kind, N = jobs[i].shape.N;
+      // A small level is latency-bound: one CTA per child.  The choice goes by the level's
+      // width in the full tree its Philox keys belong to (key level, not plan level), so that
+      // a node is always built by the same kernel, and so rounded the same, whether a plan
+      // builds it fresh or continues a kept subtree that holds it.
+      long long w = 1;
+      for (int t = 0; t <= l + jobs[i].lvl_off && w < kExpandVecMinChildren; ++t) w *= jobs[i].shape.AW;
+      if (kd == kCrowd || (l == 0 && fused[i]) || w < kExpandVecMinChildren)
+        return std::make_pair(-1, 0);
+      return std::make_pair(kd, (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1));
+    };
+    const std::pair<int, int> classes[] = {{-1, 0}, {kNav, 4}, {kNav, 2}, {kNav, 1},
+                                           {kGrid, 4}, {kGrid, 2}, {kGrid, 1},
+                                           {kToy, 4}, {kToy, 2}, {kToy, 1}};
+    for (const auto &cls : classes) {
+      const int kd = cls.first;
+      StageBuild s;
+      s.family = F_EXPAND;
+      s.level = l;
+      s.kind = kd;
+      s.vec_width = cls.second;
+      long long acc = 0;
+      for (int i : order_exp) {
+        if (!takes(i) || vec_class(i) != cls) continue;
         s.plans.push_back(i);
         s.levels.push_back(l);
         s.prefix.push_back(acc);
         acc += nodes(jobs[i], l + 1);
         s.maxN = std::max(s.maxN, jobs[i].shape.N);
         if (jobs[i].shape.kind == kCrowd) s.long_step = true;
-        s.smem = std::max(s.smem, (l == 0 && fused[i])
-                                      ? expand_fused_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N)
-                                      : expand_smem_bytes(jobs[i].shape.N));
+        if (kd < 0)
+          s.smem = std::max(s.smem, (l == 0 && fused[i])
+                                        ? expand_fused_smem_bytes(jobs[i].shape.kind, jobs[i].shape.N)
+                                        : expand_smem_bytes(jobs[i].shape.N));
       }
+      if (!acc) continue;
+      s.prefix.push_back(acc);
+      s.total = acc;
+      stages.push_back(s);
     }
-    s.prefix.push_back(acc);
-    s.total = acc;
-    if (acc) stages.push_back(s);
   }
   // Leaf stage: one launch per model and shared-memory class (powers of two of the node
   // buffer), so that each model runs its own kernel and small-N plans are not held to the
@@ -752,7 +793,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       if (!pers) sb.st.counter = nullptr;
       grids[k] = pers ? persistent_grid(c, sb.kind, sb.smem) : std::min<long long>(sb.total, c->grid_cap);
     } else if (sb.family == F_EXPAND) {
-      grids[k] = std::min<long long>(sb.total, c->grid_cap);
+      const long long per = sb.vec_width ? kExpandVecChildrenPerCta : 1;
+      grids[k] = std::min<long long>((sb.total + per - 1) / per, c->grid_cap);
     } else {
       grids[k] = sb.st.n_plans;
     }
@@ -768,15 +810,18 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       TimedLaunch tl;
       vopp::NvtxRange nvtx_range(sb.family == F_ROOT ? "k_root_prep" :
                                  (sb.family == F_EXPAND ? "k_expand" : "k_leaf"));
-      if (timed) timed_begin(c, sb.family, tl);
+      if (timed) timed_begin(c, sb.family, tl, sb.family == F_EXPAND ? sb.level : -1);
       cudaError_t e = cudaSuccess;
       switch (sb.family) {
         case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
         case F_EXPAND:
           // a level of long steps with at most one CTA per SM takes wider CTAs (fewer
           // particles per thread on its critical path; measured faster for CROWD only)
-          e = launch_expand(dd, sb.st, sb.total, sb.smem, grids[k],
-                            sb.long_step && grids[k] <= c->sm_count, stream);
+          if (sb.vec_width)
+            e = launch_expand_vec(sb.kind, sb.vec_width, dd, sb.st, sb.total, grids[k], stream);
+          else
+            e = launch_expand(dd, sb.st, sb.total, sb.smem, grids[k],
+                              sb.long_step && grids[k] <= c->sm_count, stream);
           break;
         case F_LEAF: e = launch_leaf(sb.kind, dd, sb.st, sb.total, sb.smem, c->leaf_threads, grids[k], stream); break;
       }
@@ -807,6 +852,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     put(&sb.family, sizeof sb.family);
     put(&sb.kind, sizeof sb.kind);
     put(&sb.long_step, sizeof sb.long_step);
+    put(&sb.vec_width, sizeof sb.vec_width);
     put(&sb.total, sizeof sb.total);
     put(&sb.smem, sizeof sb.smem);
     put(&sb.maxN, sizeof sb.maxN);
@@ -1275,7 +1321,7 @@ int vopp_ctx_set_timing(vopp_ctx *c, int enable) {
 
 int vopp_ctx_kernel_times(vopp_ctx *c, const char **names, double *ms, uint64_t *launches, int *n) {
   if (!c || !n) return fail(VOPP_E_INVALID, "NULL argument");
-  const int m = std::min(*n, (int)F_COUNT);
+  const int m = std::min(*n, (int)F_ALL);
   for (int i = 0; i < m; ++i) {
     if (names) names[i] = kFamilies[i];
     if (ms) ms[i] = c->fam_ms[i];
@@ -1287,7 +1333,7 @@ int vopp_ctx_kernel_times(vopp_ctx *c, const char **names, double *ms, uint64_t 
 
 int vopp_ctx_reset_kernel_times(vopp_ctx *c) {
   if (!c) return fail(VOPP_E_INVALID, "ctx is NULL");
-  for (int i = 0; i < F_COUNT; ++i) { c->fam_ms[i] = 0; c->fam_n[i] = 0; }
+  for (int i = 0; i < F_ALL; ++i) { c->fam_ms[i] = 0; c->fam_n[i] = 0; }
   c->h2d_bytes = c->d2h_bytes = c->launches = 0;
   return VOPP_OK;
 }

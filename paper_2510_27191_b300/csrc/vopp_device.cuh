@@ -6,6 +6,7 @@
 // the expansion and backup kernels read.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -45,6 +46,10 @@ struct DevModel {
   float toy_lc2, toy_lw2;               // TOY2: log2 0.85, log2 0.15
   float toy_pc, toy_pw;                 // TOY2: 0.85, 0.15
 };
+
+// The GRID expansion indexes log2 Z as lacc2[d^2 + 256 * disagree].
+static_assert(offsetof(DevModel, l1macc2) == offsetof(DevModel, lacc2) + sizeof(float) * kGridD2,
+              "l1macc2 follows lacc2");
 
 struct DevResult {
   int status;                 // kStatus* bits

@@ -79,6 +79,17 @@ cudaError_t init_kernel_attributes();
 cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long total, size_t smem,
                           long long grid, bool wide, cudaStream_t s);
 // kind selects the model's leaf kernel (kNav, kGrid, kToy)
+// Vectorised expansion (NAV2D, GRID, TOY2): vw particles per lane unit (4, 2 or 1, dividing
+// every plan's N); one child per warp, kExpandVecChildrenPerCta children per CTA.
+#ifndef VOPP_EXPAND_VEC_THREADS
+#define VOPP_EXPAND_VEC_THREADS 128
+#endif
+constexpr int kExpandVecChildrenPerCta = VOPP_EXPAND_VEC_THREADS / 32;
+// Levels (counted in the full tree of their Philox keys) narrower than this expand one CTA
+// per child instead.
+constexpr long long kExpandVecMinChildren = 512;
+cudaError_t launch_expand_vec(int kind, int vw, const PlanDesc *d, const StageTable &st,
+                              long long total, long long grid, cudaStream_t s);
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
                         size_t smem, int threads, long long grid, cudaStream_t s);
 cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_sm);

@@ -908,6 +908,431 @@ __global__ void __launch_bounds__(T, (T <= 256) ? 2 : 1) k_expand(const PlanDesc
 }
 
 // ---------------------------------------------------------------------------------------
+// K2, vectorised: the expansion of the models whose particle is one or two words (NAV2D,
+// GRID, TOY2), one kernel per model and vector width.  One warp builds one child: particle
+// i of a child depends only on particle i of its parent (and on the branch observation),
+// so a lane owns units of V consecutive particles (V = 4, 2 or 1: the largest that divides
+// N, so that every node's store starts on a 16-, 8- or 4-byte boundary) from the parent
+// load to the child store.  Pass 1 reads the parent's states and log weights as V-wide
+// vectors, steps them, writes the child's states as V-wide streaming stores and parks the
+// unnormalised base-2 log weights in the child's own log-weight store (the lane reads
+// back only what it wrote), folding them into running max-shifted sums; the lanes merge
+// their sums with shuffles (no barrier, no shared memory), and pass 2 rewrites the log
+// weights normalised.  A CTA's warps take consecutive children, so siblings share their
+// parent's lines in L2.
+// ---------------------------------------------------------------------------------------
+constexpr int kExpandVecThreads = VOPP_EXPAND_VEC_THREADS;
+constexpr int kExpandVecWarps = kExpandVecThreads / 32;
+
+template <int V> __device__ __forceinline__ void ldg_v(const float *p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (V == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+template <int V> __device__ __forceinline__ void ldg_v(const int *p, int (&v)[V]) {
+  if constexpr (V == 4) {
+    const int4 t = __ldg(reinterpret_cast<const int4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (V == 2) {
+    const int2 t = __ldg(reinterpret_cast<const int2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+// Child stores: plain write-back (1: streaming, evict-first; measured slower, 0.283 against
+// 0.272 ms on the widest grid level).
+#ifndef VOPP_EXPAND_STREAMING
+#define VOPP_EXPAND_STREAMING 0
+#endif
+template <int V> __device__ __forceinline__ void st_child_v(float *p, const float (&v)[V]) {
+  if constexpr (!VOPP_EXPAND_STREAMING) {
+    if constexpr (V == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else *p = v[0];
+  } else if constexpr (V == 4) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else if constexpr (V == 2) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+  } else {
+    __stcs(p, v[0]);
+  }
+}
+template <int V> __device__ __forceinline__ void st_child_v(int *p, const int (&v)[V]) {
+  if constexpr (!VOPP_EXPAND_STREAMING) {
+    if constexpr (V == 4) *reinterpret_cast<int4 *>(p) = make_int4(v[0], v[1], v[2], v[3]);
+    else if constexpr (V == 2) *reinterpret_cast<int2 *>(p) = make_int2(v[0], v[1]);
+    else *p = v[0];
+  } else if constexpr (V == 4) {
+    __stcs(reinterpret_cast<int4 *>(p), make_int4(v[0], v[1], v[2], v[3]));
+  } else if constexpr (V == 2) {
+    __stcs(reinterpret_cast<int2 *>(p), make_int2(v[0], v[1]));
+  } else {
+    __stcs(p, v[0]);
+  }
+}
+
+// Step the V particles of unit u (particles u V .. u V + V - 1) of a NAV2D parent under
+// branch (a, k): states in place, rewards r, base-2 log-likelihoods e.  Pairs of a unit share
+// their Philox call; a single particle (V = 1) takes its half of its pair's words.
+template <int V>
+__device__ __forceinline__ void nav_unit(float (&x)[V], float (&y)[V], float (&r)[V], float (&e)[V],
+                                         long long u, int a, uint32_t c1, unsigned long long kn,
+                                         uint32_t key0, uint32_t key1, const NavModel::O &o,
+                                         const DevModel &dm) {
+  if constexpr (V >= 2) {
+    const float dx = NavModel::dx_of(a), dy = NavModel::dy_of(a);
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) {
+      const uint32_t p = (uint32_t)(u * (V / 2) + q);
+      const uint4 w = philox(make_uint4(p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
+      float2 X = make_float2(x[2 * q], x[2 * q + 1]), Y = make_float2(y[2 * q], y[2 * q + 1]);
+      bool t0, t1;
+      const float2 rr = NavModel::step_pair(X, Y, dx, dy, w, t0, t1);
+      const float2 ee = NavModel::loglik2_pair(X, Y, o);
+      x[2 * q] = X.x; x[2 * q + 1] = X.y; y[2 * q] = Y.x; y[2 * q + 1] = Y.y;
+      r[2 * q] = rr.x; r[2 * q + 1] = rr.y; e[2 * q] = ee.x; e[2 * q + 1] = ee.y;
+    }
+  } else {
+    const uint32_t i = (uint32_t)u;
+    const uint4 w = philox(make_uint4(i >> 1, c1, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
+    NavModel::S s{x[0], y[0]};
+    r[0] = NavModel::step(s, a, (i & 1) ? w.z : w.x, (i & 1) ? w.w : w.y, dm);
+    e[0] = NavModel::loglik2(s, a, o, dm);
+    x[0] = s.x;
+    y[0] = s.y;
+  }
+}
+
+template <int V> __device__ __forceinline__ void st_v(float *p, const float (&v)[V]) {
+  if constexpr (V == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+  else *p = v[0];
+}
+template <int V> __device__ __forceinline__ void ld_v(const float *p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (V == 2) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    v[0] = *p;
+  }
+}
+
+// A GRID child's action decided once (as the leaf's branch loops do): a sense action keeps
+// the state, earns 0 and weighs by Z(o | s') from the model's log tables; a move changes
+// one 4-bit field by one unless it is at its blocking value (east at x = 10 exits: x = 11
+// and the terminal bit, +10); collect reads the cell's rock.  The same states, rewards and
+// log-likelihoods as GridModel::step and GridModel::loglik2.
+struct GridChild {
+  int kind;                   // 0 sense, 1 move, 2 collect
+  float e_null;               // log2 Z of a move's or collect's reading (0 if NULL, else -inf)
+  int rk, rx, ry, want;       // sense: rock, its cell, the bit the reading agrees with
+  bool valid;                 // sense: the reading is good or bad
+  const float *lagree, *ldis; // sense: log2 Z when the reading agrees / disagrees, by d^2
+  int shift, lo, span, delta, at_lim;
+  float r_lim;
+};
+__device__ __forceinline__ GridChild grid_child(int a, GridModel::O o, const DevModel &dm) {
+  GridChild g;
+  g.e_null = (o.o == 0) ? 0.0f : -CUDART_INF_F;
+  g.rk = g.rx = g.ry = g.want = 0;
+  g.valid = false;
+  g.lagree = g.ldis = nullptr;
+  g.shift = g.lo = g.span = g.delta = g.at_lim = 0;
+  g.r_lim = 0.0f;
+  if (a >= 5) {
+    g.kind = 0;
+    g.rk = a - 5;
+    g.rx = dm.rock_x[g.rk];
+    g.ry = dm.rock_y[g.rk];
+    g.valid = o.o == 1 || o.o == 2;
+    g.want = (o.o == 1) ? 1 : 0;
+    g.lagree = dm.lacc2;
+    g.ldis = dm.l1macc2;   // = lacc2 + kGridD2
+  } else if (a == 4) {
+    g.kind = 2;
+  } else {
+    g.kind = 1;
+    g.shift = (a < 2) ? 8 : 12;
+    g.lo = (a == 0 || a == 2) ? 10 : 0;
+    g.span = (a == 2) ? 5 : 0;
+    g.delta = (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000;
+    g.at_lim = (a == 0) ? 0x10100 : 0;
+    g.r_lim = (a == 0) ? 10.0f : 0.0f;
+  }
+  return g;
+}
+template <int V, int GK>
+__device__ __forceinline__ void grid_child_unit(int (&sv)[V], float (&r)[V], float (&e)[V],
+                                                const GridChild &g, const DevModel &dm) {
+  if constexpr (GK == 0) {
+    // log2 Z from [agree, disagree][d^2] (the model's log2 acc and log2(1 - acc) tables are
+    // adjacent): disagree = the rock's bit differs from the one the reading agrees with
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = sv[t], dx = gx(s) - g.rx, dy = gy(s) - g.ry;
+      const int miss = ((s >> g.rk) ^ g.want) & 1;
+      const float lz = __ldg(g.lagree + (dx * dx + dy * dy + (miss << 8)));
+      e[t] = g.valid ? lz : -CUDART_INF_F;
+      r[t] = 0.0f;
+    }
+  } else if constexpr (GK == 1) {
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = sv[t];
+      const bool term = gterm(s) != 0;
+      const bool blk = (unsigned)(((s >> g.shift) & 0xF) - g.lo) <= (unsigned)g.span;
+      sv[t] = term ? s : s + (blk ? g.at_lim : g.delta);
+      r[t] = (term || !blk) ? 0.0f : g.r_lim;
+      e[t] = g.e_null;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = sv[t], x = gx(s);
+      const int rk = (gterm(s) == 0 && x <= 10) ? __ldg(dm.rock_at + x + 11 * gy(s)) : -1;
+      const bool good = rk >= 0 && ((s >> (rk & 7)) & 1);
+      r[t] = (rk >= 0) ? (good ? 10.0f : -10.0f) : 0.0f;
+      sv[t] = good ? (s & ~(1 << (rk & 7))) : s;
+      e[t] = g.e_null;
+    }
+  }
+}
+
+// Unrolling of the two unit loops of a vectorised child (loads of several units in flight).
+#ifndef VOPP_EXPAND_UNROLL1
+#define VOPP_EXPAND_UNROLL1 1
+#endif
+#ifndef VOPP_EXPAND_UNROLL2
+#define VOPP_EXPAND_UNROLL2 4
+#endif
+constexpr int kExpandUnroll1 = VOPP_EXPAND_UNROLL1, kExpandUnroll2 = VOPP_EXPAND_UNROLL2;
+// Running sums of a child's pass 1 (per lane).
+struct ChildPass {
+  Kahan R, S1, S0, MX, MY;
+  float m1, m0;
+};
+
+// Pass 1 of a child over this lane's units (GK: the GRID action case, -1 for the generic
+// step of the other models).
+template <class M, int V, int GK>
+__device__ __forceinline__ void child_pass1(const PlanDesc &P, const DevModel &dm, int l, int a,
+                                            uint32_t c1, unsigned long long kn,
+                                            const typename M::O o, const GridChild &gc,
+                                            long long pb, long long cb, float *clw, ChildPass &cp) {
+  const int lane = threadIdx.x & 31, units = P.N / V;
+  // the mean particle is needed for the distance-softmax policy, a NAV2D policy only
+  const bool want_mu = std::is_same<M, NavModel>::value && P.pi_mode == kPiNavDist;
+  constexpr bool kNavM = std::is_same<M, NavModel>::value;
+  const float *plw = P.plw[l] + pb;
+  const float *sx = kNavM ? P.px[l] + pb : nullptr, *sy = kNavM ? P.py[l] + pb : nullptr;
+  float *dx = kNavM ? P.px[l + 1] + cb : nullptr, *dy = kNavM ? P.py[l + 1] + cb : nullptr;
+  const int *ss = kNavM ? nullptr : P.ps[l] + pb;
+  int *ds = kNavM ? nullptr : P.ps[l + 1] + cb;
+#pragma unroll kExpandUnroll1
+  for (int u = lane; u < units; u += 32) {
+    const int i0 = u * V;
+    float lw[V], r[V], e[V], X[V], Y[V];
+    int sv[V];
+    ldg_v<V>(plw + i0, lw);
+    if constexpr (kNavM) {
+      ldg_v<V>(sx + i0, X);
+      ldg_v<V>(sy + i0, Y);
+    } else {
+      ldg_v<V>(ss + i0, sv);
+    }
+    if constexpr (kNavM) {
+      nav_unit<V>(X, Y, r, e, u, a, c1, kn, P.key0, P.key1, o, dm);
+      st_child_v<V>(dx + i0, X);
+      st_child_v<V>(dy + i0, Y);
+    } else {
+      if constexpr (GK >= 0) {
+        grid_child_unit<V, GK>(sv, r, e, gc, dm);
+      } else {
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          typename M::S s{sv[t]};
+          r[t] = M::step(s, a, 0u, 0u, dm);
+          e[t] = M::loglik2(s, a, o, dm);
+          sv[t] = s.s;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < V; ++t) X[t] = Y[t] = 0.f;
+      st_child_v<V>(ds + i0, sv);
+    }
+    float L[V], rp = 0.f, cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F;
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      L[t] = fmaf(lw[t], kLog2e, e[t]);
+      // a GRID sense step earns exactly 0: its reward sum is skipped
+      if constexpr (GK != 0)
+        if (lw[t] > -CUDART_INF_F) rp = fmaf(ex2(lw[t] * kLog2e), r[t], rp);
+      cm1 = fmaxf(cm1, L[t]);
+      cm0 = fmaxf(cm0, e[t]);
+    }
+    st_v<V>(clw + i0, L);            // parked until the normalisation pass
+    // move the shifts to the unit's maxima, then add its shifted terms
+    if (cm1 > cp.m1) {
+      const float f = (cp.m1 > -CUDART_INF_F) ? ex2(cp.m1 - cm1) : 0.f;
+      cp.S1.scale(f);
+      if (want_mu) { cp.MX.scale(f); cp.MY.scale(f); }
+      cp.m1 = cm1;
+    }
+    if (cm0 > cp.m0) {
+      const float f = (cp.m0 > -CUDART_INF_F) ? ex2(cp.m0 - cm0) : 0.f;
+      cp.S0.scale(f);
+      cp.m0 = cm0;
+    }
+    float a1 = 0.f, a0 = 0.f, ax = 0.f, ay = 0.f;
+    if (cp.m1 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const float x1 = ex2(L[t] - cp.m1);   // L = -inf gives 0
+        a1 += x1;
+        if constexpr (std::is_same<M, NavModel>::value) {
+          ax = fmaf(x1, X[t], ax);
+          ay = fmaf(x1, Y[t], ay);
+        }
+      }
+    }
+    if (cp.m0 > -CUDART_INF_F) {
+#pragma unroll
+      for (int t = 0; t < V; ++t) a0 += ex2(e[t] - cp.m0);
+    }
+    cp.S1.add(a1); cp.S0.add(a0);
+    if constexpr (GK != 0) cp.R.add(rp);
+    if (want_mu) { cp.MX.add(ax); cp.MY.add(ay); }
+  }
+}
+
+// One child of a vectorised expansion, by one warp (see above).
+template <class M, int V>
+__device__ __forceinline__ void expand_child_warp(const PlanDesc &P, const DevModel &dm, int l,
+                                                  unsigned long long child) {
+  const int lane = threadIdx.x & 31;
+  const int N = P.N, AW = P.AW, W = P.W;
+  unsigned long long parent;
+  int slot;
+  if (child < (1ull << 32)) {   // 32-bit division in the common case
+    const uint32_t c32 = (uint32_t)child, p32 = c32 / (uint32_t)AW;
+    parent = p32;
+    slot = (int)(c32 - p32 * (uint32_t)AW);
+  } else {
+    parent = child / (unsigned long long)AW;
+    slot = (int)(child - parent * (unsigned long long)AW);
+  }
+  const int a = slot / W, k = slot - (slot / W) * W;
+  const unsigned long long kn = key_node(P, l, parent);
+  const uint32_t c1 = key_level(P, l) | ((uint32_t)a << 8) | ((uint32_t)k << 16);
+  const bool want_mu = P.pi_mode == kPiNavDist;
+  const long long pb = (long long)parent * N, cb = (long long)child * N;
+  float *clw = P.plw[l + 1] + cb;
+  const int units = N / V;
+  int j;
+  const typename M::O o = branch_obs<M>(P, GNode<M>::at(P, l, (long long)parent), l, a, k, kn, dm, j);
+
+  ChildPass cp;
+  cp.R.init(); cp.S1.init(); cp.S0.init(); cp.MX.init(); cp.MY.init();
+  cp.m1 = cp.m0 = -CUDART_INF_F;
+  GridChild gc;
+  if constexpr (std::is_same<M, GridModel>::value) {
+    gc = grid_child(a, o, dm);
+    if (gc.kind == 0) child_pass1<M, V, 0>(P, dm, l, a, c1, kn, o, gc, pb, cb, clw, cp);
+    else if (gc.kind == 1) child_pass1<M, V, 1>(P, dm, l, a, c1, kn, o, gc, pb, cb, clw, cp);
+    else child_pass1<M, V, 2>(P, dm, l, a, c1, kn, o, gc, pb, cb, clw, cp);
+  } else {
+    child_pass1<M, V, -1>(P, dm, l, a, c1, kn, o, gc, pb, cb, clw, cp);
+  }
+  // the lanes' sums at the warp's largest shifts
+  float w1 = cp.m1, w0 = cp.m0, s1 = cp.S1.value(), mx = cp.MX.value(), my = cp.MY.value();
+  float s0 = cp.S0.value();
+  warp_lse2(w1, s1, mx);
+  float dummy = 0.f;
+  warp_lse2(w0, s0, dummy);
+  my *= (cp.m1 > -CUDART_INF_F) ? ex2(cp.m1 - w1) : 0.f;
+  my = warp_sum(my);
+  const float rbar = warp_sum(cp.R.value());
+  const float lse2 = (s1 > 0.f) ? w1 + lg2(s1) : -CUDART_INF_F;   // base 2
+  if (lse2 > -CUDART_INF_F) {
+    const float off = -kLn2 * lse2;   // natural log weight = ln 2 (L - lse2)
+#pragma unroll kExpandUnroll2
+    for (int u = lane; u < units; u += 32) {
+      const int i0 = u * V;
+      float L[V];
+      ld_v<V>(clw + i0, L);
+#pragma unroll
+      for (int t = 0; t < V; ++t) L[t] = fmaf(L[t], kLn2, off);
+      st_child_v<V>(clw + i0, L);
+    }
+  } else {   // no weight left: every child particle has log weight -inf
+    float L[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) L[t] = -CUDART_INF_F;
+    for (int u = lane; u < units; u += 32) st_child_v<V>(clw + u * V, L);
+  }
+  if (lane == 0) {
+    float lom;
+    if (P.branch_mode == kEnumerate) lom = kLn2 * lse2;
+    else lom = (lse2 > -CUDART_INF_F) ? __logf((float)N) + kLn2 * (lse2 - (w0 + lg2(s0))) : -CUDART_INF_F;
+    const int cl = l + 1;
+    if (cl <= P.D - 2) P.cnt[cl][child] = 0u;   // completion counter of the new node
+    P.rbar[cl][child] = rbar;
+    P.lom[cl][child] = lom;
+    if (want_mu && P.mu[cl]) {
+      float2 mu = make_float2(0.f, 0.f);
+      if (s1 > 0.f) mu = make_float2(mx / s1, my / s1);
+      P.mu[cl][2 * child] = mu.x;
+      P.mu[cl][2 * child + 1] = mu.y;
+    }
+    if (P.rep[cl]) P.rep[cl][child] = j;
+    if (P.obs[cl]) {
+      const float2 of = M::obs_f2(o);
+      P.obs[cl][2 * child] = of.x;
+      P.obs[cl][2 * child + 1] = of.y;
+    }
+  }
+}
+
+// Per model: the resident CTAs per SM the register budget is set for (128-thread CTAs).
+#ifndef VOPP_EXPAND_NAV_MINBLOCKS
+#define VOPP_EXPAND_NAV_MINBLOCKS 6
+#endif
+#ifndef VOPP_EXPAND_GRID_MINBLOCKS
+#define VOPP_EXPAND_GRID_MINBLOCKS 8
+#endif
+template <int K> struct ExpandModel;
+template <> struct ExpandModel<kNav> { using type = NavModel; static constexpr int kMinBlocks = VOPP_EXPAND_NAV_MINBLOCKS; };
+template <> struct ExpandModel<kGrid> { using type = GridModel; static constexpr int kMinBlocks = VOPP_EXPAND_GRID_MINBLOCKS; };
+template <> struct ExpandModel<kToy> { using type = ToyModel; static constexpr int kMinBlocks = VOPP_EXPAND_GRID_MINBLOCKS; };
+
+// Work items: the children of every plan of the stage at level l + 1, one per warp.
+template <int K, int V>
+__global__ void __launch_bounds__(kExpandVecThreads, ExpandModel<K>::kMinBlocks)
+k_expand_vec(const PlanDesc *plans, StageTable st, long long total) {
+  using M = typename ExpandModel<K>::type;
+  pdl_release_next();
+  pdl_wait_prev();
+  const long long wid = threadIdx.x >> 5;
+  for (long long item = (long long)blockIdx.x * kExpandVecWarps + wid; item < total;
+       item += (long long)gridDim.x * kExpandVecWarps) {
+    const int pi = find_plan(st, item);
+    const PlanDesc &P = plans[st.plan[pi]];
+    const int l = st.levels ? st.levels[pi] : st.level;
+    expand_child_warp<M, V>(P, *P.model, l, (unsigned long long)(item - st.prefix[pi]));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // K3: leaf expansion of one level-(D-1) node, fused with its backup.
 // ---------------------------------------------------------------------------------------
 // Compile-time tuning of the leaf loop (results do not depend on them beyond the rounding
@@ -1804,6 +2229,25 @@ cudaError_t launch_expand(const PlanDesc *d, const StageTable &st, long long tot
     return launch_pdl(k_expand<kExpandWide>, (unsigned)grid, (unsigned)kExpandWide, smem, s, d, st, total);
   return launch_pdl(k_expand<256>, (unsigned)grid, 256u, smem, s, d, st, total);
 }
+
+cudaError_t launch_expand_vec(int kind, int vw, const PlanDesc *d, const StageTable &st,
+                              long long total, long long grid, cudaStream_t s) {
+  static_assert(kExpandVecWarps == kExpandVecChildrenPerCta, "one child per warp");
+  const unsigned g = (unsigned)grid, t = (unsigned)kExpandVecThreads;
+#define VOPP_EXPAND_VEC_CASE(K)                                                      \
+  if (kind == K) {                                                                   \
+    if (vw == 4) return launch_pdl(k_expand_vec<K, 4>, g, t, 0, s, d, st, total);    \
+    if (vw == 2) return launch_pdl(k_expand_vec<K, 2>, g, t, 0, s, d, st, total);    \
+    return launch_pdl(k_expand_vec<K, 1>, g, t, 0, s, d, st, total);                 \
+  }
+  VOPP_EXPAND_VEC_CASE(kNav)
+  VOPP_EXPAND_VEC_CASE(kGrid)
+  VOPP_EXPAND_VEC_CASE(kToy)
+#undef VOPP_EXPAND_VEC_CASE
+  return cudaErrorInvalidValue;
+}
+
+
 
 cudaError_t launch_leaf(int kind, const PlanDesc *d, const StageTable &st, long long total,
                         size_t smem, int threads, long long grid, cudaStream_t s) {

@@ -512,11 +512,11 @@ def vopp_belief_update_noalloc(model: int, states, log_weights, action: int, obs
     tensors = [("states", states), ("log_weights", log_weights)]
     if ancestors is not None:
         tensors.append(("ancestors", ancestors))
-    for name, t in tensors:
-        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+    for name, ten in tensors:
+        if not isinstance(ten, torch.Tensor) or not ten.is_cuda or not ten.is_contiguous():
             raise ValueError(f"{name} must be a contiguous CUDA tensor")
-        if t.device != log_weights.device:
-            raise ValueError(f"{name} is on {t.device}, log_weights on {log_weights.device}")
+        if ten.device != log_weights.device:
+            raise ValueError(f"{name} is on {ten.device}, log_weights on {log_weights.device}")
     if log_weights.dtype != torch.float32:
         raise ValueError("log_weights must be float32")
     if states.element_size() != 4 or states.numel() != words * n:

@@ -40,7 +40,7 @@ def test_toy2_enumerate_matches_oracle(depth, eta):
     _full(spec)
 
 
-@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (257, 2, 4), (1, 3, 2), (1000, 2, 3)])
+@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (257, 2, 4), (1, 3, 2), (1000, 2, 3), (130, 3, 2)])
 @pytest.mark.parametrize("leaf_gen", [True, False])
 def test_nav_small_full_tree(N, D, W, leaf_gen):
     _full(Spec(WL.NAV2D, N, D, W, eta=0.7, seed=3, root_seed=N), leaf_gen=leaf_gen)
@@ -85,10 +85,18 @@ def test_nav_nav_dist_policy_and_weights():
                weights="sparse", root_seed=4))
 
 
-@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (333, 2, 3), (2048, 2, 1)])
+@pytest.mark.parametrize("N,D,W", [(64, 3, 2), (333, 2, 3), (2048, 2, 1), (130, 3, 2)])
 @pytest.mark.parametrize("leaf_gen", [True, False])
 def test_grid_small_full_tree_bit_exact_integers(N, D, W, leaf_gen):
     _full(Spec(WL.GRID, N, D, W, seed=5, weights="random", root_seed=2), leaf_gen=leaf_gen)
+
+
+@pytest.mark.parametrize("kind,N,D,W", [(WL.NAV2D, 4, 5, 4), (WL.GRID, 6, 4, 3), (WL.GRID, 5, 4, 3)])
+def test_wide_levels_full_tree(kind, N, D, W):
+    """Levels of tens of thousands of children (65,536 and 59,319), every one materialised
+    and compared with the oracle: the expansion takes several sibling children per work
+    item there, with 4-, 2- and 1-particle vector units (N = 4, 6, 5)."""
+    _full(Spec(kind, N, D, W, seed=23, weights="random", root_seed=3), leaf_gen=False)
 
 
 def test_grid_enumerate_and_fixed_policy():
