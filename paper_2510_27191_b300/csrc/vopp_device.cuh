@@ -171,12 +171,24 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).  Built from the float
 // 1 + (x >> 9) 2^-23 in [1, 2) minus (1 - 2^-24); the difference is representable, so the
 // subtraction is exact.
+#ifndef VOPP_U01_MADHI
+#define VOPP_U01_MADHI 0
+#endif
+// The bits of 1 + (x >> 9) 2^-23: (x >> 9) | 0x3F800000, or, as one integer multiply-add on
+// the FMA pipe, hi(x 2^23) + 0x3F800000 (the same value: x >> 9 < 2^23 leaves the exponent
+// bits clear).
+__device__ __forceinline__ uint32_t u01_bits(uint32_t x) {
+#if VOPP_U01_MADHI
+  return __umulhi(x, 1u << 23) + 0x3F800000u;
+#else
+  return (x >> 9) | 0x3F800000u;
+#endif
+}
 __device__ __forceinline__ float u01(uint32_t x) {
-  return __fadd_rn(__uint_as_float((x >> 9) | 0x3F800000u), -0.999999940395355225f);
+  return __fadd_rn(__uint_as_float(u01_bits(x)), -0.999999940395355225f);
 }
 __device__ __forceinline__ float2 u01_2(uint32_t a, uint32_t b) {
-  return add2(make_float2(__uint_as_float((a >> 9) | 0x3F800000u),
-                          __uint_as_float((b >> 9) | 0x3F800000u)),
+  return add2(make_float2(__uint_as_float(u01_bits(a)), __uint_as_float(u01_bits(b))),
               bc2(-0.999999940395355225f));
 }
 
@@ -199,6 +211,22 @@ __device__ __forceinline__ float rcpa(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// fma(a, b, c) saturated to [0, 1] (PTX fma.rn.sat: an FMA-pipe instruction).
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float y;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+  return y;
+}
+#ifndef VOPP_NAV_CLAMP_SAT
+#define VOPP_NAV_CLAMP_SAT 1
+#endif
+#ifndef VOPP_NAV_ABS_FFMA
+#define VOPP_NAV_ABS_FFMA 0
+#endif
+#ifndef VOPP_NAV_HEUR_SAT
+#define VOPP_NAV_HEUR_SAT 0
+#endif
 
 // max(a, b, c) in one instruction (three-input max of sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -412,10 +440,26 @@ struct NavModel {
     float s0, c0, s1, c1;
     __sincosf(t.x, &s0, &c0);
     __sincosf(t.y, &s1, &c1);
+#if VOPP_NAV_CLAMP_SAT
+    // The same values with the lower clamp on the FMA pipe: in units of 16 (a power of two,
+    // so every scaling is exact) the step is t = fma(-0.1 / 16, r cos, (x + dx) / 16) =
+    // nx / 16 exactly, a saturating FMA gives max(t, 0) (t < 1: |nx| < 16), and 16 max(t, 0)
+    // = max(nx, 0); only the upper clamp stays a min on the half-rate ALU pipe.
+    const float2 wx = fma2(x, bc2(0.0625f), bc2(0.0625f * dx));
+    const float2 wy = fma2(y, bc2(0.0625f), bc2(0.0625f * dy));
+    const float2 rc = mul2(r, make_float2(c0, c1)), rs = mul2(r, make_float2(s0, s1));
+    float2 nx = mul2(bc2(16.0f), make_float2(fma_sat(rc.x, -0.00625f, wx.x),
+                                             fma_sat(rc.y, -0.00625f, wx.y)));
+    float2 ny = mul2(bc2(16.0f), make_float2(fma_sat(rs.x, -0.00625f, wy.x),
+                                             fma_sat(rs.y, -0.00625f, wy.y)));
+    nx = make_float2(fminf(nx.x, 10.0f), fminf(nx.y, 10.0f));
+    ny = make_float2(fminf(ny.x, 10.0f), fminf(ny.y, 10.0f));
+#else
     float2 nx = fma2(bc2(-0.1f), mul2(r, make_float2(c0, c1)), add2(x, bc2(dx)));
     float2 ny = fma2(bc2(-0.1f), mul2(r, make_float2(s0, s1)), add2(y, bc2(dy)));
     nx = make_float2(fminf(fmaxf(nx.x, 0.0f), 10.0f), fminf(fmaxf(nx.y, 0.0f), 10.0f));
     ny = make_float2(fminf(fmaxf(ny.x, 0.0f), 10.0f), fminf(fmaxf(ny.y, 0.0f), 10.0f));
+#endif
     const float2 r2 = fma2(nx, nx, mul2(ny, ny));
     const bool g0 = r2.x <= 0.25f, g1 = r2.y <= 0.25f;
     x = make_float2(p0 ? x.x : nx.x, p1 ? x.y : nx.y);
@@ -455,8 +499,14 @@ struct NavModel {
   // sigma / sqrt(c) comes from one fused multiply-add, pk from one reciprocal.
   __device__ __forceinline__ static float2 zlin_pair(float2 x, float2 y, const O &o) {
     const float2 dm = add2(x, bc2(-9.0f));
+#if VOPP_NAV_ABS_FFMA
+    // scalar FMAs take |dm| as an operand modifier (no separate absolute value)
+    const float2 sc = make_float2(fmaf(0.588705011f, fabsf(dm.x), 0.0588705011f),
+                                  fmaf(0.588705011f, fabsf(dm.y), 0.0588705011f));
+#else
     const float2 sc = fma2(bc2(0.588705011f), make_float2(fabsf(dm.x), fabsf(dm.y)),
                            bc2(0.0588705011f));          // (0.5 |x - 9| + 0.05) / sqrt(c)
+#endif
     const float2 s2 = mul2(sc, sc);
     const float2 pk = make_float2(rcpa(s2.x), rcpa(s2.y));
     const float2 ex = fma2(x, bc2(-1.0f), bc2(o.x)), ey = fma2(y, bc2(-1.0f), bc2(o.y));
@@ -468,9 +518,16 @@ struct NavModel {
   __device__ __forceinline__ static float2 heuristic_pair(float2 x, float2 y, bool t0, bool t1,
                                                           float log2g, float a0, float b0, bool hz) {
     // m - 1 = max(x + y - 1/2, 1) - 1 = max(x + y, 3/2) - 3/2
+#if VOPP_NAV_HEUR_SAT
+    // max(v - 3/2, 0) = 20 sat((v - 3/2) / 20) for v = x + y <= 20: one saturating FMA
+    const float2 v = add2(x, y);
+    const float2 q = make_float2(fma_sat(v.x, 0.05f, -0.075f), fma_sat(v.y, 0.05f, -0.075f));
+    const float2 e = mul2(q, bc2(20.0f * log2g));
+#else
     float2 m = add2(x, y);
     m = make_float2(fmaxf(m.x, 1.5f), fmaxf(m.y, 1.5f));
     const float2 e = fma2(m, bc2(log2g), bc2(-1.5f * log2g));
+#endif
     const float2 h = fma2(bc2(b0), make_float2(ex2(e.x), ex2(e.y)), bc2(a0));
     return make_float2((hz || t0) ? 0.0f : h.x, (hz || t1) ? 0.0f : h.y);
   }
