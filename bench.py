@@ -504,7 +504,11 @@ def main():
     ap.add_argument("--no-batch-serve", action="store_true",
                     help="skip the batched (512 mixed plans), served (Poisson requests) and "
                          "other-mode (anytime, episodes, closed loop) legs")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served and plain legs at the serving workload's rate "
+                         "(2,000 requests/s; 60 s as the workload specifies)")
+    ap.add_argument("--overload-seconds", type=float, default=4.0,
+                    help="length of the legs at 16,000 requests/s (overload)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every plan's kernels one by one instead of replaying the "
                          "captured CUDA graph of the plan's shape")
@@ -659,12 +663,13 @@ def main():
             # plain: one synchronous plan per request, then its own belief update
             for rate in (2000.0, 16000.0):
                 for mode in ("served", "plain"):
-                    r = LG.serve_run(V, ctx, seconds=args.serve_seconds, rate=rate, mode=mode,
+                    secs = args.serve_seconds if rate == 2000.0 else args.overload_seconds
+                    r = LG.serve_run(V, ctx, seconds=secs, rate=rate, mode=mode,
                                      drain_factor=2.0, reuse=(mode == "served"))
                     served[f"{mode}_{int(rate)}"] = {k: r[k] for k in (
                         "plans_per_s", "particle_steps_per_s", "p50_ms", "p99_ms",
                         "deadline_misses", "completed", "requests", "unfinished",
-                        "subtree_reuse", "reused_plans")}
+                        "subtree_reuse", "reused_plans", "seconds", "hbm_budget_bytes")}
                     if mode == "served":
                         served[f"{mode}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
             out["served"] = served

@@ -72,7 +72,12 @@ extern "C" {
                         gamma 0.97 in the paper.  Particle layout: 15 rows of N 32-bit words
                         -- robot x, robot y, people x0 y0 ... x5 y5 (float32), then int32
                         flags (bits 0-5 traits, 1 = curious; 8-13 "came closer"; 16
-                        terminal).  ENUMERATE branches and the distance-softmax policy are
+                        terminal).  A person's "came closer" bit is decided from its
+                        displacement d before the hall's walls clamp the new position:
+                        d.(d + 2(p - r)) < 0, with p its old position and r the robot's new
+                        one.  Away from the walls this is exactly |p + d - r| < |p - r|; for
+                        a person a wall stops, the bit describes the attempted move, not the
+                        clamped one.  ENUMERATE branches and the distance-softmax policy are
                         not available. */
 
 #define VOPP_BRANCH_SAMPLE 0    /* o_k drawn from a uniformly chosen representative      */

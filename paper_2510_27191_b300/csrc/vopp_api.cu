@@ -96,15 +96,20 @@ struct Slot {
 namespace {
 // A captured launch sequence (metadata upload, every kernel, result download) of one batch
 // shape, replayed while the shape, the buffers and the options stay the same.
-struct GraphCache {
-  std::vector<unsigned char> sig;
-  cudaGraphExec_t exec = nullptr;
+// Instantiated launch sequences by signature (every launch shape, kernel parameter and
+// buffer address the recorded operations bake in; the plans' tree pointers are not among
+// them -- the kernels read those from the descriptors uploaded by the sequence itself).  At
+// most kMaxGraphs are kept; the oldest is dropped first.
+struct GraphSet {
+  static constexpr size_t kMaxGraphs = 4096;
+  std::unordered_map<std::string, cudaGraphExec_t> execs;
+  std::deque<std::string> order;
   cudaStream_t capture = nullptr;   // private stream the sequence is recorded on (the legacy
                                     // default stream cannot be captured)
   void reset() {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    sig.clear();
+    for (auto &kv : execs) cudaGraphExecDestroy(kv.second);
+    execs.clear();
+    order.clear();
   }
   void release() {
     reset();
@@ -118,7 +123,7 @@ struct Job;   // one plan of a launch sequence (below)
 struct vopp_ctx {
   int device = 0;
   int use_graphs = 0;            // replay captured launch sequences of repeated shapes
-  GraphCache graph;
+  GraphSet graph;
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   char *arena = nullptr;
@@ -515,7 +520,7 @@ void reuse_copies(const vopp_ctx *c, const Job &j, char *base, std::vector<CopyO
 // every launch and the device->host copy of the results on the slot's stream.  Nothing
 // here waits for the device.
 int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, bool timed,
-                 GraphCache *graph) {
+                 GraphSet *graph) {
   const int n = (int)jobs.size();
   int rc = VOPP_OK;
   const std::vector<int> order_leaf = lpt_order(jobs, true), order_exp = lpt_order(jobs, false);
@@ -645,6 +650,17 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     off = align_up(off + 4 * k, 8);            // levels
     off = align_up(off + 8, 256);              // work counter (persistent launches)
   }
+  // copies of kept subtrees into the memory of the plans that continue them: their
+  // descriptors travel in the metadata block, so that a recorded sequence can be replayed
+  std::vector<CopyOp> copies;
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    if (j.reuse_src) reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies);
+  }
+  const size_t off_copy = off;
+  off = align_up(off + sizeof(CopyDesc) * copies.size(), 256);
+  unsigned long long copy_most = 0;
+  for (const CopyOp &op : copies) copy_most = std::max<unsigned long long>(copy_most, op.bytes);
   std::vector<size_t> root_off(n, kNone);
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
@@ -664,10 +680,12 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   sl.n = n;
   PlanDesc *hd = reinterpret_cast<PlanDesc *>(H + off_desc);
   const PlanDesc *dd = reinterpret_cast<const PlanDesc *>(Dm + off_desc);
-  std::vector<CopyOp> copies;     // kept subtrees into the arenas of the plans that continue them
-  bool kept = false;              // some plan keeps its tree (its memory is not the arena's)
+  {
+    CopyDesc *hc = reinterpret_cast<CopyDesc *>(H + off_copy);
+    for (size_t q = 0; q < copies.size(); ++q)
+      hc[q] = CopyDesc{copies[q].dst, copies[q].src, (unsigned long long)copies[q].bytes};
+  }
   for (int i = 0; i < n; ++i) {
-    kept |= jobs[i].own_arena != nullptr;
     const Job &j = jobs[i];
     const PlanShape &sh = j.shape;
     PlanDesc P;
@@ -705,7 +723,6 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     for (int l = 0; l <= kMaxDepth; ++l)
       P.node_off[l] = (l <= sh.D) ? j.root_idx * ipow(sh.AW, l) : 0ull;
     char *base = j.own_arena ? j.own_arena : arena + j.arena_off;
-    if (j.reuse_src) reuse_copies(c, j, base, copies);
     const PlanLayout &L = j.lay;
     auto fp = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<float *>(base + o); };
     auto ip = [&](size_t o) { return o == kNone ? nullptr : reinterpret_cast<int *>(base + o); };
@@ -801,10 +818,9 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   }
   auto record = [&](cudaStream_t stream) -> int {
     CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
-    for (const CopyOp &op : copies) {
-      if (op.src) CUDA_TRY(cudaMemcpyAsync(op.dst, op.src, op.bytes, cudaMemcpyDeviceToDevice, stream));
-      else CUDA_TRY(cudaMemsetAsync(op.dst, 0, op.bytes, stream));
-    }
+    if (!copies.empty())   // one launch for every copy, after the descriptors' upload
+      CUDA_TRY(launch_copy_table(reinterpret_cast<const CopyDesc *>(Dm + off_copy), (int)copies.size(),
+                                 copy_most, stream));
     for (size_t k = 0; k < stages.size(); ++k) {
       StageBuild &sb = stages[k];
       TimedLaunch tl;
@@ -832,8 +848,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
                              stream));
     return VOPP_OK;
   };
-  // batches that continue or keep agents' trees touch memory outside the arena: not replayed
-  if (!graph || timed || kept || !copies.empty()) return record(stream);
+  if (!graph || timed) return record(stream);
 
   // signature of everything the recorded operations depend on
   std::vector<unsigned char> sig;
@@ -841,10 +856,14 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     const unsigned char *q = static_cast<const unsigned char *>(p);
     sig.insert(sig.end(), q, q + b);
   };
-  const void *ptrs[3] = {Dm, H, arena};
+  const void *ptrs[2] = {Dm, H};
   put(ptrs, sizeof ptrs);
   put(&off, sizeof off);
   put(&off_res, sizeof off_res);
+  put(&off_copy, sizeof off_copy);
+  const size_t n_copies = copies.size();
+  put(&n_copies, sizeof n_copies);
+  put(&copy_most, sizeof copy_most);
   put(&n, sizeof n);
   put(&c->leaf_threads, sizeof c->leaf_threads);
   for (size_t k = 0; k < stages.size(); ++k) {
@@ -859,27 +878,42 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     put(&sb.st, sizeof sb.st);
     put(&grids[k], sizeof grids[k]);
   }
-  if (!graph->exec || graph->sig != sig) {
-    graph->reset();
-    if (!graph->capture) CUDA_TRY(cudaStreamCreateWithFlags(&graph->capture, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamBeginCapture(graph->capture, cudaStreamCaptureModeThreadLocal));
-    const int rc2 = record(graph->capture);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(graph->capture, &g);
-    if (rc2 != VOPP_OK || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      return rc2 != VOPP_OK ? rc2 : fail(VOPP_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    }
-    const cudaError_t ei = cudaGraphInstantiate(&graph->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (ei != cudaSuccess) {
-      graph->exec = nullptr;
-      return fail(VOPP_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
-    }
-    graph->sig = std::move(sig);
+  const std::string key(sig.begin(), sig.end());
+  auto it = graph->execs.find(key);
+  if (it != graph->execs.end()) {
+    CUDA_TRY(cudaGraphLaunch(it->second, stream));
+    return VOPP_OK;
   }
-  CUDA_TRY(cudaGraphLaunch(graph->exec, stream));
+  // a sequence not seen before runs directly; then, while the device works on it, it is
+  // recorded and instantiated for the next time (a failed capture only means no replay)
+  const int rc1 = record(stream);
+  if (rc1 != VOPP_OK) return rc1;
+  if (!graph->capture && cudaStreamCreateWithFlags(&graph->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return VOPP_OK;
+  }
+  if (cudaStreamBeginCapture(graph->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return VOPP_OK;
+  }
+  const int rc2 = record(graph->capture);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(graph->capture, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (rc2 == VOPP_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+    if (graph->order.size() >= GraphSet::kMaxGraphs) {
+      auto old = graph->execs.find(graph->order.front());
+      if (old != graph->execs.end()) {
+        cudaGraphExecDestroy(old->second);
+        graph->execs.erase(old);
+      }
+      graph->order.pop_front();
+    }
+    graph->execs.emplace(key, exec);
+    graph->order.push_back(key);
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
   return VOPP_OK;
 }
 
@@ -1013,10 +1047,10 @@ int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
   }
   const PlanLayout &S = t.lay, &L = sb->lay;
   cudaError_t e = cudaSuccess;
+  std::vector<CopyOp> ops;   // issued as one copy-list launch (or a few)
   auto cp = [&](size_t d, size_t src, size_t elem_off, size_t elem_bytes, size_t bytes) {
-    if (e == cudaSuccess && d != kNone && src != kNone)
-      e = cudaMemcpyAsync(sb->mem + d, t.mem + src + elem_off * elem_bytes, bytes,
-                          cudaMemcpyDeviceToDevice, s);
+    if (d != kNone && src != kNone)
+      ops.push_back(CopyOp{sb->mem + d, t.mem + src + elem_off * elem_bytes, bytes});
   };
   for (int l = 0; l <= sh.mat_top; ++l) {
     const size_t nodes = (size_t)ipow(AW, l), first = (size_t)slot * nodes;   // first node there
@@ -1033,15 +1067,23 @@ int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
   }
   // the agent's belief: the adopted node's particles in the agent's row layout
   auto cpa = [&](void *d, size_t src, size_t elem_bytes, size_t rows) {
-    if (e == cudaSuccess && src != kNone)
-      e = cudaMemcpyAsync(d, t.mem + src + (size_t)slot * N * elem_bytes, rows * 4 * N,
-                          cudaMemcpyDeviceToDevice, s);
+    if (src != kNone) ops.push_back(CopyOp{d, t.mem + src + (size_t)slot * N * elem_bytes, rows * 4 * N});
   };
   const int kind = t.shape.kind;
   if (kind == kNav || kind == kCrowd) { cpa(g->xy, S.px[1], 4, 1); cpa(g->xy + N, S.py[1], 4, 1); }
   if (kind == kCrowd) cpa(g->pf, S.pf[1], 48, 12);
   if (kind != kNav) cpa(g->s, S.ps[1], 4, 1);
   cpa(g->lw, S.plw[1], 4, 1);
+  for (size_t b = 0; e == cudaSuccess && b < ops.size(); b += kMaxCopyOps) {
+    CopyList cl;
+    cl.n = (int)std::min<size_t>(kMaxCopyOps, ops.size() - b);
+    for (int q = 0; q < cl.n; ++q) {
+      cl.dst[q] = ops[b + q].dst;
+      cl.src[q] = ops[b + q].src;
+      cl.bytes[q] = ops[b + q].bytes;
+    }
+    e = launch_copy_list(cl, s);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFreeAsync(sb->mem, s);
@@ -2207,6 +2249,7 @@ struct ServerReq {
 // Slot state is touched by the worker thread only.
 struct ServerSlot {
   Slot slot;
+  GraphSet graphs;                 // the slot's replayable launch sequences (server graphs on)
   cudaEvent_t done_ev = nullptr;   // recorded after the batch's last operation
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -2226,6 +2269,7 @@ struct Done {
 struct vopp_server {
   vopp_ctx *c = nullptr;
   int max_batch = 64;
+  int use_graphs = 0;              // replay recorded launch sequences (VOPP_OPT_GRAPHS at creation)
   size_t budget = 0, in_flight = 0, peak_in_flight = 0;
   std::vector<ServerSlot *> slots;
   std::thread worker;
@@ -2360,7 +2404,9 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
     if (e == cudaSuccess && j.agent)
       e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, srv->c->pool,
                                   s->slot.stream);
-  int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false, nullptr) : VOPP_E_NOMEM;
+  int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false,
+                                             srv->use_graphs ? &s->graphs : nullptr)
+                               : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
     if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
         cudaEventRecord(s->done_ev, s->slot.stream) != cudaSuccess)
@@ -2542,6 +2588,7 @@ int vopp_server_create(vopp_ctx *c, int32_t max_batch, int32_t n_slots, size_t h
   if (!srv) return fail(VOPP_E_NOMEM, "server alloc");
   srv->c = c;
   srv->max_batch = max_batch;
+  srv->use_graphs = c->use_graphs;
   srv->budget = hbm_budget_bytes ? hbm_budget_bytes : c->budget;
   for (int i = 0; i < n_slots; ++i) {
     ServerSlot *s = new (std::nothrow) ServerSlot;
@@ -2584,6 +2631,7 @@ void vopp_server_destroy(vopp_server *srv) {
   if (srv->worker.joinable()) srv->worker.join();
   for (auto *s : srv->slots) {
     cudaStreamSynchronize(s->slot.stream);
+    s->graphs.release();
     free_slot(s->slot);
     cudaEventDestroy(s->done_ev);
     cudaStreamDestroy(s->slot.stream);

@@ -98,6 +98,25 @@ cudaError_t launch_belief(const BeliefArgs &B, cudaStream_t s);
 cudaError_t launch_belief_batch(const BeliefArgs *d_args, int n, cudaStream_t s);
 cudaError_t launch_env(const EnvArgs &E, cudaStream_t s);
 
+// A batch of device-to-device copies (src null: zero dst) in one launch: the arrays a plan
+// that continues a kept subtree takes from it, or an adopted subtree's nodes.  Every
+// address and size is a multiple of 4 bytes.
+constexpr int kMaxCopyOps = 48;
+struct CopyList {
+  int n;
+  void *dst[kMaxCopyOps];
+  const void *src[kMaxCopyOps];
+  unsigned long long bytes[kMaxCopyOps];
+};
+cudaError_t launch_copy_list(const CopyList &L, cudaStream_t s);
+// The same from a descriptor table in device memory (n entries; `most` = the largest size).
+struct CopyDesc {
+  void *dst;
+  const void *src;
+  unsigned long long bytes;
+};
+cudaError_t launch_copy_table(const CopyDesc *table, int n, unsigned long long most, cudaStream_t s);
+
 }  // namespace vopp
 
 struct vopp_model;

@@ -2367,6 +2367,57 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
   }
 }
 
+// Copy i of the list in slices of kCopySlice bytes, one CTA per (copy, slice): 16-byte words
+// where both ends and the size allow, else 4-byte words.
+constexpr unsigned long long kCopySlice = 64 * 1024;
+// Slice blockIdx.y (and every gridDim.y-th after it) of one copy, by one CTA.
+__device__ __forceinline__ void copy_slices(void *dst, const void *src, unsigned long long bytes) {
+  char *d = static_cast<char *>(dst);
+  const char *sp = static_cast<const char *>(src);
+  const bool v16 = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(sp) | bytes) & 15) == 0;
+  for (unsigned long long lo = (unsigned long long)blockIdx.y * kCopySlice; lo < bytes;
+       lo += (unsigned long long)gridDim.y * kCopySlice) {
+    const unsigned long long hi = min(bytes, lo + kCopySlice);
+    if (v16) {
+      uint4 *d4 = reinterpret_cast<uint4 *>(d);
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(sp);
+      for (unsigned long long w = lo / 16 + threadIdx.x; w < hi / 16; w += blockDim.x)
+        d4[w] = sp ? s4[w] : make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      uint32_t *d1 = reinterpret_cast<uint32_t *>(d);
+      const uint32_t *s1 = reinterpret_cast<const uint32_t *>(sp);
+      for (unsigned long long w = lo / 4 + threadIdx.x; w < hi / 4; w += blockDim.x) d1[w] = sp ? s1[w] : 0u;
+    }
+  }
+}
+__global__ void __launch_bounds__(256) k_copy_list(CopyList L) {
+  const int i = blockIdx.x;
+  if (i < L.n) copy_slices(L.dst[i], L.src[i], L.bytes[i]);
+}
+__global__ void __launch_bounds__(256) k_copy_table(const CopyDesc *t, int n) {
+  const int i = blockIdx.x;
+  if (i < n) copy_slices(t[i].dst, t[i].src, t[i].bytes);
+}
+
+static unsigned copy_slice_count(unsigned long long most) {
+  return (unsigned)std::min<unsigned long long>(
+      65535, std::max<unsigned long long>(1, (most + kCopySlice - 1) / kCopySlice));
+}
+
+cudaError_t launch_copy_table(const CopyDesc *table, int n, unsigned long long most, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_table<<<dim3((unsigned)n, copy_slice_count(most)), 256, 0, s>>>(table, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_list(const CopyList &L, cudaStream_t s) {
+  if (L.n <= 0) return cudaSuccess;
+  unsigned long long most = 0;
+  for (int i = 0; i < L.n; ++i) most = std::max(most, L.bytes[i]);
+  k_copy_list<<<dim3((unsigned)L.n, copy_slice_count(most)), 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_env(const EnvArgs &E, cudaStream_t s) {
   k_env<<<1, 32, 0, s>>>(E);
   return cudaGetLastError();

@@ -117,13 +117,19 @@ def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3):
             "batched_particle_steps_per_s": steps / t_b, "batched_equals_sequential": bool(same)}
 
 
+SERVE_HBM_BUDGET = 120 * (1 << 30)   # the serving workload's admission budget: 120 GB
+
+
 def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int = 1024,
               seed: int = 11, mode: str = "served", deadline_s: float = 0.05, max_batch: int = 64,
-              n_slots: int = 3, drain_factor: float = 3.0, reuse: bool = False):
+              n_slots: int = 3, drain_factor: float = 3.0, reuse: bool = False,
+              hbm_budget_bytes: int = SERVE_HBM_BUDGET, graphs: bool = True):
     """Poisson arrivals at `rate` per second over `n_agents` agents for `seconds`; each
     agent's requests are served in order, a belief update follows every completed plan.
-    Served mode updates the agents of all plans that finished together in one batched call;
-    reuse: agents keep their trees (subtree reuse)."""
+    Served mode updates the agents of all plans that finished together in one batched call
+    and admits batches by the HBM budget; reuse: agents keep their trees (subtree reuse);
+    graphs: the server replays the recorded launch sequences of batch shapes it has seen (it
+    reads the context's graph option when it is created; the option is left off)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x73657276]))
     specs = WL.draw_mixed_plans(n_agents, seed, WL.SERVE_CAP_STEPS)
     models = make_models(V, ctx)
@@ -144,7 +150,11 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
     busy = np.zeros(n_agents, dtype=bool)
     lat, steps_done, updates = [], 0, 0
     plan_count = np.zeros(n_agents, dtype=np.int64)
-    srv = V.vopp_server_create(ctx, max_batch, n_slots) if mode == "served" else None
+    srv = None
+    if mode == "served":
+        V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, int(graphs))
+        srv = V.vopp_server_create(ctx, max_batch, n_slots, hbm_budget_bytes)
+        V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, 0)
     inflight = {}          # ticket -> (agent, arrival)
 
     def obs_for(ps, action):
@@ -292,7 +302,9 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
            "deadline_misses": int(np.sum(lat > deadline_s)), "belief_updates": updates,
            "reused_plans": int(reused), "subtree_reuse": bool(reuse),
            "episodes_restarted": resets,
-           "offered_rate": rate, "agents": n_agents, "seconds": seconds}
+           "offered_rate": rate, "agents": n_agents, "seconds": seconds,
+           "hbm_budget_bytes": int(hbm_budget_bytes) if mode == "served" else None,
+           "graphs": bool(graphs) if mode == "served" else False}
     if stats:
         out["batches"] = int(stats["batches"])
         out["mean_batch"] = stats["batched_plans"] / max(stats["batches"], 1)

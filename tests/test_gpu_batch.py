@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 from paper_2510_27191_b300 import workloads as WL
-from tests.parity import Gpu, Spec, action_agrees, assert_close
+from tests.parity import Gpu, Spec, action_agrees, assert_close, compare_full_tree
 
 pytestmark = pytest.mark.gpu
 
@@ -94,7 +94,13 @@ def test_batch_tree_read_per_plan():
 
 def test_config3_grid_sampled_subtrees_bit_exact():
     """GRID 11x11, 8 rocks, N=2048, depth 5, 13 actions x 3 branches (9.0e7 leaves,
-    1.9e11 particle-steps): three level-3 subtrees against the oracle, integers exact."""
+    1.9e11 particle-steps): one whole level-2 subtree (1.25e8 particle-steps of FP64 oracle:
+    the node's particles, Q and V, and every node and branch below it) and three level-3
+    subtrees against the oracle's path mode, integers exact.  The root and level 1 are too
+    large for the oracle here (the root is 1.9e11 particle-steps, a level-1 node 4.9e9): the
+    root's Q and V are checked against the closed-form backup (Alg. 3, Eq. 1) of the GPU's
+    own level-1 statistics, so the upper tree's arithmetic, not its inputs, is what that
+    check covers."""
     from paper_2510_27191_b300 import vopp as V
     spec = Spec.from_plan(WL.CONFIG3)
     g = Gpu(spec)
@@ -128,6 +134,29 @@ def test_config3_grid_sampled_subtrees_bit_exact():
             sub_d = spec.run_oracle(path=path, dump_levels=3, outputs=False)
             np.testing.assert_array_equal(ps, sub_d["ps"][3][0])
             assert_close(g.read(V.VOPP_FIELD_PLW, 3, 2048, n3 * 2048), sub_d["plw"][3][0], "plw3")
+        # one level-2 node and its whole subtree (depth 3 below it)
+        path2 = (int(rng.integers(0, AW)), int(rng.integers(0, AW)))
+        n2 = path2[0] * AW + path2[1]
+        sub2 = spec.run_oracle(path=path2, dump_levels=2)
+        assert sub2["status"] == O.OK
+        assert_close(g.read(V.VOPP_FIELD_V, 2, 1, n2), sub2["V"][2], f"V2 {path2}")
+        assert_close(g.read(V.VOPP_FIELD_Q, 2, 13, n2 * 13), sub2["Q"][2][0], f"Q2 {path2}")
+        assert_close(g.read(V.VOPP_FIELD_RBAR, 2, 1, n2), sub2["rbar"][2], f"rbar2 {path2}")
+        assert_close(g.read(V.VOPP_FIELD_LOMEGA, 2, 1, n2), sub2["lomega"][2], f"lom2 {path2}")
+        np.testing.assert_array_equal(g.read(V.VOPP_FIELD_PS, 2, 2048, n2 * 2048), sub2["ps"][2][0])
+        assert_close(g.read(V.VOPP_FIELD_PLW, 2, 2048, n2 * 2048), sub2["plw"][2][0], "plw2")
+        assert_close(g.read(V.VOPP_FIELD_V, 3, AW, n2 * AW), sub2["V"][3], f"V3 below {path2}")
+        assert_close(g.read(V.VOPP_FIELD_Q, 3, AW * 13, n2 * AW * 13), sub2["Q"][3].ravel(),
+                     f"Q3 below {path2}")
+        np.testing.assert_array_equal(g.read(V.VOPP_FIELD_REP, 3, AW, n2 * AW), sub2["rep"][3])
+        n4 = AW * AW
+        assert_close(g.read(V.VOPP_FIELD_V, 4, n4, n2 * n4), sub2["V"][4], f"V4 below {path2}")
+        assert_close(g.read(V.VOPP_FIELD_LOMEGA, 4, n4, n2 * n4), sub2["lomega"][4],
+                     f"lom4 below {path2}")
+        n5 = AW ** 3
+        assert_close(g.read(V.VOPP_FIELD_V, 5, n5, n2 * n5), sub2["V"][5], f"V5 below {path2}")
+        assert_close(g.read(V.VOPP_FIELD_RBAR, 5, n5, n2 * n5), sub2["rbar"][5],
+                     f"rbar5 below {path2}")
         # root: the FP64 root backup of the level-1 stats (closed form, any size)
         q1 = np.zeros(13)
         rb = g.read(V.VOPP_FIELD_RBAR, 1, AW).astype(np.float64).reshape(13, 3)
@@ -232,6 +261,72 @@ def test_batch_with_crowd_plans_equals_individual_plans_and_oracle():
             assert orc["status"] == O.OK
             assert_close(outs[i]["q"], orc["q_root"], f"plan {i} root Q")
             assert action_agrees(outs[i], orc, s)
+        del keep
+    finally:
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
+
+
+def test_config4_mixed_batch_at_full_size_against_oracle():
+    """The 512-plan mixed batch of the batching workload (NAV2D and GRID, N log-uniform in
+    [128, 4096], depth 3-6, width 2 or 4: 9.2e10 particle-steps) in one vopp_plan_batch call
+    with every plan's tree kept: each of its 82 plans of at most 1e7 particle-steps equals the
+    oracle node by node (root, every node's Q and V, every branch's statistics, the
+    representatives and discrete observations exact), and three of the largest plans equal
+    the oracle's subtree below a level-(D-2) node.  The FP64 oracle cannot run the larger
+    plans' roots in test time (up to 1e9 particle-steps each)."""
+    import concurrent.futures as cf
+    import os
+    import torch
+    from paper_2510_27191_b300 import vopp as V
+    specs = WL.draw_mixed_plans(512, 7)
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    V.vopp_ctx_set_tree_detail(ctx, V.VOPP_TREE_FULL)
+    rx, ry = WL.grid_layout(7)
+    models = {WL.NAV2D: V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D)),
+              WL.GRID: V.vopp_create_model(ctx, V.make_desc(V.VOPP_GRID, rock_x=rx, rock_y=ry))}
+    try:
+        pspecs = [Spec.from_plan(ps) for ps in specs]
+        reqs = [dict(model=models[s.kind], states=torch.from_numpy(s.states()).cuda(),
+                     weights=None, n=s.N, depth=s.D, width=s.W, eta=s.eta, gamma=s.gamma,
+                     seed=s.seed, A=s.A) for s in pspecs]
+        outs, keep = V.vopp_plan_batch(ctx, reqs)
+        small = [i for i, ps in enumerate(specs) if ps.steps <= 1e7]
+        assert len(small) == 82
+        threads = max(1, min(16, len(os.sched_getaffinity(0))))
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            orcs = list(ex.map(lambda i: pspecs[i].run_oracle(dump_levels=max(pspecs[i].D - 2, 0)),
+                               small))
+        for i, orc in zip(small, orcs):
+            s = pspecs[i]
+            assert orc["status"] == O.OK
+            g = Gpu.__new__(Gpu)           # read plan i's tree through the batch's context
+            g.V, g.spec, g.ctx = V, s, ctx
+            g.read = (lambda f, l, c, o=0, p=i: V.vopp_tree_read(ctx, f, l, c, o, p))
+            compare_full_tree(s, g, outs[i], orc, max(s.D - 2, 0))
+            assert action_agrees(outs[i], orc, s), i
+            assert outs[i]["particle_steps"] == orc["particle_steps"]
+        rng = np.random.default_rng(4)
+        for i in sorted(range(len(specs)), key=lambda k: -specs[k].steps)[:3]:
+            s = pspecs[i]
+            AW = s.A * s.W
+            path = tuple(int(v) for v in rng.integers(0, AW, s.D - 2))
+            sub = s.run_oracle(path=path)
+            assert sub["status"] == O.OK
+            n = 0
+            for c in path:
+                n = n * AW + c
+            assert_close(V.vopp_tree_read(ctx, V.VOPP_FIELD_V, s.D - 2, 1, n, i), sub["V"][s.D - 2],
+                         f"plan {i} V at {path}")
+            assert_close(V.vopp_tree_read(ctx, V.VOPP_FIELD_Q, s.D - 2, s.A, n * s.A, i),
+                         sub["Q"][s.D - 2][0], f"plan {i} Q at {path}")
+            assert_close(V.vopp_tree_read(ctx, V.VOPP_FIELD_V, s.D - 1, AW, n * AW, i),
+                         sub["V"][s.D - 1], f"plan {i} V below {path}")
+            assert_close(V.vopp_tree_read(ctx, V.VOPP_FIELD_V, s.D, AW * AW, n * AW * AW, i),
+                         sub["V"][s.D], f"plan {i} leaves below {path}")
+            np.testing.assert_array_equal(
+                V.vopp_tree_read(ctx, V.VOPP_FIELD_REP, s.D, AW * AW, n * AW * AW, i), sub["rep"][s.D])
         del keep
     finally:
         for m in models.values():
