@@ -1408,28 +1408,23 @@ struct ShiftedSum {
 // with the same arithmetic as GridModel::heuristic.
 // The disagreeing half of the Z table starts kGridZStride floats after the agreeing one: an
 // odd offset puts the two readings of one d^2 (a warp's usual pair of addresses) in different
-// shared-memory banks.
-#ifndef VOPP_GRID_ZSTRIDE
-#define VOPP_GRID_ZSTRIDE 257
-#endif
-constexpr int kGridZStride = VOPP_GRID_ZSTRIDE;
-// GRID leaf loops: 1 = the CTA's tables by cell (distance to each rock, heuristic, rock) in
-// place of coordinate arithmetic; 1 = compensated sums two at a time, S0 = N for NULL readings
-#ifndef VOPP_GRID_CELLTAB
-#define VOPP_GRID_CELLTAB 1
-#endif
-#ifndef VOPP_GRID_KAHAN2
-#define VOPP_GRID_KAHAN2 1
-#endif
-__shared__ float s_grid_h[16];
+// shared-memory banks.  Squared agent-rock distances run 0..221.
+constexpr int kGridZStride = 223;
+// GRID leaf tables by cell c = x + 16 y (x <= 11, y <= 10, so c < 172): squared distance to
+// each rock (bytes), heuristic (0 at the exited column x = 11) and the rock on the cell (-1 if
+// none).  Kept small so that seven 128-thread leaf CTAs fit an SM's shared memory.
+constexpr int kGridCells = 172;
 __shared__ float s_grid_z[2 * kGridZStride];   // GRID leaf: Z by (disagree, d^2), from the model
-__shared__ int s_grid_rock[121];          // GRID leaf: rock index of cell x + 11 y, or -1
+__shared__ unsigned char s_grid_d2[8 * kGridCells];
+__shared__ float s_grid_hc[kGridCells];
+__shared__ signed char s_grid_rockc[kGridCells];
+__device__ __forceinline__ int gcell(int s) { return (s >> 8) & 0xFF; }
 
 // The leaf heuristic (GRID: from the CTA's column table).
 template <class M>
 __device__ __forceinline__ float leaf_heuristic(const typename M::S &s, float log2g, float a0,
                                                 float b0, bool hz) {
-  if constexpr (std::is_same<M, GridModel>::value) return s_grid_h[gx(s.s)];
+  if constexpr (std::is_same<M, GridModel>::value) return s_grid_hc[gcell(s.s)];
   else return M::heuristic(s, log2g, a0, b0, hz);
 }
 
@@ -1582,20 +1577,12 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
 // same states and rewards as GridModel::step, which the other kernels use.  A move's or
 // collect's reading is NULL (Z = 1) and a sense reading good or bad; any other reading has
 // Z = 0 everywhere and is left to the log-domain path (false returned).
-struct GridSense { int rk, rx, ry, flip; const unsigned char *d2; };
+struct GridSense { int rk, flip; const unsigned char *d2; };
 struct GridMove { int shift, lo, span, delta, at_lim; float r_lim; };
 struct GridSums { float s0, s1, h1, rs; };
 
-// Cell x + 16 y of a packed GRID state; the CTA's tables by cell: squared distance to each
-// rock (bytes), heuristic (0 at x = 11) and the rock on the cell (-1 if none).
-__device__ __forceinline__ int gcell(int s) { return (s >> 8) & 0xFF; }
-constexpr int kGridCells = 256;
-__shared__ unsigned char s_grid_d2[8 * kGridCells];
-__shared__ float s_grid_hc[kGridCells];
-__shared__ int s_grid_rockc[kGridCells];
 
 __device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense &g, GridSums &t) {
-#if VOPP_GRID_CELLTAB
   const int c = gcell(sv);
   const int miss = ((sv >> g.rk) & 1) ^ g.flip;
   const float z = s_grid_z[miss * kGridZStride + g.d2[c]];
@@ -1603,15 +1590,6 @@ __device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense 
   t.s0 += z;
   t.s1 += wz;
   t.h1 = fmaf(wz, s_grid_hc[c], t.h1);
-#else
-  const int x = gx(sv), dx = x - g.rx, dy = gy(sv) - g.ry;
-  const int miss = ((sv >> g.rk) & 1) ^ g.flip;
-  const float z = s_grid_z[miss * kGridZStride + dx * dx + dy * dy];
-  const float wz = w * z;
-  t.s0 += z;
-  t.s1 += wz;
-  t.h1 = fmaf(wz, s_grid_h[x], t.h1);
-#endif
 }
 __device__ __forceinline__ void grid_move_one(int sv, float w, const GridMove &g, GridSums &t) {
   const bool term = gterm(sv) != 0;
@@ -1620,23 +1598,13 @@ __device__ __forceinline__ void grid_move_one(int sv, float w, const GridMove &g
   const float r = (term || !blk) ? 0.0f : g.r_lim;
   t.s0 += 1.0f;
   t.s1 += w;
-#if VOPP_GRID_CELLTAB
   t.h1 = fmaf(w, s_grid_hc[gcell(ns)], t.h1);
-#else
-  t.h1 = fmaf(w, s_grid_h[gx(ns)], t.h1);
-#endif
   t.rs = fmaf(w, r, t.rs);
 }
 __device__ __forceinline__ void grid_collect_one(int sv, float w, GridSums &t) {
-#if VOPP_GRID_CELLTAB
   const int c = gcell(sv);
   const int rk = gterm(sv) ? -1 : s_grid_rockc[c];
   const float h = s_grid_hc[c];
-#else
-  const int x = gx(sv);
-  const int rk = (gterm(sv) == 0 && x <= 10) ? s_grid_rock[x + 11 * gy(sv)] : -1;
-  const float h = s_grid_h[x];
-#endif
   const bool good = rk >= 0 && ((sv >> (rk & 7)) & 1);
   const float r = (rk >= 0) ? (good ? 10.0f : -10.0f) : 0.0f;
   t.s0 += 1.0f;
@@ -1667,7 +1635,6 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
                                            Kahan &S1, Kahan &H, Kahan &R) {
   const int lane = threadIdx.x & 31, nfull = N >> 1;
   constexpr int kCh = kGridChunk;
-#if VOPP_GRID_KAHAN2
   Kahan2 K;
   K.init();
   auto fold = [&](const GridSums &t) {
@@ -1679,14 +1646,6 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
       H.add(t.h1);
     }
   };
-#else
-  auto fold = [&](const GridSums &t) {
-    S0.add(t.s0);
-    S1.add(t.s1);
-    H.add(t.h1);
-    if (kR) R.add(t.rs);
-  };
-#endif
   for (int base = lane; base < nfull; base += 32 * kCh) {
     GridSums t{0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -1706,7 +1665,6 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
     one(nb.A[nfull].x, nb.B[nfull].z, t);
     fold(t);
   }
-#if VOPP_GRID_KAHAN2
   if (kR) {
     S0.s = (lane == 0) ? (float)N : 0.f;   // the lanes' shares of S0 = N
     S0.c = 0.f;
@@ -1716,7 +1674,6 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
     S0.s = K.s.x; S0.c = K.c.x;
     S1.s = K.s.y; S1.c = K.c.y;
   }
-#endif
 }
 
 __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevModel &dm,
@@ -1727,8 +1684,7 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
   if (a >= 5) {
     if (o.o != 1 && o.o != 2) return false;
     const int rk = a - 5;
-    const GridSense g{rk, dm.rock_x[rk], dm.rock_y[rk], (o.o == 1) ? 1 : 0,
-                      s_grid_d2 + rk * kGridCells};
+    const GridSense g{rk, (o.o == 1) ? 1 : 0, s_grid_d2 + rk * kGridCells};
     grid_pairs<false>(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
                       S0, S1, H, R);    // R stays 0: a sense action earns nothing
     return true;
@@ -1931,11 +1887,13 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   float *sm_lo = sm_rb + AW, *sm_v = sm_lo + AW;
   __shared__ float2 s_mu;
   if constexpr (std::is_same<M, GridModel>::value) {
-    // the heuristic by column; x = 11 (exited) is the terminal column, 0 like a forced-zero
-    // heuristic (a terminal state with x <= 10 exists only at the root, with weight 0)
-    for (int i = threadIdx.x; i < 2 * kGridD2; i += blockDim.x)
-      s_grid_z[(i / kGridD2) * kGridZStride + (i % kGridD2)] = dm.pz[i];
-    for (int i = threadIdx.x; i < 121; i += blockDim.x) s_grid_rock[i] = dm.rock_at[i];
+    // the Z table and the tables by cell; x = 11 (exited) is the terminal column, its
+    // heuristic 0 like a forced-zero one (a terminal state with x <= 10 exists only at the
+    // root, with weight 0); the tables are read after the node build's barriers
+    for (int i = threadIdx.x; i < 2 * kGridZStride; i += blockDim.x) {
+      const int half = i / kGridZStride, d2 = i - half * kGridZStride;
+      s_grid_z[i] = (d2 < kGridD2) ? dm.pz[half * kGridD2 + d2] : 0.f;
+    }
     for (int c = threadIdx.x; c < kGridCells; c += blockDim.x) {
       const int x = c & 15, y = c >> 4;
       const bool cell_ok = x <= 11 && y <= 10;
@@ -1943,16 +1901,10 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
         const int dx = x - dm.rock_x[r], dy = y - dm.rock_y[r];
         s_grid_d2[r * kGridCells + c] = cell_ok ? (unsigned char)(dx * dx + dy * dy) : 0;
       }
-      s_grid_rockc[c] = (x <= 10 && y <= 10) ? dm.rock_at[x + 11 * y] : -1;
+      s_grid_rockc[c] = (signed char)((x <= 10 && y <= 10) ? dm.rock_at[x + 11 * y] : -1);
       const GridModel::S col{gpack(0, x <= 10 ? x : 0, 0, 0)};
       s_grid_hc[c] = (x <= 10 && P.h_zero == 0)
                          ? GridModel::heuristic(col, P.log2_gamma, P.h_a0, P.h_b0, false) : 0.0f;
-    }
-    if (threadIdx.x < 16) {   // both tables are read after the node build's barriers
-      const int x = threadIdx.x;
-      const GridModel::S col{gpack(0, x, 0, 0)};
-      s_grid_h[x] = (x <= 10 && P.h_zero == 0)
-                        ? GridModel::heuristic(col, P.log2_gamma, P.h_a0, P.h_b0, false) : 0.0f;
     }
   }
 
