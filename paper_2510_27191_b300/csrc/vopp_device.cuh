@@ -171,19 +171,8 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).  Built from the float
 // 1 + (x >> 9) 2^-23 in [1, 2) minus (1 - 2^-24); the difference is representable, so the
 // subtraction is exact.
-#ifndef VOPP_U01_MADHI
-#define VOPP_U01_MADHI 0
-#endif
-// The bits of 1 + (x >> 9) 2^-23: (x >> 9) | 0x3F800000, or, as one integer multiply-add on
-// the FMA pipe, hi(x 2^23) + 0x3F800000 (the same value: x >> 9 < 2^23 leaves the exponent
-// bits clear).
-__device__ __forceinline__ uint32_t u01_bits(uint32_t x) {
-#if VOPP_U01_MADHI
-  return __umulhi(x, 1u << 23) + 0x3F800000u;
-#else
-  return (x >> 9) | 0x3F800000u;
-#endif
-}
+// The bits of 1 + (x >> 9) 2^-23.
+__device__ __forceinline__ uint32_t u01_bits(uint32_t x) { return (x >> 9) | 0x3F800000u; }
 __device__ __forceinline__ float u01(uint32_t x) {
   return __fadd_rn(__uint_as_float(u01_bits(x)), -0.999999940395355225f);
 }
