@@ -32,8 +32,10 @@ def make_models(V, ctx, layout_seed: int = 1):
 
 
 def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequential: bool = True,
-              autotune: bool = True):
-    """Returns a dict with the batched and sequential times (CUDA events around each)."""
+              autotune: bool = True, graphs: bool = True):
+    """Returns a dict with the batched and sequential times (CUDA events around each).
+    graphs: the batch replays its recorded launch sequence (the sequential plans always
+    launch stage by stage); the context's graph option is left off."""
     import torch
     specs = WL.draw_mixed_plans(n_plans, seed)
     models = make_models(V, ctx)
@@ -53,13 +55,15 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
         return a.elapsed_time(b) / 1e3, out
 
     tune = V.vopp_autotune(ctx, reqs[::8], reps=1) if autotune else None   # tiles from the tuner
-    V.vopp_plan_batch(ctx, reqs[:8])          # warm-up
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, int(graphs))
+    V.vopp_plan_batch(ctx, reqs)              # warm-up (and the recorded sequence)
     t_batch = []
     for _ in range(reps):
         t, (outs, keep) = timed(lambda: V.vopp_plan_batch(ctx, reqs))
         t_batch.append(t)
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, 0)
     res = {"plans": n_plans, "particle_steps": steps, "batched_s": min(t_batch),
-           "autotune": tune,
+           "autotune": tune, "graphs": bool(graphs),
            "batched_particle_steps_per_s": steps / min(t_batch),
            "batched_plans_per_s": n_plans / min(t_batch)}
     if sequential:
@@ -76,9 +80,10 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
     return res
 
 
-def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3):
+def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3, graphs: bool = True):
     """n_plans small navigation plans (N=256, depth 3, 4x4 branches: the latency-bound shape)
-    with different seeds and roots, one batch against one plan at a time (CUDA events)."""
+    with different seeds and roots, one batch against one plan at a time (CUDA events); the
+    batch replays its recorded launch sequence when graphs is set."""
     import torch
     model = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
     ps = WL.CONFIG1
@@ -103,10 +108,12 @@ def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3):
         return [V.vopp_plan(q["model"], q["states"], None, q["n"], q["depth"], q["width"],
                             q["eta"], q["gamma"], None, q["seed"]) for q in reqs]
 
-    V.vopp_plan_batch(ctx, reqs[:8])
-    seq()
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, int(graphs))
+    V.vopp_plan_batch(ctx, reqs)              # warm-up (and the recorded sequence)
     t_b = min(timed(lambda: V.vopp_plan_batch(ctx, reqs))[0] for _ in range(reps))
     outs, _ = V.vopp_plan_batch(ctx, reqs)
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_GRAPHS, 0)
+    seq()
     t_s, singles = min((timed(seq) for _ in range(reps)), key=lambda r: r[0])
     same = all(a["q"].tolist() == b["q"].tolist() for a, b in zip(outs, singles))
     V.vopp_model_destroy(model)
@@ -114,7 +121,8 @@ def small_batch_run(V, ctx, n_plans: int = 512, reps: int = 3):
     return {"plans": n_plans, "workload": "nav2d N=256 D=3 A=4 W=4 (different roots and seeds)",
             "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
             "batched_plans_per_s": n_plans / t_b, "sequential_plans_per_s": n_plans / t_s,
-            "batched_particle_steps_per_s": steps / t_b, "batched_equals_sequential": bool(same)}
+            "batched_particle_steps_per_s": steps / t_b, "batched_equals_sequential": bool(same),
+            "graphs": bool(graphs)}
 
 
 SERVE_HBM_BUDGET = 120 * (1 << 30)   # the serving workload's admission budget: 120 GB
