@@ -153,6 +153,20 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The same generator with the round keys (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85) taken from a
+// table (rk[r] = round r's key pair), e.g. one a CTA fills once in shared memory.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2 *rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint2 k = rk[r];
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, uint32_t purpose,
                                       uint32_t level, uint32_t a, uint32_t k,
                                       unsigned long long node) {
@@ -163,10 +177,19 @@ __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, ui
 
 // Two-wide FP32 arithmetic (Blackwell packed f32x2 FMA / ADD / MUL on float2), used to run
 // the two particles of a Philox pair through the same instruction.
+#ifndef VOPP_SCALAR2
+#define VOPP_SCALAR2 0
+#endif
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+#if VOPP_SCALAR2
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)); }
+#else
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#endif
 
 // u = (2 (x >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).  Built from the float
 // 1 + (x >> 9) 2^-23 in [1, 2) minus (1 - 2^-24); the difference is representable, so the
