@@ -224,6 +224,21 @@ __device__ __forceinline__ float rcpa(float x) {
   return y;
 }
 
+// Hardware square root (PTX sqrt.approx, flush-to-zero): one SFU operation where
+// x * rsqrt(x) takes an SFU operation and a multiply.
+__device__ __forceinline__ float sqrta(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 1.0f if a <= b, else 0.0f (PTX set with a float destination: one compare, no select).
+__device__ __forceinline__ float setle1(float a, float b) {
+  float y;
+  asm("set.le.f32.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+
 // fma(a, b, c) saturated to [0, 1] (PTX fma.rn.sat: an FMA-pipe instruction).
 __device__ __forceinline__ float fma_sat(float a, float b, float c) {
   float y;
@@ -286,7 +301,7 @@ __device__ __forceinline__ float2 neg2_log_u2(float2 u) {
 __device__ __forceinline__ float2 box_muller_neg(uint32_t a, uint32_t b) {
   const float u1 = u01(a), u2 = u01(b);
   const float s = neg2_log_u(u1);
-  const float r = __fmul_rn(s, rsqrtf(s));
+  const float r = sqrta(s);
   const float t = fmaf(6.28318531f, u2, -3.14159265f);
   float sn, cs;
   __sincosf(t, &sn, &cs);
@@ -447,7 +462,7 @@ struct NavModel {
     const bool p0 = rr.x <= 0.25f, p1 = rr.y <= 0.25f;
     const float2 u1 = u01_2(w.x, w.z), u2 = u01_2(w.y, w.w);
     const float2 sq = neg2_log_u2(u1);
-    const float2 r = mul2(sq, make_float2(rsqrtf(sq.x), rsqrtf(sq.y)));
+    const float2 r = make_float2(sqrta(sq.x), sqrta(sq.y));
     const float2 t = fma2(bc2(6.28318531f), u2, bc2(-3.14159265f));
     float s0, c0, s1, c1;
     __sincosf(t.x, &s0, &c0);
@@ -479,6 +494,59 @@ struct NavModel {
     t0 = p0 || g0;
     t1 = p1 || g1;
     return make_float2(p0 ? 0.0f : (g0 ? 100.0f : -1.0f), p1 ? 0.0f : (g1 ? 100.0f : -1.0f));
+  }
+  // The leaf's pair step on positions in units of 16 (x / 16, y / 16: power-of-two scalings,
+  // so every value below is 1/16 of step_pair's, bit for bit, and the clamp's upper bound is
+  // 10 / 16).  m = (m0, m1): 1 for a live particle, 0 for a terminal one, which then draws
+  // no noise and takes no move (x + m dx + m r cos = x), and earns m (101 gm - 1) = 0.
+  // gm: 1.0 where the new state is in the goal disc (x^2 + y^2 <= 1/4, i.e. 2^-10 in these
+  // units), else 0.0 -- also 1 for every terminal particle, which sits in the disc.  No
+  // selects: the masks enter as FMA operands.  Returns the rewards.
+  __device__ __forceinline__ static float2 step_pair16(float2 &x, float2 &y, float dx16,
+                                                       float dy16, uint4 w, float2 m,
+                                                       float2 &gm) {
+    const float2 u1 = u01_2(w.x, w.z), u2 = u01_2(w.y, w.w);
+    const float2 sq = mul2(neg2_log_u2(u1), m);
+    const float2 r = make_float2(sqrta(sq.x), sqrta(sq.y));
+    const float2 t = fma2(bc2(6.28318531f), u2, bc2(-3.14159265f));
+    float s0, c0, s1, c1;
+    __sincosf(t.x, &s0, &c0);
+    __sincosf(t.y, &s1, &c1);
+    const float2 wx = fma2(m, bc2(dx16), x), wy = fma2(m, bc2(dy16), y);
+    const float2 rc = mul2(r, make_float2(c0, c1)), rs = mul2(r, make_float2(s0, s1));
+    // the lower clamp as a saturating FMA (values below 1 here), the upper one a min
+    float2 nx = make_float2(fma_sat(rc.x, -0.00625f, wx.x), fma_sat(rc.y, -0.00625f, wx.y));
+    float2 ny = make_float2(fma_sat(rs.x, -0.00625f, wy.x), fma_sat(rs.y, -0.00625f, wy.y));
+    nx = make_float2(fminf(nx.x, 0.625f), fminf(nx.y, 0.625f));
+    ny = make_float2(fminf(ny.x, 0.625f), fminf(ny.y, 0.625f));
+    const float2 r2 = fma2(nx, nx, mul2(ny, ny));
+    gm = make_float2(setle1(r2.x, 0.0009765625f), setle1(r2.y, 0.0009765625f));
+    x = nx;
+    y = ny;
+    return mul2(fma2(gm, bc2(101.0f), bc2(-1.0f)), m);
+  }
+  // zlin_pair on positions in units of 16 (x - 9 = fma(x16, 16, -9) and o - x =
+  // fma(x16, -16, o) round exactly as the unscaled forms).
+  __device__ __forceinline__ static float2 zlin_pair16(float2 x, float2 y, const O &o) {
+    const float2 dm = fma2(x, bc2(16.0f), bc2(-9.0f));
+    const float2 sc = fma2(bc2(0.588705011f), make_float2(fabsf(dm.x), fabsf(dm.y)),
+                           bc2(0.0588705011f));          // (0.5 |x - 9| + 0.05) / sqrt(c)
+    const float2 s2 = mul2(sc, sc);
+    const float2 pk = make_float2(rcpa(s2.x), rcpa(s2.y));
+    const float2 ex = fma2(x, bc2(-16.0f), bc2(o.x)), ey = fma2(y, bc2(-16.0f), bc2(o.y));
+    const float2 d2 = fma2(ex, ex, mul2(ey, ey));
+    const float2 q = mul2(d2, make_float2(-pk.x, -pk.y));
+    return mul2(make_float2(ex2(q.x), ex2(q.y)), pk);
+  }
+  // heuristic_pair on positions in units of 16; zero where gm = 1 (goal reached or terminal:
+  // h - h gm), and everywhere when a0 = b0 = 0 (the forced-zero heuristic).
+  __device__ __forceinline__ static float2 heuristic_pair16(float2 x, float2 y, float2 gm,
+                                                            float log2g, float a0, float b0) {
+    float2 v = add2(x, y);                                // (x + y) / 16
+    v = make_float2(fmaxf(v.x, 0.09375f), fmaxf(v.y, 0.09375f));
+    const float2 e = fma2(v, bc2(16.0f * log2g), bc2(-1.5f * log2g));
+    const float2 h = fma2(bc2(b0), make_float2(ex2(e.x), ex2(e.y)), bc2(a0));
+    return fma2(make_float2(-h.x, -h.y), gm, h);
   }
   __device__ __forceinline__ static float sigma(float x) {
     return fmaf(0.5f, fabsf(__fadd_rn(x, -9.0f)), 0.05f);
