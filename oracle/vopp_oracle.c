@@ -34,13 +34,13 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11) with the counter layout below.
  *
  * Counter layout (key = 64-bit seed, low word first):
- *   c0 = idx | purpose << 24, c1 = level | action << 8 | branch << 16, c2,c3 = node (lo,hi)
+ *   c0 = level | action << 8 | branch << 16, c1 = idx | purpose << 24, c2,c3 = node (lo,hi)
  *   purpose 0: transition noise of particle pair idx (words 0,1 -> particle 2idx, 2,3 -> 2idx+1)
  *   purpose 1: observation draw of a branch (words 0,1 -> noise / sense outcome, word 2 -> j)
- *   purpose 3: belief-update transition of pair idx, c1 = 0, node = time step t
- *   purpose 4: belief-update resampling offset, idx 0, c1 = 0, node = t
- *   purpose 5: environment transition of the true state, idx 0, c1 = 0, node = t
- *   purpose 6: environment observation, idx 0, c1 = 0, node = t (words 0,1 as purpose 1)
+ *   purpose 3: belief-update transition of pair idx, c0 = 0, node = time step t
+ *   purpose 4: belief-update resampling offset, idx 0, c0 = 0, node = t
+ *   purpose 5: environment transition of the true state, idx 0, c0 = 0, node = t
+ *   purpose 6: environment observation, idx 0, c0 = 0, node = t (words 0,1 as purpose 1)
  *   episode mode (iteration k as the node word, episode e as idx, depth d as level):
  *   purpose 7: root state sample (word 0), 8: action sample (word 0), 9: transition
  *   (words 0,1), 10: observation (words 0,1)
@@ -134,8 +134,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 static void draw_j(uint64_t seed, uint32_t idx, uint32_t purpose, uint32_t level, uint32_t action,
                    uint32_t branch, uint32_t call, uint64_t node, uint32_t out[4]) {
   uint32_t ctr[4], key[2];
-  ctr[0] = idx | (purpose << 24);
-  ctr[1] = level | (action << 8) | (branch << 16) | (call << 24);
+  ctr[0] = level | (action << 8) | (branch << 16) | (call << 24);
+  ctr[1] = idx | (purpose << 24);
   ctr[2] = (uint32_t)node;
   ctr[3] = (uint32_t)(node >> 32);
   key[0] = (uint32_t)seed;

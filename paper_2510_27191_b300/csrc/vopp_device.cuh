@@ -137,7 +137,10 @@ __device__ __forceinline__ int find_plan(const StageTable &st, long long item) {
 
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter words:
-//   c0 = idx | purpose << 24, c1 = level | action << 8 | branch << 16, (c2, c3) = node.
+//   c0 = level | action << 8 | branch << 16, c1 = idx | purpose << 24, (c2, c3) = node.
+// The word that varies across a loop's particles (idx) is c1, which the first round does not
+// multiply: with the other words fixed in a loop, the first two rounds' products of c0 and
+// c2 are loop-invariant (two wide multiplies fewer per call).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -170,7 +173,7 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2 *rk) {
 __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t idx, uint32_t purpose,
                                       uint32_t level, uint32_t a, uint32_t k,
                                       unsigned long long node) {
-  return philox(make_uint4(idx | (purpose << 24), level | (a << 8) | (k << 16),
+  return philox(make_uint4(level | (a << 8) | (k << 16), idx | (purpose << 24),
                            (uint32_t)node, (uint32_t)(node >> 32)),
                 k0, k1);
 }
@@ -795,7 +798,7 @@ struct CrowdModel {
 
   __device__ __forceinline__ static bool terminal(const S &s) { return (s.f >> 16) & 1; }
   __device__ __forceinline__ static uint4 words(const DrawCtx &c, uint32_t idx, uint32_t j) {
-    return philox(make_uint4(idx | (c.purpose << 24), c.c1 | (j << 24), (uint32_t)c.node,
+    return philox(make_uint4(c.c1 | (j << 24), idx | (c.purpose << 24), (uint32_t)c.node,
                              (uint32_t)(c.node >> 32)), c.k0, c.k1);
   }
   __device__ __forceinline__ static float step_drawn(S &s, int a, const DrawCtx &c, uint32_t idx) {

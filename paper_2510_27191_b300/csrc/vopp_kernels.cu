@@ -382,7 +382,7 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
         const int i0 = 2 * p, i1 = 2 * p + 1;
         const bool v1 = i1 < N;
         const uint4 w = M::kStochastic
-                            ? philox(make_uint4((uint32_t)p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)),
+                            ? philox(make_uint4(c1, (uint32_t)p, (uint32_t)kn, (uint32_t)(kn >> 32)),
                                      P.key0, P.key1)
                             : make_uint4(0u, 0u, 0u, 0u);
         const float lw0 = src.lw(i0), lw1 = v1 ? src.lw(i1) : -CUDART_INF_F;
@@ -1005,7 +1005,7 @@ __device__ __forceinline__ void nav_unit(float (&x)[V], float (&y)[V], float (&r
 #pragma unroll
     for (int q = 0; q < V / 2; ++q) {
       const uint32_t p = (uint32_t)(u * (V / 2) + q);
-      const uint4 w = philox(make_uint4(p, c1, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
+      const uint4 w = philox(make_uint4(c1, p, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
       float2 X = make_float2(x[2 * q], x[2 * q + 1]), Y = make_float2(y[2 * q], y[2 * q + 1]);
       bool t0, t1;
       const float2 rr = NavModel::step_pair(X, Y, dx, dy, w, t0, t1);
@@ -1015,7 +1015,7 @@ __device__ __forceinline__ void nav_unit(float (&x)[V], float (&y)[V], float (&r
     }
   } else {
     const uint32_t i = (uint32_t)u;
-    const uint4 w = philox(make_uint4(i >> 1, c1, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
+    const uint4 w = philox(make_uint4(c1, i >> 1, (uint32_t)kn, (uint32_t)(kn >> 32)), key0, key1);
     NavModel::S s{x[0], y[0]};
     r[0] = NavModel::step(s, a, (i & 1) ? w.z : w.x, (i & 1) ? w.w : w.y, dm);
     e[0] = NavModel::loglik2(s, a, o, dm);
@@ -1477,7 +1477,7 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
         L[c] = E[c] = bc2(-CUDART_INF_F);
         Hh[c] = bc2(0.f);
         if (p < npairs) {
-          const uint4 w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+          const uint4 w = philox(make_uint4(c1, (uint32_t)p, c2, c3), key0, key1);
           const float4 xy = nb.xy(p);              // (x0, x1, y0, y1)
           const float4 b = nb.B[p];                // (lw2_0, lw2_1, w_0, w_1)
           float2 X = make_float2(xy.x, xy.y), Y = make_float2(xy.z, xy.w);
@@ -1531,7 +1531,7 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
       if (p < npairs) {
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (M::kStochastic) {   // purpose 0 (transition): counter word 0 is the pair index
-          w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+          w = philox(make_uint4(c1, (uint32_t)p, c2, c3), key0, key1);
         }
         typename M::S s0, s1;
         nb.get_pair(p, s0, s1);
@@ -1764,7 +1764,7 @@ __device__ __forceinline__ void nav_lin_loop(const SNode<NavModel> &nb, int N, i
     for (int c = 0; c < kLeafChunkLin; ++c) {
       const int p = base + 32 * c;
       if (kFull || p < npairs) {
-        const uint4 w = philox_rk(make_uint4((uint32_t)p, c1, c2, c3), s_leaf_rk);
+        const uint4 w = philox_rk(make_uint4(c1, (uint32_t)p, c2, c3), s_leaf_rk);
         const float4 xy = nb.A16(p);             // (x0, x1, y0, y1) / 16
         const float4 b = nb.B[p];                // (lw2_0, lw2_1, w_0, w_1)
         const float2 m = nb.Mk[p];
@@ -1849,7 +1849,7 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
         const int p = base + 32 * c;
         if (p < npairs) {
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
-          if (M::kStochastic) w = philox(make_uint4((uint32_t)p, c1, c2, c3), key0, key1);
+          if (M::kStochastic) w = philox(make_uint4(c1, (uint32_t)p, c2, c3), key0, key1);
           typename M::S x0, x1;
           nb.get_pair(p, x0, x1);
           const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)

@@ -89,7 +89,7 @@ def episode_mode_reference(model, A, n_obs, root_states, root_w, M, K, eta, gamm
     episode, leaf heuristics aggregated per leaf, and the visit-weighted backup applying
     Psi <- Psi - L Psi + Q (Q = 0 for an action without visits) to every belief above the
     leaves, deepest first.  ``philox_words(idx, purpose, level, node)`` returns the four
-    Philox words of counter (idx | purpose << 24, level, node, 0)."""
+    Philox words of counter (level, idx | purpose << 24, node, 0)."""
     from oracle import uniform
     w = np.asarray(root_w, dtype=np.float64)
     w = np.where([terminal(s) for s in root_states], 0.0, w)
