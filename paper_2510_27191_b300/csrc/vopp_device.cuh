@@ -384,6 +384,26 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Four warp sums at once: the halves of the warp exchange two values, the quarters one, so
+// that 10 shuffles (5 exchanges, 4 broadcasts) replace 20; every lane gets the four totals.
+__device__ __forceinline__ void warp_sum4(float a, float b, float c, float d, float &sa,
+                                          float &sb, float &sc, float &sd) {
+  const unsigned F = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool hi = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  float k0 = hi ? c : a, k1 = hi ? d : b;                 // kept: (a, b) low half, (c, d) high
+  k0 += __shfl_xor_sync(F, hi ? a : c, 16);
+  k1 += __shfl_xor_sync(F, hi ? b : d, 16);
+  float k = h8 ? k1 : k0;                                  // lanes 0-7 a, 8-15 b, 16-23 c, 24-31 d
+  k += __shfl_xor_sync(F, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(F, k, 4);
+  k += __shfl_xor_sync(F, k, 2);
+  k += __shfl_xor_sync(F, k, 1);
+  sa = __shfl_sync(F, k, 0);
+  sb = __shfl_sync(F, k, 8);
+  sc = __shfl_sync(F, k, 16);
+  sd = __shfl_sync(F, k, 24);
+}
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
