@@ -536,7 +536,9 @@ VOPP_API int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp
                        double *latency_s);
 /* Wait up to timeout_s seconds for the next plan to finish, in completion order; writes its
  * ticket (and result and latency) and releases it.  Returns the plan's status, or
- * VOPP_E_TIMEOUT when nothing finished in time. */
+ * VOPP_E_TIMEOUT when nothing finished in time.  A timeout of at most 5 ms is spent spinning
+ * on the calling thread (no sleep: a completion is seen within about a microsecond, for a
+ * serving loop that waits for its next completion or arrival); longer timeouts sleep. */
 VOPP_API int vopp_wait_any(vopp_server *srv, double timeout_s, uint64_t *ticket,
                            vopp_plan_result *out, double *latency_s);
 VOPP_API int vopp_server_get_stats(vopp_server *srv, vopp_server_stats *out);

@@ -2237,6 +2237,20 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// A short pause for spin loops (no system call).
+inline void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+  __builtin_ia32_pause();
+#elif defined(__aarch64__)
+  asm volatile("yield");
+#endif
+}
+
+// Waits of at most this long spin instead of sleeping on the condition variable (a serving
+// loop that waits for its next completion or arrival sees either within a microsecond; a
+// sleeping thread would pay a wake-up, tens of microseconds, on every request).
+constexpr double kSpinWaitMax = 5e-3;
+
 struct ServerReq {
   uint64_t ticket = 0;
   Job job;
@@ -2253,6 +2267,10 @@ struct ServerSlot {
   cudaEvent_t done_ev = nullptr;   // recorded after the batch's last operation
   char *arena = nullptr;
   size_t arena_bytes = 0;
+  // the slot's plan memory, kept between batches (the slot's stream orders its batches) so
+  // that a batch that fits needs no allocation; larger batches replace it up to kSlotKeepMax
+  char *kept = nullptr;
+  size_t kept_bytes = 0;
   std::vector<ServerReq> reqs;
   std::vector<Job> jobs;
   bool busy = false;
@@ -2386,6 +2404,9 @@ std::vector<ServerReq> take_batch(vopp_server *srv, size_t *bytes_out) {
   return batch;
 }
 
+// The most plan memory a slot keeps between batches.
+constexpr size_t kSlotKeepMax = size_t(256) << 20;
+
 // Enqueue a batch on a slot's stream (worker thread, lock NOT held).
 int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch) {
   std::vector<Job> jobs;
@@ -2398,8 +2419,23 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
   }
   const size_t arena_bytes = place_jobs(jobs);
   char *arena = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&arena), arena_bytes, srv->c->pool,
-                                          s->slot.stream);
+  cudaError_t e = cudaSuccess;
+  bool own = false;                         // a one-off arena, released after the batch
+  if (arena_bytes <= s->kept_bytes) {
+    arena = s->kept;
+  } else {
+    if (s->kept) cudaFreeAsync(s->kept, s->slot.stream);
+    s->kept = nullptr;
+    s->kept_bytes = 0;
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&arena), arena_bytes, srv->c->pool,
+                                s->slot.stream);
+    if (e == cudaSuccess && arena_bytes <= kSlotKeepMax) {
+      s->kept = arena;
+      s->kept_bytes = arena_bytes;
+    } else {
+      own = e == cudaSuccess;
+    }
+  }
   for (auto &j : jobs)   // plans whose agents keep their trees get memory of their own
     if (e == cudaSuccess && j.agent)
       e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, srv->c->pool,
@@ -2408,13 +2444,13 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
                                              srv->use_graphs ? &s->graphs : nullptr)
                                : VOPP_E_NOMEM;
   if (rc == VOPP_OK) {
-    if (cudaFreeAsync(arena, s->slot.stream) != cudaSuccess ||
+    if ((own && cudaFreeAsync(arena, s->slot.stream) != cudaSuccess) ||
         cudaEventRecord(s->done_ev, s->slot.stream) != cudaSuccess)
       rc = VOPP_E_CUDA;
   }
   if (rc != VOPP_OK) {
     cudaGetLastError();
-    if (arena) cudaFreeAsync(arena, s->slot.stream);
+    if (own) cudaFreeAsync(arena, s->slot.stream);
     for (auto &j : jobs)
       if (j.own_arena) cudaFreeAsync(j.own_arena, s->slot.stream);
     cudaStreamSynchronize(s->slot.stream);
@@ -2484,7 +2520,7 @@ void worker_main(vopp_server *srv) {
       // again without the lock, in flight or within the idle polling window
       const size_t queued = srv->n_pending.load();
       if (busy_now > 0 && (queued == 0 || busy_now == (int)srv->slots.size())) {
-        std::this_thread::yield();
+        for (int k = 0; k < 8; ++k) cpu_relax();   // batches in flight: poll again soon
         idle_since = now_s();
         continue;
       }
@@ -2630,6 +2666,7 @@ void vopp_server_destroy(vopp_server *srv) {
   srv->cv_work.notify_all();
   if (srv->worker.joinable()) srv->worker.join();
   for (auto *s : srv->slots) {
+    if (s->kept) cudaFreeAsync(s->kept, s->slot.stream);
     cudaStreamSynchronize(s->slot.stream);
     s->graphs.release();
     free_slot(s->slot);
@@ -2707,25 +2744,42 @@ int vopp_wait(vopp_server *srv, uint64_t ticket, double timeout_s, vopp_plan_res
 int vopp_wait_any(vopp_server *srv, double timeout_s, uint64_t *ticket, vopp_plan_result *out,
                   double *latency_s) {
   if (!srv || !ticket) return fail(VOPP_E_INVALID, "NULL argument");
-  // a zero-timeout poll with nothing finished answers without the lock, so that a caller
-  // polling in a loop never holds up the worker
-  if (!(timeout_s > 0.0) && srv->n_order.load() == 0)
-    return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
-  std::unique_lock<std::mutex> lock(srv->mu);
-  auto ready = [&] {
+  auto ready = [&] {   // (lock held)
     while (!srv->completion_order.empty() && !srv->done.count(srv->completion_order.front()))
       srv->completion_order.pop_front();   // already taken by vopp_poll / vopp_wait
     srv->n_order.store(srv->completion_order.size());
     return !srv->completion_order.empty();
   };
+  auto take_front = [&] {   // (lock held, ready() true)
+    *ticket = srv->completion_order.front();
+    srv->completion_order.pop_front();
+    srv->n_order.store(srv->completion_order.size());
+    return take_done(srv, *ticket, out, latency_s);
+  };
+  // a short timeout spins on the completion count (no lock, no sleep) until a plan has
+  // finished or the time is up; entries of tickets already taken by vopp_poll / vopp_wait
+  // are dropped under the lock and the spin goes on
+  if (timeout_s > 0.0 && timeout_s <= kSpinWaitMax) {
+    const double t_end = now_s() + timeout_s;
+    for (;;) {
+      while (srv->n_order.load() == 0 && now_s() < t_end)
+        for (int k = 0; k < 4; ++k) cpu_relax();
+      if (srv->n_order.load() == 0) return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
+      std::unique_lock<std::mutex> lock(srv->mu);
+      if (ready()) return take_front();
+      if (now_s() >= t_end) return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
+    }
+  }
+  // a zero-timeout poll with nothing finished answers without the lock, so that a caller
+  // polling in a loop never holds up the worker
+  if (!(timeout_s > 0.0) && srv->n_order.load() == 0)
+    return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
+  std::unique_lock<std::mutex> lock(srv->mu);
   const bool ok = timeout_s > 0.0
                       ? srv->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), ready)
                       : ready();   // a zero timeout only looks
   if (!ok) return fail(VOPP_E_TIMEOUT, "no plan completed within the timeout");
-  *ticket = srv->completion_order.front();
-  srv->completion_order.pop_front();
-  srv->n_order.store(srv->completion_order.size());
-  return take_done(srv, *ticket, out, latency_s);
+  return take_front();
 }
 
 int vopp_server_set_paused(vopp_server *srv, int paused) {

@@ -249,9 +249,14 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
                 break
             if now > seconds * drain_factor:
                 break                                  # overloaded: stop draining
-            # poll: a completion or an arrival is picked up within microseconds (a blocking
-            # wait would add a thread wake-up to every request)
-            got = V.vopp_wait_any(srv, 0.0) if inflight else None
+            # wait for a completion until the next arrival is due: the library spins for such
+            # short waits, so a completion or an arrival is picked up within a microsecond
+            # (a sleeping wait would add a thread wake-up to every request)
+            if inflight:
+                wait = (arrivals[k] - now) if k < n_req else 1e-3
+                got = V.vopp_wait_any(srv, min(max(wait, 0.0), 1e-3))
+            else:
+                got = None
             if got is None:
                 if not inflight and k < n_req:
                     while time.perf_counter() - t0 < arrivals[k]:
