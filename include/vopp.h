@@ -207,6 +207,13 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 #define VOPP_OPT_REUSE_COPY 8   /* 1 (default): a plan that continues a kept subtree copies its
                                    materialised levels; 0: it expands them again under the same
                                    keys (the same result; for checking the copies) */
+#define VOPP_OPT_SERVER_DIRECT 9 /* 1 (default): a server created while the option is on lets
+                                   a submitting thread that finds it idle (nothing queued, a
+                                   slot free, the request within the budget) launch the request
+                                   itself, as a batch of one, instead of handing it to the
+                                   worker (the submit call then returns after the launch,
+                                   without waiting for the device); 0: the worker launches
+                                   every batch */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);

@@ -140,6 +140,7 @@ struct vopp_ctx {
   int leaf_threads = 128;
   int grid_cap = 1 << 30;
   int reuse_copy = 1;            // plans continuing a kept subtree copy its levels (else recompute)
+  int server_direct = 1;         // servers created now launch an idle server's requests at submit
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -1350,6 +1351,7 @@ int vopp_ctx_set_option(vopp_ctx *c, int32_t option, int64_t value) {
       if (!c->use_graphs) c->graph.reset();
       return VOPP_OK;
     case VOPP_OPT_REUSE_COPY: c->reuse_copy = value ? 1 : 0; return VOPP_OK;
+    case VOPP_OPT_SERVER_DIRECT: c->server_direct = value ? 1 : 0; return VOPP_OK;
     default: return fail(VOPP_E_INVALID, "unknown option %d", option);
   }
 }
@@ -2260,7 +2262,10 @@ struct ServerReq {
   double t_submit = 0.0;
 };
 
-// Slot state is touched by the worker thread only.
+// A slot is claimed (busy set) under the server mutex by the thread that launches its batch:
+// the worker, or a submitting thread that found the server idle.  While `launching` is set
+// only that thread touches the slot; afterwards only the worker does, until it posts the
+// batch and clears busy.
 struct ServerSlot {
   Slot slot;
   GraphSet graphs;                 // the slot's replayable launch sequences (server graphs on)
@@ -2273,7 +2278,8 @@ struct ServerSlot {
   size_t kept_bytes = 0;
   std::vector<ServerReq> reqs;
   std::vector<Job> jobs;
-  bool busy = false;
+  std::atomic<bool> busy{false};
+  std::atomic<bool> launching{false};   // claimed, batch not yet enqueued (worker: hands off)
 };
 
 struct Done {
@@ -2288,6 +2294,7 @@ struct vopp_server {
   vopp_ctx *c = nullptr;
   int max_batch = 64;
   int use_graphs = 0;              // replay recorded launch sequences (VOPP_OPT_GRAPHS at creation)
+  bool direct = true;              // an idle server's submitting thread launches the request
   size_t budget = 0, in_flight = 0, peak_in_flight = 0;
   std::vector<ServerSlot *> slots;
   std::thread worker;
@@ -2509,7 +2516,7 @@ void worker_main(vopp_server *srv) {
     fin.clear();
     hv.clear();
     for (auto *s : srv->slots) {
-      if (!s->busy) continue;
+      if (!s->busy.load() || s->launching.load()) continue;
       const int st = slot_state(s);
       if (st != 0) { fin.push_back(s); hv.push_back(gather(srv, s, st > 0)); }
     }
@@ -2569,7 +2576,7 @@ void worker_main(vopp_server *srv) {
       // shutting down: wait (bounded) for the busy slots rather than polling at full rate
       lock.unlock();
       for (auto *s : srv->slots) {
-        if (!s->busy) continue;
+        if (!s->busy || s->launching) continue;   // (a submitting thread's launch: next pass)
         int st = 0;
         for (int spins = 0; (st = slot_state(s)) == 0 && spins < 200000; ++spins)   // <= ~10 s
           std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -2589,22 +2596,72 @@ void worker_main(vopp_server *srv) {
       std::this_thread::yield();
     } else {
       srv->cv_work.wait_for(lock, std::chrono::milliseconds(1), [&] {
-        return srv->stop || (!srv->pending.empty() && !srv->paused);
+        if (srv->stop || (!srv->pending.empty() && !srv->paused)) return true;
+        for (auto *q : srv->slots)   // a batch a submitting thread launched
+          if (q->busy && !q->launching) return true;
+        return false;
       });
     }
     if (busy) idle_since = now_s();
   }
 }
 
+// Queue a request; or, when the server is idle (nothing queued, not paused, a slot free and
+// the request within the budget), launch it at once as a batch of one on the calling thread,
+// which saves the hand-off to the worker.  The worker then watches the slot as its own.
 int submit_req(vopp_server *srv, ServerReq &&r, uint64_t *ticket) {
+  std::vector<ServerReq> batch;
+  ServerSlot *s = nullptr;
+  size_t bytes = 0;
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     r.ticket = srv->next_ticket++;
     r.t_submit = now_s();
     *ticket = r.ticket;
     srv->stats.submitted += 1;
-    srv->pending.push_back(std::move(r));
-    srv->n_pending.store(srv->pending.size());
+    if (srv->direct && !srv->stop && !srv->paused && srv->pending.empty() &&
+        srv->in_flight + r.bytes <= srv->budget) {
+      bytes = r.bytes;
+      batch.push_back(std::move(r));
+      s = pick_slot(srv, batch);
+      if (s) {
+        // launching first: the worker polls without the lock, reading busy and then
+        // launching, so a slot it sees busy is one it also sees launching until the batch
+        // is in place
+        s->launching = true;
+        s->busy = true;
+        srv->in_flight += bytes;
+      } else {
+        r = std::move(batch.back());
+        batch.clear();
+      }
+    }
+    if (!s) {
+      srv->pending.push_back(std::move(r));
+      srv->n_pending.store(srv->pending.size());
+    }
+  }
+  if (s) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != srv->c->device) cudaSetDevice(srv->c->device);
+    const int rc = launch_batch(srv, s, batch);
+    if (prev >= 0 && prev != srv->c->device) cudaSetDevice(prev);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (rc != VOPP_OK) {
+      srv->in_flight -= bytes;
+      post_failure(srv, batch, rc);
+      s->busy = false;
+      srv->cv_done.notify_all();
+    } else {
+      s->arena_bytes = bytes;
+      s->reqs = std::move(batch);
+      srv->peak_in_flight = std::max(srv->peak_in_flight, srv->in_flight);
+      srv->stats.batches += 1;
+      srv->stats.batched_plans += 1;
+      srv->stats.max_batch_seen = std::max<uint64_t>(srv->stats.max_batch_seen, 1);
+    }
+    s->launching = false;
   }
   srv->cv_work.notify_one();
   return VOPP_OK;
@@ -2625,6 +2682,7 @@ int vopp_server_create(vopp_ctx *c, int32_t max_batch, int32_t n_slots, size_t h
   srv->c = c;
   srv->max_batch = max_batch;
   srv->use_graphs = c->use_graphs;
+  srv->direct = c->server_direct != 0;
   srv->budget = hbm_budget_bytes ? hbm_budget_bytes : c->budget;
   for (int i = 0; i < n_slots; ++i) {
     ServerSlot *s = new (std::nothrow) ServerSlot;

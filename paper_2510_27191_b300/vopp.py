@@ -32,6 +32,7 @@ VOPP_OPT_PERSISTENT = 5
 VOPP_OPT_FP64_ROOT = 6
 VOPP_OPT_GRAPHS = 7
 VOPP_OPT_REUSE_COPY = 8
+VOPP_OPT_SERVER_DIRECT = 9
 VOPP_MAX_ACTIONS = 16
 NUM_ACTIONS = {VOPP_NAV2D: 4, VOPP_GRID: 13, VOPP_TOY2: 2}
 

@@ -258,3 +258,64 @@ def test_agents_come_and_go_while_plans_run():
         for m in models.values():
             V.vopp_model_destroy(m)
         V.vopp_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("direct", [1, 0])
+def test_direct_dispatch_matches_alone(direct):
+    """An idle server's submitting thread launches the request itself (VOPP_OPT_SERVER_DIRECT
+    1) or hands every request to the worker (0): one request at a time and in a burst, every
+    result equals the plan run alone, bit for bit, and every request is accounted for."""
+    from paper_2510_27191_b300 import vopp as V
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    models = _models(V, ctx)
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_SERVER_DIRECT, direct)
+    srv = V.vopp_server_create(ctx, max_batch=8, n_slots=3)
+    V.vopp_ctx_set_option(ctx, V.VOPP_OPT_SERVER_DIRECT, 1)
+    try:
+        specs = WL.draw_mixed_plans(24, 5, 1 << 21)
+        inputs = [(ps, Spec.from_plan(ps).states()) for ps in specs]
+        A = {WL.NAV2D: 4, WL.GRID: 13}
+        one_by_one = []
+        for ps, st in inputs[:12]:
+            t = V.vopp_submit(srv, models[ps.kind], st, None, ps.N, ps.D, ps.W, ps.eta,
+                              ps.gamma, ps.seed)
+            one_by_one.append(V.vopp_wait(srv, t, A[ps.kind], 20.0)[0])
+        stats = V.vopp_server_get_stats(srv)
+        assert stats["completed"] == 12 and stats["batches"] == 12   # each ran alone
+        tickets = [V.vopp_submit(srv, models[ps.kind], st, None, ps.N, ps.D, ps.W, ps.eta,
+                                 ps.gamma, ps.seed) for ps, st in inputs[12:]]
+        burst = []
+        for t, (ps, _) in zip(tickets, inputs[12:]):
+            burst.append(V.vopp_wait(srv, t, A[ps.kind], 20.0)[0])
+        stats = V.vopp_server_get_stats(srv)
+        assert stats["completed"] == 24 and stats["rejected"] == 0 and stats["pending"] == 0
+        for res, (ps, st) in zip(one_by_one + burst, inputs):
+            alone = V.vopp_plan(models[ps.kind], st, None, ps.N, ps.D, ps.W, ps.eta, ps.gamma,
+                                None, ps.seed)
+            assert res["q"].tolist() == alone["q"].tolist()
+            assert res["action"] == alone["action"] and res["v_root"] == alone["v_root"]
+        # stress: tiny plans kept three in flight, each next one submitted the moment one
+        # finishes (submitting threads and the worker race for the slots); every ticket
+        # completes exactly once and the in-flight reservation returns to zero
+        x, y, _ = WL.nav_root(64, 9)
+        st = np.concatenate([x, y])
+        nav = models[WL.NAV2D]
+        live, seen, n_sub = set(), set(), 0
+        while n_sub < 3000 or live:
+            while n_sub < 3000 and len(live) < 3:
+                live.add(V.vopp_submit(srv, nav, st, None, 64, 2, 2, 1.0, 0.95, n_sub + 1))
+                n_sub += 1
+            got = V.vopp_wait_any(srv, 2.0)
+            assert got is not None, "a submitted plan never completed"
+            t, rc, _, _ = got
+            assert rc == V.VOPP_OK and t in live and t not in seen
+            live.discard(t)
+            seen.add(t)
+        stats = V.vopp_server_get_stats(srv)
+        assert stats["completed"] == stats["submitted"] == 24 + 3000
+        assert stats["pending"] == 0 and stats["in_flight_bytes"] == 0
+    finally:
+        V.vopp_server_destroy(srv)
+        for m in models.values():
+            V.vopp_model_destroy(m)
+        V.vopp_ctx_destroy(ctx)
