@@ -207,13 +207,16 @@ VOPP_API int vopp_ctx_set_tree_detail(vopp_ctx *ctx, int detail);
 #define VOPP_OPT_REUSE_COPY 8   /* 1 (default): a plan that continues a kept subtree copies its
                                    materialised levels; 0: it expands them again under the same
                                    keys (the same result; for checking the copies) */
-#define VOPP_OPT_SERVER_DIRECT 9 /* 1 (default): a server created while the option is on lets
+#define VOPP_OPT_SERVER_DIRECT 9 /* 1: a server created while the option is on lets
                                    a submitting thread that finds it idle (nothing queued, a
                                    slot free, the request within the budget) launch the request
                                    itself, as a batch of one, instead of handing it to the
                                    worker (the submit call then returns after the launch,
-                                   without waiting for the device); 0: the worker launches
-                                   every batch */
+                                   without waiting for the device); 0 (default): the worker
+                                   launches every batch (for a caller that submits and
+                                   collects on one thread the cheaper submit measured better:
+                                   the launch no longer delays its noticing other plans'
+                                   completions) */
 VOPP_API int vopp_ctx_set_option(vopp_ctx *ctx, int32_t option, int64_t value);
 /* Enable (1) / disable (0) per-kernel CUDA-event timing on the context's stream. */
 VOPP_API int vopp_ctx_set_timing(vopp_ctx *ctx, int enable);
@@ -407,7 +410,11 @@ VOPP_API int vopp_belief_update_batch(vopp_ctx *ctx, int32_t n, vopp_agent *cons
  *     subtree already has instead of expanding them (VOPP_FLAG_REUSED, reused_levels).  A
  *     reused plan therefore equals the subtree below the adopted branches of one tree that
  *     is that much deeper, and every reused plan from the same belief is the same plan.
- * Anytime and episode-mode plans of the agent neither keep nor continue trees. */
+ * Anytime and episode-mode plans of the agent neither keep nor continue trees.
+ * enable: 0 off; 1 on for models with discrete observations (GRID, TOY2, CROWD) and off for
+ * NAV2D, whose continuous observations practically never equal a sampled one (its plans
+ * would pay for kept trees that are never adopted); 2 on for every model (a caller that
+ * feeds back the trees' own sampled observations).  Other values: VOPP_E_INVALID. */
 VOPP_API int vopp_agent_set_reuse(vopp_agent *agent, int32_t enable);
 /* After a belief update: the adopted branch a*W + k (or -1 when the SIR update ran), the
  * materialised levels of the kept subtree (root included, 0 if none) and the key level of

@@ -140,7 +140,7 @@ struct vopp_ctx {
   int leaf_threads = 128;
   int grid_cap = 1 << 30;
   int reuse_copy = 1;            // plans continuing a kept subtree copy its levels (else recompute)
-  int server_direct = 1;         // servers created now launch an idle server's requests at submit
+  int server_direct = 0;         // servers created now launch an idle server's requests at submit
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -188,6 +188,11 @@ struct vopp_agent {
   int reuse = 0;
   KeptTree *tree = nullptr, *sub = nullptr;
   int adopted_slot = -1;                // branch a*W + k adopted by the last update, or -1
+  // the memory of a released kept tree, for the agent's next plan (no allocation per plan):
+  // taken once spare_ev, recorded after the last work that read it, has completed
+  char *spare = nullptr;
+  size_t spare_bytes = 0;
+  cudaEvent_t spare_ev = nullptr;
   float *xy = nullptr, *lw = nullptr;   // NAV2D: xy[2N] (x then y)
   int *s = nullptr;                     // GRID / TOY2
   float *txy = nullptr, *tlw = nullptr;
@@ -999,10 +1004,42 @@ void attach_reuse(vopp_agent *g, Job &j) {
   j.lay = make_layout(j.shape);
 }
 
+// Release an agent's kept tree, its memory becoming the agent's spare (the larger of the two
+// is kept) once the work enqueued on s so far -- the last that read it -- has completed.
+void release_kept(vopp_agent *g, KeptTree *&t, cudaStream_t s) {
+  if (t && t->mem && (!g->spare || t->bytes > g->spare_bytes)) {
+    if (g->spare_ev || cudaEventCreateWithFlags(&g->spare_ev, cudaEventDisableTiming) == cudaSuccess) {
+      if (cudaEventRecord(g->spare_ev, s) == cudaSuccess) {
+        if (g->spare) cudaFreeAsync(g->spare, s);
+        g->spare = t->mem;
+        g->spare_bytes = t->bytes;
+        t->mem = nullptr;
+      }
+    }
+    cudaGetLastError();
+  }
+  free_kept(t, s);
+}
+
+// Memory of at least `bytes` for an agent's plan from its spare, or null (the caller
+// allocates).
+char *take_spare(vopp_agent *g, size_t bytes) {
+  if (!g->spare || g->spare_bytes < bytes) return nullptr;
+  const cudaError_t q = cudaEventQuery(g->spare_ev);
+  if (q != cudaSuccess) {
+    if (q != cudaErrorNotReady) cudaGetLastError();
+    return nullptr;
+  }
+  char *p = g->spare;
+  g->spare = nullptr;
+  g->spare_bytes = 0;
+  return p;
+}
+
 // After an agent's plan: its tree replaces the agent's kept tree (or is released if the
 // plan failed).
 void keep_tree(vopp_agent *g, Job &j, bool ok, cudaStream_t s) {
-  free_kept(g->tree, s);
+  release_kept(g, g->tree, s);
   if (!ok || !j.own_arena) {
     if (j.own_arena) cudaFreeAsync(j.own_arena, s);
     j.own_arena = nullptr;
@@ -1911,8 +1948,9 @@ void vopp_agent_destroy(vopp_agent *g) {
     free_kept(g->tree, s);
     free_kept(g->sub, s);
     for (void *p : {(void *)g->blk, (void *)g->tblk, (void *)g->lw, (void *)g->tlw,
-                    (void *)g->cdf, (void *)g->anc, (void *)g->dout})
+                    (void *)g->cdf, (void *)g->anc, (void *)g->dout, (void *)g->spare})
       if (p) cudaFreeAsync(p, s);
+    if (g->spare_ev) cudaEventDestroy(g->spare_ev);
   }
   delete g;
 }
@@ -1935,8 +1973,10 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
   if (!g->reuse) return run_jobs(c, jobs, out, nullptr);
   Job &j = jobs[0];
   attach_reuse(g, j);
-  if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, c->pool, c->stream) !=
-      cudaSuccess) {
+  j.own_arena = take_spare(g, j.lay.bytes);
+  if (!j.own_arena &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, c->pool, c->stream) !=
+          cudaSuccess) {
     cudaGetLastError();
     return fail(VOPP_E_NOMEM, "plan memory for the kept tree");
   }
@@ -1947,11 +1987,17 @@ int vopp_agent_plan(vopp_agent *g, const vopp_plan_params *p, vopp_plan_result *
 
 int vopp_agent_set_reuse(vopp_agent *g, int32_t enable) {
   if (!g) return fail(VOPP_E_INVALID, "agent is NULL");
-  g->reuse = enable != 0;
+  if (enable < 0 || enable > 2) return fail(VOPP_E_INVALID, "enable must be 0, 1 or 2");
+  // continuous observations (NAV2D) practically never equal a branch's sampled one: a kept
+  // tree would cost every plan its memory and observation stores for nothing
+  g->reuse = enable == 2 || (enable == 1 && g->model->desc.kind != VOPP_NAV2D);
   if (!g->reuse) {
     cudaStream_t s = g->model->ctx->stream;
     free_kept(g->tree, s);
     free_kept(g->sub, s);
+    if (g->spare) cudaFreeAsync(g->spare, s);
+    g->spare = nullptr;
+    g->spare_bytes = 0;
     g->adopted_slot = -1;
   }
   return VOPP_OK;
@@ -2030,11 +2076,11 @@ int reuse_update(vopp_agent *g, int slot, cudaStream_t s) {
   free_kept(g->sub, s);
   g->adopted_slot = -1;
   if (slot < 0) {
-    free_kept(g->tree, s);
+    release_kept(g, g->tree, s);
     return VOPP_OK;
   }
   const int rc = adopt_subtree(g, slot, s);
-  free_kept(g->tree, s);
+  release_kept(g, g->tree, s);
   if (rc) return rc;
   g->adopted_slot = slot;
   return VOPP_OK;
@@ -2294,7 +2340,7 @@ struct vopp_server {
   vopp_ctx *c = nullptr;
   int max_batch = 64;
   int use_graphs = 0;              // replay recorded launch sequences (VOPP_OPT_GRAPHS at creation)
-  bool direct = true;              // an idle server's submitting thread launches the request
+  bool direct = false;             // an idle server's submitting thread launches the request
   size_t budget = 0, in_flight = 0, peak_in_flight = 0;
   std::vector<ServerSlot *> slots;
   std::thread worker;
@@ -2444,7 +2490,7 @@ int launch_batch(vopp_server *srv, ServerSlot *s, std::vector<ServerReq> &batch)
     }
   }
   for (auto &j : jobs)   // plans whose agents keep their trees get memory of their own
-    if (e == cudaSuccess && j.agent)
+    if (e == cudaSuccess && j.agent && !(j.own_arena = take_spare(j.agent, j.lay.bytes)))
       e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j.own_arena), j.lay.bytes, srv->c->pool,
                                   s->slot.stream);
   int rc = (e == cudaSuccess) ? enqueue_jobs(srv->c, s->slot, arena, jobs, false,

@@ -253,7 +253,8 @@ def serve_run(V, ctx, seconds: float = 5.0, rate: float = 2000.0, n_agents: int 
             # short waits, so a completion or an arrival is picked up within a microsecond
             # (a sleeping wait would add a thread wake-up to every request)
             if inflight:
-                wait = (arrivals[k] - now) if k < n_req else 1e-3
+                # (the clock read again: the submissions above take time)
+                wait = (arrivals[k] - (time.perf_counter() - t0)) if k < n_req else 1e-3
                 got = V.vopp_wait_any(srv, min(max(wait, 0.0), 1e-3))
             else:
                 got = None

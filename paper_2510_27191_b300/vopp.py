@@ -474,7 +474,9 @@ def vopp_belief_update_batch(ctx: int, agents, actions, obs, kinds):
     return st, ess, res.astype(bool)
 
 
-def vopp_agent_set_reuse(agent: int, enable: bool = True) -> None:
+def vopp_agent_set_reuse(agent: int, enable: int = 1) -> None:
+    """enable: 0 off, 1 (or True) on for discrete-observation models (NAV2D keeps nothing),
+    2 on for every model."""
     check(lib.vopp_agent_set_reuse(agent, int(enable)))
 
 

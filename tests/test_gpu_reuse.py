@@ -237,3 +237,43 @@ def test_shallow_tree_or_width_change_plans_afresh():
         V.vopp_model_destroy(model)
     finally:
         V.vopp_ctx_destroy(ctx)
+
+
+def test_reuse_keeps_no_tree_for_continuous_observations_unless_forced():
+    """enable = 1 keeps no tree for a NAV2D agent (continuous observations practically never
+    match) and its plans equal an agent's without reuse bit for bit; enable = 2 keeps the tree
+    for NAV2D too: the observation a root branch sampled, fed back, is adopted."""
+    from paper_2510_27191_b300 import vopp as V
+    x, y, _ = WL.nav_root(N, 3)
+    st = np.concatenate([x, y]).astype(np.float32)
+    ctx = V.vopp_ctx_create(0, 0, 0)
+    try:
+        V.vopp_ctx_set_tree_detail(ctx, V.VOPP_TREE_FULL)
+        model = V.vopp_create_model(ctx, V.make_desc(V.VOPP_NAV2D))
+        with pytest.raises(V.VoppError):
+            g = V.vopp_agent_create(model, st, None, N, 11)
+            try:
+                V.vopp_agent_set_reuse(g, 3)
+            finally:
+                V.vopp_agent_destroy(g)
+        out = {}
+        for enable in (0, 1, 2):
+            g = V.vopp_agent_create(model, st, None, N, 11)
+            V.vopp_agent_set_reuse(g, enable)
+            r0 = V.vopp_agent_plan(g, model, 3, 2, 0.5, 0.95, 3)
+            a = int(r0["action"])
+            obs = V.vopp_tree_read(ctx, V.VOPP_FIELD_OBS, 1, 2 * 4 * 2)   # level 1: (x, y) per child
+            slot = a * 2 + 1                                   # the second branch of action a
+            o = (float(obs[2 * slot]), float(obs[2 * slot + 1]))
+            V.vopp_belief_update(g, a, o, WL.NAV2D)
+            info = V.vopp_agent_reuse_info(g)
+            r1 = V.vopp_agent_plan(g, model, 3, 2, 0.5, 0.95, 4)
+            out[enable] = (info["adopted_slot"], r1)
+            V.vopp_agent_destroy(g)
+        assert out[0][0] == -1 and out[1][0] == -1
+        np.testing.assert_array_equal(out[0][1]["q"], out[1][1]["q"])
+        assert not (out[1][1]["flags"] & V.VOPP_FLAG_REUSED)
+        assert out[2][0] >= 0 and (out[2][1]["flags"] & V.VOPP_FLAG_REUSED)
+        V.vopp_model_destroy(model)
+    finally:
+        V.vopp_ctx_destroy(ctx)
