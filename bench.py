@@ -659,19 +659,23 @@ def main():
             out["batched"] = LG.batch_run(V, ctx)
             out["batched_small"] = LG.small_batch_run(V, ctx)
             served = {}
-            # served: continuous batching, batched belief updates, agents with subtree reuse;
-            # plain: one synchronous plan per request, then its own belief update
-            for rate in (2000.0, 16000.0):
-                for mode in ("served", "plain"):
-                    secs = args.serve_seconds if rate == 2000.0 else args.overload_seconds
-                    r = LG.serve_run(V, ctx, seconds=secs, rate=rate, mode=mode,
-                                     drain_factor=2.0, reuse=(mode == "served"))
-                    served[f"{mode}_{int(rate)}"] = {k: r[k] for k in (
-                        "plans_per_s", "particle_steps_per_s", "p50_ms", "p99_ms",
-                        "deadline_misses", "completed", "requests", "unfinished",
-                        "subtree_reuse", "reused_plans", "seconds", "hbm_budget_bytes")}
-                    if mode == "served":
-                        served[f"{mode}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
+            # served: continuous batching, batched belief updates, agents with subtree reuse
+            # (the workload as specified); served_noreuse: the same without kept trees; plain:
+            # one synchronous plan per request, then its own belief update
+            legs = [(2000.0, "served", True), (2000.0, "plain", False),
+                    (2000.0, "served_noreuse", False), (16000.0, "served", True),
+                    (16000.0, "plain", False)]
+            for rate, name, reuse in legs:
+                mode = "plain" if name == "plain" else "served"
+                secs = args.serve_seconds if rate == 2000.0 else args.overload_seconds
+                r = LG.serve_run(V, ctx, seconds=secs, rate=rate, mode=mode,
+                                 drain_factor=2.0, reuse=reuse)
+                served[f"{name}_{int(rate)}"] = {k: r[k] for k in (
+                    "plans_per_s", "particle_steps_per_s", "p50_ms", "p99_ms",
+                    "deadline_misses", "completed", "requests", "unfinished",
+                    "subtree_reuse", "reused_plans", "seconds", "hbm_budget_bytes")}
+                if mode == "served":
+                    served[f"{name}_{int(rate)}"]["mean_batch"] = r.get("mean_batch")
             out["served"] = served
         if not args.no_batch_serve:
             out["modes"] = modes_run(V, ctx, spec, dev_states)
