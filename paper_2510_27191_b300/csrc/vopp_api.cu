@@ -496,8 +496,10 @@ int reuse_top(const vopp_ctx *c, const Job &j) {
 
 // The copies that put a kept subtree's levels 0..reuse_top into a plan's arena `base`:
 // particle stores, branch statistics, observations and mean particles, and zeroed
-// completion counters (the kernels that would have written them do not run).
-void reuse_copies(const vopp_ctx *c, const Job &j, char *base, std::vector<CopyOp> &ops) {
+// completion counters (the kernels that would have written them do not run).  level0:
+// only level 0's (the root's particles and log weights); otherwise only levels >= 1.
+void reuse_copies(const vopp_ctx *c, const Job &j, char *base, std::vector<CopyOp> &ops,
+                  bool level0) {
   const KeptTree &t = *j.reuse_src;
   const PlanLayout &L = j.lay, &S = t.lay;
   const size_t N = (size_t)j.shape.N;
@@ -505,7 +507,7 @@ void reuse_copies(const vopp_ctx *c, const Job &j, char *base, std::vector<CopyO
   auto add = [&](size_t d, size_t s, size_t bytes) {
     if (d != kNone && s != kNone) ops.push_back(CopyOp{base + d, t.mem + s, bytes});
   };
-  for (int l = 0; l <= top; ++l) {
+  for (int l = level0 ? 0 : 1; l <= (level0 ? 0 : top); ++l) {
     const size_t nodes = (size_t)ipow(j.shape.AW, l), n = nodes * N;
     add(L.px[l], S.px[l], 4 * n);
     add(L.py[l], S.py[l], 4 * n);
@@ -657,16 +659,34 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     off = align_up(off + 8, 256);              // work counter (persistent launches)
   }
   // copies of kept subtrees into the memory of the plans that continue them: their
-  // descriptors travel in the metadata block, so that a recorded sequence can be replayed
+  // descriptors travel in the metadata block, so that a recorded sequence can be replayed.
+  // Levels >= 1 of every continued plan first (slices of them run as extra CTAs of the root
+  // preparation launch), then each plan's level 0 (copied by its own root preparation CTA,
+  // which reads it next); a continued plan always has a root preparation CTA.
   std::vector<CopyOp> copies;
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
-    if (j.reuse_src) reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies);
+    if (j.reuse_src) reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies, false);
   }
-  const size_t off_copy = off;
-  off = align_up(off + sizeof(CopyDesc) * copies.size(), 256);
+  const int n_rest = (int)copies.size();
   unsigned long long copy_most = 0;
   for (const CopyOp &op : copies) copy_most = std::max<unsigned long long>(copy_most, op.bytes);
+  std::vector<int> copy0_first(n, 0), copy0_n(n, 0);
+  bool copies_in_root = true;
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    if (!j.reuse_src) continue;
+    copies_in_root = copies_in_root && !fused[i];
+    copy0_first[i] = (int)copies.size();
+    reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies, true);
+    copy0_n[i] = (int)copies.size() - copy0_first[i];
+  }
+  if (!copies_in_root)   // (not reached: a continued plan never fuses its root) one copy launch
+    for (int i = 0; i < n; ++i) copy0_n[i] = 0;
+  unsigned long long copy_most_all = copy_most;
+  for (const CopyOp &op : copies) copy_most_all = std::max<unsigned long long>(copy_most_all, op.bytes);
+  const size_t off_copy = off;
+  off = align_up(off + sizeof(CopyDesc) * copies.size(), 256);
   std::vector<size_t> root_off(n, kNone);
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
@@ -726,6 +746,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     P.lvl_off = j.lvl_off;
     P.reuse_root = j.reuse_root;
     P.root_fused = fused[i];
+    P.copy0_first = copy0_first[i];
+    P.copy0_n = copy0_n[i];
     for (int l = 0; l <= kMaxDepth; ++l)
       P.node_off[l] = (l <= sh.D) ? j.root_idx * ipow(sh.AW, l) : 0ull;
     char *base = j.own_arena ? j.own_arena : arena + j.arena_off;
@@ -824,9 +846,9 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   }
   auto record = [&](cudaStream_t stream) -> int {
     CUDA_TRY(cudaMemcpyAsync(Dm, H, off, cudaMemcpyHostToDevice, stream));
-    if (!copies.empty())   // one launch for every copy, after the descriptors' upload
+    if (!copies.empty() && !copies_in_root)   // one launch for every copy, after the upload
       CUDA_TRY(launch_copy_table(reinterpret_cast<const CopyDesc *>(Dm + off_copy), (int)copies.size(),
-                                 copy_most, stream));
+                                 copy_most_all, stream));
     for (size_t k = 0; k < stages.size(); ++k) {
       StageBuild &sb = stages[k];
       TimedLaunch tl;
@@ -835,7 +857,12 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       if (timed) timed_begin(c, sb.family, tl, sb.family == F_EXPAND ? sb.level : -1);
       cudaError_t e = cudaSuccess;
       switch (sb.family) {
-        case F_ROOT: e = launch_root_prep(dd, sb.st, stream); break;
+        case F_ROOT:
+          e = (copies.empty() || !copies_in_root)
+                  ? launch_root_prep(dd, sb.st, stream)
+                  : launch_root_prep_copy(dd, sb.st, reinterpret_cast<const CopyDesc *>(Dm + off_copy),
+                                          n_rest, copy_most, stream);
+          break;
         case F_EXPAND:
           // a level of long steps with at most one CTA per SM takes wider CTAs (fewer
           // particles per thread on its critical path; measured faster for CROWD only)
@@ -870,6 +897,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   const size_t n_copies = copies.size();
   put(&n_copies, sizeof n_copies);
   put(&copy_most, sizeof copy_most);
+  put(&n_rest, sizeof n_rest);
+  put(&copies_in_root, sizeof copies_in_root);
   put(&n, sizeof n);
   put(&c->leaf_threads, sizeof c->leaf_threads);
   for (size_t k = 0; k < stages.size(); ++k) {

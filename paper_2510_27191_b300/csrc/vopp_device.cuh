@@ -104,6 +104,9 @@ struct PlanDesc {
   unsigned long long node_off[kMaxDepth + 1];
   // the level-0 expansion prepares the root itself (no separate root preparation launch)
   int root_fused;
+  // a plan continuing a kept subtree: its level-0 copies (entries copy0_first ..
+  // copy0_first + copy0_n - 1 of the batch's copy table), made by its root preparation CTA
+  int copy0_first, copy0_n;
   DevResult *result;
 };
 

@@ -116,6 +116,11 @@ struct CopyDesc {
   unsigned long long bytes;
 };
 cudaError_t launch_copy_table(const CopyDesc *table, int n, unsigned long long most, cudaStream_t s);
+// Root preparation with the copies of continued subtrees in the same launch: one CTA per
+// plan of the stage (a continued plan's CTA first makes its own level-0 copies), then CTAs
+// for slices of table entries 0 .. n_rest - 1 (the other levels' copies; `most`: the largest).
+cudaError_t launch_root_prep_copy(const PlanDesc *d, const StageTable &st, const CopyDesc *table,
+                                  int n_rest, unsigned long long most, cudaStream_t s);
 
 }  // namespace vopp
 

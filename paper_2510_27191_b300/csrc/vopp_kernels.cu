@@ -2441,6 +2441,56 @@ __global__ void __launch_bounds__(256) k_copy_table(const CopyDesc *t, int n) {
   if (i < n) copy_slices(t[i].dst, t[i].src, t[i].bytes);
 }
 
+// All of one copy by the whole CTA (a plan's level-0 copies in its root preparation CTA).
+__device__ __forceinline__ void copy_cta(void *dst, const void *src, unsigned long long bytes) {
+  char *d = static_cast<char *>(dst);
+  const char *sp = static_cast<const char *>(src);
+  const bool v16 = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(sp) | bytes) & 15) == 0;
+  if (v16) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(d);
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sp);
+    for (unsigned long long w = threadIdx.x; w < bytes / 16; w += blockDim.x)
+      d4[w] = sp ? s4[w] : make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    uint32_t *d1 = reinterpret_cast<uint32_t *>(d);
+    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(sp);
+    for (unsigned long long w = threadIdx.x; w < bytes / 4; w += blockDim.x) d1[w] = sp ? s1[w] : 0u;
+  }
+}
+
+// Root preparation and the copies of continued subtrees in one launch (see the declaration).
+// The copies of levels >= 1 read only the kept stores and write only levels the root
+// preparation does not touch, so the two kinds of CTA need no order between them.
+__global__ void __launch_bounds__(1024) k_root_prep_copy(const PlanDesc *plans, StageTable st,
+                                                         const CopyDesc *t, int n_rest,
+                                                         unsigned slices) {
+  __shared__ float red[128];
+  pdl_release_next();
+  const unsigned b = blockIdx.x;
+  if (b >= (unsigned)st.n_plans) {   // a slice of one of the other copies
+    const unsigned r = b - (unsigned)st.n_plans, q = r / slices, sl = r - q * slices;
+    if (q >= (unsigned)n_rest) return;
+    const unsigned long long lo = (unsigned long long)sl * kCopySlice;
+    if (lo >= t[q].bytes) return;
+    const unsigned long long n = min(t[q].bytes - lo, kCopySlice);
+    copy_cta(static_cast<char *>(t[q].dst) + lo,
+             t[q].src ? static_cast<const char *>(t[q].src) + lo : nullptr, n);
+    return;
+  }
+  const PlanDesc &P = plans[st.plan[b]];
+  if (P.copy0_n > 0) {   // the root's particles and log weights, before the root reads them
+    for (int q = P.copy0_first; q < P.copy0_first + P.copy0_n; ++q) copy_cta(t[q].dst, t[q].src, t[q].bytes);
+    __syncthreads();
+  }
+  const DevModel &dm = *P.model;
+  switch (P.kind) {
+    case kNav: root_prep_plan<NavModel>(P, dm, red); break;
+    case kGrid: root_prep_plan<GridModel>(P, dm, red); break;
+    case kCrowd: root_prep_plan<CrowdModel>(P, dm, red); break;
+    default: root_prep_plan<ToyModel>(P, dm, red); break;
+  }
+}
+
 static unsigned copy_slice_count(unsigned long long most) {
   return (unsigned)std::min<unsigned long long>(
       65535, std::max<unsigned long long>(1, (most + kCopySlice - 1) / kCopySlice));
@@ -2449,6 +2499,18 @@ static unsigned copy_slice_count(unsigned long long most) {
 cudaError_t launch_copy_table(const CopyDesc *table, int n, unsigned long long most, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_copy_table<<<dim3((unsigned)n, copy_slice_count(most)), 256, 0, s>>>(table, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_prep_copy(const PlanDesc *d, const StageTable &st, const CopyDesc *table,
+                                  int n_rest, unsigned long long most, cudaStream_t s) {
+  // 64 KB slices of every other copy: at most 65,535 of them per copy (as the copy table)
+  const unsigned slices = n_rest > 0 ? (unsigned)std::min<unsigned long long>(
+                                           65535, std::max<unsigned long long>(1, (most + kCopySlice - 1) / kCopySlice))
+                                     : 1u;
+  const unsigned long long grid = (unsigned long long)st.n_plans + (unsigned long long)n_rest * slices;
+  if (grid == 0 || grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  k_root_prep_copy<<<(unsigned)grid, 1024, 0, s>>>(d, st, table, n_rest, slices);
   return cudaGetLastError();
 }
 
