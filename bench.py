@@ -628,7 +628,6 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded root particles; no datasets)",
             "config": _config(spec, args),
-            "launch": "stream launches" if args.no_graphs else "CUDA graph replay",
             "plans_per_s": args.steps * world / (total_ms / 1e3),
             "nodes_per_s": (sum(AW ** l for l in range(spec.D + 1))) * args.steps * world / (total_ms / 1e3),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
