@@ -544,12 +544,22 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     fused[i] = j.shape.mat_top >= 1 && j.first_expand == 0 && !j.reuse_root &&
                expand_fused_smem_bytes(j.shape.kind, j.shape.N) <= kLeafSmemLimit;
   }
+  // A plan continuing a kept subtree with copies on (and no distance-softmax policy, whose
+  // root mean a root preparation computes) needs no root preparation: its root is the kept
+  // subtree's level 0 as it stands (a branch whose particles all have zero weight is never
+  // adopted), its kernels read the stored levels from the subtree itself, and the copies that
+  // make its own tree whole run off its critical path (a copy tail, below).
+  std::vector<char> zc(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const Job &j = jobs[i];
+    zc[i] = j.reuse_src && c->reuse_copy && !(j.shape.pi_mode == kPiNavDist && !j.p.pi_bar);
+  }
   {
     StageBuild s;
     s.family = F_ROOT;
     s.level = 0;
     for (int i = 0; i < n; ++i)
-      if (!fused[i]) { s.prefix.push_back((long long)s.plans.size()); s.plans.push_back(i); }
+      if (!fused[i] && !zc[i]) { s.prefix.push_back((long long)s.plans.size()); s.plans.push_back(i); }
     s.prefix.push_back((long long)s.plans.size());
     s.total = (long long)s.plans.size();
     if (s.total) stages.push_back(s);
@@ -666,7 +676,13 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   std::vector<CopyOp> copies;
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
-    if (j.reuse_src) reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies, false);
+    if (!j.reuse_src) continue;
+    char *base = j.own_arena ? j.own_arena : arena + j.arena_off;
+    if (zc[i]) {   // every level's copies and the root's completion counter, in the tail
+      reuse_copies(c, j, base, copies, true);
+      if (j.shape.D >= 2 && j.lay.cnt[0] != kNone) copies.push_back(CopyOp{base + j.lay.cnt[0], nullptr, 4});
+    }
+    reuse_copies(c, j, base, copies, false);
   }
   const int n_rest = (int)copies.size();
   unsigned long long copy_most = 0;
@@ -675,7 +691,7 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   bool copies_in_root = true;
   for (int i = 0; i < n; ++i) {
     const Job &j = jobs[i];
-    if (!j.reuse_src) continue;
+    if (!j.reuse_src || zc[i]) continue;
     copies_in_root = copies_in_root && !fused[i];
     copy0_first[i] = (int)copies.size();
     reuse_copies(c, j, j.own_arena ? j.own_arena : arena + j.arena_off, copies, true);
@@ -685,6 +701,17 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     for (int i = 0; i < n; ++i) copy0_n[i] = 0;
   unsigned long long copy_most_all = copy_most;
   for (const CopyOp &op : copies) copy_most_all = std::max<unsigned long long>(copy_most_all, op.bytes);
+  // where entries 0 .. n_rest - 1 run: in the root preparation launch when there is one, else
+  // as the copy tail of the first expansion launch (both precede the leaves, whose climb
+  // reads the zeroed counters), else in a copy launch of their own ahead of the leaves
+  const bool has_root = !stages.empty() && stages[0].family == F_ROOT;
+  int tail_stage = -1;
+  if (n_rest > 0 && !has_root)
+    for (size_t k = 0; k < stages.size(); ++k)
+      if (stages[k].family == F_EXPAND) { tail_stage = (int)k; break; }
+  const bool tail_separate = n_rest > 0 && !has_root && tail_stage < 0 && copies_in_root;
+  const unsigned tail_slices = (unsigned)std::min<unsigned long long>(
+      65535, std::max<unsigned long long>(1, (copy_most + (64ull << 10) - 1) / (64ull << 10)));
   const size_t off_copy = off;
   off = align_up(off + sizeof(CopyDesc) * copies.size(), 256);
   std::vector<size_t> root_off(n, kNone);
@@ -766,6 +793,21 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
       P.rbar[l] = fp(L.rbar[l]); P.lom[l] = fp(L.lom[l]); P.V[l] = fp(L.V[l]);
       P.rep[l] = ip(L.rep[l]); P.obs[l] = fp(L.obs[l]);
     }
+    if (zc[i]) {   // the stored levels are read from the kept subtree (copied for the tree later)
+      const KeptTree &t = *j.reuse_src;
+      const PlanLayout &S = t.lay;
+      auto sfp = [&](size_t o, float *own) { return o == kNone ? own : reinterpret_cast<float *>(t.mem + o); };
+      auto sip = [&](size_t o, int *own) { return o == kNone ? own : reinterpret_cast<int *>(t.mem + o); };
+      const int top = reuse_top(c, j);
+      for (int l = 0; l <= top; ++l) {
+        P.px[l] = sfp(S.px[l], P.px[l]); P.py[l] = sfp(S.py[l], P.py[l]);
+        P.plw[l] = sfp(S.plw[l], P.plw[l]); P.ps[l] = sip(S.ps[l], P.ps[l]);
+        P.pf[l] = sfp(S.pf[l], P.pf[l]);
+        if (l == 0) continue;
+        P.rbar[l] = sfp(S.rbar[l], P.rbar[l]); P.lom[l] = sfp(S.lom[l], P.lom[l]);
+        P.obs[l] = sfp(S.obs[l], P.obs[l]); P.rep[l] = sip(S.rep[l], P.rep[l]);
+      }
+    }
     P.result = reinterpret_cast<DevResult *>(Dm + off_res) + i;
     // root input
     if (j.log_weights) {
@@ -840,6 +882,13 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     } else if (sb.family == F_EXPAND) {
       const long long per = sb.vec_width ? kExpandVecChildrenPerCta : 1;
       grids[k] = std::min<long long>((sb.total + per - 1) / per, c->grid_cap);
+      if ((int)k == tail_stage) {   // the copy tail of continued subtrees
+        sb.st.copies = Dm + off_copy;
+        sb.st.n_copies = n_rest;
+        sb.st.copy_slices = tail_slices;
+        sb.st.work_grid = (unsigned)grids[k];
+        grids[k] += (long long)n_rest * tail_slices;
+      }
     } else {
       grids[k] = sb.st.n_plans;
     }
@@ -849,6 +898,9 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
     if (!copies.empty() && !copies_in_root)   // one launch for every copy, after the upload
       CUDA_TRY(launch_copy_table(reinterpret_cast<const CopyDesc *>(Dm + off_copy), (int)copies.size(),
                                  copy_most_all, stream));
+    if (tail_separate)   // continued subtrees' copies with no launch to ride in before the leaves
+      CUDA_TRY(launch_copy_table(reinterpret_cast<const CopyDesc *>(Dm + off_copy), n_rest, copy_most,
+                                 stream));
     for (size_t k = 0; k < stages.size(); ++k) {
       StageBuild &sb = stages[k];
       TimedLaunch tl;
@@ -899,6 +951,8 @@ int enqueue_jobs(vopp_ctx *c, Slot &sl, char *arena, std::vector<Job> &jobs, boo
   put(&copy_most, sizeof copy_most);
   put(&n_rest, sizeof n_rest);
   put(&copies_in_root, sizeof copies_in_root);
+  put(&tail_stage, sizeof tail_stage);
+  put(&tail_separate, sizeof tail_separate);
   put(&n, sizeof n);
   put(&c->leaf_threads, sizeof c->leaf_threads);
   for (size_t k = 0; k < stages.size(); ++k) {
@@ -960,6 +1014,25 @@ int collect_results(vopp_ctx *c, const Slot &sl, const std::vector<Job> &jobs,
   if (remember) {
     c->last_desc.assign(hd, hd + n);
     c->last_ok.assign(n, 1);
+    // a plan that read its stored levels from a kept subtree has them in its own memory too
+    // (the copy tail): the tree record points there, the subtree being released later
+    for (int i = 0; i < n; ++i) {
+      const Job &j = jobs[i];
+      if (!j.reuse_src || !j.own_arena) continue;
+      PlanDesc &D = c->last_desc[i];
+      const PlanLayout &L = j.lay;
+      auto fp = [&](size_t o, float *cur) { return o == kNone ? cur : reinterpret_cast<float *>(j.own_arena + o); };
+      auto ip = [&](size_t o, int *cur) { return o == kNone ? cur : reinterpret_cast<int *>(j.own_arena + o); };
+      const int top = reuse_top(c, j);
+      for (int l = 0; l <= top; ++l) {
+        D.px[l] = fp(L.px[l], D.px[l]); D.py[l] = fp(L.py[l], D.py[l]);
+        D.plw[l] = fp(L.plw[l], D.plw[l]); D.ps[l] = ip(L.ps[l], D.ps[l]);
+        D.pf[l] = fp(L.pf[l], D.pf[l]);
+        if (l == 0) continue;
+        D.rbar[l] = fp(L.rbar[l], D.rbar[l]); D.lom[l] = fp(L.lom[l], D.lom[l]);
+        D.obs[l] = fp(L.obs[l], D.obs[l]); D.rep[l] = ip(L.rep[l], D.rep[l]);
+      }
+    }
   }
   const DevResult *hr = reinterpret_cast<const DevResult *>(sl.hmeta + sl.off_res);
   int first_err = VOPP_OK;
@@ -1168,9 +1241,14 @@ int matching_branch(vopp_agent *g, int action, const float *obs_f, int obs_i, cu
   const KeptTree *t = g->tree;
   if (!t || t->shape.mat_top < 1 || t->lay.obs[1] == kNone) return -1;
   const int W = t->shape.W;
-  std::vector<float> ob(2 * (size_t)W);
+  // the action's branch observations and branch weights (a branch whose particles all have
+  // zero weight, log omega = -inf, is never adopted: its belief would be degenerate)
+  std::vector<float> ob(2 * (size_t)W), lo((size_t)W, 0.0f);
   if (cudaMemcpyAsync(ob.data(), t->mem + t->lay.obs[1] + 8 * (size_t)action * W, 8 * (size_t)W,
                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (t->lay.lom[1] != kNone &&
+       cudaMemcpyAsync(lo.data(), t->mem + t->lay.lom[1] + 4 * (size_t)action * W, 4 * (size_t)W,
+                       cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -1178,7 +1256,7 @@ int matching_branch(vopp_agent *g, int action, const float *obs_f, int obs_i, cu
   for (int k = 0; k < W; ++k) {
     const bool eq = (t->shape.kind == kNav) ? (ob[2 * k] == obs_f[0] && ob[2 * k + 1] == obs_f[1])
                                             : ((int)ob[2 * k] == obs_i);
-    if (eq) return action * W + k;
+    if (eq) return (lo[k] > -INFINITY) ? action * W + k : -1;
   }
   return -1;
 }
@@ -2183,24 +2261,30 @@ int vopp_belief_update_batch(vopp_ctx *c, int32_t n, vopp_agent *const *agents,
   std::vector<BeliefArgs> args(n);
   for (int i = 0; i < n; ++i) args[i] = belief_args(agents[i], actions[i], obs[i], nullptr);
 
-  // subtree reuse: the kept trees' level-1 observations of the agents' actions, one copy
-  // each and one synchronisation for all, then adoptions
+  // subtree reuse: the kept trees' level-1 observations and branch weights of the agents'
+  // actions, one copy each and one synchronisation for all, then adoptions (a branch whose
+  // particles all have zero weight, log omega = -inf, is never adopted)
   std::vector<int> slot(n, -1);
   {
     std::vector<int> asked;
-    std::vector<float> ob;
-    std::vector<size_t> at(n, 0);
+    std::vector<float> ob, lo;
+    std::vector<size_t> at(n, 0), atl(n, 0);
     for (int i = 0; i < n; ++i) {
       const KeptTree *t = agents[i]->reuse ? agents[i]->tree : nullptr;
       if (!t || t->shape.mat_top < 1 || t->lay.obs[1] == kNone) continue;
       at[i] = ob.size();
       ob.resize(ob.size() + 2 * (size_t)t->shape.W);
+      atl[i] = lo.size();
+      lo.resize(lo.size() + (size_t)t->shape.W, 0.0f);
       asked.push_back(i);
     }
     for (int i : asked) {
       const KeptTree *t = agents[i]->tree;
       CUDA_TRY(cudaMemcpyAsync(ob.data() + at[i], t->mem + t->lay.obs[1] + 8 * (size_t)actions[i] * t->shape.W,
                                8 * (size_t)t->shape.W, cudaMemcpyDeviceToHost, s));
+      if (t->lay.lom[1] != kNone)
+        CUDA_TRY(cudaMemcpyAsync(lo.data() + atl[i], t->mem + t->lay.lom[1] + 4 * (size_t)actions[i] * t->shape.W,
+                                 4 * (size_t)t->shape.W, cudaMemcpyDeviceToHost, s));
     }
     if (!asked.empty()) CUDA_TRY(cudaStreamSynchronize(s));
     for (int i : asked) {
@@ -2209,7 +2293,10 @@ int vopp_belief_update_batch(vopp_ctx *c, int32_t n, vopp_agent *const *agents,
         const float *o = ob.data() + at[i] + 2 * k;
         const bool eq = (t->shape.kind == kNav) ? (o[0] == args[i].obs_f[0] && o[1] == args[i].obs_f[1])
                                                 : ((int)o[0] == args[i].obs_i);
-        if (eq) { slot[i] = actions[i] * t->shape.W + k; break; }
+        if (eq) {
+          if (lo[atl[i] + k] > -INFINITY) slot[i] = actions[i] * t->shape.W + k;
+          break;
+        }
       }
     }
     for (int i = 0; i < n; ++i) {

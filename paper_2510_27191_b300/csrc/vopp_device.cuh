@@ -127,6 +127,13 @@ struct StageTable {
   const long long *prefix;    // [n_plans + 1]
   const int *levels;          // [n_plans] per-plan level (overrides `level` when non-null)
   unsigned long long *counter;  // persistent launches: next work item (zero at launch)
+  // A copy tail: blocks >= work_grid of the launch copy 64 KB slices (copy_slices per entry)
+  // of the n_copies entries of a CopyDesc table instead of taking work items (copies == null:
+  // no tail, every block takes work items).
+  const void *copies;
+  int n_copies;
+  unsigned copy_slices;
+  unsigned work_grid;
 };
 
 __device__ __forceinline__ int find_plan(const StageTable &st, long long item) {

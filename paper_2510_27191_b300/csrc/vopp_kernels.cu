@@ -767,6 +767,46 @@ __device__ void climb_warp(const PlanDesc &P, int l, unsigned long long node) {
 // ---------------------------------------------------------------------------------------
 // K1: root preparation (one CTA per plan).
 // ---------------------------------------------------------------------------------------
+// Copies in 64 KB slices.
+constexpr unsigned long long kCopySlice = 64 * 1024;
+
+// All of one copy by the whole CTA (a plan's level-0 copies in its root preparation CTA).
+__device__ __forceinline__ void copy_cta(void *dst, const void *src, unsigned long long bytes) {
+  char *d = static_cast<char *>(dst);
+  const char *sp = static_cast<const char *>(src);
+  const bool v16 = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(sp) | bytes) & 15) == 0;
+  if (v16) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(d);
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sp);
+    for (unsigned long long w = threadIdx.x; w < bytes / 16; w += blockDim.x)
+      d4[w] = sp ? s4[w] : make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    uint32_t *d1 = reinterpret_cast<uint32_t *>(d);
+    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(sp);
+    for (unsigned long long w = threadIdx.x; w < bytes / 4; w += blockDim.x) d1[w] = sp ? s1[w] : 0u;
+  }
+}
+
+// Slice r (in copy-major order, `slices` per copy) of a CopyDesc table, by the whole CTA.
+__device__ __forceinline__ void copy_table_slice(const CopyDesc *t, int n, unsigned slices, unsigned r) {
+  const unsigned q = r / slices, sl = r - q * slices;
+  if (q >= (unsigned)n) return;
+  const unsigned long long lo = (unsigned long long)sl * kCopySlice;
+  if (lo >= t[q].bytes) return;
+  const unsigned long long len = min(t[q].bytes - lo, kCopySlice);
+  copy_cta(static_cast<char *>(t[q].dst) + lo, t[q].src ? static_cast<const char *>(t[q].src) + lo : nullptr, len);
+}
+
+// The work-item grid of a launch with a copy tail; blocks past it run their slice and
+// report true (the caller returns).
+__device__ __forceinline__ bool copy_tail_block(const StageTable &st, unsigned &work_grid) {
+  work_grid = st.copies ? st.work_grid : gridDim.x;
+  if (blockIdx.x < work_grid) return false;
+  copy_table_slice(static_cast<const CopyDesc *>(st.copies), st.n_copies, st.copy_slices,
+                   blockIdx.x - work_grid);
+  return true;
+}
+
 template <class M>
 __device__ void root_prepare(const PlanDesc &P, const DevModel &dm, const GNode<M> &dst, float *red,
                              bool outputs) {
@@ -948,7 +988,9 @@ __global__ void __launch_bounds__(T, (T <= 256) ? 2 : 1) k_expand(const PlanDesc
   __shared__ float red[kRedFloats];
   pdl_release_next();
   pdl_wait_prev();
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+  unsigned wg;
+  if (copy_tail_block(st, wg)) return;
+  for (long long item = blockIdx.x; item < total; item += wg) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
     const int l = st.levels ? st.levels[pi] : st.level;
@@ -1377,9 +1419,11 @@ k_expand_vec(const PlanDesc *plans, StageTable st, long long total) {
   using M = typename ExpandModel<K>::type;
   pdl_release_next();
   pdl_wait_prev();
+  unsigned wg;
+  if (copy_tail_block(st, wg)) return;
   const long long wid = threadIdx.x >> 5;
   for (long long item = (long long)blockIdx.x * kExpandVecWarps + wid; item < total;
-       item += (long long)gridDim.x * kExpandVecWarps) {
+       item += (long long)wg * kExpandVecWarps) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
     const int l = st.levels ? st.levels[pi] : st.level;
@@ -2411,7 +2455,6 @@ cudaError_t leaf_occupancy(int kind, int threads, size_t smem, int *blocks_per_s
 
 // Copy i of the list in slices of kCopySlice bytes, one CTA per (copy, slice): 16-byte words
 // where both ends and the size allow, else 4-byte words.
-constexpr unsigned long long kCopySlice = 64 * 1024;
 // Slice blockIdx.y (and every gridDim.y-th after it) of one copy, by one CTA.
 __device__ __forceinline__ void copy_slices(void *dst, const void *src, unsigned long long bytes) {
   char *d = static_cast<char *>(dst);
@@ -2441,23 +2484,6 @@ __global__ void __launch_bounds__(256) k_copy_table(const CopyDesc *t, int n) {
   if (i < n) copy_slices(t[i].dst, t[i].src, t[i].bytes);
 }
 
-// All of one copy by the whole CTA (a plan's level-0 copies in its root preparation CTA).
-__device__ __forceinline__ void copy_cta(void *dst, const void *src, unsigned long long bytes) {
-  char *d = static_cast<char *>(dst);
-  const char *sp = static_cast<const char *>(src);
-  const bool v16 = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(sp) | bytes) & 15) == 0;
-  if (v16) {
-    uint4 *d4 = reinterpret_cast<uint4 *>(d);
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(sp);
-    for (unsigned long long w = threadIdx.x; w < bytes / 16; w += blockDim.x)
-      d4[w] = sp ? s4[w] : make_uint4(0u, 0u, 0u, 0u);
-  } else {
-    uint32_t *d1 = reinterpret_cast<uint32_t *>(d);
-    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(sp);
-    for (unsigned long long w = threadIdx.x; w < bytes / 4; w += blockDim.x) d1[w] = sp ? s1[w] : 0u;
-  }
-}
-
 // Root preparation and the copies of continued subtrees in one launch (see the declaration).
 // The copies of levels >= 1 read only the kept stores and write only levels the root
 // preparation does not touch, so the two kinds of CTA need no order between them.
@@ -2468,13 +2494,7 @@ __global__ void __launch_bounds__(1024) k_root_prep_copy(const PlanDesc *plans, 
   pdl_release_next();
   const unsigned b = blockIdx.x;
   if (b >= (unsigned)st.n_plans) {   // a slice of one of the other copies
-    const unsigned r = b - (unsigned)st.n_plans, q = r / slices, sl = r - q * slices;
-    if (q >= (unsigned)n_rest) return;
-    const unsigned long long lo = (unsigned long long)sl * kCopySlice;
-    if (lo >= t[q].bytes) return;
-    const unsigned long long n = min(t[q].bytes - lo, kCopySlice);
-    copy_cta(static_cast<char *>(t[q].dst) + lo,
-             t[q].src ? static_cast<const char *>(t[q].src) + lo : nullptr, n);
+    copy_table_slice(t, n_rest, slices, b - (unsigned)st.n_plans);
     return;
   }
   const PlanDesc &P = plans[st.plan[b]];
