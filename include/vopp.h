@@ -397,8 +397,9 @@ VOPP_API int vopp_belief_update_batch(vopp_ctx *ctx, int32_t n, vopp_agent *cons
  *     agent's next plan or belief update;
  *   - vopp_belief_update(a, o) looks for a root branch (a, k) of the kept tree whose sampled
  *     observation equals o exactly (lowest k; discrete observations match, continuous ones
- *     practically never do).  If there is one and the tree's level 1 is materialised (depth
- *     >= 3), that child's particle set and normalised log weights become the belief as the
+ *     practically never do).  If there is one, its branch weight is not zero (log omega >
+ *     -inf) and the tree's level 1 is materialised (depth >= 3), that child's particle set
+ *     and normalised log weights become the belief as the
  *     tree holds them (no propagation, no resampling; *ess_out = -1, *resampled_out = 0, the
  *     time step still advances) and its materialised subtree is kept; otherwise the SIR
  *     update runs and nothing is kept;
@@ -406,8 +407,10 @@ VOPP_API int vopp_belief_update_batch(vopp_ctx *ctx, int32_t n, vopp_agent *cons
  *     and as long as the keys stay in range (key level + depth <= 255, node indices below
  *     2^64): they draw their random numbers as the nodes they are in the kept tree (the
  *     kept tree's seed, not params->seed), take the root as it stands (terminal particles
- *     keep their weight: they add no reward or value), and copy the materialised levels the
- *     subtree already has instead of expanding them (VOPP_FLAG_REUSED, reused_levels).  A
+ *     keep their weight: they add no reward or value), and take the materialised levels the
+ *     subtree already has instead of expanding them (VOPP_FLAG_REUSED, reused_levels): the
+ *     plan's kernels read them where the subtree holds them, and copies into the plan's own
+ *     tree run beside its first expansion.  A
  *     reused plan therefore equals the subtree below the adopted branches of one tree that
  *     is that much deeper, and every reused plan from the same belief is the same plan.
  * Anytime and episode-mode plans of the agent neither keep nor continue trees.
