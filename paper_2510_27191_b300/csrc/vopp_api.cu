@@ -1160,10 +1160,12 @@ void keep_tree(vopp_agent *g, Job &j, bool ok, cudaStream_t s) {
 }
 
 // Adopt child `slot` (= a W + k) of the kept tree's root: its particle set becomes the
-// agent's belief and its materialised subtree (levels 1..mat_top of the tree, the child's
-// nodes, contiguous at every level) is copied into a compact store keyed as it was.
+// agent's belief, and its materialised subtree (levels 1..mat_top of the tree, the child's
+// nodes, contiguous at every level) is kept where it is: the subtree is a view into the
+// tree's memory, which it takes over (level l of the subtree is the child's part of the
+// tree's level l + 1), keyed as it was.  Only the belief is copied.
 int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
-  const KeptTree &t = *g->tree;
+  KeptTree &t = *g->tree;
   const int AW = t.shape.AW;
   const size_t N = (size_t)t.shape.N;
   PlanShape sh = t.shape;
@@ -1174,38 +1176,35 @@ int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
   KeptTree *sb = new (std::nothrow) KeptTree;
   if (!sb) return fail(VOPP_E_NOMEM, "subtree alloc");
   sb->shape = sh;
-  sb->lay = make_layout(sh);
-  sb->bytes = sb->lay.bytes;
   sb->seed = t.seed;
   sb->lvl_off = t.lvl_off + 1;
   sb->root_idx = t.root_idx * (unsigned long long)AW + (unsigned long long)slot;
-  if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&sb->mem), sb->bytes, g->model->ctx->pool, s) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    delete sb;
-    return fail(VOPP_E_NOMEM, "subtree device alloc");
-  }
-  const PlanLayout &S = t.lay, &L = sb->lay;
-  cudaError_t e = cudaSuccess;
-  std::vector<CopyOp> ops;   // issued as one copy-list launch (or a few)
-  auto cp = [&](size_t d, size_t src, size_t elem_off, size_t elem_bytes, size_t bytes) {
-    if (d != kNone && src != kNone)
-      ops.push_back(CopyOp{sb->mem + d, t.mem + src + elem_off * elem_bytes, bytes});
-  };
+  const PlanLayout &S = t.lay;
+  PlanLayout &L = sb->lay;
+  size_t *fields[] = {L.px, L.py, L.plw, L.ps, L.pf, L.Q, L.mu, L.cnt, L.psi};
+  for (size_t *f : fields)
+    for (int l = 0; l < kMaxDepth; ++l) f[l] = kNone;
+  size_t *fields1[] = {L.rbar, L.lom, L.V, L.rep, L.obs};
+  for (size_t *f : fields1)
+    for (int l = 0; l <= kMaxDepth; ++l) f[l] = kNone;
+  L.bytes = t.lay.bytes;
+  auto at = [](size_t base, size_t off) { return base == kNone ? kNone : base + off; };
   for (int l = 0; l <= sh.mat_top; ++l) {
     const size_t nodes = (size_t)ipow(AW, l), first = (size_t)slot * nodes;   // first node there
-    cp(L.px[l], S.px[l + 1], first * N, 4, 4 * nodes * N);
-    cp(L.py[l], S.py[l + 1], first * N, 4, 4 * nodes * N);
-    cp(L.ps[l], S.ps[l + 1], first * N, 4, 4 * nodes * N);
-    cp(L.pf[l], S.pf[l + 1], first * N, 48, 48 * nodes * N);
-    cp(L.plw[l], S.plw[l + 1], first * N, 4, 4 * nodes * N);
+    L.px[l] = at(S.px[l + 1], 4 * first * N);
+    L.py[l] = at(S.py[l + 1], 4 * first * N);
+    L.ps[l] = at(S.ps[l + 1], 4 * first * N);
+    L.pf[l] = at(S.pf[l + 1], 48 * first * N);
+    L.plw[l] = at(S.plw[l + 1], 4 * first * N);
     if (l == 0) continue;
-    cp(L.rbar[l], S.rbar[l + 1], first, 4, 4 * nodes);
-    cp(L.lom[l], S.lom[l + 1], first, 4, 4 * nodes);
-    cp(L.obs[l], S.obs[l + 1], first, 8, 8 * nodes);
-    cp(L.mu[l], S.mu[l + 1], first, 8, 8 * nodes);
+    L.rbar[l] = at(S.rbar[l + 1], 4 * first);
+    L.lom[l] = at(S.lom[l + 1], 4 * first);
+    L.obs[l] = at(S.obs[l + 1], 8 * first);
+    L.mu[l] = at(S.mu[l + 1], 8 * first);
   }
   // the agent's belief: the adopted node's particles in the agent's row layout
+  cudaError_t e = cudaSuccess;
+  std::vector<CopyOp> ops;
   auto cpa = [&](void *d, size_t src, size_t elem_bytes, size_t rows) {
     if (src != kNone) ops.push_back(CopyOp{d, t.mem + src + (size_t)slot * N * elem_bytes, rows * 4 * N});
   };
@@ -1226,11 +1225,13 @@ int adopt_subtree(vopp_agent *g, int slot, cudaStream_t s) {
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFreeAsync(sb->mem, s);
     delete sb;
-    return fail(VOPP_E_CUDA, "subtree copy: %s", cudaGetErrorString(e));
+    return fail(VOPP_E_CUDA, "belief copy: %s", cudaGetErrorString(e));
   }
-  free_kept(g->sub, s);
+  sb->mem = t.mem;        // the subtree takes the tree's memory over
+  sb->bytes = t.bytes;
+  t.mem = nullptr;
+  release_kept(g, g->sub, s);
   g->sub = sb;
   return VOPP_OK;
 }
@@ -2180,7 +2181,7 @@ BeliefArgs belief_args(vopp_agent *g, int32_t action, const void *obs, BeliefOut
 // Subtree reuse at a belief update: adopt the matching branch of the kept tree (slot >= 0,
 // its subtree kept) or release what the agent kept (slot < 0: the SIR update follows).
 int reuse_update(vopp_agent *g, int slot, cudaStream_t s) {
-  free_kept(g->sub, s);
+  release_kept(g, g->sub, s);
   g->adopted_slot = -1;
   if (slot < 0) {
     release_kept(g, g->tree, s);
