@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 N, W, ETA, GAMMA, SEED = 256, 3, 1.0, 0.95, 5
 SENSE_A1, SENSE_A2 = 6, 9          # sense actions: their branches sample "good" / "bad"
+MIXED_SEED = 4321
 
 
 def _grid():
@@ -48,16 +49,23 @@ def _run_chain(V, ctx, model, s, obs_fn, **kw):
     agent = V.vopp_agent_create(model, s, None, N, 77)
     V.vopp_agent_set_reuse(agent, True)
     served = kw.get("served", False)
+    mixed = kw.get("mixed", False)   # each served plan batched with a depth-2 plan from s
     srv = V.vopp_server_create(ctx, 8, 2) if served else None
     depths = kw.get("depths", (4, 3, 3))
 
     def plan(d, seed):
         if not served:
             return V.vopp_agent_plan(agent, model, d, W, ETA, GAMMA, seed)
+        if mixed:
+            V.vopp_server_set_paused(srv, True)
         t = V.vopp_submit_agent(srv, agent, d, W, ETA, GAMMA, seed)
+        if mixed:
+            t2 = V.vopp_submit(srv, model, s, None, N, 2, W, ETA, GAMMA, MIXED_SEED)
+            V.vopp_server_set_paused(srv, False)
+            out["extra"].append(V.vopp_wait(srv, t2, 13, 30.0)[0])
         return V.vopp_wait(srv, t, 13, 30.0)[0]
 
-    out = dict(res=[], particles=[], info=[], slots=[], trees=[])
+    out = dict(res=[], particles=[], info=[], slots=[], trees=[], extra=[])
     try:
         out["res"].append(plan(depths[0], SEED))
         for step, a in enumerate((SENSE_A1, SENSE_A2)):
@@ -116,13 +124,17 @@ def grid_chain():
         recompute = _run_chain(V, ctx, model, s, obs_fn_chain)
         V.vopp_ctx_set_option(ctx, V.VOPP_OPT_REUSE_COPY, 1)
         served = _run_chain(V, ctx, model, s, obs_fn_chain, served=True)
+        # the same chain with a plan that needs a root preparation in every batch (the
+        # continued plans' copies then run in that launch)
+        mixed = _run_chain(V, ctx, model, s, obs_fn_chain, served=True, mixed=True)
+        mixed_ref = V.vopp_plan(model, s, None, N, 2, W, ETA, GAMMA, None, MIXED_SEED)
         V.vopp_model_destroy(model)
     finally:
         V.vopp_ctx_destroy(ctx)
     path2 = [picks[0][1], picks[1][1]]
     o3 = O.plan(om, N, 2 + 3, W, ETA, GAMMA, SEED, root_s=s, path=path2, dump_levels=2)
-    return dict(copy=copy, recompute=recompute, served=served, oracle=[o_plans[0], o3],
-                picks=picks)
+    return dict(copy=copy, recompute=recompute, served=served, mixed=mixed, mixed_ref=mixed_ref,
+                oracle=[o_plans[0], o3], picks=picks)
 
 
 def test_adoption_takes_the_matching_branch_and_its_particles(grid_chain):
@@ -179,6 +191,21 @@ def test_served_reused_plans_equal_synchronous(grid_chain):
         assert ra["v_root"] == rb["v_root"] and ra["action"] == rb["action"]
         assert ra["flags"] == rb["flags"] and ra["reused_levels"] == rb["reused_levels"]
     assert [i["adopted_slot"] for i in a["info"]] == [i["adopted_slot"] for i in b["info"]]
+
+
+def test_reused_plans_batched_with_a_root_preparation(grid_chain):
+    """Continued plans batched with a plan that needs a root preparation (their copies then
+    ride in the root preparation launch) equal the synchronous chain bit for bit, and so does
+    the other plan its plain run."""
+    a, b = grid_chain["copy"], grid_chain["mixed"]
+    for ra, rb in zip(a["res"], b["res"]):
+        np.testing.assert_array_equal(ra["q"], rb["q"])
+        assert ra["v_root"] == rb["v_root"] and ra["action"] == rb["action"]
+        assert ra["flags"] == rb["flags"] and ra["reused_levels"] == rb["reused_levels"]
+    assert len(b["extra"]) == 3
+    for r in b["extra"]:
+        np.testing.assert_array_equal(r["q"], grid_chain["mixed_ref"]["q"])
+        assert r["v_root"] == grid_chain["mixed_ref"]["v_root"]
 
 
 def test_unmatched_observation_falls_back_to_the_sir_update():
