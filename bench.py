@@ -65,6 +65,7 @@ WORKLOADS = {
 ALG_INSTR_PER_STEP = {WL.NAV2D: 83.0, WL.GRID: 18.5, WL.TOY2: 16.0, WL.CROWD: 525.0}
 SMS = 148
 LANES_PER_CLK = 128
+DATA = "synthetic (seeded root particles; no datasets)"   # both arms' lines
 
 
 def kernel_source_hash():
@@ -241,7 +242,7 @@ def run_reference(args, spec, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": _config(spec, args),
+           "data": DATA, "config": _config(spec, args),
            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": threads,
                             "sample": f"{threads} level-1 subtrees per step, one per thread "
                                       f"({steps_per_subtree} particle-steps each, 1/{AW} of "
@@ -626,7 +627,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded root particles; no datasets)",
+            "data": DATA,
             "config": _config(spec, args),
             "plans_per_s": args.steps * world / (total_ms / 1e3),
             "nodes_per_s": (sum(AW ** l for l in range(spec.D + 1))) * args.steps * world / (total_ms / 1e3),
