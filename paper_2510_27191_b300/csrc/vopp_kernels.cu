@@ -1467,7 +1467,7 @@ constexpr int kLeafChunkLin = VOPP_LEAF_CHUNK_LIN;   // pairs per compensated ad
 #endif
 constexpr int kSelfChunk = VOPP_SELF_CHUNK;          // particles per compensated add, CROWD
 #ifndef VOPP_GRID_CHUNK
-#define VOPP_GRID_CHUNK 1
+#define VOPP_GRID_CHUNK 4
 #endif
 constexpr int kGridChunk = VOPP_GRID_CHUNK;          // pairs per compensated add, GRID loops
 #ifndef VOPP_LOG_COLD_GRID
@@ -1726,8 +1726,9 @@ struct Kahan2 {
   }
 };
 
-// Every whole pair through `one` (chunks of kGridChunk pairs per lane between compensated
-// adds), then the last particle of an odd N (no pad particle is stepped).  kR: a move or
+// Every whole pair through `one`: when the pairs make whole chunks of kGridChunk pairs per
+// lane, a chunk between compensated adds with no bounds test; otherwise one pair per
+// compensated add; then the last particle of an odd N (no pad particle is stepped).  kR: a move or
 // collect branch -- its reading is NULL, so Z = 1 for every particle and S0 = N exactly (not
 // summed), and its rewards are summed; a sense branch earns nothing.  The compensated sums
 // run two at a time: (S0, S1) for sense, (S1, H) for move and collect.
@@ -1747,19 +1748,28 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
       H.add(t.h1);
     }
   };
-  for (int base = lane; base < nfull; base += 32 * kCh) {
-    GridSums t{0.f, 0.f, 0.f, 0.f};
+  if (nfull % (32 * kCh) == 0) {   // whole chunks only
+    for (int base = lane; base < nfull; base += 32 * kCh) {
+      GridSums t{0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < kCh; ++c) {
-      const int p = base + 32 * c;
-      if (p < nfull) {
+      for (int c = 0; c < kCh; ++c) {
+        const int p = base + 32 * c;
         const int2 st = nb.A[p];
         const float2 b = reinterpret_cast<const float2 *>(nb.B + p)[1];   // (w_0, w_1)
         one(st.x, b.x, t);
         one(st.y, b.y, t);
       }
+      fold(t);
     }
-    fold(t);
+  } else {   // a pair at a time
+    for (int p = lane; p < nfull; p += 32) {
+      GridSums t{0.f, 0.f, 0.f, 0.f};
+      const int2 st = nb.A[p];
+      const float2 b = reinterpret_cast<const float2 *>(nb.B + p)[1];
+      one(st.x, b.x, t);
+      one(st.y, b.y, t);
+      fold(t);
+    }
   }
   if ((N & 1) && lane == 0) {
     GridSums t{0.f, 0.f, 0.f, 0.f};
