@@ -373,6 +373,10 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
   Kahan R, S1, S0, MX, MY;
   R.init(); S1.init(); S0.init(); MX.init(); MY.init();
   float m1 = -CUDART_INF_F, m0 = -CUDART_INF_F;
+  // GRID: whole chunks of kBC pairs per thread, when npairs allows, with no bounds test
+  // (depth-4 grid leaf 4.35 -> 4.28 ms; the navigation leaf is slower that way)
+  auto pass1 = [&](auto full_tag) {
+    constexpr bool kFull = decltype(full_tag)::value;
   for (int base = threadIdx.x; base < npairs; base += blockDim.x * kBC) {
     float Lc[2 * kBC], Ec[2 * kBC], Xc[2 * kBC], Yc[2 * kBC];
     float cm1 = -CUDART_INF_F, cm0 = -CUDART_INF_F, rp = 0.f;
@@ -381,7 +385,7 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       const int p = base + c * blockDim.x;
       Lc[2 * c] = Lc[2 * c + 1] = Ec[2 * c] = Ec[2 * c + 1] = -CUDART_INF_F;
       Xc[2 * c] = Xc[2 * c + 1] = Yc[2 * c] = Yc[2 * c + 1] = 0.f;
-      if (p < npairs) {
+      if (kFull || p < npairs) {
         const int i0 = 2 * p, i1 = 2 * p + 1;
         const bool v1 = i1 < N;
         const uint4 w = M::kStochastic
@@ -456,6 +460,9 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
     S1.add(a1); S0.add(a0); R.add(rp);
     if (want_mu) { MX.add(ax); MY.add(ay); }
   }
+  };
+  if (std::is_same<M, GridModel>::value && npairs % (blockDim.x * kBC) == 0) pass1(std::true_type{});
+  else pass1(std::false_type{});
   // block-wide merge: each warp merges its lanes' shifted sums at the warp's largest shift,
   // then every warp merges the warps' partial sums the same way (identically in every warp)
   float v[5];
