@@ -1450,7 +1450,9 @@ k_expand_vec(const PlanDesc *plans, StageTable st, long long total) {
 //   VOPP_SELF_CHUNK      particles per lane between two compensated adds, CROWD
 //   VOPP_LOG_COLD_NAV / VOPP_LOG_COLD_GRID  1: the log-domain fallback is an out-of-line call
 //   VOPP_LEAF_NAV_MAXREG registers per thread of the NAV2D leaf kernel (72: seven 128-thread
-//                        CTAs per SM); VOPP_LEAF_GRID_MAXREG: GRID and TOY2 (64);
+//                        CTAs per SM); VOPP_LEAF_GRID_MAXREG: GRID (72: its shared memory
+//                        allows seven CTAs per SM, which 72 registers still fit; 64 spilled,
+//                        4.28 against 4.19 ms on the depth-4 grid plan); VOPP_LEAF_TOY_MAXREG: TOY2 (64);
 //                        VOPP_LEAF_CROWD_MINBLOCKS: resident 160-thread CROWD CTAs per SM (3)
 #ifndef VOPP_LEAF_CHUNK
 #define VOPP_LEAF_CHUNK 4
@@ -1459,7 +1461,10 @@ k_expand_vec(const PlanDesc *plans, StageTable st, long long total) {
 #define VOPP_LEAF_NAV_MAXREG 72
 #endif
 #ifndef VOPP_LEAF_GRID_MAXREG
-#define VOPP_LEAF_GRID_MAXREG 64
+#define VOPP_LEAF_GRID_MAXREG 72
+#endif
+#ifndef VOPP_LEAF_TOY_MAXREG
+#define VOPP_LEAF_TOY_MAXREG 64
 #endif
 #ifndef VOPP_LEAF_CROWD_MINBLOCKS
 #define VOPP_LEAF_CROWD_MINBLOCKS 3
@@ -2129,7 +2134,7 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
 template <int K> struct LeafModel;
 template <> struct LeafModel<kNav> { using type = NavModel; static constexpr int kMaxReg = VOPP_LEAF_NAV_MAXREG; };
 template <> struct LeafModel<kGrid> { using type = GridModel; static constexpr int kMaxReg = VOPP_LEAF_GRID_MAXREG; };
-template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMaxReg = VOPP_LEAF_GRID_MAXREG; };
+template <> struct LeafModel<kToy> { using type = ToyModel; static constexpr int kMaxReg = VOPP_LEAF_TOY_MAXREG; };
 template <> struct LeafModel<kCrowd> { using type = CrowdModel; };
 
 template <int K>
