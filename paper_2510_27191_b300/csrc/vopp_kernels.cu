@@ -143,6 +143,7 @@ template <> struct SNode<NavModel> {
   __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
   __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
   __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+  __device__ __forceinline__ float4 pairB(int p) const { return B[p]; }   // (lw0, lw1, w0, w1)
 };
 
 template <class M> struct SNodeInt {
@@ -168,10 +169,55 @@ template <class M> struct SNodeInt {
   __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
   __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
   __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+  __device__ __forceinline__ float4 pairB(int p) const { return B[p]; }   // (lw0, lw1, w0, w1)
 };
-template <> struct SNode<GridModel> : SNodeInt<GridModel> {
-  __device__ static SNode at(float *base, int np) {
-    SNode r; static_cast<SNodeInt<GridModel> &>(r) = SNodeInt<GridModel>::at(base, np); return r;
+// GRID leaf node: {s0, s1} and {w0, w1} (linear weights) per pair, 16 B, and no stored log
+// weights: the rare log-domain path recomputes a particle's base-2 log weight as the node
+// build made it, from the per-node values in s_grid_lw -- which leaves shared memory for the
+// sense table by (rock, cell).
+struct GridLwCtx {
+  const float *par_lw;    // leaf_gen: the parent's natural log weights (its level store)
+  const float *node_lw;   // otherwise: the node's own natural log weights (its level store)
+  const DevModel *dm;
+  float lse2;             // the node build's base-2 normaliser
+  int a, o, N, gen;       // the node's action and observation, N, leaf_gen
+};
+__shared__ GridLwCtx s_grid_lw;
+template <> struct SNode<GridModel> {
+  int2 *A;
+  float2 *W2;
+  static constexpr int kPairBytes = 16;
+  __device__ static SNode at(float *base, int npairs) {
+    float2 *w = reinterpret_cast<float2 *>(base);
+    return SNode{reinterpret_cast<int2 *>(w + npairs), w};
+  }
+  __device__ __forceinline__ GridModel::S get(int i) const {
+    return GridModel::S{reinterpret_cast<const int *>(A + (i >> 1))[i & 1]};
+  }
+  __device__ __forceinline__ void put(int i, const GridModel::S &v) const {
+    reinterpret_cast<int *>(A + (i >> 1))[i & 1] = v.s;
+  }
+  __device__ __forceinline__ void get_pair(int p, GridModel::S &s0, GridModel::S &s1) const {
+    const int2 a = A[p];
+    s0 = GridModel::S{a.x};
+    s1 = GridModel::S{a.y};
+  }
+  __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(W2 + (i >> 1))[i & 1]; }
+  __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(W2 + (i >> 1))[i & 1] = v; }
+  __device__ __forceinline__ void set_lw(int, float) const {}   // not stored (see lw)
+  // the node build's value, bit for bit: (lw_parent log2 e + log2 Z) - lse2 with leaf_gen
+  // (node_build, pass 3), lw log2 e from a materialised level otherwise; -inf past N
+  __device__ __forceinline__ float lw(int i) const {
+    const GridLwCtx &c = s_grid_lw;
+    if (i >= c.N) return -CUDART_INF_F;
+    if (!c.gen) return kLog2e * c.node_lw[i];
+    if (!(c.lse2 > -CUDART_INF_F)) return -CUDART_INF_F;
+    const float e = GridModel::loglik2(get(i), c.a, GridModel::O{c.o}, *c.dm);
+    return fmaf(c.par_lw[i], kLog2e, e) - c.lse2;
+  }
+  __device__ __forceinline__ float4 pairB(int p) const {
+    const float2 w2 = W2[p];
+    return make_float4(lw(2 * p), lw(2 * p + 1), w2.x, w2.y);
   }
 };
 template <> struct SNode<ToyModel> : SNodeInt<ToyModel> {
@@ -215,6 +261,7 @@ template <> struct SNode<CrowdModel> {
   __device__ __forceinline__ void set_lw(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[i & 1] = v; }
   __device__ __forceinline__ float w(int i) const { return reinterpret_cast<const float *>(B + (i >> 1))[2 + (i & 1)]; }
   __device__ __forceinline__ void set_w(int i, float v) const { reinterpret_cast<float *>(B + (i >> 1))[2 + (i & 1)] = v; }
+  __device__ __forceinline__ float4 pairB(int p) const { return B[p]; }   // (lw0, lw1, w0, w1)
 };
 
 // Scratch for the two per-particle values a child build keeps between its passes.
@@ -229,6 +276,13 @@ template <class M> struct ScratchInNode {   // K3: the destination node's lw / w
   SNode<M> n;
   __device__ __forceinline__ float getL(int i) const { return n.lw(i); }
   __device__ __forceinline__ void setL(int i, float v) const { n.set_lw(i, v); }
+  __device__ __forceinline__ float getE(int i) const { return n.w(i); }
+  __device__ __forceinline__ void setE(int i, float v) const { n.set_w(i, v); }
+};
+template <> struct ScratchInNode<GridModel> {   // L in the linear-weight slot, then w there
+  SNode<GridModel> n;
+  __device__ __forceinline__ float getL(int i) const { return n.w(i); }
+  __device__ __forceinline__ void setL(int i, float v) const { n.set_w(i, v); }
   __device__ __forceinline__ float getE(int i) const { return n.w(i); }
   __device__ __forceinline__ void setE(int i, float v) const { n.set_w(i, v); }
 };
@@ -354,7 +408,8 @@ template <class M, class Src, class Dst, class Scr>
 __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
                             unsigned long long child, const Src &src, const Dst &dst,
                             const Scr &sc, float *red, bool dst_has_w, bool dst_log2,
-                            float2 *mu_out) {
+                            float2 *mu_out, typename M::O *o_out = nullptr,
+                            float *lse2_out = nullptr) {
   const int N = P.N, AW = P.AW, W = P.W, npairs = (N + 1) >> 1;
   constexpr int kBC = BuildChunk<M>::value;
   const unsigned long long parent = child / (unsigned long long)AW;
@@ -524,6 +579,8 @@ __device__ void build_child(const PlanDesc &P, const DevModel &dm, int l,
       P.mu[cl][2 * child + 1] = mu.y;
     }
     if (mu_out) *mu_out = mu;
+    if (o_out) *o_out = o;
+    if (lse2_out) *lse2_out = lse2;
     if (P.rep[cl]) P.rep[cl][child] = j;
     if (P.obs[cl]) {   // full detail, or the level-1 observations a kept tree needs
       const float2 of = M::obs_f2(o);
@@ -1517,16 +1574,12 @@ struct ShiftedSum {
 // over log2 Z (the proposal normaliser of omega), rescaled once per chunk of pairs.
 // GRID: the leaf heuristic per column x (it depends on x alone), filled by each leaf CTA
 // with the same arithmetic as GridModel::heuristic.
-// The disagreeing half of the Z table starts kGridZStride floats after the agreeing one: an
-// odd offset puts the two readings of one d^2 (a warp's usual pair of addresses) in different
-// shared-memory banks.  Squared agent-rock distances run 0..221.
-constexpr int kGridZStride = 223;
-// GRID leaf tables by cell c = x + 16 y (x <= 11, y <= 10, so c < 172): squared distance to
-// each rock (bytes), heuristic (0 at the exited column x = 11) and the rock on the cell (-1 if
-// none).  Kept small so that seven 128-thread leaf CTAs fit an SM's shared memory.
+// GRID leaf tables by cell c = x + 16 y (x <= 11, y <= 10, so c < 172): Z of a sense of each
+// rock (agreeing, disagreeing reading) at the cell's squared distance to it, heuristic (0 at
+// the exited column x = 11) and the rock on the cell (-1 if none).  Small enough, with the
+// 16-byte node pairs, for seven 128-thread leaf CTAs per SM.
 constexpr int kGridCells = 172;
-__shared__ float s_grid_z[2 * kGridZStride];   // GRID leaf: Z by (disagree, d^2), from the model
-__shared__ unsigned char s_grid_d2[8 * kGridCells];
+__shared__ float2 s_grid_zc[8 * kGridCells];
 __shared__ float s_grid_hc[kGridCells];
 __shared__ signed char s_grid_rockc[kGridCells];
 // (s >> 8) & 0xFF as one byte permute (byte 1 of s, zero bytes above it) instead of a shift
@@ -1632,7 +1685,7 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
         }
         typename M::S s0, s1;
         nb.get_pair(p, s0, s1);
-        const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+        const float4 b = nb.pairB(p);      // (lw2_0, lw2_1, w_0, w_1)
         const DrawCtx dc{P.key0, P.key1, kPurposeTransition, c1, kn};
         const float r0 = step_particle<M>(s0, a, w, 2 * p, dc, dm);
         const float r1 = step_particle<M>(s1, a, w, 2 * p + 1, dc, dm);
@@ -1690,7 +1743,7 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
 // same states and rewards as GridModel::step, which the other kernels use.  A move's or
 // collect's reading is NULL (Z = 1) and a sense reading good or bad; any other reading has
 // Z = 0 everywhere and is left to the log-domain path (false returned).
-struct GridSense { int rk, flip; const unsigned char *d2; };
+struct GridSense { int rk, flip; const float2 *zc; };
 struct GridMove { int shift, lo, span, delta, at_lim; float r_lim; };
 struct GridSums { float s0, s1, h1, rs; };
 
@@ -1698,7 +1751,8 @@ struct GridSums { float s0, s1, h1, rs; };
 __device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense &g, GridSums &t) {
   const int c = gcell(sv);
   const int miss = ((sv >> g.rk) & 1) ^ g.flip;
-  const float z = s_grid_z[miss * kGridZStride + g.d2[c]];
+  const float2 zz = g.zc[c];
+  const float z = miss ? zz.y : zz.x;
   const float wz = w * z;
   t.s0 += z;
   t.s1 += wz;
@@ -1767,7 +1821,7 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
       for (int c = 0; c < kCh; ++c) {
         const int p = base + 32 * c;
         const int2 st = nb.A[p];
-        const float2 b = reinterpret_cast<const float2 *>(nb.B + p)[1];   // (w_0, w_1)
+        const float2 b = nb.W2[p];                 // (w_0, w_1)
         one(st.x, b.x, t);
         one(st.y, b.y, t);
       }
@@ -1777,7 +1831,7 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
     for (int p = lane; p < nfull; p += 32) {
       GridSums t{0.f, 0.f, 0.f, 0.f};
       const int2 st = nb.A[p];
-      const float2 b = reinterpret_cast<const float2 *>(nb.B + p)[1];
+      const float2 b = nb.W2[p];
       one(st.x, b.x, t);
       one(st.y, b.y, t);
       fold(t);
@@ -1785,7 +1839,7 @@ __device__ __forceinline__ void grid_pairs(const SNode<GridModel> &nb, int N, F 
   }
   if ((N & 1) && lane == 0) {
     GridSums t{0.f, 0.f, 0.f, 0.f};
-    one(nb.A[nfull].x, nb.B[nfull].z, t);
+    one(nb.A[nfull].x, nb.W2[nfull].x, t);
     fold(t);
   }
   if (kR) {
@@ -1807,7 +1861,7 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
   if (a >= 5) {
     if (o.o != 1 && o.o != 2) return false;
     const int rk = a - 5;
-    const GridSense g{rk, (o.o == 1) ? 1 : 0, s_grid_d2 + rk * kGridCells};
+    const GridSense g{rk, (o.o == 1) ? 1 : 0, s_grid_zc + rk * kGridCells};
     grid_pairs<false>(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
                       S0, S1, H, R);    // R stays 0: a sense action earns nothing
     return true;
@@ -1917,10 +1971,8 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
       nav_lin_loop<true>(nb, N, a, c1, c2, c3, o_nav(o), log2g, h_a0, h_b0, hz, S0, S1, H, R);
     else
       nav_lin_loop<false>(nb, N, a, c1, c2, c3, o_nav(o), log2g, h_a0, h_b0, hz, S0, S1, H, R);
-  } else if (std::is_same<M, GridModel>::value) {
-    if constexpr (std::is_same<M, GridModel>::value) {
-      if (!grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R)) return false;
-    }
+  } else if constexpr (std::is_same<M, GridModel>::value) {
+    if (!grid_branch_sums(P, dm, nb, a, o, S0, S1, H, R)) return false;
   } else if (SelfDraw<M>::value) {
     // a self-drawing step is long and needs no pair words: one particle per loop body (the
     // instruction cache), kSelfChunk particles per lane between compensated adds
@@ -1959,7 +2011,7 @@ __device__ __forceinline__ bool leaf_sums_lin(const PlanDesc &P, const DevModel 
           if (M::kStochastic) w = philox(make_uint4(c1, (uint32_t)p, c2, c3), key0, key1);
           typename M::S x0, x1;
           nb.get_pair(p, x0, x1);
-          const float4 b = nb.B[p];          // (lw2_0, lw2_1, w_0, w_1)
+          const float4 b = nb.pairB(p);      // (lw2_0, lw2_1, w_0, w_1)
           const DrawCtx dc{key0, key1, kPurposeTransition, c1, kn};
           const float r0 = step_particle<M>(x0, a, w, 2 * p, dc, dm);
           const float r1 = step_particle<M>(x1, a, w, 2 * p + 1, dc, dm);
@@ -2037,16 +2089,13 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
     // the Z table and the tables by cell; x = 11 (exited) is the terminal column, its
     // heuristic 0 like a forced-zero one (a terminal state with x <= 10 exists only at the
     // root, with weight 0); the tables are read after the node build's barriers
-    for (int i = threadIdx.x; i < 2 * kGridZStride; i += blockDim.x) {
-      const int half = i / kGridZStride, d2 = i - half * kGridZStride;
-      s_grid_z[i] = (d2 < kGridD2) ? dm.pz[half * kGridD2 + d2] : 0.f;
-    }
     for (int c = threadIdx.x; c < kGridCells; c += blockDim.x) {
       const int x = c & 15, y = c >> 4;
       const bool cell_ok = x <= 11 && y <= 10;
       for (int r = 0; r < 8; ++r) {
         const int dx = x - dm.rock_x[r], dy = y - dm.rock_y[r];
-        s_grid_d2[r * kGridCells + c] = cell_ok ? (unsigned char)(dx * dx + dy * dy) : 0;
+        const int d2 = cell_ok ? dx * dx + dy * dy : 0;
+        s_grid_zc[r * kGridCells + c] = make_float2(dm.pz[d2], dm.pz[kGridD2 + d2]);
       }
       s_grid_rockc[c] = (signed char)((x <= 10 && y <= 10) ? dm.rock_at[x + 11 * y] : -1);
       const GridModel::S col{gpack(0, x <= 10 ? x : 0, 0, 0)};
@@ -2059,10 +2108,23 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
     const unsigned long long parent = node / (unsigned long long)AW;
     const GNode<M> src = GNode<M>::at(P, l - 1, (long long)parent);
     float2 mu;
-    build_child<M>(P, dm, l - 1, node, src, nb, ScratchInNode<M>{nb}, red, true, true, &mu);
-    if (threadIdx.x == 0) s_mu = mu;
+    typename M::O o;
+    float lse2;
+    build_child<M>(P, dm, l - 1, node, src, nb, ScratchInNode<M>{nb}, red, true, true, &mu, &o,
+                   &lse2);
+    if (threadIdx.x == 0) {
+      s_mu = mu;
+      if constexpr (std::is_same<M, GridModel>::value) {
+        const int slot = (int)(node - parent * (unsigned long long)AW);
+        s_grid_lw = GridLwCtx{src.lwp, nullptr, &dm, lse2, slot / P.W, o.o, N, 1};
+      }
+    }
   } else {
     const GNode<M> src = GNode<M>::at(P, l, (long long)node);
+    if constexpr (std::is_same<M, GridModel>::value) {
+      if (threadIdx.x == 0)
+        s_grid_lw = GridLwCtx{nullptr, src.lwp, &dm, -CUDART_INF_F, 0, 0, N, 0};
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       nb.put(i, src.get(i));
       const float lw = src.lw(i);
@@ -2371,7 +2433,8 @@ __global__ void k_env(EnvArgs E) {
 // ---------------------------------------------------------------------------------------
 size_t leaf_smem_bytes(int kind, int N, int AW) {
   const size_t pair = (kind == kNav) ? SNode<NavModel>::kPairBytes
-                                     : (kind == kCrowd ? SNode<CrowdModel>::kPairBytes : 24);
+                                     : kind == kCrowd ? SNode<CrowdModel>::kPairBytes
+                                     : kind == kGrid ? SNode<GridModel>::kPairBytes : 24;
   // node pairs; per branch: r̄, log ω, V, and the sampled observation (2 floats) with its
   // representative
   return pair * (size_t)((N + 1) / 2) + 6 * sizeof(float) * (size_t)AW + 64;
