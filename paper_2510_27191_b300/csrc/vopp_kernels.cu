@@ -2078,7 +2078,8 @@ __device__ void leaf_child_warp(const PlanDesc &P, const DevModel &dm, const SNo
 }
 
 template <class M>
-__device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *smem, float *red) {
+__device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *smem, float *red,
+                          bool fill_tables) {
   const DevModel &dm = *P.model;
   const int N = P.N, AW = P.AW, l = P.D - 1, npairs = (N + 1) >> 1;
   const SNode<M> nb = SNode<M>::at(smem, npairs);
@@ -2088,7 +2089,9 @@ __device__ void leaf_item(const PlanDesc &P, unsigned long long node, float *sme
   if constexpr (std::is_same<M, GridModel>::value) {
     // the Z table and the tables by cell; x = 11 (exited) is the terminal column, its
     // heuristic 0 like a forced-zero one (a terminal state with x <= 10 exists only at the
-    // root, with weight 0); the tables are read after the node build's barriers
+    // root, with weight 0); the tables are read after the node build's barriers, and kept
+    // from one work item to the next of the same plan
+    if (fill_tables)
     for (int c = threadIdx.x; c < kGridCells; c += blockDim.x) {
       const int x = c & 15, y = c >> 4;
       const bool cell_ok = x <= 11 && y <= 10;
@@ -2214,13 +2217,18 @@ __device__ __forceinline__ void leaf_kernel_body(const PlanDesc *plans, const St
     item = s_item;
     __syncthreads();
   }
+  int tab_plan = -1;   // the plan whose model tables the CTA's shared memory holds
   while (item < total) {
     const int pi = find_plan(st, item);
     const PlanDesc &P = plans[st.plan[pi]];
     const unsigned long long node = (unsigned long long)(item - st.prefix[pi]);
-    leaf_item<typename LeafModel<K>::type>(P, node, smem, red);
+    // persistent: the next item is taken now, its atomic's latency hidden by this item
+    unsigned long long nxt = 0;
+    if (st.counter && threadIdx.x == 0) nxt = atomicAdd(st.counter, 1ull);
+    leaf_item<typename LeafModel<K>::type>(P, node, smem, red, pi != tab_plan);
+    tab_plan = pi;
     if (st.counter) {
-      if (threadIdx.x == 0) s_item = (long long)atomicAdd(st.counter, 1ull);
+      if (threadIdx.x == 0) s_item = (long long)nxt;
       __syncthreads();
       item = s_item;
       __syncthreads();

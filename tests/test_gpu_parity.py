@@ -103,9 +103,12 @@ def test_wide_levels_full_tree(kind, N, D, W):
     _full(Spec(kind, N, D, W, seed=24, weights="random", root_seed=3), leaf_gen=False)
 
 
-def test_grid_enumerate_and_fixed_policy():
+@pytest.mark.parametrize("leaf_gen", [True, False])
+def test_grid_enumerate_and_fixed_policy(leaf_gen):
+    """Enumerated observations take every leaf branch through the log-domain sums, whose
+    log weights the grid leaf rebuilds from the parent's level (leaf_gen) or the node's own."""
     _full(Spec(WL.GRID, 96, 2, 3, branch_mode=WL.BRANCH_ENUMERATE, pi_mode=WL.PI_FIXED,
-               pi_fixed=[3, 1, 1, 1, 2, 1, 1, 1, 1, 1, 1, 1, 1], seed=7))
+               pi_fixed=[3, 1, 1, 1, 2, 1, 1, 1, 1, 1, 1, 1, 1], seed=7), leaf_gen=leaf_gen)
 
 
 def test_caller_pi_bar_overrides_model_policy():
