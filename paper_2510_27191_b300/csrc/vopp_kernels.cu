@@ -39,8 +39,9 @@ __device__ __forceinline__ void pdl_wait_prev() {
 //   GNode: a node's particles in a global level store (SoA x[N], y[N] / s[N], lw[N]); the
 //          linear weight is exp(lw).
 //   SNode: a node's particles in shared memory, pair-interleaved so that one 16-byte load
-//          gives both particles of a Philox pair: NAV2D {x0,x1,y0,y1}, GRID/TOY2 {s0,s1};
-//          then {lw0,lw1,w0,w1}.  Odd N pads the last pair with a zero-weight particle.
+//          gives both particles of a Philox pair: NAV2D {x0,x1,y0,y1}, TOY2 {s0,s1}, then
+//          {lw0,lw1,w0,w1}; GRID {w0,w1} then {s0,s1}.  Odd N pads the last pair with a
+//          zero-weight particle.
 // ---------------------------------------------------------------------------------------
 template <class M> struct GNode;
 template <> struct GNode<NavModel> {
