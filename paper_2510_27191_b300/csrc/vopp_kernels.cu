@@ -1744,14 +1744,18 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
 // same states and rewards as GridModel::step, which the other kernels use.  A move's or
 // collect's reading is NULL (Z = 1) and a sense reading good or bad; any other reading has
 // Z = 0 everywhere and is left to the log-domain path (false returned).
-struct GridSense { int rk, flip; const float2 *zc; };
-struct GridMove { int shift, lo, span, delta, at_lim; float r_lim; };
+// sense of rock rk: mask = the rock's bit, fm = mask when the reading is "good" (so that
+// (s ^ fm) & mask is nonzero exactly when the reading disagrees with the rock's bit: one
+// three-input logic op)
+struct GridSense { int mask, fm; const float2 *zc; };
+// move: the moved field in place (fmask), its blocking range's start and span shifted to it
+struct GridMove { int fmask, lo_s, span_s, delta, at_lim; float r_lim; };
 struct GridSums { float s0, s1, h1, rs; };
 
 
 __device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense &g, GridSums &t) {
   const int c = gcell(sv);
-  const int miss = ((sv >> g.rk) & 1) ^ g.flip;
+  const bool miss = ((sv ^ g.fm) & g.mask) != 0;
   const float2 zz = g.zc[c];
   const float z = miss ? zz.y : zz.x;
   const float wz = w * z;
@@ -1761,7 +1765,7 @@ __device__ __forceinline__ void grid_sense_one(int sv, float w, const GridSense 
 }
 __device__ __forceinline__ void grid_move_one(int sv, float w, const GridMove &g, GridSums &t) {
   const bool term = gterm(sv) != 0;
-  const bool blk = (unsigned)(((sv >> g.shift) & 0xF) - g.lo) <= (unsigned)g.span;
+  const bool blk = (unsigned)((sv & g.fmask) - g.lo_s) <= (unsigned)g.span_s;
   const int ns = term ? sv : sv + (blk ? g.at_lim : g.delta);
   const float r = (term || !blk) ? 0.0f : g.r_lim;
   t.s0 += 1.0f;
@@ -1862,7 +1866,7 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
   if (a >= 5) {
     if (o.o != 1 && o.o != 2) return false;
     const int rk = a - 5;
-    const GridSense g{rk, (o.o == 1) ? 1 : 0, s_grid_zc + rk * kGridCells};
+    const GridSense g{1 << rk, (o.o == 1) ? (1 << rk) : 0, s_grid_zc + rk * kGridCells};
     grid_pairs<false>(nb, N, [&](int sv, float w, GridSums &t) { grid_sense_one(sv, w, g, t); },
                       S0, S1, H, R);    // R stays 0: a sense action earns nothing
     return true;
@@ -1874,7 +1878,8 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
     return true;
   }
   // a = 0 E, 1 W, 2 N, 3 S; N is blocked at y >= 10
-  const GridMove g{(a < 2) ? 8 : 12, (a == 0 || a == 2) ? 10 : 0, (a == 2) ? 5 : 0,
+  const int sh = (a < 2) ? 8 : 12;
+  const GridMove g{0xF << sh, ((a == 0 || a == 2) ? 10 : 0) << sh, ((a == 2) ? 5 : 0) << sh,
                    (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000,
                    (a == 0) ? 0x10100 : 0, (a == 0) ? 10.0f : 0.0f};
   grid_pairs<true>(nb, N, [&](int sv, float w, GridSums &t) { grid_move_one(sv, w, g, t); },
