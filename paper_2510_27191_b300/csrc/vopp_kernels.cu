@@ -1748,7 +1748,9 @@ __device__ __forceinline__ void leaf_sums_log(const PlanDesc &P, const DevModel 
 // (s ^ fm) & mask is nonzero exactly when the reading disagrees with the rock's bit: one
 // three-input logic op)
 struct GridSense { int mask, fm; const float2 *zc; };
-// move: the moved field in place (fmask), its blocking range's start and span shifted to it
+// move: the moved field in place and the terminal bit (fmask), the blocking range's start
+// and span shifted to the field; a terminal state's masked value lies above every range, so
+// it is never blocked
 struct GridMove { int fmask, lo_s, span_s, delta, at_lim; float r_lim; };
 struct GridSums { float s0, s1, h1, rs; };
 
@@ -1767,7 +1769,7 @@ __device__ __forceinline__ void grid_move_one(int sv, float w, const GridMove &g
   const bool term = gterm(sv) != 0;
   const bool blk = (unsigned)((sv & g.fmask) - g.lo_s) <= (unsigned)g.span_s;
   const int ns = term ? sv : sv + (blk ? g.at_lim : g.delta);
-  const float r = (term || !blk) ? 0.0f : g.r_lim;
+  const float r = blk ? g.r_lim : 0.0f;
   t.s0 += 1.0f;
   t.s1 += w;
   t.h1 = fmaf(w, s_grid_hc[gcell(ns)], t.h1);
@@ -1879,7 +1881,7 @@ __device__ __forceinline__ bool grid_branch_sums(const PlanDesc &P, const DevMod
   }
   // a = 0 E, 1 W, 2 N, 3 S; N is blocked at y >= 10
   const int sh = (a < 2) ? 8 : 12;
-  const GridMove g{0xF << sh, ((a == 0 || a == 2) ? 10 : 0) << sh, ((a == 2) ? 5 : 0) << sh,
+  const GridMove g{(0xF << sh) | 0x10000, ((a == 0 || a == 2) ? 10 : 0) << sh, ((a == 2) ? 5 : 0) << sh,
                    (a == 0) ? 0x100 : (a == 1) ? -0x100 : (a == 2) ? 0x1000 : -0x1000,
                    (a == 0) ? 0x10100 : 0, (a == 0) ? 10.0f : 0.0f};
   grid_pairs<true>(nb, N, [&](int sv, float w, GridSums &t) { grid_move_one(sv, w, g, t); },
