@@ -35,7 +35,10 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
               autotune: bool = True, graphs: bool = True):
     """Returns a dict with the batched and sequential times (CUDA events around each).
     graphs: the batch replays its recorded launch sequence (the sequential plans always
-    launch stage by stage); the context's graph option is left off."""
+    launch stage by stage); the context's graph option is left off.  autotune: both times use
+    the leaf CTA size and scheduling the tuner picks for this batch; the context's defaults
+    (128 threads, per-model scheduling) are put back afterwards, so that later single plans
+    on the context do not inherit a choice made for the mixed batch."""
     import torch
     specs = WL.draw_mixed_plans(n_plans, seed)
     models = make_models(V, ctx)
@@ -77,6 +80,9 @@ def batch_run(V, ctx, n_plans: int = 512, seed: int = 7, reps: int = 2, sequenti
                     "batched_equals_sequential": bool(same)})
     for m in models.values():
         V.vopp_model_destroy(m)
+    if autotune:
+        V.vopp_ctx_set_option(ctx, V.VOPP_OPT_LEAF_THREADS, 128)
+        V.vopp_ctx_set_option(ctx, V.VOPP_OPT_PERSISTENT, 2)
     return res
 
 
