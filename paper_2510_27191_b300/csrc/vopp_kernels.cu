@@ -1277,12 +1277,33 @@ __device__ __forceinline__ void grid_child_unit(int (&sv)[V], float (&r)[V], flo
 #ifndef VOPP_EXPAND_UNROLL2
 #define VOPP_EXPAND_UNROLL2 4
 #endif
+// Parent units a lane keeps in flight in pass 1 of a GRID / TOY2 child (4-particle units):
+// config 3's level 3 took 275 us with plain loads, 230 / 224 / 234 us with 2 / 4 / 6.
+#ifndef VOPP_K2_RING
+#define VOPP_K2_RING 4
+#endif
 constexpr int kExpandUnroll1 = VOPP_EXPAND_UNROLL1, kExpandUnroll2 = VOPP_EXPAND_UNROLL2;
 // Running sums of a child's pass 1 (per lane).
 struct ChildPass {
   Kahan R, S1, S0, MX, MY;
   float m1, m0;
 };
+
+// Asynchronous 16-byte copies from global into shared memory (cp.async, through L2 only),
+// committed and waited for by group; each lane reads back only what it copied itself.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+// Per warp of a vectorised expansion: kRing slots × (states, log weights) × 32 lanes of one
+// 4-particle unit each.  The loop's loads were its latency: with the next kRing - 1 units of
+// a lane already on their way, no register holds them meanwhile.
+constexpr int kRing = VOPP_K2_RING;
+__shared__ __align__(16) uint4 s_ring[kExpandVecWarps][kRing][2][32];
 
 // Pass 1 of a child over this lane's units (GK: the GRID action case, -1 for the generic
 // step of the other models).
@@ -1300,17 +1321,46 @@ __device__ __forceinline__ void child_pass1(const PlanDesc &P, const DevModel &d
   float *dx = kNavM ? P.px[l + 1] + cb : nullptr, *dy = kNavM ? P.py[l + 1] + cb : nullptr;
   const int *ss = kNavM ? nullptr : P.ps[l] + pb;
   int *ds = kNavM ? nullptr : P.ps[l + 1] + cb;
+  // GRID / TOY2 with 4-particle units: the parent's states and log weights through the ring
+  constexpr bool kRingOn = !kNavM && V == 4;
+  if constexpr (kRingOn) {
+#pragma unroll
+    for (int k = 0; k < kRing - 1; ++k) {
+      const int u = lane + 32 * k;
+      if (u < units) {
+        cp_async16(&s_ring[threadIdx.x >> 5][k][0][lane], ss + 4 * u);
+        cp_async16(&s_ring[threadIdx.x >> 5][k][1][lane], plw + 4 * u);
+      }
+      cp_commit();   // (an empty group past the last unit keeps the count uniform)
+    }
+  }
 #pragma unroll kExpandUnroll1
   for (int u = lane; u < units; u += 32) {
     const int i0 = u * V;
     float lw[V], r[V], e[V], X[V], Y[V];
     int sv[V];
-    ldg_v<V>(plw + i0, lw);
-    if constexpr (kNavM) {
-      ldg_v<V>(sx + i0, X);
-      ldg_v<V>(sy + i0, Y);
+    if constexpr (kRingOn) {
+      // unit u is this lane's iteration it; the slot refilled now held iteration it - 1
+      const int it = u >> 5, un = u + 32 * (kRing - 1), sn = (it + kRing - 1) % kRing;
+      uint4 (*ring)[2][32] = s_ring[threadIdx.x >> 5];
+      if (un < units) {
+        cp_async16(&ring[sn][0][lane], ss + 4 * un);
+        cp_async16(&ring[sn][1][lane], plw + 4 * un);
+      }
+      cp_commit();
+      cp_wait<kRing - 1>();   // all but the newest kRing - 1 groups: unit u has landed
+      const uint4 a4 = ring[it % kRing][0][lane], b4 = ring[it % kRing][1][lane];
+      sv[0] = (int)a4.x; sv[1] = (int)a4.y; sv[2] = (int)a4.z; sv[3] = (int)a4.w;
+      lw[0] = __uint_as_float(b4.x); lw[1] = __uint_as_float(b4.y);
+      lw[2] = __uint_as_float(b4.z); lw[3] = __uint_as_float(b4.w);
     } else {
-      ldg_v<V>(ss + i0, sv);
+      ldg_v<V>(plw + i0, lw);
+      if constexpr (kNavM) {
+        ldg_v<V>(sx + i0, X);
+        ldg_v<V>(sy + i0, Y);
+      } else {
+        ldg_v<V>(ss + i0, sv);
+      }
     }
     if constexpr (kNavM) {
       nav_unit<V>(X, Y, r, e, u, a, c1, kn, P.key0, P.key1, o, dm);
